@@ -1,0 +1,100 @@
+"""KKR tau_00 oracle -- TEST INFRASTRUCTURE ONLY.
+
+Sec. 3.2 of the paper: the dominant cost of the LSMS method is the LU-based inversion of
+the multiple scattering matrix at each point of the complex energy contour, done with
+ZGEMM and ZTRSM.  The quantity the inversion yields for an atom is the central block of
+the scattering-path matrix; with the standard KKR convention (the paper does not write
+the formula) it is
+
+    M = I - t G,   tau = M^-1 t,   tau_00 = [M^-1]_00 t_0,
+
+with t block diagonal (one b x b block per LIZ site, site 0 the centre) and G the
+structure-constant matrix with zero diagonal blocks.
+
+Two oracles:
+
+* ``tau00_full`` inverts M by textbook Gauss-Jordan elimination with partial pivoting in
+  binary64 and takes the (0, 0) block times t_0.
+* ``tau00_block`` is the block-LU algorithm of the GPU path written out: the centre block
+  is ordered last, panels of width nb are eliminated right-looking with no pivoting
+  across panels (partial pivoting only inside the inverse of each pivot block), every
+  panel product and trailing update is an emulated ZGEMM (or a binary64 matmul when
+  S is None), and tau_00 = S_00^-1 t_0 with S_00 the Schur complement left in the centre.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import ozaki
+
+
+class SingularError(ArithmeticError):
+    pass
+
+
+def gepp_inverse(M: np.ndarray) -> np.ndarray:
+    """Gauss-Jordan inverse with partial pivoting (largest modulus in the column)."""
+    M = np.asarray(M, dtype=np.complex128)
+    n = M.shape[0]
+    A = np.concatenate([M.copy(), np.eye(n, dtype=np.complex128)], axis=1)
+    for p in range(n):
+        piv = p + int(np.argmax(np.abs(A[p:, p])))
+        if A[piv, p] == 0:
+            raise SingularError(f"zero pivot in column {p}")
+        if piv != p:
+            A[[p, piv]] = A[[piv, p]]
+        A[p] = A[p] / A[p, p]
+        col = A[:, p].copy()
+        col[p] = 0
+        A -= np.outer(col, A[p])
+    return A[:, n:]
+
+
+def tau00_full(M: np.ndarray, t0: np.ndarray) -> np.ndarray:
+    b = t0.shape[0]
+    return gepp_inverse(M)[:b, :b] @ t0
+
+
+def center_last(M: np.ndarray, b: int) -> np.ndarray:
+    n = M.shape[0]
+    perm = np.concatenate([np.arange(b, n), np.arange(0, b)])
+    return M[np.ix_(perm, perm)]
+
+
+def tau00_block(M: np.ndarray, t0: np.ndarray, nb: int, S=None, mode: str = "tri") -> np.ndarray:
+    """Right-looking block LU with the centre last (see module docstring)."""
+    b = t0.shape[0]
+    A = np.array(center_last(np.asarray(M, dtype=np.complex128), b))
+    n = A.shape[0]
+    m0 = n - b
+
+    def mul(X, Y):
+        return X @ Y if S is None else ozaki.ozaki_zgemm(X, Y, S, mode)
+
+    def sub_mul(C, X, Y):
+        return C - X @ Y if S is None else ozaki.ozaki_lu_update(C, X, Y, S, mode)
+
+    p = 0
+    while p < m0:
+        q = min(p + nb, m0)
+        Dinv = gepp_inverse(A[p:q, p:q])
+        A[q:, p:q] = mul(A[q:, p:q], Dinv)                 # L panel  = M_RJ D^-1
+        A[q:, q:] = sub_mul(A[q:, q:], A[q:, p:q], A[p:q, q:])   # Schur update
+        p = q
+    S00 = A[m0:, m0:]
+    return gepp_inverse(S00) @ t0
+
+
+def kkr_build(t: np.ndarray, G: np.ndarray) -> np.ndarray:
+    """M = I - blockdiag(t) G, binary64."""
+    L, b, _ = t.shape
+    n = L * b
+    M = -np.einsum("lij,ljn->lin", t, G.reshape(L, b, n)).reshape(n, n)
+    M[np.arange(n), np.arange(n)] += 1.0
+    return M
+
+
+def rel_err(X: np.ndarray, Y: np.ndarray) -> float:
+    """Relative Frobenius error ||X - Y||_F / ||Y||_F."""
+    d = np.linalg.norm(Y)
+    return float(np.linalg.norm(X - Y) / d) if d else float(np.linalg.norm(X))
