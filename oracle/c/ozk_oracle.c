@@ -332,27 +332,20 @@ static void put_block(double* dst, int ldd, int r0, int c0, int rows, int cols, 
         memcpy(dst + 2 * ((long)(r0 + i) * ldd + c0), src + 2 * (long)i * cols, sizeof(double) * 2 * (size_t)cols);
 }
 
-/* tau_00 = S00^-1 t0 by right-looking block LU with the centre block ordered last.
- * M is n x n (site 0 = rows/cols 0..b-1), t0 is b x b.  S = 0: binary64 GEMMs,
- * S > 0: every panel product and trailing update is the emulated ZGEMM with S slices. */
+/* tau_00 = S00^-1 t0 by block LU: panels J = [p, q) are eliminated from the trailing end
+ * of M towards the front, so the remainder is always the leading block R = [0, p) and the
+ * centre block (site 0, rows/cols 0..b-1) is eliminated last:
+ *     L_RJ = M_RJ D^-1,  M_RR -= L_RJ M_JR,  D = M_JJ (Gauss-Jordan inverse, partial pivoting).
+ * S = 0: binary64 GEMMs; S > 0: every panel product and update is the emulated ZGEMM. */
 int oz_tau00_block(const double* M, const double* t0, int n, int b, int nb, int S, int full,
                    double* tau) {
     if (n <= 0 || b <= 0 || n % b || nb <= 0) return OZ_ERR_ARG;
     double* A = (double*)malloc(sizeof(double) * 2 * (size_t)n * n);
-    /* reorder: sites 1..L-1 first, then site 0 */
-    for (int i = 0; i < n; i++) {
-        int si = i < n - b ? i + b : i - (n - b);
-        for (int j = 0; j < n; j++) {
-            int sj = j < n - b ? j + b : j - (n - b);
-            A[2 * ((long)i * n + j)] = M[2 * ((long)si * n + sj)];
-            A[2 * ((long)i * n + j) + 1] = M[2 * ((long)si * n + sj) + 1];
-        }
-    }
-    const int m0 = n - b;
+    memcpy(A, M, sizeof(double) * 2 * (size_t)n * n);
     int st = OZ_OK;
-    for (int p = 0; p < m0 && !st; p += nb) {
-        int q = p + nb < m0 ? p + nb : m0;
-        int w = q - p, r = n - q;
+    for (int q = n; q > b && !st;) {
+        int p = q - nb > b ? q - nb : b;
+        int w = q - p, r = p;
         double* D = (double*)malloc(sizeof(double) * 2 * (size_t)w * w);
         double* Lp = (double*)malloc(sizeof(double) * 2 * (size_t)r * w);
         double* Up = (double*)malloc(sizeof(double) * 2 * (size_t)w * r);
@@ -361,12 +354,12 @@ int oz_tau00_block(const double* M, const double* t0, int n, int b, int nb, int 
         copy_block(A, n, p, p, w, w, D);
         st = oz_gepp_inverse(D, w);
         if (!st) {
-            copy_block(A, n, q, p, r, w, Lp);
+            copy_block(A, n, 0, p, r, w, Lp);
             if (S > 0) st = oz_zgemm(Lp, D, r, w, w, S, full, 0, T);
             else oz_zgemm_fp64(Lp, D, r, w, w, T);
-            put_block(A, n, q, p, r, w, T);
-            copy_block(A, n, p, q, w, r, Up);
-            copy_block(A, n, q, q, r, r, Cr);
+            put_block(A, n, 0, p, r, w, T);
+            copy_block(A, n, p, 0, w, r, Up);
+            copy_block(A, n, 0, 0, r, r, Cr);
             if (!st) {
                 if (S > 0) st = oz_zgemm(T, Up, r, r, w, S, full, 1, Cr);
                 else {
@@ -375,14 +368,15 @@ int oz_tau00_block(const double* M, const double* t0, int n, int b, int nb, int 
                     for (long x = 0; x < 2L * r * r; x++) Cr[x] -= P[x];
                     free(P);
                 }
-                put_block(A, n, q, q, r, r, Cr);
+                put_block(A, n, 0, 0, r, r, Cr);
             }
         }
         free(D); free(Lp); free(Up); free(Cr); free(T);
+        q = p;
     }
     if (!st) {
         double* S00 = (double*)malloc(sizeof(double) * 2 * (size_t)b * b);
-        copy_block(A, n, m0, m0, b, b, S00);
+        copy_block(A, n, 0, 0, b, b, S00);
         st = oz_gepp_inverse(S00, b);
         if (!st) oz_zgemm_fp64(S00, t0, b, b, b, tau);
         free(S00);

@@ -15,11 +15,15 @@ Two oracles:
 
 * ``tau00_full`` inverts M by textbook Gauss-Jordan elimination with partial pivoting in
   binary64 and takes the (0, 0) block times t_0.
-* ``tau00_block`` is the block-LU algorithm of the GPU path written out: the centre block
-  is ordered last, panels of width nb are eliminated right-looking with no pivoting
-  across panels (partial pivoting only inside the inverse of each pivot block), every
-  panel product and trailing update is an emulated ZGEMM (or a binary64 matmul when
-  S is None), and tau_00 = S_00^-1 t_0 with S_00 the Schur complement left in the centre.
+* ``tau00_block`` is the block-LU algorithm of the GPU path written out.  The centre
+  block (site 0, the leading b x b block) is eliminated last: panels J of width nb are
+  eliminated from the trailing end of the matrix towards the front, so that what remains
+  after each step is the leading r x r block R = [0, r).  Each step computes
+      L_RJ = M_RJ D^-1,   M_RR <- M_RR - L_RJ M_JR,   D = M_JJ,
+  with no pivoting across panels (partial pivoting only inside the inverse of each pivot
+  block).  Every panel product and every Schur update is an emulated ZGEMM (or a
+  binary64 matmul when S is None), and tau_00 = S_00^-1 t_0 with S_00 the Schur
+  complement left in the centre block.
 """
 from __future__ import annotations
 
@@ -55,18 +59,11 @@ def tau00_full(M: np.ndarray, t0: np.ndarray) -> np.ndarray:
     return gepp_inverse(M)[:b, :b] @ t0
 
 
-def center_last(M: np.ndarray, b: int) -> np.ndarray:
-    n = M.shape[0]
-    perm = np.concatenate([np.arange(b, n), np.arange(0, b)])
-    return M[np.ix_(perm, perm)]
-
-
 def tau00_block(M: np.ndarray, t0: np.ndarray, nb: int, S=None, mode: str = "tri") -> np.ndarray:
-    """Right-looking block LU with the centre last (see module docstring)."""
+    """Block LU eliminating from the trailing end, the centre block last (see module docstring)."""
     b = t0.shape[0]
-    A = np.array(center_last(np.asarray(M, dtype=np.complex128), b))
+    A = np.array(M, dtype=np.complex128)
     n = A.shape[0]
-    m0 = n - b
 
     def mul(X, Y):
         return X @ Y if S is None else ozaki.ozaki_zgemm(X, Y, S, mode)
@@ -74,15 +71,14 @@ def tau00_block(M: np.ndarray, t0: np.ndarray, nb: int, S=None, mode: str = "tri
     def sub_mul(C, X, Y):
         return C - X @ Y if S is None else ozaki.ozaki_lu_update(C, X, Y, S, mode)
 
-    p = 0
-    while p < m0:
-        q = min(p + nb, m0)
+    q = n                                   # eliminate J = [p, q), keep R = [0, p)
+    while q > b:
+        p = max(q - nb, b)
         Dinv = gepp_inverse(A[p:q, p:q])
-        A[q:, p:q] = mul(A[q:, p:q], Dinv)                 # L panel  = M_RJ D^-1
-        A[q:, q:] = sub_mul(A[q:, q:], A[q:, p:q], A[p:q, q:])   # Schur update
-        p = q
-    S00 = A[m0:, m0:]
-    return gepp_inverse(S00) @ t0
+        A[:p, p:q] = mul(A[:p, p:q], Dinv)                     # L panel = M_RJ D^-1
+        A[:p, :p] = sub_mul(A[:p, :p], A[:p, p:q], A[p:q, :p])  # Schur update of R
+        q = p
+    return gepp_inverse(A[:b, :b]) @ t0
 
 
 def kkr_build(t: np.ndarray, G: np.ndarray) -> np.ndarray:
