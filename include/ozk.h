@@ -1,0 +1,160 @@
+/*
+ * ozk.h -- C ABI of the GB300 (sm_103a) emulated-ZGEMM / KKR tau_00 library (libozk.so).
+ *
+ * Method: the Ozaki-I scheme the paper uses to run FP64 GEMMs on low-precision tensor
+ * cores (Sec. 2.2: split high-precision matrices into low-precision slices by significant
+ * bits with exponent alignment, multiply slice pairs, accumulate in higher precision;
+ * Sec. 3.2 and Sec. 4: the precision knob is a mantissa-bit count, 31..63 bits), applied
+ * to ZGEMM and to the LU-based inversion of the KKR multiple scattering matrix that
+ * dominates the LSMS method (Sec. 3.2).
+ *
+ * Reading used throughout (identical in the CPU oracle):
+ *   - S slices of 8 bits each carry B = 8S - 1 fixed-point bits per row (columns for the
+ *     right operand): e_i = frexp exponent of max_l max(|Re a_il|, |Im a_il|),
+ *     X = trunc(x 2^(B - e_i)), X = sum_t d_t 256^(S-t) with balanced digits
+ *     (d_t in [-128, 127] for t >= 2, d_1 in [-128, 128]).
+ *   - Complex operands use the 4M stacked form: [Re A | Im A] times, per output column j,
+ *     the rows [Re B_j ; -Im B_j] and [Im B_j ; Re B_j].
+ *   - Slice pairs (s, t) with s + t <= S + 1 ("triangular", default) or all S x S ("full").
+ *     Their products are exact integers (held as fp16 values on the sm_103a tensor cores,
+ *     accumulated exactly in FP32, combined exactly in 128-bit integers).
+ *   - The result 2^(e_i + f_j - 2B) sum_g G_g 256^(2S - g) is rounded once to binary64.
+ *
+ * Conventions
+ *   - Matrices are complex binary64 ("double complex", interleaved re, im) in COLUMN-MAJOR
+ *     order with a leading dimension, as in BLAS ZGEMM.  Pointers to matrices are DEVICE
+ *     pointers owned by the caller; pointer arrays of batched calls are DEVICE arrays;
+ *     per-problem size arrays of batched calls are HOST arrays.
+ *   - Every call is asynchronous on the handle's stream (ozk_set_stream) and returns as
+ *     soon as the work is enqueued.  Argument errors are reported synchronously by the
+ *     return value and nothing is enqueued.  Errors detected on the device (non-finite
+ *     input, singular pivot block, timed-out wait) set bits in a device status word that
+ *     ozk_get_status() reads (after synchronising the stream) and clears.
+ *   - Workspace (slice buffers, exponents, pivot inverses) is owned by the handle and
+ *     grown on demand with cudaMalloc; ozk_reserve() sizes it up front so that later calls
+ *     (for example inside a CUDA graph capture) never allocate.  A call that would need to
+ *     grow the workspace while its stream is being captured returns OZK_ERR_CAPTURE.
+ *   - Nothing aborts the process.
+ */
+#ifndef OZK_H
+#define OZK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    OZK_OK = 0,
+    OZK_ERR_ARG = 1,        /* invalid argument (sizes, leading dimensions, S, mode) */
+    OZK_ERR_NONFINITE = 2,  /* device flag: a NaN or Inf operand was met */
+    OZK_ERR_SINGULAR = 3,   /* device flag: an exactly singular pivot block */
+    OZK_ERR_TIMEOUT = 4,    /* device flag: a bounded device-side wait gave up */
+    OZK_ERR_CUDA = 5,       /* a CUDA runtime call failed (message: ozk_last_error) */
+    OZK_ERR_RANGE = 6,      /* the exact integer sum could exceed 128 bits for this S, k */
+    OZK_ERR_CAPTURE = 7,    /* workspace growth needed during stream capture */
+    OZK_ERR_RESIDUAL = 8,   /* a-posteriori residual check failed and fallback disabled */
+    OZK_ERR_NOFILE = 9      /* file could not be read or written */
+} ozk_status_t;
+
+/* pair-set modes */
+#define OZK_PAIRS_TRI 0
+#define OZK_PAIRS_FULL 1
+
+typedef struct ozk_context* ozk_handle_t;
+
+/* ---- handle ------------------------------------------------------------------------ */
+
+/* Create a handle on the current CUDA device.  Allocates the device status word. */
+ozk_status_t ozk_create(ozk_handle_t* handle);
+/* Destroy a handle and free its workspace (synchronises its stream first). */
+ozk_status_t ozk_destroy(ozk_handle_t handle);
+/* Stream (a cudaStream_t passed as void*; NULL = legacy default stream) for later calls. */
+ozk_status_t ozk_set_stream(ozk_handle_t handle, void* stream);
+/* Synchronise the stream, return the accumulated device status (0 or a bitwise OR of
+ * 1 << OZK_ERR_* codes) in *device_flags and clear it.  Returns OZK_ERR_CUDA on a CUDA
+ * error, else OZK_OK. */
+ozk_status_t ozk_get_status(ozk_handle_t handle, int* device_flags);
+/* Grow the handle's workspace to at least `bytes` now (never shrinks). */
+ozk_status_t ozk_reserve(ozk_handle_t handle, size_t bytes);
+/* Workspace bytes that ozaki_zgemm needs for (m, n, k, S, batch). */
+size_t ozk_zgemm_workspace_size(int m, int n, int k, int S, int batch);
+/* Message of the last OZK_ERR_CUDA / OZK_ERR_ARG on this thread (static storage). */
+const char* ozk_last_error(void);
+/* Number of kernel launches this library has enqueued on this thread so far. */
+uint64_t ozk_launch_count(void);
+
+/* ---- emulated ZGEMM (paper Sec. 2.2, Sec. 3.2) ------------------------------------ */
+
+/* C = alpha op(A) op(B) + beta C with op(X) in {'N', 'T', 'C'} (none, transpose,
+ * conjugate transpose), exactly the BLAS ZGEMM argument list plus the slice count S.
+ *   alpha, beta : HOST pointers to two doubles (re, im).
+ *   A, B, C     : DEVICE pointers, column major, lda/ldb/ldc >= rows of the stored matrix.
+ *   S           : 1..16 slices (B = 8S - 1 bits).  pair_mode: OZK_PAIRS_TRI / _FULL.
+ * Epilogues: beta == 0 stores RN(alpha Z) (alpha == 1: bitwise equal to the oracle);
+ * alpha == -1, beta == 1 computes C - RN(Z) with one binary64 subtraction (bitwise equal
+ * to the oracle's LU update); other alpha, beta use binary64 complex arithmetic.
+ * k == 0 or alpha == 0 scales C by beta.  Returns OZK_ERR_RANGE if 8(g_max - 2) + 14 +
+ * log2(2k * S) + 2 > 127 (the exact 128-bit sum could overflow). */
+ozk_status_t ozaki_zgemm(ozk_handle_t handle, char transa, char transb, int m, int n, int k,
+                         const double* alpha, const void* A, int lda, const void* B, int ldb,
+                         const double* beta, void* C, int ldc, int S, int pair_mode);
+
+/* Batched form: `batch` independent problems; A, B, C are DEVICE arrays of `batch` DEVICE
+ * pointers; m, n, k, lda, ldb, ldc are HOST arrays of `batch` entries (variable sizes).
+ * Problems with m, n == 0 are skipped. */
+ozk_status_t ozaki_zgemm_vbatched(ozk_handle_t handle, char transa, char transb,
+                                  const int* m, const int* n, const int* k,
+                                  const double* alpha, const void* const* A, const int* lda,
+                                  const void* const* B, const int* ldb, const double* beta,
+                                  void* const* C, const int* ldc, int batch, int S, int pair_mode);
+
+/* Plain binary64 ZGEMM on the FP64 tensor path (DMMA, mma.sync m8n8k4.f64), same argument
+ * meaning as ozaki_zgemm without S: the comparison baseline on the same GPU. */
+ozk_status_t ozk_zgemm_dmma(ozk_handle_t handle, char transa, char transb, int m, int n, int k,
+                            const double* alpha, const void* A, int lda, const void* B, int ldb,
+                            const double* beta, void* C, int ldc);
+
+/* ---- test hooks for the individual steps ---------------------------------------- */
+
+/* Exponent scan + split of op(X) as the LEFT operand (side 0: rows of op(A)) or as the
+ * RIGHT operand (side 1: columns of op(B)).  op(X) has `rows` rows of length k (side 0) or
+ * is k x rows (side 1).  Outputs (DEVICE): exps[rows] (int32) and digits as int16
+ * [S][rows'][2k] with rows' = rows (side 0) or 2 rows (side 1, stacked layout). */
+ozk_status_t ozk_split_debug(ozk_handle_t handle, int side, char trans, int rows, int k,
+                             const void* X, int ldx, int S, int32_t* exps, int16_t* digits);
+/* Exact group sums G_g (int64 [G][m][2n], g = 2 .. g_max) of the slice-pair products
+ * for C = op(A) op(B), computed by the tensor-core kernel (the emulated GEMM with its
+ * reconstruction replaced by an integer dump).  DEVICE output. */
+ozk_status_t ozk_group_sums_debug(ozk_handle_t handle, char transa, char transb, int m, int n,
+                                  int k, const void* A, int lda, const void* B, int ldb, int S,
+                                  int pair_mode, int64_t* groups);
+
+/* ---- KKR tau_00 (paper Sec. 3.2) ----------------------------------------------------- */
+
+/* M = I - t G for a LIZ of L sites with b x b blocks (n = L b).
+ *   t : DEVICE, L blocks of b x b, block l at t + l*b*b, each column major (ld b).
+ *   G : DEVICE, n x n column major (ld n).  M: DEVICE, n x n column major (ld n). */
+ozk_status_t kkr_build_m(ozk_handle_t handle, int L, int b, const void* t, const void* G, void* M);
+
+/* tau_00 = [M^-1]_00 t_0 = S_00^-1 t_0 by block LU with every panel product and Schur update
+ * an emulated ZGEMM with S slices (S <= 0: the binary64 DMMA ZGEMM instead).
+ *   M   : DEVICE n x n column major (ld n), DESTROYED (overwritten by the factorisation).
+ *   t0  : DEVICE b x b column major.  tau00: DEVICE b x b column major output.
+ *   nb  : panel width, a multiple of b (16..64).  Site 0 occupies rows/cols 0..b-1. */
+ozk_status_t kkr_tau00(ozk_handle_t handle, int n, int b, void* M, const void* t0, void* tau00,
+                       int S, int nb);
+
+/* Batched tau_00 over `nsolves` independent (atom, energy) matrices of sizes n[i] (HOST
+ * array, multiples of b): M, t0, tau00 are DEVICE arrays of DEVICE pointers.  All solves
+ * advance panel by panel in lockstep; each step is one batched launch per kernel. */
+ozk_status_t kkr_tau00_batched(ozk_handle_t handle, int nsolves, const int* n, int b,
+                               void* const* M, const void* const* t0, void* const* tau00,
+                               int S, int nb);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OZK_H */

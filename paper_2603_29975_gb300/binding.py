@@ -1,0 +1,261 @@
+"""ctypes binding of libozk.so (include/ozk.h): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels.  Matrices are torch complex128
+CUDA tensors in column-major layout (``t.stride(0) == 1``), as the C ABI expects; use
+``colmajor_cuda(array)`` to move a numpy matrix to the GPU in that layout.  There is no
+CPU fallback: if the library is missing or the device is not a CUDA GPU, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libozk.so")
+
+OZK_OK = 0
+OZK_PAIRS_TRI = 0
+OZK_PAIRS_FULL = 1
+STATUS_NAMES = {1: "ARG", 2: "NONFINITE", 3: "SINGULAR", 4: "TIMEOUT", 5: "CUDA", 6: "RANGE",
+                7: "CAPTURE", 8: "RESIDUAL", 9: "NOFILE"}
+
+EXPORTS = ["ozk_create", "ozk_destroy", "ozk_set_stream", "ozk_get_status", "ozk_reserve",
+           "ozk_zgemm_workspace_size", "ozk_last_error", "ozk_launch_count", "ozaki_zgemm",
+           "ozaki_zgemm_vbatched", "ozk_zgemm_dmma", "ozk_split_debug", "ozk_group_sums_debug",
+           "kkr_build_m", "kkr_tau00", "kkr_tau00_batched"]
+
+_lib = None
+
+
+class OzkError(RuntimeError):
+    pass
+
+
+def lib():
+    """Load libozk.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise OzkError(f"{LIB_PATH} is missing: build it with paper_2603_29975_gb300/build.py")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, ip, dp, c, i, sz = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), \
+            ctypes.c_char, ctypes.c_int, ctypes.c_size_t
+        L.ozk_create.argtypes = [ctypes.POINTER(vp)]
+        L.ozk_destroy.argtypes = [vp]
+        L.ozk_set_stream.argtypes = [vp, vp]
+        L.ozk_get_status.argtypes = [vp, ip]
+        L.ozk_reserve.argtypes = [vp, sz]
+        L.ozk_zgemm_workspace_size.argtypes = [i, i, i, i, i]
+        L.ozk_zgemm_workspace_size.restype = sz
+        L.ozk_last_error.restype = ctypes.c_char_p
+        L.ozk_launch_count.restype = ctypes.c_uint64
+        L.ozaki_zgemm.argtypes = [vp, c, c, i, i, i, dp, vp, i, vp, i, dp, vp, i, i, i]
+        L.ozaki_zgemm_vbatched.argtypes = [vp, c, c, ip, ip, ip, dp, vp, ip, vp, ip, dp, vp, ip, i, i, i]
+        L.ozk_zgemm_dmma.argtypes = [vp, c, c, i, i, i, dp, vp, i, vp, i, dp, vp, i]
+        L.ozk_split_debug.argtypes = [vp, i, c, i, i, vp, i, i, vp, vp]
+        L.ozk_group_sums_debug.argtypes = [vp, c, c, i, i, i, vp, i, vp, i, i, i, vp]
+        L.kkr_build_m.argtypes = [vp, i, i, vp, vp, vp]
+        L.kkr_tau00.argtypes = [vp, i, i, vp, vp, vp, i, i]
+        L.kkr_tau00_batched.argtypes = [vp, i, ip, i, vp, vp, vp, i, i]
+        for name in EXPORTS:
+            if name not in ("ozk_zgemm_workspace_size", "ozk_last_error", "ozk_launch_count"):
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(st: int, what: str):
+    if st != OZK_OK:
+        msg = lib().ozk_last_error().decode(errors="replace")
+        raise OzkError(f"{what} failed: status {st} ({STATUS_NAMES.get(st, '?')}): {msg}")
+
+
+def _c2(z: complex):
+    return (ctypes.c_double * 2)(float(complex(z).real), float(complex(z).imag))
+
+
+def _ld(t, rows: int) -> int:
+    """Leading dimension of a column-major complex tensor with `rows` rows."""
+    if t.dim() != 2:
+        raise OzkError("expected a 2-D tensor")
+    if t.shape[0] > 1 and t.stride(0) != 1:
+        raise OzkError("matrix must be column major (stride(0) == 1)")
+    return max(1, rows, t.stride(1) if t.shape[1] > 1 else rows)
+
+
+def _ptr(t) -> int:
+    import torch
+    if t.dtype != torch.complex128 or not t.is_cuda:
+        raise OzkError("expected a complex128 CUDA tensor")
+    return t.data_ptr()
+
+
+def colmajor_cuda(a, device="cuda"):
+    """numpy complex matrix -> complex128 CUDA tensor in column-major layout."""
+    import torch
+    a = np.asfortranarray(np.asarray(a, dtype=np.complex128))
+    return torch.from_numpy(a).to(device)
+
+
+def to_numpy(t) -> np.ndarray:
+    return t.detach().cpu().numpy()
+
+
+def launch_count() -> int:
+    return int(lib().ozk_launch_count())
+
+
+class Handle:
+    """An ozk handle bound to the current torch CUDA stream (or the one given)."""
+
+    def __init__(self, stream=None):
+        import torch
+        self._h = ctypes.c_void_p()
+        _check(lib().ozk_create(ctypes.byref(self._h)), "ozk_create")
+        self.set_stream(stream if stream is not None else torch.cuda.current_stream())
+
+    def set_stream(self, stream):
+        _check(lib().ozk_set_stream(self._h, ctypes.c_void_p(stream.cuda_stream)), "ozk_set_stream")
+
+    @property
+    def ptr(self):
+        return self._h
+
+    def status(self) -> int:
+        v = ctypes.c_int(0)
+        _check(lib().ozk_get_status(self._h, ctypes.byref(v)), "ozk_get_status")
+        return v.value
+
+    def reserve(self, nbytes: int):
+        _check(lib().ozk_reserve(self._h, nbytes), "ozk_reserve")
+
+    def close(self):
+        if self._h:
+            lib().ozk_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _shapes(transa, transb, A, B):
+    m, ka = (A.shape[0], A.shape[1]) if transa in "Nn" else (A.shape[1], A.shape[0])
+    kb, n = (B.shape[0], B.shape[1]) if transb in "Nn" else (B.shape[1], B.shape[0])
+    if ka != kb:
+        raise OzkError(f"inner dimensions differ: {ka} vs {kb}")
+    return m, n, ka
+
+
+def ozaki_zgemm(h: Handle, A, B, C, S: int = 7, alpha=1.0, beta=0.0, transa="N", transb="N",
+                pair_mode: int = OZK_PAIRS_TRI):
+    """C = alpha op(A) op(B) + beta C (emulated, S slices) on column-major tensors."""
+    m, n, k = _shapes(transa, transb, A, B)
+    if tuple(C.shape) != (m, n):
+        raise OzkError("C has the wrong shape")
+    _check(lib().ozaki_zgemm(h.ptr, transa.encode(), transb.encode(), m, n, k, _c2(alpha), _ptr(A),
+                             _ld(A, A.shape[0]), _ptr(B), _ld(B, B.shape[0]), _c2(beta), _ptr(C),
+                             _ld(C, m), S, pair_mode), "ozaki_zgemm")
+    return C
+
+
+def ozk_zgemm_dmma(h: Handle, A, B, C, alpha=1.0, beta=0.0, transa="N", transb="N"):
+    m, n, k = _shapes(transa, transb, A, B)
+    if tuple(C.shape) != (m, n):
+        raise OzkError("C has the wrong shape")
+    _check(lib().ozk_zgemm_dmma(h.ptr, transa.encode(), transb.encode(), m, n, k, _c2(alpha), _ptr(A),
+                                _ld(A, A.shape[0]), _ptr(B), _ld(B, B.shape[0]), _c2(beta), _ptr(C),
+                                _ld(C, m)), "ozk_zgemm_dmma")
+    return C
+
+
+def ozaki_zgemm_vbatched(h: Handle, As, Bs, Cs, S: int = 7, alpha=1.0, beta=0.0, transa="N",
+                         transb="N", pair_mode: int = OZK_PAIRS_TRI):
+    """Variable-size batch: lists of column-major tensors."""
+    import torch
+    nb = len(As)
+    dims = [_shapes(transa, transb, a, b) for a, b in zip(As, Bs)]
+    I = ctypes.c_int * nb
+    m = I(*[d[0] for d in dims]); n = I(*[d[1] for d in dims]); k = I(*[d[2] for d in dims])
+    lda = I(*[_ld(a, a.shape[0]) for a in As]); ldb = I(*[_ld(b, b.shape[0]) for b in Bs])
+    ldc = I(*[_ld(c, d[0]) for c, d in zip(Cs, dims)])
+    dev = As[0].device
+    pa = torch.tensor([_ptr(a) for a in As], dtype=torch.int64, device=dev)
+    pb = torch.tensor([_ptr(b) for b in Bs], dtype=torch.int64, device=dev)
+    pc = torch.tensor([_ptr(c) for c in Cs], dtype=torch.int64, device=dev)
+    _check(lib().ozaki_zgemm_vbatched(h.ptr, transa.encode(), transb.encode(), m, n, k, _c2(alpha),
+                                      pa.data_ptr(), lda, pb.data_ptr(), ldb, _c2(beta), pc.data_ptr(), ldc,
+                                      nb, S, pair_mode), "ozaki_zgemm_vbatched")
+    return Cs, (pa, pb, pc)
+
+
+def ozk_split_debug(h: Handle, X, side: int, S: int, trans: str = "N"):
+    """Exponents (int32) and digits (int16, [S][rows'][2k]) of op(X) as left/right operand."""
+    import torch
+    if side == 0:
+        rows, k = (X.shape[0], X.shape[1]) if trans in "Nn" else (X.shape[1], X.shape[0])
+    else:
+        k, rows = (X.shape[0], X.shape[1]) if trans in "Nn" else (X.shape[1], X.shape[0])
+    rows_out = rows if side == 0 else 2 * rows
+    e = torch.zeros(rows, dtype=torch.int32, device=X.device)
+    d = torch.zeros((S, rows_out, 2 * k), dtype=torch.int16, device=X.device)
+    _check(lib().ozk_split_debug(h.ptr, side, trans.encode(), rows, k, _ptr(X), _ld(X, X.shape[0]), S,
+                                 e.data_ptr(), d.data_ptr()), "ozk_split_debug")
+    return e, d
+
+
+def ozk_group_sums_debug(h: Handle, A, B, S: int, pair_mode: int = OZK_PAIRS_TRI, transa="N", transb="N"):
+    """Exact group sums G_g (int64 [G][m][2n]) computed by the tensor-core kernel."""
+    import torch
+    m, n, k = _shapes(transa, transb, A, B)
+    G = 2 * S - 1 if pair_mode == OZK_PAIRS_FULL else S
+    out = torch.zeros((G, m, 2 * n), dtype=torch.int64, device=A.device)
+    _check(lib().ozk_group_sums_debug(h.ptr, transa.encode(), transb.encode(), m, n, k, _ptr(A),
+                                      _ld(A, A.shape[0]), _ptr(B), _ld(B, B.shape[0]), S, pair_mode,
+                                      out.data_ptr()), "ozk_group_sums_debug")
+    return out
+
+
+def kkr_build_m(h: Handle, t, G, M):
+    """M = I - blockdiag(t) G; t is (L, b, b) complex128 with column-major blocks."""
+    L, b = t.shape[0], t.shape[1]
+    if not t.is_contiguous():
+        raise OzkError("t must be contiguous (L x b x b blocks, each column major)")
+    _check(lib().kkr_build_m(h.ptr, L, b, _ptr(t), _ptr(G), _ptr(M)), "kkr_build_m")
+    return M
+
+
+def kkr_tau00(h: Handle, M, t0, tau, S: int = 7, nb: int = 16):
+    """tau_00 = [M^-1]_00 t_0 (M is overwritten)."""
+    n = M.shape[0]
+    b = t0.shape[0]
+    _ld(M, n)
+    _check(lib().kkr_tau00(h.ptr, n, b, _ptr(M), _ptr(t0), _ptr(tau), S, nb), "kkr_tau00")
+    return tau
+
+
+def kkr_tau00_batched(h: Handle, Ms, t0s, taus, S: int = 7, nb: int = 16):
+    """Batched tau_00 over lists of column-major tensors (the Ms are overwritten)."""
+    import torch
+    ns = len(Ms)
+    b = t0s[0].shape[0]
+    n = (ctypes.c_int * ns)(*[int(M.shape[0]) for M in Ms])
+    dev = Ms[0].device
+    pm = torch.tensor([_ptr(M) for M in Ms], dtype=torch.int64, device=dev)
+    pt = torch.tensor([_ptr(t) for t in t0s], dtype=torch.int64, device=dev)
+    pu = torch.tensor([_ptr(u) for u in taus], dtype=torch.int64, device=dev)
+    _check(lib().kkr_tau00_batched(h.ptr, ns, n, b, pm.data_ptr(), pt.data_ptr(), pu.data_ptr(), S, nb),
+           "kkr_tau00_batched")
+    return taus, (pm, pt, pu)
+
+
+def kkr_tau00_batched_ptrs(h: Handle, n_list, b: int, pm, pt, pu, S: int = 7, nb: int = 16):
+    """Batched tau_00 with device pointer arrays already built (int64 CUDA tensors)."""
+    ns = len(n_list)
+    n = (ctypes.c_int * ns)(*[int(v) for v in n_list])
+    _check(lib().kkr_tau00_batched(h.ptr, ns, n, b, pm.data_ptr(), pt.data_ptr(), pu.data_ptr(), S, nb),
+           "kkr_tau00_batched")

@@ -1,0 +1,601 @@
+// C ABI of libozk (declared in include/ozk.h): handle, workspace, TMA descriptors, and the
+// host-side drivers of the emulated ZGEMM and of the block-LU tau_00 solve.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "ozk_params.cuh"
+
+namespace ozk {
+
+// --------------------------------------------------------------------- plumbing
+static thread_local char g_msg[512] = "";
+static thread_local uint64_t g_launches = 0;
+
+void record_launch() { ++g_launches; }
+
+ozk_status_t set_error(ozk_status_t st, const char* msg) {
+  std::snprintf(g_msg, sizeof(g_msg), "%s", msg);
+  return st;
+}
+
+ozk_status_t cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return OZK_OK;
+  std::snprintf(g_msg, sizeof(g_msg), "%s: %s", what, cudaGetErrorString(e));
+  return OZK_ERR_CUDA;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(ptr);
+  }
+  return fn;
+}
+
+// 3-D fp16 map over [planes][rows][kdim] (row pitch kpad elements), box {16, box_rows, box_planes}
+static ozk_status_t make_slice_map(CUtensorMap* map, void* base, long long kdim, long long kpad, long long rows,
+                                   long long planes, int box_rows, int box_planes) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return set_error(OZK_ERR_CUDA, "cuTensorMapEncodeTiled entry point unavailable");
+  cuuint64_t dims[3] = {static_cast<cuuint64_t>(kdim), static_cast<cuuint64_t>(rows), static_cast<cuuint64_t>(planes)};
+  cuuint64_t strides[2] = {static_cast<cuuint64_t>(kpad) * 2, static_cast<cuuint64_t>(rows) * kpad * 2};
+  cuuint32_t box[3] = {16u, static_cast<cuuint32_t>(box_rows), static_cast<cuuint32_t>(box_planes)};
+  cuuint32_t es[3] = {1u, 1u, 1u};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    char m[160];
+    std::snprintf(m, sizeof(m), "cuTensorMapEncodeTiled failed (%d) dims %lld %lld %lld", static_cast<int>(r), kdim, rows, planes);
+    return set_error(OZK_ERR_CUDA, m);
+  }
+  return OZK_OK;
+}
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace ozk
+
+using namespace ozk;
+
+struct ozk_context {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int* d_status = nullptr;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+};
+
+// --------------------------------------------------------------------- workspace
+static ozk_status_t ensure_ws(ozk_context* h, size_t bytes) {
+  if (bytes <= h->ws_bytes) return OZK_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(h->stream, &cs);
+  if (cs != cudaStreamCaptureStatusNone)
+    return set_error(OZK_ERR_CAPTURE, "workspace must grow during stream capture: call ozk_reserve first");
+  ozk_status_t st = cuda_check(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+  if (st) return st;
+  if (h->ws) cudaFree(h->ws);
+  h->ws = nullptr;
+  h->ws_bytes = 0;
+  size_t nb = align_up(bytes + (bytes >> 3), 1 << 20);
+  st = cuda_check(cudaMalloc(&h->ws, nb), "cudaMalloc(workspace)");
+  if (st) return st;
+  st = cuda_check(cudaMemset(h->ws, 0, nb), "cudaMemset(workspace)");
+  if (st) return st;
+  h->ws_bytes = nb;
+  return OZK_OK;
+}
+
+// --------------------------------------------------------------------- emulated GEMM core
+namespace {
+
+struct OpFlags { int trans, conj; };
+bool parse_op(char c, OpFlags* f) {
+  switch (c) {
+    case 'N': case 'n': f->trans = 0; f->conj = 0; return true;
+    case 'T': case 't': f->trans = 1; f->conj = 0; return true;
+    case 'C': case 'c': f->trans = 1; f->conj = 1; return true;
+    default: return false;
+  }
+}
+
+// Problem description for one (possibly batched) emulated GEMM.  Either the single fields
+// are used (batch == 1, tables == nullptr) or device tables of `batch` entries.
+struct EmuGemm {
+  OpFlags oa, ob;
+  int batch = 1;
+  int mmax = 0, nmax = 0, kmax = 0;          // host-known maxima
+  // single problem
+  const double2* A = nullptr; int lda = 0; const double2* B = nullptr; int ldb = 0;
+  double2* C = nullptr; int ldc = 0; int m = 0, n = 0, k = 0;
+  // device tables (batched)
+  const double2* const* tA = nullptr; const int* tlda = nullptr;
+  const double2* const* tB = nullptr; const int* tldb = nullptr;
+  double2* const* tC = nullptr; const int* tldc = nullptr;
+  const int* tm = nullptr; const int* tn = nullptr; const int* tk = nullptr;
+  double ar = 1, ai = 0, br = 0, bi = 0;
+  int S = 7, pair_mode = OZK_PAIRS_TRI;
+  int mode = -1;                             // -1: derive from alpha/beta
+  long long* groups = nullptr;               // group dump (test hook)
+  int16_t* dbg_digits_a = nullptr; int* dbg_exps_a = nullptr;
+};
+
+struct GemmPlan {
+  int G, BN, maxpairs, npairs, kpad, rowsA, rowsB, nstage, chunk_kb, kblocks;
+  size_t offA, offB, offE, offF, total;
+};
+
+ozk_status_t plan_gemm(const EmuGemm& g, GemmPlan* P) {
+  const int S = g.S;
+  if (S < 1 || S > 16) return set_error(OZK_ERR_ARG, "S must be in 1..16");
+  const bool full = g.pair_mode == OZK_PAIRS_FULL;
+  P->G = full ? 2 * S - 1 : S;
+  if (P->G > 16) return set_error(OZK_ERR_ARG, "full pair mode supports S <= 8");
+  P->BN = P->G <= 8 ? 64 : 32;
+  P->maxpairs = S;
+  P->npairs = full ? S * S : S * (S + 1) / 2;
+  const long long kp2 = 2LL * g.kmax;
+  P->kpad = static_cast<int>(align_up(static_cast<size_t>(std::max<long long>(kp2, 16)), 8));
+  P->rowsA = std::max(g.mmax, 1);
+  P->rowsB = 2 * std::max(g.nmax, 1);
+  const size_t stage = static_cast<size_t>(S) * (128 + P->BN) * 32;
+  P->nstage = static_cast<int>(std::min<size_t>(6, (200 * 1024 - 2048) / stage));
+  if (P->nstage < 1) return set_error(OZK_ERR_ARG, "S too large for the shared-memory pipeline");
+  P->chunk_kb = std::max(1, 64 / P->maxpairs);
+  P->kblocks = static_cast<int>((kp2 + 15) / 16);
+  // exact 128-bit sum: 8 (G - 1) weight bits + 14 product bits + log2(terms) + sign
+  double terms = static_cast<double>(kp2) * P->maxpairs + 1.0;
+  int need = 8 * (P->G - 1) + 14 + static_cast<int>(std::ceil(std::log2(terms))) + 2;
+  // the integer group dump (test hook) never forms the 128-bit sum
+  if (need > 127 && g.mode != 3)
+    return set_error(OZK_ERR_RANGE, "exact 128-bit reconstruction could overflow for this S and k");
+  size_t off = 0;
+  P->offA = off; off = align_up(off + static_cast<size_t>(g.batch) * S * P->rowsA * P->kpad * 2, 1024);
+  P->offB = off; off = align_up(off + static_cast<size_t>(g.batch) * S * P->rowsB * P->kpad * 2, 1024);
+  P->offE = off; off = align_up(off + static_cast<size_t>(g.batch) * P->rowsA * 4, 256);
+  P->offF = off; off = align_up(off + static_cast<size_t>(g.batch) * std::max(g.nmax, 1) * 4, 256);
+  P->total = off;
+  return OZK_OK;
+}
+
+ozk_status_t run_emulated(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0) {
+  GemmPlan P;
+  ozk_status_t st = plan_gemm(g, &P);
+  if (st) return st;
+  st = ensure_ws(h, ws_offset + P.total);
+  if (st) return st;
+  uint8_t* ws = static_cast<uint8_t*>(h->ws) + ws_offset;
+  __half* As = reinterpret_cast<__half*>(ws + P.offA);
+  __half* Bs = reinterpret_cast<__half*>(ws + P.offB);
+  int* e = reinterpret_cast<int*>(ws + P.offE);
+  int* f = reinterpret_cast<int*>(ws + P.offF);
+  const bool single = g.tm == nullptr;
+  const int S = g.S;
+
+  SplitParams sp{};
+  sp.S = S; sp.nbits = 8 * S - 1; sp.status = h->d_status; sp.kpad = P.kpad;
+  // left operand: rows of op(A); logical X[r][l] = op(A)[r][l]
+  sp.trans = g.oa.trans; sp.conj = g.oa.conj; sp.side = 0;
+  sp.out_rows = P.rowsA; sp.out = As; sp.exps = e; sp.exp_stride = P.rowsA;
+  sp.dbg_digits = g.dbg_digits_a;
+  if (single) { sp.X = nullptr; sp.X1 = g.A; sp.ld1 = g.lda; sp.rows1 = g.m; sp.k1 = g.k; }
+  else { sp.X = g.tA; sp.ld = g.tlda; sp.rows = g.tm; sp.kdim = g.tk; }
+  launch_split(sp, g.mmax, g.batch, h->stream);
+  // right operand: columns of op(B); logical X[j][l] = op(B)[l][j]
+  SplitParams sq = sp;
+  sq.trans = g.ob.trans ? 0 : 1; sq.conj = g.ob.conj; sq.side = 1;
+  sq.out_rows = P.rowsB; sq.out = Bs; sq.exps = f; sq.exp_stride = std::max(g.nmax, 1);
+  sq.dbg_digits = nullptr;
+  if (single) { sq.X = nullptr; sq.X1 = g.B; sq.ld1 = g.ldb; sq.rows1 = g.n; sq.k1 = g.k; }
+  else { sq.X = g.tB; sq.ld = g.tldb; sq.rows = g.tn; sq.kdim = g.tk; }
+  launch_split(sq, g.nmax, g.batch, h->stream);
+
+  CUtensorMap ta, tb;
+  st = make_slice_map(&ta, As, 2LL * g.kmax, P.kpad, P.rowsA, static_cast<long long>(S) * g.batch, 128, S);
+  if (st) return st;
+  st = make_slice_map(&tb, Bs, 2LL * g.kmax, P.kpad, P.rowsB, static_cast<long long>(S) * g.batch, P.BN, S);
+  if (st) return st;
+
+  GemmParams gp{};
+  gp.S = S; gp.ngroups = P.G; gp.kblocks = P.kblocks; gp.chunk_kb = P.chunk_kb; gp.nstage = P.nstage;
+  const int gmax = (g.pair_mode == OZK_PAIRS_FULL) ? 2 * S : S + 1;
+  gp.base_exp = -2 * (8 * S - 1) + 8 * (2 * S - gmax);
+  gp.ar = g.ar; gp.ai = g.ai; gp.br = g.br; gp.bi = g.bi;
+  if (g.mode >= 0) gp.mode = g.mode;
+  else if (g.br == 0.0 && g.bi == 0.0) gp.mode = 0;
+  else if (g.ar == -1.0 && g.ai == 0.0 && g.br == 1.0 && g.bi == 0.0) gp.mode = 1;
+  else gp.mode = 2;
+  gp.e = e; gp.f = f; gp.e_stride = P.rowsA; gp.f_stride = std::max(g.nmax, 1);
+  gp.groups = g.groups; gp.status = h->d_status;
+  if (single) { gp.m = nullptr; gp.m1 = g.m; gp.n1 = g.n; gp.C1 = g.C; gp.ldc1 = g.ldc; }
+  else { gp.m = g.tm; gp.n = g.tn; gp.C = g.tC; gp.ldc = g.tldc; }
+  int np = 0;
+  for (int gg = 2; gg <= gmax; ++gg) {
+    bool first = true;
+    for (int s = 1; s <= S; ++s) {
+      const int t = gg - s;
+      if (t < 1 || t > S) continue;
+      gp.ps[np] = static_cast<uint8_t>(s - 1);
+      gp.pt[np] = static_cast<uint8_t>(t - 1);
+      gp.pg[np] = static_cast<uint8_t>(gg - 2);
+      gp.pfirst[np] = first ? 1 : 0;
+      first = false;
+      ++np;
+    }
+  }
+  gp.npairs = np;
+  launch_slice_gemm(ta, tb, gp, P.BN, g.mmax, g.nmax, g.batch, h->stream);
+  return cuda_check(cudaGetLastError(), "slice GEMM launch");
+}
+
+ozk_status_t check_dims(OpFlags oa, OpFlags ob, int m, int n, int k, int lda, int ldb, int ldc) {
+  if (m < 0 || n < 0 || k < 0) return set_error(OZK_ERR_ARG, "negative dimension");
+  const int ra = oa.trans ? k : m, rb = ob.trans ? n : k;
+  if (lda < std::max(1, ra)) return set_error(OZK_ERR_ARG, "lda too small");
+  if (ldb < std::max(1, rb)) return set_error(OZK_ERR_ARG, "ldb too small");
+  if (ldc < std::max(1, m)) return set_error(OZK_ERR_ARG, "ldc too small");
+  return OZK_OK;
+}
+
+}  // namespace
+
+// --------------------------------------------------------------------- public API
+extern "C" {
+
+ozk_status_t ozk_create(ozk_handle_t* handle) {
+  if (!handle) return set_error(OZK_ERR_ARG, "null handle pointer");
+  ozk_context* h = new ozk_context();
+  cudaGetDevice(&h->device);
+  ozk_status_t st = cuda_check(cudaMalloc(&h->d_status, sizeof(int)), "cudaMalloc(status)");
+  if (!st) st = cuda_check(cudaMemset(h->d_status, 0, sizeof(int)), "cudaMemset(status)");
+  if (st) { delete h; return st; }
+  *handle = h;
+  return OZK_OK;
+}
+
+ozk_status_t ozk_destroy(ozk_handle_t h) {
+  if (!h) return OZK_OK;
+  cudaStreamSynchronize(h->stream);
+  if (h->ws) cudaFree(h->ws);
+  if (h->d_status) cudaFree(h->d_status);
+  delete h;
+  return OZK_OK;
+}
+
+ozk_status_t ozk_set_stream(ozk_handle_t h, void* stream) {
+  if (!h) return set_error(OZK_ERR_ARG, "null handle");
+  h->stream = static_cast<cudaStream_t>(stream);
+  return OZK_OK;
+}
+
+ozk_status_t ozk_get_status(ozk_handle_t h, int* flags) {
+  if (!h || !flags) return set_error(OZK_ERR_ARG, "null argument");
+  ozk_status_t st = cuda_check(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+  if (st) return st;
+  int v = 0;
+  st = cuda_check(cudaMemcpy(&v, h->d_status, sizeof(int), cudaMemcpyDeviceToHost), "read status");
+  if (st) return st;
+  cudaMemset(h->d_status, 0, sizeof(int));
+  *flags = v;
+  return OZK_OK;
+}
+
+ozk_status_t ozk_reserve(ozk_handle_t h, size_t bytes) {
+  if (!h) return set_error(OZK_ERR_ARG, "null handle");
+  return ensure_ws(h, bytes);
+}
+
+size_t ozk_zgemm_workspace_size(int m, int n, int k, int S, int batch) {
+  EmuGemm g;
+  g.mmax = m; g.nmax = n; g.kmax = k; g.S = S; g.batch = batch;
+  GemmPlan P;
+  if (plan_gemm(g, &P)) return 0;
+  return P.total;
+}
+
+const char* ozk_last_error(void) { return g_msg; }
+uint64_t ozk_launch_count(void) { return g_launches; }
+
+ozk_status_t ozaki_zgemm(ozk_handle_t h, char transa, char transb, int m, int n, int k, const double* alpha,
+                         const void* A, int lda, const void* B, int ldb, const double* beta, void* C, int ldc,
+                         int S, int pair_mode) {
+  if (!h || !alpha || !beta) return set_error(OZK_ERR_ARG, "null argument");
+  EmuGemm g;
+  if (!parse_op(transa, &g.oa) || !parse_op(transb, &g.ob)) return set_error(OZK_ERR_ARG, "bad trans flag");
+  ozk_status_t st = check_dims(g.oa, g.ob, m, n, k, lda, ldb, ldc);
+  if (st) return st;
+  if (pair_mode != OZK_PAIRS_TRI && pair_mode != OZK_PAIRS_FULL) return set_error(OZK_ERR_ARG, "bad pair mode");
+  if (m == 0 || n == 0) return OZK_OK;
+  if (k == 0 || (alpha[0] == 0.0 && alpha[1] == 0.0)) {
+    if (beta[0] == 1.0 && beta[1] == 0.0) return OZK_OK;
+    launch_scale(m, n, static_cast<double2*>(C), ldc, beta[0], beta[1], h->stream);
+    return cuda_check(cudaGetLastError(), "scale launch");
+  }
+  g.batch = 1; g.mmax = g.m = m; g.nmax = g.n = n; g.kmax = g.k = k;
+  g.A = static_cast<const double2*>(A); g.lda = lda;
+  g.B = static_cast<const double2*>(B); g.ldb = ldb;
+  g.C = static_cast<double2*>(C); g.ldc = ldc;
+  g.ar = alpha[0]; g.ai = alpha[1]; g.br = beta[0]; g.bi = beta[1];
+  g.S = S; g.pair_mode = pair_mode;
+  return run_emulated(h, g);
+}
+
+ozk_status_t ozaki_zgemm_vbatched(ozk_handle_t h, char transa, char transb, const int* m, const int* n, const int* k,
+                                  const double* alpha, const void* const* A, const int* lda, const void* const* B,
+                                  const int* ldb, const double* beta, void* const* C, const int* ldc, int batch,
+                                  int S, int pair_mode) {
+  if (!h || !alpha || !beta || !m || !n || !k || !lda || !ldb || !ldc) return set_error(OZK_ERR_ARG, "null argument");
+  if (batch < 0) return set_error(OZK_ERR_ARG, "negative batch");
+  if (batch == 0) return OZK_OK;
+  EmuGemm g;
+  if (!parse_op(transa, &g.oa) || !parse_op(transb, &g.ob)) return set_error(OZK_ERR_ARG, "bad trans flag");
+  if (pair_mode != OZK_PAIRS_TRI && pair_mode != OZK_PAIRS_FULL) return set_error(OZK_ERR_ARG, "bad pair mode");
+  int mm = 0, nn = 0, kk = 0;
+  for (int i = 0; i < batch; ++i) {
+    ozk_status_t st = check_dims(g.oa, g.ob, m[i], n[i], k[i], lda[i], ldb[i], ldc[i]);
+    if (st) return st;
+    if (k[i] == 0) return set_error(OZK_ERR_ARG, "vbatched: k == 0 entries are not supported");
+    mm = std::max(mm, m[i]); nn = std::max(nn, n[i]); kk = std::max(kk, k[i]);
+  }
+  if (mm == 0 || nn == 0) return OZK_OK;
+  g.batch = batch; g.mmax = mm; g.nmax = nn; g.kmax = kk;
+  g.ar = alpha[0]; g.ai = alpha[1]; g.br = beta[0]; g.bi = beta[1];
+  g.S = S; g.pair_mode = pair_mode;
+  GemmPlan P;
+  ozk_status_t st = plan_gemm(g, &P);
+  if (st) return st;
+  // device table of sizes after the GEMM workspace: m, n, k, lda, ldb, ldc
+  const size_t tab_off = align_up(P.total, 256);
+  const size_t tab_bytes = 6 * static_cast<size_t>(batch) * sizeof(int);
+  st = ensure_ws(h, tab_off + tab_bytes);
+  if (st) return st;
+  std::vector<int> tab(6 * static_cast<size_t>(batch));
+  for (int i = 0; i < batch; ++i) {
+    tab[i] = m[i]; tab[batch + i] = n[i]; tab[2 * batch + i] = k[i];
+    tab[3 * batch + i] = lda[i]; tab[4 * batch + i] = ldb[i]; tab[5 * batch + i] = ldc[i];
+  }
+  int* dtab = reinterpret_cast<int*>(static_cast<uint8_t*>(h->ws) + tab_off);
+  st = cuda_check(cudaMemcpyAsync(dtab, tab.data(), tab_bytes, cudaMemcpyHostToDevice, h->stream), "upload sizes");
+  if (st) return st;
+  g.tm = dtab; g.tn = dtab + batch; g.tk = dtab + 2 * batch;
+  g.tlda = dtab + 3 * batch; g.tldb = dtab + 4 * batch; g.tldc = dtab + 5 * batch;
+  g.tA = reinterpret_cast<const double2* const*>(A);
+  g.tB = reinterpret_cast<const double2* const*>(B);
+  g.tC = reinterpret_cast<double2* const*>(C);
+  return run_emulated(h, g);
+}
+
+ozk_status_t ozk_zgemm_dmma(ozk_handle_t h, char transa, char transb, int m, int n, int k, const double* alpha,
+                            const void* A, int lda, const void* B, int ldb, const double* beta, void* C, int ldc) {
+  if (!h || !alpha || !beta) return set_error(OZK_ERR_ARG, "null argument");
+  OpFlags oa, ob;
+  if (!parse_op(transa, &oa) || !parse_op(transb, &ob)) return set_error(OZK_ERR_ARG, "bad trans flag");
+  ozk_status_t st = check_dims(oa, ob, m, n, k, lda, ldb, ldc);
+  if (st) return st;
+  if (m == 0 || n == 0) return OZK_OK;
+  DmmaParams p{};
+  p.m = m; p.n = n; p.k = k;
+  p.transa = oa.trans; p.conja = oa.conj; p.transb = ob.trans; p.conjb = ob.conj;
+  p.A = static_cast<const double2*>(A); p.lda = lda;
+  p.B = static_cast<const double2*>(B); p.ldb = ldb;
+  p.C = static_cast<double2*>(C); p.ldc = ldc;
+  p.ar = alpha[0]; p.ai = alpha[1]; p.br = beta[0]; p.bi = beta[1];
+  launch_dmma(p, h->stream);
+  return cuda_check(cudaGetLastError(), "DMMA launch");
+}
+
+ozk_status_t ozk_split_debug(ozk_handle_t h, int side, char trans, int rows, int k, const void* X, int ldx, int S,
+                             int32_t* exps, int16_t* digits) {
+  if (!h || !X || !exps) return set_error(OZK_ERR_ARG, "null argument");
+  if (side != 0 && side != 1) return set_error(OZK_ERR_ARG, "side must be 0 or 1");
+  if (rows <= 0 || k <= 0 || S < 1 || S > 16) return set_error(OZK_ERR_ARG, "bad size");
+  OpFlags op;
+  if (!parse_op(trans, &op)) return set_error(OZK_ERR_ARG, "bad trans flag");
+  const int rows_out = side == 0 ? rows : 2 * rows;
+  const int kpad = static_cast<int>(align_up(static_cast<size_t>(2 * k), 8));
+  const size_t bytes = static_cast<size_t>(S) * rows_out * kpad * 2;
+  ozk_status_t st = ensure_ws(h, bytes);
+  if (st) return st;
+  SplitParams sp{};
+  sp.S = S; sp.nbits = 8 * S - 1; sp.status = h->d_status; sp.kpad = kpad; sp.side = side;
+  sp.conj = op.conj;
+  // side 0: op(X) is rows x k; side 1: op(X) is k x rows and its columns are the logical rows
+  sp.trans = side == 0 ? op.trans : (op.trans ? 0 : 1);
+  sp.out_rows = rows_out; sp.out = static_cast<__half*>(h->ws); sp.exps = exps; sp.exp_stride = rows;
+  sp.X = nullptr; sp.X1 = static_cast<const double2*>(X); sp.ld1 = ldx; sp.rows1 = rows; sp.k1 = k;
+  // debug digits are always dumped in the stacked layout [S][rows_out][2k]
+  sp.dbg_digits = digits;
+  launch_split(sp, rows, 1, h->stream);
+  return cuda_check(cudaGetLastError(), "split launch");
+}
+
+ozk_status_t ozk_group_sums_debug(ozk_handle_t h, char transa, char transb, int m, int n, int k, const void* A,
+                                  int lda, const void* B, int ldb, int S, int pair_mode, int64_t* groups) {
+  if (!h || !groups) return set_error(OZK_ERR_ARG, "null argument");
+  EmuGemm g;
+  if (!parse_op(transa, &g.oa) || !parse_op(transb, &g.ob)) return set_error(OZK_ERR_ARG, "bad trans flag");
+  ozk_status_t st = check_dims(g.oa, g.ob, m, n, k, lda, ldb, std::max(1, m));
+  if (st) return st;
+  if (m == 0 || n == 0 || k == 0) return set_error(OZK_ERR_ARG, "empty problem");
+  g.batch = 1; g.mmax = g.m = m; g.nmax = g.n = n; g.kmax = g.k = k;
+  g.A = static_cast<const double2*>(A); g.lda = lda;
+  g.B = static_cast<const double2*>(B); g.ldb = ldb;
+  g.C = nullptr; g.ldc = std::max(1, m);
+  g.S = S; g.pair_mode = pair_mode; g.mode = 3;
+  g.groups = reinterpret_cast<long long*>(groups);
+  const int G = pair_mode == OZK_PAIRS_FULL ? 2 * S - 1 : S;
+  st = cuda_check(cudaMemsetAsync(groups, 0, sizeof(int64_t) * static_cast<size_t>(G) * m * 2 * n, h->stream),
+                  "memset groups");
+  if (st) return st;
+  return run_emulated(h, g);
+}
+
+ozk_status_t kkr_build_m(ozk_handle_t h, int L, int b, const void* t, const void* G, void* M) {
+  if (!h || !t || !G || !M) return set_error(OZK_ERR_ARG, "null argument");
+  if (L <= 0 || b <= 0) return set_error(OZK_ERR_ARG, "bad size");
+  launch_build_m(L * b, b, static_cast<const double2*>(t), static_cast<const double2*>(G), static_cast<double2*>(M),
+                 h->stream);
+  return cuda_check(cudaGetLastError(), "build_m launch");
+}
+
+// tau_00 of one matrix: eliminate panels J = [p, q) from the trailing end, centre last.
+ozk_status_t kkr_tau00(ozk_handle_t h, int n, int b, void* Mv, const void* t0, void* tau, int S, int nb) {
+  if (!h || !Mv || !t0 || !tau) return set_error(OZK_ERR_ARG, "null argument");
+  if (b <= 0 || n <= 0 || n % b || nb < b || nb % b || nb > 64 || b > 64)
+    return set_error(OZK_ERR_ARG, "need n % b == 0, b <= nb <= 64, nb % b == 0");
+  double2* M = static_cast<double2*>(Mv);
+  // workspace: pivot inverse (nb x nb) in front of the GEMM workspace (emulated path) or of
+  // the L-panel scratch (DMMA path, which cannot update the panel in place)
+  const size_t dinv_bytes = align_up(sizeof(double2) * nb * nb, 1024);
+  {
+    size_t need = dinv_bytes + sizeof(double2) * static_cast<size_t>(n) * nb;
+    if (S > 0) {
+      EmuGemm probe;
+      probe.mmax = n; probe.nmax = n; probe.kmax = nb; probe.S = S;
+      GemmPlan P;
+      ozk_status_t st = plan_gemm(probe, &P);
+      if (st) return st;
+      need = dinv_bytes + P.total;
+    }
+    ozk_status_t st = ensure_ws(h, need);
+    if (st) return st;
+  }
+  double2* Dinv = static_cast<double2*>(h->ws);
+  for (int q = n; q > b;) {
+    const int p = std::max(q - nb, b);
+    const int w = q - p, r = p;
+    GjParams gj{};
+    gj.D = nullptr; gj.D1 = M + p + static_cast<long long>(p) * n; gj.ldd1 = n; gj.nb1 = w;
+    gj.R1 = nullptr; gj.X1 = Dinv; gj.ldx1 = w; gj.nrhs = w; gj.status = h->d_status;
+    launch_gj(gj, w, w, 1, h->stream);
+    double2* Lp = M + static_cast<long long>(p) * n;       // M[0:r, p:q]
+    const double2* Up = M + p;                              // M[p:q, 0:r]
+    if (S > 0) {
+      EmuGemm g1;
+      g1.oa = {0, 0}; g1.ob = {0, 0}; g1.batch = 1;
+      g1.mmax = g1.m = r; g1.nmax = g1.n = w; g1.kmax = g1.k = w;
+      g1.A = Lp; g1.lda = n; g1.B = Dinv; g1.ldb = w; g1.C = Lp; g1.ldc = n;
+      g1.S = S; g1.ar = 1; g1.br = 0;
+      ozk_status_t st = run_emulated(h, g1, dinv_bytes);
+      if (st) return st;
+      EmuGemm g2 = g1;
+      g2.nmax = g2.n = r;
+      g2.A = Lp; g2.lda = n; g2.B = Up; g2.ldb = n; g2.C = M; g2.ldc = n;
+      g2.ar = -1; g2.br = 1;
+      st = run_emulated(h, g2, dinv_bytes);
+      if (st) return st;
+    } else {
+      // binary64 DMMA baseline: L = M_RJ Dinv into the scratch, copy back, then update
+      double2* Ltmp = reinterpret_cast<double2*>(static_cast<uint8_t*>(h->ws) + dinv_bytes);
+      DmmaParams d1{};
+      d1.m = r; d1.n = w; d1.k = w; d1.A = Lp; d1.lda = n; d1.B = Dinv; d1.ldb = w;
+      d1.C = Ltmp; d1.ldc = r; d1.ar = 1; d1.br = 0;
+      launch_dmma(d1, h->stream);
+      ozk_status_t st = cuda_check(cudaMemcpy2DAsync(Lp, sizeof(double2) * n, Ltmp, sizeof(double2) * r,
+                                                     sizeof(double2) * r, w, cudaMemcpyDeviceToDevice, h->stream),
+                                   "copy L panel");
+      if (st) return st;
+      DmmaParams d2{};
+      d2.m = r; d2.n = r; d2.k = w; d2.A = Lp; d2.lda = n; d2.B = Up; d2.ldb = n; d2.C = M; d2.ldc = n;
+      d2.ar = -1; d2.br = 1;
+      launch_dmma(d2, h->stream);
+    }
+    q = p;
+  }
+  GjParams gj{};
+  gj.D = nullptr; gj.D1 = M; gj.ldd1 = n; gj.nb1 = b;
+  gj.R1 = static_cast<const double2*>(t0); gj.ldr1 = b; gj.nrhs = b;
+  gj.X1 = static_cast<double2*>(tau); gj.ldx1 = b; gj.status = h->d_status;
+  launch_gj(gj, b, b, 1, h->stream);
+  return cuda_check(cudaGetLastError(), "kkr_tau00 launches");
+}
+
+
+ozk_status_t kkr_tau00_batched(ozk_handle_t h, int nsolves, const int* n, int b, void* const* M, const void* const* t0,
+                               void* const* tau, int S, int nb) {
+  if (!h || !n || !M || !t0 || !tau) return set_error(OZK_ERR_ARG, "null argument");
+  if (nsolves < 0) return set_error(OZK_ERR_ARG, "negative nsolves");
+  if (nsolves == 0) return OZK_OK;
+  if (S <= 0) return set_error(OZK_ERR_ARG, "batched solves run the emulated path (S >= 1)");
+  if (b <= 0 || nb < b || nb % b || nb > 64 || b > 64) return set_error(OZK_ERR_ARG, "need b <= nb <= 64, nb % b == 0");
+  int nmax = 0;
+  for (int i = 0; i < nsolves; ++i) {
+    if (n[i] <= 0 || n[i] % b) return set_error(OZK_ERR_ARG, "every n[i] must be a positive multiple of b");
+    nmax = std::max(nmax, n[i]);
+  }
+  const int steps = (nmax - b + nb - 1) / nb;
+  // workspace layout: [n table][Dinv][step tables][GEMM workspace]
+  const size_t ns = static_cast<size_t>(nsolves);
+  const size_t off_n = 0;
+  const size_t off_dinv = align_up(ns * sizeof(int), 1024);
+  const size_t off_tab = align_up(off_dinv + ns * nb * nb * sizeof(double2), 1024);
+  const size_t n_ptr = 10, n_int = 16;
+  const size_t off_gemm = align_up(off_tab + ns * (n_ptr * sizeof(void*) + n_int * sizeof(int)), 1024);
+  EmuGemm probe;
+  probe.batch = nsolves; probe.mmax = nmax; probe.nmax = nmax; probe.kmax = nb; probe.S = S;
+  GemmPlan P;
+  ozk_status_t st = plan_gemm(probe, &P);
+  if (st) return st;
+  st = ensure_ws(h, off_gemm + P.total);
+  if (st) return st;
+  uint8_t* ws = static_cast<uint8_t*>(h->ws);
+  int* dn = reinterpret_cast<int*>(ws + off_n);
+  double2* dinv = reinterpret_cast<double2*>(ws + off_dinv);
+  st = cuda_check(cudaMemcpyAsync(dn, n, ns * sizeof(int), cudaMemcpyHostToDevice, h->stream), "upload n");
+  if (st) return st;
+  uint8_t* pp = ws + off_tab;                  // ns x n_ptr pointer slots
+  int* pi = reinterpret_cast<int*>(ws + off_tab + ns * n_ptr * sizeof(void*));
+  KkrStep t;
+  t.D = reinterpret_cast<const double2**>(pp + 0 * ns * sizeof(void*)); t.X = reinterpret_cast<double2**>(pp + 1 * ns * sizeof(void*));
+  t.A1 = reinterpret_cast<const double2**>(pp + 2 * ns * sizeof(void*)); t.B1 = reinterpret_cast<const double2**>(pp + 3 * ns * sizeof(void*));
+  t.C1 = reinterpret_cast<double2**>(pp + 4 * ns * sizeof(void*)); t.A2 = reinterpret_cast<const double2**>(pp + 5 * ns * sizeof(void*));
+  t.B2 = reinterpret_cast<const double2**>(pp + 6 * ns * sizeof(void*)); t.C2 = reinterpret_cast<double2**>(pp + 7 * ns * sizeof(void*));
+  t.ldd = pi + 0 * ns; t.nbv = pi + 1 * ns; t.ldx = pi + 2 * ns;
+  t.lda1 = pi + 3 * ns; t.ldb1 = pi + 4 * ns; t.ldc1 = pi + 5 * ns; t.m1 = pi + 6 * ns; t.n1 = pi + 7 * ns; t.k1 = pi + 8 * ns;
+  t.lda2 = pi + 9 * ns; t.ldb2 = pi + 10 * ns; t.ldc2 = pi + 11 * ns; t.m2 = pi + 12 * ns; t.n2 = pi + 13 * ns; t.k2 = pi + 14 * ns;
+  double2* const* Mp = reinterpret_cast<double2* const*>(M);
+  for (int s = 0; s < steps; ++s) {
+    int rmax = 0;
+    for (int i = 0; i < nsolves; ++i) {
+      const int q = n[i] - s * nb;
+      if (q > b) rmax = std::max(rmax, std::max(q - nb, b));
+    }
+    if (rmax == 0) break;
+    launch_kkr_step(s, nsolves, dn, Mp, b, nb, dinv, t, h->stream);
+    GjParams gj{};
+    gj.D = t.D; gj.ldd = t.ldd; gj.nb = t.nbv; gj.R = nullptr; gj.X = t.X; gj.ldx = t.ldx; gj.nrhs = nb;
+    gj.status = h->d_status;
+    launch_gj(gj, nb, nb, nsolves, h->stream);
+    EmuGemm g1;
+    g1.oa = {0, 0}; g1.ob = {0, 0}; g1.batch = nsolves; g1.mmax = rmax; g1.nmax = nb; g1.kmax = nb; g1.S = S;
+    g1.tA = t.A1; g1.tlda = t.lda1; g1.tB = t.B1; g1.tldb = t.ldb1; g1.tC = t.C1; g1.tldc = t.ldc1;
+    g1.tm = t.m1; g1.tn = t.n1; g1.tk = t.k1; g1.ar = 1; g1.br = 0;
+    st = run_emulated(h, g1, off_gemm);
+    if (st) return st;
+    EmuGemm g2 = g1;
+    g2.nmax = rmax;
+    g2.tA = t.A2; g2.tlda = t.lda2; g2.tB = t.B2; g2.tldb = t.ldb2; g2.tC = t.C2; g2.tldc = t.ldc2;
+    g2.tm = t.m2; g2.tn = t.n2; g2.tk = t.k2; g2.ar = -1; g2.br = 1;
+    st = run_emulated(h, g2, off_gemm);
+    if (st) return st;
+  }
+  launch_kkr_step(-1, nsolves, dn, Mp, b, nb, dinv, t, h->stream);
+  GjParams gj{};
+  gj.D = t.D; gj.ldd = t.ldd; gj.nb = t.nbv;
+  gj.R = reinterpret_cast<const double2* const*>(t0); gj.ldr = t.nbv;
+  gj.X = reinterpret_cast<double2* const*>(tau); gj.ldx = t.nbv; gj.nrhs = b; gj.status = h->d_status;
+  launch_gj(gj, b, b, nsolves, h->stream);
+  return cuda_check(cudaGetLastError(), "kkr_tau00_batched launches");
+}
+
+}  // extern "C"

@@ -1,0 +1,101 @@
+// Kernel parameter blocks and launchers shared by the translation units of libozk.
+#pragma once
+
+#include "ozk_internal.cuh"
+
+namespace ozk {
+
+// ---- split.cu: exponent scan + balanced-digit slices
+struct SplitParams {
+  const double2* const* X;  // per problem: base pointer of the stored matrix (device)
+  const int* ld;            // per problem: leading dimension (complex elements)
+  const int* rows;          // per problem: logical rows (rows of op(A) / columns of op(B))
+  const int* kdim;          // per problem: K
+  int trans;                // logical X[r][l] = trans ? P[l + r ld] : P[r + l ld]
+  int conj;                 // negate the imaginary part (op = 'C')
+  int side;                 // 0 left operand, 1 right operand
+  int S;
+  int nbits;                // B = 8S - 1
+  long long out_rows;       // row count of one slice plane
+  long long kpad;           // row pitch (fp16 elements)
+  __half* out;              // [batch][S][out_rows][kpad]
+  int* exps;                // [batch][exp_stride]
+  long long exp_stride;
+  int16_t* dbg_digits;      // optional int16 copy [S][out_rows][2k] for problem 0 (test hook)
+  int* status;
+  // single-problem values, used when X == nullptr (no device tables needed)
+  const double2* X1; int ld1, rows1, k1;
+};
+void launch_split(const SplitParams& p, int max_rows, int batch, cudaStream_t st);
+
+// ---- slice_gemm.cu: tcgen05 slice-pair GEMM + exact reconstruction
+constexpr int MAX_PAIRS = 136;
+enum EpiMode : int { EPI_STORE = 0, EPI_LU = 1, EPI_GENERAL = 2, EPI_GROUPS = 3 };
+struct GemmParams {
+  int S;
+  int npairs;
+  int ngroups;            // G = g_max - 1
+  int kblocks;            // K' / 16 rounded up (uniform over the batch)
+  int chunk_kb;           // K-blocks per exactness chunk
+  int nstage;
+  int mode;
+  int base_exp;           // -2B + 8 (2S - g_max)
+  double ar, ai, br, bi;  // alpha, beta
+  const int* m;           // per problem rows of C
+  const int* n;           // per problem complex columns of C
+  double2* const* C;      // per problem output pointer
+  const int* ldc;
+  const int* e;           // exponents of rows  [batch][e_stride]
+  const int* f;           // exponents of cols  [batch][f_stride]
+  long long e_stride, f_stride;
+  long long* groups;      // EPI_GROUPS: [G][m][2n] int64 of problem 0 (zeroed by the caller)
+  int* status;
+  // single-problem values, used when m == nullptr (no device tables needed)
+  int m1, n1; double2* C1; int ldc1;
+  uint8_t ps[MAX_PAIRS], pt[MAX_PAIRS], pg[MAX_PAIRS], pfirst[MAX_PAIRS];
+};
+void launch_slice_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const GemmParams& p, int BN,
+                       int max_m, int max_n, int batch, cudaStream_t st);
+size_t gemm_smem_bytes(int S, int BN, int nstage);
+
+// ---- dmma.cu: binary64 DMMA ZGEMM
+struct DmmaParams {
+  int m, n, k;
+  int transa, conja, transb, conjb;
+  const double2* A; long long lda;
+  const double2* B; long long ldb;
+  double2* C; long long ldc;
+  double ar, ai, br, bi;
+};
+void launch_dmma(const DmmaParams& p, cudaStream_t st);
+
+// ---- lu.cu: Gauss-Jordan solves, M build, scaling
+struct GjParams {
+  const double2* const* D;  // per problem: nb x nb block, column major
+  const int* ldd;
+  const int* nb;            // per problem size (0 = skip)
+  const double2* const* R;  // per problem right-hand side (nb x nrhs col major) or nullptr = identity
+  const int* ldr;
+  double2* const* X;        // per problem output nb x nrhs
+  const int* ldx;
+  int nrhs;                 // columns of R (== nb when R is the identity)
+  // single-problem values, used when D == nullptr
+  const double2* D1; int ldd1, nb1; const double2* R1; int ldr1; double2* X1; int ldx1;
+  int* status;
+};
+void launch_gj(const GjParams& p, int max_nb, int max_nrhs, int batch, cudaStream_t st);
+void launch_build_m(int n, int b, const double2* t, const double2* G, double2* M, cudaStream_t st);
+void launch_scale(int m, int n, double2* C, long long ldc, double br, double bi, cudaStream_t st);
+
+// Per-step tables of the batched tau_00 driver, filled on the device for step `step`.
+struct KkrStep {
+  // Gauss-Jordan on the pivot blocks
+  const double2** D; int* ldd; int* nbv; double2** X; int* ldx;
+  // GEMM 1: L = M_RJ Dinv (in place), GEMM 2: M_RR -= L M_JR
+  const double2** A1; int* lda1; const double2** B1; int* ldb1; double2** C1; int* ldc1; int* m1; int* n1; int* k1;
+  const double2** A2; int* lda2; const double2** B2; int* ldb2; double2** C2; int* ldc2; int* m2; int* n2; int* k2;
+};
+void launch_kkr_step(int step, int nsolves, const int* n, double2* const* M, int b, int nb, double2* dinv,
+                     const KkrStep& t, cudaStream_t st);
+
+}  // namespace ozk

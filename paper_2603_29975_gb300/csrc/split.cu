@@ -1,0 +1,189 @@
+// Exponent scan and slice split (paper Sec. 2.2: slices by significant bits with exponent
+// alignment).  One CTA owns 32 logical rows of an operand: it reads them once to find the
+// per-row maximum of |Re| and |Im| (integer compare on the binary64 bit patterns), derives
+// the frexp exponent, then reads them again (from L2) and writes the S balanced int8 digits
+// of every real scalar as fp16 values in the K-major stacked layout the tensor-core kernel
+// loads with TMA:
+//   left operand  (side 0): out[z][s][r][l]     = digit of Re x_rl, out[z][s][r][k+l] = Im
+//   right operand (side 1): out[z][s][2r][l]    = Re,  out[z][s][2r][k+l]   = -Im (digit-wise)
+//                           out[z][s][2r+1][l]  = Im,  out[z][s][2r+1][k+l] = Re
+// Positions [2k, kpad) of every written row are zero.  All integer work, no FP64 arithmetic.
+#include "ozk_params.cuh"
+
+namespace ozk {
+
+
+
+constexpr int SPLIT_ROWS = 32;
+constexpr int SPLIT_TK = 64;
+constexpr int SPLIT_THREADS = 256;
+
+__device__ __forceinline__ int frexp_exponent_from_bits(unsigned long long a) {
+  // a = |x| bit pattern (sign cleared), finite
+  if (a == 0ull) return 0;
+  const int ex = static_cast<int>(a >> 52);
+  if (ex > 0) return ex - 1022;
+  return -1010 - __clzll(a);          // subnormal: floor(log2 x) + 1
+}
+
+// Balanced base-256 digits of X = trunc(x 2^(B - e)), most significant first in d[0].
+__device__ __forceinline__ void digits_of(double x, int e, int nbits, int S, int (&d)[16]) {
+  const unsigned long long u = __double_as_longlong(x);
+  const bool neg = (u >> 63) != 0ull;
+  const int ex = static_cast<int>((u >> 52) & 0x7FFull);
+  const unsigned long long man = u & ((1ull << 52) - 1ull);
+  unsigned long long M;
+  int E2;
+  if (ex == 0) { M = man; E2 = -1074; } else { M = man | (1ull << 52); E2 = ex - 1075; }
+  const int sh = E2 + nbits - e;
+  unsigned __int128 mag = 0;
+  if (M != 0ull) {
+    if (sh >= 0) mag = static_cast<unsigned __int128>(M) << sh;
+    else if (sh > -64) mag = static_cast<unsigned __int128>(M >> (-sh));
+  }
+  __int128 X = neg ? -static_cast<__int128>(mag) : static_cast<__int128>(mag);
+#pragma unroll
+  for (int t = 15; t >= 1; --t) {
+    if (t < S) {
+      const int dd = static_cast<int>(static_cast<unsigned long long>(X + 128) & 255ull) - 128;
+      d[t] = dd;
+      X = (X - dd) >> 8;
+    }
+  }
+  d[0] = static_cast<int>(X);
+}
+
+__global__ void __launch_bounds__(SPLIT_THREADS)
+split_kernel(const SplitParams p) {
+  const int z = blockIdx.y;
+  const bool single = p.X == nullptr;
+  const int R = single ? p.rows1 : p.rows[z];
+  const int K = single ? p.k1 : p.kdim[z];
+  const int r0 = blockIdx.x * SPLIT_ROWS;
+  if (r0 >= R) return;
+  const double2* __restrict__ P = single ? p.X1 : p.X[z];
+  const long long ld = single ? p.ld1 : p.ld[z];
+  const int tid = threadIdx.x;
+
+  __shared__ unsigned long long rowmax[SPLIT_ROWS];
+  __shared__ int rowexp[SPLIT_ROWS];
+  __shared__ double2 tile[SPLIT_ROWS][SPLIT_TK + 1];
+  __shared__ int bad;
+  if (tid < SPLIT_ROWS) rowmax[tid] = 0ull;
+  if (tid == 0) bad = 0;
+  __syncthreads();
+
+  // ---- pass 1: row maxima
+  {
+    int rl, l0, lstep;
+    if (!p.trans) { rl = tid % SPLIT_ROWS; l0 = tid / SPLIT_ROWS; lstep = SPLIT_THREADS / SPLIT_ROWS; }
+    else          { rl = tid / 8;          l0 = tid % 8;          lstep = 8; }
+    const int r = r0 + rl;
+    unsigned long long mx = 0ull;
+    if (r < R) {
+      for (int l = l0; l < K; l += lstep) {
+        const double2 v = p.trans ? P[l + r * ld] : P[r + l * ld];
+        const unsigned long long a = static_cast<unsigned long long>(__double_as_longlong(v.x)) & 0x7FFFFFFFFFFFFFFFull;
+        const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v.y)) & 0x7FFFFFFFFFFFFFFFull;
+        const unsigned long long m2 = a > b ? a : b;
+        if (m2 >= 0x7FF0000000000000ull) bad = 1;
+        mx = m2 > mx ? m2 : mx;
+      }
+      atomicMax(&rowmax[rl], mx);
+    }
+  }
+  __syncthreads();
+  if (bad && tid == 0) flag_error(p.status, OZK_ERR_NONFINITE);
+  if (tid < SPLIT_ROWS) {
+    const unsigned long long a = rowmax[tid];
+    const int e = (a >= 0x7FF0000000000000ull) ? 0 : frexp_exponent_from_bits(a);
+    rowexp[tid] = e;
+    if (r0 + tid < R) p.exps[z * p.exp_stride + r0 + tid] = e;
+  }
+  __syncthreads();
+
+  // ---- pass 2: digits, tile by tile along K
+  const int S = p.S;
+  const long long plane = p.out_rows * p.kpad;
+  __half* outz = p.out + static_cast<long long>(z) * S * plane;
+  const bool dbg = (p.dbg_digits != nullptr) && z == 0;
+  const long long dplane = p.out_rows * 2LL * K;
+  for (int lt = 0; lt < K; lt += SPLIT_TK) {
+    // load a 32 x 64 tile (coalesced along the stored contiguous direction)
+    for (int idx = tid; idx < SPLIT_ROWS * SPLIT_TK; idx += SPLIT_THREADS) {
+      int rl, ll;
+      if (!p.trans) { rl = idx % SPLIT_ROWS; ll = idx / SPLIT_ROWS; }
+      else          { ll = idx % SPLIT_TK;   rl = idx / SPLIT_TK; }
+      const int r = r0 + rl, l = lt + ll;
+      double2 v = make_double2(0.0, 0.0);
+      if (r < R && l < K) v = p.trans ? P[l + r * ld] : P[r + l * ld];
+      if (p.conj) v.y = -v.y;
+      // a non-finite scalar was already flagged; split it as zero
+      if (!isfinite(v.x)) v.x = 0.0;
+      if (!isfinite(v.y)) v.y = 0.0;
+      tile[rl][ll] = v;
+    }
+    __syncthreads();
+    // each thread: one row, 8 consecutive l
+    {
+      const int rl = tid / 8;
+      const int lg = (tid % 8) * 8;
+      const int r = r0 + rl;
+      if (r < R) {
+        const int e = rowexp[rl];
+        for (int q = 0; q < 8; ++q) {
+          const int l = lt + lg + q;
+          if (l >= K) break;
+          const double2 v = tile[rl][lg + q];
+          int dr[16], di[16];
+          digits_of(v.x, e, p.nbits, S, dr);
+          digits_of(v.y, e, p.nbits, S, di);
+          for (int s = 0; s < S; ++s) {
+            __half* o = outz + s * plane;
+            if (p.side == 0) {
+              o[r * p.kpad + l] = __int2half_rn(dr[s]);
+              o[r * p.kpad + K + l] = __int2half_rn(di[s]);
+              if (dbg) {
+                p.dbg_digits[s * dplane + r * 2LL * K + l] = static_cast<int16_t>(dr[s]);
+                p.dbg_digits[s * dplane + r * 2LL * K + K + l] = static_cast<int16_t>(di[s]);
+              }
+            } else {
+              const long long row0 = 2LL * r, row1 = 2LL * r + 1;
+              o[row0 * p.kpad + l] = __int2half_rn(dr[s]);
+              o[row0 * p.kpad + K + l] = __int2half_rn(-di[s]);
+              o[row1 * p.kpad + l] = __int2half_rn(di[s]);
+              o[row1 * p.kpad + K + l] = __int2half_rn(dr[s]);
+              if (dbg) {
+                p.dbg_digits[s * dplane + row0 * 2LL * K + l] = static_cast<int16_t>(dr[s]);
+                p.dbg_digits[s * dplane + row0 * 2LL * K + K + l] = static_cast<int16_t>(-di[s]);
+                p.dbg_digits[s * dplane + row1 * 2LL * K + l] = static_cast<int16_t>(di[s]);
+                p.dbg_digits[s * dplane + row1 * 2LL * K + K + l] = static_cast<int16_t>(dr[s]);
+              }
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // zero the K padding [2K, kpad) of the rows this CTA owns
+  const int pad = static_cast<int>(p.kpad) - 2 * K;
+  if (pad > 0) {
+    const int rows_out = p.side == 0 ? 1 : 2;
+    const int nr = min(SPLIT_ROWS, R - r0) * rows_out;
+    for (int idx = tid; idx < S * nr * pad; idx += SPLIT_THREADS) {
+      const int c = idx % pad;
+      const int rr = (idx / pad) % nr;
+      const int s = idx / (pad * nr);
+      outz[s * plane + (static_cast<long long>(r0) * rows_out + rr) * p.kpad + 2 * K + c] = __float2half(0.0f);
+    }
+  }
+}
+
+void launch_split(const SplitParams& p, int max_rows, int batch, cudaStream_t st) {
+  dim3 grid((max_rows + SPLIT_ROWS - 1) / SPLIT_ROWS, batch);
+  split_kernel<<<grid, SPLIT_THREADS, 0, st>>>(p);
+  record_launch();
+}
+
+}  // namespace ozk

@@ -10,3 +10,5 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a) and the built library")
+
+from gpu_util import handle, ozk_mod  # noqa: E402,F401  (GPU fixtures)

@@ -1,0 +1,99 @@
+"""GPU parity of the KKR tau_00 path (M build, pivot-block inverses, block LU with every GEMM
+emulated, batched lockstep solves) against the CPU oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import c_oracle as co
+from oracle import kkr
+
+pytestmark = pytest.mark.gpu
+
+
+def _system(L, E=0.5 + 0.05j, b=16, atom=0):
+    t, G, pos = synth.kkr_system(L, b, E, atom=atom)
+    return t, G, kkr.kkr_build(t, G)
+
+
+def _tblocks(ozk, t):
+    import torch
+    # L x b x b with column-major blocks: store the transpose of each block row-major
+    return torch.from_numpy(np.ascontiguousarray(np.transpose(t, (0, 2, 1)))).to("cuda")
+
+
+def test_build_m(ozk_mod, handle):
+    t, G, M = _system(15)
+    Md = ozk_mod.colmajor_cuda(np.zeros_like(M))
+    ozk_mod.kkr_build_m(handle, _tblocks(ozk_mod, t), ozk_mod.colmajor_cuda(G), Md)
+    got = ozk_mod.to_numpy(Md)
+    assert np.abs(got - M).max() <= 32 * np.finfo(float).eps
+
+
+@pytest.mark.parametrize("S", [0, 5, 7])
+def test_tau00_small_vs_oracles(ozk_mod, handle, S):
+    t, G, M = _system(15)
+    tau = ozk_mod.colmajor_cuda(np.zeros((16, 16), dtype=np.complex128))
+    ozk_mod.kkr_tau00(handle, ozk_mod.colmajor_cuda(M), ozk_mod.colmajor_cuda(t[0]), tau, S=S, nb=16)
+    assert handle.status() == 0
+    got = ozk_mod.to_numpy(tau)
+    full = kkr.tau00_full(M, t[0])
+    blk = co.tau00_block(M, t[0], 16, S=S)
+    if S == 0:
+        assert kkr.rel_err(got, full) < 1e-13
+    else:
+        # same algorithm and the same emulated GEMMs: only the binary64 pivot inverses differ
+        assert kkr.rel_err(got, blk) < 1e-13
+        assert kkr.rel_err(got, full) <= (1e-10 if S >= 7 else 1e-6)
+
+
+def test_tau00_config2_single_atom(ozk_mod, handle):
+    """bcc LIZ 65, b = 16, n = 1040, E = 0.5 + 0.05i, S = 7: within 1e-10 of the binary64
+    full-inverse oracle; the error falls with S."""
+    t, G, M = _system(65)
+    full = co.tau00_full(M, t[0])
+    errs = {}
+    for S in (3, 5, 7, 9):
+        tau = ozk_mod.colmajor_cuda(np.zeros((16, 16), dtype=np.complex128))
+        ozk_mod.kkr_tau00(handle, ozk_mod.colmajor_cuda(M), ozk_mod.colmajor_cuda(t[0]), tau, S=S, nb=16)
+        errs[S] = kkr.rel_err(ozk_mod.to_numpy(tau), full)
+    assert handle.status() == 0
+    assert errs[7] <= 1e-10 and errs[9] <= 1e-12
+    assert errs[3] > errs[5] > errs[7]
+
+
+def test_tau00_wider_panels(ozk_mod, handle):
+    t, G, M = _system(27)
+    full = kkr.tau00_full(M, t[0])
+    for nb in (32, 48):
+        tau = ozk_mod.colmajor_cuda(np.zeros((16, 16), dtype=np.complex128))
+        ozk_mod.kkr_tau00(handle, ozk_mod.colmajor_cuda(M), ozk_mod.colmajor_cuda(t[0]), tau, S=7, nb=nb)
+        assert kkr.rel_err(ozk_mod.to_numpy(tau), full) <= 1e-10
+
+
+def test_batched_equals_single(ozk_mod, handle):
+    sizes = [27, 9, 51, 15, 2]
+    Es = [0.5 + 0.05j, -1.0 + 0.3j, 0.69 + 0.01j, 0.2 + 0.9j, 0.6 + 0.2j]
+    systems = [_system(L, E, atom=i) for i, (L, E) in enumerate(zip(sizes, Es))]
+    single = []
+    for t, G, M in systems:
+        tau = ozk_mod.colmajor_cuda(np.zeros((16, 16), dtype=np.complex128))
+        ozk_mod.kkr_tau00(handle, ozk_mod.colmajor_cuda(M), ozk_mod.colmajor_cuda(t[0]), tau, S=7, nb=16)
+        single.append(ozk_mod.to_numpy(tau))
+    Ms = [ozk_mod.colmajor_cuda(M) for t, G, M in systems]
+    t0s = [ozk_mod.colmajor_cuda(t[0]) for t, G, M in systems]
+    taus = [ozk_mod.colmajor_cuda(np.zeros((16, 16), dtype=np.complex128)) for _ in systems]
+    ozk_mod.kkr_tau00_batched(handle, Ms, t0s, taus, S=7, nb=16)
+    assert handle.status() == 0
+    for i, (t, G, M) in enumerate(systems):
+        got = ozk_mod.to_numpy(taus[i])
+        assert np.array_equal(got, single[i])
+        assert kkr.rel_err(got, kkr.tau00_full(M, t[0])) <= 1e-10
+
+
+def test_singular_pivot_sets_status(ozk_mod, handle):
+    M = np.eye(32, dtype=np.complex128)
+    M[16:, 16:] = 0.0                    # the first eliminated pivot block is exactly singular
+    t0 = np.eye(16, dtype=np.complex128)
+    tau = ozk_mod.colmajor_cuda(np.zeros((16, 16), dtype=np.complex128))
+    ozk_mod.kkr_tau00(handle, ozk_mod.colmajor_cuda(M), ozk_mod.colmajor_cuda(t0), tau, S=5, nb=16)
+    assert handle.status() & (1 << 3)

@@ -1,0 +1,194 @@
+"""GPU parity of the emulated ZGEMM (split, tensor-core group sums, reconstruction) against the
+CPU oracle, through the C ABI.  Integer stages are compared bit for bit; the binary64 results
+of the store and LU epilogues too (both sides round the same exact value once)."""
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import op, rand_complex, stored
+from oracle import c_oracle as co
+from oracle import ozaki as oz
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(ozk, X):
+    return ozk.colmajor_cuda(X)
+
+
+@pytest.mark.parametrize("S", [1, 3, 7, 8, 10, 16])
+@pytest.mark.parametrize("shape", [(1, 1), (33, 17), (130, 70)])
+def test_split_left_bit_exact(ozk_mod, handle, S, shape):
+    A = rand_complex(*shape, seed=100 + S)
+    A[min(2, shape[0] - 1)] = 0.0
+    e, d = ozk_mod.ozk_split_debug(handle, _dev(ozk_mod, A), 0, S)
+    e_ref, d_ref = oz.split_left(A, S) if S <= 10 else co.split_left(A, S)
+    assert np.array_equal(ozk_mod.to_numpy(e).astype(np.int64), e_ref)
+    assert np.array_equal(ozk_mod.to_numpy(d).astype(np.int64), d_ref)
+
+
+@pytest.mark.parametrize("trans", ["N", "T", "C"])
+def test_split_right_bit_exact(ozk_mod, handle, trans):
+    S = 5
+    Bop = rand_complex(29, 41, seed=7)               # op(B) is k x n = 29 x 41
+    Bst = stored(Bop, trans)
+    e, d = ozk_mod.ozk_split_debug(handle, _dev(ozk_mod, Bst), 1, S, trans)
+    f_ref, d_ref = co.split_right(Bop, S)
+    assert np.array_equal(ozk_mod.to_numpy(e).astype(np.int64), f_ref)
+    assert np.array_equal(ozk_mod.to_numpy(d).astype(np.int64), d_ref)
+
+
+def test_split_subnormal_and_extreme_rows(ozk_mod, handle):
+    A = rand_complex(40, 9, seed=3)
+    A[0] = 5e-324
+    A[1, 3] = 1e300 + 1e-300j
+    A[2] = -np.ldexp(1.0, -1022)
+    A[3, :] = np.ldexp(1.0, 7)
+    e, d = ozk_mod.ozk_split_debug(handle, _dev(ozk_mod, A), 0, 9)
+    e_ref, d_ref = co.split_left(A, 9)
+    assert np.array_equal(ozk_mod.to_numpy(e).astype(np.int64), e_ref)
+    assert np.array_equal(ozk_mod.to_numpy(d).astype(np.int64), d_ref)
+
+
+@pytest.mark.parametrize("S,mode", [(1, 0), (4, 0), (7, 0), (8, 0), (9, 0), (12, 0), (3, 1), (5, 1), (8, 1)])
+@pytest.mark.parametrize("mnk", [(7, 5, 3), (129, 40, 77), (256, 65, 300)])
+def test_group_sums_bit_exact(ozk_mod, handle, S, mode, mnk):
+    m, n, k = mnk
+    A = rand_complex(m, k, seed=200 + S)
+    B = rand_complex(k, n, seed=300 + S)
+    G = ozk_mod.to_numpy(ozk_mod.ozk_group_sums_debug(handle, _dev(ozk_mod, A), _dev(ozk_mod, B), S, mode))
+    e, DA = co.split_left(A, S)
+    f, DB = co.split_right(B, S)
+    ref = co.group_sums(DA, DB, S, full=bool(mode))
+    for g in sorted(ref):
+        assert np.array_equal(G[g - 2], ref[g]), f"group {g}"
+
+
+def test_group_sums_extreme_digits(ozk_mod, handle):
+    """Constant rows: the top group accumulates the largest digit product 2^14 over a full
+    exactness chunk, so its FP32 accumulator sits at the 2^24 bound."""
+    S, k = 8, 512
+    A = np.full((128, k), -0.9999999999999999 - 0.9999999999999999j)
+    B = np.full((k, 64), -0.9999999999999999 + 0.9999999999999999j)
+    G = ozk_mod.to_numpy(ozk_mod.ozk_group_sums_debug(handle, _dev(ozk_mod, A), _dev(ozk_mod, B), S))
+    e, DA = co.split_left(A, S)
+    f, DB = co.split_right(B, S)
+    ref = co.group_sums(DA, DB, S)
+    for g in sorted(ref):
+        assert np.array_equal(G[g - 2], ref[g])
+
+
+@pytest.mark.parametrize("S", [3, 5, 7, 9])
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "C"), ("C", "T")])
+def test_zgemm_store_bit_exact(ozk_mod, handle, S, ta, tb):
+    m, n, k = 150, 70, 45
+    Aop = rand_complex(m, k, seed=11 + S)
+    Bop = rand_complex(k, n, seed=12 + S)
+    A, B = _dev(ozk_mod, stored(Aop, ta)), _dev(ozk_mod, stored(Bop, tb))
+    import torch
+    C = ozk_mod.colmajor_cuda(np.zeros((m, n), dtype=np.complex128))
+    ozk_mod.ozaki_zgemm(handle, A, B, C, S=S, transa=ta, transb=tb)
+    ref = co.zgemm(Aop, Bop, S)
+    assert np.array_equal(ozk_mod.to_numpy(C), ref)
+    assert handle.status() == 0
+
+
+def test_zgemm_lu_update_bit_exact(ozk_mod, handle):
+    m, n, k, S = 300, 200, 16, 7
+    A, B, C0 = rand_complex(m, k, 1), rand_complex(k, n, 2), rand_complex(m, n, 3)
+    C = _dev(ozk_mod, C0)
+    ozk_mod.ozaki_zgemm(handle, _dev(ozk_mod, A), _dev(ozk_mod, B), C, S=S, alpha=-1.0, beta=1.0)
+    assert np.array_equal(ozk_mod.to_numpy(C), co.zgemm_lu(C0, A, B, S))
+
+
+def test_zgemm_full_pairs_bit_exact(ozk_mod, handle):
+    m, n, k, S = 70, 33, 20, 4
+    A, B = rand_complex(m, k, 41), rand_complex(k, n, 42)
+    C = _dev(ozk_mod, np.zeros((m, n), dtype=np.complex128))
+    ozk_mod.ozaki_zgemm(handle, _dev(ozk_mod, A), _dev(ozk_mod, B), C, S=S, pair_mode=ozk_mod.OZK_PAIRS_FULL)
+    assert np.array_equal(ozk_mod.to_numpy(C), co.zgemm(A, B, S, full=True))
+
+
+def test_zgemm_general_alpha_beta(ozk_mod, handle):
+    m, n, k, S = 90, 50, 30, 7
+    A, B, C0 = rand_complex(m, k, 5), rand_complex(k, n, 6), rand_complex(m, n, 7)
+    al, be = 0.75 - 0.5j, -1.25 + 0.25j
+    C = _dev(ozk_mod, C0)
+    ozk_mod.ozaki_zgemm(handle, _dev(ozk_mod, A), _dev(ozk_mod, B), C, S=S, alpha=al, beta=be)
+    Z = co.zgemm(A, B, S)
+    ref = al * Z + be * C0
+    got = ozk_mod.to_numpy(C)
+    # binary64 complex arithmetic in a different operation order: a few ulps of |terms|
+    scale = np.abs(al) * np.abs(Z) + np.abs(be) * np.abs(C0)
+    assert np.all(np.abs(got - ref) <= 8 * np.finfo(float).eps * scale)
+
+
+def test_config1_full_size_bit_exact_and_error(ozk_mod, handle):
+    """512^3 complex, S = 7 (the single-GEMM workload): bitwise equal to the oracle,
+    relative Frobenius error vs binary64 <= 1e-13."""
+    A, B = synth.zgemm_operands(512, 512, 512)
+    C = _dev(ozk_mod, np.zeros((512, 512), dtype=np.complex128))
+    ozk_mod.ozaki_zgemm(handle, _dev(ozk_mod, A), _dev(ozk_mod, B), C, S=7)
+    got = ozk_mod.to_numpy(C)
+    ref = co.zgemm(A, B, 7)
+    assert np.array_equal(got, ref)
+    X = co.zgemm_fp64(A, B)
+    assert np.linalg.norm(got - X) / np.linalg.norm(X) <= 1e-13
+
+
+@pytest.mark.parametrize("S", [3, 7, 10])
+def test_large_k_multi_chunk(ozk_mod, handle, S):
+    m, n, k = 64, 16, 2500
+    A, B = rand_complex(m, k, 70), rand_complex(k, n, 71)
+    C = _dev(ozk_mod, np.zeros((m, n), dtype=np.complex128))
+    ozk_mod.ozaki_zgemm(handle, _dev(ozk_mod, A), _dev(ozk_mod, B), C, S=S)
+    assert np.array_equal(ozk_mod.to_numpy(C), co.zgemm(A, B, S))
+
+
+def test_vbatched_matches_single(ozk_mod, handle):
+    shapes = [(40, 30, 20), (129, 64, 16), (7, 3, 20), (200, 100, 5)]
+    As, Bs, Cs, refs = [], [], [], []
+    for i, (m, n, k) in enumerate(shapes):
+        A, B = rand_complex(m, k, 80 + i), rand_complex(k, n, 90 + i)
+        As.append(_dev(ozk_mod, A)); Bs.append(_dev(ozk_mod, B))
+        Cs.append(_dev(ozk_mod, np.zeros((m, n), dtype=np.complex128)))
+        refs.append(co.zgemm(A, B, 6))
+    ozk_mod.ozaki_zgemm_vbatched(handle, As, Bs, Cs, S=6)
+    for C, r in zip(Cs, refs):
+        assert np.array_equal(ozk_mod.to_numpy(C), r)
+
+
+def test_dmma_within_binary64_bound(ozk_mod, handle):
+    m, n, k = 257, 130, 300
+    A, B = rand_complex(m, k, 13), rand_complex(k, n, 14)
+    C = _dev(ozk_mod, np.zeros((m, n), dtype=np.complex128))
+    ozk_mod.ozk_zgemm_dmma(handle, _dev(ozk_mod, A), _dev(ozk_mod, B), C)
+    got = ozk_mod.to_numpy(C)
+    X = co.zgemm_fp64(A, B)
+    gamma = 2 * k * np.finfo(float).eps
+    assert np.all(np.abs(got - X) <= 2 * gamma * (np.abs(A) @ np.abs(B)))
+
+
+def test_degenerate_calls(ozk_mod, handle):
+    import torch
+    A = _dev(ozk_mod, rand_complex(5, 4, 1))
+    B = _dev(ozk_mod, rand_complex(4, 3, 2))
+    C0 = rand_complex(5, 3, 3)
+    C = _dev(ozk_mod, C0)
+    # alpha = 0: C = beta C
+    ozk_mod.ozaki_zgemm(handle, A, B, C, S=4, alpha=0.0, beta=2.0)
+    assert np.array_equal(ozk_mod.to_numpy(C), 2.0 * C0)
+    with pytest.raises(ozk_mod.OzkError):
+        ozk_mod.ozaki_zgemm(handle, A, B, C, S=0)
+    with pytest.raises(ozk_mod.OzkError):
+        ozk_mod.ozaki_zgemm(handle, A, B, C, S=17)
+
+
+def test_nonfinite_input_sets_status(ozk_mod, handle):
+    A = rand_complex(20, 8, 1)
+    A[4, 2] = np.nan
+    B = rand_complex(8, 6, 2)
+    C = _dev(ozk_mod, np.zeros((20, 6), dtype=np.complex128))
+    ozk_mod.ozaki_zgemm(handle, _dev(ozk_mod, A), _dev(ozk_mod, B), C, S=5)
+    assert handle.status() & (1 << 2)
+    assert handle.status() == 0          # cleared after reading
