@@ -1,0 +1,422 @@
+#!/usr/bin/env python
+"""Benchmark of the emulated-ZGEMM KKR tau_00 path on GB300 (one JSON line on stdout).
+
+Workload (one "step"): the single-atom KKR system of the paper's LSMS setting at its
+configuration-2 shape -- bcc LIZ of 65 sites, lmax = 3 (b = 16), n = 1040, E = 0.5 + 0.05i --
+for a batch of atoms per GPU (independent single-site t per atom, one structure-constant
+matrix G per energy, all synthetic and seeded): M = I - t G is built on the GPU, then the
+block-LU solve with every GEMM emulated (S = 7 slices) yields tau_00 of every atom.
+Metric: tau_00 solves per second (whole job, all GPUs), effective FP64 flops (8/3) n^3 per
+solve reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 launch with torchrun (one rank per GPU, NCCL); every rank solves its own batch
+(weak scaling) and rank 0 prints the line.  ``--impl reference`` times the CPU oracle
+(oracle/) on the host cores instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "emulated ZGEMM eff. FP64 TFLOPS and tau_00 solves/s vs FP64 DMMA at <=1e-10 error"
+L_SITES, B, E0 = 65, 16, 0.5 + 0.05j
+N = L_SITES * B
+FLOPS_PER_SOLVE = 8.0 / 3.0 * N ** 3          # effective FP64 flops of one tau_00 solve
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# dram bytes per slice_gemm launch from the committed ncu capture of this workload (profiles/);
+# None until a capture of the current kernel exists
+SLICE_GEMM_DRAM_BYTES_PER_LAUNCH = None
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=64, help="atoms per GPU per step")
+    ap.add_argument("--S", type=int, default=7)
+    ap.add_argument("--nb", type=int, default=64)
+    ap.add_argument("--no-extras", action="store_true", help="skip comparisons and the CPU baseline")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(PEAKS) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            c = [x.strip() for x in line.split(",")]
+            if len(c) < 9:
+                continue
+            try:
+                sms.append(float(c[1]))
+                mx = float(c[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, c[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sms) if sms else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sms)}
+
+
+# ----------------------------------------------------------------------------- inputs
+def make_inputs(rank: int, batch: int):
+    """Single-site t of `batch` atoms and the structure-constant matrix G they share (one
+    lattice, one energy), numpy, mathematical orientation."""
+    import synth
+    t_first, G, _ = synth.kkr_system(L_SITES, B, E0, atom=rank * batch)
+    return [t_first] + [synth.kkr_t(L_SITES, B, atom=rank * batch + a) for a in range(1, batch)], G
+
+
+def colblocks(t):
+    import numpy as np
+    return np.ascontiguousarray(np.transpose(t, (0, 2, 1)))      # column-major b x b blocks
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2603_29975_gb300 as ozk
+
+    h = ozk.Handle()
+    batch = args.batch
+    t_np, G_np = make_inputs(rank, batch)
+    G = torch.from_numpy(np.asfortranarray(G_np)).to(dev)
+    ts = [torch.from_numpy(colblocks(t)).to(dev) for t in t_np]
+    # only device pointers cross the C ABI: M (n x n), tau (b x b) and the t blocks are
+    # column-major buffers; block 0 of each atom's t is its t_0
+    Ms = [torch.empty((N, N), dtype=torch.complex128, device=dev) for _ in range(batch)]
+    taus = [torch.zeros((B, B), dtype=torch.complex128, device=dev) for _ in range(batch)]
+    i64 = lambda xs: torch.tensor([x.data_ptr() for x in xs], dtype=torch.int64, device=dev)
+    pt, pg, pm = i64(ts), i64([G] * batch), i64(Ms)
+    pt0, ptau = i64(ts), i64(taus)
+    Ls = [L_SITES] * batch
+    ns = [N] * batch
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
+
+    def step():
+        ozk.kkr_build_m_batched_ptrs(h, Ls, B, pt, pg, pm)
+        ozk.kkr_tau00_batched_ptrs(h, ns, B, pm, pt0, ptau, S=args.S, nb=args.nb)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if h.status():
+        raise RuntimeError("device status set during warm-up")
+
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clk = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    l0 = ozk.launch_count()
+    h.profile_begin()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))                     # L2 flush between timed steps (not timed)
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    prof = h.profile_end()
+    launches = ozk.launch_count() - l0
+    clocks = clk.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    local_ms = sum(step_ms)
+    if world > 1:
+        tt = torch.tensor([local_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        local_ms = float(tt.item())
+        dist.barrier()
+    if h.status():
+        raise RuntimeError("device status set during the timed steps")
+    ms_per_step = local_ms / args.steps
+    solves_per_s = world * batch * args.steps / (local_ms / 1e3)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    pk, pk_kind = peaks()
+    sg = prof["slice_gemm"]
+    achieved = sg["flops"] / (sg["ms"] / 1e3) / 1e12 if sg["ms"] > 0 else 0.0
+    peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+    per_launch = sg["flops"] / max(1, sg["launches"])
+    roofline = {"bound": "tensor", "kernel": "slice_gemm_kernel (tcgen05 kind::f16, fp16-held int8 digits)",
+                "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "peak_source": f"{pk_kind} bf16 sustained (fp16 same rate)",
+                "traffic": SLICE_GEMM_DRAM_BYTES_PER_LAUNCH,
+                "algorithmic_flops_per_launch": per_launch, "launches": sg["launches"],
+                "avg_launch_us": round(1e3 * sg["ms"] / max(1, sg["launches"]), 2)}
+    kernels = {k: {"launches": v["launches"], "ms_per_step": round(v["ms"] / args.steps, 3),
+                   "share": round(v["ms"] / max(1e-9, sum(x["ms"] for x in prof.values())), 4)}
+               for k, v in prof.items() if v["launches"]}
+
+    line = {"metric": METRIC, "value": round(solves_per_s, 2), "unit": "tau00 solves/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int8 digits (fp16-held) x tensor cores -> exact int -> f64",
+            "data": "synthetic (seeded SplitMix64; bcc LIZ, KKR-shaped t and G)",
+            "config": {"workload": f"KKR tau_00, bcc LIZ {L_SITES} sites, lmax=3 (b={B}), n={N}, E=0.5+0.05i; "
+                                   f"{batch} atoms per GPU per step; M=I-tG built on GPU; block LU nb={args.nb}, "
+                                   f"every GEMM emulated with S={args.S}",
+                       "atoms_per_gpu_per_step": batch, "n": N, "S": args.S, "nb": args.nb,
+                       "eff_fp64_flops_per_solve": FLOPS_PER_SOLVE,
+                       "l2": "256 MB buffer written between timed steps (outside the events); per-step "
+                             f"working set {batch * N * N * 16 / 2**30:.2f} GiB of M",
+                       "parallelism": f"dp{world} (independent atoms per GPU)"},
+            "eff_fp64_tflops": round(solves_per_s * FLOPS_PER_SOLVE / 1e12, 3),
+            "roofline": roofline, "kernels": kernels, "gpu_launches": int(launches),
+            "clocks": clocks, "wall_s_timed": round(t_wall, 3)}
+    if not args.no_extras:
+        line["e2e"] = e2e_measure(ozk, h, args, dev, t_np, G_np, batch)
+        line["comparisons"] = comparisons(ozk, h, args, dev, t_np, G_np)
+        line["cpu_baseline"] = cpu_baseline(t_np[0], G_np, args.S, args.nb)
+    print(json.dumps(line))
+    h.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def e2e_measure(ozk, h, args, dev, t_np, G_np, batch):
+    """Same metric through the public API with HOST inputs: pinned t and G copied in each step,
+    tau_00 of every atom copied back, all inside the timed region."""
+    import numpy as np
+    import torch
+    Gh = torch.from_numpy(np.ascontiguousarray(G_np.T)).pin_memory()     # column-major buffer of G
+    th = torch.from_numpy(np.stack([colblocks(t) for t in t_np])).pin_memory()
+    Gd = torch.empty((N, N), dtype=torch.complex128, device=dev)
+    td = torch.empty(th.shape, dtype=torch.complex128, device=dev)
+    Ms = [torch.empty((N, N), dtype=torch.complex128, device=dev) for _ in range(batch)]
+    taus = torch.zeros((batch, B, B), dtype=torch.complex128, device=dev)
+    tau_h = torch.zeros((batch, B, B), dtype=torch.complex128).pin_memory()
+    i64 = lambda xs: torch.tensor(xs, dtype=torch.int64, device=dev)
+    pt = i64([td[a].data_ptr() for a in range(batch)])
+    pg = i64([Gd.data_ptr()] * batch)
+    pm = i64([m.data_ptr() for m in Ms])
+    pt0 = i64([td[a].data_ptr() for a in range(batch)])      # block 0 of each t is t_0
+    ptau = i64([taus[a].data_ptr() for a in range(batch)])
+    Ls, ns = [L_SITES] * batch, [N] * batch
+    steps = max(2, min(args.steps, 5))
+
+    def step():
+        Gd.copy_(Gh, non_blocking=True)
+        td.copy_(th, non_blocking=True)
+        ozk.kkr_build_m_batched_ptrs(h, Ls, B, pt, pg, pm)
+        ozk.kkr_tau00_batched_ptrs(h, ns, B, pm, pt0, ptau, S=args.S, nb=args.nb)
+        tau_h.copy_(taus, non_blocking=True)
+
+    step()
+    torch.cuda.synchronize()
+    a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        step()
+    b_.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b_) / steps
+    return {"value": round(batch / (ms / 1e3), 2), "unit": "tau00 solves/s",
+            "h2d_bytes_per_step": int(Gh.numel() * 16 + th.numel() * 16),
+            "d2h_bytes_per_step": int(tau_h.numel() * 16), "steps": steps}
+
+
+def rel_err(X, Y) -> float:
+    import numpy as np
+    d = np.linalg.norm(Y)
+    return float(np.linalg.norm(X - Y) / d) if d else float(np.linalg.norm(X))
+
+
+def comparisons(ozk, h, args, dev, t_np, G_np):
+    """FP64 DMMA baseline and accuracy on the same GPU, plus single-GEMM throughput (not timed
+    as part of the step)."""
+    import numpy as np
+    import torch
+    import synth
+    out = {}
+    t0 = t_np[0]
+    Gd = torch.from_numpy(np.asfortranarray(G_np)).to(dev)
+    tb = torch.from_numpy(colblocks(t0)).to(dev)
+    t0d = torch.from_numpy(np.asfortranarray(t0[0])).to(dev)
+    M = torch.empty((N, N), dtype=torch.complex128, device=dev).t()
+
+    def solve(S, reps, nb_override=None):
+        taus = []
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ms = 0.0
+        for r in range(reps):
+            ozk.kkr_build_m(h, tb, Gd, M)
+            tau = torch.zeros((B, B), dtype=torch.complex128, device=dev).t()
+            ev[0].record()
+            ozk.kkr_tau00(h, M, t0d, tau, S=S, nb=nb_override or args.nb)
+            ev[1].record()
+            torch.cuda.synchronize()
+            ms += ev[0].elapsed_time(ev[1])
+            taus.append(tau.cpu().numpy())
+        return taus[-1], ms / reps
+
+    tau_ref, ms_dmma = solve(0, 2, nb_override=32)
+    out["dmma_tau00_solve_ms"] = round(ms_dmma, 3)
+    out["dmma_tau00_nb"] = 32
+    out["dmma_tau00_solves_per_s_single"] = round(1e3 / ms_dmma, 2)
+    errs = {}
+    for S in (3, 5, 6, 7, 8, 9):
+        tau, ms = solve(S, 2)
+        errs[str(S)] = {"rel_err_vs_dmma_fp64": float(rel_err(tau, tau_ref)), "single_solve_ms": round(ms, 3)}
+    out["tau00_per_S"] = errs
+    # single ZGEMM, 512^3 (configuration 1) and 2048^3
+    for (m, S) in ((512, 7), (2048, 7)):
+        A, Bm = synth.zgemm_operands(m, m, m)
+        Ad = ozk.colmajor_cuda(A)
+        Bd = ozk.colmajor_cuda(Bm)
+        C = ozk.colmajor_cuda(np.zeros((m, m), dtype=np.complex128))
+        C2 = ozk.colmajor_cuda(np.zeros((m, m), dtype=np.complex128))
+        for _ in range(2):
+            ozk.ozaki_zgemm(h, Ad, Bd, C, S=S)
+            ozk.ozk_zgemm_dmma(h, Ad, Bd, C2)
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        reps = 5
+        e[0].record()
+        for _ in range(reps):
+            ozk.ozaki_zgemm(h, Ad, Bd, C, S=S)
+        e[1].record()
+        for _ in range(2):
+            ozk.ozk_zgemm_dmma(h, Ad, Bd, C2)
+        e[2].record()
+        torch.cuda.synchronize()
+        t_emu = e[0].elapsed_time(e[1]) / reps
+        t_dm = e[1].elapsed_time(e[2]) / 2
+        fl = 8.0 * m ** 3
+        out[f"zgemm_{m}^3_S{S}"] = {"emulated_eff_fp64_tflops": round(fl / t_emu / 1e9, 3),
+                                    "dmma_tflops": round(fl / t_dm / 1e9, 3),
+                                    "rel_err_vs_dmma": float(rel_err(C.cpu().numpy(), C2.cpu().numpy()))}
+    return out
+
+
+def cpu_baseline(t0_atom, G_np, S, nb):
+    """The oracle (plain C, OpenMP on all host cores) on a bounded sample: one solve of the
+    same workload with every GEMM emulated."""
+    import numpy as np
+    from oracle import c_oracle as co
+    from oracle import kkr
+    co.build()
+    M = kkr.kkr_build(t0_atom, G_np)
+    t1 = time.perf_counter()
+    co.tau00_block(M, t0_atom[0], nb, S=S)
+    dt = time.perf_counter() - t1
+    return {"value": round(1.0 / dt, 4), "unit": "tau00 solves/s", "cores": co.num_threads(), "kind": "oracle",
+            "sample": f"1 solve of the same workload (n={N}, S={S}, nb={nb}) by oracle/c (OpenMP), {dt:.1f} s"}
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    import synth
+    from oracle import c_oracle as co
+    from oracle import kkr
+    co.build()
+    t, G, _ = synth.kkr_system(L_SITES, B, E0, atom=0)
+    M = kkr.kkr_build(t, G)
+    for _ in range(args.warmup):
+        co.tau00_block(M, t[0], args.nb, S=args.S)
+    t1 = time.perf_counter()
+    for _ in range(args.steps):
+        co.tau00_block(M, t[0], args.nb, S=args.S)
+    dt = time.perf_counter() - t1
+    v = args.steps / dt
+    sample = (f"{args.steps} timed solves of the configuration-2 system (n={N}, S={args.S}, nb={args.nb}) "
+              f"by oracle/c with OpenMP; one solve per step")
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "tau00 solves/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int8 digits -> exact int64/int128 -> f64 (CPU)", "data": "synthetic",
+            "config": {"workload": f"KKR tau_00, bcc LIZ {L_SITES} sites, b={B}, n={N}, E=0.5+0.05i, S={args.S}"},
+            "cpu_baseline": {"value": round(v, 4), "unit": "tau00 solves/s", "cores": co.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(v, 4), "unit": "tau00 solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -86,6 +86,26 @@ const char* ozk_last_error(void);
 /* Number of kernel launches this library has enqueued on this thread so far. */
 uint64_t ozk_launch_count(void);
 
+/* ---- launch profiler ---------------------------------------------------------------- */
+
+/* Kernel kinds reported by ozk_profile_end (array index). */
+#define OZK_KIND_SPLIT 0       /* exponent scan + slice split */
+#define OZK_KIND_SLICE_GEMM 1  /* tcgen05 slice-pair GEMM + reconstruction */
+#define OZK_KIND_GJ 2          /* pivot-block Gauss-Jordan inverse / solve */
+#define OZK_KIND_BUILD_M 3     /* M = I - t G */
+#define OZK_KIND_DMMA 4        /* binary64 DMMA ZGEMM */
+#define OZK_KIND_OTHER 5
+#define OZK_KERNEL_KINDS 6
+
+/* Start recording a CUDA event pair on the handle's stream around every launch (no
+ * synchronisation; negligible overhead), clearing earlier records. */
+ozk_status_t ozk_profile_begin(ozk_handle_t handle);
+/* Stop recording, synchronise, and return per kind (arrays of OZK_KERNEL_KINDS entries):
+ * launches, summed device milliseconds, summed algorithmic flops (slice GEMM: integer
+ * multiply-adds x 2 of all slice pairs, P_S 8 m n k; DMMA: 8 m n k) and algorithmic bytes. */
+ozk_status_t ozk_profile_end(ozk_handle_t handle, uint64_t* launches, double* ms, double* flops,
+                             double* bytes);
+
 /* ---- emulated ZGEMM (paper Sec. 2.2, Sec. 3.2) ------------------------------------ */
 
 /* C = alpha op(A) op(B) + beta C with op(X) in {'N', 'T', 'C'} (none, transpose,
@@ -139,11 +159,24 @@ ozk_status_t ozk_group_sums_debug(ozk_handle_t handle, char transa, char transb,
  *   G : DEVICE, n x n column major (ld n).  M: DEVICE, n x n column major (ld n). */
 ozk_status_t kkr_build_m(ozk_handle_t handle, int L, int b, const void* t, const void* G, void* M);
 
-/* tau_00 = [M^-1]_00 t_0 = S_00^-1 t_0 by block LU with every panel product and Schur update
- * an emulated ZGEMM with S slices (S <= 0: the binary64 DMMA ZGEMM instead).
+/* Batched M_z = I - t_z G_z for `batch` LIZs of L[z] sites (HOST array) with b x b blocks;
+ * t, G, M are DEVICE arrays of DEVICE pointers with the layouts of kkr_build_m.  Several
+ * entries may share one G (atoms of one lattice at one energy). */
+ozk_status_t kkr_build_m_batched(ozk_handle_t handle, int batch, const int* L, int b,
+                                 const void* const* t, const void* const* G, void* const* M);
+
+/* tau_00 = [M^-1]_00 t_0 = S_00^-1 t_0 by block LU (paper Sec. 3.2: LU-based inversion of the
+ * multiple scattering matrix).  Panels J = [p, q) of width nb are eliminated from the trailing
+ * end of M, so the centre block (site 0, rows/cols 0..b-1) is eliminated last and S_00 is the
+ * Schur complement left there.
+ *   S >= 1: every GEMM is the emulated ZGEMM with S slices; each panel is factored leaf by leaf
+ *           (b x b pivot blocks, Gauss-Jordan with partial pivoting in binary64), each leaf
+ *           updating only the rows and columns outside [0, p) x [0, p); the panel's update
+ *           of [0, p) x [0, p) is one GEMM with k = q - p.  nb <= 128.
+ *   S <= 0: binary64 DMMA GEMMs with one nb x nb pivot block per panel (nb <= 64).
  *   M   : DEVICE n x n column major (ld n), DESTROYED (overwritten by the factorisation).
  *   t0  : DEVICE b x b column major.  tau00: DEVICE b x b column major output.
- *   nb  : panel width, a multiple of b (16..64).  Site 0 occupies rows/cols 0..b-1. */
+ *   b <= 16, nb a multiple of b.  Site 0 occupies rows/cols 0..b-1. */
 ozk_status_t kkr_tau00(ozk_handle_t handle, int n, int b, void* M, const void* t0, void* tau00,
                        int S, int nb);
 

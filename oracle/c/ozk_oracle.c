@@ -334,44 +334,68 @@ static void put_block(double* dst, int ldd, int r0, int c0, int rows, int cols, 
 
 /* tau_00 = S00^-1 t0 by block LU: panels J = [p, q) are eliminated from the trailing end
  * of M towards the front, so the remainder is always the leading block R = [0, p) and the
- * centre block (site 0, rows/cols 0..b-1) is eliminated last:
- *     L_RJ = M_RJ D^-1,  M_RR -= L_RJ M_JR,  D = M_JJ (Gauss-Jordan inverse, partial pivoting).
- * S = 0: binary64 GEMMs; S > 0: every panel product and update is the emulated ZGEMM. */
-int oz_tau00_block(const double* M, const double* t0, int n, int b, int nb, int S, int full,
+ * centre block (site 0, rows/cols 0..b-1) is eliminated last.  leaf = 0: the whole panel is
+ * one pivot block (L_RJ = M_RJ D^-1, M_RR -= L_RJ M_JR).  leaf = w > 0: the panel is factored
+ * leaf by leaf from its last w-wide leaf [a, a+w): L column M[0:a, a:a+w] D_a^-1, then the
+ * rank-w update of [0, a) x [0, a) outside [0, p) x [0, p); after the panel, [0, p) x [0, p)
+ * gets the whole panel's update M[0:p, p:q] M[p:q, 0:p] at once.
+ * S = 0: binary64 GEMMs; S > 0: every GEMM is the emulated ZGEMM. */
+static int gemm_into(const double* X, const double* Y, int m, int n, int k, int S, int full, int lu, double* C) {
+    if (S > 0) return oz_zgemm(X, Y, m, n, k, S, full, lu, C);
+    if (!lu) { oz_zgemm_fp64(X, Y, m, n, k, C); return OZ_OK; }
+    double* P = (double*)malloc(sizeof(double) * 2 * (size_t)m * n);
+    oz_zgemm_fp64(X, Y, m, n, k, P);
+    for (long x = 0; x < 2L * m * n; x++) C[x] -= P[x];
+    free(P);
+    return OZ_OK;
+}
+
+int oz_tau00_block(const double* M, const double* t0, int n, int b, int nb, int leaf, int S, int full,
                    double* tau) {
-    if (n <= 0 || b <= 0 || n % b || nb <= 0) return OZ_ERR_ARG;
+    if (n <= 0 || b <= 0 || n % b || nb <= 0 || leaf < 0) return OZ_ERR_ARG;
     double* A = (double*)malloc(sizeof(double) * 2 * (size_t)n * n);
     memcpy(A, M, sizeof(double) * 2 * (size_t)n * n);
     int st = OZ_OK;
     for (int q = n; q > b && !st;) {
         int p = q - nb > b ? q - nb : b;
-        int w = q - p, r = p;
-        double* D = (double*)malloc(sizeof(double) * 2 * (size_t)w * w);
-        double* Lp = (double*)malloc(sizeof(double) * 2 * (size_t)r * w);
-        double* Up = (double*)malloc(sizeof(double) * 2 * (size_t)w * r);
-        double* Cr = (double*)malloc(sizeof(double) * 2 * (size_t)r * r);
-        double* T = (double*)malloc(sizeof(double) * 2 * (size_t)r * w);
-        copy_block(A, n, p, p, w, w, D);
-        st = oz_gepp_inverse(D, w);
-        if (!st) {
-            copy_block(A, n, 0, p, r, w, Lp);
-            if (S > 0) st = oz_zgemm(Lp, D, r, w, w, S, full, 0, T);
-            else oz_zgemm_fp64(Lp, D, r, w, w, T);
-            put_block(A, n, 0, p, r, w, T);
-            copy_block(A, n, p, 0, w, r, Up);
-            copy_block(A, n, 0, 0, r, r, Cr);
-            if (!st) {
-                if (S > 0) st = oz_zgemm(T, Up, r, r, w, S, full, 1, Cr);
-                else {
-                    double* P = (double*)malloc(sizeof(double) * 2 * (size_t)r * r);
-                    oz_zgemm_fp64(T, Up, r, r, w, P);
-                    for (long x = 0; x < 2L * r * r; x++) Cr[x] -= P[x];
-                    free(P);
-                }
-                put_block(A, n, 0, 0, r, r, Cr);
+        int w = leaf > 0 ? leaf : q - p;
+        for (int a = q - w; a >= p && !st; a -= w) {
+            double* D = (double*)malloc(sizeof(double) * 2 * (size_t)w * w);
+            double* Lc = (double*)malloc(sizeof(double) * 2 * (size_t)(a > 0 ? a : 1) * w);
+            double* T = (double*)malloc(sizeof(double) * 2 * (size_t)(a > 0 ? a : 1) * w);
+            copy_block(A, n, a, a, w, w, D);
+            st = oz_gepp_inverse(D, w);
+            if (!st && a > 0) {
+                copy_block(A, n, 0, a, a, w, Lc);
+                st = gemm_into(Lc, D, a, w, w, S, full, 0, T);
+                put_block(A, n, 0, a, a, w, T);
             }
+            if (!st && a > p) {
+                double* Ur = (double*)malloc(sizeof(double) * 2 * (size_t)w * a);
+                double* Cr = (double*)malloc(sizeof(double) * 2 * (size_t)a * a);
+                double* box = (double*)malloc(sizeof(double) * 2 * (size_t)p * p);
+                copy_block(A, n, a, 0, w, a, Ur);
+                copy_block(A, n, 0, 0, a, a, Cr);
+                copy_block(A, n, 0, 0, p, p, box);
+                st = gemm_into(T, Ur, a, a, w, S, full, 1, Cr);
+                put_block(A, n, 0, 0, a, a, Cr);
+                put_block(A, n, 0, 0, p, p, box);
+                free(Ur); free(Cr); free(box);
+            }
+            free(D); free(Lc); free(T);
         }
-        free(D); free(Lp); free(Up); free(Cr); free(T);
+        if (!st) {
+            int wp = q - p;
+            double* Lp = (double*)malloc(sizeof(double) * 2 * (size_t)p * wp);
+            double* Up = (double*)malloc(sizeof(double) * 2 * (size_t)wp * p);
+            double* Cr = (double*)malloc(sizeof(double) * 2 * (size_t)p * p);
+            copy_block(A, n, 0, p, p, wp, Lp);
+            copy_block(A, n, p, 0, wp, p, Up);
+            copy_block(A, n, 0, 0, p, p, Cr);
+            st = gemm_into(Lp, Up, p, p, wp, S, full, 1, Cr);
+            put_block(A, n, 0, 0, p, p, Cr);
+            free(Lp); free(Up); free(Cr);
+        }
         q = p;
     }
     if (!st) {

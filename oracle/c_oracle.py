@@ -48,7 +48,7 @@ def lib():
         L.oz_zgemm_fp64.restype = None
         L.oz_gepp_inverse.argtypes = [dp, ctypes.c_int]
         L.oz_tau00_block.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                     ctypes.c_int, dp]
+                                     ctypes.c_int, ctypes.c_int, dp]
         L.oz_tau00_full.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, dp]
         L.oz_num_threads.restype = ctypes.c_int
         _lib = L
@@ -146,11 +146,12 @@ def gepp_inverse(M):
     return M
 
 
-def tau00_block(M, t0, nb, S=0, full=False):
+def tau00_block(M, t0, nb, S=0, full=False, leaf=None):
     M, t0 = _c(M), _c(t0)
     n, b = M.shape[0], t0.shape[0]
     tau = np.zeros((b, b), dtype=np.complex128)
-    _check(lib().oz_tau00_block(_dp(M), _dp(t0), n, b, nb, S or 0, int(full), _dp(tau)), "tau00_block")
+    _check(lib().oz_tau00_block(_dp(M), _dp(t0), n, b, nb, leaf or 0, S or 0, int(full), _dp(tau)),
+           "tau00_block")
     return tau
 
 

@@ -59,8 +59,14 @@ def tau00_full(M: np.ndarray, t0: np.ndarray) -> np.ndarray:
     return gepp_inverse(M)[:b, :b] @ t0
 
 
-def tau00_block(M: np.ndarray, t0: np.ndarray, nb: int, S=None, mode: str = "tri") -> np.ndarray:
-    """Block LU eliminating from the trailing end, the centre block last (see module docstring)."""
+def tau00_block(M: np.ndarray, t0: np.ndarray, nb: int, S=None, mode: str = "tri", leaf=None) -> np.ndarray:
+    """Block LU eliminating from the trailing end, the centre block last (module docstring).
+
+    leaf=None: each panel J = [p, q) is one pivot block (D = M_JJ inverted whole).
+    leaf=w:    the panel is factored leaf by leaf (w x w pivot blocks, from its last leaf):
+               L column of the leaf, then its rank-w update of the rows and columns of
+               [0, a) outside [0, p) x [0, p); the update of [0, p) x [0, p) by the whole
+               panel is applied once afterwards.  Same block LU, fewer trailing updates."""
     b = t0.shape[0]
     A = np.array(M, dtype=np.complex128)
     n = A.shape[0]
@@ -71,12 +77,20 @@ def tau00_block(M: np.ndarray, t0: np.ndarray, nb: int, S=None, mode: str = "tri
     def sub_mul(C, X, Y):
         return C - X @ Y if S is None else ozaki.ozaki_lu_update(C, X, Y, S, mode)
 
-    q = n                                   # eliminate J = [p, q), keep R = [0, p)
+    q = n                                   # panel J = [p, q), remainder R = [0, p)
     while q > b:
         p = max(q - nb, b)
-        Dinv = gepp_inverse(A[p:q, p:q])
-        A[:p, p:q] = mul(A[:p, p:q], Dinv)                     # L panel = M_RJ D^-1
-        A[:p, :p] = sub_mul(A[:p, :p], A[:p, p:q], A[p:q, :p])  # Schur update of R
+        w = (q - p) if leaf is None else leaf
+        a = q - w
+        while a >= p:                        # leaves [a, a + w), last one first
+            Dinv = gepp_inverse(A[a:a + w, a:a + w])
+            A[:a, a:a + w] = mul(A[:a, a:a + w], Dinv)                       # L column
+            if a > p:
+                box = A[:p, :p].copy()
+                A[:a, :a] = sub_mul(A[:a, :a], A[:a, a:a + w], A[a:a + w, :a])  # outside the box
+                A[:p, :p] = box
+            a -= w
+        A[:p, :p] = sub_mul(A[:p, :p], A[:p, p:q], A[p:q, :p])                 # deferred update
         q = p
     return gepp_inverse(A[:b, :b]) @ t0
 

@@ -6,11 +6,13 @@ The compute path is libozk.so (CUDA kernels behind the C ABI in include/ozk.h);
 ``binding`` is its ctypes binding.  Build with ``python paper_2603_29975_gb300/build.py``.
 """
 from .binding import (OZK_PAIRS_FULL, OZK_PAIRS_TRI, Handle, OzkError, colmajor_cuda, kkr_build_m,
+                      kkr_build_m_batched_ptrs,
                       kkr_tau00, kkr_tau00_batched, kkr_tau00_batched_ptrs, launch_count, lib,
                       ozaki_zgemm, ozaki_zgemm_vbatched, ozk_group_sums_debug, ozk_split_debug,
                       ozk_zgemm_dmma, to_numpy)
 
 __all__ = ["OZK_PAIRS_FULL", "OZK_PAIRS_TRI", "Handle", "OzkError", "colmajor_cuda", "kkr_build_m",
+           "kkr_build_m_batched_ptrs",
            "kkr_tau00", "kkr_tau00_batched", "kkr_tau00_batched_ptrs", "launch_count", "lib",
            "ozaki_zgemm", "ozaki_zgemm_vbatched", "ozk_group_sums_debug", "ozk_split_debug",
            "ozk_zgemm_dmma", "to_numpy"]

@@ -24,7 +24,9 @@ STATUS_NAMES = {1: "ARG", 2: "NONFINITE", 3: "SINGULAR", 4: "TIMEOUT", 5: "CUDA"
 EXPORTS = ["ozk_create", "ozk_destroy", "ozk_set_stream", "ozk_get_status", "ozk_reserve",
            "ozk_zgemm_workspace_size", "ozk_last_error", "ozk_launch_count", "ozaki_zgemm",
            "ozaki_zgemm_vbatched", "ozk_zgemm_dmma", "ozk_split_debug", "ozk_group_sums_debug",
-           "kkr_build_m", "kkr_tau00", "kkr_tau00_batched"]
+           "kkr_build_m", "kkr_tau00", "kkr_tau00_batched", "ozk_profile_begin", "ozk_profile_end",
+           "kkr_build_m_batched"]
+KIND_NAMES = ["split", "slice_gemm", "gj", "build_m", "dmma", "other"]
 
 _lib = None
 
@@ -59,6 +61,9 @@ def lib():
         L.kkr_build_m.argtypes = [vp, i, i, vp, vp, vp]
         L.kkr_tau00.argtypes = [vp, i, i, vp, vp, vp, i, i]
         L.kkr_tau00_batched.argtypes = [vp, i, ip, i, vp, vp, vp, i, i]
+        L.kkr_build_m_batched.argtypes = [vp, i, ip, i, vp, vp, vp]
+        L.ozk_profile_begin.argtypes = [vp]
+        L.ozk_profile_end.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), dp, dp, dp]
         for name in EXPORTS:
             if name not in ("ozk_zgemm_workspace_size", "ozk_last_error", "ozk_launch_count"):
                 getattr(L, name).restype = ctypes.c_int
@@ -130,6 +135,18 @@ class Handle:
 
     def reserve(self, nbytes: int):
         _check(lib().ozk_reserve(self._h, nbytes), "ozk_reserve")
+
+    def profile_begin(self):
+        _check(lib().ozk_profile_begin(self._h), "ozk_profile_begin")
+
+    def profile_end(self) -> dict:
+        """Per kernel kind: launches, device ms, algorithmic flops and bytes (CUDA events)."""
+        K = len(KIND_NAMES)
+        n = (ctypes.c_uint64 * K)()
+        ms, fl, by = (ctypes.c_double * K)(), (ctypes.c_double * K)(), (ctypes.c_double * K)()
+        _check(lib().ozk_profile_end(self._h, n, ms, fl, by), "ozk_profile_end")
+        return {KIND_NAMES[k]: {"launches": int(n[k]), "ms": float(ms[k]), "flops": float(fl[k]),
+                                "bytes": float(by[k])} for k in range(K)}
 
     def close(self):
         if self._h:
@@ -229,7 +246,15 @@ def kkr_build_m(h: Handle, t, G, M):
     return M
 
 
-def kkr_tau00(h: Handle, M, t0, tau, S: int = 7, nb: int = 16):
+def kkr_build_m_batched_ptrs(h: Handle, L_list, b: int, pt, pg, pm):
+    """Batched M = I - t G with device pointer arrays (int64 CUDA tensors)."""
+    nb_ = len(L_list)
+    L = (ctypes.c_int * nb_)(*[int(v) for v in L_list])
+    _check(lib().kkr_build_m_batched(h.ptr, nb_, L, b, pt.data_ptr(), pg.data_ptr(), pm.data_ptr()),
+           "kkr_build_m_batched")
+
+
+def kkr_tau00(h: Handle, M, t0, tau, S: int = 7, nb: int = 64):
     """tau_00 = [M^-1]_00 t_0 (M is overwritten)."""
     n = M.shape[0]
     b = t0.shape[0]
@@ -238,7 +263,7 @@ def kkr_tau00(h: Handle, M, t0, tau, S: int = 7, nb: int = 16):
     return tau
 
 
-def kkr_tau00_batched(h: Handle, Ms, t0s, taus, S: int = 7, nb: int = 16):
+def kkr_tau00_batched(h: Handle, Ms, t0s, taus, S: int = 7, nb: int = 64):
     """Batched tau_00 over lists of column-major tensors (the Ms are overwritten)."""
     import torch
     ns = len(Ms)
@@ -253,7 +278,7 @@ def kkr_tau00_batched(h: Handle, Ms, t0s, taus, S: int = 7, nb: int = 16):
     return taus, (pm, pt, pu)
 
 
-def kkr_tau00_batched_ptrs(h: Handle, n_list, b: int, pm, pt, pu, S: int = 7, nb: int = 16):
+def kkr_tau00_batched_ptrs(h: Handle, n_list, b: int, pm, pt, pu, S: int = 7, nb: int = 64):
     """Batched tau_00 with device pointer arrays already built (int64 CUDA tensors)."""
     ns = len(n_list)
     n = (ctypes.c_int * ns)(*[int(v) for v in n_list])

@@ -67,13 +67,47 @@ static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 using namespace ozk;
 
+// Per-kernel-kind launch profiler: CUDA events recorded on the handle's stream around each
+// launch while enabled, with the algorithmic flops and bytes of that launch.
+struct ProfRec { int kind; cudaEvent_t a, b; double flops, bytes; };
+
 struct ozk_context {
   int device = 0;
   cudaStream_t stream = nullptr;
   int* d_status = nullptr;
   void* ws = nullptr;
   size_t ws_bytes = 0;
+  bool prof = false;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t pool_used = 0;
 };
+
+namespace {
+cudaEvent_t prof_event(ozk_context* h) {
+  if (h->pool_used == h->pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    h->pool.push_back(e);
+  }
+  return h->pool[h->pool_used++];
+}
+
+// RAII scope: records a start event before and a stop event after the launches in its body.
+struct Prof {
+  ozk_context* h; int kind; double flops, bytes; cudaEvent_t a = nullptr;
+  Prof(ozk_context* hh, int k, double f, double by) : h(hh), kind(k), flops(f), bytes(by) {
+    if (h->prof) { a = prof_event(h); cudaEventRecord(a, h->stream); }
+  }
+  ~Prof() {
+    if (h->prof) {
+      cudaEvent_t b = prof_event(h);
+      cudaEventRecord(b, h->stream);
+      h->recs.push_back({kind, a, b, flops, bytes});
+    }
+  }
+};
+}  // namespace
 
 // --------------------------------------------------------------------- workspace
 static ozk_status_t ensure_ws(ozk_context* h, size_t bytes) {
@@ -128,10 +162,14 @@ struct EmuGemm {
   int mode = -1;                             // -1: derive from alpha/beta
   long long* groups = nullptr;               // group dump (test hook)
   int16_t* dbg_digits_a = nullptr; int* dbg_exps_a = nullptr;
+  int skm = 0, skn = 0;                        // skip box (single problem)
+  const int* tskm = nullptr; const int* tskn = nullptr;   // skip box tables (batched)
+  double sum_mnk = -1;                        // sum over problems of m n k (batched; -1: single)
+  double sum_mk = 0, sum_nk = 0;              // operand sizes (complex elements) for byte counts
 };
 
 struct GemmPlan {
-  int G, BN, maxpairs, npairs, kpad, rowsA, rowsB, nstage, chunk_kb, kblocks;
+  int G, BN, maxpairs, npairs, kpad, rowsA, rowsB, nstage, chunk_kb, kblocks, magic;
   size_t offA, offB, offE, offF, total;
 };
 
@@ -151,8 +189,12 @@ ozk_status_t plan_gemm(const EmuGemm& g, GemmPlan* P) {
   const size_t stage = static_cast<size_t>(S) * (128 + P->BN) * 32;
   P->nstage = static_cast<int>(std::min<size_t>(6, (200 * 1024 - 2048) / stage));
   if (P->nstage < 1) return set_error(OZK_ERR_ARG, "S too large for the shared-memory pipeline");
-  P->chunk_kb = std::max(1, 64 / P->maxpairs);
   P->kblocks = static_cast<int>((kp2 + 15) / 16);
+  // exactness chunk: every product of two digits is <= 2^14 in magnitude; an FP32 accumulator
+  // stays exact up to 2^24 (1024 terms) and allows the one-add conversion below 2^22 (255 terms)
+  const int kb_magic = 255 / (16 * P->maxpairs);
+  if (kb_magic >= 1 && P->kblocks <= kb_magic) { P->chunk_kb = P->kblocks; P->magic = 1; }
+  else { P->chunk_kb = std::max(1, 64 / P->maxpairs); P->magic = 0; }
   // exact 128-bit sum: 8 (G - 1) weight bits + 14 product bits + log2(terms) + sign
   double terms = static_cast<double>(kp2) * P->maxpairs + 1.0;
   int need = 8 * (P->G - 1) + 14 + static_cast<int>(std::ceil(std::log2(terms))) + 2;
@@ -190,7 +232,14 @@ ozk_status_t run_emulated(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0
   sp.dbg_digits = g.dbg_digits_a;
   if (single) { sp.X = nullptr; sp.X1 = g.A; sp.ld1 = g.lda; sp.rows1 = g.m; sp.k1 = g.k; }
   else { sp.X = g.tA; sp.ld = g.tlda; sp.rows = g.tm; sp.kdim = g.tk; }
-  launch_split(sp, g.mmax, g.batch, h->stream);
+  const double smnk = g.sum_mnk >= 0 ? g.sum_mnk : static_cast<double>(g.m) * g.n * g.k;
+  const double smk = g.sum_mnk >= 0 ? g.sum_mk : static_cast<double>(g.m) * g.k;
+  const double snk = g.sum_mnk >= 0 ? g.sum_nk : static_cast<double>(g.n) * g.k;
+  {
+    // algorithmic bytes: read 16 per complex element (twice: scan + split), write S x 2 fp16
+    Prof pr(h, OZK_KIND_SPLIT, 0.0, smk * (32.0 + 4.0 * S));
+    launch_split(sp, g.mmax, g.batch, h->stream);
+  }
   // right operand: columns of op(B); logical X[j][l] = op(B)[l][j]
   SplitParams sq = sp;
   sq.trans = g.ob.trans ? 0 : 1; sq.conj = g.ob.conj; sq.side = 1;
@@ -198,7 +247,10 @@ ozk_status_t run_emulated(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0
   sq.dbg_digits = nullptr;
   if (single) { sq.X = nullptr; sq.X1 = g.B; sq.ld1 = g.ldb; sq.rows1 = g.n; sq.k1 = g.k; }
   else { sq.X = g.tB; sq.ld = g.tldb; sq.rows = g.tn; sq.kdim = g.tk; }
-  launch_split(sq, g.nmax, g.batch, h->stream);
+  {
+    Prof pr(h, OZK_KIND_SPLIT, 0.0, snk * (32.0 + 8.0 * S));
+    launch_split(sq, g.nmax, g.batch, h->stream);
+  }
 
   CUtensorMap ta, tb;
   st = make_slice_map(&ta, As, 2LL * g.kmax, P.kpad, P.rowsA, static_cast<long long>(S) * g.batch, 128, S);
@@ -208,6 +260,7 @@ ozk_status_t run_emulated(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0
 
   GemmParams gp{};
   gp.S = S; gp.ngroups = P.G; gp.kblocks = P.kblocks; gp.chunk_kb = P.chunk_kb; gp.nstage = P.nstage;
+  gp.magic = P.magic;
   const int gmax = (g.pair_mode == OZK_PAIRS_FULL) ? 2 * S : S + 1;
   gp.base_exp = -2 * (8 * S - 1) + 8 * (2 * S - gmax);
   gp.ar = g.ar; gp.ai = g.ai; gp.br = g.br; gp.bi = g.bi;
@@ -217,8 +270,8 @@ ozk_status_t run_emulated(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0
   else gp.mode = 2;
   gp.e = e; gp.f = f; gp.e_stride = P.rowsA; gp.f_stride = std::max(g.nmax, 1);
   gp.groups = g.groups; gp.status = h->d_status;
-  if (single) { gp.m = nullptr; gp.m1 = g.m; gp.n1 = g.n; gp.C1 = g.C; gp.ldc1 = g.ldc; }
-  else { gp.m = g.tm; gp.n = g.tn; gp.C = g.tC; gp.ldc = g.tldc; }
+  if (single) { gp.m = nullptr; gp.m1 = g.m; gp.n1 = g.n; gp.C1 = g.C; gp.ldc1 = g.ldc; gp.skm1 = g.skm; gp.skn1 = g.skn; }
+  else { gp.m = g.tm; gp.n = g.tn; gp.C = g.tC; gp.ldc = g.tldc; gp.skm = g.tskm; gp.skn = g.tskn; }
   int np = 0;
   for (int gg = 2; gg <= gmax; ++gg) {
     bool first = true;
@@ -234,7 +287,11 @@ ozk_status_t run_emulated(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0
     }
   }
   gp.npairs = np;
-  launch_slice_gemm(ta, tb, gp, P.BN, g.mmax, g.nmax, g.batch, h->stream);
+  {
+    // algorithmic integer ops: every pair is one real GEMM m x 2n x 2k (8 m n k)
+    Prof pr(h, OZK_KIND_SLICE_GEMM, 8.0 * np * smnk, 0.0);
+    launch_slice_gemm(ta, tb, gp, P.BN, g.mmax, g.nmax, g.batch, h->stream);
+  }
   return cuda_check(cudaGetLastError(), "slice GEMM launch");
 }
 
@@ -268,6 +325,7 @@ ozk_status_t ozk_destroy(ozk_handle_t h) {
   cudaStreamSynchronize(h->stream);
   if (h->ws) cudaFree(h->ws);
   if (h->d_status) cudaFree(h->d_status);
+  for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
   delete h;
   return OZK_OK;
 }
@@ -372,6 +430,12 @@ ozk_status_t ozaki_zgemm_vbatched(ozk_handle_t h, char transa, char transb, cons
   g.tA = reinterpret_cast<const double2* const*>(A);
   g.tB = reinterpret_cast<const double2* const*>(B);
   g.tC = reinterpret_cast<double2* const*>(C);
+  g.sum_mnk = 0;
+  for (int i = 0; i < batch; ++i) {
+    g.sum_mnk += static_cast<double>(m[i]) * n[i] * k[i];
+    g.sum_mk += static_cast<double>(m[i]) * k[i];
+    g.sum_nk += static_cast<double>(n[i]) * k[i];
+  }
   return run_emulated(h, g);
 }
 
@@ -390,7 +454,10 @@ ozk_status_t ozk_zgemm_dmma(ozk_handle_t h, char transa, char transb, int m, int
   p.B = static_cast<const double2*>(B); p.ldb = ldb;
   p.C = static_cast<double2*>(C); p.ldc = ldc;
   p.ar = alpha[0]; p.ai = alpha[1]; p.br = beta[0]; p.bi = beta[1];
-  launch_dmma(p, h->stream);
+  {
+    Prof pr(h, OZK_KIND_DMMA, 8.0 * m * static_cast<double>(n) * k, 0.0);
+    launch_dmma(p, h->stream);
+  }
   return cuda_check(cudaGetLastError(), "DMMA launch");
 }
 
@@ -443,19 +510,23 @@ ozk_status_t ozk_group_sums_debug(ozk_handle_t h, char transa, char transb, int 
 ozk_status_t kkr_build_m(ozk_handle_t h, int L, int b, const void* t, const void* G, void* M) {
   if (!h || !t || !G || !M) return set_error(OZK_ERR_ARG, "null argument");
   if (L <= 0 || b <= 0) return set_error(OZK_ERR_ARG, "bad size");
-  launch_build_m(L * b, b, static_cast<const double2*>(t), static_cast<const double2*>(G), static_cast<double2*>(M),
-                 h->stream);
+  {
+    const double nn = static_cast<double>(L) * b;
+    Prof pr(h, OZK_KIND_BUILD_M, 8.0 * nn * nn * b, 32.0 * nn * nn);
+    launch_build_m(L * b, b, static_cast<const double2*>(t), static_cast<const double2*>(G), static_cast<double2*>(M),
+                   h->stream);
+  }
   return cuda_check(cudaGetLastError(), "build_m launch");
 }
 
 // tau_00 of one matrix: eliminate panels J = [p, q) from the trailing end, centre last.
+// Emulated path: two-level block LU, each panel factored leaf by leaf (b x b pivot blocks), its
+// trailing update deferred to one GEMM with k = q - p.  DMMA path: one pivot block per panel.
 ozk_status_t kkr_tau00(ozk_handle_t h, int n, int b, void* Mv, const void* t0, void* tau, int S, int nb) {
   if (!h || !Mv || !t0 || !tau) return set_error(OZK_ERR_ARG, "null argument");
-  if (b <= 0 || n <= 0 || n % b || nb < b || nb % b || nb > 64 || b > 64)
-    return set_error(OZK_ERR_ARG, "need n % b == 0, b <= nb <= 64, nb % b == 0");
+  if (b <= 0 || n <= 0 || n % b || nb < b || nb % b || b > 16 || nb > (S > 0 ? 128 : 64))
+    return set_error(OZK_ERR_ARG, "need n % b == 0, b <= 16, b <= nb, nb % b == 0, nb <= 128 (64 for S <= 0)");
   double2* M = static_cast<double2*>(Mv);
-  // workspace: pivot inverse (nb x nb) in front of the GEMM workspace (emulated path) or of
-  // the L-panel scratch (DMMA path, which cannot update the panel in place)
   const size_t dinv_bytes = align_up(sizeof(double2) * nb * nb, 1024);
   {
     size_t need = dinv_bytes + sizeof(double2) * static_cast<size_t>(n) * nb;
@@ -465,7 +536,7 @@ ozk_status_t kkr_tau00(ozk_handle_t h, int n, int b, void* Mv, const void* t0, v
       GemmPlan P;
       ozk_status_t st = plan_gemm(probe, &P);
       if (st) return st;
-      need = dinv_bytes + P.total;
+      need = std::max(need, dinv_bytes + P.total);
     }
     ozk_status_t st = ensure_ws(h, need);
     if (st) return st;
@@ -473,34 +544,59 @@ ozk_status_t kkr_tau00(ozk_handle_t h, int n, int b, void* Mv, const void* t0, v
   double2* Dinv = static_cast<double2*>(h->ws);
   for (int q = n; q > b;) {
     const int p = std::max(q - nb, b);
-    const int w = q - p, r = p;
-    GjParams gj{};
-    gj.D = nullptr; gj.D1 = M + p + static_cast<long long>(p) * n; gj.ldd1 = n; gj.nb1 = w;
-    gj.R1 = nullptr; gj.X1 = Dinv; gj.ldx1 = w; gj.nrhs = w; gj.status = h->d_status;
-    launch_gj(gj, w, w, 1, h->stream);
-    double2* Lp = M + static_cast<long long>(p) * n;       // M[0:r, p:q]
-    const double2* Up = M + p;                              // M[p:q, 0:r]
     if (S > 0) {
-      EmuGemm g1;
-      g1.oa = {0, 0}; g1.ob = {0, 0}; g1.batch = 1;
-      g1.mmax = g1.m = r; g1.nmax = g1.n = w; g1.kmax = g1.k = w;
-      g1.A = Lp; g1.lda = n; g1.B = Dinv; g1.ldb = w; g1.C = Lp; g1.ldc = n;
-      g1.S = S; g1.ar = 1; g1.br = 0;
-      ozk_status_t st = run_emulated(h, g1, dinv_bytes);
-      if (st) return st;
-      EmuGemm g2 = g1;
-      g2.nmax = g2.n = r;
-      g2.A = Lp; g2.lda = n; g2.B = Up; g2.ldb = n; g2.C = M; g2.ldc = n;
-      g2.ar = -1; g2.br = 1;
-      st = run_emulated(h, g2, dinv_bytes);
+      for (int a = q - b; a >= p; a -= b) {
+        GjParams gj{};
+        gj.D = nullptr; gj.D1 = M + a + static_cast<long long>(a) * n; gj.ldd1 = n; gj.nb1 = b;
+        gj.R1 = nullptr; gj.X1 = Dinv; gj.ldx1 = b; gj.nrhs = b; gj.status = h->d_status;
+        {
+          Prof pr(h, OZK_KIND_GJ, 16.0 * b * b * b, 32.0 * b * b);
+          launch_gj(gj, b, b, 1, h->stream);
+        }
+        double2* Lc = M + static_cast<long long>(a) * n;          // M[0:a, a:a+b]
+        EmuGemm g1;
+        g1.oa = {0, 0}; g1.ob = {0, 0}; g1.batch = 1;
+        g1.mmax = g1.m = a; g1.nmax = g1.n = b; g1.kmax = g1.k = b;
+        g1.A = Lc; g1.lda = n; g1.B = Dinv; g1.ldb = b; g1.C = Lc; g1.ldc = n;
+        g1.S = S; g1.ar = 1; g1.br = 0;
+        ozk_status_t st = run_emulated(h, g1, dinv_bytes);
+        if (st) return st;
+        if (a > p) {
+          EmuGemm g2 = g1;                                          // rank-b update outside [0,p)^2
+          g2.nmax = g2.n = a;
+          g2.A = Lc; g2.lda = n; g2.B = M + a; g2.ldb = n; g2.C = M; g2.ldc = n;
+          g2.ar = -1; g2.br = 1; g2.skm = p; g2.skn = p;
+          st = run_emulated(h, g2, dinv_bytes);
+          if (st) return st;
+        }
+      }
+      EmuGemm g3;                                                   // deferred panel update
+      g3.oa = {0, 0}; g3.ob = {0, 0}; g3.batch = 1;
+      g3.mmax = g3.m = p; g3.nmax = g3.n = p; g3.kmax = g3.k = q - p;
+      g3.A = M + static_cast<long long>(p) * n; g3.lda = n; g3.B = M + p; g3.ldb = n; g3.C = M; g3.ldc = n;
+      g3.S = S; g3.ar = -1; g3.br = 1;
+      ozk_status_t st = run_emulated(h, g3, dinv_bytes);
       if (st) return st;
     } else {
+      const int w = q - p, r = p;
+      GjParams gj{};
+      gj.D = nullptr; gj.D1 = M + p + static_cast<long long>(p) * n; gj.ldd1 = n; gj.nb1 = w;
+      gj.R1 = nullptr; gj.X1 = Dinv; gj.ldx1 = w; gj.nrhs = w; gj.status = h->d_status;
+      {
+        Prof pr(h, OZK_KIND_GJ, 16.0 * w * w * w, 32.0 * w * w);
+        launch_gj(gj, w, w, 1, h->stream);
+      }
+      double2* Lp = M + static_cast<long long>(p) * n;
+      const double2* Up = M + p;
       // binary64 DMMA baseline: L = M_RJ Dinv into the scratch, copy back, then update
       double2* Ltmp = reinterpret_cast<double2*>(static_cast<uint8_t*>(h->ws) + dinv_bytes);
       DmmaParams d1{};
       d1.m = r; d1.n = w; d1.k = w; d1.A = Lp; d1.lda = n; d1.B = Dinv; d1.ldb = w;
       d1.C = Ltmp; d1.ldc = r; d1.ar = 1; d1.br = 0;
-      launch_dmma(d1, h->stream);
+      {
+        Prof pr(h, OZK_KIND_DMMA, 8.0 * r * static_cast<double>(w) * w, 0.0);
+        launch_dmma(d1, h->stream);
+      }
       ozk_status_t st = cuda_check(cudaMemcpy2DAsync(Lp, sizeof(double2) * n, Ltmp, sizeof(double2) * r,
                                                      sizeof(double2) * r, w, cudaMemcpyDeviceToDevice, h->stream),
                                    "copy L panel");
@@ -508,7 +604,10 @@ ozk_status_t kkr_tau00(ozk_handle_t h, int n, int b, void* Mv, const void* t0, v
       DmmaParams d2{};
       d2.m = r; d2.n = r; d2.k = w; d2.A = Lp; d2.lda = n; d2.B = Up; d2.ldb = n; d2.C = M; d2.ldc = n;
       d2.ar = -1; d2.br = 1;
-      launch_dmma(d2, h->stream);
+      {
+        Prof pr(h, OZK_KIND_DMMA, 8.0 * r * static_cast<double>(r) * w, 0.0);
+        launch_dmma(d2, h->stream);
+      }
     }
     q = p;
   }
@@ -516,10 +615,12 @@ ozk_status_t kkr_tau00(ozk_handle_t h, int n, int b, void* Mv, const void* t0, v
   gj.D = nullptr; gj.D1 = M; gj.ldd1 = n; gj.nb1 = b;
   gj.R1 = static_cast<const double2*>(t0); gj.ldr1 = b; gj.nrhs = b;
   gj.X1 = static_cast<double2*>(tau); gj.ldx1 = b; gj.status = h->d_status;
-  launch_gj(gj, b, b, 1, h->stream);
+  {
+    Prof pr(h, OZK_KIND_GJ, 8.0 * b * b * 2.0 * b, 48.0 * b * b);
+    launch_gj(gj, b, b, 1, h->stream);
+  }
   return cuda_check(cudaGetLastError(), "kkr_tau00 launches");
 }
-
 
 ozk_status_t kkr_tau00_batched(ozk_handle_t h, int nsolves, const int* n, int b, void* const* M, const void* const* t0,
                                void* const* tau, int S, int nb) {
@@ -527,19 +628,20 @@ ozk_status_t kkr_tau00_batched(ozk_handle_t h, int nsolves, const int* n, int b,
   if (nsolves < 0) return set_error(OZK_ERR_ARG, "negative nsolves");
   if (nsolves == 0) return OZK_OK;
   if (S <= 0) return set_error(OZK_ERR_ARG, "batched solves run the emulated path (S >= 1)");
-  if (b <= 0 || nb < b || nb % b || nb > 64 || b > 64) return set_error(OZK_ERR_ARG, "need b <= nb <= 64, nb % b == 0");
+  if (b <= 0 || b > 16 || nb < b || nb % b || nb > 128) return set_error(OZK_ERR_ARG, "need b <= 16, b <= nb <= 128, nb % b == 0");
   int nmax = 0;
   for (int i = 0; i < nsolves; ++i) {
     if (n[i] <= 0 || n[i] % b) return set_error(OZK_ERR_ARG, "every n[i] must be a positive multiple of b");
     nmax = std::max(nmax, n[i]);
   }
-  const int steps = (nmax - b + nb - 1) / nb;
+  const int panels = (nmax - b + nb - 1) / nb;
+  const int leaves = nb / b;
   // workspace layout: [n table][Dinv][step tables][GEMM workspace]
   const size_t ns = static_cast<size_t>(nsolves);
   const size_t off_n = 0;
   const size_t off_dinv = align_up(ns * sizeof(int), 1024);
-  const size_t off_tab = align_up(off_dinv + ns * nb * nb * sizeof(double2), 1024);
-  const size_t n_ptr = 10, n_int = 16;
+  const size_t off_tab = align_up(off_dinv + ns * b * b * sizeof(double2), 1024);
+  const size_t n_ptr = 10, n_int = 18;
   const size_t off_gemm = align_up(off_tab + ns * (n_ptr * sizeof(void*) + n_int * sizeof(int)), 1024);
   EmuGemm probe;
   probe.batch = nsolves; probe.mmax = nmax; probe.nmax = nmax; probe.kmax = nb; probe.S = S;
@@ -563,39 +665,136 @@ ozk_status_t kkr_tau00_batched(ozk_handle_t h, int nsolves, const int* n, int b,
   t.ldd = pi + 0 * ns; t.nbv = pi + 1 * ns; t.ldx = pi + 2 * ns;
   t.lda1 = pi + 3 * ns; t.ldb1 = pi + 4 * ns; t.ldc1 = pi + 5 * ns; t.m1 = pi + 6 * ns; t.n1 = pi + 7 * ns; t.k1 = pi + 8 * ns;
   t.lda2 = pi + 9 * ns; t.ldb2 = pi + 10 * ns; t.ldc2 = pi + 11 * ns; t.m2 = pi + 12 * ns; t.n2 = pi + 13 * ns; t.k2 = pi + 14 * ns;
+  t.skm2 = pi + 15 * ns; t.skn2 = pi + 16 * ns;
   double2* const* Mp = reinterpret_cast<double2* const*>(M);
-  for (int s = 0; s < steps; ++s) {
-    int rmax = 0;
+
+  auto gemm_tables = [&](int which, int mmax, int nmaxg, int kmax, double smnk, double smk, double snk,
+                         bool lu, bool skip) -> ozk_status_t {
+    EmuGemm g;
+    g.oa = {0, 0}; g.ob = {0, 0}; g.batch = nsolves; g.mmax = mmax; g.nmax = nmaxg; g.kmax = kmax; g.S = S;
+    if (which == 1) {
+      g.tA = t.A1; g.tlda = t.lda1; g.tB = t.B1; g.tldb = t.ldb1; g.tC = t.C1; g.tldc = t.ldc1;
+      g.tm = t.m1; g.tn = t.n1; g.tk = t.k1;
+    } else {
+      g.tA = t.A2; g.tlda = t.lda2; g.tB = t.B2; g.tldb = t.ldb2; g.tC = t.C2; g.tldc = t.ldc2;
+      g.tm = t.m2; g.tn = t.n2; g.tk = t.k2;
+      if (skip) { g.tskm = t.skm2; g.tskn = t.skn2; }
+    }
+    g.ar = lu ? -1 : 1; g.br = lu ? 1 : 0;
+    g.sum_mnk = smnk; g.sum_mk = smk; g.sum_nk = snk;
+    return run_emulated(h, g, off_gemm);
+  };
+
+  for (int s = 0; s < panels; ++s) {
+    for (int l = 0; l < leaves; ++l) {
+      int amax = 0, a2max = 0, nact = 0;
+      double s1 = 0, s2 = 0, sa = 0;
+      for (int i = 0; i < nsolves; ++i) {
+        const int q = n[i] - s * nb;
+        if (q <= b) continue;
+        const int p = std::max(q - nb, b);
+        const int a = q - b * (l + 1);
+        if (a < p) continue;
+        ++nact;
+        amax = std::max(amax, a);
+        s1 += static_cast<double>(a) * b * b;
+        sa += static_cast<double>(a) * b;
+        if (a > p) { a2max = std::max(a2max, a); s2 += (static_cast<double>(a) * a - static_cast<double>(p) * p) * b; }
+      }
+      if (nact == 0) continue;
+      launch_kkr_step(s, l, nsolves, dn, Mp, b, nb, dinv, t, h->stream);
+      GjParams gj{};
+      gj.D = t.D; gj.ldd = t.ldd; gj.nb = t.nbv; gj.R = nullptr; gj.X = t.X; gj.ldx = t.ldx; gj.nrhs = b;
+      gj.status = h->d_status;
+      {
+        Prof pr(h, OZK_KIND_GJ, 16.0 * b * b * b * nact, 32.0 * nact * b * b);
+        launch_gj(gj, b, b, nsolves, h->stream);
+      }
+      st = gemm_tables(1, amax, b, b, s1, sa, nact * static_cast<double>(b) * b, false, false);
+      if (st) return st;
+      if (a2max > 0) {
+        st = gemm_tables(2, a2max, a2max, b, s2, sa, sa, true, true);
+        if (st) return st;
+      }
+    }
+    int pmax = 0;
+    double s3 = 0, sa3 = 0;
     for (int i = 0; i < nsolves; ++i) {
       const int q = n[i] - s * nb;
-      if (q > b) rmax = std::max(rmax, std::max(q - nb, b));
+      if (q <= b) continue;
+      const int p = std::max(q - nb, b);
+      pmax = std::max(pmax, p);
+      s3 += static_cast<double>(p) * p * (q - p);
+      sa3 += static_cast<double>(p) * (q - p);
     }
-    if (rmax == 0) break;
-    launch_kkr_step(s, nsolves, dn, Mp, b, nb, dinv, t, h->stream);
-    GjParams gj{};
-    gj.D = t.D; gj.ldd = t.ldd; gj.nb = t.nbv; gj.R = nullptr; gj.X = t.X; gj.ldx = t.ldx; gj.nrhs = nb;
-    gj.status = h->d_status;
-    launch_gj(gj, nb, nb, nsolves, h->stream);
-    EmuGemm g1;
-    g1.oa = {0, 0}; g1.ob = {0, 0}; g1.batch = nsolves; g1.mmax = rmax; g1.nmax = nb; g1.kmax = nb; g1.S = S;
-    g1.tA = t.A1; g1.tlda = t.lda1; g1.tB = t.B1; g1.tldb = t.ldb1; g1.tC = t.C1; g1.tldc = t.ldc1;
-    g1.tm = t.m1; g1.tn = t.n1; g1.tk = t.k1; g1.ar = 1; g1.br = 0;
-    st = run_emulated(h, g1, off_gemm);
-    if (st) return st;
-    EmuGemm g2 = g1;
-    g2.nmax = rmax;
-    g2.tA = t.A2; g2.tlda = t.lda2; g2.tB = t.B2; g2.tldb = t.ldb2; g2.tC = t.C2; g2.tldc = t.ldc2;
-    g2.tm = t.m2; g2.tn = t.n2; g2.tk = t.k2; g2.ar = -1; g2.br = 1;
-    st = run_emulated(h, g2, off_gemm);
+    if (pmax == 0) continue;
+    launch_kkr_step(s, -1, nsolves, dn, Mp, b, nb, dinv, t, h->stream);
+    st = gemm_tables(2, pmax, pmax, nb, s3, sa3, sa3, true, false);
     if (st) return st;
   }
-  launch_kkr_step(-1, nsolves, dn, Mp, b, nb, dinv, t, h->stream);
+  launch_kkr_step(-1, 0, nsolves, dn, Mp, b, nb, dinv, t, h->stream);
   GjParams gj{};
   gj.D = t.D; gj.ldd = t.ldd; gj.nb = t.nbv;
   gj.R = reinterpret_cast<const double2* const*>(t0); gj.ldr = t.nbv;
   gj.X = reinterpret_cast<double2* const*>(tau); gj.ldx = t.nbv; gj.nrhs = b; gj.status = h->d_status;
-  launch_gj(gj, b, b, nsolves, h->stream);
+  {
+    Prof pr(h, OZK_KIND_GJ, 16.0 * b * b * b * nsolves, 48.0 * b * b * nsolves);
+    launch_gj(gj, b, b, nsolves, h->stream);
+  }
   return cuda_check(cudaGetLastError(), "kkr_tau00_batched launches");
+}
+
+ozk_status_t ozk_profile_begin(ozk_handle_t h) {
+  if (!h) return set_error(OZK_ERR_ARG, "null handle");
+  h->recs.clear();
+  h->pool_used = 0;
+  h->prof = true;
+  return OZK_OK;
+}
+
+ozk_status_t ozk_profile_end(ozk_handle_t h, uint64_t* launches, double* ms, double* flops, double* bytes) {
+  if (!h || !launches || !ms || !flops || !bytes) return set_error(OZK_ERR_ARG, "null argument");
+  h->prof = false;
+  ozk_status_t st = cuda_check(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+  if (st) return st;
+  for (int k = 0; k < OZK_KERNEL_KINDS; ++k) { launches[k] = 0; ms[k] = 0; flops[k] = 0; bytes[k] = 0; }
+  for (const ProfRec& r : h->recs) {
+    float t = 0.f;
+    st = cuda_check(cudaEventElapsedTime(&t, r.a, r.b), "cudaEventElapsedTime");
+    if (st) return st;
+    launches[r.kind] += 1;
+    ms[r.kind] += t;
+    flops[r.kind] += r.flops;
+    bytes[r.kind] += r.bytes;
+  }
+  h->recs.clear();
+  return OZK_OK;
+}
+
+
+ozk_status_t kkr_build_m_batched(ozk_handle_t h, int batch, const int* L, int b, const void* const* t,
+                                 const void* const* G, void* const* M) {
+  if (!h || !L || !t || !G || !M) return set_error(OZK_ERR_ARG, "null argument");
+  if (batch < 0 || b <= 0) return set_error(OZK_ERR_ARG, "bad size");
+  if (batch == 0) return OZK_OK;
+  int nmax = 0;
+  double nn2 = 0;
+  for (int i = 0; i < batch; ++i) {
+    if (L[i] <= 0) return set_error(OZK_ERR_ARG, "L[i] must be positive");
+    nmax = std::max(nmax, L[i] * b);
+    nn2 += static_cast<double>(L[i]) * b * L[i] * b;
+  }
+  ozk_status_t st = ensure_ws(h, align_up(sizeof(int) * batch, 256));
+  if (st) return st;
+  int* dL = static_cast<int*>(h->ws);
+  st = cuda_check(cudaMemcpyAsync(dL, L, sizeof(int) * batch, cudaMemcpyHostToDevice, h->stream), "upload L");
+  if (st) return st;
+  {
+    Prof pr(h, OZK_KIND_BUILD_M, 8.0 * nn2 * b, 32.0 * nn2);
+    launch_build_m_batched(dL, b, reinterpret_cast<const double2* const*>(t), reinterpret_cast<const double2* const*>(G),
+                           reinterpret_cast<double2* const*>(M), nmax, batch, h->stream);
+  }
+  return cuda_check(cudaGetLastError(), "build_m_batched launch");
 }
 
 }  // extern "C"

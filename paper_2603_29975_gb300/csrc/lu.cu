@@ -6,6 +6,8 @@
 //   * build_m_kernel   : M = I - blockdiag(t) G.
 //   * scale_kernel     : C = beta C (the k == 0 / alpha == 0 case of the GEMM API).
 // These are the only places with O(n b^2) / O(n^2 b) binary64 arithmetic of the solve.
+#include <algorithm>
+
 #include "ozk_params.cuh"
 
 namespace ozk {
@@ -104,10 +106,110 @@ gj_solve_kernel(const GjParams p) {
   }
 }
 
+// Small blocks (nb <= 16, nb + nrhs <= 32): 128 threads per problem, so the binary64 work of
+// every elimination step is spread over all four SM sub-partitions (binary64 issue is the
+// scarce resource on this GPU); the pivot search and the single complex reciprocal of a step
+// are done by one warp / one thread.
+constexpr int GJ16_THREADS = 128;
+
+__global__ void __launch_bounds__(GJ16_THREADS)
+gj16_kernel(const GjParams p) {
+  __shared__ double2 A[16][33];
+  __shared__ double2 fcol[16];
+  __shared__ int s_piv, s_sing;
+  __shared__ double s_ir, s_ii;
+  const int z = blockIdx.x;
+  const int tid = threadIdx.x;
+  const bool single = p.D == nullptr;
+  const int nb = single ? p.nb1 : p.nb[z];
+  if (nb <= 0) return;
+  const double2* D = single ? p.D1 : p.D[z];
+  const long long ldd = single ? p.ldd1 : p.ldd[z];
+  const double2* R = single ? p.R1 : (p.R ? p.R[z] : nullptr);
+  const long long ldr = single ? p.ldr1 : (p.R ? p.ldr[z] : 0);
+  double2* X = single ? p.X1 : p.X[z];
+  const long long ldx = single ? p.ldx1 : p.ldx[z];
+  const int nrhs = R ? p.nrhs : nb;
+  const int w = nb + nrhs;
+  for (int idx = tid; idx < nb * w; idx += GJ16_THREADS) {
+    const int r = idx % nb, c = idx / nb;
+    double2 v;
+    if (c < nb) v = D[r + c * ldd];
+    else if (R) v = R[r + (c - nb) * ldr];
+    else v = make_double2((c - nb) == r ? 1.0 : 0.0, 0.0);
+    A[r][c] = v;
+  }
+  if (tid == 0) s_sing = 0;
+  __syncthreads();
+  for (int pc = 0; pc < nb; ++pc) {
+    if (tid < 32) {
+      // partial pivoting: first row of largest |.|^2 in column pc (lane = row)
+      double best = -1.0;
+      int bi = pc;
+      if (tid >= pc && tid < nb) {
+        const double2 v = A[tid][pc];
+        best = v.x * v.x + v.y * v.y;
+        bi = tid;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_down_sync(0xffffffffu, best, o);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (tid == 0) {
+        s_piv = bi;
+        if (best <= 0.0) {
+          s_sing = 1;
+        } else {
+          const double2 v = A[bi][pc];
+          const double inv = 1.0 / best;                 // the one division of the step
+          s_ir = v.x * inv;
+          s_ii = -v.y * inv;
+        }
+      }
+    }
+    __syncthreads();
+    if (s_sing) break;
+    const int piv = s_piv;
+    if (tid < w) {                                       // swap rows pc, piv and scale row pc
+      const double2 t = A[piv][tid];
+      if (piv != pc) A[piv][tid] = A[pc][tid];
+      A[pc][tid] = make_double2(t.x * s_ir - t.y * s_ii, t.x * s_ii + t.y * s_ir);
+    }
+    __syncthreads();
+    if (tid < nb) fcol[tid] = (tid == pc) ? make_double2(0.0, 0.0) : A[tid][pc];
+    __syncthreads();
+    const int wc = w - pc;                               // columns pc .. w-1
+    for (int idx = tid; idx < nb * wc; idx += GJ16_THREADS) {
+      const int r = idx % nb, c = pc + idx / nb;
+      if (r == pc) continue;
+      if (c == pc) { A[r][c] = make_double2(0.0, 0.0); continue; }
+      const double2 f = fcol[r];
+      const double2 x = A[pc][c];
+      double2 y = A[r][c];
+      y.x -= f.x * x.x - f.y * x.y;
+      y.y -= f.x * x.y + f.y * x.x;
+      A[r][c] = y;
+    }
+    __syncthreads();
+  }
+  const bool singular = s_sing != 0;
+  if (singular && tid == 0) flag_error(p.status, OZK_ERR_SINGULAR);
+  for (int idx = tid; idx < nb * nrhs; idx += GJ16_THREADS) {
+    const int r = idx % nb, c = idx / nb;
+    X[r + c * ldx] = singular ? make_double2(0.0, 0.0) : A[r][nb + c];
+  }
+}
+
 void launch_gj(const GjParams& p, int max_nb, int max_nrhs, int batch, cudaStream_t st) {
-  const size_t smem = sizeof(double2) * static_cast<size_t>(max_nb) * (max_nb + max_nrhs);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(gj_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  gj_solve_kernel<<<batch, GJ_THREADS, smem, st>>>(p);
+  if (max_nb <= 16 && max_nb + max_nrhs <= 32) {
+    gj16_kernel<<<batch, GJ16_THREADS, 0, st>>>(p);
+  } else {
+    const size_t smem = sizeof(double2) * static_cast<size_t>(max_nb) * (max_nb + max_nrhs);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(gj_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    gj_solve_kernel<<<batch, GJ_THREADS, smem, st>>>(p);
+  }
   record_launch();
 }
 
@@ -135,6 +237,38 @@ void launch_build_m(int n, int b, const double2* t, const double2* G, double2* M
   record_launch();
 }
 
+// Batched M_z = I - blockdiag(t_z) G_z over grid.y = problem z (n_z = L_z b).
+__global__ void build_m_batched_kernel(const int* __restrict__ L, int b, const double2* const* t,
+                                       const double2* const* G, double2* const* M) {
+  const int z = blockIdx.y;
+  const int n = L[z] * b;
+  const double2* __restrict__ tz = t[z];
+  const double2* __restrict__ Gz = G[z];
+  double2* __restrict__ Mz = M[z];
+  for (long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; idx < static_cast<long long>(n) * n;
+       idx += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int i = static_cast<int>(idx % n), j = static_cast<int>(idx / n);
+    const int l = i / b, r = i % b;
+    const double2* tl = tz + static_cast<long long>(l) * b * b;
+    double sr = 0.0, si = 0.0;
+    for (int c = 0; c < b; ++c) {
+      const double2 a = tl[r + c * b];
+      const double2 g = Gz[(l * b + c) + static_cast<long long>(j) * n];
+      sr += a.x * g.x - a.y * g.y;
+      si += a.x * g.y + a.y * g.x;
+    }
+    Mz[idx] = make_double2((i == j ? 1.0 : 0.0) - sr, -si);
+  }
+}
+
+void launch_build_m_batched(const int* L, int b, const double2* const* t, const double2* const* G, double2* const* M,
+                            int nmax, int batch, cudaStream_t st) {
+  const long long tot = static_cast<long long>(nmax) * nmax;
+  const unsigned gx = static_cast<unsigned>(std::min<long long>((tot + 255) / 256, 4096));
+  build_m_batched_kernel<<<dim3(gx, batch), 256, 0, st>>>(L, b, t, G, M);
+  record_launch();
+}
+
 __global__ void scale_kernel(int m, int n, double2* C, long long ldc, double br, double bi) {
   const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (idx >= static_cast<long long>(m) * n) return;
@@ -156,41 +290,48 @@ void launch_scale(int m, int n, double2* C, long long ldc, double br, double bi,
 
 namespace ozk {
 
-// Fill the per-solve tables of one step of the batched block LU (step >= 0), or of the final
-// S_00^-1 t_0 solve (step < 0).  Step s eliminates J = [p, q) with q = n - s nb and
-// p = max(q - nb, b), keeping R = [0, p); solves with q <= b are finished (sizes set to 0).
-__global__ void kkr_step_kernel(int step, int nsolves, const int* __restrict__ n, double2* const* M, int b,
+// Per-solve tables of one sub-step of the batched two-level block LU.  Panel `step` is
+// J = [p, q) with q = n - step nb, p = max(q - nb, b); its leaves [a, a + b) run from the last
+// (leaf 0: a = q - b) down to a = p.  A leaf sub-step fills the Gauss-Jordan table (pivot block
+// M[a:a+b, a:a+b]), GEMM 1 (L column M[0:a, a:a+b] D^-1, in place) and GEMM 2 (rank-b update of
+// [0, a) x [0, a) outside the skip box [0, p) x [0, p)); leaf < 0 fills GEMM 2 with the panel's
+// deferred update of [0, p) x [0, p); step < 0 the final S_00 solve.  Finished or inactive
+// solves get zero sizes.
+__global__ void kkr_step_kernel(int step, int leaf, int nsolves, const int* __restrict__ n, double2* const* M, int b,
                                 int nb, double2* dinv, KkrStep t) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nsolves) return;
   const int ni = n[i];
   double2* Mi = M[i];
-  if (step < 0) {
-    t.D[i] = Mi; t.ldd[i] = ni; t.nbv[i] = b;
-    return;
-  }
+  double2* Di = dinv + static_cast<long long>(i) * b * b;
+  // defaults: nothing to do
+  t.D[i] = Mi; t.ldd[i] = ni; t.nbv[i] = 0; t.X[i] = Di; t.ldx[i] = b;
+  t.A1[i] = Mi; t.lda1[i] = ni; t.B1[i] = Di; t.ldb1[i] = b; t.C1[i] = Mi; t.ldc1[i] = ni;
+  t.m1[i] = 0; t.n1[i] = 0; t.k1[i] = b;
+  t.A2[i] = Mi; t.lda2[i] = ni; t.B2[i] = Mi; t.ldb2[i] = ni; t.C2[i] = Mi; t.ldc2[i] = ni;
+  t.m2[i] = 0; t.n2[i] = 0; t.k2[i] = b; t.skm2[i] = 0; t.skn2[i] = 0;
+  if (step < 0) { t.nbv[i] = b; return; }
   const int q = ni - step * nb;
-  if (q <= b) {
-    t.nbv[i] = 0; t.m1[i] = 0; t.n1[i] = 0; t.k1[i] = 1; t.m2[i] = 0; t.n2[i] = 0; t.k2[i] = 1;
-    t.D[i] = Mi; t.ldd[i] = ni; t.X[i] = dinv; t.ldx[i] = 1;
-    t.A1[i] = Mi; t.lda1[i] = ni; t.B1[i] = dinv; t.ldb1[i] = 1; t.C1[i] = Mi; t.ldc1[i] = ni;
-    t.A2[i] = Mi; t.lda2[i] = ni; t.B2[i] = Mi; t.ldb2[i] = ni; t.C2[i] = Mi; t.ldc2[i] = ni;
-    return;
-  }
+  if (q <= b) return;
   const int p = max(q - nb, b);
-  const int w = q - p;
-  double2* Di = dinv + static_cast<long long>(i) * nb * nb;
-  t.D[i] = Mi + p + static_cast<long long>(p) * ni; t.ldd[i] = ni; t.nbv[i] = w; t.X[i] = Di; t.ldx[i] = w;
-  double2* L = Mi + static_cast<long long>(p) * ni;
-  t.A1[i] = L; t.lda1[i] = ni; t.B1[i] = Di; t.ldb1[i] = w; t.C1[i] = L; t.ldc1[i] = ni;
-  t.m1[i] = p; t.n1[i] = w; t.k1[i] = w;
-  t.A2[i] = L; t.lda2[i] = ni; t.B2[i] = Mi + p; t.ldb2[i] = ni; t.C2[i] = Mi; t.ldc2[i] = ni;
-  t.m2[i] = p; t.n2[i] = p; t.k2[i] = w;
+  if (leaf >= 0) {
+    const int a = q - b * (leaf + 1);
+    if (a < p) return;
+    t.D[i] = Mi + a + static_cast<long long>(a) * ni; t.nbv[i] = b;
+    double2* Lc = Mi + static_cast<long long>(a) * ni;
+    t.A1[i] = Lc; t.C1[i] = Lc; t.m1[i] = a; t.n1[i] = b;
+    if (a > p) {
+      t.A2[i] = Lc; t.B2[i] = Mi + a; t.m2[i] = a; t.n2[i] = a; t.skm2[i] = p; t.skn2[i] = p;
+    }
+  } else {
+    t.A2[i] = Mi + static_cast<long long>(p) * ni; t.B2[i] = Mi + p;
+    t.m2[i] = p; t.n2[i] = p; t.k2[i] = q - p;
+  }
 }
 
-void launch_kkr_step(int step, int nsolves, const int* n, double2* const* M, int b, int nb, double2* dinv,
+void launch_kkr_step(int step, int leaf, int nsolves, const int* n, double2* const* M, int b, int nb, double2* dinv,
                      const KkrStep& t, cudaStream_t st) {
-  kkr_step_kernel<<<(nsolves + 127) / 128, 128, 0, st>>>(step, nsolves, n, M, b, nb, dinv, t);
+  kkr_step_kernel<<<(nsolves + 127) / 128, 128, 0, st>>>(step, leaf, nsolves, n, M, b, nb, dinv, t);
   record_launch();
 }
 

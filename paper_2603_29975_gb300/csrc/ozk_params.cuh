@@ -40,6 +40,11 @@ struct GemmParams {
   int nstage;
   int mode;
   int base_exp;           // -2B + 8 (2S - g_max)
+  int magic;              // 1: every accumulator stays below 2^22 (FP32 add-and-reinterpret conversion)
+  int ntx, nty, batch;    // tile grid (set by the launcher): column tiles, row tiles, problems
+  // skip box: outputs with row < skm and complex column < skn are neither computed (whole
+  // tiles) nor written (per element); per problem (skm, skn) or single values (skm1, skn1)
+  const int* skm; const int* skn; int skm1, skn1;
   double ar, ai, br, bi;  // alpha, beta
   const int* m;           // per problem rows of C
   const int* n;           // per problem complex columns of C
@@ -85,6 +90,8 @@ struct GjParams {
 };
 void launch_gj(const GjParams& p, int max_nb, int max_nrhs, int batch, cudaStream_t st);
 void launch_build_m(int n, int b, const double2* t, const double2* G, double2* M, cudaStream_t st);
+void launch_build_m_batched(const int* L, int b, const double2* const* t, const double2* const* G, double2* const* M,
+                            int nmax, int batch, cudaStream_t st);
 void launch_scale(int m, int n, double2* C, long long ldc, double br, double bi, cudaStream_t st);
 
 // Per-step tables of the batched tau_00 driver, filled on the device for step `step`.
@@ -94,8 +101,12 @@ struct KkrStep {
   // GEMM 1: L = M_RJ Dinv (in place), GEMM 2: M_RR -= L M_JR
   const double2** A1; int* lda1; const double2** B1; int* ldb1; double2** C1; int* ldc1; int* m1; int* n1; int* k1;
   const double2** A2; int* lda2; const double2** B2; int* ldb2; double2** C2; int* ldc2; int* m2; int* n2; int* k2;
+  int* skm2; int* skn2;     // skip box of GEMM 2 (the block deferred to the panel's trailing update)
 };
-void launch_kkr_step(int step, int nsolves, const int* n, double2* const* M, int b, int nb, double2* dinv,
+// step >= 0, leaf >= 0: tables of leaf `leaf` of panel `step` (Gauss-Jordan, L column, masked
+// rank-b update); leaf < 0: the panel's trailing update (GEMM 2 fields); step < 0: the final
+// S_00^-1 t_0 solve.
+void launch_kkr_step(int step, int leaf, int nsolves, const int* n, double2* const* M, int b, int nb, double2* dinv,
                      const KkrStep& t, cudaStream_t st);
 
 }  // namespace ozk

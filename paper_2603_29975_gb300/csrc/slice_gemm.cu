@@ -19,6 +19,8 @@
 //     subtracted from C (LU update), or combined with alpha/beta.
 // No FP64 instruction touches the products; the only binary64 arithmetic is the final
 // subtraction / alpha-beta combination per element.
+#include <algorithm>
+
 #include "ozk_params.cuh"
 
 namespace ozk {
@@ -32,29 +34,16 @@ constexpr int GEMM_THREADS = (2 + GEMM_EPI_WARPS) * 32;
 __device__ __forceinline__ double round_scaled_dev(__int128 T, int E) {
   if (T == 0) return 0.0;
   const bool neg = T < 0;
-  const unsigned __int128 u = neg ? static_cast<unsigned __int128>(-T) : static_cast<unsigned __int128>(T);
-  const unsigned long long hi = static_cast<unsigned long long>(u >> 64);
-  const unsigned long long lo = static_cast<unsigned long long>(u);
-  // normalise to a 64-bit significand M (top bit set) with a sticky bit for the rest
-  unsigned long long M;
-  int nb;              // bit length of u
-  bool sticky;
-  if (hi) {
-    const int lz = __clzll(hi);
-    nb = 128 - lz;
-    M = lz ? ((hi << lz) | (lo >> (64 - lz))) : hi;
-    sticky = lz ? ((lo << lz) != 0ull) : (lo != 0ull);
-  } else {
-    const int lz = __clzll(lo);
-    nb = 64 - lz;
-    M = lo << lz;
-    sticky = false;
-  }
-  // value = (M + sticky*) * 2^(E + nb - 64); ulp exponent of the result:
-  const int Ep = E + nb - 64;
-  int q = Ep + 11;                 // 64 - 53
-  if (q < -1074) q = -1074;
-  const int drop = q - Ep;         // >= 11
+  unsigned __int128 u = neg ? static_cast<unsigned __int128>(-T) : static_cast<unsigned __int128>(T);
+  const unsigned long long hi0 = static_cast<unsigned long long>(u >> 64);
+  const int lz = hi0 ? __clzll(hi0) : 64 + __clzll(static_cast<unsigned long long>(u));
+  u <<= lz;                                           // leading one at bit 127
+  const unsigned long long M = static_cast<unsigned long long>(u >> 64);
+  bool sticky = static_cast<unsigned long long>(u) != 0ull;
+  const int Ep = E + 64 - lz;                         // value = (M + sticky) 2^Ep
+  int q = Ep + 11;                                    // ulp exponent for a 53-bit result
+  if (q < -1074) q = -1074;                           // subnormal range
+  const int drop = q - Ep;                            // >= 11
   unsigned long long keep, rem, half;
   if (drop < 64) {
     keep = M >> drop;
@@ -63,17 +52,16 @@ __device__ __forceinline__ double round_scaled_dev(__int128 T, int E) {
   } else if (drop == 64) {
     keep = 0ull; rem = M; half = 1ull << 63;
   } else {
-    keep = 0ull; rem = 0ull; half = 1ull; sticky = sticky || (M != 0ull);  // far below half an ulp
+    keep = 0ull; rem = 0ull; half = 1ull;             // below half an ulp of the smallest subnormal
   }
-  const bool up = (rem > half) || (rem == half && (sticky || (keep & 1ull)));
-  keep += up ? 1ull : 0ull;
-  if (keep == 0ull) return neg ? -0.0 : 0.0;
-  // keep <= 2^53; value = keep * 2^q; bits = ((q + 1074) << 52) + keep covers normals and
-  // subnormals alike (a carry out of the significand bumps the exponent field)
+  keep += ((rem > half) || (rem == half && (sticky || (keep & 1ull)))) ? 1ull : 0ull;
   unsigned long long bits;
-  if (q + 1074 >= 2047) {
-    bits = 0x7FF0000000000000ull;   // overflow to infinity
+  if (keep == 0ull) {
+    bits = 0ull;
+  } else if (q + 1074 >= 2047) {
+    bits = 0x7FF0000000000000ull;                     // overflow
   } else {
+    // keep <= 2^53: ((q + 1074) << 52) + keep encodes normals and subnormals alike
     bits = (static_cast<unsigned long long>(q + 1074) << 52) + keep;
     if (bits >= 0x7FF0000000000000ull) bits = 0x7FF0000000000000ull;
   }
@@ -81,22 +69,62 @@ __device__ __forceinline__ double round_scaled_dev(__int128 T, int E) {
   return __longlong_as_double(static_cast<long long>(bits));
 }
 
+// RN-even of (hi 2^64 + lo) 2^E, the 128-bit two's-complement integer given as halves.
+// Normal results take the short path; subnormal or overflowing ones the general routine.
+__device__ __forceinline__ double round_hl(long long hi, unsigned long long lo, int E) {
+  const bool neg = hi < 0;
+  unsigned long long uh = static_cast<unsigned long long>(hi);
+  if (neg) {                                          // |value|
+    lo = ~lo + 1ull;
+    uh = ~uh + (lo == 0ull ? 1ull : 0ull);
+  }
+  if ((uh | lo) == 0ull) return 0.0;
+  const int lz = uh ? __clzll(uh) : 64 + __clzll(lo);
+  unsigned long long M;
+  bool sticky;
+  if (lz >= 64) { M = lo << (lz - 64); sticky = false; }
+  else if (lz == 0) { M = uh; sticky = lo != 0ull; }
+  else { M = (uh << lz) | (lo >> (64 - lz)); sticky = (lo << lz) != 0ull; }
+  const int q = E + 64 - lz + 11;                     // ulp exponent of a normal 53-bit result
+  if (q < -1074 || q > 970) {
+    const unsigned __int128 mag = (static_cast<unsigned __int128>(uh) << 64) | lo;
+    const __int128 sv = neg ? -static_cast<__int128>(mag) : static_cast<__int128>(mag);
+    return round_scaled_dev(sv, E);
+  }
+  unsigned long long keep = M >> 11;
+  const unsigned long long rem = M & 0x7FFull;
+  keep += ((rem > 0x400ull) || (rem == 0x400ull && (sticky || (keep & 1ull)))) ? 1ull : 0ull;
+  unsigned long long bits = (static_cast<unsigned long long>(q + 1074) << 52) + keep;
+  if (neg) bits |= 0x8000000000000000ull;
+  return __longlong_as_double(static_cast<long long>(bits));
+}
+
+// Exact FP32 integer accumulator value -> int32.  "magic": |v| < 2^22, one FP32 add puts the
+// integer in the low mantissa bits; otherwise the hardware conversion (exact for |v| <= 2^24).
+__device__ __forceinline__ int acc_to_int(uint32_t bits, bool magic) {
+  const float x = __uint_as_float(bits);
+  return magic ? (__float_as_int(x + 12582912.0f) - 0x4B400000) : __float2int_rn(x);
+}
+
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, uint32_t& a, uint32_t& b) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(a), "=r"(b) : "r"(taddr));
+}
+
 template <int BN>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
 slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                   const __grid_constant__ GemmParams p) {
+  // Persistent: CTA b handles tiles b, b + gridDim.x, ... (column tile fastest, then row
+  // tile, then problem).  All three roles walk the same tile sequence.
   constexpr int COLS = BN / 4;            // stacked columns per epilogue thread
-  const int z = blockIdx.z;
   const bool single = p.m == nullptr;
-  const int m_z = single ? p.m1 : p.m[z];
-  const int n2_z = 2 * (single ? p.n1 : p.n[z]);
-  const int m0 = blockIdx.y * GEMM_BM;
-  const int n0 = blockIdx.x * BN;
-  if (m0 >= m_z || n0 >= n2_z) return;
+  const int ntx = p.ntx, nty = p.nty;
+  const int ntiles = ntx * nty * p.batch;
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int S = p.S;
+  const int G = p.ngroups;
   const uint32_t a_bytes = static_cast<uint32_t>(S) * GEMM_BM * 32;
   const uint32_t b_bytes = static_cast<uint32_t>(S) * BN * 32;
   const uint32_t stage_bytes = a_bytes + b_bytes;
@@ -104,8 +132,8 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + nstage * stage_bytes);
   uint64_t* empty = full + nstage;
   uint64_t* acc_full = empty + nstage;
-  uint64_t* acc_empty = acc_full + 1;
-  uint64_t* done_bar = acc_empty + 1;
+  uint64_t* acc_empty = acc_full + 1;          // one per group accumulator
+  uint64_t* done_bar = acc_empty + 16;
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(done_bar + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
 
@@ -114,7 +142,7 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   if (threadIdx.x == 0) {
     for (int i = 0; i < nstage; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
     mbar_init(acc_full, 1);
-    mbar_init(acc_empty, GEMM_EPI_WARPS);
+    for (int i = 0; i < 16; ++i) mbar_init(&acc_empty[i], GEMM_EPI_WARPS);
     mbar_init(done_bar, 1);
     *abort_flag = 0;
     mbar_fence_init();
@@ -130,56 +158,86 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   const int nkb = p.kblocks;
   const int nchunks = (nkb + p.chunk_kb - 1) / p.chunk_kb;
 
+  // tile decode; returns false for tiles outside the problem's extent (skipped by all roles)
+  auto tile_of = [&](int t, int& z, int& m0, int& n0, int& m_z, int& n2_z) -> bool {
+    const int x = t % ntx;
+    const int y = (t / ntx) % nty;
+    z = t / (ntx * nty);
+    m_z = single ? p.m1 : p.m[z];
+    n2_z = 2 * (single ? p.n1 : p.n[z]);
+    m0 = y * GEMM_BM;
+    n0 = x * BN;
+    if (m0 >= m_z || n0 >= n2_z) return false;
+    const int km = single ? p.skm1 : (p.skm ? p.skm[z] : 0);
+    const int kn = single ? p.skn1 : (p.skn ? p.skn[z] : 0);
+    return !(m0 + GEMM_BM <= km && 2 * ((n0 + BN) / 2) <= 2 * kn);   // tile inside the skip box
+  };
+
   if (warp == 0) {
     if (lane == 0) {
-      // ---------------- TMA producer
-      int issued = 0;
-      for (int kb = 0; kb < nkb; ++kb) {
-        const int stage = kb % nstage;
-        const uint32_t round = kb / nstage;
-        if (kb >= nstage && !mbar_wait(&empty[stage], (round - 1) & 1, p.status, abort_flag)) break;
-        uint8_t* sa = smem + stage * stage_bytes;
-        mbar_arrive_expect_tx(&full[stage], stage_bytes);
-        tma_load_3d(&tmA, sa, &full[stage], kb * 16, m0, z * S);
-        tma_load_3d(&tmB, sa + a_bytes, &full[stage], kb * 16, n0, z * S);
-        issued = kb + 1;
+      // ---------------- TMA producer: one ring of stages across all tiles
+      uint32_t kbc = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        int z, m0, n0, m_z, n2_z;
+        if (!tile_of(t, z, m0, n0, m_z, n2_z)) continue;
+        for (int kb = 0; kb < nkb; ++kb, ++kbc) {
+          const int stage = kbc % nstage;
+          const uint32_t ph = kbc / nstage;
+          if (kbc >= static_cast<uint32_t>(nstage) && !mbar_wait(&empty[stage], (ph - 1) & 1, p.status, abort_flag)) {
+            ok = false;
+            break;
+          }
+          uint8_t* sa = smem + stage * stage_bytes;
+          mbar_arrive_expect_tx(&full[stage], stage_bytes);
+          tma_load_3d(&tmA, sa, &full[stage], kb * 16, m0, z * S);
+          tma_load_3d(&tmB, sa + a_bytes, &full[stage], kb * 16, n0, z * S);
+        }
       }
-      if (*abort_flag) {
+      if (!ok || *abort_flag) {
         // another role gave up: let the copies this thread issued land before the CTA exits
-        for (int kb = max(0, issued - nstage); kb < issued; ++kb) {
+        for (uint32_t k = kbc > static_cast<uint32_t>(nstage) ? kbc - nstage : 0u; k < kbc; ++k) {
           const long long t0 = clock64();
-          while (!mbar_try_wait(&full[kb % nstage], (kb / nstage) & 1) && clock64() - t0 < kWaitBudget) {
+          while (!mbar_try_wait(&full[k % nstage], (k / nstage) & 1) && clock64() - t0 < kWaitBudget) {
           }
         }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      // ---------------- MMA issuer
+      // ---------------- MMA issuer.  Group g's accumulator of chunk cc may be overwritten
+      // once the epilogue released it for chunk cc - 1 (per-group barrier), so the MMAs of
+      // the next tile overlap the reconstruction of the current one.
       const uint32_t idesc = idesc_f16_f32(GEMM_BM, BN);
+      uint32_t kbc = 0, cc = 0;
       bool ok = true;
-      for (int c = 0; c < nchunks && ok; ++c) {
-        if (c > 0) { ok = mbar_wait(acc_empty, (c - 1) & 1, p.status, abort_flag); if (!ok) break; }
-        tc_fence_after();
-        const int kb0 = c * p.chunk_kb;
-        const int kb1 = min(nkb, kb0 + p.chunk_kb);
-        for (int kb = kb0; kb < kb1; ++kb) {
-          const int stage = kb % nstage;
-          const uint32_t round = kb / nstage;
-          if (!mbar_wait(&full[stage], round & 1, p.status, abort_flag)) { ok = false; break; }
-          tc_fence_after();
-          const uint32_t sa = smem_u32(smem + stage * stage_bytes);
-          const uint32_t sb = sa + a_bytes;
-          for (int pi = 0; pi < p.npairs; ++pi) {
-            const uint32_t s = p.ps[pi], t = p.pt[pi], g = p.pg[pi];
-            const uint64_t ad = smem_desc_sw32(sa + s * (GEMM_BM * 32));
-            const uint64_t bd = smem_desc_sw32(sb + t * (BN * 32));
-            const uint32_t acc = (kb == kb0 && p.pfirst[pi]) ? 0u : 1u;
-            mma_f16(tmem + g * BN, ad, bd, idesc, acc);
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        int z, m0, n0, m_z, n2_z;
+        if (!tile_of(t, z, m0, n0, m_z, n2_z)) continue;
+        for (int c = 0; c < nchunks && ok; ++c, ++cc) {
+          const int kb0 = c * p.chunk_kb;
+          const int kb1 = min(nkb, kb0 + p.chunk_kb);
+          for (int kb = kb0; kb < kb1 && ok; ++kb, ++kbc) {
+            const int stage = kbc % nstage;
+            if (!mbar_wait(&full[stage], (kbc / nstage) & 1, p.status, abort_flag)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(smem + stage * stage_bytes);
+            const uint32_t sb = sa + a_bytes;
+            for (int pi = 0; pi < p.npairs; ++pi) {
+              const uint32_t s = p.ps[pi], tt = p.pt[pi], g = p.pg[pi];
+              const bool first = (kb == kb0) && p.pfirst[pi];
+              if (first && cc > 0) {
+                if (!mbar_wait(&acc_empty[g], (cc - 1) & 1, p.status, abort_flag)) { ok = false; break; }
+                tc_fence_after();
+              }
+              const uint64_t ad = smem_desc_sw32(sa + s * (GEMM_BM * 32));
+              const uint64_t bd = smem_desc_sw32(sb + tt * (BN * 32));
+              mma_f16(tmem + g * BN, ad, bd, idesc, first ? 0u : 1u);
+            }
+            mma_commit(&empty[stage]);
           }
-          mma_commit(&empty[stage]);
+          if (ok) mma_commit(acc_full);
         }
-        if (ok) mma_commit(acc_full);
       }
       // make sure no MMA is still in flight before TMEM is released
       mma_commit(done_bar);
@@ -192,69 +250,161 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     // ---------------- epilogue: 16 warps = 4 TMEM lane quadrants x 4 column slabs
     const int quad = warp & 3;
     const int slab = (warp - 2) >> 2;
-    const int row = m0 + quad * 32 + lane;
     const int c0 = slab * COLS;                  // first local stacked column of this thread
-    const int G = p.ngroups;
-    __int128 T[COLS];
-#pragma unroll
-    for (int j = 0; j < COLS; ++j) T[j] = 0;
     const uint32_t tbase = tmem + (static_cast<uint32_t>(quad * 32) << 16) + c0;
+    const bool magic = p.magic != 0;
+    const bool horner = nchunks == 1;
+    uint32_t cc = 0;
     bool ok = true;
-    for (int c = 0; c < nchunks; ++c) {
-      if (!mbar_wait(acc_full, c & 1, p.status, abort_flag)) { ok = false; break; }
-      tc_fence_after();
-      for (int gi = 0; gi < G; ++gi) {
-        uint32_t v[COLS];
-        if constexpr (COLS == 16) tmem_ld16(tbase + gi * BN, v); else tmem_ld8(tbase + gi * BN, v);
-        tmem_wait_ld();
-        if (p.mode == EPI_GROUPS) {
-          if (z == 0 && row < m_z) {
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      int z, m0, n0, m_z, n2_z;
+      if (!tile_of(t, z, m0, n0, m_z, n2_z)) continue;
+      const int row = m0 + quad * 32 + lane;
+      const bool rowok = row < m_z;
+      if (horner && G <= 8 && p.mode != EPI_GROUPS && COLS == 16) {
+        // one chunk, at most 8 groups: the exact sum is H 2^(8 nl) + L with H the first
+        // nh = min(G, 4) groups and L the remaining nl, each combined with 32 x 32 -> 64-bit
+        // multiply-adds at weights 2^24, 2^16, 2^8, 1 (|v| <= 2^24, so |H|, |L| < 2^49).
+        // The 16 columns are handled in two halves of 8 to bound the live registers; the
+        // second half releases each group's accumulator to the next tile's MMAs.
+        const int nh = G < 4 ? G : 4;
+        const int nl = G - nh;
+        if (!mbar_wait(acc_full, cc & 1, p.status, abort_flag)) { ok = false; break; }
+        tc_fence_after();
+        ++cc;
+        const int er = rowok ? p.e[z * p.e_stride + row] + p.base_exp : 0;
+        const int skip_n = (row < (single ? p.skm1 : (p.skm ? p.skm[z] : 0))) ? (single ? p.skn1 : p.skn[z]) : 0;
+        double2* Cz = single ? p.C1 : p.C[z];
+        const long long ldc = single ? p.ldc1 : p.ldc[z];
 #pragma unroll
-            for (int j = 0; j < COLS; ++j) {
-              const int col = n0 + c0 + j;
-              if (col < n2_z) {
-                const long long iv = __float2int_rn(__uint_as_float(v[j]));
-                atomicAdd(reinterpret_cast<unsigned long long*>(&p.groups[(static_cast<long long>(gi) * m_z + row) * n2_z + col]),
-                          static_cast<unsigned long long>(iv));
+        for (int half = 0; half < 2; ++half) {
+          long long H[8], L[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) { H[j] = 0; L[j] = 0; }
+          for (int gi = 0; gi < G; ++gi) {
+            uint32_t v[8];
+            tmem_ld8(tbase + gi * BN + half * 8, v);
+            tmem_wait_ld();
+            if (half == 1) {
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&acc_empty[gi]);   // group gi may be overwritten now
+            }
+            if (gi < nh) {
+              const long long w = 1ll << (8 * (nh - 1 - gi));
+#pragma unroll
+              for (int j = 0; j < 8; ++j) H[j] += static_cast<long long>(acc_to_int(v[j], magic)) * w;
+            } else {
+              const long long w = 1ll << (8 * (nl - 1 - (gi - nh)));
+#pragma unroll
+              for (int j = 0; j < 8; ++j) L[j] += static_cast<long long>(acc_to_int(v[j], magic)) * w;
+            }
+          }
+          if (rowok) {
+            const int s8 = 8 * nl;
+            double2 cv[4];
+            int fe[4];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {             // issue all loads before the arithmetic
+              const int jc = (n0 + c0) / 2 + half * 4 + jj;
+              const bool in = 2 * jc < n2_z;
+              fe[jj] = in ? p.f[z * p.f_stride + jc] : 0;
+              cv[jj] = (in && p.mode != EPI_STORE) ? Cz[row + jc * ldc] : make_double2(0.0, 0.0);
+            }
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+              const int jc = (n0 + c0) / 2 + half * 4 + jj;
+              if (2 * jc < n2_z && jc >= skip_n) {
+                const int E = er + fe[jj];
+                double zz[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                  const long long Hh = H[2 * jj + h], Lh = L[2 * jj + h];
+                  long long hi = s8 ? (Hh >> (64 - s8)) : (Hh >> 63);
+                  const unsigned long long lo = static_cast<unsigned long long>(Hh) << s8;
+                  const unsigned long long lo2 = lo + static_cast<unsigned long long>(Lh);
+                  hi += (Lh >> 63) + (lo2 < lo ? 1 : 0);
+                  zz[h] = round_hl(hi, lo2, E);
+                }
+                double2* dst = Cz + row + jc * ldc;
+                if (p.mode == EPI_STORE) {
+                  if (p.ar == 1.0 && p.ai == 0.0) *dst = make_double2(zz[0], zz[1]);
+                  else *dst = make_double2(p.ar * zz[0] - p.ai * zz[1], p.ar * zz[1] + p.ai * zz[0]);
+                } else if (p.mode == EPI_LU) {
+                  *dst = make_double2(cv[jj].x - zz[0], cv[jj].y - zz[1]);
+                } else {
+                  const double xr = p.ar * zz[0] - p.ai * zz[1], xi = p.ar * zz[1] + p.ai * zz[0];
+                  const double yr = p.br * cv[jj].x - p.bi * cv[jj].y, yi = p.br * cv[jj].y + p.bi * cv[jj].x;
+                  *dst = make_double2(xr + yr, xi + yi);
+                }
               }
             }
           }
-        } else {
-          const int w = 8 * (G - 1 - gi);
+        }
+        continue;
+      }
+      __int128 T[COLS];
 #pragma unroll
-          for (int j = 0; j < COLS; ++j) {
-            const int iv = __float2int_rn(__uint_as_float(v[j]));
-            T[j] += static_cast<__int128>(iv) << w;
+      for (int j = 0; j < COLS; ++j) T[j] = 0;
+      for (int c = 0; c < nchunks; ++c, ++cc) {
+        if (!mbar_wait(acc_full, cc & 1, p.status, abort_flag)) { ok = false; break; }
+        tc_fence_after();
+        for (int gi = 0; gi < G; ++gi) {
+          uint32_t v[COLS];
+          if constexpr (COLS == 16) tmem_ld16(tbase + gi * BN, v); else tmem_ld8(tbase + gi * BN, v);
+          tmem_wait_ld();
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&acc_empty[gi]);       // group gi may be overwritten now
+          if (p.mode == EPI_GROUPS) {
+            if (z == 0 && rowok) {
+#pragma unroll
+              for (int j = 0; j < COLS; ++j) {
+                const int col = n0 + c0 + j;
+                if (col < n2_z) {
+                  const long long iv = __float2int_rn(__uint_as_float(v[j]));
+                  atomicAdd(reinterpret_cast<unsigned long long*>(&p.groups[(static_cast<long long>(gi) * m_z + row) * n2_z + col]),
+                            static_cast<unsigned long long>(iv));
+                }
+              }
+            }
+          } else if (horner) {
+            // one chunk: Horner over the groups, highest weight first, 8-bit steps
+#pragma unroll
+            for (int j = 0; j < COLS; ++j) T[j] = (T[j] << 8) + static_cast<__int128>(acc_to_int(v[j], magic));
+          } else {
+            const int w = 8 * (G - 1 - gi);
+#pragma unroll
+            for (int j = 0; j < COLS; ++j) T[j] += static_cast<__int128>(__float2int_rn(__uint_as_float(v[j]))) << w;
           }
         }
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(acc_empty);
-    }
-    if (ok && p.mode != EPI_GROUPS && row < m_z) {
-      const int er = p.e[z * p.e_stride + row] + p.base_exp;
-      double2* Cz = single ? p.C1 : p.C[z];
-      const long long ldc = single ? p.ldc1 : p.ldc[z];
+      if (!ok) break;
+      if (p.mode != EPI_GROUPS && rowok) {
+        const int er = p.e[z * p.e_stride + row] + p.base_exp;
+        const int skip_n = (row < (single ? p.skm1 : (p.skm ? p.skm[z] : 0))) ? (single ? p.skn1 : p.skn[z]) : 0;
+        double2* Cz = single ? p.C1 : p.C[z];
+        const long long ldc = single ? p.ldc1 : p.ldc[z];
 #pragma unroll
-      for (int j = 0; j < COLS; j += 2) {
-        const int jc = (n0 + c0 + j) >> 1;          // complex column
-        if (2 * jc < n2_z) {
-          const int E = er + p.f[z * p.f_stride + jc];
-          const double zr = round_scaled_dev(T[j], E);
-          const double zi = round_scaled_dev(T[j + 1], E);
-          double2* dst = Cz + row + jc * ldc;
-          if (p.mode == EPI_STORE) {
-            if (p.ar == 1.0 && p.ai == 0.0) *dst = make_double2(zr, zi);
-            else *dst = make_double2(p.ar * zr - p.ai * zi, p.ar * zi + p.ai * zr);
-          } else if (p.mode == EPI_LU) {
-            const double2 cv = *dst;
-            *dst = make_double2(cv.x - zr, cv.y - zi);
-          } else {
-            const double2 cv = *dst;
-            const double xr = p.ar * zr - p.ai * zi, xi = p.ar * zi + p.ai * zr;
-            const double yr = p.br * cv.x - p.bi * cv.y, yi = p.br * cv.y + p.bi * cv.x;
-            *dst = make_double2(xr + yr, xi + yi);
+        for (int j = 0; j < COLS; j += 2) {
+          const int jc = (n0 + c0 + j) >> 1;          // complex column
+          if (2 * jc < n2_z && jc >= skip_n) {
+            const int E = er + p.f[z * p.f_stride + jc];
+            const double zr = round_scaled_dev(T[j], E);
+            const double zi = round_scaled_dev(T[j + 1], E);
+            double2* dst = Cz + row + jc * ldc;
+            if (p.mode == EPI_STORE) {
+              if (p.ar == 1.0 && p.ai == 0.0) *dst = make_double2(zr, zi);
+              else *dst = make_double2(p.ar * zr - p.ai * zi, p.ar * zi + p.ai * zr);
+            } else if (p.mode == EPI_LU) {
+              const double2 cv = *dst;
+              *dst = make_double2(cv.x - zr, cv.y - zi);
+            } else {
+              const double2 cv = *dst;
+              const double xr = p.ar * zr - p.ai * zi, xi = p.ar * zi + p.ai * zr;
+              const double yr = p.br * cv.x - p.bi * cv.y, yi = p.br * cv.y + p.bi * cv.x;
+              *dst = make_double2(xr + yr, xi + yi);
+            }
           }
         }
       }
@@ -270,13 +420,29 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
 
 size_t gemm_smem_bytes(int S, int BN, int nstage) {
   const size_t stage = static_cast<size_t>(S) * (GEMM_BM + BN) * 32;
-  return 1024 + nstage * stage + (2 * nstage + 3) * 8 + 16;
+  return 1024 + nstage * stage + (2 * nstage + 18) * 8 + 16;
 }
 
-void launch_slice_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const GemmParams& p, int BN,
+static int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+void launch_slice_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const GemmParams& p0, int BN,
                        int max_m, int max_n, int batch, cudaStream_t st) {
+  GemmParams p = p0;
+  p.ntx = (2 * max_n + BN - 1) / BN;
+  p.nty = (max_m + GEMM_BM - 1) / GEMM_BM;
+  p.batch = batch;
+  const long long ntiles = static_cast<long long>(p.ntx) * p.nty * batch;
+  const int grid = static_cast<int>(std::min<long long>(ntiles, num_sms()));
   const size_t smem = gemm_smem_bytes(p.S, BN, p.nstage);
-  dim3 grid((2 * max_n + BN - 1) / BN, (max_m + GEMM_BM - 1) / GEMM_BM, batch);
   if (BN == 64) {
     cudaFuncSetAttribute(slice_gemm_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     slice_gemm_kernel<64><<<grid, GEMM_THREADS, smem, st>>>(ta, tb, p);

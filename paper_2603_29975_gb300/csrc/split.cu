@@ -26,8 +26,8 @@ __device__ __forceinline__ int frexp_exponent_from_bits(unsigned long long a) {
   return -1010 - __clzll(a);          // subnormal: floor(log2 x) + 1
 }
 
-// Balanced base-256 digits of X = trunc(x 2^(B - e)), most significant first in d[0].
-__device__ __forceinline__ void digits_of(double x, int e, int nbits, int S, int (&d)[16]) {
+// X = trunc(x 2^(B - e)) computed exactly from the binary64 fields of x.
+__device__ __forceinline__ __int128 integer_image(double x, int e, int nbits) {
   const unsigned long long u = __double_as_longlong(x);
   const bool neg = (u >> 63) != 0ull;
   const int ex = static_cast<int>((u >> 52) & 0x7FFull);
@@ -41,16 +41,14 @@ __device__ __forceinline__ void digits_of(double x, int e, int nbits, int S, int
     if (sh >= 0) mag = static_cast<unsigned __int128>(M) << sh;
     else if (sh > -64) mag = static_cast<unsigned __int128>(M >> (-sh));
   }
-  __int128 X = neg ? -static_cast<__int128>(mag) : static_cast<__int128>(mag);
-#pragma unroll
-  for (int t = 15; t >= 1; --t) {
-    if (t < S) {
-      const int dd = static_cast<int>(static_cast<unsigned long long>(X + 128) & 255ull) - 128;
-      d[t] = dd;
-      X = (X - dd) >> 8;
-    }
-  }
-  d[0] = static_cast<int>(X);
+  return neg ? -static_cast<__int128>(mag) : static_cast<__int128>(mag);
+}
+
+// Next balanced base-256 digit of X (least significant first); X is advanced.
+__device__ __forceinline__ int next_digit(__int128& X) {
+  const int d = static_cast<int>(static_cast<unsigned long long>(X + 128) & 255ull) - 128;
+  X = (X - d) >> 8;
+  return d;
 }
 
 __global__ void __launch_bounds__(SPLIT_THREADS)
@@ -108,12 +106,15 @@ split_kernel(const SplitParams p) {
   __half* outz = p.out + static_cast<long long>(z) * S * plane;
   const bool dbg = (p.dbg_digits != nullptr) && z == 0;
   const long long dplane = p.out_rows * 2LL * K;
-  for (int lt = 0; lt < K; lt += SPLIT_TK) {
-    // load a 32 x 64 tile (coalesced along the stored contiguous direction)
-    for (int idx = tid; idx < SPLIT_ROWS * SPLIT_TK; idx += SPLIT_THREADS) {
+  // tile width along K: 64, or K rounded up to 8 for short rows (so no thread idles on padding)
+  const int TK = K >= SPLIT_TK ? SPLIT_TK : ((K + 7) & ~7);
+  const int per = TK / 8;                      // consecutive l per thread
+  for (int lt = 0; lt < K; lt += TK) {
+    // load a 32 x TK tile (coalesced along the stored contiguous direction)
+    for (int idx = tid; idx < SPLIT_ROWS * TK; idx += SPLIT_THREADS) {
       int rl, ll;
       if (!p.trans) { rl = idx % SPLIT_ROWS; ll = idx / SPLIT_ROWS; }
-      else          { ll = idx % SPLIT_TK;   rl = idx / SPLIT_TK; }
+      else          { ll = idx % TK;         rl = idx / TK; }
       const int r = r0 + rl, l = lt + ll;
       double2 v = make_double2(0.0, 0.0);
       if (r < R && l < K) v = p.trans ? P[l + r * ld] : P[r + l * ld];
@@ -127,37 +128,39 @@ split_kernel(const SplitParams p) {
     // each thread: one row, 8 consecutive l
     {
       const int rl = tid / 8;
-      const int lg = (tid % 8) * 8;
+      const int lg = (tid % 8) * per;
       const int r = r0 + rl;
       if (r < R) {
         const int e = rowexp[rl];
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 0; q < per; ++q) {
           const int l = lt + lg + q;
           if (l >= K) break;
           const double2 v = tile[rl][lg + q];
-          int dr[16], di[16];
-          digits_of(v.x, e, p.nbits, S, dr);
-          digits_of(v.y, e, p.nbits, S, di);
-          for (int s = 0; s < S; ++s) {
+          __int128 Xr = integer_image(v.x, e, p.nbits);
+          __int128 Xi = integer_image(v.y, e, p.nbits);
+          // digits from the least significant (plane S-1) to the most significant (plane 0)
+          for (int s = S - 1; s >= 0; --s) {
+            const int dr = s ? next_digit(Xr) : static_cast<int>(Xr);
+            const int di = s ? next_digit(Xi) : static_cast<int>(Xi);
             __half* o = outz + s * plane;
             if (p.side == 0) {
-              o[r * p.kpad + l] = __int2half_rn(dr[s]);
-              o[r * p.kpad + K + l] = __int2half_rn(di[s]);
+              o[r * p.kpad + l] = __int2half_rn(dr);
+              o[r * p.kpad + K + l] = __int2half_rn(di);
               if (dbg) {
-                p.dbg_digits[s * dplane + r * 2LL * K + l] = static_cast<int16_t>(dr[s]);
-                p.dbg_digits[s * dplane + r * 2LL * K + K + l] = static_cast<int16_t>(di[s]);
+                p.dbg_digits[s * dplane + r * 2LL * K + l] = static_cast<int16_t>(dr);
+                p.dbg_digits[s * dplane + r * 2LL * K + K + l] = static_cast<int16_t>(di);
               }
             } else {
               const long long row0 = 2LL * r, row1 = 2LL * r + 1;
-              o[row0 * p.kpad + l] = __int2half_rn(dr[s]);
-              o[row0 * p.kpad + K + l] = __int2half_rn(-di[s]);
-              o[row1 * p.kpad + l] = __int2half_rn(di[s]);
-              o[row1 * p.kpad + K + l] = __int2half_rn(dr[s]);
+              o[row0 * p.kpad + l] = __int2half_rn(dr);
+              o[row0 * p.kpad + K + l] = __int2half_rn(-di);
+              o[row1 * p.kpad + l] = __int2half_rn(di);
+              o[row1 * p.kpad + K + l] = __int2half_rn(dr);
               if (dbg) {
-                p.dbg_digits[s * dplane + row0 * 2LL * K + l] = static_cast<int16_t>(dr[s]);
-                p.dbg_digits[s * dplane + row0 * 2LL * K + K + l] = static_cast<int16_t>(-di[s]);
-                p.dbg_digits[s * dplane + row1 * 2LL * K + l] = static_cast<int16_t>(di[s]);
-                p.dbg_digits[s * dplane + row1 * 2LL * K + K + l] = static_cast<int16_t>(dr[s]);
+                p.dbg_digits[s * dplane + row0 * 2LL * K + l] = static_cast<int16_t>(dr);
+                p.dbg_digits[s * dplane + row0 * 2LL * K + K + l] = static_cast<int16_t>(-di);
+                p.dbg_digits[s * dplane + row1 * 2LL * K + l] = static_cast<int16_t>(di);
+                p.dbg_digits[s * dplane + row1 * 2LL * K + K + l] = static_cast<int16_t>(dr);
               }
             }
           }

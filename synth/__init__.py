@@ -134,13 +134,8 @@ def kkr_system(L: int, b: int, E: complex, seed: int = 20260331, atom: int = 0,
     """
     n = L * b
     pos = bcc_sites(L)
-    # t blocks: diagonal
     st = 4 * atom
-    u = uniform(seed, st, np.arange(L * b, dtype=np.uint64)).reshape(L, b)
-    phi = 2 * np.pi * uniform(seed, st + 1, np.arange(L * b, dtype=np.uint64)).reshape(L, b)
-    tdiag = 0.1 * (0.5 + u) * np.exp(1j * phi)
-    t = np.zeros((L, b, b), dtype=np.complex128)
-    t[:, np.arange(b), np.arange(b)] = tdiag
+    t = kkr_t(L, b, seed=seed, atom=atom)
     # G
     idx = np.arange(n * n, dtype=np.uint64)
     Rr = 2.0 * uniform(seed, st + 2, idx) - 1.0
@@ -158,6 +153,16 @@ def kkr_system(L: int, b: int, E: complex, seed: int = 20260331, atom: int = 0,
     if nrm > max_norm:
         G *= max_norm / nrm
     return t, G, pos
+
+
+def kkr_t(L: int, b: int, seed: int = 20260331, atom: int = 0) -> np.ndarray:
+    """Single-site t of one atom: L diagonal b x b blocks, entries 0.1 (0.5 + U(0,1)) e^(i phi)."""
+    st = 4 * atom
+    u = uniform(seed, st, np.arange(L * b, dtype=np.uint64)).reshape(L, b)
+    phi = 2 * np.pi * uniform(seed, st + 1, np.arange(L * b, dtype=np.uint64)).reshape(L, b)
+    t = np.zeros((L, b, b), dtype=np.complex128)
+    t[:, np.arange(b), np.arange(b)] = 0.1 * (0.5 + u) * np.exp(1j * phi)
+    return t
 
 
 def block_diag_times(t: np.ndarray, X: np.ndarray) -> np.ndarray:

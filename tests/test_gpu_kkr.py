@@ -29,15 +29,16 @@ def test_build_m(ozk_mod, handle):
     assert np.abs(got - M).max() <= 32 * np.finfo(float).eps
 
 
-@pytest.mark.parametrize("S", [0, 5, 7])
-def test_tau00_small_vs_oracles(ozk_mod, handle, S):
+@pytest.mark.parametrize("S,nb", [(0, 16), (0, 32), (5, 16), (5, 64), (7, 48), (7, 64)])
+def test_tau00_small_vs_oracles(ozk_mod, handle, S, nb):
     t, G, M = _system(15)
     tau = ozk_mod.colmajor_cuda(np.zeros((16, 16), dtype=np.complex128))
-    ozk_mod.kkr_tau00(handle, ozk_mod.colmajor_cuda(M), ozk_mod.colmajor_cuda(t[0]), tau, S=S, nb=16)
+    ozk_mod.kkr_tau00(handle, ozk_mod.colmajor_cuda(M), ozk_mod.colmajor_cuda(t[0]), tau, S=S, nb=nb)
     assert handle.status() == 0
     got = ozk_mod.to_numpy(tau)
     full = kkr.tau00_full(M, t[0])
-    blk = co.tau00_block(M, t[0], 16, S=S)
+    # the oracle's restatement of the same algorithm: leaf-wise panels for the emulated path
+    blk = co.tau00_block(M, t[0], nb, S=S, leaf=16 if S > 0 else None)
     if S == 0:
         assert kkr.rel_err(got, full) < 1e-13
     else:
@@ -54,7 +55,7 @@ def test_tau00_config2_single_atom(ozk_mod, handle):
     errs = {}
     for S in (3, 5, 7, 9):
         tau = ozk_mod.colmajor_cuda(np.zeros((16, 16), dtype=np.complex128))
-        ozk_mod.kkr_tau00(handle, ozk_mod.colmajor_cuda(M), ozk_mod.colmajor_cuda(t[0]), tau, S=S, nb=16)
+        ozk_mod.kkr_tau00(handle, ozk_mod.colmajor_cuda(M), ozk_mod.colmajor_cuda(t[0]), tau, S=S, nb=64)
         errs[S] = kkr.rel_err(ozk_mod.to_numpy(tau), full)
     assert handle.status() == 0
     assert errs[7] <= 1e-10 and errs[9] <= 1e-12
@@ -64,7 +65,7 @@ def test_tau00_config2_single_atom(ozk_mod, handle):
 def test_tau00_wider_panels(ozk_mod, handle):
     t, G, M = _system(27)
     full = kkr.tau00_full(M, t[0])
-    for nb in (32, 48):
+    for nb in (32, 48, 96, 128):
         tau = ozk_mod.colmajor_cuda(np.zeros((16, 16), dtype=np.complex128))
         ozk_mod.kkr_tau00(handle, ozk_mod.colmajor_cuda(M), ozk_mod.colmajor_cuda(t[0]), tau, S=7, nb=nb)
         assert kkr.rel_err(ozk_mod.to_numpy(tau), full) <= 1e-10
@@ -77,12 +78,12 @@ def test_batched_equals_single(ozk_mod, handle):
     single = []
     for t, G, M in systems:
         tau = ozk_mod.colmajor_cuda(np.zeros((16, 16), dtype=np.complex128))
-        ozk_mod.kkr_tau00(handle, ozk_mod.colmajor_cuda(M), ozk_mod.colmajor_cuda(t[0]), tau, S=7, nb=16)
+        ozk_mod.kkr_tau00(handle, ozk_mod.colmajor_cuda(M), ozk_mod.colmajor_cuda(t[0]), tau, S=7, nb=64)
         single.append(ozk_mod.to_numpy(tau))
     Ms = [ozk_mod.colmajor_cuda(M) for t, G, M in systems]
     t0s = [ozk_mod.colmajor_cuda(t[0]) for t, G, M in systems]
     taus = [ozk_mod.colmajor_cuda(np.zeros((16, 16), dtype=np.complex128)) for _ in systems]
-    ozk_mod.kkr_tau00_batched(handle, Ms, t0s, taus, S=7, nb=16)
+    ozk_mod.kkr_tau00_batched(handle, Ms, t0s, taus, S=7, nb=64)
     assert handle.status() == 0
     for i, (t, G, M) in enumerate(systems):
         got = ozk_mod.to_numpy(taus[i])
@@ -95,5 +96,5 @@ def test_singular_pivot_sets_status(ozk_mod, handle):
     M[16:, 16:] = 0.0                    # the first eliminated pivot block is exactly singular
     t0 = np.eye(16, dtype=np.complex128)
     tau = ozk_mod.colmajor_cuda(np.zeros((16, 16), dtype=np.complex128))
-    ozk_mod.kkr_tau00(handle, ozk_mod.colmajor_cuda(M), ozk_mod.colmajor_cuda(t0), tau, S=5, nb=16)
+    ozk_mod.kkr_tau00(handle, ozk_mod.colmajor_cuda(M), ozk_mod.colmajor_cuda(t0), tau, S=5, nb=64)
     assert handle.status() & (1 << 3)

@@ -61,12 +61,21 @@ def test_tau00_full_against_library_solve():
     assert kkr.rel_err(co.tau00_full(M, t[0]), ref) < 1e-13
 
 
-@pytest.mark.parametrize("nb", [16, 32, 48])
-def test_block_lu_agrees_with_full_inverse(nb):
+@pytest.mark.parametrize("nb,leaf", [(16, None), (32, None), (48, None), (64, 16), (48, 16), (128, 16)])
+def test_block_lu_agrees_with_full_inverse(nb, leaf):
     t, G, M = _system(15)
     ref = kkr.tau00_full(M, t[0])
-    assert kkr.rel_err(kkr.tau00_block(M, t[0], nb), ref) < 1e-12
-    assert kkr.rel_err(co.tau00_block(M, t[0], nb), ref) < 1e-12
+    assert kkr.rel_err(kkr.tau00_block(M, t[0], nb, leaf=leaf), ref) < 1e-12
+    assert kkr.rel_err(co.tau00_block(M, t[0], nb, leaf=leaf), ref) < 1e-12
+
+
+def test_leafwise_panel_equals_whole_panel_in_exact_arithmetic():
+    """With binary64 GEMMs the leaf-wise factorisation of a panel and the whole-panel pivot
+    inverse differ only by rounding: the same block LU."""
+    t, G, M = _system(9)
+    a = kkr.tau00_block(M, t[0], 64, leaf=16)
+    b = kkr.tau00_block(M, t[0], 64)
+    assert kkr.rel_err(a, b) < 1e-13
 
 
 def test_two_site_closed_form():
@@ -94,13 +103,13 @@ def test_degenerate_t_and_G():
 def test_emulated_block_lu_error_per_S():
     t, G, M = _system(15)
     ref = kkr.tau00_full(M, t[0])
-    errs = {S: kkr.rel_err(co.tau00_block(M, t[0], 16, S=S), ref) for S in (3, 4, 5, 6, 7)}
+    errs = {S: kkr.rel_err(co.tau00_block(M, t[0], 64, S=S, leaf=16), ref) for S in (3, 4, 5, 6, 7)}
     assert errs[7] <= 1e-10
     for S in (3, 4, 5, 6):
         assert errs[S + 1] < errs[S]
     # the Python and C restatements of the algorithm agree to rounding
-    py = kkr.tau00_block(M, t[0], 16, S=5)
-    assert kkr.rel_err(py, co.tau00_block(M, t[0], 16, S=5)) < 1e-13
+    py = kkr.tau00_block(M, t[0], 64, S=5, leaf=16)
+    assert kkr.rel_err(py, co.tau00_block(M, t[0], 64, S=5, leaf=16)) < 1e-13
 
 
 def test_config2_system_is_well_posed():
