@@ -261,6 +261,7 @@ ozk_status_t run_emulated(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0
   GemmParams gp{};
   gp.S = S; gp.ngroups = P.G; gp.kblocks = P.kblocks; gp.chunk_kb = P.chunk_kb; gp.nstage = P.nstage;
   gp.magic = P.magic;
+  gp.fullset = g.pair_mode == OZK_PAIRS_FULL ? 1 : 0;
   const int gmax = (g.pair_mode == OZK_PAIRS_FULL) ? 2 * S : S + 1;
   gp.base_exp = -2 * (8 * S - 1) + 8 * (2 * S - gmax);
   gp.ar = g.ar; gp.ai = g.ai; gp.br = g.br; gp.bi = g.bi;

@@ -42,6 +42,7 @@ struct GemmParams {
   int base_exp;           // -2B + 8 (2S - g_max)
   int magic;              // 1: every accumulator stays below 2^22 (FP32 add-and-reinterpret conversion)
   int ntx, nty, batch;    // tile grid (set by the launcher): column tiles, row tiles, problems
+  int fullset;            // 1: all S x S pairs, 0: triangular s + t <= S + 1
   // skip box: outputs with row < skm and complex column < skn are neither computed (whole
   // tiles) nor written (per element); per problem (skm, skn) or single values (skm1, skn1)
   const int* skm; const int* skn; int skm1, skn1;

@@ -110,6 +110,187 @@ __device__ __forceinline__ void tmem_ld2(uint32_t taddr, uint32_t& a, uint32_t& 
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(a), "=r"(b) : "r"(taddr));
 }
 
+// Epilogue of one 128 x 64 tile for a single exactness chunk and G <= 8 groups (compile-time):
+// the exact sum of the group values v_g (|v| <= 2^24) is H 2^(8 NL) + L with H = the first
+// NH = min(G, 4) groups and L = the rest, each accumulated by 32 x 32 -> 64-bit multiply-adds
+// with constant weights 2^24, 2^16, 2^8, 1 (|H|, |L| < 2^49).  A thread owns one row and 16
+// stacked columns (8 complex), handled in two halves of 8; the second half releases every
+// group accumulator to the next tile's MMAs.  C and the column exponents of a half are
+// loaded before its arithmetic.
+// Compile-time slice-pair schedule: pairs (s, t) in order of their group g = s + t, the first
+// pair of each group flagged.  The MMA issuer walks it fully unrolled, so one MMA costs two
+// 32-bit descriptor additions and the tcgen05.mma itself.
+__device__ __forceinline__ void mma_f16_lo(uint32_t d_tmem, uint32_t a_lo, uint32_t b_lo, uint32_t hi, uint32_t idesc,
+                                           uint32_t accumulate) {
+  const uint64_t ad = (static_cast<uint64_t>(hi) << 32) | a_lo;
+  const uint64_t bd = (static_cast<uint64_t>(hi) << 32) | b_lo;
+  mma_f16(d_tmem, ad, bd, idesc, accumulate);
+}
+
+// One K-block of MMAs for every pair.  FIRST: first K-block of an exactness chunk -- the first
+// pair of each group overwrites its accumulator (after the epilogue released it, when
+// `wait_release`); returns false if a wait gave up.
+template <int S, bool FULLSET, int BN, bool FIRST>
+__device__ __forceinline__ bool issue_kblock(uint32_t tmem, uint32_t a_lo, uint32_t b_lo, uint32_t hi, uint32_t idesc,
+                                             uint64_t* acc_empty, uint32_t rel_parity, bool wait_release, int* status,
+                                             volatile int* abort_flag) {
+  constexpr int GMAX = FULLSET ? 2 * S : S + 1;
+#pragma unroll
+  for (int g = 2; g <= GMAX; ++g) {
+    bool first = true;
+#pragma unroll
+    for (int s = 1; s <= S; ++s) {
+      const int t = g - s;
+      if (t < 1 || t > S) continue;
+      if (FIRST && first && wait_release) {
+        if (!mbar_wait(&acc_empty[g - 2], rel_parity, status, abort_flag)) return false;
+        tc_fence_after();
+      }
+      mma_f16_lo(tmem + (g - 2) * BN, a_lo + (s - 1) * (GEMM_BM * 32 / 16), b_lo + (t - 1) * (BN * 32 / 16), hi, idesc,
+                 (FIRST && first) ? 0u : 1u);
+      first = false;
+    }
+  }
+  return true;
+}
+
+template <int S, bool FULLSET, int BN>
+__device__ __forceinline__ bool issue_kblock_any(bool firstkb, uint32_t tmem, uint32_t a_lo, uint32_t b_lo, uint32_t hi,
+                                                 uint32_t idesc, uint64_t* acc_empty, uint32_t rel_parity,
+                                                 bool wait_release, int* status, volatile int* abort_flag) {
+  if (firstkb)
+    return issue_kblock<S, FULLSET, BN, true>(tmem, a_lo, b_lo, hi, idesc, acc_empty, rel_parity, wait_release, status,
+                                              abort_flag);
+  return issue_kblock<S, FULLSET, BN, false>(tmem, a_lo, b_lo, hi, idesc, acc_empty, rel_parity, wait_release, status,
+                                             abort_flag);
+}
+
+// Runtime schedule (S > 8, or S > 4 with the full pair set: the 32-column tiles).
+template <int BN>
+__device__ __forceinline__ bool issue_runtime(const GemmParams& p, bool firstkb, uint32_t tmem, uint32_t a_lo,
+                                              uint32_t b_lo, uint32_t hi, uint32_t idesc, uint64_t* acc_empty,
+                                              uint32_t rel_parity, bool wait_release, volatile int* abort_flag) {
+  for (int pi = 0; pi < p.npairs; ++pi) {
+    const uint32_t s = p.ps[pi], t = p.pt[pi], g = p.pg[pi];
+    const bool first = firstkb && p.pfirst[pi];
+    if (first && wait_release) {
+      if (!mbar_wait(&acc_empty[g], rel_parity, p.status, abort_flag)) return false;
+      tc_fence_after();
+    }
+    mma_f16_lo(tmem + g * BN, a_lo + s * (GEMM_BM * 32 / 16), b_lo + t * (BN * 32 / 16), hi, idesc, first ? 0u : 1u);
+  }
+  return true;
+}
+
+template <int BN>
+__device__ __forceinline__ bool issue_dispatch(int S, bool fullset, bool firstkb, uint32_t tmem, uint32_t a_lo,
+                                               uint32_t b_lo, uint32_t hi, uint32_t idesc, uint64_t* acc_empty,
+                                               uint32_t rel_parity, bool wait_release, int* status,
+                                               volatile int* abort_flag) {
+#define OZK_ISSUE(SS, FF) return issue_kblock_any<SS, FF, BN>(firstkb, tmem, a_lo, b_lo, hi, idesc, acc_empty, rel_parity, wait_release, status, abort_flag)
+  if constexpr (BN == 64) {
+    if (!fullset) {
+      switch (S) { case 1: OZK_ISSUE(1, false); case 2: OZK_ISSUE(2, false); case 3: OZK_ISSUE(3, false);
+                   case 4: OZK_ISSUE(4, false); case 5: OZK_ISSUE(5, false); case 6: OZK_ISSUE(6, false);
+                   case 7: OZK_ISSUE(7, false); default: OZK_ISSUE(8, false); }
+    } else {
+      switch (S) { case 1: OZK_ISSUE(1, true); case 2: OZK_ISSUE(2, true); case 3: OZK_ISSUE(3, true);
+                   default: OZK_ISSUE(4, true); }
+    }
+  }
+#undef OZK_ISSUE
+  return false;
+}
+
+struct EpiCtx {
+  int row, z, m_z, n2_z, n0, c0, skip_n, er;
+  uint32_t tbase;
+  double2* Cz;
+  long long ldc;
+  bool rowok;
+};
+
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(taddr));
+}
+
+template <int G>
+__device__ __forceinline__ void epilogue_fast(const GemmParams& p, const EpiCtx& x, uint64_t* acc_empty, bool magic,
+                                              int lane) {
+  constexpr int NH = G < 4 ? G : 4;
+  constexpr int NL = G - NH;
+  constexpr int S8 = 8 * NL;
+  constexpr int BN = 64;
+  // phase A: drain -- fold every group of the 16 columns into H, L and release its
+  // accumulator at once, so the next tile's MMAs start while phase B runs
+  long long H[16], L[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) { H[j] = 0; L[j] = 0; }
+#pragma unroll
+  for (int gi = 0; gi < G; ++gi) {
+    uint32_t v[8], u[8];
+    tmem_ld8(x.tbase + gi * BN, v);
+    tmem_ld8(x.tbase + gi * BN + 8, u);
+    tmem_wait_ld();
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&acc_empty[gi]);         // group gi may be overwritten now
+    const int w = gi < NH ? (1 << (8 * (NH - 1 - gi))) : (1 << (8 * (NL - 1 - (gi - NH))));
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const long long a = static_cast<long long>(acc_to_int(v[j], magic)) * w;
+      const long long b = static_cast<long long>(acc_to_int(u[j], magic)) * w;
+      if (gi < NH) { H[j] += a; H[j + 8] += b; } else { L[j] += a; L[j + 8] += b; }
+    }
+  }
+  if (!x.rowok) return;
+  // phase B: round and write, the next column's loads issued one step ahead
+  double2 cv = make_double2(0.0, 0.0);
+  int fe = 0;
+  const int jc0 = (x.n0 + x.c0) / 2;
+  auto load_col = [&](int jj, double2& c, int& f) {
+    const int jc = jc0 + jj;
+    const bool in = 2 * jc < x.n2_z;
+    f = in ? p.f[x.z * p.f_stride + jc] : 0;
+    c = (in && p.mode != EPI_STORE) ? x.Cz[x.row + jc * x.ldc] : make_double2(0.0, 0.0);
+  };
+  load_col(0, cv, fe);
+#pragma unroll
+  for (int jj = 0; jj < 8; ++jj) {
+    double2 cn = make_double2(0.0, 0.0);
+    int fn = 0;
+    if (jj < 7) load_col(jj + 1, cn, fn);
+    const int jc = jc0 + jj;
+    if (2 * jc < x.n2_z && jc >= x.skip_n) {
+      const int E = x.er + fe;
+      double zz[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const long long Hh = H[2 * jj + h], Lh = L[2 * jj + h];
+        long long hi = S8 ? (Hh >> (64 - S8)) : (Hh >> 63);
+        const unsigned long long lo = static_cast<unsigned long long>(Hh) << S8;
+        const unsigned long long lo2 = lo + static_cast<unsigned long long>(Lh);
+        hi += (Lh >> 63) + (lo2 < lo ? 1 : 0);
+        zz[h] = round_hl(hi, lo2, E);
+      }
+      double2* dst = x.Cz + x.row + jc * x.ldc;
+      if (p.mode == EPI_STORE) {
+        if (p.ar == 1.0 && p.ai == 0.0) *dst = make_double2(zz[0], zz[1]);
+        else *dst = make_double2(p.ar * zz[0] - p.ai * zz[1], p.ar * zz[1] + p.ai * zz[0]);
+      } else if (p.mode == EPI_LU) {
+        *dst = make_double2(cv.x - zz[0], cv.y - zz[1]);
+      } else {
+        const double xr = p.ar * zz[0] - p.ai * zz[1], xi = p.ar * zz[1] + p.ai * zz[0];
+        const double yr = p.br * cv.x - p.bi * cv.y, yi = p.br * cv.y + p.bi * cv.x;
+        *dst = make_double2(xr + yr, xi + yi);
+      }
+    }
+    cv = cn;
+    fe = fn;
+  }
+}
+
 template <int BN>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
 slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -223,17 +404,16 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
             tc_fence_after();
             const uint32_t sa = smem_u32(smem + stage * stage_bytes);
             const uint32_t sb = sa + a_bytes;
-            for (int pi = 0; pi < p.npairs; ++pi) {
-              const uint32_t s = p.ps[pi], tt = p.pt[pi], g = p.pg[pi];
-              const bool first = (kb == kb0) && p.pfirst[pi];
-              if (first && cc > 0) {
-                if (!mbar_wait(&acc_empty[g], (cc - 1) & 1, p.status, abort_flag)) { ok = false; break; }
-                tc_fence_after();
-              }
-              const uint64_t ad = smem_desc_sw32(sa + s * (GEMM_BM * 32));
-              const uint64_t bd = smem_desc_sw32(sb + tt * (BN * 32));
-              mma_f16(tmem + g * BN, ad, bd, idesc, first ? 0u : 1u);
-            }
+            const uint64_t da = smem_desc_sw32(sa), db = smem_desc_sw32(sb);
+            if constexpr (BN == 64)
+              ok = issue_dispatch<BN>(S, p.fullset != 0, kb == kb0, tmem, static_cast<uint32_t>(da),
+                                      static_cast<uint32_t>(db), static_cast<uint32_t>(da >> 32), idesc, acc_empty,
+                                      (cc - 1) & 1, cc > 0, p.status, abort_flag);
+            else
+              ok = issue_runtime<BN>(p, kb == kb0, tmem, static_cast<uint32_t>(da), static_cast<uint32_t>(db),
+                                     static_cast<uint32_t>(da >> 32), idesc, acc_empty, (cc - 1) & 1, cc > 0,
+                                     abort_flag);
+            if (!ok) break;
             mma_commit(&empty[stage]);
           }
           if (ok) mma_commit(acc_full);
@@ -261,87 +441,30 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       if (!tile_of(t, z, m0, n0, m_z, n2_z)) continue;
       const int row = m0 + quad * 32 + lane;
       const bool rowok = row < m_z;
-      if (horner && G <= 8 && p.mode != EPI_GROUPS && COLS == 16) {
-        // one chunk, at most 8 groups: the exact sum is H 2^(8 nl) + L with H the first
-        // nh = min(G, 4) groups and L the remaining nl, each combined with 32 x 32 -> 64-bit
-        // multiply-adds at weights 2^24, 2^16, 2^8, 1 (|v| <= 2^24, so |H|, |L| < 2^49).
-        // The 16 columns are handled in two halves of 8 to bound the live registers; the
-        // second half releases each group's accumulator to the next tile's MMAs.
-        const int nh = G < 4 ? G : 4;
-        const int nl = G - nh;
-        if (!mbar_wait(acc_full, cc & 1, p.status, abort_flag)) { ok = false; break; }
-        tc_fence_after();
-        ++cc;
-        const int er = rowok ? p.e[z * p.e_stride + row] + p.base_exp : 0;
-        const int skip_n = (row < (single ? p.skm1 : (p.skm ? p.skm[z] : 0))) ? (single ? p.skn1 : p.skn[z]) : 0;
-        double2* Cz = single ? p.C1 : p.C[z];
-        const long long ldc = single ? p.ldc1 : p.ldc[z];
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-          long long H[8], L[8];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) { H[j] = 0; L[j] = 0; }
-          for (int gi = 0; gi < G; ++gi) {
-            uint32_t v[8];
-            tmem_ld8(tbase + gi * BN + half * 8, v);
-            tmem_wait_ld();
-            if (half == 1) {
-              tc_fence_before();
-              __syncwarp();
-              if (lane == 0) mbar_arrive(&acc_empty[gi]);   // group gi may be overwritten now
-            }
-            if (gi < nh) {
-              const long long w = 1ll << (8 * (nh - 1 - gi));
-#pragma unroll
-              for (int j = 0; j < 8; ++j) H[j] += static_cast<long long>(acc_to_int(v[j], magic)) * w;
-            } else {
-              const long long w = 1ll << (8 * (nl - 1 - (gi - nh)));
-#pragma unroll
-              for (int j = 0; j < 8; ++j) L[j] += static_cast<long long>(acc_to_int(v[j], magic)) * w;
-            }
+      if constexpr (COLS == 16) {
+        if (horner && G <= 8 && p.mode != EPI_GROUPS) {
+          EpiCtx x;
+          x.row = row; x.z = z; x.m_z = m_z; x.n2_z = n2_z; x.n0 = n0; x.c0 = c0; x.tbase = tbase;
+          x.rowok = rowok;
+          x.skip_n = (row < (single ? p.skm1 : (p.skm ? p.skm[z] : 0))) ? (single ? p.skn1 : p.skn[z]) : 0;
+          x.Cz = single ? p.C1 : p.C[z];
+          x.ldc = single ? p.ldc1 : p.ldc[z];
+          x.er = rowok ? p.e[z * p.e_stride + row] + p.base_exp : 0;
+          if (!mbar_wait(acc_full, cc & 1, p.status, abort_flag)) { ok = false; break; }
+          tc_fence_after();
+          ++cc;
+          switch (G) {
+            case 1: epilogue_fast<1>(p, x, acc_empty, magic, lane); break;
+            case 2: epilogue_fast<2>(p, x, acc_empty, magic, lane); break;
+            case 3: epilogue_fast<3>(p, x, acc_empty, magic, lane); break;
+            case 4: epilogue_fast<4>(p, x, acc_empty, magic, lane); break;
+            case 5: epilogue_fast<5>(p, x, acc_empty, magic, lane); break;
+            case 6: epilogue_fast<6>(p, x, acc_empty, magic, lane); break;
+            case 7: epilogue_fast<7>(p, x, acc_empty, magic, lane); break;
+            default: epilogue_fast<8>(p, x, acc_empty, magic, lane); break;
           }
-          if (rowok) {
-            const int s8 = 8 * nl;
-            double2 cv[4];
-            int fe[4];
-#pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {             // issue all loads before the arithmetic
-              const int jc = (n0 + c0) / 2 + half * 4 + jj;
-              const bool in = 2 * jc < n2_z;
-              fe[jj] = in ? p.f[z * p.f_stride + jc] : 0;
-              cv[jj] = (in && p.mode != EPI_STORE) ? Cz[row + jc * ldc] : make_double2(0.0, 0.0);
-            }
-#pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
-              const int jc = (n0 + c0) / 2 + half * 4 + jj;
-              if (2 * jc < n2_z && jc >= skip_n) {
-                const int E = er + fe[jj];
-                double zz[2];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                  const long long Hh = H[2 * jj + h], Lh = L[2 * jj + h];
-                  long long hi = s8 ? (Hh >> (64 - s8)) : (Hh >> 63);
-                  const unsigned long long lo = static_cast<unsigned long long>(Hh) << s8;
-                  const unsigned long long lo2 = lo + static_cast<unsigned long long>(Lh);
-                  hi += (Lh >> 63) + (lo2 < lo ? 1 : 0);
-                  zz[h] = round_hl(hi, lo2, E);
-                }
-                double2* dst = Cz + row + jc * ldc;
-                if (p.mode == EPI_STORE) {
-                  if (p.ar == 1.0 && p.ai == 0.0) *dst = make_double2(zz[0], zz[1]);
-                  else *dst = make_double2(p.ar * zz[0] - p.ai * zz[1], p.ar * zz[1] + p.ai * zz[0]);
-                } else if (p.mode == EPI_LU) {
-                  *dst = make_double2(cv[jj].x - zz[0], cv[jj].y - zz[1]);
-                } else {
-                  const double xr = p.ar * zz[0] - p.ai * zz[1], xi = p.ar * zz[1] + p.ai * zz[0];
-                  const double yr = p.br * cv[jj].x - p.bi * cv[jj].y, yi = p.br * cv[jj].y + p.bi * cv[jj].x;
-                  *dst = make_double2(xr + yr, xi + yi);
-                }
-              }
-            }
-          }
+          continue;
         }
-        continue;
       }
       __int128 T[COLS];
 #pragma unroll
