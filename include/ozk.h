@@ -131,6 +131,28 @@ ozk_status_t ozaki_zgemm_vbatched(ozk_handle_t handle, char transa, char transb,
                                   const void* const* B, const int* ldb, const double* beta,
                                   void* const* C, const int* ldc, int batch, int S, int pair_mode);
 
+/* Allocation-free emulated ZGEMM (no counterpart in the paper: an interface for callers that
+ * cannot allocate device memory when they call -- for example code running inside a CUDA
+ * graph capture, where cudaMalloc is not allowed, or inside a framework whose memory pool
+ * forbids allocations it does not own).  Same arguments and results as ozaki_zgemm, but with
+ * no handle: `stream` is a cudaStream_t (NULL = legacy default stream) and the scratch is a
+ * static device array of OZK_NOALLOC_SCRATCH_BYTES compiled into the library, so nothing is
+ * allocated.  Every GPU that loads the library holds that array until the process exits.
+ *   - The first call on each device looks up the array's device address with
+ *     cudaGetSymbolAddress (once per device, with that device current); make that first call
+ *     before any stream capture.
+ *   - Problems whose scratch (ozk_zgemm_workspace_size) exceeds OZK_NOALLOC_SCRATCH_BYTES are
+ *     rejected with OZK_ERR_ARG before anything is enqueued.
+ *   - All calls share the array and it keeps the last call's contents (each call rewrites
+ *     what it reads); calls that may overlap on the GPU race and must be serialised.
+ *   - device_status: DEVICE int that collects OZK_ERR_* bits as in ozk_get_status (the caller
+ *     clears and reads it); NULL uses a flag inside the library that nobody reads. */
+#define OZK_NOALLOC_SCRATCH_BYTES (32u << 20)
+ozk_status_t ozaki_zgemm_noalloc(void* stream, char transa, char transb, int m, int n, int k,
+                                 const double* alpha, const void* A, int lda, const void* B, int ldb,
+                                 const double* beta, void* C, int ldc, int S, int pair_mode,
+                                 int* device_status);
+
 /* Plain binary64 ZGEMM on the FP64 tensor path (DMMA, mma.sync m8n8k4.f64), same argument
  * meaning as ozaki_zgemm without S: the comparison baseline on the same GPU. */
 ozk_status_t ozk_zgemm_dmma(ozk_handle_t handle, char transa, char transb, int m, int n, int k,

@@ -8,11 +8,12 @@ The compute path is libozk.so (CUDA kernels behind the C ABI in include/ozk.h);
 from .binding import (OZK_PAIRS_FULL, OZK_PAIRS_TRI, Handle, OzkError, colmajor_cuda, kkr_build_m,
                       kkr_build_m_batched_ptrs,
                       kkr_tau00, kkr_tau00_batched, kkr_tau00_batched_ptrs, launch_count, lib,
-                      ozaki_zgemm, ozaki_zgemm_vbatched, ozk_group_sums_debug, ozk_split_debug,
+                      ozaki_zgemm, ozaki_zgemm_noalloc, ozaki_zgemm_vbatched, ozk_group_sums_debug,
+                      ozk_split_debug,
                       ozk_zgemm_dmma, to_numpy)
 
 __all__ = ["OZK_PAIRS_FULL", "OZK_PAIRS_TRI", "Handle", "OzkError", "colmajor_cuda", "kkr_build_m",
            "kkr_build_m_batched_ptrs",
            "kkr_tau00", "kkr_tau00_batched", "kkr_tau00_batched_ptrs", "launch_count", "lib",
-           "ozaki_zgemm", "ozaki_zgemm_vbatched", "ozk_group_sums_debug", "ozk_split_debug",
+           "ozaki_zgemm", "ozaki_zgemm_noalloc", "ozaki_zgemm_vbatched", "ozk_group_sums_debug", "ozk_split_debug",
            "ozk_zgemm_dmma", "to_numpy"]

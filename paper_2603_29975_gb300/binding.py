@@ -25,7 +25,7 @@ EXPORTS = ["ozk_create", "ozk_destroy", "ozk_set_stream", "ozk_get_status", "ozk
            "ozk_zgemm_workspace_size", "ozk_last_error", "ozk_launch_count", "ozaki_zgemm",
            "ozaki_zgemm_vbatched", "ozk_zgemm_dmma", "ozk_split_debug", "ozk_group_sums_debug",
            "kkr_build_m", "kkr_tau00", "kkr_tau00_batched", "ozk_profile_begin", "ozk_profile_end",
-           "kkr_build_m_batched"]
+           "kkr_build_m_batched", "ozaki_zgemm_noalloc"]
 KIND_NAMES = ["split", "slice_gemm", "gj", "build_m", "dmma", "other"]
 
 _lib = None
@@ -62,6 +62,7 @@ def lib():
         L.kkr_tau00.argtypes = [vp, i, i, vp, vp, vp, i, i]
         L.kkr_tau00_batched.argtypes = [vp, i, ip, i, vp, vp, vp, i, i]
         L.kkr_build_m_batched.argtypes = [vp, i, ip, i, vp, vp, vp]
+        L.ozaki_zgemm_noalloc.argtypes = [vp, c, c, i, i, i, dp, vp, i, vp, i, dp, vp, i, i, i, vp]
         L.ozk_profile_begin.argtypes = [vp]
         L.ozk_profile_end.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), dp, dp, dp]
         for name in EXPORTS:
@@ -177,6 +178,22 @@ def ozaki_zgemm(h: Handle, A, B, C, S: int = 7, alpha=1.0, beta=0.0, transa="N",
     _check(lib().ozaki_zgemm(h.ptr, transa.encode(), transb.encode(), m, n, k, _c2(alpha), _ptr(A),
                              _ld(A, A.shape[0]), _ptr(B), _ld(B, B.shape[0]), _c2(beta), _ptr(C),
                              _ld(C, m), S, pair_mode), "ozaki_zgemm")
+    return C
+
+
+def ozaki_zgemm_noalloc(A, B, C, S: int = 7, alpha=1.0, beta=0.0, transa="N", transb="N",
+                        pair_mode: int = OZK_PAIRS_TRI, stream=None, device_status=None):
+    """Allocation-free emulated ZGEMM (static scratch inside the library, no handle)."""
+    import torch
+    m, n, k = _shapes(transa, transb, A, B)
+    if tuple(C.shape) != (m, n):
+        raise OzkError("C has the wrong shape")
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().ozaki_zgemm_noalloc(ctypes.c_void_p(s.cuda_stream), transa.encode(), transb.encode(), m, n, k,
+                                     _c2(alpha), _ptr(A), _ld(A, A.shape[0]), _ptr(B), _ld(B, B.shape[0]), _c2(beta),
+                                     _ptr(C), _ld(C, m), S, pair_mode,
+                                     ctypes.c_void_p(device_status.data_ptr() if device_status is not None else 0)),
+           "ozaki_zgemm_noalloc")
     return C
 
 

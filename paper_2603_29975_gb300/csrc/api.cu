@@ -799,3 +799,90 @@ ozk_status_t kkr_build_m_batched(ozk_handle_t h, int batch, const int* L, int b,
 }
 
 }  // extern "C"
+
+// --------------------------------------------------------------------- allocation-free ZGEMM
+// Some callers cannot allocate device memory at the point where they need a GEMM: code that
+// runs while a CUDA graph is being captured (cudaMalloc is not a capturable operation), code
+// inside a memory-pool-managed framework that forbids allocations outside its allocator, or
+// a host thread holding a lock that a device allocation would contend for.  For them this
+// entry point runs the same emulated ZGEMM with its scratch (slice planes and exponents) in a
+// statically sized device array of this file, so it allocates nothing.  The array is part of
+// the library image: every GPU that loads the library keeps OZK_NOALLOC_SCRATCH_BYTES of it
+// until the process exits.  All calls share it, so calls that may overlap on the GPU (other
+// streams, other threads) race and must be serialised by the caller.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[OZK_NOALLOC_SCRATCH_BYTES];
+static __device__ int g_noalloc_status;
+
+namespace {
+constexpr int kMaxDevices = 64;
+void* g_noalloc_ptr[kMaxDevices] = {};
+int* g_noalloc_status_ptr[kMaxDevices] = {};
+
+// Device address of the static scratch for the current device, looked up once per device
+// (the name is only a host-side stand-in for the device symbol).
+ozk_status_t noalloc_setup(int dev, void** scratch, int** status) {
+  if (dev < 0 || dev >= kMaxDevices) return set_error(OZK_ERR_ARG, "device index out of range for the static scratch");
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    void* s = nullptr;
+    ozk_status_t st = cuda_check(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress(scratch)");
+    if (st) return st;
+    st = cuda_check(cudaGetSymbolAddress(&s, g_noalloc_status), "cudaGetSymbolAddress(status)");
+    if (st) return st;
+    g_noalloc_ptr[dev] = p;
+    g_noalloc_status_ptr[dev] = static_cast<int*>(s);
+  }
+  *scratch = g_noalloc_ptr[dev];
+  *status = g_noalloc_status_ptr[dev];
+  return OZK_OK;
+}
+}  // namespace
+
+extern "C" ozk_status_t ozaki_zgemm_noalloc(void* stream, char transa, char transb, int m, int n, int k,
+                                           const double* alpha, const void* A, int lda, const void* B, int ldb,
+                                           const double* beta, void* C, int ldc, int S, int pair_mode,
+                                           int* device_status) {
+  if (!alpha || !beta) return set_error(OZK_ERR_ARG, "null argument");
+  EmuGemm g;
+  if (!parse_op(transa, &g.oa) || !parse_op(transb, &g.ob)) return set_error(OZK_ERR_ARG, "bad trans flag");
+  ozk_status_t st = check_dims(g.oa, g.ob, m, n, k, lda, ldb, ldc);
+  if (st) return st;
+  if (pair_mode != OZK_PAIRS_TRI && pair_mode != OZK_PAIRS_FULL) return set_error(OZK_ERR_ARG, "bad pair mode");
+  g.batch = 1; g.mmax = g.m = m; g.nmax = g.n = n; g.kmax = g.k = k;
+  g.A = static_cast<const double2*>(A); g.lda = lda;
+  g.B = static_cast<const double2*>(B); g.ldb = ldb;
+  g.C = static_cast<double2*>(C); g.ldc = ldc;
+  g.ar = alpha[0]; g.ai = alpha[1]; g.br = beta[0]; g.bi = beta[1];
+  g.S = S; g.pair_mode = pair_mode;
+  const bool trivial = (m == 0 || n == 0 || k == 0 || (alpha[0] == 0.0 && alpha[1] == 0.0));
+  if (!trivial) {
+    GemmPlan P;
+    st = plan_gemm(g, &P);
+    if (st) return st;
+    if (P.total > OZK_NOALLOC_SCRATCH_BYTES)
+      return set_error(OZK_ERR_ARG, "ozaki_zgemm_noalloc: problem needs more scratch than OZK_NOALLOC_SCRATCH_BYTES "
+                                    "(use ozaki_zgemm with a handle)");
+  }
+  int dev = 0;
+  st = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+  if (st) return st;
+  void* scratch = nullptr;
+  int* status = nullptr;
+  st = noalloc_setup(dev, &scratch, &status);
+  if (st) return st;
+  // a context on the stack whose workspace is the static scratch (it owns nothing; run_emulated
+  // never grows the workspace because the size was checked above)
+  ozk_context ctx;
+  ctx.device = dev;
+  ctx.stream = static_cast<cudaStream_t>(stream);
+  ctx.d_status = device_status ? device_status : status;
+  ctx.ws = scratch;
+  ctx.ws_bytes = OZK_NOALLOC_SCRATCH_BYTES;
+  if (m == 0 || n == 0) return OZK_OK;
+  if (trivial) {
+    if (beta[0] == 1.0 && beta[1] == 0.0) return OZK_OK;
+    launch_scale(m, n, static_cast<double2*>(C), ldc, beta[0], beta[1], ctx.stream);
+    return cuda_check(cudaGetLastError(), "scale launch");
+  }
+  return run_emulated(&ctx, g);
+}
