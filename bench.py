@@ -35,8 +35,10 @@ L_SITES, B, E0 = 65, 16, 0.5 + 0.05j
 N = L_SITES * B
 FLOPS_PER_SOLVE = 8.0 / 3.0 * N ** 3          # effective FP64 flops of one tau_00 solve
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# dram bytes per slice_gemm launch from the committed ncu capture of this workload (profiles/);
-# None until a capture of the current kernel exists
+# dram__bytes_read.sum + dram__bytes_write.sum per slice_gemm launch, averaged over the 128
+# launches of one step of this workload (64 atoms), from the ncu capture summarised in
+# profiles/slice_gemm_kkr_batch64_dram.md; set back to None whenever the kernel or the
+# step's launch sequence changes until it is captured again
 SLICE_GEMM_DRAM_BYTES_PER_LAUNCH = None
 
 
@@ -125,6 +127,18 @@ def colblocks(t):
     return np.ascontiguousarray(np.transpose(t, (0, 2, 1)))      # column-major b x b blocks
 
 
+def workload_config(args, world):
+    batch = args.batch
+    return {"workload": f"KKR tau_00, bcc LIZ {L_SITES} sites, lmax=3 (b={B}), n={N}, E=0.5+0.05i; "
+                        f"{batch} atoms per GPU per step sharing G; M=I-tG built on the GPU; block LU nb={args.nb}; "
+                        f"every GEMM (M build and LU) emulated with S={args.S}",
+            "atoms_per_gpu_per_step": batch, "n": N, "S": args.S, "nb": args.nb,
+            "eff_fp64_flops_per_solve": FLOPS_PER_SOLVE,
+            "l2": "256 MB buffer written between timed steps (outside the events); per-step "
+                  f"working set {batch * N * N * 16 / 2**30:.2f} GiB of M",
+            "parallelism": f"dp{world} (independent atoms per GPU)"}
+
+
 # ----------------------------------------------------------------------------- our arm
 def run_ours(args):
     import numpy as np
@@ -153,14 +167,15 @@ def run_ours(args):
     Ms = [torch.empty((N, N), dtype=torch.complex128, device=dev) for _ in range(batch)]
     taus = [torch.zeros((B, B), dtype=torch.complex128, device=dev) for _ in range(batch)]
     i64 = lambda xs: torch.tensor([x.data_ptr() for x in xs], dtype=torch.int64, device=dev)
-    pt, pg, pm = i64(ts), i64([G] * batch), i64(Ms)
+    pt, pm = i64(ts), i64(Ms)
     pt0, ptau = i64(ts), i64(taus)
-    Ls = [L_SITES] * batch
     ns = [N] * batch
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
 
     def step():
-        ozk.kkr_build_m_batched_ptrs(h, Ls, B, pt, pg, pm)
+        # every atom of the step shares G (one lattice, one energy): M_a = I - t_a G by emulated
+        # GEMMs, one per site block row for all atoms
+        ozk.kkr_build_m_shared_ptrs(h, batch, L_SITES, B, pt, G, pm, S=args.S)
         ozk.kkr_tau00_batched_ptrs(h, ns, B, pm, pt0, ptau, S=args.S, nb=args.nb)
 
     for _ in range(args.warmup):
@@ -226,18 +241,12 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int8 digits (fp16-held) x tensor cores -> exact int -> f64",
             "data": "synthetic (seeded SplitMix64; bcc LIZ, KKR-shaped t and G)",
-            "config": {"workload": f"KKR tau_00, bcc LIZ {L_SITES} sites, lmax=3 (b={B}), n={N}, E=0.5+0.05i; "
-                                   f"{batch} atoms per GPU per step; M=I-tG built on GPU; block LU nb={args.nb}, "
-                                   f"every GEMM emulated with S={args.S}",
-                       "atoms_per_gpu_per_step": batch, "n": N, "S": args.S, "nb": args.nb,
-                       "eff_fp64_flops_per_solve": FLOPS_PER_SOLVE,
-                       "l2": "256 MB buffer written between timed steps (outside the events); per-step "
-                             f"working set {batch * N * N * 16 / 2**30:.2f} GiB of M",
-                       "parallelism": f"dp{world} (independent atoms per GPU)"},
+            "config": workload_config(args, world),
             "eff_fp64_tflops": round(solves_per_s * FLOPS_PER_SOLVE / 1e12, 3),
             "roofline": roofline, "kernels": kernels, "gpu_launches": int(launches),
             "clocks": clocks, "wall_s_timed": round(t_wall, 3)}
     if not args.no_extras:
+        line["graph"] = graph_measure(ozk, h, args, step, flush)
         line["e2e"] = e2e_measure(ozk, h, args, dev, t_np, G_np, batch)
         line["comparisons"] = comparisons(ozk, h, args, dev, t_np, G_np)
         line["cpu_baseline"] = cpu_baseline(t_np[0], G_np, args.S, args.nb)
@@ -245,6 +254,38 @@ def run_ours(args):
     h.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def graph_measure(ozk, h, args, step, flush):
+    """The same step captured once into a CUDA graph and replayed (same buffers, same L2 flush
+    between steps outside the events)."""
+    import torch
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        h.set_stream(torch.cuda.current_stream())
+        l0 = ozk.launch_count()
+        step()
+        launches = ozk.launch_count() - l0
+    h.set_stream(torch.cuda.current_stream())
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ms = 0.0
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g.replay()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms += a.elapsed_time(b)
+    if h.status():
+        raise RuntimeError("device status set during graph replays")
+    ms /= args.steps
+    del g
+    return {"ms_per_step": round(ms, 3), "value": round(args.batch / (ms / 1e3), 2), "unit": "tau00 solves/s",
+            "kernels_per_graph": int(launches)}
 
 
 def e2e_measure(ozk, h, args, dev, t_np, G_np, batch):
@@ -261,17 +302,16 @@ def e2e_measure(ozk, h, args, dev, t_np, G_np, batch):
     tau_h = torch.zeros((batch, B, B), dtype=torch.complex128).pin_memory()
     i64 = lambda xs: torch.tensor(xs, dtype=torch.int64, device=dev)
     pt = i64([td[a].data_ptr() for a in range(batch)])
-    pg = i64([Gd.data_ptr()] * batch)
     pm = i64([m.data_ptr() for m in Ms])
     pt0 = i64([td[a].data_ptr() for a in range(batch)])      # block 0 of each t is t_0
     ptau = i64([taus[a].data_ptr() for a in range(batch)])
-    Ls, ns = [L_SITES] * batch, [N] * batch
+    ns = [N] * batch
     steps = max(2, min(args.steps, 5))
 
     def step():
         Gd.copy_(Gh, non_blocking=True)
         td.copy_(th, non_blocking=True)
-        ozk.kkr_build_m_batched_ptrs(h, Ls, B, pt, pg, pm)
+        ozk.kkr_build_m_shared_ptrs(h, batch, L_SITES, B, pt, Gd, pm, S=args.S)
         ozk.kkr_tau00_batched_ptrs(h, ns, B, pm, pt0, ptau, S=args.S, nb=args.nb)
         tau_h.copy_(taus, non_blocking=True)
 
@@ -371,10 +411,11 @@ def cpu_baseline(t0_atom, G_np, S, nb):
     co.build()
     M = kkr.kkr_build(t0_atom, G_np)
     t1 = time.perf_counter()
-    co.tau00_block(M, t0_atom[0], nb, S=S)
+    co.tau00_block(M, t0_atom[0], nb, S=S, leaf=B)
     dt = time.perf_counter() - t1
     return {"value": round(1.0 / dt, 4), "unit": "tau00 solves/s", "cores": co.num_threads(), "kind": "oracle",
-            "sample": f"1 solve of the same workload (n={N}, S={S}, nb={nb}) by oracle/c (OpenMP), {dt:.1f} s"}
+            "sample": f"1 solve of the same workload (n={N}, S={S}, panels nb={nb} of {B}x{B} leaves) by "
+                      f"oracle/c (OpenMP), {dt:.1f} s"}
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -391,19 +432,19 @@ def run_reference(args):
     t, G, _ = synth.kkr_system(L_SITES, B, E0, atom=0)
     M = kkr.kkr_build(t, G)
     for _ in range(args.warmup):
-        co.tau00_block(M, t[0], args.nb, S=args.S)
+        co.tau00_block(M, t[0], args.nb, S=args.S, leaf=B)
     t1 = time.perf_counter()
     for _ in range(args.steps):
-        co.tau00_block(M, t[0], args.nb, S=args.S)
+        co.tau00_block(M, t[0], args.nb, S=args.S, leaf=B)
     dt = time.perf_counter() - t1
     v = args.steps / dt
-    sample = (f"{args.steps} timed solves of the configuration-2 system (n={N}, S={args.S}, nb={args.nb}) "
-              f"by oracle/c with OpenMP; one solve per step")
+    sample = (f"{args.steps} timed solves of one atom of the workload (n={N}, S={args.S}, panels nb={args.nb} "
+              f"of {B}x{B} leaves) by oracle/c with OpenMP; one solve per step instead of {args.batch}")
     line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "tau00 solves/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int8 digits -> exact int64/int128 -> f64 (CPU)", "data": "synthetic",
-            "config": {"workload": f"KKR tau_00, bcc LIZ {L_SITES} sites, b={B}, n={N}, E=0.5+0.05i, S={args.S}"},
+            "config": workload_config(args, world),
             "cpu_baseline": {"value": round(v, 4), "unit": "tau00 solves/s", "cores": co.num_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": round(v, 4), "unit": "tau00 solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -34,6 +34,15 @@
  *     grown on demand with cudaMalloc; ozk_reserve() sizes it up front so that later calls
  *     (for example inside a CUDA graph capture) never allocate.  A call that would need to
  *     grow the workspace while its stream is being captured returns OZK_ERR_CAPTURE.
+ *   - Stream capture: a call may be captured into a CUDA graph once a call with the same
+ *     sizes has run on the handle outside capture.  That call sizes the workspace and copies
+ *     the host size arrays of batched calls to device memory, where the handle keeps each
+ *     distinct array until it is destroyed (up to 4096 of them; the 4097th empties the
+ *     cache).  Sizes first seen during capture return OZK_ERR_CAPTURE.  A captured graph
+ *     holds the workspace and size-table addresses: it stays valid while the handle lives,
+ *     its workspace does not grow and its size cache is not emptied, and its replays must
+ *     not overlap other work that uses the same handle.  The launch profiler does not time
+ *     captured launches.
  *   - Nothing aborts the process.
  */
 #ifndef OZK_H
@@ -112,7 +121,9 @@ ozk_status_t ozk_profile_end(ozk_handle_t handle, uint64_t* launches, double* ms
  * conjugate transpose), exactly the BLAS ZGEMM argument list plus the slice count S.
  *   alpha, beta : HOST pointers to two doubles (re, im).
  *   A, B, C     : DEVICE pointers, column major, lda/ldb/ldc >= rows of the stored matrix.
- *   S           : 1..16 slices (B = 8S - 1 bits).  pair_mode: OZK_PAIRS_TRI / _FULL.
+ *   S           : 1..16 slices (B = 8S - 1 bits), or 0: the slice-count selector chooses S
+ *                 in 3..10 and checks the result (see the selector section; triangular pairs).
+ *                 pair_mode: OZK_PAIRS_TRI / _FULL.
  * Epilogues: beta == 0 stores RN(alpha Z) (alpha == 1: bitwise equal to the oracle);
  * alpha == -1, beta == 1 computes C - RN(Z) with one binary64 subtraction (bitwise equal
  * to the oracle's LU update); other alpha, beta use binary64 complex arithmetic.
@@ -153,6 +164,77 @@ ozk_status_t ozaki_zgemm_noalloc(void* stream, char transa, char transb, int m, 
                                  const double* beta, void* C, int ldc, int S, int pair_mode,
                                  int* device_status);
 
+/* ---- slice-count selector -------------------------------------------------------------
+ *
+ * The paper finds that accuracy depends on the precision and on the operator and handles it
+ * by tuning the precision (Abstract; Sec. 4 shows the error falling mode by mode; Sec. 5
+ * argues for adaptive precision); it gives no rule for choosing S.  This library's selector:
+ *   1. computes 16 features of op(A) op(B) (ozk_selector_features; definitions in
+ *      csrc/selector.cu) from per-row / per-column statistics and a probe product
+ *      z = op(A) (op(B) X), X = 2 counter-based random probe vectors;
+ *   2. predicts log10 of the relative Frobenius error for S = 3..10 with a float32
+ *      perceptron 16 -> 64 -> 64 -> 8 (ReLU), whose parameters are trained on the GPU by
+ *      ozk_selector_train_step (mean squared error, Adam);
+ *   3. picks the smallest S whose prediction is <= log10(tol) - margin (else 10);
+ *   4. checks the computed product D a posteriori: r = ||D X - z|| / ||z|| estimates
+ *      ||D - AB||_F / ||AB||_F; if r > tol the product is recomputed with S = 10 (fallback),
+ *      unless OZK_SEL_NO_FALLBACK is set, in which case OZK_ERR_RESIDUAL is returned.
+ * ozaki_zgemm with S = 0 runs these steps.  It synchronises the stream twice (to read the
+ * chosen S and the residual) and cannot be captured (OZK_ERR_CAPTURE).  Parameter layout,
+ * OZK_SEL_NPARAMS floats: W1[64][16], b1[64], W2[64][64], b2[64], W3[8][64], b3[8]. */
+#define OZK_SEL_FEATURES 16
+#define OZK_SEL_OUTPUTS 8
+#define OZK_SEL_NPARAMS 5768
+#define OZK_SEL_SMIN 3
+#define OZK_SEL_SMAX 10
+#define OZK_SEL_NO_FALLBACK 1
+
+typedef struct {
+    int S_selected;            /* S chosen from the prediction */
+    int S_used;                /* S of the returned product (S_selected or OZK_SEL_SMAX) */
+    int fallback;              /* 1 if the product was recomputed with OZK_SEL_SMAX */
+    int residual_ok;           /* 1 if the returned product passed the residual check */
+    double residual;           /* residual estimate of the returned product */
+    double residual_selected;  /* residual estimate of the product at S_selected */
+    float predicted_log10_err[OZK_SEL_OUTPUTS];   /* for S = 3..10 */
+    uint64_t probe_seed;       /* seed of the probe vectors of this call */
+} ozk_selector_info;
+
+/* Random initial parameters (He-scaled normals from a counter-based generator seeded by
+ * `seed`, zero biases); resets the Adam state. */
+ozk_status_t ozk_selector_init(ozk_handle_t handle, uint64_t seed);
+/* Copy parameters from / to a HOST array of OZK_SEL_NPARAMS floats (set resets Adam). */
+ozk_status_t ozk_selector_set_params(ozk_handle_t handle, const float* params);
+ozk_status_t ozk_selector_get_params(ozk_handle_t handle, float* params);
+/* Parameter file: 8 bytes "OZKSEL1\0", int32 OZK_SEL_NPARAMS, then the floats (little
+ * endian).  OZK_ERR_NOFILE if it cannot be read or written, OZK_ERR_ARG if malformed. */
+ozk_status_t ozk_selector_load(ozk_handle_t handle, const char* path);
+ozk_status_t ozk_selector_save(ozk_handle_t handle, const char* path);
+/* Tolerance on the relative Frobenius error (default 1e-10), safety margin in decades
+ * subtracted from log10(tol) when choosing (default 0.3), flags (OZK_SEL_NO_FALLBACK). */
+ozk_status_t ozk_selector_configure(ozk_handle_t handle, double tol, double margin, int flags);
+/* The 16 features of op(A) op(B) into a DEVICE array of 16 floats, with the probe vectors
+ * of `probe_seed`.  k >= 1. */
+ozk_status_t ozk_selector_features(ozk_handle_t handle, char transa, char transb, int m, int n, int k,
+                                   const void* A, int lda, const void* B, int ldb, uint64_t probe_seed,
+                                   float* features);
+/* Y (N x 8) = perceptron(X (N x 16)); DEVICE row-major float arrays. */
+ozk_status_t ozk_selector_predict(ozk_handle_t handle, int N, const float* X, float* Y);
+/* One Adam step (lr; beta1 0.9, beta2 0.999, eps 1e-8) on the mean squared error of the
+ * predictions of X (N x 16) against targets T (N x 8), DEVICE row-major float arrays.
+ * *loss (HOST, may be NULL) receives the loss before the step (synchronises the stream). */
+ozk_status_t ozk_selector_train_step(ozk_handle_t handle, int N, const float* X, const float* T, float lr,
+                                     double* loss);
+/* Gradient of that loss with respect to the parameters, into a DEVICE array of
+ * OZK_SEL_NPARAMS floats, without updating them. */
+ozk_status_t ozk_selector_gradient(ozk_handle_t handle, int N, const float* X, const float* T, float* grad);
+/* What the last S = 0 ozaki_zgemm on this handle chose and measured. */
+ozk_status_t ozk_selector_last(ozk_handle_t handle, ozk_selector_info* info);
+/* ||X - Y||_F / ||Y||_F of two m x n DEVICE matrices (column major) into *rel (HOST);
+ * synchronises the stream. */
+ozk_status_t ozk_rel_diff(ozk_handle_t handle, int m, int n, const void* X, int ldx, const void* Y, int ldy,
+                          double* rel);
+
 /* Plain binary64 ZGEMM on the FP64 tensor path (DMMA, mma.sync m8n8k4.f64), same argument
  * meaning as ozaki_zgemm without S: the comparison baseline on the same GPU. */
 ozk_status_t ozk_zgemm_dmma(ozk_handle_t handle, char transa, char transb, int m, int n, int k,
@@ -186,6 +268,18 @@ ozk_status_t kkr_build_m(ozk_handle_t handle, int L, int b, const void* t, const
  * entries may share one G (atoms of one lattice at one energy). */
 ozk_status_t kkr_build_m_batched(ozk_handle_t handle, int batch, const int* L, int b,
                                  const void* const* t, const void* const* G, void* const* M);
+
+/* M_a = I - blockdiag(t_a) G for natoms atoms that share one G (atoms of one lattice at one
+ * energy), every product an emulated GEMM with S slices (paper Sec. 3.2: the KKR matrix is
+ * built by the ZGEMMs the emulation intercepts).  For each site block row i the atoms' blocks
+ * t_{a,i} are stacked into one (natoms b) x b left operand and multiplied by the block row
+ * G[ib:(i+1)b, :] in one GEMM (L GEMMs in one launch); the epilogue writes I - RN(Z) straight
+ * into the atoms' M (row a b + r of GEMM i is row i b + r of M_a), reading no C.
+ *   t: DEVICE array of natoms DEVICE pointers, each to L column-major b x b blocks (block l
+ *      at offset l b b).  G: DEVICE n x n column major (n = L b).  M: DEVICE array of natoms
+ *      DEVICE pointers to n x n column-major outputs (ld n). */
+ozk_status_t kkr_build_m_shared(ozk_handle_t handle, int natoms, int L, int b, const void* const* t,
+                                const void* G, void* const* M, int S);
 
 /* tau_00 = [M^-1]_00 t_0 = S_00^-1 t_0 by block LU (paper Sec. 3.2: LU-based inversion of the
  * multiple scattering matrix).  Panels J = [p, q) of width nb are eliminated from the trailing

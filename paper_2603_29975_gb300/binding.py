@@ -18,6 +18,20 @@ LIB_PATH = os.path.join(HERE, "libozk.so")
 OZK_OK = 0
 OZK_PAIRS_TRI = 0
 OZK_PAIRS_FULL = 1
+OZK_SEL_FEATURES = 16
+OZK_SEL_OUTPUTS = 8
+OZK_SEL_NPARAMS = 5768
+OZK_SEL_SMIN, OZK_SEL_SMAX = 3, 10
+OZK_SEL_NO_FALLBACK = 1
+SELECTOR_WEIGHTS = os.path.join(HERE, "selector_weights.bin")
+
+
+class SelectorInfo(ctypes.Structure):
+    """ozk_selector_info (include/ozk.h)."""
+    _fields_ = [("S_selected", ctypes.c_int), ("S_used", ctypes.c_int), ("fallback", ctypes.c_int),
+                ("residual_ok", ctypes.c_int), ("residual", ctypes.c_double),
+                ("residual_selected", ctypes.c_double),
+                ("predicted_log10_err", ctypes.c_float * OZK_SEL_OUTPUTS), ("probe_seed", ctypes.c_uint64)]
 STATUS_NAMES = {1: "ARG", 2: "NONFINITE", 3: "SINGULAR", 4: "TIMEOUT", 5: "CUDA", 6: "RANGE",
                 7: "CAPTURE", 8: "RESIDUAL", 9: "NOFILE"}
 
@@ -25,7 +39,10 @@ EXPORTS = ["ozk_create", "ozk_destroy", "ozk_set_stream", "ozk_get_status", "ozk
            "ozk_zgemm_workspace_size", "ozk_last_error", "ozk_launch_count", "ozaki_zgemm",
            "ozaki_zgemm_vbatched", "ozk_zgemm_dmma", "ozk_split_debug", "ozk_group_sums_debug",
            "kkr_build_m", "kkr_tau00", "kkr_tau00_batched", "ozk_profile_begin", "ozk_profile_end",
-           "kkr_build_m_batched", "ozaki_zgemm_noalloc"]
+           "kkr_build_m_batched", "ozaki_zgemm_noalloc", "ozk_selector_init", "ozk_selector_set_params",
+           "ozk_selector_get_params", "ozk_selector_load", "ozk_selector_save", "ozk_selector_configure",
+           "ozk_selector_features", "ozk_selector_predict", "ozk_selector_train_step", "ozk_selector_gradient",
+           "ozk_selector_last", "ozk_rel_diff", "kkr_build_m_shared"]
 KIND_NAMES = ["split", "slice_gemm", "gj", "build_m", "dmma", "other"]
 
 _lib = None
@@ -62,7 +79,21 @@ def lib():
         L.kkr_tau00.argtypes = [vp, i, i, vp, vp, vp, i, i]
         L.kkr_tau00_batched.argtypes = [vp, i, ip, i, vp, vp, vp, i, i]
         L.kkr_build_m_batched.argtypes = [vp, i, ip, i, vp, vp, vp]
+        L.kkr_build_m_shared.argtypes = [vp, i, i, i, vp, vp, vp, i]
         L.ozaki_zgemm_noalloc.argtypes = [vp, c, c, i, i, i, dp, vp, i, vp, i, dp, vp, i, i, i, vp]
+        fp, u64, f32 = ctypes.POINTER(ctypes.c_float), ctypes.c_uint64, ctypes.c_float
+        L.ozk_selector_init.argtypes = [vp, u64]
+        L.ozk_selector_set_params.argtypes = [vp, fp]
+        L.ozk_selector_get_params.argtypes = [vp, fp]
+        L.ozk_selector_load.argtypes = [vp, ctypes.c_char_p]
+        L.ozk_selector_save.argtypes = [vp, ctypes.c_char_p]
+        L.ozk_selector_configure.argtypes = [vp, ctypes.c_double, ctypes.c_double, i]
+        L.ozk_selector_features.argtypes = [vp, c, c, i, i, i, vp, i, vp, i, u64, vp]
+        L.ozk_selector_predict.argtypes = [vp, i, vp, vp]
+        L.ozk_selector_train_step.argtypes = [vp, i, vp, vp, f32, dp]
+        L.ozk_selector_gradient.argtypes = [vp, i, vp, vp, vp]
+        L.ozk_selector_last.argtypes = [vp, ctypes.POINTER(SelectorInfo)]
+        L.ozk_rel_diff.argtypes = [vp, i, i, vp, i, vp, i, dp]
         L.ozk_profile_begin.argtypes = [vp]
         L.ozk_profile_end.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), dp, dp, dp]
         for name in EXPORTS:
@@ -148,6 +179,41 @@ class Handle:
         _check(lib().ozk_profile_end(self._h, n, ms, fl, by), "ozk_profile_end")
         return {KIND_NAMES[k]: {"launches": int(n[k]), "ms": float(ms[k]), "flops": float(fl[k]),
                                 "bytes": float(by[k])} for k in range(K)}
+
+    # ---- slice-count selector
+    def selector_init(self, seed: int = 1):
+        _check(lib().ozk_selector_init(self._h, seed), "ozk_selector_init")
+
+    def selector_set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != OZK_SEL_NPARAMS:
+            raise OzkError(f"expected {OZK_SEL_NPARAMS} parameters")
+        _check(lib().ozk_selector_set_params(self._h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+               "ozk_selector_set_params")
+
+    def selector_get_params(self) -> np.ndarray:
+        p = np.zeros(OZK_SEL_NPARAMS, dtype=np.float32)
+        _check(lib().ozk_selector_get_params(self._h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+               "ozk_selector_get_params")
+        return p
+
+    def selector_load(self, path: str = SELECTOR_WEIGHTS):
+        _check(lib().ozk_selector_load(self._h, os.fsencode(path)), "ozk_selector_load")
+
+    def selector_save(self, path: str):
+        _check(lib().ozk_selector_save(self._h, os.fsencode(path)), "ozk_selector_save")
+
+    def selector_configure(self, tol: float = 1e-10, margin: float = 0.3, flags: int = 0):
+        _check(lib().ozk_selector_configure(self._h, tol, margin, flags), "ozk_selector_configure")
+
+    def selector_last(self) -> dict:
+        info = SelectorInfo()
+        _check(lib().ozk_selector_last(self._h, ctypes.byref(info)), "ozk_selector_last")
+        return {"S_selected": info.S_selected, "S_used": info.S_used, "fallback": bool(info.fallback),
+                "residual_ok": bool(info.residual_ok), "residual": info.residual,
+                "residual_selected": info.residual_selected,
+                "predicted_log10_err": [float(v) for v in info.predicted_log10_err],
+                "probe_seed": int(info.probe_seed)}
 
     def close(self):
         if self._h:
@@ -271,6 +337,13 @@ def kkr_build_m_batched_ptrs(h: Handle, L_list, b: int, pt, pg, pm):
            "kkr_build_m_batched")
 
 
+def kkr_build_m_shared_ptrs(h: Handle, natoms: int, L: int, b: int, pt, G, pm, S: int = 7):
+    """M_a = I - blockdiag(t_a) G for atoms sharing G, emulated with S slices; pt, pm: int64
+    CUDA tensors of device pointers (t blocks, M outputs), G a column-major CUDA tensor."""
+    _check(lib().kkr_build_m_shared(h.ptr, natoms, L, b, pt.data_ptr(), _ptr(G), pm.data_ptr(), S),
+           "kkr_build_m_shared")
+
+
 def kkr_tau00(h: Handle, M, t0, tau, S: int = 7, nb: int = 64):
     """tau_00 = [M^-1]_00 t_0 (M is overwritten)."""
     n = M.shape[0]
@@ -301,3 +374,63 @@ def kkr_tau00_batched_ptrs(h: Handle, n_list, b: int, pm, pt, pu, S: int = 7, nb
     n = (ctypes.c_int * ns)(*[int(v) for v in n_list])
     _check(lib().kkr_tau00_batched(h.ptr, ns, n, b, pm.data_ptr(), pt.data_ptr(), pu.data_ptr(), S, nb),
            "kkr_tau00_batched")
+
+
+# ----------------------------------------------------------------------------- selector
+def _f32(t, shape):
+    import torch
+    if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous() or tuple(t.shape) != tuple(shape):
+        raise OzkError(f"expected a contiguous float32 CUDA tensor of shape {shape}")
+    return t.data_ptr()
+
+
+def selector_features(h: Handle, A, B, transa="N", transb="N", seed: int = 0):
+    """The 16 selector features of op(A) op(B) (float32 CUDA tensor)."""
+    import torch
+    m, n, k = _shapes(transa, transb, A, B)
+    f = torch.empty(OZK_SEL_FEATURES, dtype=torch.float32, device=A.device)
+    _check(lib().ozk_selector_features(h.ptr, transa.encode(), transb.encode(), m, n, k, _ptr(A),
+                                       _ld(A, A.shape[0]), _ptr(B), _ld(B, B.shape[0]), seed, f.data_ptr()),
+           "ozk_selector_features")
+    return f
+
+
+def selector_predict(h: Handle, X):
+    """Perceptron outputs (N x 8) for features X (N x 16), float32 CUDA tensors."""
+    import torch
+    N = X.shape[0]
+    Y = torch.empty((N, OZK_SEL_OUTPUTS), dtype=torch.float32, device=X.device)
+    _check(lib().ozk_selector_predict(h.ptr, N, _f32(X, (N, OZK_SEL_FEATURES)), Y.data_ptr()),
+           "ozk_selector_predict")
+    return Y
+
+
+def selector_train_step(h: Handle, X, T, lr: float, want_loss: bool = True):
+    """One Adam step on the mean squared error of X (N x 16) against T (N x 8); returns the
+    loss before the step (or None)."""
+    N = X.shape[0]
+    loss = ctypes.c_double(0.0)
+    _check(lib().ozk_selector_train_step(h.ptr, N, _f32(X, (N, OZK_SEL_FEATURES)), _f32(T, (N, OZK_SEL_OUTPUTS)),
+                                         float(lr), ctypes.byref(loss) if want_loss else None),
+           "ozk_selector_train_step")
+    return loss.value if want_loss else None
+
+
+def selector_gradient(h: Handle, X, T):
+    import torch
+    N = X.shape[0]
+    g = torch.empty(OZK_SEL_NPARAMS, dtype=torch.float32, device=X.device)
+    _check(lib().ozk_selector_gradient(h.ptr, N, _f32(X, (N, OZK_SEL_FEATURES)), _f32(T, (N, OZK_SEL_OUTPUTS)),
+                                       g.data_ptr()), "ozk_selector_gradient")
+    return g
+
+
+def rel_diff(h: Handle, X, Y) -> float:
+    """||X - Y||_F / ||Y||_F of two column-major complex CUDA matrices of one shape."""
+    if tuple(X.shape) != tuple(Y.shape):
+        raise OzkError("shapes differ")
+    m, n = X.shape
+    out = ctypes.c_double(0.0)
+    _check(lib().ozk_rel_diff(h.ptr, m, n, _ptr(X), _ld(X, m), _ptr(Y), _ld(Y, m), ctypes.byref(out)),
+           "ozk_rel_diff")
+    return out.value

@@ -1,8 +1,10 @@
 // C ABI of libozk (declared in include/ozk.h): handle, workspace, TMA descriptors, and the
 // host-side drivers of the emulated ZGEMM and of the block-LU tau_00 solve.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <vector>
 
 #include "ozk_params.cuh"
@@ -81,9 +83,27 @@ struct ozk_context {
   std::vector<ProfRec> recs;
   std::vector<cudaEvent_t> pool;
   size_t pool_used = 0;
+  // device copies of the host size lists of batched calls, kept by content for the life of
+  // the handle (see size_table)
+  std::map<std::vector<int>, int*> tables;
+  // slice-count selector: [parameters | Adam first moments | second moments | gradient]
+  float* sel_p = nullptr;
+  int sel_t = 0;
+  bool sel_ready = false;
+  double sel_tol = 1e-10, sel_margin = 0.3;
+  int sel_flags = 0;
+  uint64_t sel_seed = 0x5E1EC7ull, sel_calls = 0;
+  void* sel_ws = nullptr;                   // selector scratch (features, probes, products)
+  size_t sel_ws_bytes = 0;
+  ozk_selector_info sel_last{};
 };
 
 namespace {
+bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+
 cudaEvent_t prof_event(ozk_context* h) {
   if (h->pool_used == h->pool.size()) {
     cudaEvent_t e;
@@ -94,13 +114,15 @@ cudaEvent_t prof_event(ozk_context* h) {
 }
 
 // RAII scope: records a start event before and a stop event after the launches in its body.
+// Launches enqueued while the stream is being captured are not timed (they run later, as graph
+// nodes).
 struct Prof {
-  ozk_context* h; int kind; double flops, bytes; cudaEvent_t a = nullptr;
+  ozk_context* h; int kind; double flops, bytes; cudaEvent_t a = nullptr; bool on = false;
   Prof(ozk_context* hh, int k, double f, double by) : h(hh), kind(k), flops(f), bytes(by) {
-    if (h->prof) { a = prof_event(h); cudaEventRecord(a, h->stream); }
+    if (h->prof && !capturing(h->stream)) { on = true; a = prof_event(h); cudaEventRecord(a, h->stream); }
   }
   ~Prof() {
-    if (h->prof) {
+    if (on) {
       cudaEvent_t b = prof_event(h);
       cudaEventRecord(b, h->stream);
       h->recs.push_back({kind, a, b, flops, bytes});
@@ -112,9 +134,7 @@ struct Prof {
 // --------------------------------------------------------------------- workspace
 static ozk_status_t ensure_ws(ozk_context* h, size_t bytes) {
   if (bytes <= h->ws_bytes) return OZK_OK;
-  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  cudaStreamIsCapturing(h->stream, &cs);
-  if (cs != cudaStreamCaptureStatusNone)
+  if (capturing(h->stream))
     return set_error(OZK_ERR_CAPTURE, "workspace must grow during stream capture: call ozk_reserve first");
   ozk_status_t st = cuda_check(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
   if (st) return st;
@@ -127,6 +147,39 @@ static ozk_status_t ensure_ws(ozk_context* h, size_t bytes) {
   st = cuda_check(cudaMemset(h->ws, 0, nb), "cudaMemset(workspace)");
   if (st) return st;
   h->ws_bytes = nb;
+  return OZK_OK;
+}
+
+// Device copy of a host size list of a batched call.  Lists are kept by content for the life of
+// the handle, so a launch captured into a CUDA graph keeps reading a table that later calls
+// never overwrite, and a repeated call uploads nothing.  A list first seen while the stream is
+// being captured is an error: neither the allocation nor the upload of a pageable host array can
+// be captured, so one call with the same sizes has to come before the capture.  Past
+// kMaxTables distinct lists the cache is emptied (after synchronising the stream), which
+// invalidates graphs captured before.
+constexpr size_t kMaxTables = 4096;
+
+static ozk_status_t size_table(ozk_context* h, std::vector<int>&& key, const int** out) {
+  auto it = h->tables.find(key);
+  if (it != h->tables.end()) { *out = it->second; return OZK_OK; }
+  if (capturing(h->stream))
+    return set_error(OZK_ERR_CAPTURE, "batched sizes first seen during stream capture: make one call with the "
+                                      "same sizes before capturing");
+  if (h->tables.size() >= kMaxTables) {
+    ozk_status_t st = cuda_check(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    if (st) return st;
+    for (auto& kv : h->tables) cudaFree(kv.second);
+    h->tables.clear();
+  }
+  int* d = nullptr;
+  const size_t bytes = std::max<size_t>(1, key.size()) * sizeof(int);
+  ozk_status_t st = cuda_check(cudaMalloc(&d, bytes), "cudaMalloc(size table)");
+  if (st) return st;
+  st = cuda_check(cudaMemcpyAsync(d, key.data(), key.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream),
+                  "upload size table");
+  if (st) { cudaFree(d); return st; }
+  *out = d;
+  h->tables.emplace(std::move(key), d);
   return OZK_OK;
 }
 
@@ -166,6 +219,8 @@ struct EmuGemm {
   const int* tskm = nullptr; const int* tskn = nullptr;   // skip box tables (batched)
   double sum_mnk = -1;                        // sum over problems of m n k (batched; -1: single)
   double sum_mk = 0, sum_nk = 0;              // operand sizes (complex elements) for byte counts
+  long long zsA = 0, zsB = 0;                 // uniform batch of single-size problems: operand strides
+  double2* const* crow = nullptr; int crow_b = 0;   // row-block scatter of the output
 };
 
 struct GemmPlan {
@@ -230,7 +285,7 @@ ozk_status_t run_emulated(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0
   sp.trans = g.oa.trans; sp.conj = g.oa.conj; sp.side = 0;
   sp.out_rows = P.rowsA; sp.out = As; sp.exps = e; sp.exp_stride = P.rowsA;
   sp.dbg_digits = g.dbg_digits_a;
-  if (single) { sp.X = nullptr; sp.X1 = g.A; sp.ld1 = g.lda; sp.rows1 = g.m; sp.k1 = g.k; }
+  if (single) { sp.X = nullptr; sp.X1 = g.A; sp.ld1 = g.lda; sp.rows1 = g.m; sp.k1 = g.k; sp.zstride1 = g.zsA; }
   else { sp.X = g.tA; sp.ld = g.tlda; sp.rows = g.tm; sp.kdim = g.tk; }
   const double smnk = g.sum_mnk >= 0 ? g.sum_mnk : static_cast<double>(g.m) * g.n * g.k;
   const double smk = g.sum_mnk >= 0 ? g.sum_mk : static_cast<double>(g.m) * g.k;
@@ -245,7 +300,7 @@ ozk_status_t run_emulated(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0
   sq.trans = g.ob.trans ? 0 : 1; sq.conj = g.ob.conj; sq.side = 1;
   sq.out_rows = P.rowsB; sq.out = Bs; sq.exps = f; sq.exp_stride = std::max(g.nmax, 1);
   sq.dbg_digits = nullptr;
-  if (single) { sq.X = nullptr; sq.X1 = g.B; sq.ld1 = g.ldb; sq.rows1 = g.n; sq.k1 = g.k; }
+  if (single) { sq.X = nullptr; sq.X1 = g.B; sq.ld1 = g.ldb; sq.rows1 = g.n; sq.k1 = g.k; sq.zstride1 = g.zsB; }
   else { sq.X = g.tB; sq.ld = g.tldb; sq.rows = g.tn; sq.kdim = g.tk; }
   {
     Prof pr(h, OZK_KIND_SPLIT, 0.0, snk * (32.0 + 8.0 * S));
@@ -273,6 +328,7 @@ ozk_status_t run_emulated(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0
   gp.groups = g.groups; gp.status = h->d_status;
   if (single) { gp.m = nullptr; gp.m1 = g.m; gp.n1 = g.n; gp.C1 = g.C; gp.ldc1 = g.ldc; gp.skm1 = g.skm; gp.skn1 = g.skn; }
   else { gp.m = g.tm; gp.n = g.tn; gp.C = g.tC; gp.ldc = g.tldc; gp.skm = g.tskm; gp.skn = g.tskn; }
+  gp.crow = g.crow; gp.crow_b = g.crow_b;
   int np = 0;
   for (int gg = 2; gg <= gmax; ++gg) {
     bool first = true;
@@ -307,6 +363,169 @@ ozk_status_t check_dims(OpFlags oa, OpFlags ob, int m, int n, int k, int lda, in
 
 }  // namespace
 
+// --------------------------------------------------------------------- slice-count selector
+// Scratch of the selector, separate from the GEMM workspace (the S = 0 path runs emulated
+// GEMMs while its features and probe products are alive).
+static ozk_status_t ensure_sel_ws(ozk_context* h, size_t bytes) {
+  if (bytes <= h->sel_ws_bytes) return OZK_OK;
+  if (capturing(h->stream)) return set_error(OZK_ERR_CAPTURE, "selector scratch must grow during stream capture");
+  ozk_status_t st = cuda_check(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+  if (st) return st;
+  if (h->sel_ws) cudaFree(h->sel_ws);
+  h->sel_ws = nullptr;
+  h->sel_ws_bytes = 0;
+  const size_t nb = align_up(bytes + (bytes >> 3), 1 << 20);
+  st = cuda_check(cudaMalloc(&h->sel_ws, nb), "cudaMalloc(selector scratch)");
+  if (st) return st;
+  h->sel_ws_bytes = nb;
+  return OZK_OK;
+}
+
+static ozk_status_t sel_alloc_params(ozk_context* h) {
+  if (h->sel_p) return OZK_OK;
+  ozk_status_t st = cuda_check(cudaMalloc(&h->sel_p, 4 * sizeof(float) * SEL_NPARAMS), "cudaMalloc(selector)");
+  if (st) return st;
+  return cuda_check(cudaMemset(h->sel_p, 0, 4 * sizeof(float) * SEL_NPARAMS), "cudaMemset(selector)");
+}
+
+// upload parameters, clear the Adam moments
+static ozk_status_t sel_upload(ozk_context* h, const float* host) {
+  ozk_status_t st = sel_alloc_params(h);
+  if (st) return st;
+  st = cuda_check(cudaMemcpy(h->sel_p, host, sizeof(float) * SEL_NPARAMS, cudaMemcpyHostToDevice), "upload params");
+  if (st) return st;
+  st = cuda_check(cudaMemset(h->sel_p + SEL_NPARAMS, 0, 3 * sizeof(float) * SEL_NPARAMS), "clear Adam state");
+  if (st) return st;
+  h->sel_t = 0;
+  h->sel_ready = true;
+  return OZK_OK;
+}
+
+struct SelScratch {
+  SelVecStats a, b;
+  int* ex;
+  double2 *X, *y, *zs, *W, *D;
+  float *f, *Y;
+  SelAux* aux;
+};
+
+// carve the scratch of the product op(A) op(B) (m x k times k x n); D (m x n) on request
+static ozk_status_t sel_scratch(ozk_context* h, int m, int n, int k, bool needD, SelScratch* s) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) { const size_t o = off; off = align_up(off + std::max<size_t>(bytes, 1), 256); return o; };
+  const size_t P = SEL_PROBES;
+  const size_t o_ar = take(8 * size_t(m)), o_ae = take(4 * size_t(m)), o_ash = take(8 * size_t(m)), o_az = take(4 * size_t(m));
+  const size_t o_br = take(8 * size_t(n)), o_be = take(4 * size_t(n)), o_bsh = take(8 * size_t(n)), o_bz = take(4 * size_t(n));
+  const size_t o_ex = take(8), o_X = take(16 * P * n), o_y = take(16 * P * k), o_zs = take(16 * P * m);
+  const size_t o_W = take(16 * P * m), o_f = take(4 * SEL_NF), o_Y = take(4 * SEL_NO), o_aux = take(sizeof(SelAux));
+  const size_t o_D = needD ? take(16 * size_t(m) * n) : 0;
+  ozk_status_t st = ensure_sel_ws(h, off);
+  if (st) return st;
+  uint8_t* b = static_cast<uint8_t*>(h->sel_ws);
+  s->a = {reinterpret_cast<double*>(b + o_ar), reinterpret_cast<int*>(b + o_ae), reinterpret_cast<double*>(b + o_ash),
+          reinterpret_cast<int*>(b + o_az)};
+  s->b = {reinterpret_cast<double*>(b + o_br), reinterpret_cast<int*>(b + o_be), reinterpret_cast<double*>(b + o_bsh),
+          reinterpret_cast<int*>(b + o_bz)};
+  s->ex = reinterpret_cast<int*>(b + o_ex);
+  s->X = reinterpret_cast<double2*>(b + o_X);
+  s->y = reinterpret_cast<double2*>(b + o_y);
+  s->zs = reinterpret_cast<double2*>(b + o_zs);
+  s->W = reinterpret_cast<double2*>(b + o_W);
+  s->f = reinterpret_cast<float*>(b + o_f);
+  s->Y = reinterpret_cast<float*>(b + o_Y);
+  s->aux = reinterpret_cast<SelAux*>(b + o_aux);
+  s->D = needD ? reinterpret_cast<double2*>(b + o_D) : nullptr;
+  return OZK_OK;
+}
+
+// features of op(A) op(B) into s.f, the scaled probe product into s.zs, E and ||zs||^2 into s.aux
+static ozk_status_t sel_features(ozk_context* h, const OpFlags& oa, const OpFlags& ob, int m, int n, int k,
+                                 const double2* A, int lda, const double2* B, int ldb, uint64_t seed,
+                                 const SelScratch& s) {
+  cudaStream_t st = h->stream;
+  SelBases bs;
+  for (int i = 0; i < 2 * SEL_PROBES; ++i) bs.b[i] = sm_base_host(seed, static_cast<uint64_t>(i));
+  launch_probe(s.X, n, bs, st);
+  // rows of op(A): rows of A (strided) or columns of A (contiguous)
+  launch_vec_stats(A, lda, m, k, oa.trans != 0, s.a, st);
+  // columns of op(B): columns of B (contiguous) or rows of B (strided)
+  launch_vec_stats(B, ldb, n, k, ob.trans == 0, s.b, st);
+  launch_max_exp(s.a, m, s.b, n, s.ex, st);
+  // y = (2^-EB op(B)) X, zs = (2^-EA op(A)) y
+  launch_gemv(B, ldb, k, n, ob.trans == 0 ? 0 : (ob.conj ? 2 : 1), s.X, n, s.y, k, s.ex, 1, st);
+  launch_gemv(A, lda, m, k, oa.trans == 0 ? 0 : (oa.conj ? 2 : 1), s.y, k, s.zs, m, s.ex, 0, st);
+  launch_selector_features(s.a, m, s.b, n, k, s.X, s.zs, s.ex, s.f, s.aux, st);
+  return cuda_check(cudaGetLastError(), "selector feature launches");
+}
+
+static ozk_status_t read_aux(ozk_context* h, const SelAux* d, SelAux* out) {
+  ozk_status_t st = cuda_check(cudaMemcpyAsync(out, d, sizeof(SelAux), cudaMemcpyDeviceToHost, h->stream), "read aux");
+  if (st) return st;
+  return cuda_check(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+}
+
+// S = 0: choose S, compute the product, check it with the probes, fall back to SMAX.
+static ozk_status_t zgemm_auto(ozk_context* h, const EmuGemm& g) {
+  if (!h->sel_ready)
+    return set_error(OZK_ERR_ARG, "S = 0 needs selector parameters (ozk_selector_init, _load or _set_params)");
+  if (capturing(h->stream))
+    return set_error(OZK_ERR_CAPTURE, "S = 0 synchronises to read the selector's choice and cannot be captured");
+  const int m = g.m, n = g.n, k = g.k;
+  const bool direct = g.ar == 1.0 && g.ai == 0.0 && g.br == 0.0 && g.bi == 0.0;
+  SelScratch s;
+  ozk_status_t st = sel_scratch(h, m, n, k, !direct, &s);
+  if (st) return st;
+  ozk_selector_info info{};
+  info.probe_seed = h->sel_seed + h->sel_calls++;
+  st = sel_features(h, g.oa, g.ob, m, n, k, g.A, g.lda, g.B, g.ldb, info.probe_seed, s);
+  if (st) return st;
+  launch_mlp_forward(h->sel_p, s.f, 1, nullptr, nullptr, s.Y, h->stream);
+  launch_choose(s.Y, static_cast<float>(std::log10(h->sel_tol) - h->sel_margin), s.aux, h->stream);
+  SelAux aux;
+  st = read_aux(h, s.aux, &aux);
+  if (st) return st;
+  info.S_selected = aux.S;
+  for (int o = 0; o < SEL_NO; ++o) info.predicted_log10_err[o] = aux.pred[o];
+  EmuGemm d = g;
+  d.C = direct ? g.C : s.D;
+  d.ldc = direct ? g.ldc : m;
+  d.ar = 1; d.ai = 0; d.br = 0; d.bi = 0;
+  d.pair_mode = OZK_PAIRS_TRI;
+  auto product_and_check = [&](int S, double* r) -> ozk_status_t {
+    d.S = S;
+    ozk_status_t e = run_emulated(h, d);
+    if (e) return e;
+    launch_gemv(d.C, d.ldc, m, n, 0, s.X, n, s.W, m, nullptr, 0, h->stream);
+    launch_residual(s.W, s.zs, m, s.aux, h->stream);
+    SelAux a2;
+    e = read_aux(h, s.aux, &a2);
+    *r = a2.resid;
+    return e;
+  };
+  double r = 0.0;
+  st = product_and_check(aux.S, &r);
+  if (st) return st;
+  info.residual_selected = r;
+  info.S_used = aux.S;
+  if (!(r <= h->sel_tol) && !(h->sel_flags & OZK_SEL_NO_FALLBACK) && aux.S < SEL_SMAX) {
+    st = product_and_check(SEL_SMAX, &r);
+    if (st) return st;
+    info.S_used = SEL_SMAX;
+    info.fallback = 1;
+  }
+  info.residual = r;
+  info.residual_ok = r <= h->sel_tol ? 1 : 0;
+  if (!direct) {
+    launch_axpby(m, n, s.D, m, g.C, g.ldc, g.ar, g.ai, g.br, g.bi, h->stream);
+    st = cuda_check(cudaGetLastError(), "axpby launch");
+    if (st) return st;
+  }
+  h->sel_last = info;
+  if (!info.residual_ok && (h->sel_flags & OZK_SEL_NO_FALLBACK))
+    return set_error(OZK_ERR_RESIDUAL, "residual check failed at the selected S and fallback is disabled");
+  return OZK_OK;
+}
+
 // --------------------------------------------------------------------- public API
 extern "C" {
 
@@ -326,6 +545,9 @@ ozk_status_t ozk_destroy(ozk_handle_t h) {
   cudaStreamSynchronize(h->stream);
   if (h->ws) cudaFree(h->ws);
   if (h->d_status) cudaFree(h->d_status);
+  if (h->sel_p) cudaFree(h->sel_p);
+  if (h->sel_ws) cudaFree(h->sel_ws);
+  for (auto& kv : h->tables) cudaFree(kv.second);
   for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
   delete h;
   return OZK_OK;
@@ -386,6 +608,7 @@ ozk_status_t ozaki_zgemm(ozk_handle_t h, char transa, char transb, int m, int n,
   g.C = static_cast<double2*>(C); g.ldc = ldc;
   g.ar = alpha[0]; g.ai = alpha[1]; g.br = beta[0]; g.bi = beta[1];
   g.S = S; g.pair_mode = pair_mode;
+  if (S == 0) return zgemm_auto(h, g);
   return run_emulated(h, g);
 }
 
@@ -413,18 +636,16 @@ ozk_status_t ozaki_zgemm_vbatched(ozk_handle_t h, char transa, char transb, cons
   GemmPlan P;
   ozk_status_t st = plan_gemm(g, &P);
   if (st) return st;
-  // device table of sizes after the GEMM workspace: m, n, k, lda, ldb, ldc
-  const size_t tab_off = align_up(P.total, 256);
-  const size_t tab_bytes = 6 * static_cast<size_t>(batch) * sizeof(int);
-  st = ensure_ws(h, tab_off + tab_bytes);
+  st = ensure_ws(h, P.total);
   if (st) return st;
+  // device table of sizes: m, n, k, lda, ldb, ldc
   std::vector<int> tab(6 * static_cast<size_t>(batch));
   for (int i = 0; i < batch; ++i) {
     tab[i] = m[i]; tab[batch + i] = n[i]; tab[2 * batch + i] = k[i];
     tab[3 * batch + i] = lda[i]; tab[4 * batch + i] = ldb[i]; tab[5 * batch + i] = ldc[i];
   }
-  int* dtab = reinterpret_cast<int*>(static_cast<uint8_t*>(h->ws) + tab_off);
-  st = cuda_check(cudaMemcpyAsync(dtab, tab.data(), tab_bytes, cudaMemcpyHostToDevice, h->stream), "upload sizes");
+  const int* dtab = nullptr;
+  st = size_table(h, std::move(tab), &dtab);
   if (st) return st;
   g.tm = dtab; g.tn = dtab + batch; g.tk = dtab + 2 * batch;
   g.tlda = dtab + 3 * batch; g.tldb = dtab + 4 * batch; g.tldc = dtab + 5 * batch;
@@ -623,6 +844,44 @@ ozk_status_t kkr_tau00(ozk_handle_t h, int n, int b, void* Mv, const void* t0, v
   return cuda_check(cudaGetLastError(), "kkr_tau00 launches");
 }
 
+ozk_status_t kkr_build_m_shared(ozk_handle_t h, int natoms, int L, int b, const void* const* t, const void* G,
+                                void* const* M, int S) {
+  if (!h || !t || !G || !M) return set_error(OZK_ERR_ARG, "null argument");
+  if (natoms < 0 || L < 1 || b < 1) return set_error(OZK_ERR_ARG, "need natoms >= 0, L >= 1, b >= 1");
+  if (S < 1 || S > 16) return set_error(OZK_ERR_ARG, "S must be in 1..16");
+  if (natoms == 0) return OZK_OK;
+  const long long rows = static_cast<long long>(natoms) * b, n = static_cast<long long>(L) * b;
+  if (rows > (1 << 30) || n > (1 << 30)) return set_error(OZK_ERR_ARG, "sizes too large");
+  // block row i of every atom's M: I - (t_{a,i} stacked over the atoms) G[ib:(i+1)b, :], one
+  // emulated GEMM per i (m = natoms b, n = L b, k = b), the rows scattered back to the atoms
+  const size_t stack_bytes = align_up(sizeof(double2) * static_cast<size_t>(L) * rows * b, 1024);
+  EmuGemm g;
+  g.oa = {0, 0}; g.ob = {0, 0}; g.batch = L;
+  g.mmax = g.m = static_cast<int>(rows); g.nmax = g.n = static_cast<int>(n); g.kmax = g.k = b;
+  g.lda = static_cast<int>(rows); g.zsA = rows * b;
+  g.B = static_cast<const double2*>(G); g.ldb = static_cast<int>(n); g.zsB = b;
+  g.C = nullptr; g.ldc = static_cast<int>(n);
+  g.crow = reinterpret_cast<double2* const*>(M); g.crow_b = b;
+  g.mode = EPI_IMINUS; g.S = S;
+  g.sum_mnk = static_cast<double>(L) * rows * n * b;
+  g.sum_mk = static_cast<double>(L) * rows * b;
+  g.sum_nk = static_cast<double>(L) * n * b;
+  GemmPlan P;
+  ozk_status_t st = plan_gemm(g, &P);
+  if (st) return st;
+  st = ensure_ws(h, stack_bytes + P.total);
+  if (st) return st;
+  double2* stack = static_cast<double2*>(h->ws);
+  g.A = stack;
+  {
+    Prof pr(h, OZK_KIND_BUILD_M, 0.0, 32.0 * static_cast<double>(L) * rows * b);
+    launch_stack_t(reinterpret_cast<const double2* const*>(t), natoms, L, b, stack, h->stream);
+  }
+  st = cuda_check(cudaGetLastError(), "stack_t launch");
+  if (st) return st;
+  return run_emulated(h, g, stack_bytes);
+}
+
 ozk_status_t kkr_tau00_batched(ozk_handle_t h, int nsolves, const int* n, int b, void* const* M, const void* const* t0,
                                void* const* tau, int S, int nb) {
   if (!h || !n || !M || !t0 || !tau) return set_error(OZK_ERR_ARG, "null argument");
@@ -637,10 +896,9 @@ ozk_status_t kkr_tau00_batched(ozk_handle_t h, int nsolves, const int* n, int b,
   }
   const int panels = (nmax - b + nb - 1) / nb;
   const int leaves = nb / b;
-  // workspace layout: [n table][Dinv][step tables][GEMM workspace]
+  // workspace layout: [Dinv][step tables][GEMM workspace]; the n table is a size table
   const size_t ns = static_cast<size_t>(nsolves);
-  const size_t off_n = 0;
-  const size_t off_dinv = align_up(ns * sizeof(int), 1024);
+  const size_t off_dinv = 0;
   const size_t off_tab = align_up(off_dinv + ns * b * b * sizeof(double2), 1024);
   const size_t n_ptr = 10, n_int = 18;
   const size_t off_gemm = align_up(off_tab + ns * (n_ptr * sizeof(void*) + n_int * sizeof(int)), 1024);
@@ -651,11 +909,11 @@ ozk_status_t kkr_tau00_batched(ozk_handle_t h, int nsolves, const int* n, int b,
   if (st) return st;
   st = ensure_ws(h, off_gemm + P.total);
   if (st) return st;
-  uint8_t* ws = static_cast<uint8_t*>(h->ws);
-  int* dn = reinterpret_cast<int*>(ws + off_n);
-  double2* dinv = reinterpret_cast<double2*>(ws + off_dinv);
-  st = cuda_check(cudaMemcpyAsync(dn, n, ns * sizeof(int), cudaMemcpyHostToDevice, h->stream), "upload n");
+  const int* dn = nullptr;
+  st = size_table(h, std::vector<int>(n, n + nsolves), &dn);
   if (st) return st;
+  uint8_t* ws = static_cast<uint8_t*>(h->ws);
+  double2* dinv = reinterpret_cast<double2*>(ws + off_dinv);
   uint8_t* pp = ws + off_tab;                  // ns x n_ptr pointer slots
   int* pi = reinterpret_cast<int*>(ws + off_tab + ns * n_ptr * sizeof(void*));
   KkrStep t;
@@ -703,7 +961,10 @@ ozk_status_t kkr_tau00_batched(ozk_handle_t h, int nsolves, const int* n, int b,
         if (a > p) { a2max = std::max(a2max, a); s2 += (static_cast<double>(a) * a - static_cast<double>(p) * p) * b; }
       }
       if (nact == 0) continue;
-      launch_kkr_step(s, l, nsolves, dn, Mp, b, nb, dinv, t, h->stream);
+      {
+        Prof pr(h, OZK_KIND_OTHER, 0.0, 0.0);
+        launch_kkr_step(s, l, nsolves, dn, Mp, b, nb, dinv, t, h->stream);
+      }
       GjParams gj{};
       gj.D = t.D; gj.ldd = t.ldd; gj.nb = t.nbv; gj.R = nullptr; gj.X = t.X; gj.ldx = t.ldx; gj.nrhs = b;
       gj.status = h->d_status;
@@ -729,11 +990,17 @@ ozk_status_t kkr_tau00_batched(ozk_handle_t h, int nsolves, const int* n, int b,
       sa3 += static_cast<double>(p) * (q - p);
     }
     if (pmax == 0) continue;
-    launch_kkr_step(s, -1, nsolves, dn, Mp, b, nb, dinv, t, h->stream);
+    {
+      Prof pr(h, OZK_KIND_OTHER, 0.0, 0.0);
+      launch_kkr_step(s, -1, nsolves, dn, Mp, b, nb, dinv, t, h->stream);
+    }
     st = gemm_tables(2, pmax, pmax, nb, s3, sa3, sa3, true, false);
     if (st) return st;
   }
-  launch_kkr_step(-1, 0, nsolves, dn, Mp, b, nb, dinv, t, h->stream);
+  {
+    Prof pr(h, OZK_KIND_OTHER, 0.0, 0.0);
+    launch_kkr_step(-1, 0, nsolves, dn, Mp, b, nb, dinv, t, h->stream);
+  }
   GjParams gj{};
   gj.D = t.D; gj.ldd = t.ldd; gj.nb = t.nbv;
   gj.R = reinterpret_cast<const double2* const*>(t0); gj.ldr = t.nbv;
@@ -743,6 +1010,177 @@ ozk_status_t kkr_tau00_batched(ozk_handle_t h, int nsolves, const int* n, int b,
     launch_gj(gj, b, b, nsolves, h->stream);
   }
   return cuda_check(cudaGetLastError(), "kkr_tau00_batched launches");
+}
+
+// ---- slice-count selector
+ozk_status_t ozk_selector_init(ozk_handle_t h, uint64_t seed) {
+  if (!h) return set_error(OZK_ERR_ARG, "null handle");
+  // He-scaled normals (Box-Muller on a SplitMix64 stream), zero hidden biases, output biases
+  // at -8 (the middle of the log10 error range the outputs predict)
+  std::vector<float> p(SEL_NPARAMS, 0.0f);
+  const uint64_t base = sm_base_host(seed, 0x5E1ull);
+  auto mix = [](uint64_t z) {
+    z ^= z >> 30; z *= 0xBF58476D1CE4E5B9ull; z ^= z >> 27; z *= 0x94D049BB133111EBull; z ^= z >> 31;
+    return z;
+  };
+  uint64_t ctr = 0;
+  auto unif = [&]() { return static_cast<double>(mix(base + (++ctr) * 0x9E3779B97F4A7C15ull) >> 11) * 0x1.0p-53; };
+  auto normal = [&]() {
+    const double u1 = 1.0 - unif(), u2 = unif();
+    return std::sqrt(-2.0 * std::log(u1)) * std::cos(2.0 * 3.141592653589793 * u2);
+  };
+  const int W1 = 0, W2 = SEL_NH * SEL_NF + SEL_NH, W3 = W2 + SEL_NH * SEL_NH + SEL_NH, B3 = W3 + SEL_NO * SEL_NH;
+  for (int i = 0; i < SEL_NH * SEL_NF; ++i) p[W1 + i] = static_cast<float>(normal() * std::sqrt(2.0 / SEL_NF));
+  for (int i = 0; i < SEL_NH * SEL_NH; ++i) p[W2 + i] = static_cast<float>(normal() * std::sqrt(2.0 / SEL_NH));
+  for (int i = 0; i < SEL_NO * SEL_NH; ++i) p[W3 + i] = static_cast<float>(normal() * std::sqrt(1.0 / SEL_NH));
+  for (int o = 0; o < SEL_NO; ++o) p[B3 + o] = -8.0f;
+  return sel_upload(h, p.data());
+}
+
+ozk_status_t ozk_selector_set_params(ozk_handle_t h, const float* params) {
+  if (!h || !params) return set_error(OZK_ERR_ARG, "null argument");
+  for (int i = 0; i < SEL_NPARAMS; ++i)
+    if (!std::isfinite(params[i])) return set_error(OZK_ERR_ARG, "non-finite selector parameter");
+  return sel_upload(h, params);
+}
+
+ozk_status_t ozk_selector_get_params(ozk_handle_t h, float* params) {
+  if (!h || !params) return set_error(OZK_ERR_ARG, "null argument");
+  if (!h->sel_ready) return set_error(OZK_ERR_ARG, "selector has no parameters");
+  ozk_status_t st = cuda_check(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+  if (st) return st;
+  return cuda_check(cudaMemcpy(params, h->sel_p, sizeof(float) * SEL_NPARAMS, cudaMemcpyDeviceToHost), "read params");
+}
+
+static const char kSelMagic[8] = {'O', 'Z', 'K', 'S', 'E', 'L', '1', '\0'};
+
+ozk_status_t ozk_selector_load(ozk_handle_t h, const char* path) {
+  if (!h || !path) return set_error(OZK_ERR_ARG, "null argument");
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return set_error(OZK_ERR_NOFILE, "cannot open selector parameter file");
+  char magic[8];
+  int32_t np = 0;
+  std::vector<float> p(SEL_NPARAMS);
+  const bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kSelMagic, 8) == 0 &&
+                  std::fread(&np, sizeof(np), 1, f) == 1 && np == SEL_NPARAMS &&
+                  std::fread(p.data(), sizeof(float), SEL_NPARAMS, f) == static_cast<size_t>(SEL_NPARAMS);
+  std::fclose(f);
+  if (!ok) return set_error(OZK_ERR_ARG, "malformed selector parameter file");
+  return ozk_selector_set_params(h, p.data());
+}
+
+ozk_status_t ozk_selector_save(ozk_handle_t h, const char* path) {
+  if (!h || !path) return set_error(OZK_ERR_ARG, "null argument");
+  std::vector<float> p(SEL_NPARAMS);
+  ozk_status_t st = ozk_selector_get_params(h, p.data());
+  if (st) return st;
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return set_error(OZK_ERR_NOFILE, "cannot create selector parameter file");
+  const int32_t np = SEL_NPARAMS;
+  const bool ok = std::fwrite(kSelMagic, 1, 8, f) == 8 && std::fwrite(&np, sizeof(np), 1, f) == 1 &&
+                  std::fwrite(p.data(), sizeof(float), SEL_NPARAMS, f) == static_cast<size_t>(SEL_NPARAMS);
+  const bool closed = std::fclose(f) == 0;
+  return ok && closed ? OZK_OK : set_error(OZK_ERR_NOFILE, "cannot write selector parameter file");
+}
+
+ozk_status_t ozk_selector_configure(ozk_handle_t h, double tol, double margin, int flags) {
+  if (!h) return set_error(OZK_ERR_ARG, "null handle");
+  if (!(tol > 0.0) || !std::isfinite(tol) || !std::isfinite(margin) || (flags & ~OZK_SEL_NO_FALLBACK))
+    return set_error(OZK_ERR_ARG, "need tol > 0, finite margin, flags in {0, OZK_SEL_NO_FALLBACK}");
+  h->sel_tol = tol;
+  h->sel_margin = margin;
+  h->sel_flags = flags;
+  return OZK_OK;
+}
+
+ozk_status_t ozk_selector_features(ozk_handle_t h, char transa, char transb, int m, int n, int k, const void* A,
+                                   int lda, const void* B, int ldb, uint64_t probe_seed, float* features) {
+  if (!h || !A || !B || !features) return set_error(OZK_ERR_ARG, "null argument");
+  OpFlags oa, ob;
+  if (!parse_op(transa, &oa) || !parse_op(transb, &ob)) return set_error(OZK_ERR_ARG, "bad trans flag");
+  if (m < 1 || n < 1 || k < 1) return set_error(OZK_ERR_ARG, "features need m, n, k >= 1");
+  ozk_status_t st = check_dims(oa, ob, m, n, k, lda, ldb, m);
+  if (st) return st;
+  SelScratch s;
+  st = sel_scratch(h, m, n, k, false, &s);
+  if (st) return st;
+  st = sel_features(h, oa, ob, m, n, k, static_cast<const double2*>(A), lda, static_cast<const double2*>(B), ldb,
+                    probe_seed, s);
+  if (st) return st;
+  return cuda_check(cudaMemcpyAsync(features, s.f, sizeof(float) * SEL_NF, cudaMemcpyDeviceToDevice, h->stream),
+                    "copy features");
+}
+
+ozk_status_t ozk_selector_predict(ozk_handle_t h, int N, const float* X, float* Y) {
+  if (!h || (N > 0 && (!X || !Y))) return set_error(OZK_ERR_ARG, "null argument");
+  if (N < 0) return set_error(OZK_ERR_ARG, "negative N");
+  if (!h->sel_ready) return set_error(OZK_ERR_ARG, "selector has no parameters");
+  launch_mlp_forward(h->sel_p, X, N, nullptr, nullptr, Y, h->stream);
+  return cuda_check(cudaGetLastError(), "selector forward launch");
+}
+
+// training scratch for N samples: Z1, Z2, dZ2, dZ1 (N x 64), Y, dY (N x 8), loss
+struct SelTrain { float *Z1, *Z2, *dZ2, *dZ1, *Y, *dY; double* loss; };
+static ozk_status_t sel_train_scratch(ozk_context* h, int N, SelTrain* t) {
+  const size_t a = align_up(sizeof(float) * size_t(N) * SEL_NH, 256), b = align_up(sizeof(float) * size_t(N) * SEL_NO, 256);
+  ozk_status_t st = ensure_sel_ws(h, 4 * a + 2 * b + 256);
+  if (st) return st;
+  uint8_t* p = static_cast<uint8_t*>(h->sel_ws);
+  t->Z1 = reinterpret_cast<float*>(p); t->Z2 = reinterpret_cast<float*>(p + a);
+  t->dZ2 = reinterpret_cast<float*>(p + 2 * a); t->dZ1 = reinterpret_cast<float*>(p + 3 * a);
+  t->Y = reinterpret_cast<float*>(p + 4 * a); t->dY = reinterpret_cast<float*>(p + 4 * a + b);
+  t->loss = reinterpret_cast<double*>(p + 4 * a + 2 * b);
+  return OZK_OK;
+}
+
+ozk_status_t ozk_selector_train_step(ozk_handle_t h, int N, const float* X, const float* T, float lr, double* loss) {
+  if (!h || !X || !T) return set_error(OZK_ERR_ARG, "null argument");
+  if (N < 1 || !(lr > 0.0f)) return set_error(OZK_ERR_ARG, "need N >= 1 and lr > 0");
+  if (!h->sel_ready) return set_error(OZK_ERR_ARG, "selector has no parameters");
+  SelTrain t;
+  ozk_status_t st = sel_train_scratch(h, N, &t);
+  if (st) return st;
+  h->sel_t += 1;
+  float* P = h->sel_p;
+  launch_mlp_train(P, P + 3 * SEL_NPARAMS, P + SEL_NPARAMS, P + 2 * SEL_NPARAMS, h->sel_t, lr, X, T, N, t.Z1, t.Z2,
+                   t.Y, t.dY, t.dZ2, t.dZ1, t.loss, h->stream);
+  st = cuda_check(cudaGetLastError(), "selector training launches");
+  if (st || !loss) return st;
+  st = cuda_check(cudaMemcpyAsync(loss, t.loss, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "read loss");
+  if (st) return st;
+  return cuda_check(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+}
+
+ozk_status_t ozk_selector_gradient(ozk_handle_t h, int N, const float* X, const float* T, float* grad) {
+  if (!h || !X || !T || !grad) return set_error(OZK_ERR_ARG, "null argument");
+  if (N < 1) return set_error(OZK_ERR_ARG, "need N >= 1");
+  if (!h->sel_ready) return set_error(OZK_ERR_ARG, "selector has no parameters");
+  SelTrain t;
+  ozk_status_t st = sel_train_scratch(h, N, &t);
+  if (st) return st;
+  launch_mlp_grad_only(h->sel_p, grad, X, T, N, t.Z1, t.Z2, t.Y, t.dY, t.dZ2, t.dZ1, h->stream);
+  return cuda_check(cudaGetLastError(), "selector gradient launches");
+}
+
+ozk_status_t ozk_selector_last(ozk_handle_t h, ozk_selector_info* info) {
+  if (!h || !info) return set_error(OZK_ERR_ARG, "null argument");
+  *info = h->sel_last;
+  return OZK_OK;
+}
+
+ozk_status_t ozk_rel_diff(ozk_handle_t h, int m, int n, const void* X, int ldx, const void* Y, int ldy, double* rel) {
+  if (!h || !X || !Y || !rel) return set_error(OZK_ERR_ARG, "null argument");
+  if (m < 1 || n < 1 || ldx < m || ldy < m) return set_error(OZK_ERR_ARG, "need m, n >= 1 and ld >= m");
+  ozk_status_t st = ensure_sel_ws(h, align_up(sizeof(double) * 2 * size_t(n), 256) + 256);
+  if (st) return st;
+  double* part = static_cast<double*>(h->sel_ws);
+  double* out = reinterpret_cast<double*>(static_cast<uint8_t*>(h->sel_ws) + align_up(sizeof(double) * 2 * size_t(n), 256));
+  launch_rel_diff(m, n, static_cast<const double2*>(X), ldx, static_cast<const double2*>(Y), ldy, part, out, h->stream);
+  st = cuda_check(cudaGetLastError(), "rel diff launches");
+  if (st) return st;
+  st = cuda_check(cudaMemcpyAsync(rel, out, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "read rel diff");
+  if (st) return st;
+  return cuda_check(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
 }
 
 ozk_status_t ozk_profile_begin(ozk_handle_t h) {
@@ -785,10 +1223,8 @@ ozk_status_t kkr_build_m_batched(ozk_handle_t h, int batch, const int* L, int b,
     nmax = std::max(nmax, L[i] * b);
     nn2 += static_cast<double>(L[i]) * b * L[i] * b;
   }
-  ozk_status_t st = ensure_ws(h, align_up(sizeof(int) * batch, 256));
-  if (st) return st;
-  int* dL = static_cast<int*>(h->ws);
-  st = cuda_check(cudaMemcpyAsync(dL, L, sizeof(int) * batch, cudaMemcpyHostToDevice, h->stream), "upload L");
+  const int* dL = nullptr;
+  ozk_status_t st = size_table(h, std::vector<int>(L, L + batch), &dL);
   if (st) return st;
   {
     Prof pr(h, OZK_KIND_BUILD_M, 8.0 * nn2 * b, 32.0 * nn2);

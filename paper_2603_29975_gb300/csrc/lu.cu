@@ -269,6 +269,29 @@ void launch_build_m_batched(const int* L, int b, const double2* const* t, const 
   record_launch();
 }
 
+// Stacked left operands of the shared-G build: problem i is the (natoms b) x b column-major
+// matrix whose rows a b .. a b + b - 1 are t_a's block i (t_a: L column-major b x b blocks).
+__global__ void stack_t_kernel(const double2* const* t, int natoms, int L, int b, double2* out) {
+  const long long rows = static_cast<long long>(natoms) * b, per = rows * b;
+  const long long tot = per * L;
+  for (long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; idx < tot;
+       idx += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int i = static_cast<int>(idx / per);
+    const long long rem = idx - i * per;
+    const int c = static_cast<int>(rem / rows);
+    const int ar = static_cast<int>(rem - c * rows);
+    const int a = ar / b, r = ar - a * b;
+    out[idx] = t[a][static_cast<long long>(i) * b * b + r + static_cast<long long>(c) * b];
+  }
+}
+
+void launch_stack_t(const double2* const* t, int natoms, int L, int b, double2* out, cudaStream_t st) {
+  const long long tot = static_cast<long long>(natoms) * b * b * L;
+  const unsigned blocks = static_cast<unsigned>(std::min<long long>((tot + 255) / 256, 8192));
+  stack_t_kernel<<<blocks, 256, 0, st>>>(t, natoms, L, b, out);
+  record_launch();
+}
+
 __global__ void scale_kernel(int m, int n, double2* C, long long ldc, double br, double bi) {
   const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (idx >= static_cast<long long>(m) * n) return;

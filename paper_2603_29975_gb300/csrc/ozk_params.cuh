@@ -23,14 +23,17 @@ struct SplitParams {
   long long exp_stride;
   int16_t* dbg_digits;      // optional int16 copy [S][out_rows][2k] for problem 0 (test hook)
   int* status;
-  // single-problem values, used when X == nullptr (no device tables needed)
+  // single-problem values, used when X == nullptr (no device tables needed); problem z of a
+  // uniform batch starts at X1 + z * zstride1
   const double2* X1; int ld1, rows1, k1;
+  long long zstride1;
 };
 void launch_split(const SplitParams& p, int max_rows, int batch, cudaStream_t st);
 
 // ---- slice_gemm.cu: tcgen05 slice-pair GEMM + exact reconstruction
 constexpr int MAX_PAIRS = 136;
-enum EpiMode : int { EPI_STORE = 0, EPI_LU = 1, EPI_GENERAL = 2, EPI_GROUPS = 3 };
+// EPI_IMINUS: C = I - RN(Z) without reading C (diagonal where the output row equals the column)
+enum EpiMode : int { EPI_STORE = 0, EPI_LU = 1, EPI_GENERAL = 2, EPI_GROUPS = 3, EPI_IMINUS = 4 };
 struct GemmParams {
   int S;
   int npairs;
@@ -58,6 +61,9 @@ struct GemmParams {
   int* status;
   // single-problem values, used when m == nullptr (no device tables needed)
   int m1, n1; double2* C1; int ldc1;
+  // row-block scatter (crow != nullptr): row r of problem z is row z crow_b + r % crow_b of
+  // the output crow[r / crow_b] (leading dimension ldc1)
+  double2* const* crow; int crow_b;
   uint8_t ps[MAX_PAIRS], pt[MAX_PAIRS], pg[MAX_PAIRS], pfirst[MAX_PAIRS];
 };
 void launch_slice_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const GemmParams& p, int BN,
@@ -94,6 +100,7 @@ void launch_build_m(int n, int b, const double2* t, const double2* G, double2* M
 void launch_build_m_batched(const int* L, int b, const double2* const* t, const double2* const* G, double2* const* M,
                             int nmax, int batch, cudaStream_t st);
 void launch_scale(int m, int n, double2* C, long long ldc, double br, double bi, cudaStream_t st);
+void launch_stack_t(const double2* const* t, int natoms, int L, int b, double2* out, cudaStream_t st);
 
 // Per-step tables of the batched tau_00 driver, filled on the device for step `step`.
 struct KkrStep {
@@ -109,5 +116,37 @@ struct KkrStep {
 // S_00^-1 t_0 solve.
 void launch_kkr_step(int step, int leaf, int nsolves, const int* n, double2* const* M, int b, int nb, double2* dinv,
                      const KkrStep& t, cudaStream_t st);
+
+// ---- selector.cu: slice-count selector (features, probes, residual check, perceptron)
+constexpr int SEL_NF = OZK_SEL_FEATURES, SEL_NH = 64, SEL_NO = OZK_SEL_OUTPUTS;
+constexpr int SEL_SMIN = OZK_SEL_SMIN, SEL_SMAX = OZK_SEL_SMAX, SEL_PROBES = 2;
+constexpr int SEL_NPARAMS = OZK_SEL_NPARAMS;
+static_assert(SEL_NPARAMS == SEL_NH * SEL_NF + SEL_NH + SEL_NH * SEL_NH + SEL_NH + SEL_NO * SEL_NH + SEL_NO,
+              "selector parameter count");
+struct SelVecStats { double* r; int* e; double* sh; int* z; };   // per-vector arrays
+struct SelBases { uint64_t b[2 * SEL_PROBES]; };                 // SplitMix64 stream bases
+struct SelAux { int S; int E; double z2; double resid; double diff; float pred[SEL_NO]; };
+uint64_t sm_base_host(uint64_t seed, uint64_t stream);
+void launch_probe(double2* X, int n, const SelBases& b, cudaStream_t st);
+void launch_vec_stats(const double2* M, long long ld, int count, int len, bool contiguous, const SelVecStats& out,
+                      cudaStream_t st);
+void launch_max_exp(const SelVecStats& a, int ma, const SelVecStats& b, int nb, int* ex, cudaStream_t st);
+// op: 0 = rows of M (strided), 1 = columns of M, 2 = conjugated columns of M
+void launch_gemv(const double2* M, long long ld, int rows, int len, int op, const double2* X, int ldx, double2* Y,
+                 int ldy, const int* ex, int eidx, cudaStream_t st);
+void launch_selector_features(const SelVecStats& a, int m, const SelVecStats& b, int n, int k, const double2* X,
+                              const double2* zs, const int* ex, float* f, SelAux* aux, cudaStream_t st);
+void launch_residual(const double2* W, const double2* zs, int m, SelAux* aux, cudaStream_t st);
+void launch_rel_diff(int m, int n, const double2* X, long long ldx, const double2* Y, long long ldy, double* part,
+                     double* out, cudaStream_t st);
+void launch_axpby(int m, int n, const double2* D, long long ldd, double2* C, long long ldc, double ar, double ai,
+                  double br, double bi, cudaStream_t st);
+void launch_mlp_forward(const float* P, const float* X, int N, float* Z1, float* Z2, float* Y, cudaStream_t st);
+void launch_mlp_train(float* P, float* gbuf, float* m, float* v, int t, float lr, const float* X, const float* T,
+                      int N, float* Z1, float* Z2, float* Y, float* dY, float* dZ2, float* dZ1, double* loss,
+                      cudaStream_t st);
+void launch_mlp_grad_only(const float* P, float* gbuf, const float* X, const float* T, int N, float* Z1, float* Z2,
+                          float* Y, float* dY, float* dZ2, float* dZ1, cudaStream_t st);
+void launch_choose(const float* Y, float lim, SelAux* aux, cudaStream_t st);
 
 }  // namespace ozk

@@ -204,11 +204,27 @@ __device__ __forceinline__ bool issue_dispatch(int S, bool fullset, bool firstkb
 
 struct EpiCtx {
   int row, z, m_z, n2_z, n0, c0, skip_n, er;
+  int grow;              // row of the output matrix (the diagonal test of EPI_IMINUS)
   uint32_t tbase;
-  double2* Cz;
-  long long ldc;
+  double2* Cz;           // output row r is Cz[crow + column * ldc]
+  long long crow, ldc;
   bool rowok;
 };
+
+// output matrix, row offset and matrix row of tile row `row` of problem z
+__device__ __forceinline__ void out_row(const GemmParams& p, bool single, int z, int row, bool rowok, double2*& Cz,
+                                        long long& crow, int& grow) {
+  if (p.crow) {
+    const int a = row / p.crow_b, rl = row - a * p.crow_b;
+    Cz = rowok ? p.crow[a] : nullptr;
+    crow = static_cast<long long>(z) * p.crow_b + rl;
+    grow = static_cast<int>(crow);
+  } else {
+    Cz = single ? p.C1 : p.C[z];
+    crow = row;
+    grow = row;
+  }
+}
 
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
@@ -253,7 +269,7 @@ __device__ __forceinline__ void epilogue_fast(const GemmParams& p, const EpiCtx&
     const int jc = jc0 + jj;
     const bool in = 2 * jc < x.n2_z;
     f = in ? p.f[x.z * p.f_stride + jc] : 0;
-    c = (in && p.mode != EPI_STORE) ? x.Cz[x.row + jc * x.ldc] : make_double2(0.0, 0.0);
+    c = (in && (p.mode == EPI_LU || p.mode == EPI_GENERAL)) ? x.Cz[x.crow + jc * x.ldc] : make_double2(0.0, 0.0);
   };
   load_col(0, cv, fe);
 #pragma unroll
@@ -274,12 +290,14 @@ __device__ __forceinline__ void epilogue_fast(const GemmParams& p, const EpiCtx&
         hi += (Lh >> 63) + (lo2 < lo ? 1 : 0);
         zz[h] = round_hl(hi, lo2, E);
       }
-      double2* dst = x.Cz + x.row + jc * x.ldc;
+      double2* dst = x.Cz + x.crow + jc * x.ldc;
       if (p.mode == EPI_STORE) {
         if (p.ar == 1.0 && p.ai == 0.0) *dst = make_double2(zz[0], zz[1]);
         else *dst = make_double2(p.ar * zz[0] - p.ai * zz[1], p.ar * zz[1] + p.ai * zz[0]);
       } else if (p.mode == EPI_LU) {
         *dst = make_double2(cv.x - zz[0], cv.y - zz[1]);
+      } else if (p.mode == EPI_IMINUS) {
+        *dst = make_double2((jc == x.grow ? 1.0 : 0.0) - zz[0], 0.0 - zz[1]);
       } else {
         const double xr = p.ar * zz[0] - p.ai * zz[1], xi = p.ar * zz[1] + p.ai * zz[0];
         const double yr = p.br * cv.x - p.bi * cv.y, yi = p.br * cv.y + p.bi * cv.x;
@@ -447,7 +465,7 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
           x.row = row; x.z = z; x.m_z = m_z; x.n2_z = n2_z; x.n0 = n0; x.c0 = c0; x.tbase = tbase;
           x.rowok = rowok;
           x.skip_n = (row < (single ? p.skm1 : (p.skm ? p.skm[z] : 0))) ? (single ? p.skn1 : p.skn[z]) : 0;
-          x.Cz = single ? p.C1 : p.C[z];
+          out_row(p, single, z, row, rowok, x.Cz, x.crow, x.grow);
           x.ldc = single ? p.ldc1 : p.ldc[z];
           x.er = rowok ? p.e[z * p.e_stride + row] + p.base_exp : 0;
           if (!mbar_wait(acc_full, cc & 1, p.status, abort_flag)) { ok = false; break; }
@@ -506,7 +524,10 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       if (p.mode != EPI_GROUPS && rowok) {
         const int er = p.e[z * p.e_stride + row] + p.base_exp;
         const int skip_n = (row < (single ? p.skm1 : (p.skm ? p.skm[z] : 0))) ? (single ? p.skn1 : p.skn[z]) : 0;
-        double2* Cz = single ? p.C1 : p.C[z];
+        double2* Cz;
+        long long crow;
+        int grow;
+        out_row(p, single, z, row, rowok, Cz, crow, grow);
         const long long ldc = single ? p.ldc1 : p.ldc[z];
 #pragma unroll
         for (int j = 0; j < COLS; j += 2) {
@@ -515,10 +536,12 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
             const int E = er + p.f[z * p.f_stride + jc];
             const double zr = round_scaled_dev(T[j], E);
             const double zi = round_scaled_dev(T[j + 1], E);
-            double2* dst = Cz + row + jc * ldc;
+            double2* dst = Cz + crow + jc * ldc;
             if (p.mode == EPI_STORE) {
               if (p.ar == 1.0 && p.ai == 0.0) *dst = make_double2(zr, zi);
               else *dst = make_double2(p.ar * zr - p.ai * zi, p.ar * zi + p.ai * zr);
+            } else if (p.mode == EPI_IMINUS) {
+              *dst = make_double2((jc == grow ? 1.0 : 0.0) - zr, 0.0 - zi);
             } else if (p.mode == EPI_LU) {
               const double2 cv = *dst;
               *dst = make_double2(cv.x - zr, cv.y - zi);

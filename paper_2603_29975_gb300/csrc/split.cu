@@ -59,7 +59,7 @@ split_kernel(const SplitParams p) {
   const int K = single ? p.k1 : p.kdim[z];
   const int r0 = blockIdx.x * SPLIT_ROWS;
   if (r0 >= R) return;
-  const double2* __restrict__ P = single ? p.X1 : p.X[z];
+  const double2* __restrict__ P = single ? p.X1 + z * p.zstride1 : p.X[z];
   const long long ld = single ? p.ld1 : p.ld[z];
   const int tid = threadIdx.x;
 

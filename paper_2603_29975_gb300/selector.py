@@ -1,0 +1,255 @@
+"""Training and evaluation of the slice-count selector on the GPU.
+
+This module only generates seeded synthetic GEMM instances and marshals arguments: the
+features, the emulated products at every S, the reference products, the error measurements,
+the perceptron's forward pass and its Adam steps all run in libozk's CUDA kernels.
+
+Instance families (all seeded; numpy generates the operands on the host):
+  * ``dense``   : entries U(-1, 1) 2^round(N(0, sigma)), sigma in {0, 0.5, 1, 2, 3, 4, 6};
+  * ``scaled``  : dense entries with row scales of op(A) and column scales of op(B)
+                  2^round(N(0, s)), s in {2, 8, 20} (exponent spread across rows / columns);
+  * ``cancel``  : op(B) = N R + delta R2 with N a basis of op(A)'s null space, so that
+                  ||AB|| / (||A|| ||B||) ~ delta, delta = 10^-U(0, 8);
+  * ``kkr``     : the operands of block-LU updates of KKR matrices M = I - t G (bcc LIZ of
+                  15..65 sites, contour energies): L columns M[0:p, p:q] times U rows
+                  M[p:q, 0:p], and L columns times a 16 x 16 pivot inverse.
+Labels: log10 of the relative Frobenius error of the S-slice product (S = 3..10, triangular
+pairs) against the S = 12 product (95 bits per operand, so its own error stays below 1e-20
+for these instances before its final rounding to binary64), floored at 1e-17.
+
+Usage (GPU):  python -m paper_2603_29975_gb300.selector --out selector_weights.bin
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+import time
+
+import numpy as np
+
+SMIN, SMAX = 3, 10
+SREF = 12
+FLOOR = -17.0
+KINDS = ("dense", "scaled", "cancel", "kkr")
+
+
+def _loguniform_int(rng, lo, hi):
+    return int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+
+
+def _dense(rng, m, n, sigma):
+    e = np.rint(rng.normal(0, sigma, (m, n))) if sigma > 0 else np.zeros((m, n))
+    re = rng.uniform(-1, 1, (m, n)) * np.exp2(e)
+    e2 = np.rint(rng.normal(0, sigma, (m, n))) if sigma > 0 else np.zeros((m, n))
+    im = rng.uniform(-1, 1, (m, n)) * np.exp2(e2)
+    return re + 1j * im
+
+
+class _KkrPool:
+    """A few KKR matrices M = I - t G (bcc LIZ, contour energies) to draw update operands from."""
+
+    def __init__(self, seed, sizes=(15, 27, 51, 65), energies=4):
+        import synth
+        E, _ = synth.contour(32)
+        pick = np.linspace(0, 31, energies).astype(int)
+        self.systems = []
+        for i, L in enumerate(sizes):
+            for j in pick:
+                t, G, _ = synth.kkr_system(L, 16, complex(E[j]), seed=seed + 7 * i, atom=int(j))
+                self.systems.append((i, synth.kkr_matrix(t, G)))
+
+    def draw(self, rng):
+        sid = int(rng.integers(len(self.systems)))
+        group, M = self.systems[sid]
+        n = M.shape[0]
+        if rng.uniform() < 0.7:
+            w = int(rng.choice([16, 32, 64]))
+            q = int(rng.integers(16 + w, n + 1)) // 16 * 16
+            p = max(16, q - w)
+            return group, M[:p, p:q], M[p:q, :p]
+        a = int(rng.integers(2, n // 16)) * 16
+        D = np.linalg.inv(M[a:a + 16, a:a + 16])
+        return group, M[:a, a:a + 16], D
+
+
+def generate_instances(count, seed):
+    """(group, kind, A, B) with A = op(A), B = op(B) as numpy complex matrices.  `group`
+    identifies the KKR system (instances of one system stay on one side of a split)."""
+    rng = np.random.default_rng(seed)
+    pool = _KkrPool(seed)
+    out = []
+    for i in range(count):
+        kind = KINDS[i % len(KINDS)]
+        if kind == "kkr":
+            g, A, B = pool.draw(rng)
+            out.append((1000 + g, kind, A, B))
+            continue
+        m, n, k = _loguniform_int(rng, 16, 400), _loguniform_int(rng, 16, 400), _loguniform_int(rng, 16, 800)
+        if kind == "dense":
+            sigma = float(rng.choice([0, 0.5, 1, 2, 3, 4, 6]))
+            A, B = _dense(rng, m, k, sigma), _dense(rng, k, n, sigma)
+        elif kind == "scaled":
+            s = float(rng.choice([2, 8, 20]))
+            A = _dense(rng, m, k, 1.0) * np.exp2(np.rint(rng.normal(0, s, (m, 1))))
+            B = _dense(rng, k, n, 1.0) * np.exp2(np.rint(rng.normal(0, s, (1, n))))
+        else:
+            m = min(m, 300)
+            k = min(max(k, m + 8), 400)
+            A = _dense(rng, m, k, 1.0)
+            _, _, vh = np.linalg.svd(A)
+            N = vh[m:].conj().T                                      # k x (k - m), A N = 0
+            delta = 10.0 ** -rng.uniform(0, 8)
+            B = N @ _dense(rng, k - m, n, 0.0) + delta * _dense(rng, k, n, 0.0)
+        out.append((i, kind, A, B))
+    return out
+
+
+def label(ozk, h, instances, with_times=True):
+    """Features (N x 16), target log10 errors (N x 8) and per-S times in ms (N x 8)."""
+    import torch
+    N = len(instances)
+    X = np.zeros((N, 16), dtype=np.float32)
+    T = np.zeros((N, 8), dtype=np.float32)
+    times = np.zeros((N, 8))
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for i, (_, _, A, B) in enumerate(instances):
+        Ad, Bd = ozk.colmajor_cuda(A), ozk.colmajor_cuda(B)
+        m, n = A.shape[0], B.shape[1]
+        X[i] = ozk.to_numpy(ozk.selector_features(h, Ad, Bd, seed=i))
+        ref = torch.empty((n, m), dtype=torch.complex128, device="cuda").t()
+        ozk.ozaki_zgemm(h, Ad, Bd, ref, S=SREF)
+        C = torch.empty((n, m), dtype=torch.complex128, device="cuda").t()
+        for o, S in enumerate(range(SMIN, SMAX + 1)):
+            if with_times:
+                ozk.ozaki_zgemm(h, Ad, Bd, C, S=S)                    # warm (workspace, caches)
+                ev[0].record()
+            ozk.ozaki_zgemm(h, Ad, Bd, C, S=S)
+            if with_times:
+                ev[1].record()
+            err = ozk.rel_diff(h, C, ref)
+            if with_times:
+                times[i, o] = ev[0].elapsed_time(ev[1])
+            T[i, o] = max(math.log10(err), FLOOR) if err > 0 else FLOOR
+    if h.status():
+        raise RuntimeError("device status set while labelling")
+    return X, T, times
+
+
+def split(instances, frac=0.8, seed=0):
+    """Train / test indices, split by group (a KKR system, or a single random instance)."""
+    groups = sorted({g for g, *_ in instances})
+    rng = np.random.default_rng(seed)
+    rng.shuffle(groups)
+    cut = set(groups[:int(round(frac * len(groups)))])
+    tr = [i for i, (g, *_) in enumerate(instances) if g in cut]
+    te = [i for i, (g, *_) in enumerate(instances) if g not in cut]
+    return tr, te
+
+
+def train(ozk, h, X, T, steps=3000, lr=2e-3, seed=1, log_every=500):
+    import torch
+    h.selector_init(seed)
+    Xd = torch.from_numpy(X).cuda()
+    Td = torch.from_numpy(T).cuda()
+    hist = []
+    for s in range(1, steps + 1):
+        rate = lr * (0.5 * (1 + math.cos(math.pi * (s - 1) / steps)) * 0.9 + 0.1)     # cosine decay
+        loss = ozk.selector_train_step(h, Xd, Td, rate, want_loss=(s % log_every == 0 or s == 1))
+        if loss is not None:
+            hist.append((s, loss))
+    return hist
+
+
+def choose(pred, tol, margin):
+    lim = math.log10(tol) - margin
+    for o in range(8):
+        if pred[o] <= lim:
+            return SMIN + o
+    return SMAX
+
+
+def evaluate(ozk, h, instances, X, T, times, tol=1e-10, margin=0.3, run_auto=True):
+    """Selector quality on labelled instances: chosen S, violations before the residual check
+    (label of the chosen S above tol) and after it (the S = 0 call's product against the
+    reference), and time against fixed S."""
+    import torch
+    Y = ozk.to_numpy(ozk.selector_predict(h, torch.from_numpy(X).cuda()))
+    lim = math.log10(tol)
+    chosen = np.array([choose(y, tol, margin) for y in Y])
+    viol_before = int(np.sum(T[np.arange(len(T)), chosen - SMIN] > lim))
+    ok_fixed = [S for S in range(SMIN, SMAX + 1) if np.all(T[:, S - SMIN] <= lim)]
+    best_fixed = min(ok_fixed) if ok_fixed else None
+    out = {"instances": len(T), "tol": tol, "margin": margin, "mean_S_selected": float(chosen.mean()),
+           "violations_before_check": viol_before, "best_fixed_S_meeting_tol": best_fixed,
+           "mse_log10": float(np.mean((Y - T) ** 2)), "S_hist": {int(S): int(np.sum(chosen == S))
+                                                                 for S in range(SMIN, SMAX + 1)}}
+    if run_auto:
+        h.selector_configure(tol=tol, margin=margin)
+        viol_after, fallbacks, used, t_auto = 0, 0, [], 0.0
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        for i, (_, _, A, B) in enumerate(instances):
+            Ad, Bd = ozk.colmajor_cuda(A), ozk.colmajor_cuda(B)
+            m, n = A.shape[0], B.shape[1]
+            ref = torch.empty((n, m), dtype=torch.complex128, device="cuda").t()
+            ozk.ozaki_zgemm(h, Ad, Bd, ref, S=SREF)
+            C = torch.empty((n, m), dtype=torch.complex128, device="cuda").t()
+            ozk.ozaki_zgemm(h, Ad, Bd, C, S=0)                       # warm
+            t0 = time.perf_counter()
+            ev[0].record()
+            ozk.ozaki_zgemm(h, Ad, Bd, C, S=0)
+            ev[1].record()
+            torch.cuda.synchronize()
+            t_auto += ev[0].elapsed_time(ev[1])
+            info = h.selector_last()
+            used.append(info["S_used"])
+            fallbacks += int(info["fallback"])
+            viol_after += int(ozk.rel_diff(h, C, ref) > tol)
+        out.update({"violations_after_check": viol_after, "fallbacks": fallbacks,
+                    "mean_S_used": float(np.mean(used)), "auto_ms_total": t_auto,
+                    "fixed_S10_ms_total": float(times[:, SMAX - SMIN].sum())})
+        if best_fixed is not None:
+            out["fixed_best_ms_total"] = float(times[:, best_fixed - SMIN].sum())
+        out["chosen_S_ms_total"] = float(times[np.arange(len(T)), chosen - SMIN].sum())
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--count", type=int, default=2400)
+    ap.add_argument("--seed", type=int, default=20260401)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--out", default=None)
+    ap.add_argument("--report", default=None)
+    args = ap.parse_args(argv)
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import paper_2603_29975_gb300 as ozk
+    from paper_2603_29975_gb300 import build
+    build.build()
+    h = ozk.Handle()
+    t0 = time.time()
+    inst = generate_instances(args.count, args.seed)
+    t1 = time.time()
+    X, T, times = label(ozk, h, inst)
+    t2 = time.time()
+    tr, te = split(inst, seed=args.seed)
+    hist = train(ozk, h, X[tr], T[tr], steps=args.steps, lr=args.lr, seed=args.seed)
+    t3 = time.time()
+    rep = {"generate_s": t1 - t0, "label_s": t2 - t1, "train_s": t3 - t2, "train_loss": hist,
+           "train": evaluate(ozk, h, [inst[i] for i in tr], X[tr], T[tr], times[tr], tol=args.tol, run_auto=False),
+           "test": evaluate(ozk, h, [inst[i] for i in te], X[te], T[te], times[te], tol=args.tol)}
+    if args.out:
+        h.selector_save(args.out)
+    text = json.dumps(rep, indent=1)
+    if args.report:
+        with open(args.report, "w") as f:
+            f.write(text)
+    print(text)
+
+
+if __name__ == "__main__":
+    main()

@@ -98,3 +98,28 @@ def test_singular_pivot_sets_status(ozk_mod, handle):
     tau = ozk_mod.colmajor_cuda(np.zeros((16, 16), dtype=np.complex128))
     ozk_mod.kkr_tau00(handle, ozk_mod.colmajor_cuda(M), ozk_mod.colmajor_cuda(t0), tau, S=5, nb=64)
     assert handle.status() & (1 << 3)
+
+
+@pytest.mark.parametrize("S", [5, 7])
+def test_build_m_shared_is_the_emulated_block_row_update(ozk_mod, handle, S):
+    """Atoms sharing G: block row i of M_a is (rows ib..ib+b-1 of I) - RN(t_{a,i} G_i) with the
+    emulated product, bit for bit, and close to the binary64 M = I - t G."""
+    import torch
+    L, b, natoms = 9, 16, 5
+    n = L * b
+    _, G, _ = synth.kkr_system(L, b, 0.3 + 0.2j, atom=0)
+    ts = [synth.kkr_t(L, b, atom=a) for a in range(natoms)]
+    tdev = [_tblocks(ozk_mod, t) for t in ts]
+    Ms = [ozk_mod.colmajor_cuda(np.zeros((n, n), dtype=np.complex128)) for _ in range(natoms)]
+    ptr = lambda xs: torch.tensor([x.data_ptr() for x in xs], dtype=torch.int64, device="cuda")
+    ozk_mod.kkr_build_m_shared_ptrs(handle, natoms, L, b, ptr(tdev), ozk_mod.colmajor_cuda(G), ptr(Ms), S=S)
+    assert handle.status() == 0
+    eye = np.eye(n, dtype=np.complex128)
+    for a in range(natoms):
+        got = ozk_mod.to_numpy(Ms[a])
+        for i in range(L):
+            rows = slice(i * b, (i + 1) * b)
+            want = co.zgemm_lu(eye[rows], ts[a][i], G[rows], S)
+            assert np.array_equal(got[rows], want)
+        err = np.abs(got - kkr.kkr_build(ts[a], G)).max()
+        assert err <= (1e-14 if S == 7 else 1e-9)

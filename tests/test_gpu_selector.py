@@ -1,0 +1,222 @@
+"""GPU parity of the slice-count selector (features, perceptron forward / gradient / Adam, probe
+residual check, fallback) against the float64 oracle, through the C ABI."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import op, rand_complex, stored
+from oracle import c_oracle as co
+from oracle import selector as sel
+
+pytestmark = pytest.mark.gpu
+
+
+def _cuda(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+CASES = [
+    ((37, 29, 41), "N", "N", 2.0, 0),
+    ((64, 130, 17), "T", "N", 6.0, 1),
+    ((90, 33, 120), "N", "C", 0.0, 2),
+    ((5, 7, 300), "C", "T", 2.0, 3),
+]
+
+
+@pytest.mark.parametrize("mnk,ta,tb,sigma,seed", CASES)
+def test_features_match_oracle(ozk_mod, handle, mnk, ta, tb, sigma, seed):
+    m, n, k = mnk
+    A = rand_complex(m, k, 100 + seed, sigma)
+    B = rand_complex(k, n, 200 + seed, sigma)
+    A[3 % m, :] = 0                       # a zero row of op(A)
+    B[:, 1 % n] = 0                       # a zero column of op(B)
+    A[0, :k // 2] = 0
+    As, Bs = stored(A, ta), stored(B, tb)
+    f = ozk_mod.to_numpy(ozk_mod.selector_features(handle, ozk_mod.colmajor_cuda(As), ozk_mod.colmajor_cuda(Bs),
+                                                   ta, tb, seed=77 + seed))
+    want, _, _ = sel.features(A, B, sel.probe_vectors(n, 77 + seed))
+    assert np.abs(f - want).max() <= 2e-6 * max(1.0, np.abs(want).max())
+
+
+def test_features_of_extreme_scales_and_zero_operand(ozk_mod, handle):
+    A = rand_complex(40, 30, 5, 1.0) * 2.0 ** 900
+    B = rand_complex(30, 20, 6, 1.0) * 2.0 ** -1000
+    f = ozk_mod.to_numpy(ozk_mod.selector_features(handle, ozk_mod.colmajor_cuda(A), ozk_mod.colmajor_cuda(B), seed=9))
+    want, _, _ = sel.features(A, B, sel.probe_vectors(20, 9))
+    assert np.all(np.isfinite(f)) and np.abs(f - want).max() <= 2e-6
+    Z = np.zeros((30, 20), dtype=np.complex128)
+    f0 = ozk_mod.to_numpy(ozk_mod.selector_features(handle, ozk_mod.colmajor_cuda(A), ozk_mod.colmajor_cuda(Z), seed=9))
+    want0, _, _ = sel.features(A, Z, sel.probe_vectors(20, 9))
+    assert np.array_equal(f0, want0.astype(np.float32))
+
+
+def _random_params(seed):
+    rng = np.random.default_rng(seed)
+    W1 = rng.normal(0, math.sqrt(2 / 16), (64, 16))
+    W2 = rng.normal(0, math.sqrt(2 / 64), (64, 64))
+    W3 = rng.normal(0, math.sqrt(1 / 64), (8, 64))
+    return sel.pack(W1, rng.normal(0, 0.1, 64), W2, rng.normal(0, 0.1, 64), W3, rng.normal(-8, 1, 8)).astype(np.float32)
+
+
+def test_forward_matches_oracle(ozk_mod, handle):
+    p = _random_params(1)
+    handle.selector_set_params(p)
+    X = np.random.default_rng(2).normal(0, 1, (1000, 16)).astype(np.float32)
+    Y = ozk_mod.to_numpy(ozk_mod.selector_predict(handle, _cuda(X)))
+    want, _, _ = sel.forward(p.astype(np.float64), X.astype(np.float64))
+    assert np.abs(Y - want).max() <= 1e-4 * max(1.0, np.abs(want).max())
+    assert np.array_equal(handle.selector_get_params(), p)
+
+
+def test_gradient_and_adam_step_match_oracle(ozk_mod, handle):
+    p = _random_params(3)
+    handle.selector_set_params(p)
+    rng = np.random.default_rng(4)
+    X = rng.normal(0, 1, (300, 16)).astype(np.float32)
+    T = rng.normal(-8, 3, (300, 8)).astype(np.float32)
+    p64, X64, T64 = p.astype(np.float64), X.astype(np.float64), T.astype(np.float64)
+    g = ozk_mod.to_numpy(ozk_mod.selector_gradient(handle, _cuda(X), _cuda(T)))
+    want = sel.backward(p64, X64, T64)
+    assert np.abs(g - want).max() <= 1e-4 * np.abs(want).max()
+    lr = 1e-3
+    loss = ozk_mod.selector_train_step(handle, _cuda(X), _cuda(T), lr)
+    assert loss == pytest.approx(sel.loss(p64, X64, T64), rel=1e-5)
+    p1 = handle.selector_get_params().astype(np.float64)
+    w1, _, _ = sel.adam_step(p64, want, np.zeros_like(p64), np.zeros_like(p64), 1, lr)
+    # first Adam step: lr * g / (|g| + eps); entries whose gradient is far above eps agree
+    big = np.abs(want) > 1e-5
+    assert np.abs(p1 - w1)[big].max() <= 1e-3 * lr
+    assert np.abs(p1 - p64).max() <= lr * (1 + 1e-3)
+
+
+def test_training_on_the_gpu_tracks_the_oracle(ozk_mod, handle):
+    rng = np.random.default_rng(5)
+    X = rng.uniform(-1, 1, (512, 16)).astype(np.float32)
+    A = rng.normal(size=(8, 16))
+    T = (X.astype(np.float64) @ A.T - 8.0).astype(np.float32)
+    p = _random_params(6)
+    handle.selector_set_params(p)
+    p64 = p.astype(np.float64)
+    m, v = np.zeros_like(p64), np.zeros_like(p64)
+    Xd, Td = _cuda(X), _cuda(T)
+    for t in range(1, 201):
+        ozk_mod.selector_train_step(handle, Xd, Td, 3e-3, want_loss=False)
+        p64, m, v = sel.adam_step(p64, sel.backward(p64, X.astype(np.float64), T.astype(np.float64)), m, v, t, 3e-3)
+    l_gpu = sel.loss(handle.selector_get_params().astype(np.float64), X, T)
+    l_cpu = sel.loss(p64, X, T)
+    l0 = sel.loss(p.astype(np.float64), X, T)
+    assert l_gpu < l0 / 10 and l_cpu < l0 / 10
+    assert l_gpu <= 1.5 * l_cpu + 1e-6                 # float32 and float64 trajectories stay close
+
+
+def _const_params(pred_log10):
+    """Parameters whose every output is the constant pred_log10 (zero weights)."""
+    p = np.zeros(sel.NPARAMS, dtype=np.float32)
+    p[sel.OFF_B3:] = pred_log10
+    return p
+
+
+def test_selected_S_passes_the_residual_check(ozk_mod, handle):
+    import torch
+    A, B = rand_complex(200, 150, 11, 1.0), rand_complex(150, 120, 12, 1.0)
+    Ad, Bd = ozk_mod.colmajor_cuda(A), ozk_mod.colmajor_cuda(B)
+    p = np.zeros(sel.NPARAMS, dtype=np.float32)
+    p[sel.OFF_B3:] = [-3, -5, -8, -11, -14, -16, -16, -16]        # S = 6 meets 1e-10 with margin 0.3
+    handle.selector_set_params(p)
+    handle.selector_configure(tol=1e-10, margin=0.3)
+    C = ozk_mod.colmajor_cuda(np.zeros((200, 120), dtype=np.complex128))
+    ozk_mod.ozaki_zgemm(handle, Ad, Bd, C, S=0)
+    info = handle.selector_last()
+    assert info["S_selected"] == 6 and info["S_used"] == 6 and not info["fallback"] and info["residual_ok"]
+    # the returned product is the S = 6 emulated product, bit for bit
+    C6 = ozk_mod.colmajor_cuda(np.zeros((200, 120), dtype=np.complex128))
+    ozk_mod.ozaki_zgemm(handle, Ad, Bd, C6, S=6)
+    got = ozk_mod.to_numpy(C)
+    assert np.array_equal(got, ozk_mod.to_numpy(C6))
+    # the device residual estimate is the oracle's for that product and those probes
+    X = sel.probe_vectors(120, info["probe_seed"])
+    _, zs, E = sel.features(A, B, X)
+    r = sel.residual_estimate(got, X, zs, E)
+    assert info["residual"] == pytest.approx(r, rel=1e-3, abs=1e-17)
+    assert r <= 1e-10 and np.linalg.norm(got - A @ B) / np.linalg.norm(A @ B) < 1e-10
+    torch.cuda.synchronize()
+
+
+def test_underestimated_error_falls_back_to_S_max(ozk_mod, handle):
+    A, B = rand_complex(150, 100, 13, 2.0), rand_complex(100, 90, 14, 2.0)
+    Ad, Bd = ozk_mod.colmajor_cuda(A), ozk_mod.colmajor_cuda(B)
+    handle.selector_set_params(_const_params(-30.0))                # claims S = 3 is exact enough
+    handle.selector_configure(tol=1e-10, margin=0.0)
+    C = ozk_mod.colmajor_cuda(np.zeros((150, 90), dtype=np.complex128))
+    ozk_mod.ozaki_zgemm(handle, Ad, Bd, C, S=0)
+    info = handle.selector_last()
+    assert info["S_selected"] == 3 and info["fallback"] and info["S_used"] == 10 and info["residual_ok"]
+    assert info["residual_selected"] > 1e-10
+    got = ozk_mod.to_numpy(C)
+    assert np.array_equal(got, co.zgemm(A, B, 10))                  # the S = 10 product, bit for bit
+    # with the fallback disabled the failed check is an error
+    handle.selector_configure(tol=1e-10, margin=0.0, flags=ozk_mod.OZK_SEL_NO_FALLBACK)
+    with pytest.raises(ozk_mod.OzkError, match="RESIDUAL"):
+        ozk_mod.ozaki_zgemm(handle, Ad, Bd, C, S=0)
+    handle.selector_configure()
+
+
+def test_pessimistic_prediction_selects_S_max_and_general_alpha_beta(ozk_mod, handle):
+    A, B = rand_complex(64, 48, 15, 1.0), rand_complex(48, 80, 16, 1.0)
+    C0 = rand_complex(64, 80, 17, 1.0)
+    handle.selector_set_params(_const_params(0.0))
+    handle.selector_configure(tol=1e-10)
+    alpha, beta = 0.5 - 2j, 1.5 + 0.25j
+    C = ozk_mod.colmajor_cuda(C0)
+    ozk_mod.ozaki_zgemm(handle, ozk_mod.colmajor_cuda(A), ozk_mod.colmajor_cuda(B), C, S=0, alpha=alpha, beta=beta)
+    info = handle.selector_last()
+    assert info["S_selected"] == 10 and not info["fallback"]
+    want = alpha * co.zgemm(A, B, 10) + beta * C0
+    got = ozk_mod.to_numpy(C)
+    assert np.abs(got - want).max() <= 8 * np.finfo(float).eps * (abs(alpha) * np.abs(co.zgemm(A, B, 10)) +
+                                                                  abs(beta) * np.abs(C0)).max()
+
+
+def test_S0_without_parameters_and_under_capture_is_refused(ozk_mod):
+    import torch
+    h = ozk_mod.Handle()
+    A = ozk_mod.colmajor_cuda(rand_complex(8, 8, 1))
+    C = ozk_mod.colmajor_cuda(np.zeros((8, 8), dtype=np.complex128))
+    with pytest.raises(ozk_mod.OzkError, match="selector"):
+        ozk_mod.ozaki_zgemm(h, A, A, C, S=0)
+    h.selector_init(5)
+    ozk_mod.ozaki_zgemm(h, A, A, C, S=0)                           # sizes the scratch
+    g = torch.cuda.CUDAGraph()
+    with pytest.raises(ozk_mod.OzkError, match="capture"):
+        with torch.cuda.graph(g):
+            h.set_stream(torch.cuda.current_stream())
+            ozk_mod.ozaki_zgemm(h, A, A, C, S=0)
+    h.set_stream(torch.cuda.current_stream())
+    h.close()
+
+
+def test_parameter_file_round_trip(ozk_mod, handle, tmp_path):
+    handle.selector_init(42)
+    p = handle.selector_get_params()
+    assert np.all(np.isfinite(p)) and np.abs(p).max() > 0
+    path = str(tmp_path / "sel.bin")
+    handle.selector_save(path)
+    h2 = ozk_mod.Handle()
+    h2.selector_load(path)
+    assert np.array_equal(h2.selector_get_params(), p)
+    bad = tmp_path / "bad.bin"
+    bad.write_bytes(b"OZKSEL1\x00" + (7).to_bytes(4, "little"))
+    with pytest.raises(ozk_mod.OzkError, match="ARG"):
+        h2.selector_load(str(bad))
+    with pytest.raises(ozk_mod.OzkError, match="NOFILE"):
+        h2.selector_load(str(tmp_path / "missing.bin"))
+    h2.close()
+
+
+def test_rel_diff_matches_numpy(ozk_mod, handle):
+    X, Y = rand_complex(70, 33, 21), rand_complex(70, 33, 22)
+    r = ozk_mod.rel_diff(handle, ozk_mod.colmajor_cuda(X), ozk_mod.colmajor_cuda(Y))
+    assert r == pytest.approx(np.linalg.norm(X - Y) / np.linalg.norm(Y), rel=1e-13)

@@ -178,8 +178,9 @@ def test_degenerate_calls(ozk_mod, handle):
     # alpha = 0: C = beta C
     ozk_mod.ozaki_zgemm(handle, A, B, C, S=4, alpha=0.0, beta=2.0)
     assert np.array_equal(ozk_mod.to_numpy(C), 2.0 * C0)
+    # S = 0 is the slice-count selector (tests/test_gpu_selector.py); negative and > 16 are invalid
     with pytest.raises(ozk_mod.OzkError):
-        ozk_mod.ozaki_zgemm(handle, A, B, C, S=0)
+        ozk_mod.ozaki_zgemm(handle, A, B, C, S=-1)
     with pytest.raises(ozk_mod.OzkError):
         ozk_mod.ozaki_zgemm(handle, A, B, C, S=17)
 
