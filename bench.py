@@ -49,8 +49,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=64, help="atoms per GPU per step")
-    ap.add_argument("--S", type=int, default=7)
-    ap.add_argument("--nb", type=int, default=64)
+    ap.add_argument("--S", type=int, default=0,
+                    help="slices; 0 = chosen by the trained slice-count selector at tolerance --tol")
+    ap.add_argument("--tol", type=float, default=1e-10, help="selector tolerance (relative Frobenius, per GEMM)")
+    ap.add_argument("--nb", type=int, default=0, help="panel width; 0 = autotuned for the workload")
     ap.add_argument("--no-extras", action="store_true", help="skip comparisons and the CPU baseline")
     return ap.parse_args()
 
@@ -114,12 +116,15 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- inputs
-def make_inputs(rank: int, batch: int):
-    """Single-site t of `batch` atoms and the structure-constant matrix G they share (one
-    lattice, one energy), numpy, mathematical orientation."""
+def make_inputs(rank: int, world: int, batch: int):
+    """Single-site t of this rank's `batch` atoms and the structure-constant matrix G they
+    share (one lattice, one energy), numpy, mathematical orientation.  Ranks solve disjoint
+    atoms (weak scaling)."""
     import synth
-    t_first, G, _ = synth.kkr_system(L_SITES, B, E0, atom=rank * batch)
-    return [t_first] + [synth.kkr_t(L_SITES, B, atom=rank * batch + a) for a in range(1, batch)], G
+    from paper_2603_29975_gb300 import shard
+    ids = shard.atom_range(rank, world, batch)
+    t_first, G, _ = synth.kkr_system(L_SITES, B, E0, atom=ids[0])
+    return [t_first] + [synth.kkr_t(L_SITES, B, atom=a) for a in ids[1:]], G
 
 
 def colblocks(t):
@@ -129,10 +134,15 @@ def colblocks(t):
 
 def workload_config(args, world):
     batch = args.batch
+    nbtxt = args.nb if args.nb else "autotuned"
+    S = getattr(args, "S_chosen", None)
+    stxt = (f"S={S} chosen by the trained slice-count selector at {args.tol:g}" if args.S == 0 and S
+            else ("S chosen by the trained slice-count selector" if args.S == 0 else f"S={args.S}"))
     return {"workload": f"KKR tau_00, bcc LIZ {L_SITES} sites, lmax=3 (b={B}), n={N}, E=0.5+0.05i; "
-                        f"{batch} atoms per GPU per step sharing G; M=I-tG built on the GPU; block LU nb={args.nb}; "
-                        f"every GEMM (M build and LU) emulated with S={args.S}",
-            "atoms_per_gpu_per_step": batch, "n": N, "S": args.S, "nb": args.nb,
+                        f"{batch} atoms per GPU per step sharing G; M=I-tG built on the GPU; block LU nb={nbtxt}; "
+                        f"every GEMM (M build and LU) emulated, {stxt}",
+            "atoms_per_gpu_per_step": batch, "n": N, "S": S if S else ("selector" if args.S == 0 else args.S),
+            "nb": nbtxt,
             "eff_fp64_flops_per_solve": FLOPS_PER_SOLVE,
             "l2": "256 MB buffer written between timed steps (outside the events); per-step "
                   f"working set {batch * N * N * 16 / 2**30:.2f} GiB of M",
@@ -156,10 +166,11 @@ def run_ours(args):
     import __graft_entry__
     __graft_entry__.build()
     import paper_2603_29975_gb300 as ozk
+    from paper_2603_29975_gb300 import shard
 
     h = ozk.Handle()
     batch = args.batch
-    t_np, G_np = make_inputs(rank, batch)
+    t_np, G_np = make_inputs(rank, world, batch)
     G = torch.from_numpy(np.asfortranarray(G_np)).to(dev)
     ts = [torch.from_numpy(colblocks(t)).to(dev) for t in t_np]
     # only device pointers cross the C ABI: M (n x n), tau (b x b) and the t blocks are
@@ -172,18 +183,34 @@ def run_ours(args):
     ns = [N] * batch
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
 
+    # slice count: the trained selector's choice for this workload (made again inside every
+    # timed step), or a fixed S
+    S_solve = args.S
+    if args.S == 0:
+        if not os.path.exists(ozk.SELECTOR_WEIGHTS):
+            raise RuntimeError("--S 0 needs the trained selector parameters " + ozk.SELECTOR_WEIGHTS)
+        h.selector_load()
+        h.selector_configure(tol=args.tol, margin=0.3)
+        ozk.kkr_build_m_shared_ptrs(h, batch, L_SITES, B, pt, G, pm, S=7)
+        ozk.kkr_tau00_batched_ptrs(h, ns, B, pm, pt0, ptau, S=0, nb=64)
+        args.S_chosen = h.selector_last()["S_used"]
+    else:
+        args.S_chosen = args.S
+    tune_ms = None
+    if args.nb == 0:                              # panel width from the autotuner (untimed)
+        args.nb, tune_ms = ozk.kkr_tau00_autotune(h, ns, B, S=args.S_chosen)
+
     def step():
         # every atom of the step shares G (one lattice, one energy): M_a = I - t_a G by emulated
         # GEMMs, one per site block row for all atoms
-        ozk.kkr_build_m_shared_ptrs(h, batch, L_SITES, B, pt, G, pm, S=args.S)
-        ozk.kkr_tau00_batched_ptrs(h, ns, B, pm, pt0, ptau, S=args.S, nb=args.nb)
+        ozk.kkr_build_m_shared_ptrs(h, batch, L_SITES, B, pt, G, pm, S=args.S_chosen)
+        ozk.kkr_tau00_batched_ptrs(h, ns, B, pm, pt0, ptau, S=S_solve, nb=args.nb)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     if h.status():
         raise RuntimeError("device status set during warm-up")
-
     stream = torch.cuda.current_stream()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clk = ClockSampler(local)
@@ -207,9 +234,7 @@ def run_ours(args):
     step_ms = [a.elapsed_time(b) for a, b in evs]
     local_ms = sum(step_ms)
     if world > 1:
-        tt = torch.tensor([local_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        local_ms = float(tt.item())
+        local_ms = shard.max_over_ranks(local_ms, device=dev)     # whole-job time: the slowest rank
         dist.barrier()
     if h.status():
         raise RuntimeError("device status set during the timed steps")
@@ -241,15 +266,28 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int8 digits (fp16-held) x tensor cores -> exact int -> f64",
             "data": "synthetic (seeded SplitMix64; bcc LIZ, KKR-shaped t and G)",
-            "config": workload_config(args, world),
+            "config": dict(workload_config(args, world),
+                           nb_autotune_ms=None if tune_ms is None else {str(k): round(v, 3) for k, v in tune_ms.items()}),
             "eff_fp64_tflops": round(solves_per_s * FLOPS_PER_SOLVE / 1e12, 3),
             "roofline": roofline, "kernels": kernels, "gpu_launches": int(launches),
+            "launch_mode": "eager (CUDA-graph replay of the same step under extras.graph)",
             "clocks": clocks, "wall_s_timed": round(t_wall, 3)}
     if not args.no_extras:
         line["graph"] = graph_measure(ozk, h, args, step, flush)
         line["e2e"] = e2e_measure(ozk, h, args, dev, t_np, G_np, batch)
+        del Ms, ts, G, flush
+        torch.cuda.empty_cache()
+        line["config3_mixed_liz"] = config3_measure(ozk, h, args, dev)
+        torch.cuda.empty_cache()
+        line["config4_lmax4_spin"] = config4_measure(ozk, h, args, dev)
+        torch.cuda.empty_cache()
+        line["selector"] = selector_measure(ozk)
+        line["contour_observable"] = contour_measure(ozk, h, args, dev)
         line["comparisons"] = comparisons(ozk, h, args, dev, t_np, G_np)
-        line["cpu_baseline"] = cpu_baseline(t_np[0], G_np, args.S, args.nb)
+        per_S = line["comparisons"]["tau00_per_S"]
+        line["selected_S"] = {"S": args.S_chosen, "tol_per_gemm": args.tol if args.S == 0 else None,
+                              "tau00_rel_err_vs_dmma": per_S.get(str(args.S_chosen), {}).get("rel_err_vs_dmma")}
+        line["cpu_baseline"] = cpu_baseline(t_np[0], G_np, args.S_chosen, args.nb)
     print(json.dumps(line))
     h.close()
     if world > 1:
@@ -288,6 +326,182 @@ def graph_measure(ozk, h, args, step, flush):
             "kernels_per_graph": int(launches)}
 
 
+def config3_measure(ozk, h, args, dev, natoms=256, steps=2):
+    """256 atoms of one bcc lattice at one contour energy with LIZ sizes drawn uniformly from
+    27..169 sites (n = 432..2704): M_a built from the largest LIZ's G, all tau_00 in one
+    lockstep batched solve (autotuned panel width), eager and as one CUDA graph.  The 32
+    energies of the full contour are independent repeats of this step."""
+    import numpy as np
+    import torch
+    import synth
+    u = synth.uniform(20260332, 9, np.arange(natoms, dtype=np.uint64))
+    Ls = [27 + int(x * 143) for x in u]
+    E, _ = synth.contour(32)
+    e = complex(E[16])
+    _, G_np, _ = synth.kkr_system(max(Ls), B, e, atom=0)
+    G = torch.from_numpy(np.asfortranarray(G_np)).to(dev)
+    ts = [torch.from_numpy(colblocks(synth.kkr_t(L, B, atom=a))).to(dev) for a, L in enumerate(Ls)]
+    Ms = [torch.empty((L * B, L * B), dtype=torch.complex128, device=dev) for L in Ls]
+    taus = [torch.zeros((B, B), dtype=torch.complex128, device=dev) for _ in Ls]
+    i64 = lambda xs: torch.tensor([x.data_ptr() for x in xs], dtype=torch.int64, device=dev)
+    pt, pm, ptau = i64(ts), i64(Ms), i64(taus)
+    ns = [L * B for L in Ls]
+    nb, tune = ozk.kkr_tau00_autotune(h, ns, B, S=args.S_chosen)
+
+    def step():
+        ozk.kkr_build_m_shared_sizes_ptrs(h, Ls, B, pt, G, pm, S=args.S_chosen)
+        ozk.kkr_tau00_batched_ptrs(h, ns, B, pm, pt, ptau, S=args.S_chosen, nb=nb)
+
+    step()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    for _ in range(steps):
+        step()
+    ev[1].record()
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / steps
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        h.set_stream(torch.cuda.current_stream())
+        step()
+    h.set_stream(torch.cuda.current_stream())
+    g.replay()
+    torch.cuda.synchronize()
+    ev[0].record()
+    for _ in range(steps):
+        g.replay()
+    ev[1].record()
+    torch.cuda.synchronize()
+    gms = ev[0].elapsed_time(ev[1]) / steps
+    if h.status():
+        raise RuntimeError("device status set in the mixed-LIZ batch")
+    flops = sum(8.0 / 3.0 * n ** 3 for n in ns)
+    del g
+    return {"solves": natoms, "liz_sites": [min(Ls), max(Ls)], "energy": [e.real, e.imag], "nb": nb,
+            "nb_autotune_ms": {str(k): round(v, 2) for k, v in tune.items()},
+            "eager_ms_per_step": round(ms, 2), "graph_ms_per_step": round(gms, 2),
+            "solves_per_s": round(natoms / (min(ms, gms) / 1e3), 1),
+            "eff_fp64_tflops": round(flops / (min(ms, gms) / 1e3) / 1e12, 3),
+            "est_s_for_8192_solves_32_energies": round(32 * min(ms, gms) / 1e3, 2)}
+
+
+def config4_measure(ozk, h, args, dev):
+    """Spin-polarised lmax = 4 (b = 50), LIZ of 113 sites, n = 5650: tau_00 with every GEMM
+    emulated at S = 3..10 against the binary64 DMMA path on the same GPU, and the standalone
+    5650^3 ZGEMM (M times M) per S against DMMA."""
+    import numpy as np
+    import torch
+    import synth
+    L4, b4 = 113, 50
+    t4, G4, _ = synth.kkr_system(L4, b4, E0, atom=0)
+    n = L4 * b4
+    tb = torch.from_numpy(colblocks(t4)).to(dev)
+    Gd = torch.from_numpy(np.asfortranarray(G4)).to(dev)
+    del G4
+    M0 = torch.empty((n, n), dtype=torch.complex128, device=dev).t()
+    ozk.kkr_build_m(h, tb, Gd, M0)
+    del Gd
+    t0 = torch.from_numpy(np.asfortranarray(t4[0])).to(dev)
+    M = torch.empty_like(M0)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def solve(S, nb):
+        M.copy_(M0)
+        tau = torch.zeros((b4, b4), dtype=torch.complex128, device=dev).t()
+        ev[0].record()
+        ozk.kkr_tau00(h, M, t0, tau, S=S, nb=nb)
+        ev[1].record()
+        torch.cuda.synchronize()
+        return tau.cpu().numpy(), ev[0].elapsed_time(ev[1])
+
+    ref, ms_ref = solve(0, 50)
+    flops = 8.0 / 3.0 * n ** 3
+    out = {"n": n, "b": b4, "dmma_tau00_ms": round(ms_ref, 1), "dmma_eff_tflops": round(flops / ms_ref / 1e9, 3),
+           "tau00": {}, "zgemm_5650": {}}
+    for S in range(3, 11):
+        tau, ms = solve(S, 100)
+        out["tau00"][str(S)] = {"rel_err_vs_dmma": rel_err(tau, ref), "ms": round(ms, 1),
+                                "eff_tflops": round(flops / ms / 1e9, 3)}
+    C_ref = torch.empty_like(M0)
+    ev[0].record()
+    ozk.ozk_zgemm_dmma(h, M0, M0, C_ref)
+    ev[1].record()
+    torch.cuda.synchronize()
+    gflops = 8.0 * n ** 3
+    out["zgemm_5650"]["dmma"] = {"ms": round(ev[0].elapsed_time(ev[1]), 1),
+                                 "tflops": round(gflops / ev[0].elapsed_time(ev[1]) / 1e9, 3)}
+    C = torch.empty_like(M0)
+    for S in range(3, 11):
+        ozk.ozaki_zgemm(h, M0, M0, C, S=S)
+        torch.cuda.synchronize()
+        ev[0].record()
+        ozk.ozaki_zgemm(h, M0, M0, C, S=S)
+        ev[1].record()
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1])
+        out["zgemm_5650"][str(S)] = {"ms": round(ms, 1), "eff_tflops": round(gflops / ms / 1e9, 3),
+                                     "rel_err_vs_dmma": ozk.rel_diff(h, C, C_ref)}
+    if h.status():
+        raise RuntimeError("device status set in the n = 5650 sweep")
+    return out
+
+
+def contour_measure(ozk, h, args, dev):
+    """The site-diagonal trace Tr tau_00(z) at the 32 contour energies of one atom of the
+    workload and its quadrature sum: for each S the maximum percent error across the energies
+    against the binary64 DMMA path (the analogue of the paper's G(z) error per mode, Sec. 4)."""
+    import numpy as np
+    import torch
+    import synth
+    E, w = synth.contour(32)
+    sys_ = [synth.kkr_system(L_SITES, B, complex(z), atom=0)[:2] for z in E]
+    tbs = [torch.from_numpy(colblocks(t)).to(dev) for t, G in sys_]
+    Gs = [torch.from_numpy(np.asfortranarray(G)).to(dev) for t, G in sys_]
+    Ms = [torch.empty((N, N), dtype=torch.complex128, device=dev) for _ in E]
+    taus = [torch.zeros((B, B), dtype=torch.complex128, device=dev) for _ in E]
+    i64 = lambda xs: torch.tensor([x.data_ptr() for x in xs], dtype=torch.int64, device=dev)
+    pt, pm, ptau = i64(tbs), i64(Ms), i64(taus)
+    # binary64 reference: binary64 build, DMMA block LU
+    for z in range(len(E)):
+        Mz = torch.empty((N, N), dtype=torch.complex128, device=dev).t()
+        ozk.kkr_build_m(h, tbs[z], Gs[z], Mz)
+        tz = torch.from_numpy(np.asfortranarray(sys_[z][0][0])).to(dev)
+        out = torch.zeros((B, B), dtype=torch.complex128, device=dev).t()
+        ozk.kkr_tau00(h, Mz, tz, out, S=0, nb=32)
+        taus[z].view(-1).copy_(out.t().reshape(-1))        # same column-major storage
+    ref_tr, ref_int = ozk.kkr_contour_trace(h, ptau, B, w)
+    res = {"energies": len(E), "integral_dmma": [ref_int.real, ref_int.imag], "per_S": {}}
+    for S in range(3, 10):
+        for z in range(len(E)):
+            ozk.kkr_build_m_shared_ptrs(h, 1, L_SITES, B, pt[z:z + 1], Gs[z], pm[z:z + 1], S=S)
+        ozk.kkr_tau00_batched_ptrs(h, [N] * len(E), B, pm, pt, ptau, S=S, nb=args.nb or 64)
+        tr, integ = ozk.kkr_contour_trace(h, ptau, B, w)
+        pct = 100.0 * np.abs(tr - ref_tr) / np.abs(ref_tr)
+        res["per_S"][str(S)] = {"max_pct_err_trace": float(pct.max()),
+                                "integral_rel_err": float(abs(integ - ref_int) / abs(ref_int))}
+    if h.status():
+        raise RuntimeError("device status set in the contour sweep")
+    return res
+
+
+def selector_measure(ozk):
+    """The trained slice-count selector on held-out GEMM instances (seed unseen in training):
+    chosen S, tolerance violations before and after the residual check, and GEMM time at the
+    chosen S against fixed S."""
+    import os
+    from paper_2603_29975_gb300 import selector as seltrain
+    if not os.path.exists(ozk.SELECTOR_WEIGHTS):
+        return {"unavailable": "no trained selector parameters in the package"}
+    h2 = ozk.Handle()
+    h2.selector_load()
+    inst = seltrain.generate_instances(96, 4242, kkr_sizes=(15, 27), energies=2)
+    X, T, times = seltrain.label(ozk, h2, inst)
+    res = seltrain.evaluate(ozk, h2, inst, X, T, times, tol=1e-10)
+    h2.close()
+    return res
+
+
 def e2e_measure(ozk, h, args, dev, t_np, G_np, batch):
     """Same metric through the public API with HOST inputs: pinned t and G copied in each step,
     tau_00 of every atom copied back, all inside the timed region."""
@@ -311,7 +525,7 @@ def e2e_measure(ozk, h, args, dev, t_np, G_np, batch):
     def step():
         Gd.copy_(Gh, non_blocking=True)
         td.copy_(th, non_blocking=True)
-        ozk.kkr_build_m_shared_ptrs(h, batch, L_SITES, B, pt, Gd, pm, S=args.S)
+        ozk.kkr_build_m_shared_ptrs(h, batch, L_SITES, B, pt, Gd, pm, S=args.S_chosen)
         ozk.kkr_tau00_batched_ptrs(h, ns, B, pm, pt0, ptau, S=args.S, nb=args.nb)
         tau_h.copy_(taus, non_blocking=True)
 
@@ -368,7 +582,7 @@ def comparisons(ozk, h, args, dev, t_np, G_np):
     out["dmma_tau00_nb"] = 32
     out["dmma_tau00_solves_per_s_single"] = round(1e3 / ms_dmma, 2)
     errs = {}
-    for S in (3, 5, 6, 7, 8, 9):
+    for S in (3, 4, 5, 6, 7, 8, 9):
         tau, ms = solve(S, 2)
         errs[str(S)] = {"rel_err_vs_dmma_fp64": float(rel_err(tau, tau_ref)), "single_solve_ms": round(ms, 3)}
     out["tau00_per_S"] = errs
@@ -431,14 +645,16 @@ def run_reference(args):
     co.build()
     t, G, _ = synth.kkr_system(L_SITES, B, E0, atom=0)
     M = kkr.kkr_build(t, G)
+    nb = args.nb or 64                            # the GPU arm autotunes; the oracle uses 64
+    S = args.S or 7                               # the GPU arm's selector runs on the GPU; the oracle uses 7
     for _ in range(args.warmup):
-        co.tau00_block(M, t[0], args.nb, S=args.S, leaf=B)
+        co.tau00_block(M, t[0], nb, S=S, leaf=B)
     t1 = time.perf_counter()
     for _ in range(args.steps):
-        co.tau00_block(M, t[0], args.nb, S=args.S, leaf=B)
+        co.tau00_block(M, t[0], nb, S=S, leaf=B)
     dt = time.perf_counter() - t1
     v = args.steps / dt
-    sample = (f"{args.steps} timed solves of one atom of the workload (n={N}, S={args.S}, panels nb={args.nb} "
+    sample = (f"{args.steps} timed solves of one atom of the workload (n={N}, S={S}, panels nb={nb} "
               f"of {B}x{B} leaves) by oracle/c with OpenMP; one solve per step instead of {args.batch}")
     line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "tau00 solves/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 1),

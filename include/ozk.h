@@ -176,8 +176,9 @@ ozk_status_t ozaki_zgemm_noalloc(void* stream, char transa, char transb, int m, 
  *      perceptron 16 -> 64 -> 64 -> 8 (ReLU), whose parameters are trained on the GPU by
  *      ozk_selector_train_step (mean squared error, Adam);
  *   3. picks the smallest S whose prediction is <= log10(tol) - margin (else 10);
- *   4. checks the computed product D a posteriori: r = ||D X - z|| / ||z|| estimates
- *      ||D - AB||_F / ||AB||_F; if r > tol the product is recomputed with S = 10 (fallback),
+ *   4. checks the computed product D a posteriori: r = ||D X - z|| / ||z|| (4 probe vectors,
+ *      compensated double-double products) estimates ||D - AB||_F / ||AB||_F; if r > tol / 2
+ *      (room for the estimate's scatter) the product is recomputed with S = 10 (fallback),
  *      unless OZK_SEL_NO_FALLBACK is set, in which case OZK_ERR_RESIDUAL is returned.
  * ozaki_zgemm with S = 0 runs these steps.  It synchronises the stream twice (to read the
  * chosen S and the residual) and cannot be captured (OZK_ERR_CAPTURE).  Parameter layout,
@@ -280,6 +281,13 @@ ozk_status_t kkr_build_m_batched(ozk_handle_t handle, int batch, const int* L, i
  *      DEVICE pointers to n x n column-major outputs (ld n). */
 ozk_status_t kkr_build_m_shared(ozk_handle_t handle, int natoms, int L, int b, const void* const* t,
                                 const void* G, void* const* M, int S);
+/* The same for atoms whose LIZs are the first L[a] sites (HOST array) of one site list on one
+ * lattice at one energy: atom a's G is the leading L[a] b block of G (the structure constants
+ * of the largest LIZ, leading dimension ldg >= max L[a] b), its M has order and leading
+ * dimension L[a] b, and t[a] holds L[a] blocks.  One stacked GEMM per block row i < max L[a];
+ * the rows of atoms with L[a] <= i, and columns past an atom's order, are not written. */
+ozk_status_t kkr_build_m_shared_sizes(ozk_handle_t handle, int natoms, const int* L, int b,
+                                      const void* const* t, const void* G, int ldg, void* const* M, int S);
 
 /* tau_00 = [M^-1]_00 t_0 = S_00^-1 t_0 by block LU (paper Sec. 3.2: LU-based inversion of the
  * multiple scattering matrix).  Panels J = [p, q) of width nb are eliminated from the trailing
@@ -292,16 +300,41 @@ ozk_status_t kkr_build_m_shared(ozk_handle_t handle, int natoms, int L, int b, c
  *   S <= 0: binary64 DMMA GEMMs with one nb x nb pivot block per panel (nb <= 64).
  *   M   : DEVICE n x n column major (ld n), DESTROYED (overwritten by the factorisation).
  *   t0  : DEVICE b x b column major.  tau00: DEVICE b x b column major output.
- *   b <= 16, nb a multiple of b.  Site 0 occupies rows/cols 0..b-1. */
+ *   b <= 64 (16 for lmax = 3; 50 for lmax = 4 with spin), nb a multiple of b.  Site 0 occupies
+ *   rows/cols 0..b-1.  Pivot blocks up to 16 x 16 use a 4-warp Gauss-Jordan kernel, larger ones a
+ *   256-thread one. */
 ozk_status_t kkr_tau00(ozk_handle_t handle, int n, int b, void* M, const void* t0, void* tau00,
                        int S, int nb);
 
 /* Batched tau_00 over `nsolves` independent (atom, energy) matrices of sizes n[i] (HOST
  * array, multiples of b): M, t0, tau00 are DEVICE arrays of DEVICE pointers.  All solves
- * advance panel by panel in lockstep; each step is one batched launch per kernel. */
+ * advance panel by panel in lockstep; each step is one batched launch per kernel.
+ * nb = 0: the panel width kkr_tau00_autotune chose for these sizes, b and S (tuned on the
+ * first such call, which must not be captured).
+ * S = 0: the slice-count selector chooses S once for the call, from the operands of solve 0's
+ * first trailing update (the L and U panels of its unfactored M) at the handle's tolerance;
+ * ozk_selector_last reports the choice.  Synchronises; no per-GEMM residual check on this
+ * path.  S < 0 is an error (the batched path is emulated). */
 ozk_status_t kkr_tau00_batched(ozk_handle_t handle, int nsolves, const int* n, int b,
                                void* const* M, const void* const* t0, void* const* tau00,
                                int S, int nb);
+
+/* Contour-integrated observable of the tau_00 blocks of the energy points z_i of a contour:
+ * traces[i] = Tr tau_00(z_i) and *integral = sum_i w_i Tr tau_00(z_i) (the quadrature of the
+ * site-diagonal Green's-function trace whose error per precision mode the paper reports,
+ * Sec. 4).  tau: DEVICE array of nsolves DEVICE pointers to b x b column-major blocks;
+ * w: HOST 2 nsolves doubles (re, im of the weights); traces (HOST, 2 nsolves doubles, may
+ * be NULL) and integral (HOST, 2 doubles).  Synchronises the stream. */
+ozk_status_t kkr_contour_trace(ozk_handle_t handle, int nsolves, int b, const void* const* tau, const double* w,
+                               double* traces, double* integral);
+
+/* Autotuner of the batched solve: times kkr_tau00_batched on scratch matrices of the sizes
+ * n[0..nsolves-1] (diagonally dominant test matrices, allocated and freed here) for every
+ * panel width nb = b, 2b, ... <= 128, returns the fastest in *nb_best (HOST) and the times in
+ * ms in times[] (HOST, one per candidate in that order; may be NULL), and caches the choice in
+ * the handle for nb = 0.  Synchronises; cannot be captured. */
+ozk_status_t kkr_tau00_autotune(ozk_handle_t handle, int nsolves, const int* n, int b, int S, int* nb_best,
+                                float* times);
 
 #ifdef __cplusplus
 }

@@ -108,3 +108,11 @@ def rel_err(X: np.ndarray, Y: np.ndarray) -> float:
     """Relative Frobenius error ||X - Y||_F / ||Y||_F."""
     d = np.linalg.norm(Y)
     return float(np.linalg.norm(X - Y) / d) if d else float(np.linalg.norm(X))
+
+
+def contour_trace(taus, w):
+    """Tr tau_00(z_i) for every energy point and the quadrature sum_i w_i Tr tau_00(z_i) (the
+    site-diagonal Green's-function trace integrated along the contour, whose error per
+    precision mode the paper reports, Sec. 4)."""
+    tr = np.array([np.trace(np.asarray(t)) for t in taus], dtype=np.complex128)
+    return tr, complex(np.sum(np.asarray(w, dtype=np.complex128) * tr))

@@ -36,7 +36,7 @@ OFF_B2 = OFF_W2 + NH * NH
 OFF_W3 = OFF_B2 + NH
 OFF_B3 = OFF_W3 + NO * NH
 NPARAMS = OFF_B3 + NO
-PROBES = 2
+PROBES = 4
 PROBE_SCALE = math.sqrt(6.0)          # (U[0,1) - 1/2) * sqrt(6): variance 1/2 per real part
 
 
@@ -138,6 +138,29 @@ def _vector_stats(V):
     return r, e, sh, z
 
 
+def _to_int(V):
+    """Exact integer image of a complex binary64 array: (Re, Im, e) with V = (Re + i Im) 2^e,
+    Re and Im object arrays of Python ints."""
+    V = np.asarray(V, dtype=np.complex128)
+    parts = [x.as_integer_ratio() for x in np.concatenate([V.real.ravel(), V.imag.ravel()])]
+    den = max(d for _, d in parts) if parts else 1
+    ints = np.array([n * (den // d) for n, d in parts], dtype=object)
+    half = V.size
+    e = -(den.bit_length() - 1)
+    return ints[:half].reshape(V.shape), ints[half:].reshape(V.shape), e
+
+
+def _int_mul(a, b):
+    """Exact product of two integer images (object-array matmul of Python ints)."""
+    ar, ai, ea = a
+    br, bi, eb = b
+    return ar @ br - ai @ bi, ar @ bi + ai @ br, ea + eb
+
+
+def _int_sq(re, im):
+    return int(np.sum(re * re + im * im)) if re.size else 0
+
+
 def _scaled(V, s):
     """V * 2^s, exactly (ldexp of both parts)."""
     return np.ldexp(V.real, s) + 1j * np.ldexp(V.imag, s)
@@ -152,10 +175,12 @@ def _log2sum(w, e):
                                                       2 * (np.asarray(e, dtype=np.int64) - em)))))
 
 
-def features(Aop, Bop, X):
+def features(Aop, Bop, X, exact=False):
     """The 16 selector features of the product Aop @ Bop (m x k times k x n, complex), with
     probe vectors X (n x PROBES).  Returns (f, zs, E) where zs = (2^-EA Aop)((2^-EB Bop) X)
-    is the scaled probe product the residual check reuses and E = EA + EB.
+    is the scaled probe product the residual check reuses and E = EA + EB.  With exact=True
+    the probe product is formed in exact integer arithmetic and returned as its integer
+    image (see _to_int); otherwise by binary64 matrix products.
 
     Per row i of Aop: r_i = max(|Re|, |Im|), e_i its frexp exponent, sh_i = sum |a_il/2^e_i|^2;
     per column j of Bop likewise (f_j).  EA = max e_i, EB = max f_j over nonzero vectors.
@@ -201,8 +226,14 @@ def features(Aop, Bop, X):
     nza, nzb = ra > 0, rb > 0
     EA = int(ea[nza].max()) if np.any(nza) else 0
     EB = int(eb[nzb].max()) if np.any(nzb) else 0
-    zs = _scaled(Aop, -EA) @ (_scaled(Bop, -EB) @ X)
-    z2 = float(np.sum(np.abs(zs) ** 2))
+    if exact:
+        zr, zi, ez = _int_mul(_to_int(Aop), _int_mul(_to_int(Bop), _to_int(X)))
+        zs = (zr, zi, ez - EA - EB)
+        z2 = math.ldexp(float(_int_sq(zr, zi) >> max(0, _int_sq(zr, zi).bit_length() - 60)),
+                        2 * zs[2] + max(0, _int_sq(zr, zi).bit_length() - 60))
+    else:
+        zs = _scaled(Aop, -EA) @ (_scaled(Bop, -EB) @ X)
+        z2 = float(np.sum(np.abs(zs) ** 2))
     if z2 > 0 and np.any(nza) and np.any(nzb):
         lc = 0.5 * math.log2(n * z2 / float(np.sum(np.abs(X) ** 2))) + EA + EB
         lA = _log2sum(sa[nza], ea[nza])
@@ -220,7 +251,20 @@ def features(Aop, Bop, X):
 
 def residual_estimate(D, X, zs, E):
     """||2^-E D X - zs||_F / ||zs||_F for the scaled probe product zs of ``features`` (0 when
-    both vanish, inf when only zs does)."""
+    both vanish, inf when only zs does); exact when zs is an integer image."""
+    if isinstance(zs, tuple):
+        zr, zi, ez = zs
+        wr, wi, ew = _int_mul(_to_int(D), _to_int(X))
+        ew -= E
+        e0 = min(ez, ew)                               # common scale 2^e0
+        dr = wr * (1 << (ew - e0)) - zr * (1 << (ez - e0))
+        di = wi * (1 << (ew - e0)) - zi * (1 << (ez - e0))
+        num = _int_sq(dr, di)
+        den = _int_sq(zr, zi) << (2 * (ez - e0))
+        if den == 0:
+            return 0.0 if num == 0 else math.inf
+        q = (num << 200) // den                        # num / den with 200 extra bits
+        return math.sqrt(math.ldexp(float(q >> max(0, q.bit_length() - 60)), max(0, q.bit_length() - 60) - 200))
     w = _scaled(np.asarray(D, dtype=np.complex128) @ X, -E)
     num = float(np.sum(np.abs(w - zs) ** 2))
     den = float(np.sum(np.abs(zs) ** 2))

@@ -42,7 +42,8 @@ EXPORTS = ["ozk_create", "ozk_destroy", "ozk_set_stream", "ozk_get_status", "ozk
            "kkr_build_m_batched", "ozaki_zgemm_noalloc", "ozk_selector_init", "ozk_selector_set_params",
            "ozk_selector_get_params", "ozk_selector_load", "ozk_selector_save", "ozk_selector_configure",
            "ozk_selector_features", "ozk_selector_predict", "ozk_selector_train_step", "ozk_selector_gradient",
-           "ozk_selector_last", "ozk_rel_diff", "kkr_build_m_shared"]
+           "ozk_selector_last", "ozk_rel_diff", "kkr_build_m_shared", "kkr_tau00_autotune",
+           "kkr_build_m_shared_sizes", "kkr_contour_trace"]
 KIND_NAMES = ["split", "slice_gemm", "gj", "build_m", "dmma", "other"]
 
 _lib = None
@@ -80,6 +81,9 @@ def lib():
         L.kkr_tau00_batched.argtypes = [vp, i, ip, i, vp, vp, vp, i, i]
         L.kkr_build_m_batched.argtypes = [vp, i, ip, i, vp, vp, vp]
         L.kkr_build_m_shared.argtypes = [vp, i, i, i, vp, vp, vp, i]
+        L.kkr_tau00_autotune.argtypes = [vp, i, ip, i, i, ip, ctypes.POINTER(ctypes.c_float)]
+        L.kkr_build_m_shared_sizes.argtypes = [vp, i, ip, i, vp, vp, i, vp, i]
+        L.kkr_contour_trace.argtypes = [vp, i, i, vp, dp, dp, dp]
         L.ozaki_zgemm_noalloc.argtypes = [vp, c, c, i, i, i, dp, vp, i, vp, i, dp, vp, i, i, i, vp]
         fp, u64, f32 = ctypes.POINTER(ctypes.c_float), ctypes.c_uint64, ctypes.c_float
         L.ozk_selector_init.argtypes = [vp, u64]
@@ -342,6 +346,41 @@ def kkr_build_m_shared_ptrs(h: Handle, natoms: int, L: int, b: int, pt, G, pm, S
     CUDA tensors of device pointers (t blocks, M outputs), G a column-major CUDA tensor."""
     _check(lib().kkr_build_m_shared(h.ptr, natoms, L, b, pt.data_ptr(), _ptr(G), pm.data_ptr(), S),
            "kkr_build_m_shared")
+
+
+def kkr_build_m_shared_sizes_ptrs(h: Handle, L_list, b: int, pt, G, pm, S: int = 7):
+    """M_a = I - blockdiag(t_a) G[:L_a b, :L_a b] for atoms with LIZ sizes L_list sharing the
+    largest LIZ's G (column-major CUDA tensor); pt, pm: int64 CUDA tensors of device pointers."""
+    na = len(L_list)
+    Ls = (ctypes.c_int * na)(*[int(v) for v in L_list])
+    _check(lib().kkr_build_m_shared_sizes(h.ptr, na, Ls, b, pt.data_ptr(), _ptr(G), _ld(G, G.shape[0]),
+                                          pm.data_ptr(), S), "kkr_build_m_shared_sizes")
+
+
+def kkr_contour_trace(h: Handle, ptau, b: int, weights):
+    """Tr tau_00(z_i) and sum_i w_i Tr tau_00(z_i) for the blocks behind the int64 CUDA tensor
+    of device pointers `ptau`; returns (numpy complex traces, complex integral)."""
+    ns = int(ptau.numel())
+    w = np.ascontiguousarray(np.asarray(weights, dtype=np.complex128))
+    if w.size != ns:
+        raise OzkError("one weight per block")
+    tr = np.zeros(ns, dtype=np.complex128)
+    out = np.zeros(1, dtype=np.complex128)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(lib().kkr_contour_trace(h.ptr, ns, b, ptau.data_ptr(), w.ctypes.data_as(dp), tr.ctypes.data_as(dp),
+                                   out.ctypes.data_as(dp)), "kkr_contour_trace")
+    return tr, complex(out[0])
+
+
+def kkr_tau00_autotune(h: Handle, n_list, b: int, S: int = 7):
+    """Time every panel width for these sizes; returns (best nb, {nb: ms})."""
+    ns = len(n_list)
+    n = (ctypes.c_int * ns)(*[int(v) for v in n_list])
+    cands = list(range(b, 129, b))
+    times = (ctypes.c_float * len(cands))()
+    best = ctypes.c_int(0)
+    _check(lib().kkr_tau00_autotune(h.ptr, ns, n, b, S, ctypes.byref(best), times), "kkr_tau00_autotune")
+    return best.value, {nb: float(times[i]) for i, nb in enumerate(cands)}
 
 
 def kkr_tau00(h: Handle, M, t0, tau, S: int = 7, nb: int = 64):

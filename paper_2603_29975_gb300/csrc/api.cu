@@ -96,6 +96,8 @@ struct ozk_context {
   void* sel_ws = nullptr;                   // selector scratch (features, probes, products)
   size_t sel_ws_bytes = 0;
   ozk_selector_info sel_last{};
+  // panel widths chosen by kkr_tau00_autotune, keyed by (sizes..., b, S)
+  std::map<std::vector<int>, int> tuned_nb;
 };
 
 namespace {
@@ -217,10 +219,12 @@ struct EmuGemm {
   int16_t* dbg_digits_a = nullptr; int* dbg_exps_a = nullptr;
   int skm = 0, skn = 0;                        // skip box (single problem)
   const int* tskm = nullptr; const int* tskn = nullptr;   // skip box tables (batched)
+  int box_m = 0, box_n = 0;                   // batched: smallest skip box over the problems
   double sum_mnk = -1;                        // sum over problems of m n k (batched; -1: single)
   double sum_mk = 0, sum_nk = 0;              // operand sizes (complex elements) for byte counts
   long long zsA = 0, zsB = 0;                 // uniform batch of single-size problems: operand strides
   double2* const* crow = nullptr; int crow_b = 0;   // row-block scatter of the output
+  const int* crow_n = nullptr;                // per-output order (device), or none
 };
 
 struct GemmPlan {
@@ -328,7 +332,9 @@ ozk_status_t run_emulated(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0
   gp.groups = g.groups; gp.status = h->d_status;
   if (single) { gp.m = nullptr; gp.m1 = g.m; gp.n1 = g.n; gp.C1 = g.C; gp.ldc1 = g.ldc; gp.skm1 = g.skm; gp.skn1 = g.skn; }
   else { gp.m = g.tm; gp.n = g.tn; gp.C = g.tC; gp.ldc = g.tldc; gp.skm = g.tskm; gp.skn = g.tskn; }
-  gp.crow = g.crow; gp.crow_b = g.crow_b;
+  gp.crow = g.crow; gp.crow_b = g.crow_b; gp.crow_n = g.crow_n;
+  gp.box_m = single ? g.skm : (g.tskm ? g.box_m : 0);
+  gp.box_n = single ? g.skn : (g.tskn ? g.box_n : 0);
   int np = 0;
   for (int gg = 2; gg <= gmax; ++gg) {
     bool first = true;
@@ -404,7 +410,7 @@ static ozk_status_t sel_upload(ozk_context* h, const float* host) {
 struct SelScratch {
   SelVecStats a, b;
   int* ex;
-  double2 *X, *y, *zs, *W, *D;
+  double2 *X, *yh, *yl, *zh, *zl, *Wh, *Wl, *part, *D;   // probe products as double-doubles
   float *f, *Y;
   SelAux* aux;
 };
@@ -416,8 +422,13 @@ static ozk_status_t sel_scratch(ozk_context* h, int m, int n, int k, bool needD,
   const size_t P = SEL_PROBES;
   const size_t o_ar = take(8 * size_t(m)), o_ae = take(4 * size_t(m)), o_ash = take(8 * size_t(m)), o_az = take(4 * size_t(m));
   const size_t o_br = take(8 * size_t(n)), o_be = take(4 * size_t(n)), o_bsh = take(8 * size_t(n)), o_bz = take(4 * size_t(n));
-  const size_t o_ex = take(8), o_X = take(16 * P * n), o_y = take(16 * P * k), o_zs = take(16 * P * m);
-  const size_t o_W = take(16 * P * m), o_f = take(4 * SEL_NF), o_Y = take(4 * SEL_NO), o_aux = take(sizeof(SelAux));
+  const size_t o_ex = take(8), o_X = take(16 * P * n), o_yh = take(16 * P * k), o_yl = take(16 * P * k);
+  const size_t o_zh = take(16 * P * m), o_zl = take(16 * P * m), o_Wh = take(16 * P * m), o_Wl = take(16 * P * m);
+  // chunk partials of the row-strided products: y (k rows over n), zs and W (m rows over k, n)
+  const size_t prow = std::max<size_t>({size_t(k) * gemv_chunks(n), size_t(m) * gemv_chunks(k),
+                                        size_t(m) * gemv_chunks(n)});
+  const size_t o_part = take(32 * P * prow);
+  const size_t o_f = take(4 * SEL_NF), o_Y = take(4 * SEL_NO), o_aux = take(sizeof(SelAux));
   const size_t o_D = needD ? take(16 * size_t(m) * n) : 0;
   ozk_status_t st = ensure_sel_ws(h, off);
   if (st) return st;
@@ -428,9 +439,13 @@ static ozk_status_t sel_scratch(ozk_context* h, int m, int n, int k, bool needD,
           reinterpret_cast<int*>(b + o_bz)};
   s->ex = reinterpret_cast<int*>(b + o_ex);
   s->X = reinterpret_cast<double2*>(b + o_X);
-  s->y = reinterpret_cast<double2*>(b + o_y);
-  s->zs = reinterpret_cast<double2*>(b + o_zs);
-  s->W = reinterpret_cast<double2*>(b + o_W);
+  s->yh = reinterpret_cast<double2*>(b + o_yh);
+  s->yl = reinterpret_cast<double2*>(b + o_yl);
+  s->zh = reinterpret_cast<double2*>(b + o_zh);
+  s->zl = reinterpret_cast<double2*>(b + o_zl);
+  s->Wh = reinterpret_cast<double2*>(b + o_Wh);
+  s->Wl = reinterpret_cast<double2*>(b + o_Wl);
+  s->part = reinterpret_cast<double2*>(b + o_part);
   s->f = reinterpret_cast<float*>(b + o_f);
   s->Y = reinterpret_cast<float*>(b + o_Y);
   s->aux = reinterpret_cast<SelAux*>(b + o_aux);
@@ -451,10 +466,10 @@ static ozk_status_t sel_features(ozk_context* h, const OpFlags& oa, const OpFlag
   // columns of op(B): columns of B (contiguous) or rows of B (strided)
   launch_vec_stats(B, ldb, n, k, ob.trans == 0, s.b, st);
   launch_max_exp(s.a, m, s.b, n, s.ex, st);
-  // y = (2^-EB op(B)) X, zs = (2^-EA op(A)) y
-  launch_gemv(B, ldb, k, n, ob.trans == 0 ? 0 : (ob.conj ? 2 : 1), s.X, n, s.y, k, s.ex, 1, st);
-  launch_gemv(A, lda, m, k, oa.trans == 0 ? 0 : (oa.conj ? 2 : 1), s.y, k, s.zs, m, s.ex, 0, st);
-  launch_selector_features(s.a, m, s.b, n, k, s.X, s.zs, s.ex, s.f, s.aux, st);
+  // y = (2^-EB op(B)) X, zs = (2^-EA op(A)) y, both double-doubles
+  launch_gemv(B, ldb, k, n, ob.trans == 0 ? 0 : (ob.conj ? 2 : 1), s.X, nullptr, n, s.yh, s.yl, s.part, s.ex, 1, st);
+  launch_gemv(A, lda, m, k, oa.trans == 0 ? 0 : (oa.conj ? 2 : 1), s.yh, s.yl, k, s.zh, s.zl, s.part, s.ex, 0, st);
+  launch_selector_features(s.a, m, s.b, n, k, s.X, s.zh, s.ex, s.f, s.aux, st);
   return cuda_check(cudaGetLastError(), "selector feature launches");
 }
 
@@ -495,8 +510,8 @@ static ozk_status_t zgemm_auto(ozk_context* h, const EmuGemm& g) {
     d.S = S;
     ozk_status_t e = run_emulated(h, d);
     if (e) return e;
-    launch_gemv(d.C, d.ldc, m, n, 0, s.X, n, s.W, m, nullptr, 0, h->stream);
-    launch_residual(s.W, s.zs, m, s.aux, h->stream);
+    launch_gemv(d.C, d.ldc, m, n, 0, s.X, nullptr, n, s.Wh, s.Wl, s.part, nullptr, 0, h->stream);
+    launch_residual(s.Wh, s.Wl, s.zh, s.zl, m, s.aux, h->stream);
     SelAux a2;
     e = read_aux(h, s.aux, &a2);
     *r = a2.resid;
@@ -507,14 +522,17 @@ static ozk_status_t zgemm_auto(ozk_context* h, const EmuGemm& g) {
   if (st) return st;
   info.residual_selected = r;
   info.S_used = aux.S;
-  if (!(r <= h->sel_tol) && !(h->sel_flags & OZK_SEL_NO_FALLBACK) && aux.S < SEL_SMAX) {
+  // the 4-probe estimate scatters around the true error: a product passes when its estimate is
+  // at most half the tolerance
+  const double pass = 0.5 * h->sel_tol;
+  if (!(r <= pass) && !(h->sel_flags & OZK_SEL_NO_FALLBACK) && aux.S < SEL_SMAX) {
     st = product_and_check(SEL_SMAX, &r);
     if (st) return st;
     info.S_used = SEL_SMAX;
     info.fallback = 1;
   }
   info.residual = r;
-  info.residual_ok = r <= h->sel_tol ? 1 : 0;
+  info.residual_ok = r <= pass ? 1 : 0;
   if (!direct) {
     launch_axpby(m, n, s.D, m, g.C, g.ldc, g.ar, g.ai, g.br, g.bi, h->stream);
     st = cuda_check(cudaGetLastError(), "axpby launch");
@@ -746,8 +764,8 @@ ozk_status_t kkr_build_m(ozk_handle_t h, int L, int b, const void* t, const void
 // trailing update deferred to one GEMM with k = q - p.  DMMA path: one pivot block per panel.
 ozk_status_t kkr_tau00(ozk_handle_t h, int n, int b, void* Mv, const void* t0, void* tau, int S, int nb) {
   if (!h || !Mv || !t0 || !tau) return set_error(OZK_ERR_ARG, "null argument");
-  if (b <= 0 || n <= 0 || n % b || nb < b || nb % b || b > 16 || nb > (S > 0 ? 128 : 64))
-    return set_error(OZK_ERR_ARG, "need n % b == 0, b <= 16, b <= nb, nb % b == 0, nb <= 128 (64 for S <= 0)");
+  if (b <= 0 || n <= 0 || n % b || nb < b || nb % b || b > 64 || nb > (S > 0 ? 128 : 64))
+    return set_error(OZK_ERR_ARG, "need n % b == 0, b <= 64, b <= nb, nb % b == 0, nb <= 128 (64 for S <= 0)");
   double2* M = static_cast<double2*>(Mv);
   const size_t dinv_bytes = align_up(sizeof(double2) * nb * nb, 1024);
   {
@@ -844,26 +862,37 @@ ozk_status_t kkr_tau00(ozk_handle_t h, int n, int b, void* Mv, const void* t0, v
   return cuda_check(cudaGetLastError(), "kkr_tau00 launches");
 }
 
-ozk_status_t kkr_build_m_shared(ozk_handle_t h, int natoms, int L, int b, const void* const* t, const void* G,
-                                void* const* M, int S) {
-  if (!h || !t || !G || !M) return set_error(OZK_ERR_ARG, "null argument");
-  if (natoms < 0 || L < 1 || b < 1) return set_error(OZK_ERR_ARG, "need natoms >= 0, L >= 1, b >= 1");
-  if (S < 1 || S > 16) return set_error(OZK_ERR_ARG, "S must be in 1..16");
-  if (natoms == 0) return OZK_OK;
+// Shared-G build.  Lh (HOST, per atom) may be null: every atom has L sites and G has order L b;
+// otherwise atom a has Lh[a] sites, L = max Lh[a], and its G is the leading block of G (ld ldg).
+static ozk_status_t build_m_shared_impl(ozk_context* h, int natoms, const int* Lh, int L, int b,
+                                        const void* const* t, const void* G, int ldg, void* const* M, int S) {
   const long long rows = static_cast<long long>(natoms) * b, n = static_cast<long long>(L) * b;
   if (rows > (1 << 30) || n > (1 << 30)) return set_error(OZK_ERR_ARG, "sizes too large");
+  if (ldg < n) return set_error(OZK_ERR_ARG, "ldg smaller than the largest L b");
   // block row i of every atom's M: I - (t_{a,i} stacked over the atoms) G[ib:(i+1)b, :], one
   // emulated GEMM per i (m = natoms b, n = L b, k = b), the rows scattered back to the atoms
   const size_t stack_bytes = align_up(sizeof(double2) * static_cast<size_t>(L) * rows * b, 1024);
+  const int* dL = nullptr;
+  const int* dn = nullptr;
+  double sum_n2 = static_cast<double>(natoms) * n * n;       // useful outputs: sum of n_a^2
+  if (Lh) {
+    std::vector<int> nv(natoms);
+    sum_n2 = 0;
+    for (int a = 0; a < natoms; ++a) { nv[a] = Lh[a] * b; sum_n2 += static_cast<double>(nv[a]) * nv[a]; }
+    ozk_status_t st = size_table(h, std::vector<int>(Lh, Lh + natoms), &dL);
+    if (st) return st;
+    st = size_table(h, std::move(nv), &dn);
+    if (st) return st;
+  }
   EmuGemm g;
   g.oa = {0, 0}; g.ob = {0, 0}; g.batch = L;
   g.mmax = g.m = static_cast<int>(rows); g.nmax = g.n = static_cast<int>(n); g.kmax = g.k = b;
   g.lda = static_cast<int>(rows); g.zsA = rows * b;
-  g.B = static_cast<const double2*>(G); g.ldb = static_cast<int>(n); g.zsB = b;
+  g.B = static_cast<const double2*>(G); g.ldb = ldg; g.zsB = b;
   g.C = nullptr; g.ldc = static_cast<int>(n);
-  g.crow = reinterpret_cast<double2* const*>(M); g.crow_b = b;
+  g.crow = reinterpret_cast<double2* const*>(M); g.crow_b = b; g.crow_n = dn;
   g.mode = EPI_IMINUS; g.S = S;
-  g.sum_mnk = static_cast<double>(L) * rows * n * b;
+  g.sum_mnk = sum_n2 * b;
   g.sum_mk = static_cast<double>(L) * rows * b;
   g.sum_nk = static_cast<double>(L) * n * b;
   GemmPlan P;
@@ -875,20 +904,43 @@ ozk_status_t kkr_build_m_shared(ozk_handle_t h, int natoms, int L, int b, const 
   g.A = stack;
   {
     Prof pr(h, OZK_KIND_BUILD_M, 0.0, 32.0 * static_cast<double>(L) * rows * b);
-    launch_stack_t(reinterpret_cast<const double2* const*>(t), natoms, L, b, stack, h->stream);
+    launch_stack_t(reinterpret_cast<const double2* const*>(t), dL, natoms, L, b, stack, h->stream);
   }
   st = cuda_check(cudaGetLastError(), "stack_t launch");
   if (st) return st;
   return run_emulated(h, g, stack_bytes);
 }
 
-ozk_status_t kkr_tau00_batched(ozk_handle_t h, int nsolves, const int* n, int b, void* const* M, const void* const* t0,
-                               void* const* tau, int S, int nb) {
+ozk_status_t kkr_build_m_shared(ozk_handle_t h, int natoms, int L, int b, const void* const* t, const void* G,
+                                void* const* M, int S) {
+  if (!h || !t || !G || !M) return set_error(OZK_ERR_ARG, "null argument");
+  if (natoms < 0 || L < 1 || b < 1) return set_error(OZK_ERR_ARG, "need natoms >= 0, L >= 1, b >= 1");
+  if (S < 1 || S > 16) return set_error(OZK_ERR_ARG, "S must be in 1..16");
+  if (natoms == 0) return OZK_OK;
+  return build_m_shared_impl(h, natoms, nullptr, L, b, t, G, L * b, M, S);
+}
+
+ozk_status_t kkr_build_m_shared_sizes(ozk_handle_t h, int natoms, const int* L, int b, const void* const* t,
+                                      const void* G, int ldg, void* const* M, int S) {
+  if (!h || !L || !t || !G || !M) return set_error(OZK_ERR_ARG, "null argument");
+  if (natoms < 0 || b < 1) return set_error(OZK_ERR_ARG, "need natoms >= 0, b >= 1");
+  if (S < 1 || S > 16) return set_error(OZK_ERR_ARG, "S must be in 1..16");
+  if (natoms == 0) return OZK_OK;
+  int Lmax = 0;
+  for (int a = 0; a < natoms; ++a) {
+    if (L[a] < 1) return set_error(OZK_ERR_ARG, "every L[a] must be >= 1");
+    Lmax = std::max(Lmax, L[a]);
+  }
+  return build_m_shared_impl(h, natoms, L, Lmax, b, t, G, ldg, M, S);
+}
+
+static ozk_status_t tau00_batched_impl(ozk_handle_t h, int nsolves, const int* n, int b, void* const* M,
+                                       const void* const* t0, void* const* tau, int S, int nb) {
   if (!h || !n || !M || !t0 || !tau) return set_error(OZK_ERR_ARG, "null argument");
   if (nsolves < 0) return set_error(OZK_ERR_ARG, "negative nsolves");
   if (nsolves == 0) return OZK_OK;
   if (S <= 0) return set_error(OZK_ERR_ARG, "batched solves run the emulated path (S >= 1)");
-  if (b <= 0 || b > 16 || nb < b || nb % b || nb > 128) return set_error(OZK_ERR_ARG, "need b <= 16, b <= nb <= 128, nb % b == 0");
+  if (b <= 0 || b > 64 || nb < b || nb % b || nb > 128) return set_error(OZK_ERR_ARG, "need b <= 64, b <= nb <= 128, nb % b == 0");
   int nmax = 0;
   for (int i = 0; i < nsolves; ++i) {
     if (n[i] <= 0 || n[i] % b) return set_error(OZK_ERR_ARG, "every n[i] must be a positive multiple of b");
@@ -928,7 +980,7 @@ ozk_status_t kkr_tau00_batched(ozk_handle_t h, int nsolves, const int* n, int b,
   double2* const* Mp = reinterpret_cast<double2* const*>(M);
 
   auto gemm_tables = [&](int which, int mmax, int nmaxg, int kmax, double smnk, double smk, double snk,
-                         bool lu, bool skip) -> ozk_status_t {
+                         bool lu, bool skip, int box = 0) -> ozk_status_t {
     EmuGemm g;
     g.oa = {0, 0}; g.ob = {0, 0}; g.batch = nsolves; g.mmax = mmax; g.nmax = nmaxg; g.kmax = kmax; g.S = S;
     if (which == 1) {
@@ -937,7 +989,7 @@ ozk_status_t kkr_tau00_batched(ozk_handle_t h, int nsolves, const int* n, int b,
     } else {
       g.tA = t.A2; g.tlda = t.lda2; g.tB = t.B2; g.tldb = t.ldb2; g.tC = t.C2; g.tldc = t.ldc2;
       g.tm = t.m2; g.tn = t.n2; g.tk = t.k2;
-      if (skip) { g.tskm = t.skm2; g.tskn = t.skn2; }
+      if (skip) { g.tskm = t.skm2; g.tskn = t.skn2; g.box_m = box; g.box_n = box; }
     }
     g.ar = lu ? -1 : 1; g.br = lu ? 1 : 0;
     g.sum_mnk = smnk; g.sum_mk = smk; g.sum_nk = snk;
@@ -946,7 +998,7 @@ ozk_status_t kkr_tau00_batched(ozk_handle_t h, int nsolves, const int* n, int b,
 
   for (int s = 0; s < panels; ++s) {
     for (int l = 0; l < leaves; ++l) {
-      int amax = 0, a2max = 0, nact = 0;
+      int amax = 0, a2max = 0, nact = 0, pmin = 1 << 30;
       double s1 = 0, s2 = 0, sa = 0;
       for (int i = 0; i < nsolves; ++i) {
         const int q = n[i] - s * nb;
@@ -958,7 +1010,11 @@ ozk_status_t kkr_tau00_batched(ozk_handle_t h, int nsolves, const int* n, int b,
         amax = std::max(amax, a);
         s1 += static_cast<double>(a) * b * b;
         sa += static_cast<double>(a) * b;
-        if (a > p) { a2max = std::max(a2max, a); s2 += (static_cast<double>(a) * a - static_cast<double>(p) * p) * b; }
+        if (a > p) {
+          a2max = std::max(a2max, a);
+          pmin = std::min(pmin, p);
+          s2 += (static_cast<double>(a) * a - static_cast<double>(p) * p) * b;
+        }
       }
       if (nact == 0) continue;
       {
@@ -975,7 +1031,7 @@ ozk_status_t kkr_tau00_batched(ozk_handle_t h, int nsolves, const int* n, int b,
       st = gemm_tables(1, amax, b, b, s1, sa, nact * static_cast<double>(b) * b, false, false);
       if (st) return st;
       if (a2max > 0) {
-        st = gemm_tables(2, a2max, a2max, b, s2, sa, sa, true, true);
+        st = gemm_tables(2, a2max, a2max, b, s2, sa, sa, true, true, pmin);
         if (st) return st;
       }
     }
@@ -1179,6 +1235,160 @@ ozk_status_t ozk_rel_diff(ozk_handle_t h, int m, int n, const void* X, int ldx, 
   st = cuda_check(cudaGetLastError(), "rel diff launches");
   if (st) return st;
   st = cuda_check(cudaMemcpyAsync(rel, out, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "read rel diff");
+  if (st) return st;
+  return cuda_check(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+}
+
+static std::vector<int> tune_key(int nsolves, const int* n, int b, int S) {
+  std::vector<int> key(n, n + nsolves);
+  key.push_back(b);
+  key.push_back(S);
+  return key;
+}
+
+ozk_status_t kkr_tau00_autotune(ozk_handle_t h, int nsolves, const int* n, int b, int S, int* nb_best, float* times) {
+  if (!h || !n || !nb_best) return set_error(OZK_ERR_ARG, "null argument");
+  if (nsolves < 1 || S < 1 || b < 1 || b > 64) return set_error(OZK_ERR_ARG, "need nsolves >= 1, S >= 1, 1 <= b <= 64");
+  if (capturing(h->stream)) return set_error(OZK_ERR_CAPTURE, "autotuning times launches and cannot be captured");
+  size_t total = 0;
+  for (int i = 0; i < nsolves; ++i) {
+    if (n[i] <= 0 || n[i] % b) return set_error(OZK_ERR_ARG, "every n[i] must be a positive multiple of b");
+    total += static_cast<size_t>(n[i]) * n[i];
+  }
+  // scratch: diagonally dominant test matrices (timings do not depend on the values, but the
+  // pivot blocks must be regular), a t_0, the outputs and the pointer arrays
+  void* mem = nullptr;
+  const size_t mbytes = align_up(sizeof(double2) * total, 256);
+  const size_t tbytes = align_up(sizeof(double2) * static_cast<size_t>(b) * b * (nsolves + 1), 256);
+  const size_t pbytes = align_up(3 * sizeof(void*) * static_cast<size_t>(nsolves), 256);
+  ozk_status_t st = cuda_check(cudaMalloc(&mem, mbytes + tbytes + pbytes), "cudaMalloc(autotune scratch)");
+  if (st) return st;
+  double2* Mall = static_cast<double2*>(mem);
+  double2* tall = reinterpret_cast<double2*>(static_cast<uint8_t*>(mem) + mbytes);
+  void** ptrs = reinterpret_cast<void**>(static_cast<uint8_t*>(mem) + mbytes + tbytes);
+  std::vector<void*> hp(3 * static_cast<size_t>(nsolves));
+  size_t off = 0;
+  for (int i = 0; i < nsolves; ++i) {
+    hp[i] = Mall + off;
+    off += static_cast<size_t>(n[i]) * n[i];
+    hp[nsolves + i] = tall;                                           // shared t_0
+    hp[2 * static_cast<size_t>(nsolves) + i] = tall + static_cast<size_t>(b) * b * (i + 1);
+  }
+  const int* dn = nullptr;
+  st = size_table(h, std::vector<int>(n, n + nsolves), &dn);
+  if (!st) st = cuda_check(cudaMemcpyAsync(ptrs, hp.data(), sizeof(void*) * hp.size(), cudaMemcpyHostToDevice, h->stream),
+                           "upload autotune pointers");
+  std::vector<int> cands;
+  for (int nb = b; nb <= 128; nb += b) cands.push_back(nb);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (!st) st = cuda_check(cudaEventCreate(&e0), "cudaEventCreate");
+  if (!st) st = cuda_check(cudaEventCreate(&e1), "cudaEventCreate");
+  float best = 0.0f;
+  int best_nb = 0;
+  const bool prof = h->prof;
+  h->prof = false;                                                    // tuning runs are not profiled
+  for (size_t c = 0; c < cands.size() && !st; ++c) {
+    float ms = 0.0f;
+    for (int rep = 0; rep < 2 && !st; ++rep) {                        // warm run, then the timed one
+      launch_fill_test(reinterpret_cast<double2* const*>(ptrs), dn, nsolves, b, tall, h->stream);
+      cudaEventRecord(e0, h->stream);
+      st = tau00_batched_impl(h, nsolves, n, b, ptrs, reinterpret_cast<const void* const*>(ptrs + nsolves),
+                              ptrs + 2 * nsolves, S, cands[c]);
+      cudaEventRecord(e1, h->stream);
+      if (!st) st = cuda_check(cudaEventSynchronize(e1), "cudaEventSynchronize");
+      if (!st) st = cuda_check(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+    }
+    if (st) break;
+    if (times) times[c] = ms;
+    if (best_nb == 0 || ms < best) { best = ms; best_nb = cands[c]; }
+  }
+  h->prof = prof;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(h->stream);
+  cudaFree(mem);
+  if (st) return st;
+  h->tuned_nb[tune_key(nsolves, n, b, S)] = best_nb;
+  *nb_best = best_nb;
+  return OZK_OK;
+}
+
+// S = 0 for a batched solve: the selector's choice for the operands of solve 0's first
+// trailing update (the L panel M[0:p, p:q] and the U panel M[p:q, 0:p] of the unfactored M,
+// q = n_0, p = max(q - nb, b)), made once for the whole call.
+static ozk_status_t select_S_for_solves(ozk_context* h, void* const* M, const int* n, int b, int nb, int* S_out) {
+  if (!h->sel_ready)
+    return set_error(OZK_ERR_ARG, "S = 0 needs selector parameters (ozk_selector_init, _load or _set_params)");
+  if (capturing(h->stream)) return set_error(OZK_ERR_CAPTURE, "S = 0 reads the selector's choice and cannot be captured");
+  void* m0 = nullptr;
+  ozk_status_t st = cuda_check(cudaMemcpy(&m0, M, sizeof(void*), cudaMemcpyDeviceToHost), "read M[0]");
+  if (st) return st;
+  const int n0 = n[0];
+  const int q = n0, p = std::max(q - (nb > 0 ? nb : 64), b);
+  if (q <= b || p <= 0) { *S_out = SEL_SMAX; return OZK_OK; }
+  const double2* M0 = static_cast<const double2*>(m0);
+  SelScratch sc;
+  st = sel_scratch(h, p, p, q - p, false, &sc);
+  if (st) return st;
+  ozk_selector_info info{};
+  info.probe_seed = h->sel_seed + h->sel_calls++;
+  st = sel_features(h, OpFlags{0, 0}, OpFlags{0, 0}, p, p, q - p, M0 + static_cast<long long>(p) * n0, n0, M0 + p, n0,
+                    info.probe_seed, sc);
+  if (st) return st;
+  launch_mlp_forward(h->sel_p, sc.f, 1, nullptr, nullptr, sc.Y, h->stream);
+  launch_choose(sc.Y, static_cast<float>(std::log10(h->sel_tol) - h->sel_margin), sc.aux, h->stream);
+  SelAux aux;
+  st = read_aux(h, sc.aux, &aux);
+  if (st) return st;
+  info.S_selected = info.S_used = aux.S;
+  info.residual = info.residual_selected = -1.0;      // no per-GEMM check on the batched path
+  for (int o = 0; o < SEL_NO; ++o) info.predicted_log10_err[o] = aux.pred[o];
+  h->sel_last = info;
+  *S_out = aux.S;
+  return OZK_OK;
+}
+
+ozk_status_t kkr_tau00_batched(ozk_handle_t h, int nsolves, const int* n, int b, void* const* M, const void* const* t0,
+                               void* const* tau, int S, int nb) {
+  if (!h || !n) return set_error(OZK_ERR_ARG, "null argument");
+  if (S == 0 && nsolves > 0) {
+    if (!M || n[0] <= 0) return set_error(OZK_ERR_ARG, "bad solve 0");
+    ozk_status_t st = select_S_for_solves(h, M, n, b, nb, &S);
+    if (st) return st;
+  }
+  if (nb == 0 && nsolves > 0) {
+    auto it = h->tuned_nb.find(tune_key(nsolves, n, b, S));
+    if (it != h->tuned_nb.end()) {
+      nb = it->second;
+    } else {
+      ozk_status_t st = kkr_tau00_autotune(h, nsolves, n, b, S, &nb, nullptr);
+      if (st) return st;
+    }
+  }
+  return tau00_batched_impl(h, nsolves, n, b, M, t0, tau, S, nb);
+}
+
+ozk_status_t kkr_contour_trace(ozk_handle_t h, int nsolves, int b, const void* const* tau, const double* w,
+                               double* traces, double* integral) {
+  if (!h || !tau || !w || !integral) return set_error(OZK_ERR_ARG, "null argument");
+  if (nsolves < 1 || b < 1) return set_error(OZK_ERR_ARG, "need nsolves >= 1 and b >= 1");
+  const size_t wb = align_up(sizeof(double2) * nsolves, 256);
+  ozk_status_t st = ensure_sel_ws(h, 3 * wb + 256);
+  if (st) return st;
+  uint8_t* base = static_cast<uint8_t*>(h->sel_ws);
+  double2* dw = reinterpret_cast<double2*>(base);
+  double2* tr = reinterpret_cast<double2*>(base + wb);
+  double2* out = reinterpret_cast<double2*>(base + 2 * wb);
+  st = cuda_check(cudaMemcpyAsync(dw, w, sizeof(double2) * nsolves, cudaMemcpyHostToDevice, h->stream), "upload weights");
+  if (st) return st;
+  launch_contour_trace(reinterpret_cast<const double2* const*>(tau), nsolves, b, dw, tr, out, h->stream);
+  st = cuda_check(cudaGetLastError(), "contour trace launches");
+  if (st) return st;
+  if (traces) {
+    st = cuda_check(cudaMemcpyAsync(traces, tr, sizeof(double2) * nsolves, cudaMemcpyDeviceToHost, h->stream), "read traces");
+    if (st) return st;
+  }
+  st = cuda_check(cudaMemcpyAsync(integral, out, sizeof(double2), cudaMemcpyDeviceToHost, h->stream), "read integral");
   if (st) return st;
   return cuda_check(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
 }

@@ -271,7 +271,7 @@ void launch_build_m_batched(const int* L, int b, const double2* const* t, const 
 
 // Stacked left operands of the shared-G build: problem i is the (natoms b) x b column-major
 // matrix whose rows a b .. a b + b - 1 are t_a's block i (t_a: L column-major b x b blocks).
-__global__ void stack_t_kernel(const double2* const* t, int natoms, int L, int b, double2* out) {
+__global__ void stack_t_kernel(const double2* const* t, const int* Lt, int natoms, int L, int b, double2* out) {
   const long long rows = static_cast<long long>(natoms) * b, per = rows * b;
   const long long tot = per * L;
   for (long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; idx < tot;
@@ -281,14 +281,78 @@ __global__ void stack_t_kernel(const double2* const* t, int natoms, int L, int b
     const int c = static_cast<int>(rem / rows);
     const int ar = static_cast<int>(rem - c * rows);
     const int a = ar / b, r = ar - a * b;
-    out[idx] = t[a][static_cast<long long>(i) * b * b + r + static_cast<long long>(c) * b];
+    // block rows past an atom's own LIZ are zero (that atom's rows of the product are not kept)
+    out[idx] = (Lt && i >= Lt[a]) ? make_double2(0.0, 0.0)
+                                  : t[a][static_cast<long long>(i) * b * b + r + static_cast<long long>(c) * b];
   }
 }
 
-void launch_stack_t(const double2* const* t, int natoms, int L, int b, double2* out, cudaStream_t st) {
+// Traces of the b x b blocks tau[i] (column major) and their weighted sum sum_i w_i Tr tau_i:
+// one warp per block for the traces, then one block sums the products in order.
+__global__ void trace_kernel(const double2* const* tau, int nsolves, int b, double2* tr) {
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (i >= nsolves) return;
+  double re = 0.0, im = 0.0;
+  for (int d = lane; d < b; d += 32) {
+    const double2 v = tau[i][d + static_cast<long long>(d) * b];
+    re += v.x;
+    im += v.y;
+  }
+  for (int o = 16; o; o >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, o);
+    im += __shfl_xor_sync(0xffffffffu, im, o);
+  }
+  if (lane == 0) tr[i] = make_double2(re, im);
+}
+
+__global__ void weighted_sum_kernel(const double2* tr, const double2* w, int nsolves, double2* out) {
+  if (threadIdx.x || blockIdx.x) return;
+  double re = 0.0, im = 0.0;
+  for (int i = 0; i < nsolves; ++i) {
+    re += w[i].x * tr[i].x - w[i].y * tr[i].y;
+    im += w[i].x * tr[i].y + w[i].y * tr[i].x;
+  }
+  *out = make_double2(re, im);
+}
+
+void launch_contour_trace(const double2* const* tau, int nsolves, int b, const double2* w, double2* tr, double2* out,
+                          cudaStream_t st) {
+  trace_kernel<<<(nsolves * 32 + 255) / 256, 256, 0, st>>>(tau, nsolves, b, tr);
+  record_launch();
+  weighted_sum_kernel<<<1, 32, 0, st>>>(tr, w, nsolves, out);
+  record_launch();
+}
+
+// Test matrices of the autotuner: M_i = I + off-diagonal entries of magnitude < 0.25 / n_i
+// (a fixed integer hash), strictly diagonally dominant so every pivot block is regular; t_0 = I.
+__global__ void fill_test_kernel(double2* const* M, const int* n, int b, double2* t0) {
+  const int z = blockIdx.y;
+  const int ni = n[z];
+  const long long tot = static_cast<long long>(ni) * ni;
+  for (long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; idx < tot;
+       idx += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int r = static_cast<int>(idx % ni), c = static_cast<int>(idx / ni);
+    unsigned h = static_cast<unsigned>(r) * 2654435761u ^ static_cast<unsigned>(c) * 40503u;
+    h ^= h >> 15;
+    h *= 2246822519u;
+    h ^= h >> 13;
+    const double u = (static_cast<double>(h & 0xFFFF) / 65536.0 - 0.5) * (0.5 / ni);
+    const double w = (static_cast<double>((h >> 16) & 0xFFFF) / 65536.0 - 0.5) * (0.5 / ni);
+    M[z][idx] = r == c ? make_double2(1.0, 0.0) : make_double2(u, w);
+  }
+  if (z == 0 && blockIdx.x == 0)
+    for (int i = threadIdx.x; i < b * b; i += blockDim.x) t0[i] = make_double2(i % (b + 1) == 0 ? 1.0 : 0.0, 0.0);
+}
+
+void launch_fill_test(double2* const* M, const int* n, int nsolves, int b, double2* t0, cudaStream_t st) {
+  fill_test_kernel<<<dim3(1024, nsolves), 256, 0, st>>>(M, n, b, t0);
+  record_launch();
+}
+
+void launch_stack_t(const double2* const* t, const int* Lt, int natoms, int L, int b, double2* out, cudaStream_t st) {
   const long long tot = static_cast<long long>(natoms) * b * b * L;
   const unsigned blocks = static_cast<unsigned>(std::min<long long>((tot + 255) / 256, 8192));
-  stack_t_kernel<<<blocks, 256, 0, st>>>(t, natoms, L, b, out);
+  stack_t_kernel<<<blocks, 256, 0, st>>>(t, Lt, natoms, L, b, out);
   record_launch();
 }
 

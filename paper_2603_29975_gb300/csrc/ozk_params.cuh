@@ -49,6 +49,9 @@ struct GemmParams {
   // skip box: outputs with row < skm and complex column < skn are neither computed (whole
   // tiles) nor written (per element); per problem (skm, skn) or single values (skm1, skn1)
   const int* skm; const int* skn; int skm1, skn1;
+  // smallest skip box over the problems (host hint, 0 = none) and the resulting number of
+  // tiles enumerated per problem (set by the launcher): only tiles not wholly inside a box
+  int box_m, box_n, tpp;
   double ar, ai, br, bi;  // alpha, beta
   const int* m;           // per problem rows of C
   const int* n;           // per problem complex columns of C
@@ -62,8 +65,9 @@ struct GemmParams {
   // single-problem values, used when m == nullptr (no device tables needed)
   int m1, n1; double2* C1; int ldc1;
   // row-block scatter (crow != nullptr): row r of problem z is row z crow_b + r % crow_b of
-  // the output crow[r / crow_b] (leading dimension ldc1)
-  double2* const* crow; int crow_b;
+  // the output crow[r / crow_b], whose order and leading dimension are crow_n[r / crow_b]
+  // (or ldc1 for every output when crow_n is null); rows past that order are not written
+  double2* const* crow; int crow_b; const int* crow_n;
   uint8_t ps[MAX_PAIRS], pt[MAX_PAIRS], pg[MAX_PAIRS], pfirst[MAX_PAIRS];
 };
 void launch_slice_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const GemmParams& p, int BN,
@@ -100,7 +104,11 @@ void launch_build_m(int n, int b, const double2* t, const double2* G, double2* M
 void launch_build_m_batched(const int* L, int b, const double2* const* t, const double2* const* G, double2* const* M,
                             int nmax, int batch, cudaStream_t st);
 void launch_scale(int m, int n, double2* C, long long ldc, double br, double bi, cudaStream_t st);
-void launch_stack_t(const double2* const* t, int natoms, int L, int b, double2* out, cudaStream_t st);
+// Lt (device, per atom block counts) may be null: every atom has L blocks
+void launch_stack_t(const double2* const* t, const int* Lt, int natoms, int L, int b, double2* out, cudaStream_t st);
+void launch_fill_test(double2* const* M, const int* n, int nsolves, int b, double2* t0, cudaStream_t st);
+void launch_contour_trace(const double2* const* tau, int nsolves, int b, const double2* w, double2* tr, double2* out,
+                          cudaStream_t st);
 
 // Per-step tables of the batched tau_00 driver, filled on the device for step `step`.
 struct KkrStep {
@@ -119,7 +127,7 @@ void launch_kkr_step(int step, int leaf, int nsolves, const int* n, double2* con
 
 // ---- selector.cu: slice-count selector (features, probes, residual check, perceptron)
 constexpr int SEL_NF = OZK_SEL_FEATURES, SEL_NH = 64, SEL_NO = OZK_SEL_OUTPUTS;
-constexpr int SEL_SMIN = OZK_SEL_SMIN, SEL_SMAX = OZK_SEL_SMAX, SEL_PROBES = 2;
+constexpr int SEL_SMIN = OZK_SEL_SMIN, SEL_SMAX = OZK_SEL_SMAX, SEL_PROBES = 4;
 constexpr int SEL_NPARAMS = OZK_SEL_NPARAMS;
 static_assert(SEL_NPARAMS == SEL_NH * SEL_NF + SEL_NH + SEL_NH * SEL_NH + SEL_NH + SEL_NO * SEL_NH + SEL_NO,
               "selector parameter count");
@@ -131,12 +139,16 @@ void launch_probe(double2* X, int n, const SelBases& b, cudaStream_t st);
 void launch_vec_stats(const double2* M, long long ld, int count, int len, bool contiguous, const SelVecStats& out,
                       cudaStream_t st);
 void launch_max_exp(const SelVecStats& a, int ma, const SelVecStats& b, int nb, int* ex, cudaStream_t st);
-// op: 0 = rows of M (strided), 1 = columns of M, 2 = conjugated columns of M
-void launch_gemv(const double2* M, long long ld, int rows, int len, int op, const double2* X, int ldx, double2* Y,
-                 int ldy, const int* ex, int eidx, cudaStream_t st);
+// Y = (2^-E op(M)) X in double-double (Yh + Yl, ld rows; Xl may be null), compensated sums.
+// op: 0 = rows of M (strided; uses `part`, gemv_chunks(len) x SEL_PROBES x rows x 2 double2),
+// 1 = columns of M, 2 = conjugated columns of M
+int gemv_chunks(int len);
+void launch_gemv(const double2* M, long long ld, int rows, int len, int op, const double2* Xh, const double2* Xl,
+                 int ldx, double2* Yh, double2* Yl, double2* part, const int* ex, int eidx, cudaStream_t st);
 void launch_selector_features(const SelVecStats& a, int m, const SelVecStats& b, int n, int k, const double2* X,
                               const double2* zs, const int* ex, float* f, SelAux* aux, cudaStream_t st);
-void launch_residual(const double2* W, const double2* zs, int m, SelAux* aux, cudaStream_t st);
+void launch_residual(const double2* Wh, const double2* Wl, const double2* zh, const double2* zl, int m, SelAux* aux,
+                     cudaStream_t st);
 void launch_rel_diff(int m, int n, const double2* X, long long ldx, const double2* Y, long long ldy, double* part,
                      double* out, cudaStream_t st);
 void launch_axpby(int m, int n, const double2* D, long long ldd, double2* C, long long ldc, double ar, double ai,

@@ -16,6 +16,8 @@
 // W1[64][16], b1[64], W2[64][64], b2[64], W3[8][64], b3[8].
 #include <math.h>
 
+#include <algorithm>
+
 #include "ozk_params.cuh"
 
 namespace ozk {
@@ -150,62 +152,133 @@ __global__ void max_exp_kernel(SelVecStats a, int ma, SelVecStats b, int nb, int
   }
 }
 
-// ------------------------------------------------------------------ small complex GEMV
-// Y (rows x SEL_PROBES) = (2^-E op(M)) X, E = ex[eidx] (no scaling when ex == nullptr), with
-// op(M) rows x len, M column major.  trans == 0: thread per row; else warp per row.
-__global__ void gemv_rows_kernel(const double2* M, long long ld, int rows, int len, const double2* X, int ldx,
-                                 double2* Y, int ldy, const int* ex, int eidx) {
+// ------------------------------------------------------------------ compensated complex GEMV
+// Y (rows x SEL_PROBES) = (2^-E op(M)) X with X = Xh + Xl given as a double-double (Xl may be
+// null) and Y returned as a double-double Yh + Yl.  The sums use the compensated dot product
+// of Ogita, Rump and Oishi ("Accurate sum and dot product", SIAM J. Sci. Comput. 2005): every
+// product is split exactly by an FMA, every addition by the error-free two-sum, and the
+// errors are summed separately, so the result is as accurate as a computation in twice the
+// working precision.  The intrinsics keep the compiler from contracting the error-free steps.
+__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
+  s = __dadd_rn(a, b);
+  const double bb = __dsub_rn(s, a);
+  e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+}
+
+// (s, c) += a * b
+__device__ __forceinline__ void dot2(double& s, double& c, double a, double b) {
+  const double p = __dmul_rn(a, b);
+  const double e = __fma_rn(a, b, -p);
+  double q;
+  two_sum(s, p, s, q);
+  c = __dadd_rn(c, __dadd_rn(q, e));
+}
+
+// (s, c) += (sb, cb)
+__device__ __forceinline__ void dd_add(double& s, double& c, double sb, double cb) {
+  double q;
+  two_sum(s, sb, s, q);
+  c = __dadd_rn(c, __dadd_rn(q, cb));
+}
+
+// complex accumulators (re: s, c; im: s, c) for one probe
+struct CAcc { double rs, rc, is, ic; };
+
+// acc += a * (xh + xl) for complex a and double-double x
+__device__ __forceinline__ void cmac(CAcc& A, double ar, double ai, double2 xh, double2 xl) {
+  dot2(A.rs, A.rc, ar, xh.x);
+  dot2(A.rs, A.rc, -ai, xh.y);
+  dot2(A.is, A.ic, ar, xh.y);
+  dot2(A.is, A.ic, ai, xh.x);
+  A.rc = __fma_rn(ar, xl.x, A.rc);
+  A.rc = __fma_rn(-ai, xl.y, A.rc);
+  A.ic = __fma_rn(ar, xl.y, A.ic);
+  A.ic = __fma_rn(ai, xl.x, A.ic);
+}
+
+// normalised double-double of an accumulator
+__device__ __forceinline__ void cacc_out(const CAcc& A, double2& h, double2& l) {
+  double e;
+  two_sum(A.rs, A.rc, h.x, e);
+  l.x = e;
+  two_sum(A.is, A.ic, h.y, e);
+  l.y = e;
+}
+
+constexpr int GEMV_CHUNK = 64;
+
+// op(M) = M (rows strided): grid.x over blocks of 64 rows, grid.y over chunks of GEMV_CHUNK of
+// the reduction; each thread writes its row's partial double-doubles of its chunk.
+__global__ void gemv_rows_kernel(const double2* M, long long ld, int rows, int len, const double2* Xh,
+                                 const double2* Xl, int ldx, double2* part, const int* ex, int eidx) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows) return;
   const int E = ex ? ex[eidx] : 0;
-  double2 acc[SEL_PROBES];
+  const int l0 = blockIdx.y * GEMV_CHUNK, l1 = min(len, l0 + GEMV_CHUNK);
+  CAcc acc[SEL_PROBES];
 #pragma unroll
-  for (int p = 0; p < SEL_PROBES; ++p) acc[p] = make_double2(0.0, 0.0);
-  for (int l = 0; l < len; ++l) {
-    double2 a = M[i + l * ld];
-    a.x = ldexp(a.x, -E);
-    a.y = ldexp(a.y, -E);
+  for (int q = 0; q < SEL_PROBES; ++q) acc[q] = CAcc{0.0, 0.0, 0.0, 0.0};
+  for (int l = l0; l < l1; ++l) {
+    const double2 a = M[i + l * ld];
+    const double ar = ldexp(a.x, -E), ai = ldexp(a.y, -E);
 #pragma unroll
-    for (int p = 0; p < SEL_PROBES; ++p) {
-      const double2 x = X[l + p * ldx];
-      acc[p].x += a.x * x.x - a.y * x.y;
-      acc[p].y += a.x * x.y + a.y * x.x;
-    }
+    for (int q = 0; q < SEL_PROBES; ++q)
+      cmac(acc[q], ar, ai, Xh[l + q * ldx], Xl ? Xl[l + q * ldx] : make_double2(0.0, 0.0));
   }
+  // part[chunk][q][row] as (s re, s im) then (c re, c im)
+  const long long base = static_cast<long long>(blockIdx.y) * SEL_PROBES * rows;
 #pragma unroll
-  for (int p = 0; p < SEL_PROBES; ++p) Y[i + p * ldy] = acc[p];
+  for (int q = 0; q < SEL_PROBES; ++q) {
+    const long long o = 2 * (base + static_cast<long long>(q) * rows + i);
+    part[o] = make_double2(acc[q].rs, acc[q].is);
+    part[o + 1] = make_double2(acc[q].rc, acc[q].ic);
+  }
 }
 
-__global__ void gemv_cols_kernel(const double2* M, long long ld, int rows, int len, int conj, const double2* X,
-                                 int ldx, double2* Y, int ldy, const int* ex, int eidx) {
+// sum the chunks of gemv_rows_kernel in order: Y = Yh + Yl (rows x SEL_PROBES, ld rows)
+__global__ void gemv_reduce_kernel(const double2* part, int rows, int nchunks, double2* Yh, double2* Yl) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rows * SEL_PROBES) return;
+  CAcc A{0.0, 0.0, 0.0, 0.0};
+  for (int c = 0; c < nchunks; ++c) {
+    const long long o = 2 * (static_cast<long long>(c) * SEL_PROBES * rows + idx);
+    const double2 sv = part[o], cv = part[o + 1];
+    dd_add(A.rs, A.rc, sv.x, cv.x);
+    dd_add(A.is, A.ic, sv.y, cv.y);
+  }
+  cacc_out(A, Yh[idx], Yl[idx]);
+}
+
+// op(M) = M^T or M^H (row i of op(M) is column i of M, contiguous): one warp per row
+__global__ void gemv_cols_kernel(const double2* M, long long ld, int rows, int len, int conj, const double2* Xh,
+                                 const double2* Xl, int ldx, double2* Yh, double2* Yl, int ldy, const int* ex,
+                                 int eidx) {
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= rows) return;
   const int E = ex ? ex[eidx] : 0;
   const double2* col = M + w * ld;
-  double2 acc[SEL_PROBES];
+  CAcc acc[SEL_PROBES];
 #pragma unroll
-  for (int p = 0; p < SEL_PROBES; ++p) acc[p] = make_double2(0.0, 0.0);
+  for (int q = 0; q < SEL_PROBES; ++q) acc[q] = CAcc{0.0, 0.0, 0.0, 0.0};
   for (int l = lane; l < len; l += 32) {
-    double2 a = col[l];
-    a.x = ldexp(a.x, -E);
-    a.y = conj ? -ldexp(a.y, -E) : ldexp(a.y, -E);
+    const double2 a = col[l];
+    const double ar = ldexp(a.x, -E), ai = conj ? -ldexp(a.y, -E) : ldexp(a.y, -E);
 #pragma unroll
-    for (int p = 0; p < SEL_PROBES; ++p) {
-      const double2 x = X[l + p * ldx];
-      acc[p].x += a.x * x.x - a.y * x.y;
-      acc[p].y += a.x * x.y + a.y * x.x;
-    }
+    for (int q = 0; q < SEL_PROBES; ++q)
+      cmac(acc[q], ar, ai, Xh[l + q * ldx], Xl ? Xl[l + q * ldx] : make_double2(0.0, 0.0));
   }
 #pragma unroll
-  for (int p = 0; p < SEL_PROBES; ++p)
+  for (int q = 0; q < SEL_PROBES; ++q)
     for (int o = 16; o; o >>= 1) {
-      acc[p].x += __shfl_xor_sync(0xffffffffu, acc[p].x, o);
-      acc[p].y += __shfl_xor_sync(0xffffffffu, acc[p].y, o);
+      const double rs = __shfl_xor_sync(0xffffffffu, acc[q].rs, o), rc = __shfl_xor_sync(0xffffffffu, acc[q].rc, o);
+      const double is = __shfl_xor_sync(0xffffffffu, acc[q].is, o), ic = __shfl_xor_sync(0xffffffffu, acc[q].ic, o);
+      dd_add(acc[q].rs, acc[q].rc, rs, rc);
+      dd_add(acc[q].is, acc[q].ic, is, ic);
     }
   if (lane == 0)
 #pragma unroll
-    for (int p = 0; p < SEL_PROBES; ++p) Y[w + p * ldy] = acc[p];
+    for (int q = 0; q < SEL_PROBES; ++q) cacc_out(acc[q], Yh[w + q * ldy], Yl[w + q * ldy]);
 }
 
 // ------------------------------------------------------------------ feature reduction
@@ -301,6 +374,7 @@ __device__ CrestStats crest_stats(const SelVecStats v, int count, int k, int Ema
 __global__ void __launch_bounds__(RED_T) selector_features_kernel(SelVecStats a, int m, SelVecStats b, int n, int k,
                                                                   const double2* X, const double2* zs, const int* ex,
                                                                   float* f, SelAux* aux) {
+  // zs: the leading parts of the double-double probe product
   __shared__ double sh[RED_T];
   const int EA = ex[0], EB = ex[1];
   const CrestStats ca = crest_stats(a, m, k, EA, sh);
@@ -342,15 +416,21 @@ __global__ void __launch_bounds__(RED_T) selector_features_kernel(SelVecStats a,
   }
 }
 
-// residual: r^2 = ||2^-E W - zs||^2 / ||zs||^2 with W = D X (m x SEL_PROBES)
-__global__ void __launch_bounds__(RED_T) residual_kernel(const double2* W, const double2* zs, int m, SelAux* aux) {
+// residual: r^2 = ||2^-E W - zs||^2 / ||zs||^2 with W = D X (m x SEL_PROBES), both
+// double-doubles, the difference formed before it is rounded
+__global__ void __launch_bounds__(RED_T) residual_kernel(const double2* Wh, const double2* Wl, const double2* zh,
+                                                         const double2* zl, int m, SelAux* aux) {
   __shared__ double sh[RED_T];
   const int E = aux->E;
   double num = 0, den = 0;
   for (int i = threadIdx.x; i < m * SEL_PROBES; i += RED_T) {
-    const double dx = ldexp(W[i].x, -E) - zs[i].x, dy = ldexp(W[i].y, -E) - zs[i].y;
+    double dx, ex, dy, ey;
+    two_sum(ldexp(Wh[i].x, -E), -zh[i].x, dx, ex);
+    two_sum(ldexp(Wh[i].y, -E), -zh[i].y, dy, ey);
+    dx = dx + (ex + (ldexp(Wl[i].x, -E) - zl[i].x));
+    dy = dy + (ey + (ldexp(Wl[i].y, -E) - zl[i].y));
     num += dx * dx + dy * dy;
-    den += zs[i].x * zs[i].x + zs[i].y * zs[i].y;
+    den += zh[i].x * zh[i].x + zh[i].y * zh[i].y;
   }
   num = block_sum(num, sh);
   den = block_sum(den, sh);
@@ -566,14 +646,21 @@ void launch_max_exp(const SelVecStats& a, int ma, const SelVecStats& b, int nb, 
   record_launch();
 }
 
-void launch_gemv(const double2* M, long long ld, int rows, int len, int op, const double2* X, int ldx, double2* Y,
-                 int ldy, const int* ex, int eidx, cudaStream_t st) {
+int gemv_chunks(int len) { return (len + GEMV_CHUNK - 1) / GEMV_CHUNK; }
+
+void launch_gemv(const double2* M, long long ld, int rows, int len, int op, const double2* Xh, const double2* Xl,
+                 int ldx, double2* Yh, double2* Yl, double2* part, const int* ex, int eidx, cudaStream_t st) {
   if (rows <= 0) return;
-  if (op == 0)
-    gemv_rows_kernel<<<blocks(rows, 128), 128, 0, st>>>(M, ld, rows, len, X, ldx, Y, ldy, ex, eidx);
-  else
-    gemv_cols_kernel<<<blocks(static_cast<long long>(rows) * 32, 256), 256, 0, st>>>(M, ld, rows, len, op == 2, X,
-                                                                                     ldx, Y, ldy, ex, eidx);
+  if (op == 0) {
+    const int nch = std::max(1, gemv_chunks(len));
+    gemv_rows_kernel<<<dim3(blocks(rows, 64), nch), 64, 0, st>>>(M, ld, rows, len, Xh, Xl, ldx, part, ex, eidx);
+    record_launch();
+    gemv_reduce_kernel<<<blocks(static_cast<long long>(rows) * SEL_PROBES, 128), 128, 0, st>>>(part, rows, nch, Yh,
+                                                                                              Yl);
+  } else {
+    gemv_cols_kernel<<<blocks(static_cast<long long>(rows) * 32, 256), 256, 0, st>>>(M, ld, rows, len, op == 2, Xh,
+                                                                                     Xl, ldx, Yh, Yl, rows, ex, eidx);
+  }
   record_launch();
 }
 
@@ -583,8 +670,9 @@ void launch_selector_features(const SelVecStats& a, int m, const SelVecStats& b,
   record_launch();
 }
 
-void launch_residual(const double2* W, const double2* zs, int m, SelAux* aux, cudaStream_t st) {
-  residual_kernel<<<1, RED_T, 0, st>>>(W, zs, m, aux);
+void launch_residual(const double2* Wh, const double2* Wl, const double2* zh, const double2* zl, int m, SelAux* aux,
+                     cudaStream_t st) {
+  residual_kernel<<<1, RED_T, 0, st>>>(Wh, Wl, zh, zl, m, aux);
   record_launch();
 }
 

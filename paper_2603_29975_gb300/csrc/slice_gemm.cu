@@ -205,30 +205,47 @@ __device__ __forceinline__ bool issue_dispatch(int S, bool fullset, bool firstkb
 struct EpiCtx {
   int row, z, m_z, n2_z, n0, c0, skip_n, er;
   int grow;              // row of the output matrix (the diagonal test of EPI_IMINUS)
+  int jlim;              // complex columns of the output row's matrix
   uint32_t tbase;
   double2* Cz;           // output row r is Cz[crow + column * ldc]
   long long crow, ldc;
   bool rowok;
 };
 
-// output matrix, row offset and matrix row of tile row `row` of problem z
-__device__ __forceinline__ void out_row(const GemmParams& p, bool single, int z, int row, bool rowok, double2*& Cz,
-                                        long long& crow, int& grow) {
+// output matrix, row offset, matrix row, leading dimension and column count of tile row
+// `row` of problem z; clears rowok for rows past their matrix
+__device__ __forceinline__ void out_row(const GemmParams& p, bool single, int z, int row, bool& rowok, double2*& Cz,
+                                        long long& crow, int& grow, long long& ldc, int& jlim) {
   if (p.crow) {
     const int a = row / p.crow_b, rl = row - a * p.crow_b;
     Cz = rowok ? p.crow[a] : nullptr;
     crow = static_cast<long long>(z) * p.crow_b + rl;
     grow = static_cast<int>(crow);
+    if (p.crow_n) {
+      const int na = rowok ? p.crow_n[a] : 0;
+      if (crow >= na) rowok = false;
+      ldc = na;
+      jlim = na;
+    } else {
+      ldc = p.ldc1;
+      jlim = 0x7FFFFFFF;
+    }
   } else {
     Cz = single ? p.C1 : p.C[z];
     crow = row;
     grow = row;
+    ldc = single ? p.ldc1 : p.ldc[z];
+    jlim = 0x7FFFFFFF;
   }
 }
 
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(taddr));
+}
+
+__device__ __forceinline__ void prefetch_l2(const void* ptr) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<uint64_t>(ptr)));
 }
 
 template <int G>
@@ -238,6 +255,26 @@ __device__ __forceinline__ void epilogue_fast(const GemmParams& p, const EpiCtx&
   constexpr int NL = G - NH;
   constexpr int S8 = 8 * NL;
   constexpr int BN = 64;
+  const bool needC = p.mode == EPI_LU || p.mode == EPI_GENERAL;
+  const int jc0 = (x.n0 + x.c0) / 2;                  // this thread's 8 complex columns
+  const int jend = min(min(jc0 + 8, (x.n2_z + 1) / 2), x.jlim);
+  const bool active = x.rowok && max(jc0, x.skip_n) < jend;
+  if (!__any_sync(0xffffffffu, active)) {
+    // nothing of this warp is written: release the accumulators unread
+#pragma unroll
+    for (int gi = 0; gi < G; ++gi) {
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[gi]);
+    }
+    return;
+  }
+  // C lines towards L2 now, consumed after the drain
+  if (needC && active) {
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj)
+      if (jc0 + jj < jend) prefetch_l2(x.Cz + x.crow + (jc0 + jj) * x.ldc);
+  }
   // phase A: drain -- fold every group of the 16 columns into H, L and release its
   // accumulator at once, so the next tile's MMAs start while phase B runs
   long long H[16], L[16];
@@ -260,16 +297,16 @@ __device__ __forceinline__ void epilogue_fast(const GemmParams& p, const EpiCtx&
       if (gi < NH) { H[j] += a; H[j + 8] += b; } else { L[j] += a; L[j + 8] += b; }
     }
   }
-  if (!x.rowok) return;
-  // phase B: round and write, the next column's loads issued one step ahead
+  if (!active) return;
+  // phase B: round and write, the next column's loads issued one step ahead (C was sent
+  // towards L2 before the drain)
   double2 cv = make_double2(0.0, 0.0);
   int fe = 0;
-  const int jc0 = (x.n0 + x.c0) / 2;
   auto load_col = [&](int jj, double2& c, int& f) {
     const int jc = jc0 + jj;
-    const bool in = 2 * jc < x.n2_z;
+    const bool in = jc < jend;
     f = in ? p.f[x.z * p.f_stride + jc] : 0;
-    c = (in && (p.mode == EPI_LU || p.mode == EPI_GENERAL)) ? x.Cz[x.crow + jc * x.ldc] : make_double2(0.0, 0.0);
+    c = (in && needC && jc >= x.skip_n) ? x.Cz[x.crow + jc * x.ldc] : make_double2(0.0, 0.0);
   };
   load_col(0, cv, fe);
 #pragma unroll
@@ -278,7 +315,7 @@ __device__ __forceinline__ void epilogue_fast(const GemmParams& p, const EpiCtx&
     int fn = 0;
     if (jj < 7) load_col(jj + 1, cn, fn);
     const int jc = jc0 + jj;
-    if (2 * jc < x.n2_z && jc >= x.skip_n) {
+    if (jc < jend && jc >= x.skip_n) {
       const int E = x.er + fe;
       double zz[2];
 #pragma unroll
@@ -309,6 +346,101 @@ __device__ __forceinline__ void epilogue_fast(const GemmParams& p, const EpiCtx&
   }
 }
 
+// Variant of epilogue_fast processing the 16 columns in two halves of 8: per half, the
+// group accumulators stream through a double-buffered TMEM load (group g + 1 in flight while
+// group g is folded) and the half's C values are loaded before its drain; the accumulators are
+// released during the second half.
+template <int G>
+__device__ __forceinline__ void epilogue_halves(const GemmParams& p, const EpiCtx& x, uint64_t* acc_empty, bool magic,
+                                                int lane) {
+  constexpr int NH = G < 4 ? G : 4;
+  constexpr int NL = G - NH;
+  constexpr int S8 = 8 * NL;
+  constexpr int BN = 64;
+  const bool needC = p.mode == EPI_LU || p.mode == EPI_GENERAL;
+  const int jc0 = (x.n0 + x.c0) / 2;
+  const int jend = min(min(jc0 + 8, (x.n2_z + 1) / 2), x.jlim);
+  const bool active = x.rowok && max(jc0, x.skip_n) < jend;
+  if (!__any_sync(0xffffffffu, active)) {
+#pragma unroll
+    for (int gi = 0; gi < G; ++gi) {
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[gi]);
+    }
+    return;
+  }
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    const int jh = jc0 + 4 * half;                     // first complex column of this half
+    double2 cv[4];
+    int fe[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int jc = jh + q;
+      const bool w = active && jc < jend && jc >= x.skip_n;
+      fe[q] = jc < jend ? p.f[x.z * p.f_stride + jc] : 0;
+      cv[q] = (needC && w) ? x.Cz[x.crow + jc * x.ldc] : make_double2(0.0, 0.0);
+    }
+    long long H[8], L[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) { H[j] = 0; L[j] = 0; }
+    uint32_t va[8], vb[8];
+    tmem_ld8(x.tbase + 8 * half, va);
+    tmem_wait_ld();
+#pragma unroll
+    for (int gi = 0; gi < G; ++gi) {
+      uint32_t (&cur)[8] = (gi & 1) ? vb : va;
+      uint32_t (&nxt)[8] = (gi & 1) ? va : vb;
+      if (gi + 1 < G) tmem_ld8(x.tbase + (gi + 1) * BN + 8 * half, nxt);
+      if (half == 1) {
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[gi]);     // both halves of group gi are read
+      }
+      const int w = gi < NH ? (1 << (8 * (NH - 1 - gi))) : (1 << (8 * (NL - 1 - (gi - NH))));
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const long long a = static_cast<long long>(acc_to_int(cur[j], magic)) * w;
+        if (gi < NH) H[j] += a; else L[j] += a;
+      }
+      if (gi + 1 < G) tmem_wait_ld();
+    }
+    if (active) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int jc = jh + q;
+        if (jc < jend && jc >= x.skip_n) {
+          const int E = x.er + fe[q];
+          double zz[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const long long Hh = H[2 * q + h], Lh = L[2 * q + h];
+            long long hi = S8 ? (Hh >> (64 - S8)) : (Hh >> 63);
+            const unsigned long long lo = static_cast<unsigned long long>(Hh) << S8;
+            const unsigned long long lo2 = lo + static_cast<unsigned long long>(Lh);
+            hi += (Lh >> 63) + (lo2 < lo ? 1 : 0);
+            zz[h] = round_hl(hi, lo2, E);
+          }
+          double2* dst = x.Cz + x.crow + jc * x.ldc;
+          if (p.mode == EPI_STORE) {
+            if (p.ar == 1.0 && p.ai == 0.0) *dst = make_double2(zz[0], zz[1]);
+            else *dst = make_double2(p.ar * zz[0] - p.ai * zz[1], p.ar * zz[1] + p.ai * zz[0]);
+          } else if (p.mode == EPI_LU) {
+            *dst = make_double2(cv[q].x - zz[0], cv[q].y - zz[1]);
+          } else if (p.mode == EPI_IMINUS) {
+            *dst = make_double2((jc == x.grow ? 1.0 : 0.0) - zz[0], 0.0 - zz[1]);
+          } else {
+            const double xr = p.ar * zz[0] - p.ai * zz[1], xi = p.ar * zz[1] + p.ai * zz[0];
+            const double yr = p.br * cv[q].x - p.bi * cv[q].y, yi = p.br * cv[q].y + p.bi * cv[q].x;
+            *dst = make_double2(xr + yr, xi + yi);
+          }
+        }
+      }
+    }
+  }
+}
+
 template <int BN>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
 slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -318,7 +450,7 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   constexpr int COLS = BN / 4;            // stacked columns per epilogue thread
   const bool single = p.m == nullptr;
   const int ntx = p.ntx, nty = p.nty;
-  const int ntiles = ntx * nty * p.batch;
+  const int ntiles = p.tpp * p.batch;
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -357,19 +489,32 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   const int nkb = p.kblocks;
   const int nchunks = (nkb + p.chunk_kb - 1) / p.chunk_kb;
 
-  // tile decode; returns false for tiles outside the problem's extent (skipped by all roles)
+  // tile decode.  Problem z owns tiles [z tpp, (z + 1) tpp): the tile rows below its skip box
+  // (all columns, column tile fastest), then the tiles right of the box in the rows beside
+  // it; tiles wholly inside the box are never enumerated.  Returns false for indices past the
+  // problem's own tiles or outside its extent (skipped by all roles alike).
   auto tile_of = [&](int t, int& z, int& m0, int& n0, int& m_z, int& n2_z) -> bool {
-    const int x = t % ntx;
-    const int y = (t / ntx) % nty;
-    z = t / (ntx * nty);
+    z = t / p.tpp;
+    const int r = t - z * p.tpp;
     m_z = single ? p.m1 : p.m[z];
     n2_z = 2 * (single ? p.n1 : p.n[z]);
-    m0 = y * GEMM_BM;
-    n0 = x * BN;
-    if (m0 >= m_z || n0 >= n2_z) return false;
     const int km = single ? p.skm1 : (p.skm ? p.skm[z] : 0);
     const int kn = single ? p.skn1 : (p.skn ? p.skn[z] : 0);
-    return !(m0 + GEMM_BM <= km && 2 * ((n0 + BN) / 2) <= 2 * kn);   // tile inside the skip box
+    const int ky = min(km / GEMM_BM, nty), kx = min((2 * kn) / BN, ntx);
+    const int count1 = (nty - ky) * ntx;
+    int x, y;
+    if (r < count1) {
+      y = ky + r / ntx;
+      x = r - (y - ky) * ntx;
+    } else {
+      const int w = ntx - kx, r2 = r - count1;
+      if (w <= 0 || r2 >= ky * w) return false;
+      y = r2 / w;
+      x = kx + (r2 - y * w);
+    }
+    m0 = y * GEMM_BM;
+    n0 = x * BN;
+    return m0 < m_z && n0 < n2_z;
   };
 
   if (warp == 0) {
@@ -465,21 +610,37 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
           x.row = row; x.z = z; x.m_z = m_z; x.n2_z = n2_z; x.n0 = n0; x.c0 = c0; x.tbase = tbase;
           x.rowok = rowok;
           x.skip_n = (row < (single ? p.skm1 : (p.skm ? p.skm[z] : 0))) ? (single ? p.skn1 : p.skn[z]) : 0;
-          out_row(p, single, z, row, rowok, x.Cz, x.crow, x.grow);
-          x.ldc = single ? p.ldc1 : p.ldc[z];
-          x.er = rowok ? p.e[z * p.e_stride + row] + p.base_exp : 0;
+          out_row(p, single, z, row, x.rowok, x.Cz, x.crow, x.grow, x.ldc, x.jlim);
+          x.er = x.rowok ? p.e[z * p.e_stride + row] + p.base_exp : 0;
           if (!mbar_wait(acc_full, cc & 1, p.status, abort_flag)) { ok = false; break; }
           tc_fence_after();
           ++cc;
-          switch (G) {
-            case 1: epilogue_fast<1>(p, x, acc_empty, magic, lane); break;
-            case 2: epilogue_fast<2>(p, x, acc_empty, magic, lane); break;
-            case 3: epilogue_fast<3>(p, x, acc_empty, magic, lane); break;
-            case 4: epilogue_fast<4>(p, x, acc_empty, magic, lane); break;
-            case 5: epilogue_fast<5>(p, x, acc_empty, magic, lane); break;
-            case 6: epilogue_fast<6>(p, x, acc_empty, magic, lane); break;
-            case 7: epilogue_fast<7>(p, x, acc_empty, magic, lane); break;
-            default: epilogue_fast<8>(p, x, acc_empty, magic, lane); break;
+          // short K (at most two K-blocks per tile): the epilogue bounds the tile, and the
+          // two-halves variant with streamed TMEM loads is faster (1.18x on 1024 x 1040 x 16
+          // tiles); longer K: the group-wise drain that releases accumulators earliest (1.14x
+          // on 976 x 976 x 64)
+          if (p.kblocks <= 2) {
+            switch (G) {
+              case 1: epilogue_halves<1>(p, x, acc_empty, magic, lane); break;
+              case 2: epilogue_halves<2>(p, x, acc_empty, magic, lane); break;
+              case 3: epilogue_halves<3>(p, x, acc_empty, magic, lane); break;
+              case 4: epilogue_halves<4>(p, x, acc_empty, magic, lane); break;
+              case 5: epilogue_halves<5>(p, x, acc_empty, magic, lane); break;
+              case 6: epilogue_halves<6>(p, x, acc_empty, magic, lane); break;
+              case 7: epilogue_halves<7>(p, x, acc_empty, magic, lane); break;
+              default: epilogue_halves<8>(p, x, acc_empty, magic, lane); break;
+            }
+          } else {
+            switch (G) {
+              case 1: epilogue_fast<1>(p, x, acc_empty, magic, lane); break;
+              case 2: epilogue_fast<2>(p, x, acc_empty, magic, lane); break;
+              case 3: epilogue_fast<3>(p, x, acc_empty, magic, lane); break;
+              case 4: epilogue_fast<4>(p, x, acc_empty, magic, lane); break;
+              case 5: epilogue_fast<5>(p, x, acc_empty, magic, lane); break;
+              case 6: epilogue_fast<6>(p, x, acc_empty, magic, lane); break;
+              case 7: epilogue_fast<7>(p, x, acc_empty, magic, lane); break;
+              default: epilogue_fast<8>(p, x, acc_empty, magic, lane); break;
+            }
           }
           continue;
         }
@@ -521,18 +682,18 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         }
       }
       if (!ok) break;
-      if (p.mode != EPI_GROUPS && rowok) {
+      double2* Cz = nullptr;
+      long long crow = 0, ldc = 0;
+      int grow = 0, jlim = 0;
+      bool rowok2 = rowok;
+      if (p.mode != EPI_GROUPS) out_row(p, single, z, row, rowok2, Cz, crow, grow, ldc, jlim);
+      if (p.mode != EPI_GROUPS && rowok2) {
         const int er = p.e[z * p.e_stride + row] + p.base_exp;
         const int skip_n = (row < (single ? p.skm1 : (p.skm ? p.skm[z] : 0))) ? (single ? p.skn1 : p.skn[z]) : 0;
-        double2* Cz;
-        long long crow;
-        int grow;
-        out_row(p, single, z, row, rowok, Cz, crow, grow);
-        const long long ldc = single ? p.ldc1 : p.ldc[z];
 #pragma unroll
         for (int j = 0; j < COLS; j += 2) {
           const int jc = (n0 + c0 + j) >> 1;          // complex column
-          if (2 * jc < n2_z && jc >= skip_n) {
+          if (2 * jc < n2_z && jc >= skip_n && jc < jlim) {
             const int E = er + p.f[z * p.f_stride + jc];
             const double zr = round_scaled_dev(T[j], E);
             const double zi = round_scaled_dev(T[j + 1], E);
@@ -586,7 +747,9 @@ void launch_slice_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const GemmP
   p.ntx = (2 * max_n + BN - 1) / BN;
   p.nty = (max_m + GEMM_BM - 1) / GEMM_BM;
   p.batch = batch;
-  const long long ntiles = static_cast<long long>(p.ntx) * p.nty * batch;
+  const int ky = std::min(p.box_m / GEMM_BM, p.nty), kx = std::min((2 * p.box_n) / BN, p.ntx);
+  p.tpp = p.ntx * p.nty - kx * ky;
+  const long long ntiles = static_cast<long long>(p.tpp) * batch;
   const int grid = static_cast<int>(std::min<long long>(ntiles, num_sms()));
   const size_t smem = gemm_smem_bytes(p.S, BN, p.nstage);
   if (BN == 64) {

@@ -51,6 +51,64 @@ __device__ __forceinline__ int next_digit(__int128& X) {
   return d;
 }
 
+// PER consecutive fp16 values (digits d[0..PER-1], negated when NEG) stored as one aligned
+// vector at dst.
+template <int PER, bool NEG>
+__device__ __forceinline__ void store_digits(__half* dst, const int (&d)[PER]) {
+  __half h[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) h[q] = __int2half_rn(NEG ? -d[q] : d[q]);
+  if constexpr (PER == 8) {
+    uint4 v;
+    v.x = __half_as_ushort(h[0]) | (static_cast<uint32_t>(__half_as_ushort(h[1])) << 16);
+    v.y = __half_as_ushort(h[2]) | (static_cast<uint32_t>(__half_as_ushort(h[3])) << 16);
+    v.z = __half_as_ushort(h[4]) | (static_cast<uint32_t>(__half_as_ushort(h[5])) << 16);
+    v.w = __half_as_ushort(h[6]) | (static_cast<uint32_t>(__half_as_ushort(h[7])) << 16);
+    *reinterpret_cast<uint4*>(dst) = v;
+  } else if constexpr (PER == 4) {
+    uint2 v;
+    v.x = __half_as_ushort(h[0]) | (static_cast<uint32_t>(__half_as_ushort(h[1])) << 16);
+    v.y = __half_as_ushort(h[2]) | (static_cast<uint32_t>(__half_as_ushort(h[3])) << 16);
+    *reinterpret_cast<uint2*>(dst) = v;
+  } else if constexpr (PER == 2) {
+    *reinterpret_cast<uint32_t*>(dst) = __half_as_ushort(h[0]) | (static_cast<uint32_t>(__half_as_ushort(h[1])) << 16);
+  } else {
+    *dst = h[0];
+  }
+}
+
+// Digits of PER consecutive elements of one row (positions l .. l + PER - 1, all < K, l and K
+// multiples of PER), every slice written with vector stores.
+template <int PER>
+__device__ __forceinline__ void split_run(const SplitParams& p, const double2* v, int e, int r, int l, int K,
+                                          __half* outz, long long plane) {
+  __int128 Xr[PER], Xi[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    Xr[q] = integer_image(v[q].x, e, p.nbits);
+    Xi[q] = integer_image(v[q].y, e, p.nbits);
+  }
+  for (int s = p.S - 1; s >= 0; --s) {
+    int dr[PER], di[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      dr[q] = s ? next_digit(Xr[q]) : static_cast<int>(Xr[q]);
+      di[q] = s ? next_digit(Xi[q]) : static_cast<int>(Xi[q]);
+    }
+    __half* o = outz + s * plane;
+    if (p.side == 0) {
+      store_digits<PER, false>(o + r * p.kpad + l, dr);
+      store_digits<PER, false>(o + r * p.kpad + K + l, di);
+    } else {
+      const long long row0 = 2LL * r, row1 = 2LL * r + 1;
+      store_digits<PER, false>(o + row0 * p.kpad + l, dr);
+      store_digits<PER, true>(o + row0 * p.kpad + K + l, di);
+      store_digits<PER, false>(o + row1 * p.kpad + l, di);
+      store_digits<PER, false>(o + row1 * p.kpad + K + l, dr);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(SPLIT_THREADS)
 split_kernel(const SplitParams p) {
   const int z = blockIdx.y;
@@ -130,7 +188,15 @@ split_kernel(const SplitParams p) {
       const int rl = tid / 8;
       const int lg = (tid % 8) * per;
       const int r = r0 + rl;
-      if (r < R) {
+      const int l0 = lt + lg;
+      // vector stores when this thread's run is whole and aligned (and no debug copy)
+      const bool vec = !dbg && (per == 8 || per == 4 || per == 2) && K % per == 0 && l0 + per <= K;
+      if (r < R && vec) {
+        const int e = rowexp[rl];
+        if (per == 8) split_run<8>(p, &tile[rl][lg], e, r, l0, K, outz, plane);
+        else if (per == 4) split_run<4>(p, &tile[rl][lg], e, r, l0, K, outz, plane);
+        else split_run<2>(p, &tile[rl][lg], e, r, l0, K, outz, plane);
+      } else if (r < R) {
         const int e = rowexp[rl];
         for (int q = 0; q < per; ++q) {
           const int l = lt + lg + q;

@@ -75,11 +75,11 @@ class _KkrPool:
         return group, M[:a, a:a + 16], D
 
 
-def generate_instances(count, seed):
+def generate_instances(count, seed, kkr_sizes=(15, 27, 51, 65), energies=4):
     """(group, kind, A, B) with A = op(A), B = op(B) as numpy complex matrices.  `group`
     identifies the KKR system (instances of one system stay on one side of a split)."""
     rng = np.random.default_rng(seed)
-    pool = _KkrPool(seed)
+    pool = _KkrPool(seed, kkr_sizes, energies)
     out = []
     for i in range(count):
         kind = KINDS[i % len(KINDS)]

@@ -123,3 +123,93 @@ def test_build_m_shared_is_the_emulated_block_row_update(ozk_mod, handle, S):
             assert np.array_equal(got[rows], want)
         err = np.abs(got - kkr.kkr_build(ts[a], G)).max()
         assert err <= (1e-14 if S == 7 else 1e-9)
+
+
+@pytest.mark.parametrize("S,nb", [(7, 50), (7, 100), (0, 50)])
+def test_tau00_lmax4_spin_blocks(ozk_mod, handle, S, nb):
+    """b = 50 (lmax = 4 with spin) pivot blocks: the 256-thread Gauss-Jordan kernel, leaf GEMMs
+    with k = 50 (K' = 100, not a multiple of 16)."""
+    L, b = 9, 50
+    t, G, _ = synth.kkr_system(L, b, 0.4 + 0.1j, atom=3)
+    M = kkr.kkr_build(t, G)
+    tau = ozk_mod.colmajor_cuda(np.zeros((b, b), dtype=np.complex128))
+    ozk_mod.kkr_tau00(handle, ozk_mod.colmajor_cuda(M), ozk_mod.colmajor_cuda(t[0]), tau, S=S, nb=nb)
+    assert handle.status() == 0
+    got = ozk_mod.to_numpy(tau)
+    full = co.tau00_full(M, t[0])
+    if S > 0:
+        assert kkr.rel_err(got, co.tau00_block(M, t[0], nb, S=S, leaf=b)) < 1e-13
+        assert kkr.rel_err(got, full) <= 1e-10
+    else:
+        assert kkr.rel_err(got, full) < 1e-13
+
+
+def test_autotuned_panel_width_is_cached_and_used(ozk_mod):
+    """kkr_tau00_autotune times every nb = b, 2b, ..., 128 and caches the fastest; nb = 0 then
+    runs exactly that nb (bitwise equal results)."""
+    import torch
+    h = ozk_mod.Handle()
+    sizes = [27, 15, 27]
+    systems = [_system(L, 0.5 + 0.05j, atom=i) for i, L in enumerate(sizes)]
+    best, times = ozk_mod.kkr_tau00_autotune(h, [L * 16 for L in sizes], 16, S=7)
+    assert sorted(times) == list(range(16, 129, 16)) and best in times
+    assert all(v > 0 for v in times.values()) and times[best] == min(times.values())
+
+    def run(nb):
+        Ms = [ozk_mod.colmajor_cuda(M) for t, G, M in systems]
+        t0s = [ozk_mod.colmajor_cuda(t[0]) for t, G, M in systems]
+        taus = [ozk_mod.colmajor_cuda(np.zeros((16, 16), dtype=np.complex128)) for _ in systems]
+        ozk_mod.kkr_tau00_batched(h, Ms, t0s, taus, S=7, nb=nb)
+        torch.cuda.synchronize()
+        return [ozk_mod.to_numpy(x) for x in taus]
+
+    auto, fixed = run(0), run(best)
+    assert h.status() == 0
+    for a, f, (t, G, M) in zip(auto, fixed, systems):
+        assert np.array_equal(a, f)
+        assert kkr.rel_err(a, kkr.tau00_full(M, t[0])) <= 1e-10
+    h.close()
+
+
+def test_build_m_shared_sizes_uses_leading_blocks_of_G(ozk_mod, handle):
+    """Atoms with LIZs of 9, 15 and 27 sites on one lattice: atom a's M is I - t_a G[:n_a, :n_a]
+    with the leading block of the 27-site G, block row by block row as the oracle forms it."""
+    import torch
+    b, S = 16, 7
+    Ls = [15, 27, 9, 27]
+    _, G, _ = synth.kkr_system(max(Ls), b, 0.2 + 0.3j, atom=0)
+    ts = [synth.kkr_t(L, b, atom=a) for a, L in enumerate(Ls)]
+    Ms = [ozk_mod.colmajor_cuda(np.full((L * b, L * b), np.nan, dtype=np.complex128)) for L in Ls]
+    ptr = lambda xs: torch.tensor([x.data_ptr() for x in xs], dtype=torch.int64, device="cuda")
+    tdev = [_tblocks(ozk_mod, t) for t in ts]          # kept alive until the build has run
+    Gd = ozk_mod.colmajor_cuda(G)
+    ozk_mod.kkr_build_m_shared_sizes_ptrs(handle, Ls, b, ptr(tdev), Gd, ptr(Ms), S=S)
+    assert handle.status() == 0
+    for a, L in enumerate(Ls):
+        n = L * b
+        got = ozk_mod.to_numpy(Ms[a])
+        eye = np.eye(n, dtype=np.complex128)
+        for i in range(L):
+            rows = slice(i * b, (i + 1) * b)
+            assert np.array_equal(got[rows], co.zgemm_lu(eye[rows], ts[a][i], G[rows, :n], S))
+        assert np.abs(got - kkr.kkr_build(ts[a], G[:n, :n])).max() <= 1e-14
+
+
+def test_contour_trace_matches_oracle(ozk_mod, handle):
+    """tau_00 at 8 contour energies (one batched solve), their traces and the quadrature sum
+    against the oracle's full-inverse tau_00."""
+    import torch
+    E, w = synth.contour(32)
+    pick = np.arange(0, 32, 4)
+    systems = [_system(9, complex(E[i]), atom=0) for i in pick]
+    Ms = [ozk_mod.colmajor_cuda(M) for t, G, M in systems]
+    t0s = [ozk_mod.colmajor_cuda(t[0]) for t, G, M in systems]
+    taus = [ozk_mod.colmajor_cuda(np.zeros((16, 16), dtype=np.complex128)) for _ in systems]
+    _, (pm, pt, pu) = ozk_mod.kkr_tau00_batched(handle, Ms, t0s, taus, S=7, nb=64)
+    tr, integral = ozk_mod.kkr_contour_trace(handle, pu, 16, w[pick])
+    assert handle.status() == 0
+    want_tr, want = kkr.contour_trace([kkr.tau00_full(M, t[0]) for t, G, M in systems], w[pick])
+    assert np.abs(tr - want_tr).max() <= 1e-10 * np.abs(want_tr).max()
+    assert abs(integral - want) <= 1e-10 * abs(want)
+    # the traces are those of the returned blocks
+    assert np.allclose(tr, [np.trace(ozk_mod.to_numpy(x)) for x in taus], rtol=1e-15, atol=0)

@@ -139,3 +139,16 @@ def test_generators_are_counter_based():
     # SplitMix64 published test vector: seed state 0 -> first output 0xE220A8397B1DCDAF
     z = synth._mix(np.array([0x9E3779B97F4A7C15], dtype=np.uint64))[0]
     assert int(z) == 0xE220A8397B1DCDAF
+
+
+def test_contour_trace_of_a_polynomial_is_exact():
+    """G = 0 gives tau_00 = t_0; with t_0(z) = z I the contour sum is b (z_b^2 - z_a^2) / 2,
+    which the Gauss-Legendre rule integrates exactly."""
+    E, w = synth.contour(32)
+    b = 16
+    taus = [kkr.tau00_full(np.eye(b, dtype=np.complex128), z * np.eye(b)) for z in E]
+    tr, integral = kkr.contour_trace(taus, w)
+    assert np.allclose(tr, b * E, rtol=0, atol=1e-14)
+    th0 = np.arcsin(0.005)
+    za, zb = -0.3 + np.exp(1j * (np.pi - th0)), -0.3 + np.exp(1j * th0)
+    assert abs(integral - b * (zb ** 2 - za ** 2) / 2) < 1e-11

@@ -194,3 +194,42 @@ def test_residual_estimate_measures_the_relative_frobenius_error():
         assert sel.residual_estimate(C, X, zs, E) < 1e-14
     # E||Err x||^2 / E||C x||^2 = ||Err||^2 / ||C||^2; the ratio of sample means converges to it
     assert abs(math.sqrt(np.mean(r2)) / want - 1.0) < 0.1
+
+
+def test_integer_images_are_exact():
+    V = synth.scaled_uniform(12, 0, (7, 5), 8.0) + 1j * synth.scaled_uniform(12, 1, (7, 5), 8.0)
+    re, im, e = sel._to_int(V)
+    back = np.array([[math.ldexp(int(r), e) + 1j * math.ldexp(int(i), e) for r, i in zip(rr, ii)]
+                     for rr, ii in zip(re, im)])
+    assert np.array_equal(back, V)
+    a = (np.array([[1, -2], [3, 4]], dtype=object), np.array([[0, 1], [1, 0]], dtype=object), -3)
+    b = (np.array([[5], [6]], dtype=object), np.array([[-1], [2]], dtype=object), 1)
+    pr, pi, pe = sel._int_mul(a, b)
+    A = (a[0].astype(float) + 1j * a[1].astype(float)) * 2.0 ** -3
+    B = (b[0].astype(float) + 1j * b[1].astype(float)) * 2.0
+    assert pe == -2 and np.array_equal(pr.astype(float) * 0.25 + 1j * pi.astype(float) * 0.25, A @ B)
+
+
+def test_exact_probe_residual_sees_through_cancellation():
+    """A product whose result is 1e-9 of the operands' scale: the binary64 probe product has
+    errors far above the tolerance, the exact one resolves a planted 1e-12 relative error."""
+    rng = np.random.default_rng(13)
+    m, k, n = 20, 36, 15
+    A = rng.normal(size=(m, k)) + 1j * rng.normal(size=(m, k))
+    _, _, vh = np.linalg.svd(A)
+    N = vh[m:].conj().T
+    B = N @ (rng.normal(size=(k - m, n)) + 1j * rng.normal(size=(k - m, n)))
+    B = B + 1e-9 * (rng.normal(size=(k, n)) + 1j * rng.normal(size=(k, n)))
+    X = sel.probe_vectors(n, 5)
+    _, zx, E = sel.features(A, B, X, exact=True)
+    _, zf, _ = sel.features(A, B, X)
+    # exact product of the binary64 operands, rounded: relative error ~1e-16
+    ar, ai, ea = sel._to_int(A)
+    br, bi, eb = sel._to_int(B)
+    cr, ci, ec = sel._int_mul((ar, ai, ea), (br, bi, eb))
+    C = np.array([[math.ldexp(int(x), ec) for x in row] for row in cr]) + \
+        1j * np.array([[math.ldexp(int(x), ec) for x in row] for row in ci])
+    assert sel.residual_estimate(C, X, zx, E) < 1e-15
+    assert sel.residual_estimate(C, X, zf, E) > 1e-10           # the binary64 check cannot tell
+    r = sel.residual_estimate(C * (1 + 1e-12), X, zx, E)
+    assert 0.5e-12 < r < 2e-12
