@@ -236,6 +236,19 @@ ozk_status_t ozk_selector_last(ozk_handle_t handle, ozk_selector_info* info);
 ozk_status_t ozk_rel_diff(ozk_handle_t handle, int m, int n, const void* X, int ldx, const void* Y, int ldy,
                           double* rel);
 
+/* Ozaki-II (CRT) emulated ZGEMM (paper Sec. 2.2: integers, products modulo small pairwise-
+ * coprime moduli, Chinese-Remainder reconstruction; precision knob: the number of moduli,
+ * Sec. 3.2).  Same arguments as ozaki_zgemm with nmod (2..16) in place of S.  Moduli: the nmod
+ * largest pairwise-coprime integers <= 256; integer images trunc(x 2^(beta - e)) with per-row
+ * (per-column) frexp exponents e and beta the largest bit count with 2k 4^beta < P/2 (P the
+ * product of the moduli), so the exact product is recovered; one rounding to binary64.  The
+ * residue products run on the tcgen05 tensor cores (one product per modulus, exact integers
+ * added to an int32 buffer of nmod x m x 2n in the workspace), the reconstruction in a separate
+ * kernel.  k <= 65536. */
+ozk_status_t ozaki2_zgemm(ozk_handle_t handle, char transa, char transb, int m, int n, int k,
+                          const double* alpha, const void* A, int lda, const void* B, int ldb,
+                          const double* beta, void* C, int ldc, int nmod);
+
 /* Plain binary64 ZGEMM on the FP64 tensor path (DMMA, mma.sync m8n8k4.f64), same argument
  * meaning as ozaki_zgemm without S: the comparison baseline on the same GPU. */
 ozk_status_t ozk_zgemm_dmma(ozk_handle_t handle, char transa, char transb, int m, int n, int k,

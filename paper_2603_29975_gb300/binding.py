@@ -43,7 +43,7 @@ EXPORTS = ["ozk_create", "ozk_destroy", "ozk_set_stream", "ozk_get_status", "ozk
            "ozk_selector_get_params", "ozk_selector_load", "ozk_selector_save", "ozk_selector_configure",
            "ozk_selector_features", "ozk_selector_predict", "ozk_selector_train_step", "ozk_selector_gradient",
            "ozk_selector_last", "ozk_rel_diff", "kkr_build_m_shared", "kkr_tau00_autotune",
-           "kkr_build_m_shared_sizes", "kkr_contour_trace"]
+           "kkr_build_m_shared_sizes", "kkr_contour_trace", "ozaki2_zgemm"]
 KIND_NAMES = ["split", "slice_gemm", "gj", "build_m", "dmma", "other"]
 
 _lib = None
@@ -84,6 +84,7 @@ def lib():
         L.kkr_tau00_autotune.argtypes = [vp, i, ip, i, i, ip, ctypes.POINTER(ctypes.c_float)]
         L.kkr_build_m_shared_sizes.argtypes = [vp, i, ip, i, vp, vp, i, vp, i]
         L.kkr_contour_trace.argtypes = [vp, i, i, vp, dp, dp, dp]
+        L.ozaki2_zgemm.argtypes = [vp, c, c, i, i, i, dp, vp, i, vp, i, dp, vp, i, i]
         L.ozaki_zgemm_noalloc.argtypes = [vp, c, c, i, i, i, dp, vp, i, vp, i, dp, vp, i, i, i, vp]
         fp, u64, f32 = ctypes.POINTER(ctypes.c_float), ctypes.c_uint64, ctypes.c_float
         L.ozk_selector_init.argtypes = [vp, u64]
@@ -248,6 +249,17 @@ def ozaki_zgemm(h: Handle, A, B, C, S: int = 7, alpha=1.0, beta=0.0, transa="N",
     _check(lib().ozaki_zgemm(h.ptr, transa.encode(), transb.encode(), m, n, k, _c2(alpha), _ptr(A),
                              _ld(A, A.shape[0]), _ptr(B), _ld(B, B.shape[0]), _c2(beta), _ptr(C),
                              _ld(C, m), S, pair_mode), "ozaki_zgemm")
+    return C
+
+
+def ozaki2_zgemm(h: Handle, A, B, C, nmod: int = 16, alpha=1.0, beta=0.0, transa="N", transb="N"):
+    """C = alpha op(A) op(B) + beta C by Ozaki-II (CRT) with nmod moduli, column-major tensors."""
+    m, n, k = _shapes(transa, transb, A, B)
+    if tuple(C.shape) != (m, n):
+        raise OzkError("C has the wrong shape")
+    _check(lib().ozaki2_zgemm(h.ptr, transa.encode(), transb.encode(), m, n, k, _c2(alpha), _ptr(A),
+                              _ld(A, A.shape[0]), _ptr(B), _ld(B, B.shape[0]), _c2(beta), _ptr(C), _ld(C, m), nmod),
+           "ozaki2_zgemm")
     return C
 
 

@@ -16,7 +16,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libozk.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["split.cu", "slice_gemm.cu", "dmma.cu", "lu.cu", "selector.cu", "api.cu"]
+SOURCES = ["split.cu", "slice_gemm.cu", "dmma.cu", "lu.cu", "selector.cu", "ozaki2.cu", "api.cu"]
 
 
 def nvcc() -> str:

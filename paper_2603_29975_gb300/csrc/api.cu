@@ -189,6 +189,7 @@ static ozk_status_t size_table(ozk_context* h, std::vector<int>&& key, const int
 namespace {
 
 struct OpFlags { int trans, conj; };
+constexpr int PAIRS_DIAG = 2;                        // internal pair mode of the Ozaki-II products
 bool parse_op(char c, OpFlags* f) {
   switch (c) {
     case 'N': case 'n': f->trans = 0; f->conj = 0; return true;
@@ -223,6 +224,9 @@ struct EmuGemm {
   double sum_mnk = -1;                        // sum over problems of m n k (batched; -1: single)
   double sum_mk = 0, sum_nk = 0;              // operand sizes (complex elements) for byte counts
   long long zsA = 0, zsB = 0;                 // uniform batch of single-size problems: operand strides
+  // Ozaki-II (pair_mode PAIRS_DIAG): residue planes of beta-bit integer images, products added
+  // to the int32 buffer resid (row pitch ldres)
+  const Oz2Tables* oz2 = nullptr; int beta = 0; int* resid = nullptr; long long ldres = 0;
   double2* const* crow = nullptr; int crow_b = 0;   // row-block scatter of the output
   const int* crow_n = nullptr;                // per-output order (device), or none
 };
@@ -236,11 +240,12 @@ ozk_status_t plan_gemm(const EmuGemm& g, GemmPlan* P) {
   const int S = g.S;
   if (S < 1 || S > 16) return set_error(OZK_ERR_ARG, "S must be in 1..16");
   const bool full = g.pair_mode == OZK_PAIRS_FULL;
+  const bool diag = g.pair_mode == PAIRS_DIAG;          // Ozaki-II: one product per modulus
   P->G = full ? 2 * S - 1 : S;
   if (P->G > 16) return set_error(OZK_ERR_ARG, "full pair mode supports S <= 8");
   P->BN = P->G <= 8 ? 64 : 32;
-  P->maxpairs = S;
-  P->npairs = full ? S * S : S * (S + 1) / 2;
+  P->maxpairs = diag ? 1 : S;
+  P->npairs = diag ? S : (full ? S * S : S * (S + 1) / 2);
   const long long kp2 = 2LL * g.kmax;
   P->kpad = static_cast<int>(align_up(static_cast<size_t>(std::max<long long>(kp2, 16)), 8));
   P->rowsA = std::max(g.mmax, 1);
@@ -258,7 +263,7 @@ ozk_status_t plan_gemm(const EmuGemm& g, GemmPlan* P) {
   double terms = static_cast<double>(kp2) * P->maxpairs + 1.0;
   int need = 8 * (P->G - 1) + 14 + static_cast<int>(std::ceil(std::log2(terms))) + 2;
   // the integer group dump (test hook) never forms the 128-bit sum
-  if (need > 127 && g.mode != 3)
+  if (need > 127 && g.mode != EPI_GROUPS && g.mode != EPI_RESIDUES)
     return set_error(OZK_ERR_RANGE, "exact 128-bit reconstruction could overflow for this S and k");
   size_t off = 0;
   P->offA = off; off = align_up(off + static_cast<size_t>(g.batch) * S * P->rowsA * P->kpad * 2, 1024);
@@ -283,8 +288,9 @@ ozk_status_t run_emulated(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0
   const bool single = g.tm == nullptr;
   const int S = g.S;
 
+  const bool diag = g.pair_mode == PAIRS_DIAG;
   SplitParams sp{};
-  sp.S = S; sp.nbits = 8 * S - 1; sp.status = h->d_status; sp.kpad = P.kpad;
+  sp.S = S; sp.nbits = diag ? g.beta : 8 * S - 1; sp.status = h->d_status; sp.kpad = P.kpad;
   // left operand: rows of op(A); logical X[r][l] = op(A)[r][l]
   sp.trans = g.oa.trans; sp.conj = g.oa.conj; sp.side = 0;
   sp.out_rows = P.rowsA; sp.out = As; sp.exps = e; sp.exp_stride = P.rowsA;
@@ -294,11 +300,6 @@ ozk_status_t run_emulated(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0
   const double smnk = g.sum_mnk >= 0 ? g.sum_mnk : static_cast<double>(g.m) * g.n * g.k;
   const double smk = g.sum_mnk >= 0 ? g.sum_mk : static_cast<double>(g.m) * g.k;
   const double snk = g.sum_mnk >= 0 ? g.sum_nk : static_cast<double>(g.n) * g.k;
-  {
-    // algorithmic bytes: read 16 per complex element (twice: scan + split), write S x 2 fp16
-    Prof pr(h, OZK_KIND_SPLIT, 0.0, smk * (32.0 + 4.0 * S));
-    launch_split(sp, g.mmax, g.batch, h->stream);
-  }
   // right operand: columns of op(B); logical X[j][l] = op(B)[l][j]
   SplitParams sq = sp;
   sq.trans = g.ob.trans ? 0 : 1; sq.conj = g.ob.conj; sq.side = 1;
@@ -307,8 +308,15 @@ ozk_status_t run_emulated(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0
   if (single) { sq.X = nullptr; sq.X1 = g.B; sq.ld1 = g.ldb; sq.rows1 = g.n; sq.k1 = g.k; sq.zstride1 = g.zsB; }
   else { sq.X = g.tB; sq.ld = g.tldb; sq.rows = g.tn; sq.kdim = g.tk; }
   {
-    Prof pr(h, OZK_KIND_SPLIT, 0.0, snk * (32.0 + 8.0 * S));
-    launch_split(sq, g.nmax, g.batch, h->stream);
+    // algorithmic bytes: read 16 per complex element (twice: scan + split), write S x 2 fp16
+    // (left operand) or S x 4 fp16 (right operand, two stacked rows per column)
+    Prof pr(h, OZK_KIND_SPLIT, 0.0, smk * (32.0 + 4.0 * S) + snk * (32.0 + 8.0 * S));
+    if (diag) {
+      launch_residue_split(sp, *g.oz2, g.mmax, g.batch, h->stream);
+      launch_residue_split(sq, *g.oz2, g.nmax, g.batch, h->stream);
+    } else {
+      launch_split(sp, g.mmax, &sq, g.nmax, g.batch, h->stream);
+    }
   }
 
   CUtensorMap ta, tb;
@@ -323,6 +331,8 @@ ozk_status_t run_emulated(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0
   gp.fullset = g.pair_mode == OZK_PAIRS_FULL ? 1 : 0;
   const int gmax = (g.pair_mode == OZK_PAIRS_FULL) ? 2 * S : S + 1;
   gp.base_exp = -2 * (8 * S - 1) + 8 * (2 * S - gmax);
+  gp.diag_pairs = diag ? 1 : 0;
+  gp.resid = g.resid; gp.ldres = g.ldres;
   gp.ar = g.ar; gp.ai = g.ai; gp.br = g.br; gp.bi = g.bi;
   if (g.mode >= 0) gp.mode = g.mode;
   else if (g.br == 0.0 && g.bi == 0.0) gp.mode = 0;
@@ -336,7 +346,14 @@ ozk_status_t run_emulated(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0
   gp.box_m = single ? g.skm : (g.tskm ? g.box_m : 0);
   gp.box_n = single ? g.skn : (g.tskn ? g.box_n : 0);
   int np = 0;
-  for (int gg = 2; gg <= gmax; ++gg) {
+  if (diag) {
+    for (int t = 0; t < S; ++t) {
+      gp.ps[np] = gp.pt[np] = gp.pg[np] = static_cast<uint8_t>(t);
+      gp.pfirst[np] = 1;
+      ++np;
+    }
+  }
+  for (int gg = 2; gg <= gmax && !diag; ++gg) {
     bool first = true;
     for (int s = 1; s <= S; ++s) {
       const int t = gg - s;
@@ -630,6 +647,101 @@ ozk_status_t ozaki_zgemm(ozk_handle_t h, char transa, char transb, int m, int n,
   return run_emulated(h, g);
 }
 
+// Ozaki-II tables for N moduli: the N largest pairwise-coprime integers <= 256 (greedy from 256
+// down), powers of 256, Garner constants, and P (a product of at most 16 integers <= 256 fits
+// in 128 bits).
+static void oz2_tables(int N, Oz2Tables* T, unsigned __int128* Pout) {
+  T->N = N;
+  int cnt = 0;
+  auto gcd = [](int a, int b) { while (b) { const int t = a % b; a = b; b = t; } return a; };
+  for (int c = 256; c > 1 && cnt < N; --c) {
+    bool ok = true;
+    for (int j = 0; j < cnt; ++j) ok = ok && gcd(c, T->mod[j]) == 1;
+    if (ok) T->mod[cnt++] = c;
+  }
+  unsigned __int128 P = 1;
+  for (int t = 0; t < N; ++t) {
+    const int m = T->mod[t];
+    int pw = 1;
+    for (int s = 0; s < 8; ++s) { T->pow256[t][s] = pw; pw = pw * 256 % m; }
+    int prod = 1;                                      // m_0 ... m_{j-1} mod m_t
+    for (int j = 0; j < t; ++j) { T->pm[t][j] = prod; prod = prod * T->mod[j] % m; }
+    int inv = 1;                                        // prod^-1 mod m_t by search (m <= 256)
+    for (int x = 1; x < m; ++x) if (prod * x % m == 1 % m) { inv = x; break; }
+    T->inv[t] = t == 0 ? 1 : inv;
+    P *= static_cast<unsigned>(m);
+  }
+  T->P_lo = static_cast<unsigned long long>(P);
+  T->P_hi = static_cast<unsigned long long>(P >> 64);
+  *Pout = P;
+}
+
+ozk_status_t ozaki2_zgemm(ozk_handle_t h, char transa, char transb, int m, int n, int k, const double* alpha,
+                          const void* A, int lda, const void* B, int ldb, const double* beta, void* C, int ldc,
+                          int nmod) {
+  if (!h || !alpha || !beta) return set_error(OZK_ERR_ARG, "null argument");
+  EmuGemm g;
+  if (!parse_op(transa, &g.oa) || !parse_op(transb, &g.ob)) return set_error(OZK_ERR_ARG, "bad trans flag");
+  ozk_status_t st = check_dims(g.oa, g.ob, m, n, k, lda, ldb, ldc);
+  if (st) return st;
+  if (nmod < 2 || nmod > OZ2_MAXMOD) return set_error(OZK_ERR_ARG, "number of moduli must be in 2..16");
+  if (m == 0 || n == 0) return OZK_OK;
+  if (k == 0 || (alpha[0] == 0.0 && alpha[1] == 0.0)) {
+    if (beta[0] == 1.0 && beta[1] == 0.0) return OZK_OK;
+    launch_scale(m, n, static_cast<double2*>(C), ldc, beta[0], beta[1], h->stream);
+    return cuda_check(cudaGetLastError(), "scale launch");
+  }
+  if (k > 65536) return set_error(OZK_ERR_ARG, "Ozaki-II products are accumulated in int32: k <= 65536");
+  Oz2Tables T{};
+  unsigned __int128 P = 0;
+  oz2_tables(nmod, &T, &P);
+  // largest beta with 2k 4^beta < P / 2; |integer images| < 2^beta <= 2^63
+  int bta = 0;
+  int kbits = 0;
+  for (unsigned long long v = 4ull * k; v; v >>= 1) ++kbits;
+  while (bta < 63 && kbits + 2 * (bta + 1) <= 127) {
+    const unsigned __int128 lhs = static_cast<unsigned __int128>(4ull * k) << (2 * (bta + 1));
+    if (!(lhs < P)) break;
+    ++bta;
+  }
+  if (bta < 1) return set_error(OZK_ERR_ARG, "too few moduli for this k");
+  g.batch = 1; g.mmax = g.m = m; g.nmax = g.n = n; g.kmax = g.k = k;
+  g.A = static_cast<const double2*>(A); g.lda = lda;
+  g.B = static_cast<const double2*>(B); g.ldb = ldb;
+  g.C = nullptr; g.ldc = m;
+  g.S = nmod; g.pair_mode = PAIRS_DIAG; g.mode = EPI_RESIDUES;
+  g.oz2 = &T; g.beta = bta;
+  GemmPlan Pl;
+  st = plan_gemm(g, &Pl);
+  if (st) return st;
+  const size_t rbytes = sizeof(int) * static_cast<size_t>(nmod) * m * 2 * n;
+  const size_t off_r = align_up(Pl.total, 1024);
+  st = ensure_ws(h, off_r + rbytes);
+  if (st) return st;
+  int* R = reinterpret_cast<int*>(static_cast<uint8_t*>(h->ws) + off_r);
+  st = cuda_check(cudaMemsetAsync(R, 0, rbytes, h->stream), "clear products");
+  if (st) return st;
+  g.resid = R;
+  g.ldres = 2LL * n;
+  st = run_emulated(h, g);
+  if (st) return st;
+  CrtParams cp{};
+  cp.R = R; cp.ldr = 2LL * n; cp.plane = static_cast<long long>(m) * 2 * n;
+  cp.e = reinterpret_cast<const int*>(static_cast<uint8_t*>(h->ws) + Pl.offE);
+  cp.f = reinterpret_cast<const int*>(static_cast<uint8_t*>(h->ws) + Pl.offF);
+  cp.e_stride = Pl.rowsA; cp.f_stride = std::max(n, 1);
+  cp.m = m; cp.n = n; cp.batch = 1; cp.beta = bta;
+  cp.C = static_cast<double2*>(C); cp.ldc = ldc; cp.cstride = 0;
+  cp.ar = alpha[0]; cp.ai = alpha[1]; cp.br = beta[0]; cp.bi = beta[1];
+  cp.mode = (beta[0] == 0.0 && beta[1] == 0.0) ? EPI_STORE
+            : ((alpha[0] == -1.0 && alpha[1] == 0.0 && beta[0] == 1.0 && beta[1] == 0.0) ? EPI_LU : EPI_GENERAL);
+  {
+    Prof pr(h, OZK_KIND_OTHER, 0.0, 8.0 * static_cast<double>(nmod) * m * 2 * n);
+    launch_crt(cp, T, h->stream);
+  }
+  return cuda_check(cudaGetLastError(), "CRT launch");
+}
+
 ozk_status_t ozaki_zgemm_vbatched(ozk_handle_t h, char transa, char transb, const int* m, const int* n, const int* k,
                                   const double* alpha, const void* const* A, const int* lda, const void* const* B,
                                   const int* ldb, const double* beta, void* const* C, const int* ldc, int batch,
@@ -722,7 +834,7 @@ ozk_status_t ozk_split_debug(ozk_handle_t h, int side, char trans, int rows, int
   sp.X = nullptr; sp.X1 = static_cast<const double2*>(X); sp.ld1 = ldx; sp.rows1 = rows; sp.k1 = k;
   // debug digits are always dumped in the stacked layout [S][rows_out][2k]
   sp.dbg_digits = digits;
-  launch_split(sp, rows, 1, h->stream);
+  launch_split(sp, rows, nullptr, 0, 1, h->stream);
   return cuda_check(cudaGetLastError(), "split launch");
 }
 

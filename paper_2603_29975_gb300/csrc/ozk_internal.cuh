@@ -17,6 +17,80 @@ __device__ __forceinline__ void flag_error(int* status, int code) {
   if (status) atomicOr(status, 1 << code);
 }
 
+// ------------------------------------------------------------------ integer images (splits)
+__device__ __forceinline__ int frexp_exponent_from_bits(unsigned long long a) {
+  // a = |x| bit pattern (sign cleared), finite
+  if (a == 0ull) return 0;
+  const int ex = static_cast<int>(a >> 52);
+  if (ex > 0) return ex - 1022;
+  return -1010 - __clzll(a);          // subnormal: floor(log2 x) + 1
+}
+
+// X = trunc(x 2^(B - e)) computed exactly from the binary64 fields of x.
+__device__ __forceinline__ __int128 integer_image(double x, int e, int nbits) {
+  const unsigned long long u = __double_as_longlong(x);
+  const bool neg = (u >> 63) != 0ull;
+  const int ex = static_cast<int>((u >> 52) & 0x7FFull);
+  const unsigned long long man = u & ((1ull << 52) - 1ull);
+  unsigned long long M;
+  int E2;
+  if (ex == 0) { M = man; E2 = -1074; } else { M = man | (1ull << 52); E2 = ex - 1075; }
+  const int sh = E2 + nbits - e;
+  unsigned __int128 mag = 0;
+  if (M != 0ull) {
+    if (sh >= 0) mag = static_cast<unsigned __int128>(M) << sh;
+    else if (sh > -64) mag = static_cast<unsigned __int128>(M >> (-sh));
+  }
+  return neg ? -static_cast<__int128>(mag) : static_cast<__int128>(mag);
+}
+
+// Next balanced base-256 digit of X (least significant first); X is advanced.
+__device__ __forceinline__ int next_digit(__int128& X) {
+  const int d = static_cast<int>(static_cast<unsigned long long>(X + 128) & 255ull) - 128;
+  X = (X - d) >> 8;
+  return d;
+}
+
+
+// RN-even of T * 2^E as binary64, integer instructions only (subnormals and overflow handled).
+__device__ __forceinline__ double round_scaled_dev(__int128 T, int E) {
+  if (T == 0) return 0.0;
+  const bool neg = T < 0;
+  unsigned __int128 u = neg ? static_cast<unsigned __int128>(-T) : static_cast<unsigned __int128>(T);
+  const unsigned long long hi0 = static_cast<unsigned long long>(u >> 64);
+  const int lz = hi0 ? __clzll(hi0) : 64 + __clzll(static_cast<unsigned long long>(u));
+  u <<= lz;                                           // leading one at bit 127
+  const unsigned long long M = static_cast<unsigned long long>(u >> 64);
+  bool sticky = static_cast<unsigned long long>(u) != 0ull;
+  const int Ep = E + 64 - lz;                         // value = (M + sticky) 2^Ep
+  int q = Ep + 11;                                    // ulp exponent for a 53-bit result
+  if (q < -1074) q = -1074;                           // subnormal range
+  const int drop = q - Ep;                            // >= 11
+  unsigned long long keep, rem, half;
+  if (drop < 64) {
+    keep = M >> drop;
+    rem = M & ((1ull << drop) - 1ull);
+    half = 1ull << (drop - 1);
+  } else if (drop == 64) {
+    keep = 0ull; rem = M; half = 1ull << 63;
+  } else {
+    keep = 0ull; rem = 0ull; half = 1ull;             // below half an ulp of the smallest subnormal
+  }
+  keep += ((rem > half) || (rem == half && (sticky || (keep & 1ull)))) ? 1ull : 0ull;
+  unsigned long long bits;
+  if (keep == 0ull) {
+    bits = 0ull;
+  } else if (q + 1074 >= 2047) {
+    bits = 0x7FF0000000000000ull;                     // overflow
+  } else {
+    // keep <= 2^53: ((q + 1074) << 52) + keep encodes normals and subnormals alike
+    bits = (static_cast<unsigned long long>(q + 1074) << 52) + keep;
+    if (bits >= 0x7FF0000000000000ull) bits = 0x7FF0000000000000ull;
+  }
+  if (neg) bits |= 0x8000000000000000ull;
+  return __longlong_as_double(static_cast<long long>(bits));
+}
+
 // ------------------------------------------------------------------ smem / mbarrier
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));

@@ -28,12 +28,39 @@ struct SplitParams {
   const double2* X1; int ld1, rows1, k1;
   long long zstride1;
 };
-void launch_split(const SplitParams& p, int max_rows, int batch, cudaStream_t st);
+struct SplitPair { SplitParams s[2]; int nsides; };
+
+// ---- ozaki2.cu: Ozaki-II (CRT) residues, products and reconstruction
+constexpr int OZ2_MAXMOD = 16;
+struct Oz2Tables {
+  int N;                         // number of moduli
+  int mod[OZ2_MAXMOD];           // m_t
+  int pow256[OZ2_MAXMOD][8];     // 256^s mod m_t
+  int pm[OZ2_MAXMOD][OZ2_MAXMOD];   // (m_0 ... m_{j-1}) mod m_t, j < t (Garner)
+  int inv[OZ2_MAXMOD];           // (m_0 ... m_{t-1})^-1 mod m_t
+  unsigned long long P_lo, P_hi; // P = prod m_t (< 2^128)
+};
+// residue planes [batch][N][out_rows][kpad] of the integer images (beta bits) of one operand,
+// side and layout as the slice split; exponents as the slice split
+void launch_residue_split(const SplitParams& p, const Oz2Tables& T, int max_rows, int batch, cudaStream_t st);
+struct CrtParams {
+  const int* R;                  // [batch][N][m][ldr] exact integer products (stacked columns)
+  long long ldr, plane;          // row pitch (>= 2n) and plane size of R
+  const int* e; const int* f; long long e_stride, f_stride;
+  int m, n, batch, beta;
+  double2* C; int ldc; long long cstride;   // problem z output C + z cstride
+  double ar, ai, br, bi;
+  int mode;                      // EPI_STORE / EPI_LU / EPI_GENERAL
+};
+void launch_crt(const CrtParams& p, const Oz2Tables& T, cudaStream_t st);
+// one launch for operand a (rows_a rows) and, when b is given, operand b as well
+void launch_split(const SplitParams& a, int rows_a, const SplitParams* b, int rows_b, int batch, cudaStream_t st);
 
 // ---- slice_gemm.cu: tcgen05 slice-pair GEMM + exact reconstruction
 constexpr int MAX_PAIRS = 136;
 // EPI_IMINUS: C = I - RN(Z) without reading C (diagonal where the output row equals the column)
-enum EpiMode : int { EPI_STORE = 0, EPI_LU = 1, EPI_GENERAL = 2, EPI_GROUPS = 3, EPI_IMINUS = 4 };
+// EPI_RESIDUES: add every group's exact integer value to the int32 buffer `resid` (Ozaki-II)
+enum EpiMode : int { EPI_STORE = 0, EPI_LU = 1, EPI_GENERAL = 2, EPI_GROUPS = 3, EPI_IMINUS = 4, EPI_RESIDUES = 5 };
 struct GemmParams {
   int S;
   int npairs;
@@ -68,6 +95,9 @@ struct GemmParams {
   // the output crow[r / crow_b], whose order and leading dimension are crow_n[r / crow_b]
   // (or ldc1 for every output when crow_n is null); rows past that order are not written
   double2* const* crow; int crow_b; const int* crow_n;
+  // EPI_RESIDUES: group g of problem z, row r, stacked column c at resid[((z G + g) m1 + r) ldres + c]
+  int* resid; long long ldres;
+  int diag_pairs;                // 1: the pair list is not the tri/full set (runtime issue)
   uint8_t ps[MAX_PAIRS], pt[MAX_PAIRS], pg[MAX_PAIRS], pfirst[MAX_PAIRS];
 };
 void launch_slice_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const GemmParams& p, int BN,

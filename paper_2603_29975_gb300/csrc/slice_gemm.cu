@@ -30,45 +30,6 @@ constexpr int GEMM_EPI_WARPS = 16;
 constexpr int GEMM_THREADS = (2 + GEMM_EPI_WARPS) * 32;
 
 
-// RN-even of T * 2^E as binary64, integer instructions only (subnormals and overflow handled).
-__device__ __forceinline__ double round_scaled_dev(__int128 T, int E) {
-  if (T == 0) return 0.0;
-  const bool neg = T < 0;
-  unsigned __int128 u = neg ? static_cast<unsigned __int128>(-T) : static_cast<unsigned __int128>(T);
-  const unsigned long long hi0 = static_cast<unsigned long long>(u >> 64);
-  const int lz = hi0 ? __clzll(hi0) : 64 + __clzll(static_cast<unsigned long long>(u));
-  u <<= lz;                                           // leading one at bit 127
-  const unsigned long long M = static_cast<unsigned long long>(u >> 64);
-  bool sticky = static_cast<unsigned long long>(u) != 0ull;
-  const int Ep = E + 64 - lz;                         // value = (M + sticky) 2^Ep
-  int q = Ep + 11;                                    // ulp exponent for a 53-bit result
-  if (q < -1074) q = -1074;                           // subnormal range
-  const int drop = q - Ep;                            // >= 11
-  unsigned long long keep, rem, half;
-  if (drop < 64) {
-    keep = M >> drop;
-    rem = M & ((1ull << drop) - 1ull);
-    half = 1ull << (drop - 1);
-  } else if (drop == 64) {
-    keep = 0ull; rem = M; half = 1ull << 63;
-  } else {
-    keep = 0ull; rem = 0ull; half = 1ull;             // below half an ulp of the smallest subnormal
-  }
-  keep += ((rem > half) || (rem == half && (sticky || (keep & 1ull)))) ? 1ull : 0ull;
-  unsigned long long bits;
-  if (keep == 0ull) {
-    bits = 0ull;
-  } else if (q + 1074 >= 2047) {
-    bits = 0x7FF0000000000000ull;                     // overflow
-  } else {
-    // keep <= 2^53: ((q + 1074) << 52) + keep encodes normals and subnormals alike
-    bits = (static_cast<unsigned long long>(q + 1074) << 52) + keep;
-    if (bits >= 0x7FF0000000000000ull) bits = 0x7FF0000000000000ull;
-  }
-  if (neg) bits |= 0x8000000000000000ull;
-  return __longlong_as_double(static_cast<long long>(bits));
-}
-
 // RN-even of (hi 2^64 + lo) 2^E, the 128-bit two's-complement integer given as halves.
 // Normal results take the short path; subnormal or overflowing ones the general routine.
 __device__ __forceinline__ double round_hl(long long hi, unsigned long long lo, int E) {
@@ -568,7 +529,7 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
             const uint32_t sa = smem_u32(smem + stage * stage_bytes);
             const uint32_t sb = sa + a_bytes;
             const uint64_t da = smem_desc_sw32(sa), db = smem_desc_sw32(sb);
-            if constexpr (BN == 64)
+            if (BN == 64 && !p.diag_pairs)
               ok = issue_dispatch<BN>(S, p.fullset != 0, kb == kb0, tmem, static_cast<uint32_t>(da),
                                       static_cast<uint32_t>(db), static_cast<uint32_t>(da >> 32), idesc, acc_empty,
                                       (cc - 1) & 1, cc > 0, p.status, abort_flag);
@@ -605,7 +566,7 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       const int row = m0 + quad * 32 + lane;
       const bool rowok = row < m_z;
       if constexpr (COLS == 16) {
-        if (horner && G <= 8 && p.mode != EPI_GROUPS) {
+        if (horner && G <= 8 && p.mode != EPI_GROUPS && p.mode != EPI_RESIDUES) {
           EpiCtx x;
           x.row = row; x.z = z; x.m_z = m_z; x.n2_z = n2_z; x.n0 = n0; x.c0 = c0; x.tbase = tbase;
           x.rowok = rowok;
@@ -658,7 +619,17 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(&acc_empty[gi]);       // group gi may be overwritten now
-          if (p.mode == EPI_GROUPS) {
+          if (p.mode == EPI_RESIDUES) {
+            // this chunk's exact integer value of group gi (|v| <= 2^24), added to the product
+            if (rowok) {
+              int* dst = p.resid + ((static_cast<long long>(z) * G + gi) * m_z + row) * p.ldres;
+#pragma unroll
+              for (int j = 0; j < COLS; ++j) {
+                const int col = n0 + c0 + j;
+                if (col < n2_z) atomicAdd(&dst[col], __float2int_rn(__uint_as_float(v[j])));
+              }
+            }
+          } else if (p.mode == EPI_GROUPS) {
             if (z == 0 && rowok) {
 #pragma unroll
               for (int j = 0; j < COLS; ++j) {
@@ -686,8 +657,8 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       long long crow = 0, ldc = 0;
       int grow = 0, jlim = 0;
       bool rowok2 = rowok;
-      if (p.mode != EPI_GROUPS) out_row(p, single, z, row, rowok2, Cz, crow, grow, ldc, jlim);
-      if (p.mode != EPI_GROUPS && rowok2) {
+      if (p.mode != EPI_GROUPS && p.mode != EPI_RESIDUES) out_row(p, single, z, row, rowok2, Cz, crow, grow, ldc, jlim);
+      if (p.mode != EPI_GROUPS && p.mode != EPI_RESIDUES && rowok2) {
         const int er = p.e[z * p.e_stride + row] + p.base_exp;
         const int skip_n = (row < (single ? p.skm1 : (p.skm ? p.skm[z] : 0))) ? (single ? p.skn1 : p.skn[z]) : 0;
 #pragma unroll

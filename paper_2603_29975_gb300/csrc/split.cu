@@ -8,6 +8,8 @@
 //   right operand (side 1): out[z][s][2r][l]    = Re,  out[z][s][2r][k+l]   = -Im (digit-wise)
 //                           out[z][s][2r+1][l]  = Im,  out[z][s][2r+1][k+l] = Re
 // Positions [2k, kpad) of every written row are zero.  All integer work, no FP64 arithmetic.
+#include <algorithm>
+
 #include "ozk_params.cuh"
 
 namespace ozk {
@@ -17,39 +19,6 @@ namespace ozk {
 constexpr int SPLIT_ROWS = 32;
 constexpr int SPLIT_TK = 64;
 constexpr int SPLIT_THREADS = 256;
-
-__device__ __forceinline__ int frexp_exponent_from_bits(unsigned long long a) {
-  // a = |x| bit pattern (sign cleared), finite
-  if (a == 0ull) return 0;
-  const int ex = static_cast<int>(a >> 52);
-  if (ex > 0) return ex - 1022;
-  return -1010 - __clzll(a);          // subnormal: floor(log2 x) + 1
-}
-
-// X = trunc(x 2^(B - e)) computed exactly from the binary64 fields of x.
-__device__ __forceinline__ __int128 integer_image(double x, int e, int nbits) {
-  const unsigned long long u = __double_as_longlong(x);
-  const bool neg = (u >> 63) != 0ull;
-  const int ex = static_cast<int>((u >> 52) & 0x7FFull);
-  const unsigned long long man = u & ((1ull << 52) - 1ull);
-  unsigned long long M;
-  int E2;
-  if (ex == 0) { M = man; E2 = -1074; } else { M = man | (1ull << 52); E2 = ex - 1075; }
-  const int sh = E2 + nbits - e;
-  unsigned __int128 mag = 0;
-  if (M != 0ull) {
-    if (sh >= 0) mag = static_cast<unsigned __int128>(M) << sh;
-    else if (sh > -64) mag = static_cast<unsigned __int128>(M >> (-sh));
-  }
-  return neg ? -static_cast<__int128>(mag) : static_cast<__int128>(mag);
-}
-
-// Next balanced base-256 digit of X (least significant first); X is advanced.
-__device__ __forceinline__ int next_digit(__int128& X) {
-  const int d = static_cast<int>(static_cast<unsigned long long>(X + 128) & 255ull) - 128;
-  X = (X - d) >> 8;
-  return d;
-}
 
 // PER consecutive fp16 values (digits d[0..PER-1], negated when NEG) stored as one aligned
 // vector at dst.
@@ -109,8 +78,11 @@ __device__ __forceinline__ void split_run(const SplitParams& p, const double2* v
   }
 }
 
+// Both operands of one emulated GEMM in one launch: blockIdx.z selects the side.
 __global__ void __launch_bounds__(SPLIT_THREADS)
-split_kernel(const SplitParams p) {
+split_kernel(const SplitPair pp) {
+  if (static_cast<int>(blockIdx.z) >= pp.nsides) return;
+  const SplitParams& p = pp.s[blockIdx.z];
   const int z = blockIdx.y;
   const bool single = p.X == nullptr;
   const int R = single ? p.rows1 : p.rows[z];
@@ -249,9 +221,14 @@ split_kernel(const SplitParams p) {
   }
 }
 
-void launch_split(const SplitParams& p, int max_rows, int batch, cudaStream_t st) {
-  dim3 grid((max_rows + SPLIT_ROWS - 1) / SPLIT_ROWS, batch);
-  split_kernel<<<grid, SPLIT_THREADS, 0, st>>>(p);
+void launch_split(const SplitParams& a, int rows_a, const SplitParams* b, int rows_b, int batch, cudaStream_t st) {
+  SplitPair pp;
+  pp.s[0] = a;
+  pp.nsides = b ? 2 : 1;
+  if (b) pp.s[1] = *b;
+  const int rows = std::max(rows_a, b ? rows_b : 0);
+  dim3 grid((rows + SPLIT_ROWS - 1) / SPLIT_ROWS, batch, pp.nsides);
+  split_kernel<<<grid, SPLIT_THREADS, 0, st>>>(pp);
   record_launch();
 }
 
