@@ -35,11 +35,12 @@ L_SITES, B, E0 = 65, 16, 0.5 + 0.05j
 N = L_SITES * B
 FLOPS_PER_SOLVE = 8.0 / 3.0 * N ** 3          # effective FP64 flops of one tau_00 solve
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# dram__bytes_read.sum + dram__bytes_write.sum per slice_gemm launch, averaged over the 128
-# launches of one step of this workload (64 atoms), from the ncu capture summarised in
-# profiles/slice_gemm_kkr_batch64_dram.md; set back to None whenever the kernel or the
-# step's launch sequence changes until it is captured again
-SLICE_GEMM_DRAM_BYTES_PER_LAUNCH = None
+# dram__bytes_read.sum + dram__bytes_write.sum per slice_gemm launch, averaged over the 129
+# launches of one step of the default workload (256 atoms, S = 5 chosen by the selector,
+# nb = 64 chosen by the autotuner), from the ncu capture summarised in
+# profiles/slice_gemm_kkr_batch256_dram.md; set back to None whenever the kernel, the
+# workload or the step's launch sequence changes until it is captured again
+SLICE_GEMM_DRAM_BYTES_PER_LAUNCH = 591.75e6
 
 
 def parse():
@@ -255,7 +256,7 @@ def run_ours(args):
     roofline = {"bound": "tensor", "kernel": "slice_gemm_kernel (tcgen05 kind::f16, fp16-held int8 digits)",
                 "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4), "peak_source": f"{pk_kind} bf16 sustained (fp16 same rate)",
-                "traffic": SLICE_GEMM_DRAM_BYTES_PER_LAUNCH,
+                "traffic": SLICE_GEMM_DRAM_BYTES_PER_LAUNCH if (batch, args.S_chosen, args.nb) == (256, 5, 64) else None,
                 "algorithmic_flops_per_launch": per_launch, "launches": sg["launches"],
                 "avg_launch_us": round(1e3 * sg["ms"] / max(1, sg["launches"]), 2)}
     kernels = {k: {"launches": v["launches"], "ms_per_step": round(v["ms"] / args.steps, 3),
@@ -443,6 +444,17 @@ def config4_measure(ozk, h, args, dev):
         ms = ev[0].elapsed_time(ev[1])
         out["zgemm_5650"][str(S)] = {"ms": round(ms, 1), "eff_tflops": round(gflops / ms / 1e9, 3),
                                      "rel_err_vs_dmma": ozk.rel_diff(h, C, C_ref)}
+    out["zgemm_5650_ozaki2"] = {}
+    for nm in (10, 12, 14, 16):
+        ozk.ozaki2_zgemm(h, M0, M0, C, nmod=nm)
+        torch.cuda.synchronize()
+        ev[0].record()
+        ozk.ozaki2_zgemm(h, M0, M0, C, nmod=nm)
+        ev[1].record()
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1])
+        out["zgemm_5650_ozaki2"][str(nm)] = {"ms": round(ms, 1), "eff_tflops": round(gflops / ms / 1e9, 3),
+                                             "rel_err_vs_dmma": ozk.rel_diff(h, C, C_ref)}
     if h.status():
         raise RuntimeError("device status set in the n = 5650 sweep")
     return out

@@ -73,7 +73,9 @@ __global__ void __launch_bounds__(RS_THREADS) residue_split_kernel(const SplitPa
   const long long plane = p.out_rows * p.kpad;
   __half* outz = p.out + static_cast<long long>(z) * N * plane;
   const int nr = min(RS_ROWS, R - r0);
-  for (int idx = tid; idx < nr * K; idx += RS_THREADS) {
+  // stored row-fastest (trans == 0: rows of 32 consecutive threads) or column-fastest
+  const int span = p.trans ? nr * K : RS_ROWS * K;
+  for (int idx = tid; idx < span; idx += RS_THREADS) {
     int rl, l;
     if (!p.trans) { rl = idx % RS_ROWS; l = idx / RS_ROWS; if (rl >= nr) continue; }
     else          { rl = idx / K;       l = idx % K; }
