@@ -315,7 +315,7 @@ ozk_status_t run_emulated(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0
       launch_residue_split(sp, *g.oz2, g.mmax, g.batch, h->stream);
       launch_residue_split(sq, *g.oz2, g.nmax, g.batch, h->stream);
     } else {
-      launch_split(sp, g.mmax, &sq, g.nmax, g.batch, h->stream);
+      launch_split(sp, g.mmax, &sq, g.nmax, g.kmax, g.batch, h->stream);
     }
   }
 
@@ -834,7 +834,7 @@ ozk_status_t ozk_split_debug(ozk_handle_t h, int side, char trans, int rows, int
   sp.X = nullptr; sp.X1 = static_cast<const double2*>(X); sp.ld1 = ldx; sp.rows1 = rows; sp.k1 = k;
   // debug digits are always dumped in the stacked layout [S][rows_out][2k]
   sp.dbg_digits = digits;
-  launch_split(sp, rows, nullptr, 0, 1, h->stream);
+  launch_split(sp, rows, nullptr, 0, k, 1, h->stream);
   return cuda_check(cudaGetLastError(), "split launch");
 }
 

@@ -53,8 +53,10 @@ struct CrtParams {
   int mode;                      // EPI_STORE / EPI_LU / EPI_GENERAL
 };
 void launch_crt(const CrtParams& p, const Oz2Tables& T, cudaStream_t st);
-// one launch for operand a (rows_a rows) and, when b is given, operand b as well
-void launch_split(const SplitParams& a, int rows_a, const SplitParams* b, int rows_b, int batch, cudaStream_t st);
+// one launch for operand a (rows_a rows) and, when b is given, operand b as well; kmax: the
+// largest K of the problems (selects the kernel instance)
+void launch_split(const SplitParams& a, int rows_a, const SplitParams* b, int rows_b, int kmax, int batch,
+                  cudaStream_t st);
 
 // ---- slice_gemm.cu: tcgen05 slice-pair GEMM + exact reconstruction
 constexpr int MAX_PAIRS = 136;

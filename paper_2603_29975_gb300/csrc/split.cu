@@ -78,7 +78,10 @@ __device__ __forceinline__ void split_run(const SplitParams& p, const double2* v
   }
 }
 
-// Both operands of one emulated GEMM in one launch: blockIdx.z selects the side.
+// Both operands of one emulated GEMM in one launch: blockIdx.z selects the side.  VEC: the
+// widest digit run stored as one vector (8 in general; 2 for K <= 16, where the runs are 2 wide
+// and the smaller register footprint keeps more CTAs resident).
+template <int VEC>
 __global__ void __launch_bounds__(SPLIT_THREADS)
 split_kernel(const SplitPair pp) {
   if (static_cast<int>(blockIdx.z) >= pp.nsides) return;
@@ -162,12 +165,17 @@ split_kernel(const SplitPair pp) {
       const int r = r0 + rl;
       const int l0 = lt + lg;
       // vector stores when this thread's run is whole and aligned (and no debug copy)
-      const bool vec = !dbg && (per == 8 || per == 4 || per == 2) && K % per == 0 && l0 + per <= K;
+      const bool vec = !dbg && ((VEC >= 8 && per == 8) || (VEC >= 4 && per == 4) || per == 2) && K % per == 0 &&
+                       l0 + per <= K;
       if (r < R && vec) {
         const int e = rowexp[rl];
-        if (per == 8) split_run<8>(p, &tile[rl][lg], e, r, l0, K, outz, plane);
-        else if (per == 4) split_run<4>(p, &tile[rl][lg], e, r, l0, K, outz, plane);
-        else split_run<2>(p, &tile[rl][lg], e, r, l0, K, outz, plane);
+        if constexpr (VEC >= 8) {
+          if (per == 8) split_run<8>(p, &tile[rl][lg], e, r, l0, K, outz, plane);
+          else if (per == 4) split_run<4>(p, &tile[rl][lg], e, r, l0, K, outz, plane);
+          else split_run<2>(p, &tile[rl][lg], e, r, l0, K, outz, plane);
+        } else {
+          split_run<2>(p, &tile[rl][lg], e, r, l0, K, outz, plane);
+        }
       } else if (r < R) {
         const int e = rowexp[rl];
         for (int q = 0; q < per; ++q) {
@@ -221,14 +229,16 @@ split_kernel(const SplitPair pp) {
   }
 }
 
-void launch_split(const SplitParams& a, int rows_a, const SplitParams* b, int rows_b, int batch, cudaStream_t st) {
+void launch_split(const SplitParams& a, int rows_a, const SplitParams* b, int rows_b, int kmax, int batch,
+                  cudaStream_t st) {
   SplitPair pp;
   pp.s[0] = a;
   pp.nsides = b ? 2 : 1;
   if (b) pp.s[1] = *b;
   const int rows = std::max(rows_a, b ? rows_b : 0);
   dim3 grid((rows + SPLIT_ROWS - 1) / SPLIT_ROWS, batch, pp.nsides);
-  split_kernel<<<grid, SPLIT_THREADS, 0, st>>>(pp);
+  if (kmax <= 16) split_kernel<2><<<grid, SPLIT_THREADS, 0, st>>>(pp);
+  else split_kernel<8><<<grid, SPLIT_THREADS, 0, st>>>(pp);
   record_launch();
 }
 
