@@ -35,12 +35,12 @@ L_SITES, B, E0 = 65, 16, 0.5 + 0.05j
 N = L_SITES * B
 FLOPS_PER_SOLVE = 8.0 / 3.0 * N ** 3          # effective FP64 flops of one tau_00 solve
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# dram__bytes_read.sum + dram__bytes_write.sum per slice_gemm launch, averaged over the 129
+# dram__bytes_read.sum + dram__bytes_write.sum per slice_gemm launch, averaged over the
 # launches of one step of the default workload (256 atoms, S = 5 chosen by the selector,
 # nb = 64 chosen by the autotuner), from the ncu capture summarised in
 # profiles/slice_gemm_kkr_batch256_dram.md; set back to None whenever the kernel, the
 # workload or the step's launch sequence changes until it is captured again
-SLICE_GEMM_DRAM_BYTES_PER_LAUNCH = 591.75e6
+SLICE_GEMM_DRAM_BYTES_PER_LAUNCH = None
 
 
 def parse():
@@ -638,10 +638,10 @@ def cpu_baseline(t0_atom, G_np, S, nb):
     co.build()
     M = kkr.kkr_build(t0_atom, G_np)
     t1 = time.perf_counter()
-    co.tau00_block(M, t0_atom[0], nb, S=S, leaf=B)
+    co.tau00_block(M, t0_atom[0], nb, S=S)
     dt = time.perf_counter() - t1
     return {"value": round(1.0 / dt, 4), "unit": "tau00 solves/s", "cores": co.num_threads(), "kind": "oracle",
-            "sample": f"1 solve of the same workload (n={N}, S={S}, panels nb={nb} of {B}x{B} leaves) by "
+            "sample": f"1 solve of the same workload (n={N}, S={S}, {nb}x{nb} pivot blocks) by "
                       f"oracle/c (OpenMP), {dt:.1f} s"}
 
 
@@ -661,14 +661,14 @@ def run_reference(args):
     nb = args.nb or 64                            # the GPU arm autotunes; the oracle uses 64
     S = args.S or 7                               # the GPU arm's selector runs on the GPU; the oracle uses 7
     for _ in range(args.warmup):
-        co.tau00_block(M, t[0], nb, S=S, leaf=B)
+        co.tau00_block(M, t[0], nb, S=S)
     t1 = time.perf_counter()
     for _ in range(args.steps):
-        co.tau00_block(M, t[0], nb, S=S, leaf=B)
+        co.tau00_block(M, t[0], nb, S=S)
     dt = time.perf_counter() - t1
     v = args.steps / dt
-    sample = (f"{args.steps} timed solves of one atom of the workload (n={N}, S={S}, panels nb={nb} "
-              f"of {B}x{B} leaves) by oracle/c with OpenMP; one solve per step instead of {args.batch}")
+    sample = (f"{args.steps} timed solves of one atom of the workload (n={N}, S={S}, {nb}x{nb} "
+              f"pivot blocks) by oracle/c with OpenMP; one solve per step instead of {args.batch}")
     line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "tau00 solves/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

@@ -306,16 +306,17 @@ ozk_status_t kkr_build_m_shared_sizes(ozk_handle_t handle, int natoms, const int
  * multiple scattering matrix).  Panels J = [p, q) of width nb are eliminated from the trailing
  * end of M, so the centre block (site 0, rows/cols 0..b-1) is eliminated last and S_00 is the
  * Schur complement left there.
- *   S >= 1: every GEMM is the emulated ZGEMM with S slices; each panel is factored leaf by leaf
- *           (b x b pivot blocks, Gauss-Jordan with partial pivoting in binary64), each leaf
- *           updating only the rows and columns outside [0, p) x [0, p); the panel's update
- *           of [0, p) x [0, p) is one GEMM with k = q - p.  nb <= 128.
- *   S <= 0: binary64 DMMA GEMMs with one nb x nb pivot block per panel (nb <= 64).
+ * Each panel: D^-1 of its pivot block D = M[p:q, p:q] (in-place Gauss-Jordan with partial
+ * pivoting in binary64), L = M[0:p, p:q] D^-1 written in place, M[0:p, 0:p] -= L M[p:q, 0:p].
+ *   S >= 1: both GEMMs are the emulated ZGEMM with S slices.
+ *   S <= 0: both GEMMs are binary64 DMMA GEMMs (the baseline).
+ *   nb <= OZK_NB_MAX (the pivot block is held in shared memory).
  *   M   : DEVICE n x n column major (ld n), DESTROYED (overwritten by the factorisation).
  *   t0  : DEVICE b x b column major.  tau00: DEVICE b x b column major output.
  *   b <= 64 (16 for lmax = 3; 50 for lmax = 4 with spin), nb a multiple of b.  Site 0 occupies
- *   rows/cols 0..b-1.  Pivot blocks up to 16 x 16 use a 4-warp Gauss-Jordan kernel, larger ones a
- *   256-thread one. */
+ *   rows/cols 0..b-1; the final S_00^-1 t_0 is a Gauss-Jordan solve (a 4-warp kernel up to
+ *   16 x 16, a 256-thread one above). */
+#define OZK_NB_MAX 112            /* largest panel width of the tau_00 solves */
 ozk_status_t kkr_tau00(ozk_handle_t handle, int n, int b, void* M, const void* t0, void* tau00,
                        int S, int nb);
 
@@ -343,7 +344,7 @@ ozk_status_t kkr_contour_trace(ozk_handle_t handle, int nsolves, int b, const vo
 
 /* Autotuner of the batched solve: times kkr_tau00_batched on scratch matrices of the sizes
  * n[0..nsolves-1] (diagonally dominant test matrices, allocated and freed here) for every
- * panel width nb = b, 2b, ... <= 128, returns the fastest in *nb_best (HOST) and the times in
+ * panel width nb = b, 2b, ... <= OZK_NB_MAX, returns the fastest in *nb_best (HOST) and the times in
  * ms in times[] (HOST, one per candidate in that order; may be NULL), and caches the choice in
  * the handle for nb = 0.  Synchronises; cannot be captured. */
 ozk_status_t kkr_tau00_autotune(ozk_handle_t handle, int nsolves, const int* n, int b, int S, int* nb_best,

@@ -23,6 +23,7 @@ OZK_SEL_OUTPUTS = 8
 OZK_SEL_NPARAMS = 5768
 OZK_SEL_SMIN, OZK_SEL_SMAX = 3, 10
 OZK_SEL_NO_FALLBACK = 1
+OZK_NB_MAX = 112
 SELECTOR_WEIGHTS = os.path.join(HERE, "selector_weights.bin")
 
 
@@ -388,7 +389,7 @@ def kkr_tau00_autotune(h: Handle, n_list, b: int, S: int = 7):
     """Time every panel width for these sizes; returns (best nb, {nb: ms})."""
     ns = len(n_list)
     n = (ctypes.c_int * ns)(*[int(v) for v in n_list])
-    cands = list(range(b, 129, b))
+    cands = list(range(b, OZK_NB_MAX + 1, b))
     times = (ctypes.c_float * len(cands))()
     best = ctypes.c_int(0)
     _check(lib().kkr_tau00_autotune(h.ptr, ns, n, b, S, ctypes.byref(best), times), "kkr_tau00_autotune")

@@ -871,13 +871,13 @@ ozk_status_t kkr_build_m(ozk_handle_t h, int L, int b, const void* t, const void
   return cuda_check(cudaGetLastError(), "build_m launch");
 }
 
-// tau_00 of one matrix: eliminate panels J = [p, q) from the trailing end, centre last.
-// Emulated path: two-level block LU, each panel factored leaf by leaf (b x b pivot blocks), its
-// trailing update deferred to one GEMM with k = q - p.  DMMA path: one pivot block per panel.
+// tau_00 of one matrix: eliminate panels J = [p, q) from the trailing end, centre last.  Each
+// panel: D^-1 of its pivot block (binary64 Gauss-Jordan), L = M_RJ D^-1 and M_RR -= L M_JR as
+// emulated GEMMs (S >= 1) or binary64 DMMA GEMMs (S <= 0).
 ozk_status_t kkr_tau00(ozk_handle_t h, int n, int b, void* Mv, const void* t0, void* tau, int S, int nb) {
   if (!h || !Mv || !t0 || !tau) return set_error(OZK_ERR_ARG, "null argument");
-  if (b <= 0 || n <= 0 || n % b || nb < b || nb % b || b > 64 || nb > (S > 0 ? 128 : 64))
-    return set_error(OZK_ERR_ARG, "need n % b == 0, b <= 64, b <= nb, nb % b == 0, nb <= 128 (64 for S <= 0)");
+  if (b <= 0 || n <= 0 || n % b || nb < b || nb % b || b > 64 || nb > GJINV_MAX)
+    return set_error(OZK_ERR_ARG, "need n % b == 0, b <= 64, b <= nb <= 112, nb % b == 0");
   double2* M = static_cast<double2*>(Mv);
   const size_t dinv_bytes = align_up(sizeof(double2) * nb * nb, 1024);
   {
@@ -895,51 +895,32 @@ ozk_status_t kkr_tau00(ozk_handle_t h, int n, int b, void* Mv, const void* t0, v
   }
   double2* Dinv = static_cast<double2*>(h->ws);
   for (int q = n; q > b;) {
-    const int p = std::max(q - nb, b);
+    const int p = std::max(q - nb, b), w = q - p, r = p;
+    GjParams gj{};
+    gj.D = nullptr; gj.D1 = M + p + static_cast<long long>(p) * n; gj.ldd1 = n; gj.nb1 = w;
+    gj.X1 = Dinv; gj.ldx1 = w; gj.status = h->d_status;
+    {
+      Prof pr(h, OZK_KIND_GJ, 8.0 * w * w * w, 32.0 * w * w);
+      launch_gjinv(gj, w, 1, h->stream);
+    }
+    double2* Lp = M + static_cast<long long>(p) * n;            // M[0:p, p:q]
+    const double2* Up = M + p;                                   // M[p:q, 0:p]
     if (S > 0) {
-      for (int a = q - b; a >= p; a -= b) {
-        GjParams gj{};
-        gj.D = nullptr; gj.D1 = M + a + static_cast<long long>(a) * n; gj.ldd1 = n; gj.nb1 = b;
-        gj.R1 = nullptr; gj.X1 = Dinv; gj.ldx1 = b; gj.nrhs = b; gj.status = h->d_status;
-        {
-          Prof pr(h, OZK_KIND_GJ, 16.0 * b * b * b, 32.0 * b * b);
-          launch_gj(gj, b, b, 1, h->stream);
-        }
-        double2* Lc = M + static_cast<long long>(a) * n;          // M[0:a, a:a+b]
-        EmuGemm g1;
-        g1.oa = {0, 0}; g1.ob = {0, 0}; g1.batch = 1;
-        g1.mmax = g1.m = a; g1.nmax = g1.n = b; g1.kmax = g1.k = b;
-        g1.A = Lc; g1.lda = n; g1.B = Dinv; g1.ldb = b; g1.C = Lc; g1.ldc = n;
-        g1.S = S; g1.ar = 1; g1.br = 0;
-        ozk_status_t st = run_emulated(h, g1, dinv_bytes);
-        if (st) return st;
-        if (a > p) {
-          EmuGemm g2 = g1;                                          // rank-b update outside [0,p)^2
-          g2.nmax = g2.n = a;
-          g2.A = Lc; g2.lda = n; g2.B = M + a; g2.ldb = n; g2.C = M; g2.ldc = n;
-          g2.ar = -1; g2.br = 1; g2.skm = p; g2.skn = p;
-          st = run_emulated(h, g2, dinv_bytes);
-          if (st) return st;
-        }
-      }
-      EmuGemm g3;                                                   // deferred panel update
-      g3.oa = {0, 0}; g3.ob = {0, 0}; g3.batch = 1;
-      g3.mmax = g3.m = p; g3.nmax = g3.n = p; g3.kmax = g3.k = q - p;
-      g3.A = M + static_cast<long long>(p) * n; g3.lda = n; g3.B = M + p; g3.ldb = n; g3.C = M; g3.ldc = n;
-      g3.S = S; g3.ar = -1; g3.br = 1;
-      ozk_status_t st = run_emulated(h, g3, dinv_bytes);
+      EmuGemm g1;                                                 // L = M_RJ D^-1, in place
+      g1.oa = {0, 0}; g1.ob = {0, 0}; g1.batch = 1;
+      g1.mmax = g1.m = r; g1.nmax = g1.n = w; g1.kmax = g1.k = w;
+      g1.A = Lp; g1.lda = n; g1.B = Dinv; g1.ldb = w; g1.C = Lp; g1.ldc = n;
+      g1.S = S; g1.ar = 1; g1.br = 0;
+      ozk_status_t st = run_emulated(h, g1, dinv_bytes);
+      if (st) return st;
+      EmuGemm g2;                                                 // M_RR -= L M_JR
+      g2.oa = {0, 0}; g2.ob = {0, 0}; g2.batch = 1;
+      g2.mmax = g2.m = r; g2.nmax = g2.n = r; g2.kmax = g2.k = w;
+      g2.A = Lp; g2.lda = n; g2.B = Up; g2.ldb = n; g2.C = M; g2.ldc = n;
+      g2.S = S; g2.ar = -1; g2.br = 1;
+      st = run_emulated(h, g2, dinv_bytes);
       if (st) return st;
     } else {
-      const int w = q - p, r = p;
-      GjParams gj{};
-      gj.D = nullptr; gj.D1 = M + p + static_cast<long long>(p) * n; gj.ldd1 = n; gj.nb1 = w;
-      gj.R1 = nullptr; gj.X1 = Dinv; gj.ldx1 = w; gj.nrhs = w; gj.status = h->d_status;
-      {
-        Prof pr(h, OZK_KIND_GJ, 16.0 * w * w * w, 32.0 * w * w);
-        launch_gj(gj, w, w, 1, h->stream);
-      }
-      double2* Lp = M + static_cast<long long>(p) * n;
-      const double2* Up = M + p;
       // binary64 DMMA baseline: L = M_RJ Dinv into the scratch, copy back, then update
       double2* Ltmp = reinterpret_cast<double2*>(static_cast<uint8_t*>(h->ws) + dinv_bytes);
       DmmaParams d1{};
@@ -1052,19 +1033,19 @@ static ozk_status_t tau00_batched_impl(ozk_handle_t h, int nsolves, const int* n
   if (nsolves < 0) return set_error(OZK_ERR_ARG, "negative nsolves");
   if (nsolves == 0) return OZK_OK;
   if (S <= 0) return set_error(OZK_ERR_ARG, "batched solves run the emulated path (S >= 1)");
-  if (b <= 0 || b > 64 || nb < b || nb % b || nb > 128) return set_error(OZK_ERR_ARG, "need b <= 64, b <= nb <= 128, nb % b == 0");
+  if (b <= 0 || b > 64 || nb < b || nb % b || nb > GJINV_MAX)
+    return set_error(OZK_ERR_ARG, "need b <= 64, b <= nb <= 112, nb % b == 0");
   int nmax = 0;
   for (int i = 0; i < nsolves; ++i) {
     if (n[i] <= 0 || n[i] % b) return set_error(OZK_ERR_ARG, "every n[i] must be a positive multiple of b");
     nmax = std::max(nmax, n[i]);
   }
   const int panels = (nmax - b + nb - 1) / nb;
-  const int leaves = nb / b;
-  // workspace layout: [Dinv][step tables][GEMM workspace]; the n table is a size table
+  // workspace layout: [D^-1 per solve, nb x nb][step tables][GEMM workspace]
   const size_t ns = static_cast<size_t>(nsolves);
   const size_t off_dinv = 0;
-  const size_t off_tab = align_up(off_dinv + ns * b * b * sizeof(double2), 1024);
-  const size_t n_ptr = 10, n_int = 18;
+  const size_t off_tab = align_up(off_dinv + ns * nb * nb * sizeof(double2), 1024);
+  const size_t n_ptr = 8, n_int = 16;
   const size_t off_gemm = align_up(off_tab + ns * (n_ptr * sizeof(void*) + n_int * sizeof(int)), 1024);
   EmuGemm probe;
   probe.batch = nsolves; probe.mmax = nmax; probe.nmax = nmax; probe.kmax = nb; probe.S = S;
@@ -1088,11 +1069,10 @@ static ozk_status_t tau00_batched_impl(ozk_handle_t h, int nsolves, const int* n
   t.ldd = pi + 0 * ns; t.nbv = pi + 1 * ns; t.ldx = pi + 2 * ns;
   t.lda1 = pi + 3 * ns; t.ldb1 = pi + 4 * ns; t.ldc1 = pi + 5 * ns; t.m1 = pi + 6 * ns; t.n1 = pi + 7 * ns; t.k1 = pi + 8 * ns;
   t.lda2 = pi + 9 * ns; t.ldb2 = pi + 10 * ns; t.ldc2 = pi + 11 * ns; t.m2 = pi + 12 * ns; t.n2 = pi + 13 * ns; t.k2 = pi + 14 * ns;
-  t.skm2 = pi + 15 * ns; t.skn2 = pi + 16 * ns;
   double2* const* Mp = reinterpret_cast<double2* const*>(M);
 
   auto gemm_tables = [&](int which, int mmax, int nmaxg, int kmax, double smnk, double smk, double snk,
-                         bool lu, bool skip, int box = 0) -> ozk_status_t {
+                         bool lu) -> ozk_status_t {
     EmuGemm g;
     g.oa = {0, 0}; g.ob = {0, 0}; g.batch = nsolves; g.mmax = mmax; g.nmax = nmaxg; g.kmax = kmax; g.S = S;
     if (which == 1) {
@@ -1101,73 +1081,51 @@ static ozk_status_t tau00_batched_impl(ozk_handle_t h, int nsolves, const int* n
     } else {
       g.tA = t.A2; g.tlda = t.lda2; g.tB = t.B2; g.tldb = t.ldb2; g.tC = t.C2; g.tldc = t.ldc2;
       g.tm = t.m2; g.tn = t.n2; g.tk = t.k2;
-      if (skip) { g.tskm = t.skm2; g.tskn = t.skn2; g.box_m = box; g.box_n = box; }
     }
     g.ar = lu ? -1 : 1; g.br = lu ? 1 : 0;
     g.sum_mnk = smnk; g.sum_mk = smk; g.sum_nk = snk;
     return run_emulated(h, g, off_gemm);
   };
 
+  // panel s of every solve: J = [p, q), q = n - s nb, p = max(q - nb, b), w = q - p.
+  // D^-1 of the w x w pivot block (binary64), L = M_RJ D^-1 in place (m = p, n = k = w),
+  // M_RR -= L M_JR (m = n = p, k = w); the centre block is eliminated last
   for (int s = 0; s < panels; ++s) {
-    for (int l = 0; l < leaves; ++l) {
-      int amax = 0, a2max = 0, nact = 0, pmin = 1 << 30;
-      double s1 = 0, s2 = 0, sa = 0;
-      for (int i = 0; i < nsolves; ++i) {
-        const int q = n[i] - s * nb;
-        if (q <= b) continue;
-        const int p = std::max(q - nb, b);
-        const int a = q - b * (l + 1);
-        if (a < p) continue;
-        ++nact;
-        amax = std::max(amax, a);
-        s1 += static_cast<double>(a) * b * b;
-        sa += static_cast<double>(a) * b;
-        if (a > p) {
-          a2max = std::max(a2max, a);
-          pmin = std::min(pmin, p);
-          s2 += (static_cast<double>(a) * a - static_cast<double>(p) * p) * b;
-        }
-      }
-      if (nact == 0) continue;
-      {
-        Prof pr(h, OZK_KIND_OTHER, 0.0, 0.0);
-        launch_kkr_step(s, l, nsolves, dn, Mp, b, nb, dinv, t, h->stream);
-      }
-      GjParams gj{};
-      gj.D = t.D; gj.ldd = t.ldd; gj.nb = t.nbv; gj.R = nullptr; gj.X = t.X; gj.ldx = t.ldx; gj.nrhs = b;
-      gj.status = h->d_status;
-      {
-        Prof pr(h, OZK_KIND_GJ, 16.0 * b * b * b * nact, 32.0 * nact * b * b);
-        launch_gj(gj, b, b, nsolves, h->stream);
-      }
-      st = gemm_tables(1, amax, b, b, s1, sa, nact * static_cast<double>(b) * b, false, false);
-      if (st) return st;
-      if (a2max > 0) {
-        st = gemm_tables(2, a2max, a2max, b, s2, sa, sa, true, true, pmin);
-        if (st) return st;
-      }
-    }
-    int pmax = 0;
-    double s3 = 0, sa3 = 0;
+    int pmax = 0, wmax = 0, nact = 0;
+    double s1 = 0, sa = 0, sw = 0, s3 = 0, sw3 = 0;
     for (int i = 0; i < nsolves; ++i) {
       const int q = n[i] - s * nb;
       if (q <= b) continue;
-      const int p = std::max(q - nb, b);
+      const int p = std::max(q - nb, b), w = q - p;
+      ++nact;
       pmax = std::max(pmax, p);
-      s3 += static_cast<double>(p) * p * (q - p);
-      sa3 += static_cast<double>(p) * (q - p);
+      wmax = std::max(wmax, w);
+      s1 += static_cast<double>(p) * w * w;
+      sa += static_cast<double>(p) * w;
+      sw += static_cast<double>(w) * w;
+      s3 += static_cast<double>(p) * p * w;
+      sw3 += static_cast<double>(w) * w * w;
     }
-    if (pmax == 0) continue;
+    if (nact == 0) continue;
     {
       Prof pr(h, OZK_KIND_OTHER, 0.0, 0.0);
-      launch_kkr_step(s, -1, nsolves, dn, Mp, b, nb, dinv, t, h->stream);
+      launch_kkr_step(s, nsolves, dn, Mp, b, nb, dinv, t, h->stream);
     }
-    st = gemm_tables(2, pmax, pmax, nb, s3, sa3, sa3, true, false);
+    GjParams gj{};
+    gj.D = t.D; gj.ldd = t.ldd; gj.nb = t.nbv; gj.R = nullptr; gj.X = t.X; gj.ldx = t.ldx; gj.nrhs = 0;
+    gj.status = h->d_status;
+    {
+      Prof pr(h, OZK_KIND_GJ, 8.0 * sw3, 32.0 * sw);
+      launch_gjinv(gj, wmax, nsolves, h->stream);
+    }
+    st = gemm_tables(1, pmax, wmax, wmax, s1, sa, sw, false);
+    if (st) return st;
+    st = gemm_tables(2, pmax, pmax, wmax, s3, sa, sa, true);
     if (st) return st;
   }
   {
     Prof pr(h, OZK_KIND_OTHER, 0.0, 0.0);
-    launch_kkr_step(-1, 0, nsolves, dn, Mp, b, nb, dinv, t, h->stream);
+    launch_kkr_step(-1, nsolves, dn, Mp, b, nb, dinv, t, h->stream);
   }
   GjParams gj{};
   gj.D = t.D; gj.ldd = t.ldd; gj.nb = t.nbv;
@@ -1391,7 +1349,7 @@ ozk_status_t kkr_tau00_autotune(ozk_handle_t h, int nsolves, const int* n, int b
   if (!st) st = cuda_check(cudaMemcpyAsync(ptrs, hp.data(), sizeof(void*) * hp.size(), cudaMemcpyHostToDevice, h->stream),
                            "upload autotune pointers");
   std::vector<int> cands;
-  for (int nb = b; nb <= 128; nb += b) cands.push_back(nb);
+  for (int nb = b; nb <= GJINV_MAX; nb += b) cands.push_back(nb);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (!st) st = cuda_check(cudaEventCreate(&e0), "cudaEventCreate");
   if (!st) st = cuda_check(cudaEventCreate(&e1), "cudaEventCreate");

@@ -3,6 +3,8 @@
 //   * gj_solve_kernel  : Gauss-Jordan elimination with partial pivoting on [D | R] for a
 //                        batch of small blocks (D up to 64 x 64): R = I gives D^-1 (the
 //                        pivot-block inverse of the block LU), R = t_0 gives S_00^-1 t_0.
+//   * gjinv_kernel     : in-place Gauss-Jordan inversion with partial pivoting of pivot blocks
+//                        up to 112 x 112 (the panel's D^-1 of the block LU).
 //   * build_m_kernel   : M = I - blockdiag(t) G.
 //   * scale_kernel     : C = beta C (the k == 0 / alpha == 0 case of the GEMM API).
 // These are the only places with O(n b^2) / O(n^2 b) binary64 arithmetic of the solve.
@@ -202,6 +204,130 @@ gj16_kernel(const GjParams p) {
   }
 }
 
+// In-place Gauss-Jordan inversion with partial pivoting: X = D^-1 for a batch of pivot blocks
+// of order w <= GJINV_MAX (the nb x nb diagonal block of a block-LU panel).  Step k swaps row k
+// with the row of largest |.|^2 in column k (at or below k), scales the row by the pivot's
+// reciprocal, eliminates column k from every other row and stores the k-th column of the
+// inverse in its place; after the last step the row interchanges are undone as column
+// interchanges in reverse order.  w^2 complex of shared memory (the [D | I] form of
+// gj_solve_kernel needs twice that) and w^3 complex multiply-adds per block.
+constexpr int GJINV_THREADS = 256;
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__global__ void __launch_bounds__(GJINV_THREADS)
+gjinv_kernel(const GjParams p) {
+  extern __shared__ double2 A[];            // [w][w] column major
+  __shared__ double2 colk[GJINV_MAX];
+  __shared__ int perm[GJINV_MAX];
+  __shared__ int src[GJINV_MAX];
+  __shared__ int s_piv, s_sing;
+  __shared__ double2 s_pinv;
+  const int z = blockIdx.x;
+  const bool single = p.D == nullptr;
+  const int w = single ? p.nb1 : p.nb[z];
+  if (w <= 0) return;
+  const double2* D = single ? p.D1 : p.D[z];
+  const long long ldd = single ? p.ldd1 : p.ldd[z];
+  double2* X = single ? p.X1 : p.X[z];
+  const long long ldx = single ? p.ldx1 : p.ldx[z];
+  const int tid = threadIdx.x;
+  const int ww = w * w;
+  for (int idx = tid; idx < ww; idx += GJINV_THREADS) {
+    const int j = idx / w, i = idx - j * w;
+    A[idx] = D[i + j * ldd];
+  }
+  if (tid == 0) s_sing = 0;
+  __syncthreads();
+  for (int k = 0; k < w; ++k) {
+    if (tid < 32) {
+      // partial pivoting: first row of largest |.|^2 in column k at or below row k
+      double best = -1.0;
+      int bi = k;
+      for (int r = k + tid; r < w; r += 32) {
+        const double2 v = A[r + k * w];
+        const double a = v.x * v.x + v.y * v.y;
+        if (a > best) { best = a; bi = r; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_down_sync(0xffffffffu, best, o);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (tid == 0) {
+        s_piv = bi;
+        perm[k] = bi;
+        if (best <= 0.0) {
+          s_sing = 1;
+        } else {
+          const double2 v = A[bi + k * w];
+          const double inv = 1.0 / best;               // the one division of the step
+          s_pinv = make_double2(v.x * inv, -v.y * inv);
+        }
+      }
+    }
+    __syncthreads();
+    if (s_sing) break;
+    const int piv = s_piv;
+    const double2 pinv = s_pinv;
+    // rows k and piv exchanged outside column k, the new row k scaled; column k as it reads
+    // after the exchange (zero in the pivot row) kept aside -- no thread writes it here
+    for (int j = tid; j < w; j += GJINV_THREADS) {
+      if (j == k) continue;
+      const double2 a = A[k + j * w], b = A[piv + j * w];
+      if (piv != k) A[piv + j * w] = a;
+      A[k + j * w] = cmul(b, pinv);
+    }
+    for (int i = tid; i < w; i += GJINV_THREADS)
+      colk[i] = (i == k) ? make_double2(0.0, 0.0) : A[(i == piv ? k : i) + k * w];
+    __syncthreads();
+    for (int idx = tid; idx < ww; idx += GJINV_THREADS) {
+      const int j = idx / w, i = idx - j * w;
+      if (j == k) {
+        const double2 c = cmul(colk[i], pinv);
+        A[idx] = (i == k) ? pinv : make_double2(-c.x, -c.y);
+      } else if (i != k) {
+        // y -= f x as four fused multiply-adds (binary64 issue is the scarce resource)
+        const double2 f = colk[i];
+        const double2 x = A[k + j * w];
+        double2 y = A[idx];
+        y.x = fma(-f.x, x.x, y.x);
+        y.x = fma(f.y, x.y, y.x);
+        y.y = fma(-f.x, x.y, y.y);
+        y.y = fma(-f.y, x.x, y.y);
+        A[idx] = y;
+      }
+    }
+    __syncthreads();
+  }
+  const bool singular = s_sing != 0;
+  if (tid == 0) {
+    if (singular) flag_error(p.status, OZK_ERR_SINGULAR);
+    for (int j = 0; j < w; ++j) src[j] = j;
+    if (!singular)
+      for (int k = w - 1; k >= 0; --k) {
+        const int r = perm[k];
+        if (r != k) { const int t = src[k]; src[k] = src[r]; src[r] = t; }
+      }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < ww; idx += GJINV_THREADS) {
+    const int j = idx / w, i = idx - j * w;
+    X[i + j * ldx] = singular ? make_double2(0.0, 0.0) : A[i + src[j] * w];
+  }
+}
+
+void launch_gjinv(const GjParams& p, int max_w, int batch, cudaStream_t st) {
+  const size_t smem = sizeof(double2) * static_cast<size_t>(max_w) * max_w;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(gjinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  gjinv_kernel<<<batch, GJINV_THREADS, smem, st>>>(p);
+  record_launch();
+}
+
 void launch_gj(const GjParams& p, int max_nb, int max_nrhs, int batch, cudaStream_t st) {
   if (max_nb <= 16 && max_nb + max_nrhs <= 32) {
     gj16_kernel<<<batch, GJ16_THREADS, 0, st>>>(p);
@@ -377,48 +503,37 @@ void launch_scale(int m, int n, double2* C, long long ldc, double br, double bi,
 
 namespace ozk {
 
-// Per-solve tables of one sub-step of the batched two-level block LU.  Panel `step` is
-// J = [p, q) with q = n - step nb, p = max(q - nb, b); its leaves [a, a + b) run from the last
-// (leaf 0: a = q - b) down to a = p.  A leaf sub-step fills the Gauss-Jordan table (pivot block
-// M[a:a+b, a:a+b]), GEMM 1 (L column M[0:a, a:a+b] D^-1, in place) and GEMM 2 (rank-b update of
-// [0, a) x [0, a) outside the skip box [0, p) x [0, p)); leaf < 0 fills GEMM 2 with the panel's
-// deferred update of [0, p) x [0, p); step < 0 the final S_00 solve.  Finished or inactive
-// solves get zero sizes.
-__global__ void kkr_step_kernel(int step, int leaf, int nsolves, const int* __restrict__ n, double2* const* M, int b,
-                                int nb, double2* dinv, KkrStep t) {
+// Per-solve tables of one step of the batched block LU.  Panel `step` is J = [p, q) with
+// q = n - step nb, p = max(q - nb, b), w = q - p: the pivot-block inverse table (D = M[p:q, p:q],
+// D^-1 into the solve's nb x nb slot of dinv), GEMM 1 (L = M[0:p, p:q] D^-1, in place) and GEMM 2
+// (M[0:p, 0:p] -= L M[p:q, 0:p]); step < 0 the final S_00 solve.  Finished solves get zero
+// sizes.
+__global__ void kkr_step_kernel(int step, int nsolves, const int* __restrict__ n, double2* const* M, int b, int nb,
+                                double2* dinv, KkrStep t) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nsolves) return;
   const int ni = n[i];
   double2* Mi = M[i];
-  double2* Di = dinv + static_cast<long long>(i) * b * b;
+  double2* Di = dinv + static_cast<long long>(i) * nb * nb;
   // defaults: nothing to do
-  t.D[i] = Mi; t.ldd[i] = ni; t.nbv[i] = 0; t.X[i] = Di; t.ldx[i] = b;
-  t.A1[i] = Mi; t.lda1[i] = ni; t.B1[i] = Di; t.ldb1[i] = b; t.C1[i] = Mi; t.ldc1[i] = ni;
+  t.D[i] = Mi; t.ldd[i] = ni; t.nbv[i] = 0; t.X[i] = Di; t.ldx[i] = nb;
+  t.A1[i] = Mi; t.lda1[i] = ni; t.B1[i] = Di; t.ldb1[i] = nb; t.C1[i] = Mi; t.ldc1[i] = ni;
   t.m1[i] = 0; t.n1[i] = 0; t.k1[i] = b;
   t.A2[i] = Mi; t.lda2[i] = ni; t.B2[i] = Mi; t.ldb2[i] = ni; t.C2[i] = Mi; t.ldc2[i] = ni;
-  t.m2[i] = 0; t.n2[i] = 0; t.k2[i] = b; t.skm2[i] = 0; t.skn2[i] = 0;
+  t.m2[i] = 0; t.n2[i] = 0; t.k2[i] = b;
   if (step < 0) { t.nbv[i] = b; return; }
   const int q = ni - step * nb;
   if (q <= b) return;
-  const int p = max(q - nb, b);
-  if (leaf >= 0) {
-    const int a = q - b * (leaf + 1);
-    if (a < p) return;
-    t.D[i] = Mi + a + static_cast<long long>(a) * ni; t.nbv[i] = b;
-    double2* Lc = Mi + static_cast<long long>(a) * ni;
-    t.A1[i] = Lc; t.C1[i] = Lc; t.m1[i] = a; t.n1[i] = b;
-    if (a > p) {
-      t.A2[i] = Lc; t.B2[i] = Mi + a; t.m2[i] = a; t.n2[i] = a; t.skm2[i] = p; t.skn2[i] = p;
-    }
-  } else {
-    t.A2[i] = Mi + static_cast<long long>(p) * ni; t.B2[i] = Mi + p;
-    t.m2[i] = p; t.n2[i] = p; t.k2[i] = q - p;
-  }
+  const int p = max(q - nb, b), w = q - p;
+  t.D[i] = Mi + p + static_cast<long long>(p) * ni; t.nbv[i] = w;
+  double2* Lp = Mi + static_cast<long long>(p) * ni;          // M[0:p, p:q]
+  t.A1[i] = Lp; t.C1[i] = Lp; t.m1[i] = p; t.n1[i] = w; t.k1[i] = w;
+  t.A2[i] = Lp; t.B2[i] = Mi + p; t.m2[i] = p; t.n2[i] = p; t.k2[i] = w;
 }
 
-void launch_kkr_step(int step, int leaf, int nsolves, const int* n, double2* const* M, int b, int nb, double2* dinv,
+void launch_kkr_step(int step, int nsolves, const int* n, double2* const* M, int b, int nb, double2* dinv,
                      const KkrStep& t, cudaStream_t st) {
-  kkr_step_kernel<<<(nsolves + 127) / 128, 128, 0, st>>>(step, leaf, nsolves, n, M, b, nb, dinv, t);
+  kkr_step_kernel<<<(nsolves + 127) / 128, 128, 0, st>>>(step, nsolves, n, M, b, nb, dinv, t);
   record_launch();
 }
 

@@ -132,6 +132,10 @@ struct GjParams {
   int* status;
 };
 void launch_gj(const GjParams& p, int max_nb, int max_nrhs, int batch, cudaStream_t st);
+// X = D^-1 in place (Gauss-Jordan with partial pivoting), blocks of order <= GJINV_MAX; R, nrhs
+// unused
+constexpr int GJINV_MAX = OZK_NB_MAX;
+void launch_gjinv(const GjParams& p, int max_w, int batch, cudaStream_t st);
 void launch_build_m(int n, int b, const double2* t, const double2* G, double2* M, cudaStream_t st);
 void launch_build_m_batched(const int* L, int b, const double2* const* t, const double2* const* G, double2* const* M,
                             int nmax, int batch, cudaStream_t st);
@@ -144,17 +148,16 @@ void launch_contour_trace(const double2* const* tau, int nsolves, int b, const d
 
 // Per-step tables of the batched tau_00 driver, filled on the device for step `step`.
 struct KkrStep {
-  // Gauss-Jordan on the pivot blocks
+  // pivot block inverse (or, at the end, the S_00^-1 t_0 solve)
   const double2** D; int* ldd; int* nbv; double2** X; int* ldx;
-  // GEMM 1: L = M_RJ Dinv (in place), GEMM 2: M_RR -= L M_JR
+  // GEMM 1: L = M_RJ D^-1 (in place), GEMM 2: M_RR -= L M_JR
   const double2** A1; int* lda1; const double2** B1; int* ldb1; double2** C1; int* ldc1; int* m1; int* n1; int* k1;
   const double2** A2; int* lda2; const double2** B2; int* ldb2; double2** C2; int* ldc2; int* m2; int* n2; int* k2;
-  int* skm2; int* skn2;     // skip box of GEMM 2 (the block deferred to the panel's trailing update)
 };
-// step >= 0, leaf >= 0: tables of leaf `leaf` of panel `step` (Gauss-Jordan, L column, masked
-// rank-b update); leaf < 0: the panel's trailing update (GEMM 2 fields); step < 0: the final
-// S_00^-1 t_0 solve.
-void launch_kkr_step(int step, int leaf, int nsolves, const int* n, double2* const* M, int b, int nb, double2* dinv,
+// step >= 0: tables of panel `step` (J = [p, q), q = n - step nb, p = max(q - nb, b); D^-1 into
+// dinv, pitch nb); step < 0: the final S_00^-1 t_0 solve (D = the centre block).  Solves with
+// nothing left to eliminate get empty problems.
+void launch_kkr_step(int step, int nsolves, const int* n, double2* const* M, int b, int nb, double2* dinv,
                      const KkrStep& t, cudaStream_t st);
 
 // ---- selector.cu: slice-count selector (features, probes, residual check, perceptron)

@@ -45,3 +45,13 @@ def test_argument_errors_need_no_gpu(libozk):
     assert libozk.ozk_zgemm_workspace_size(512, 512, 512, 7, 1) > 7 * 512 * 1024 * 2
     assert libozk.ozk_zgemm_workspace_size(512, 512, 512, 17, 1) == 0       # S out of range
     assert libozk.ozaki_zgemm(None, b"N", b"N", 1, 1, 1, None, None, 1, None, 1, None, None, 1, 7, 0) == 1
+
+
+def test_binding_constants_match_the_header():
+    from paper_2603_29975_gb300 import binding
+    src = open(os.path.join(ROOT, "include", "ozk.h")).read()
+    defs = dict(re.findall(r"^#define (OZK_[A-Z0-9_]+) (\d+)\b", src, flags=re.M))
+    checked = [k for k in defs if hasattr(binding, k)]
+    assert {"OZK_NB_MAX", "OZK_SEL_NPARAMS", "OZK_SEL_FEATURES", "OZK_PAIRS_FULL"} <= set(checked)
+    for k in checked:
+        assert getattr(binding, k) == int(defs[k]), k

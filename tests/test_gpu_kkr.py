@@ -37,8 +37,8 @@ def test_tau00_small_vs_oracles(ozk_mod, handle, S, nb):
     assert handle.status() == 0
     got = ozk_mod.to_numpy(tau)
     full = kkr.tau00_full(M, t[0])
-    # the oracle's restatement of the same algorithm: leaf-wise panels for the emulated path
-    blk = co.tau00_block(M, t[0], nb, S=S, leaf=16 if S > 0 else None)
+    # the oracle's restatement of the same algorithm: one pivot block per panel
+    blk = co.tau00_block(M, t[0], nb, S=S)
     if S == 0:
         assert kkr.rel_err(got, full) < 1e-13
     else:
@@ -65,7 +65,7 @@ def test_tau00_config2_single_atom(ozk_mod, handle):
 def test_tau00_wider_panels(ozk_mod, handle):
     t, G, M = _system(27)
     full = kkr.tau00_full(M, t[0])
-    for nb in (32, 48, 96, 128):
+    for nb in (32, 48, 96, 112):
         tau = ozk_mod.colmajor_cuda(np.zeros((16, 16), dtype=np.complex128))
         ozk_mod.kkr_tau00(handle, ozk_mod.colmajor_cuda(M), ozk_mod.colmajor_cuda(t[0]), tau, S=7, nb=nb)
         assert kkr.rel_err(ozk_mod.to_numpy(tau), full) <= 1e-10
@@ -100,6 +100,31 @@ def test_singular_pivot_sets_status(ozk_mod, handle):
     assert handle.status() & (1 << 3)
 
 
+@pytest.mark.parametrize("S", [0, 7])
+def test_pivot_blocks_need_row_interchanges(ozk_mod, handle, S):
+    """Pivot blocks whose diagonal is zero (every panel's leading element needs a row
+    interchange): the in-place Gauss-Jordan inverse with partial pivoting still gives tau_00
+    of the full-inverse oracle."""
+    rng = np.random.default_rng(20260403)
+    n, b, nb = 160, 16, 48
+    M = 0.02 * (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    # every block of the elimination (centre [0, 16), panels [16, 64), [64, 112), [112, 160))
+    # dominated by its reversal permutation, with a zero diagonal
+    for lo, hi in ((0, 16), (16, 64), (64, 112), (112, 160)):
+        for r in range(hi - lo):
+            M[lo + r, hi - 1 - r] += 1.0
+    np.fill_diagonal(M, 0.0)
+    t0 = np.eye(b, dtype=np.complex128) * (0.3 + 0.1j)
+    tau = ozk_mod.colmajor_cuda(np.zeros((b, b), dtype=np.complex128))
+    ozk_mod.kkr_tau00(handle, ozk_mod.colmajor_cuda(M), ozk_mod.colmajor_cuda(t0), tau, S=S, nb=nb)
+    assert handle.status() == 0
+    got = ozk_mod.to_numpy(tau)
+    full = co.tau00_full(M, t0)
+    assert kkr.rel_err(got, full) < (1e-12 if S == 0 else 1e-10)
+    if S > 0:
+        assert kkr.rel_err(got, co.tau00_block(M, t0, nb, S=S)) < 1e-12
+
+
 @pytest.mark.parametrize("S", [5, 7])
 def test_build_m_shared_is_the_emulated_block_row_update(ozk_mod, handle, S):
     """Atoms sharing G: block row i of M_a is (rows ib..ib+b-1 of I) - RN(t_{a,i} G_i) with the
@@ -127,8 +152,9 @@ def test_build_m_shared_is_the_emulated_block_row_update(ozk_mod, handle, S):
 
 @pytest.mark.parametrize("S,nb", [(7, 50), (7, 100), (0, 50)])
 def test_tau00_lmax4_spin_blocks(ozk_mod, handle, S, nb):
-    """b = 50 (lmax = 4 with spin) pivot blocks: the 256-thread Gauss-Jordan kernel, leaf GEMMs
-    with k = 50 (K' = 100, not a multiple of 16)."""
+    """b = 50 (lmax = 4 with spin): pivot blocks of order 50 and 100 (in-place Gauss-Jordan
+    inverses), panel GEMMs with k = 50 or 100 (K' = 100, not a multiple of 16), and the
+    256-thread Gauss-Jordan solve of the 50 x 50 centre block."""
     L, b = 9, 50
     t, G, _ = synth.kkr_system(L, b, 0.4 + 0.1j, atom=3)
     M = kkr.kkr_build(t, G)
@@ -138,21 +164,21 @@ def test_tau00_lmax4_spin_blocks(ozk_mod, handle, S, nb):
     got = ozk_mod.to_numpy(tau)
     full = co.tau00_full(M, t[0])
     if S > 0:
-        assert kkr.rel_err(got, co.tau00_block(M, t[0], nb, S=S, leaf=b)) < 1e-13
+        assert kkr.rel_err(got, co.tau00_block(M, t[0], nb, S=S)) < 1e-13
         assert kkr.rel_err(got, full) <= 1e-10
     else:
         assert kkr.rel_err(got, full) < 1e-13
 
 
 def test_autotuned_panel_width_is_cached_and_used(ozk_mod):
-    """kkr_tau00_autotune times every nb = b, 2b, ..., 128 and caches the fastest; nb = 0 then
+    """kkr_tau00_autotune times every nb = b, 2b, ..., 112 and caches the fastest; nb = 0 then
     runs exactly that nb (bitwise equal results)."""
     import torch
     h = ozk_mod.Handle()
     sizes = [27, 15, 27]
     systems = [_system(L, 0.5 + 0.05j, atom=i) for i, L in enumerate(sizes)]
     best, times = ozk_mod.kkr_tau00_autotune(h, [L * 16 for L in sizes], 16, S=7)
-    assert sorted(times) == list(range(16, 129, 16)) and best in times
+    assert sorted(times) == list(range(16, 113, 16)) and best in times
     assert all(v > 0 for v in times.values()) and times[best] == min(times.values())
 
     def run(nb):

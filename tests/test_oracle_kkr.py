@@ -103,13 +103,14 @@ def test_degenerate_t_and_G():
 def test_emulated_block_lu_error_per_S():
     t, G, M = _system(15)
     ref = kkr.tau00_full(M, t[0])
-    errs = {S: kkr.rel_err(co.tau00_block(M, t[0], 64, S=S, leaf=16), ref) for S in (3, 4, 5, 6, 7)}
-    assert errs[7] <= 1e-10
-    for S in (3, 4, 5, 6):
-        assert errs[S + 1] < errs[S]
-    # the Python and C restatements of the algorithm agree to rounding
-    py = kkr.tau00_block(M, t[0], 64, S=5, leaf=16)
-    assert kkr.rel_err(py, co.tau00_block(M, t[0], 64, S=5, leaf=16)) < 1e-13
+    for leaf in (None, 16):                     # whole-panel pivot blocks, and leaf by leaf
+        errs = {S: kkr.rel_err(co.tau00_block(M, t[0], 64, S=S, leaf=leaf), ref) for S in (3, 4, 5, 6, 7)}
+        assert errs[7] <= 1e-10
+        for S in (3, 4, 5, 6):
+            assert errs[S + 1] < errs[S]
+        # the Python and C restatements of the algorithm agree to rounding
+        py = kkr.tau00_block(M, t[0], 64, S=5, leaf=leaf)
+        assert kkr.rel_err(py, co.tau00_block(M, t[0], 64, S=5, leaf=leaf)) < 1e-13
 
 
 def test_config2_system_is_well_posed():
