@@ -402,6 +402,106 @@ __device__ __forceinline__ void epilogue_halves(const GemmParams& p, const EpiCt
   }
 }
 
+// RN-even of V 2^E for a two's-complement V with |V| < 2^63 (the exact sum when it fits in 64
+// bits): normalise, keep 53 bits, round half to even on the 11 bits below; integer
+// instructions only.  Results outside the normal range take the general routine.
+__device__ __forceinline__ double round_v64(long long V, int E) {
+  const bool neg = V < 0;
+  const unsigned long long u = neg ? 0ull - static_cast<unsigned long long>(V) : static_cast<unsigned long long>(V);
+  if (u == 0ull) return 0.0;
+  const int lz = __clzll(u);
+  const unsigned long long M = u << lz;
+  const int q = E - lz + 11;                          // ulp exponent of a normal 53-bit result
+  if (q < -1074 || q > 970) return round_scaled_dev(static_cast<__int128>(V), E);
+  unsigned long long keep = M >> 11;
+  const unsigned int rem = static_cast<unsigned int>(M) & 0x7FFu;
+  keep += (rem > 0x400u || (rem == 0x400u && (keep & 1ull))) ? 1ull : 0ull;
+  unsigned long long bits = (static_cast<unsigned long long>(q + 1074) << 52) + keep;
+  if (neg) bits |= 0x8000000000000000ull;
+  return __longlong_as_double(static_cast<long long>(bits));
+}
+
+// Epilogue of one 128 x 64 tile when the exact sum of every output fits in 64 bits: one
+// exactness chunk, G <= 5 groups, ceil(log2(terms)) + 14 + 8 (G - 1) + 1 <= 63 (checked on the
+// host).  Every group is folded into one int64 per stacked column with the weight
+// 2^(8 (G - 1 - g)) and its accumulator released; then the thread's C values and column
+// exponents are requested, the 16 sums rounded (their latency hides the loads') and combined.
+template <int G>
+__device__ __forceinline__ void epilogue_fast64(const GemmParams& p, const EpiCtx& x, uint64_t* acc_empty, bool magic,
+                                                int lane) {
+  constexpr int BN = 64;
+  const bool needC = p.mode == EPI_LU || p.mode == EPI_GENERAL;
+  const int jc0 = (x.n0 + x.c0) / 2;                  // this thread's 8 complex columns
+  const int jend = min(min(jc0 + 8, (x.n2_z + 1) / 2), x.jlim);
+  const bool active = x.rowok && max(jc0, x.skip_n) < jend;
+  if (!__any_sync(0xffffffffu, active)) {
+#pragma unroll
+    for (int gi = 0; gi < G; ++gi) {
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[gi]);
+    }
+    return;
+  }
+  long long V[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) V[j] = 0;
+#pragma unroll
+  for (int gi = 0; gi < G; ++gi) {
+    uint32_t v[8], u[8];
+    tmem_ld8(x.tbase + gi * BN, v);
+    tmem_ld8(x.tbase + gi * BN + 8, u);
+    tmem_wait_ld();
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&acc_empty[gi]);         // group gi may be overwritten now
+    const long long w = 1ll << (8 * (G - 1 - gi));
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      V[j] += static_cast<long long>(acc_to_int(v[j], magic)) * w;
+      V[j + 8] += static_cast<long long>(acc_to_int(u[j], magic)) * w;
+    }
+  }
+  if (!active) return;
+  // two halves of 4 complex columns: a half's C values and exponents are requested, its 8 sums
+  // rounded while they arrive, then combined and stored
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    double2 cv[4];
+    int fe[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int jc = jc0 + 4 * half + q;
+      const bool in = jc < jend;
+      fe[q] = in ? p.f[x.z * p.f_stride + jc] : 0;
+      cv[q] = (in && needC && jc >= x.skip_n) ? x.Cz[x.crow + jc * x.ldc] : make_double2(0.0, 0.0);
+    }
+    double zz[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) zz[j] = round_v64(V[8 * half + j], x.er + fe[j >> 1]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int jc = jc0 + 4 * half + q;
+      if (jc < jend && jc >= x.skip_n) {
+        double2* dst = x.Cz + x.crow + jc * x.ldc;
+        const double zr = zz[2 * q], zi = zz[2 * q + 1];
+        if (p.mode == EPI_STORE) {
+          if (p.ar == 1.0 && p.ai == 0.0) *dst = make_double2(zr, zi);
+          else *dst = make_double2(p.ar * zr - p.ai * zi, p.ar * zi + p.ai * zr);
+        } else if (p.mode == EPI_LU) {
+          *dst = make_double2(cv[q].x - zr, cv[q].y - zi);
+        } else if (p.mode == EPI_IMINUS) {
+          *dst = make_double2((jc == x.grow ? 1.0 : 0.0) - zr, 0.0 - zi);
+        } else {
+          const double xr = p.ar * zr - p.ai * zi, xi = p.ar * zi + p.ai * zr;
+          const double yr = p.br * cv[q].x - p.bi * cv[q].y, yi = p.br * cv[q].y + p.bi * cv[q].x;
+          *dst = make_double2(xr + yr, xi + yi);
+        }
+      }
+    }
+  }
+}
+
 template <int BN>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
 slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -580,7 +680,15 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
           // two-halves variant with streamed TMEM loads is faster (1.18x on 1024 x 1040 x 16
           // tiles); longer K: the group-wise drain that releases accumulators earliest (1.14x
           // on 976 x 976 x 64)
-          if (p.kblocks <= 2) {
+          if (p.fit64 && G <= 5) {
+            switch (G) {
+              case 1: epilogue_fast64<1>(p, x, acc_empty, magic, lane); break;
+              case 2: epilogue_fast64<2>(p, x, acc_empty, magic, lane); break;
+              case 3: epilogue_fast64<3>(p, x, acc_empty, magic, lane); break;
+              case 4: epilogue_fast64<4>(p, x, acc_empty, magic, lane); break;
+              default: epilogue_fast64<5>(p, x, acc_empty, magic, lane); break;
+            }
+          } else if (p.kblocks <= 2) {
             switch (G) {
               case 1: epilogue_halves<1>(p, x, acc_empty, magic, lane); break;
               case 2: epilogue_halves<2>(p, x, acc_empty, magic, lane); break;

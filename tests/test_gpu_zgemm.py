@@ -101,6 +101,37 @@ def test_zgemm_lu_update_bit_exact(ozk_mod, handle):
     assert np.array_equal(ozk_mod.to_numpy(C), co.zgemm_lu(C0, A, B, S))
 
 
+@pytest.mark.parametrize("S", [2, 4, 5])
+@pytest.mark.parametrize("k", [16, 64, 112])
+def test_zgemm_lu_update_64bit_sums_bit_exact(ozk_mod, handle, S, k):
+    """S <= 5 and one exactness chunk: every exact sum fits in 64 bits and the epilogue rounds
+    it from one int64 per output; the result equals the oracle's bit for bit."""
+    m, n = 200, 150
+    A, B, C0 = rand_complex(m, k, 51 + S), rand_complex(k, n, 52 + k), rand_complex(m, n, 53)
+    C = _dev(ozk_mod, C0)
+    ozk_mod.ozaki_zgemm(handle, _dev(ozk_mod, A), _dev(ozk_mod, B), C, S=S, alpha=-1.0, beta=1.0)
+    assert np.array_equal(ozk_mod.to_numpy(C), co.zgemm_lu(C0, A, B, S))
+
+
+def test_zgemm_64bit_sums_subnormal_and_overflowing_results(ozk_mod, handle):
+    """Rows and columns scaled so that products land in the subnormal range, below it, and
+    past the largest binary64: the 64-bit epilogue hands those to the general rounding and
+    matches the oracle bit for bit (subnormals, zeros, infinities)."""
+    S = 5
+    A, B = rand_complex(40, 20, 61), rand_complex(20, 24, 62)
+    A[0] *= 2.0 ** -1000
+    A[1] *= 2.0 ** -1030
+    B[:, 0] *= 2.0 ** -60
+    A[2] *= 2.0 ** 600
+    B[:, 1] *= 2.0 ** 500
+    C = _dev(ozk_mod, np.zeros((40, 24), dtype=np.complex128))
+    ozk_mod.ozaki_zgemm(handle, _dev(ozk_mod, A), _dev(ozk_mod, B), C, S=S)
+    ref = co.zgemm(A, B, S)
+    got = ozk_mod.to_numpy(C)
+    assert np.isinf(ref).any() and (np.abs(ref[ref != 0]) < 2.2250738585072014e-308).any()
+    assert np.array_equal(got, ref)
+
+
 def test_zgemm_full_pairs_bit_exact(ozk_mod, handle):
     m, n, k, S = 70, 33, 20, 4
     A, B = rand_complex(m, k, 41), rand_complex(k, n, 42)
