@@ -98,6 +98,10 @@ struct ozk_context {
   ozk_selector_info sel_last{};
   // panel widths chosen by kkr_tau00_autotune, keyed by (sizes..., b, S)
   std::map<std::vector<int>, int> tuned_nb;
+  // side stream of the batched solve (operand splits that overlap the pivot-block inverses)
+  // and the events that fork it from and join it to the handle's stream
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace {
@@ -119,14 +123,15 @@ cudaEvent_t prof_event(ozk_context* h) {
 // Launches enqueued while the stream is being captured are not timed (they run later, as graph
 // nodes).
 struct Prof {
-  ozk_context* h; int kind; double flops, bytes; cudaEvent_t a = nullptr; bool on = false;
-  Prof(ozk_context* hh, int k, double f, double by) : h(hh), kind(k), flops(f), bytes(by) {
-    if (h->prof && !capturing(h->stream)) { on = true; a = prof_event(h); cudaEventRecord(a, h->stream); }
+  ozk_context* h; int kind; double flops, bytes; cudaStream_t st; cudaEvent_t a = nullptr; bool on = false;
+  Prof(ozk_context* hh, int k, double f, double by, cudaStream_t s = nullptr)
+      : h(hh), kind(k), flops(f), bytes(by), st(s ? s : hh->stream) {
+    if (h->prof && !capturing(st)) { on = true; a = prof_event(h); cudaEventRecord(a, st); }
   }
   ~Prof() {
     if (on) {
       cudaEvent_t b = prof_event(h);
-      cudaEventRecord(b, h->stream);
+      cudaEventRecord(b, st);
       h->recs.push_back({kind, a, b, flops, bytes});
     }
   }
@@ -229,6 +234,12 @@ struct EmuGemm {
   const Oz2Tables* oz2 = nullptr; int beta = 0; int* resid = nullptr; long long ldres = 0;
   double2* const* crow = nullptr; int crow_b = 0;   // row-block scatter of the output
   const int* crow_n = nullptr;                // per-output order (device), or none
+  // partial runs: split only the operands in split_sides (1: A, 2: B, 3: both; an operand left
+  // out must already be split into this workspace by an earlier run of the same problem), and
+  // the slice GEMM only if run_gemm; on `stream` (nullptr: the handle's stream)
+  int split_sides = 3;
+  bool run_gemm = true;
+  cudaStream_t stream = nullptr;
 };
 
 struct GemmPlan {
@@ -287,6 +298,7 @@ ozk_status_t run_emulated(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0
   int* f = reinterpret_cast<int*>(ws + P.offF);
   const bool single = g.tm == nullptr;
   const int S = g.S;
+  cudaStream_t stream = g.stream ? g.stream : h->stream;
 
   const bool diag = g.pair_mode == PAIRS_DIAG;
   SplitParams sp{};
@@ -307,17 +319,24 @@ ozk_status_t run_emulated(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0
   sq.dbg_digits = nullptr;
   if (single) { sq.X = nullptr; sq.X1 = g.B; sq.ld1 = g.ldb; sq.rows1 = g.n; sq.k1 = g.k; sq.zstride1 = g.zsB; }
   else { sq.X = g.tB; sq.ld = g.tldb; sq.rows = g.tn; sq.kdim = g.tk; }
-  {
+  const bool split_a = (g.split_sides & 1) != 0, split_b = (g.split_sides & 2) != 0;
+  if (split_a || split_b) {
     // algorithmic bytes: read 16 per complex element (twice: scan + split), write S x 2 fp16
     // (left operand) or S x 4 fp16 (right operand, two stacked rows per column)
-    Prof pr(h, OZK_KIND_SPLIT, 0.0, smk * (32.0 + 4.0 * S) + snk * (32.0 + 8.0 * S));
+    Prof pr(h, OZK_KIND_SPLIT, 0.0, (split_a ? smk * (32.0 + 4.0 * S) : 0.0) + (split_b ? snk * (32.0 + 8.0 * S) : 0.0),
+            stream);
     if (diag) {
-      launch_residue_split(sp, *g.oz2, g.mmax, g.batch, h->stream);
-      launch_residue_split(sq, *g.oz2, g.nmax, g.batch, h->stream);
+      if (split_a) launch_residue_split(sp, *g.oz2, g.mmax, g.batch, stream);
+      if (split_b) launch_residue_split(sq, *g.oz2, g.nmax, g.batch, stream);
+    } else if (split_a && split_b) {
+      launch_split(sp, g.mmax, &sq, g.nmax, g.kmax, g.batch, stream);
+    } else if (split_a) {
+      launch_split(sp, g.mmax, nullptr, 0, g.kmax, g.batch, stream);
     } else {
-      launch_split(sp, g.mmax, &sq, g.nmax, g.kmax, g.batch, h->stream);
+      launch_split(sq, g.nmax, nullptr, 0, g.kmax, g.batch, stream);
     }
   }
+  if (!g.run_gemm) return cuda_check(cudaGetLastError(), "split launch");
 
   CUtensorMap ta, tb;
   st = make_slice_map(&ta, As, 2LL * g.kmax, P.kpad, P.rowsA, static_cast<long long>(S) * g.batch, 128, S);
@@ -376,8 +395,8 @@ ozk_status_t run_emulated(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0
   gp.npairs = np;
   {
     // algorithmic integer ops: every pair is one real GEMM m x 2n x 2k (8 m n k)
-    Prof pr(h, OZK_KIND_SLICE_GEMM, 8.0 * np * smnk, 0.0);
-    launch_slice_gemm(ta, tb, gp, P.BN, g.mmax, g.nmax, g.batch, h->stream);
+    Prof pr(h, OZK_KIND_SLICE_GEMM, 8.0 * np * smnk, 0.0, stream);
+    launch_slice_gemm(ta, tb, gp, P.BN, g.mmax, g.nmax, g.batch, stream);
   }
   return cuda_check(cudaGetLastError(), "slice GEMM launch");
 }
@@ -577,7 +596,22 @@ ozk_status_t ozk_create(ozk_handle_t* handle) {
   cudaGetDevice(&h->device);
   ozk_status_t st = cuda_check(cudaMalloc(&h->d_status, sizeof(int)), "cudaMalloc(status)");
   if (!st) st = cuda_check(cudaMemset(h->d_status, 0, sizeof(int)), "cudaMemset(status)");
-  if (st) { delete h; return st; }
+  if (!st) {
+    // the side stream at the lowest priority: its splits fill what the pivot-block inverses
+    // on the handle's stream leave free
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    st = cuda_check(cudaStreamCreateWithPriority(&h->aux, cudaStreamNonBlocking, least), "cudaStreamCreate(side)");
+  }
+  if (!st) st = cuda_check(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming), "cudaEventCreate");
+  if (!st) st = cuda_check(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming), "cudaEventCreate");
+  if (st) {
+    if (h->d_status) cudaFree(h->d_status);
+    if (h->aux) cudaStreamDestroy(h->aux);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    delete h;
+    return st;
+  }
   *handle = h;
   return OZK_OK;
 }
@@ -585,12 +619,16 @@ ozk_status_t ozk_create(ozk_handle_t* handle) {
 ozk_status_t ozk_destroy(ozk_handle_t h) {
   if (!h) return OZK_OK;
   cudaStreamSynchronize(h->stream);
+  if (h->aux) cudaStreamSynchronize(h->aux);
   if (h->ws) cudaFree(h->ws);
   if (h->d_status) cudaFree(h->d_status);
   if (h->sel_p) cudaFree(h->sel_p);
   if (h->sel_ws) cudaFree(h->sel_ws);
   for (auto& kv : h->tables) cudaFree(kv.second);
   for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
+  if (h->aux) cudaStreamDestroy(h->aux);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   delete h;
   return OZK_OK;
 }
@@ -1048,18 +1086,24 @@ static ozk_status_t tau00_batched_impl(ozk_handle_t h, int nsolves, const int* n
     nmax = std::max(nmax, n[i]);
   }
   const int panels = (nmax - b + nb - 1) / nb;
-  // workspace layout: [D^-1 per solve, nb x nb][step tables][GEMM workspace]
+  // workspace layout: [D^-1 per solve, nb x nb][step tables][GEMM 1 workspace][GEMM 2
+  // workspace] -- separate GEMM workspaces, so both GEMMs' early operand splits can run on the
+  // side stream while the pivot blocks are inverted
   const size_t ns = static_cast<size_t>(nsolves);
   const size_t off_dinv = 0;
   const size_t off_tab = align_up(off_dinv + ns * nb * nb * sizeof(double2), 1024);
   const size_t n_ptr = 8, n_int = 16;
-  const size_t off_gemm = align_up(off_tab + ns * (n_ptr * sizeof(void*) + n_int * sizeof(int)), 1024);
+  const size_t off_g1 = align_up(off_tab + ns * (n_ptr * sizeof(void*) + n_int * sizeof(int)), 1024);
   EmuGemm probe;
-  probe.batch = nsolves; probe.mmax = nmax; probe.nmax = nmax; probe.kmax = nb; probe.S = S;
+  probe.batch = nsolves; probe.mmax = nmax; probe.nmax = nb; probe.kmax = nb; probe.S = S;
   GemmPlan P;
   ozk_status_t st = plan_gemm(probe, &P);
   if (st) return st;
-  st = ensure_ws(h, off_gemm + P.total);
+  const size_t off_g2 = align_up(off_g1 + P.total, 1024);
+  probe.nmax = nmax;
+  st = plan_gemm(probe, &P);
+  if (st) return st;
+  st = ensure_ws(h, off_g2 + P.total);
   if (st) return st;
   const int* dn = nullptr;
   st = size_table(h, std::vector<int>(n, n + nsolves), &dn);
@@ -1078,8 +1122,8 @@ static ozk_status_t tau00_batched_impl(ozk_handle_t h, int nsolves, const int* n
   t.lda2 = pi + 9 * ns; t.ldb2 = pi + 10 * ns; t.ldc2 = pi + 11 * ns; t.m2 = pi + 12 * ns; t.n2 = pi + 13 * ns; t.k2 = pi + 14 * ns;
   double2* const* Mp = reinterpret_cast<double2* const*>(M);
 
-  auto gemm_tables = [&](int which, int mmax, int nmaxg, int kmax, double smnk, double smk, double snk,
-                         bool lu) -> ozk_status_t {
+  auto gemm_tables = [&](int which, int mmax, int nmaxg, int kmax, double smnk, double smk, double snk, bool lu,
+                         int sides, bool gemm, cudaStream_t stream) -> ozk_status_t {
     EmuGemm g;
     g.oa = {0, 0}; g.ob = {0, 0}; g.batch = nsolves; g.mmax = mmax; g.nmax = nmaxg; g.kmax = kmax; g.S = S;
     if (which == 1) {
@@ -1091,12 +1135,15 @@ static ozk_status_t tau00_batched_impl(ozk_handle_t h, int nsolves, const int* n
     }
     g.ar = lu ? -1 : 1; g.br = lu ? 1 : 0;
     g.sum_mnk = smnk; g.sum_mk = smk; g.sum_nk = snk;
-    return run_emulated(h, g, off_gemm);
+    g.split_sides = sides; g.run_gemm = gemm; g.stream = stream;
+    return run_emulated(h, g, which == 1 ? off_g1 : off_g2);
   };
 
   // panel s of every solve: J = [p, q), q = n - s nb, p = max(q - nb, b), w = q - p.
   // D^-1 of the w x w pivot block (binary64), L = M_RJ D^-1 in place (m = p, n = k = w),
-  // M_RR -= L M_JR (m = n = p, k = w); the centre block is eliminated last
+  // M_RR -= L M_JR (m = n = p, k = w); the centre block is eliminated last.  M_RJ (GEMM 1's A)
+  // and M_JR (GEMM 2's B) do not depend on D^-1: they are split on the side stream while the
+  // pivot blocks are inverted (binary64-bound, HBM-bound work side by side)
   for (int s = 0; s < panels; ++s) {
     int pmax = 0, wmax = 0, nact = 0;
     double s1 = 0, sa = 0, sw = 0, s3 = 0, sw3 = 0;
@@ -1118,6 +1165,9 @@ static ozk_status_t tau00_batched_impl(ozk_handle_t h, int nsolves, const int* n
       Prof pr(h, OZK_KIND_OTHER, 0.0, 0.0);
       launch_kkr_step(s, nsolves, dn, Mp, b, nb, dinv, t, h->stream);
     }
+    st = cuda_check(cudaEventRecord(h->ev_fork, h->stream), "record fork");
+    if (!st) st = cuda_check(cudaStreamWaitEvent(h->aux, h->ev_fork, 0), "side stream wait");
+    if (st) return st;
     GjParams gj{};
     gj.D = t.D; gj.ldd = t.ldd; gj.nb = t.nbv; gj.R = nullptr; gj.X = t.X; gj.ldx = t.ldx; gj.nrhs = 0;
     gj.status = h->d_status;
@@ -1125,9 +1175,14 @@ static ozk_status_t tau00_batched_impl(ozk_handle_t h, int nsolves, const int* n
       Prof pr(h, OZK_KIND_GJ, 8.0 * sw3, 32.0 * sw);
       launch_gjinv(gj, wmax, nsolves, h->stream);
     }
-    st = gemm_tables(1, pmax, wmax, wmax, s1, sa, sw, false);
+    st = gemm_tables(1, pmax, wmax, wmax, s1, sa, sw, false, 1, false, h->aux);
+    if (!st) st = gemm_tables(2, pmax, pmax, wmax, s3, sa, sa, true, 2, false, h->aux);
+    if (!st) st = cuda_check(cudaEventRecord(h->ev_join, h->aux), "record join");
+    if (!st) st = cuda_check(cudaStreamWaitEvent(h->stream, h->ev_join, 0), "join side stream");
     if (st) return st;
-    st = gemm_tables(2, pmax, pmax, wmax, s3, sa, sa, true);
+    st = gemm_tables(1, pmax, wmax, wmax, s1, sa, sw, false, 2, true, h->stream);
+    if (st) return st;
+    st = gemm_tables(2, pmax, pmax, wmax, s3, sa, sa, true, 1, true, h->stream);
     if (st) return st;
   }
   {
