@@ -113,6 +113,20 @@ def test_zgemm_lu_update_64bit_sums_bit_exact(ozk_mod, handle, S, k):
     assert np.array_equal(ozk_mod.to_numpy(C), co.zgemm_lu(C0, A, B, S))
 
 
+def test_zgemm_64bit_sums_large_group_values(ozk_mod, handle):
+    """Rows and columns of (127/255)(1 + i), whose five balanced digits are all 127: the
+    five-pair group sums of the imaginary parts reach 128 * 5 * 127^2 ~ 2^23.3, past the range
+    of the one-add FP32 conversion, so those warps take the hardware conversion; the other
+    rows are random.  Bitwise equal to the oracle."""
+    S, m, n, k = 5, 160, 48, 64
+    A, B, C0 = rand_complex(m, k, 71), rand_complex(k, n, 72), rand_complex(m, n, 73)
+    A[:40] = (127 / 255) * (1 + 1j)
+    B[:, :20] = (127 / 255) * (1 + 1j)
+    C = _dev(ozk_mod, C0)
+    ozk_mod.ozaki_zgemm(handle, _dev(ozk_mod, A), _dev(ozk_mod, B), C, S=S, alpha=-1.0, beta=1.0)
+    assert np.array_equal(ozk_mod.to_numpy(C), co.zgemm_lu(C0, A, B, S))
+
+
 def test_zgemm_64bit_sums_subnormal_and_overflowing_results(ozk_mod, handle):
     """Rows and columns scaled so that products land in the subnormal range, below it, and
     past the largest binary64: the 64-bit epilogue hands those to the general rounding and
