@@ -45,6 +45,24 @@ __device__ __forceinline__ __int128 integer_image(double x, int e, int nbits) {
 }
 
 // Next balanced base-256 digit of X (least significant first); X is advanced.
+// The same with 64-bit integers, for nbits <= 62 (S <= 7): |X| < 2^nbits when |x| < 2^e.
+__device__ __forceinline__ long long integer_image64(double x, int e, int nbits) {
+  const unsigned long long u = __double_as_longlong(x);
+  const bool neg = (u >> 63) != 0ull;
+  const int ex = static_cast<int>((u >> 52) & 0x7FFull);
+  const unsigned long long man = u & ((1ull << 52) - 1ull);
+  const unsigned long long M = ex == 0 ? man : (man | (1ull << 52));
+  const int sh = (ex == 0 ? -1074 : ex - 1075) + nbits - e;
+  const unsigned long long mag = sh >= 0 ? (sh < 64 ? M << sh : 0ull) : (sh > -64 ? M >> (-sh) : 0ull);
+  return neg ? -static_cast<long long>(mag) : static_cast<long long>(mag);
+}
+
+__device__ __forceinline__ int next_digit64(long long& X) {
+  const int d = static_cast<int>((X + 128) & 255ll) - 128;
+  X = (X - d) >> 8;
+  return d;
+}
+
 __device__ __forceinline__ int next_digit(__int128& X) {
   const int d = static_cast<int>(static_cast<unsigned long long>(X + 128) & 255ull) - 128;
   X = (X - d) >> 8;

@@ -9,6 +9,7 @@
 //                           out[z][s][2r+1][l]  = Im,  out[z][s][2r+1][k+l] = Re
 // Positions [2k, kpad) of every written row are zero.  All integer work, no FP64 arithmetic.
 #include <algorithm>
+#include <type_traits>
 
 #include "ozk_params.cuh"
 
@@ -47,22 +48,34 @@ __device__ __forceinline__ void store_digits(__half* dst, const int (&d)[PER]) {
 }
 
 // Digits of PER consecutive elements of one row (positions l .. l + PER - 1, all < K, l and K
-// multiples of PER), every slice written with vector stores.
-template <int PER>
+// multiples of PER), every slice written with vector stores.  W64: 64-bit integer images
+// (nbits <= 62), else 128-bit.
+template <int PER, bool W64>
 __device__ __forceinline__ void split_run(const SplitParams& p, const double2* v, int e, int r, int l, int K,
                                           __half* outz, long long plane) {
-  __int128 Xr[PER], Xi[PER];
+  using Int = typename std::conditional<W64, long long, __int128>::type;
+  Int Xr[PER], Xi[PER];
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
-    Xr[q] = integer_image(v[q].x, e, p.nbits);
-    Xi[q] = integer_image(v[q].y, e, p.nbits);
+    if constexpr (W64) {
+      Xr[q] = integer_image64(v[q].x, e, p.nbits);
+      Xi[q] = integer_image64(v[q].y, e, p.nbits);
+    } else {
+      Xr[q] = integer_image(v[q].x, e, p.nbits);
+      Xi[q] = integer_image(v[q].y, e, p.nbits);
+    }
   }
   for (int s = p.S - 1; s >= 0; --s) {
     int dr[PER], di[PER];
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
-      dr[q] = s ? next_digit(Xr[q]) : static_cast<int>(Xr[q]);
-      di[q] = s ? next_digit(Xi[q]) : static_cast<int>(Xi[q]);
+      if constexpr (W64) {
+        dr[q] = s ? next_digit64(Xr[q]) : static_cast<int>(Xr[q]);
+        di[q] = s ? next_digit64(Xi[q]) : static_cast<int>(Xi[q]);
+      } else {
+        dr[q] = s ? next_digit(Xr[q]) : static_cast<int>(Xr[q]);
+        di[q] = s ? next_digit(Xi[q]) : static_cast<int>(Xi[q]);
+      }
     }
     __half* o = outz + s * plane;
     if (p.side == 0) {
@@ -80,9 +93,12 @@ __device__ __forceinline__ void split_run(const SplitParams& p, const double2* v
 
 // Both operands of one emulated GEMM in one launch: blockIdx.z selects the side.  VEC: the
 // widest digit run stored as one vector (8 in general; 2 for K <= 16, where the runs are 2 wide
-// and the smaller register footprint keeps more CTAs resident).
-template <int VEC>
-__global__ void __launch_bounds__(SPLIT_THREADS)
+// and the smaller register footprint keeps more CTAs resident).  W64: 64-bit integer images
+// (S <= 7).  Rows of at most SPLIT_TK elements (every panel operand of the block LU) are read
+// from global memory once: the tile is loaded, the row maxima are taken from it, then the
+// digits; longer rows take a scan pass and then the tiles one by one.
+template <int VEC, bool W64>
+__global__ void __launch_bounds__(SPLIT_THREADS, VEC == 2 ? (W64 ? 5 : 4) : (W64 ? 3 : 2))
 split_kernel(const SplitPair pp) {
   if (static_cast<int>(blockIdx.z) >= pp.nsides) return;
   const SplitParams& p = pp.s[blockIdx.z];
@@ -95,17 +111,59 @@ split_kernel(const SplitPair pp) {
   const double2* __restrict__ P = single ? p.X1 + z * p.zstride1 : p.X[z];
   const long long ld = single ? p.ld1 : p.ld[z];
   const int tid = threadIdx.x;
+  const bool one_tile = K <= SPLIT_TK;
 
   __shared__ unsigned long long rowmax[SPLIT_ROWS];
   __shared__ int rowexp[SPLIT_ROWS];
+  __shared__ int rowbad[SPLIT_ROWS];
   __shared__ double2 tile[SPLIT_ROWS][SPLIT_TK + 1];
   __shared__ int bad;
-  if (tid < SPLIT_ROWS) rowmax[tid] = 0ull;
+  if (tid < SPLIT_ROWS) { rowmax[tid] = 0ull; rowbad[tid] = 0; }
   if (tid == 0) bad = 0;
   __syncthreads();
 
-  // ---- pass 1: row maxima
-  {
+  // tile width along K: 64, or K rounded up to 8 for short rows (so no thread idles on padding)
+  const int TK = K >= SPLIT_TK ? SPLIT_TK : ((K + 7) & ~7);
+  const int per = TK / 8;                      // consecutive l per thread
+  // a 32 x TK tile starting at column lt (coalesced along the stored contiguous direction);
+  // non-finite scalars are flagged (their row's exponent becomes 0, as a non-finite maximum
+  // gives) and split as zero
+  auto load_tile = [&](int lt) {
+    for (int idx = tid; idx < SPLIT_ROWS * TK; idx += SPLIT_THREADS) {
+      int rl, ll;
+      if (!p.trans) { rl = idx % SPLIT_ROWS; ll = idx / SPLIT_ROWS; }
+      else          { ll = idx % TK;         rl = idx / TK; }
+      const int r = r0 + rl, l = lt + ll;
+      double2 v = make_double2(0.0, 0.0);
+      if (r < R && l < K) v = p.trans ? P[l + r * ld] : P[r + l * ld];
+      if (p.conj) v.y = -v.y;
+      if (!isfinite(v.x) || !isfinite(v.y)) {
+        bad = 1;
+        rowbad[rl] = 1;
+        if (!isfinite(v.x)) v.x = 0.0;
+        if (!isfinite(v.y)) v.y = 0.0;
+      }
+      tile[rl][ll] = v;
+    }
+  };
+
+  if (one_tile) {
+    load_tile(0);
+    __syncthreads();
+    // row maxima from the tile: 8 threads per row, combined by shuffles
+    const int rl = tid >> 3, cg = tid & 7;
+    unsigned long long mx = 0ull;
+    for (int l = cg; l < K; l += 8) {
+      const double2 v = tile[rl][l];
+      const unsigned long long a = static_cast<unsigned long long>(__double_as_longlong(v.x)) & 0x7FFFFFFFFFFFFFFFull;
+      const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v.y)) & 0x7FFFFFFFFFFFFFFFull;
+      mx = max(mx, max(a, b));
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (cg == 0) rowmax[rl] = rowbad[rl] ? 0x7FF0000000000000ull : mx;
+  } else {
+    // ---- scan pass: row maxima
     int rl, l0, lstep;
     if (!p.trans) { rl = tid % SPLIT_ROWS; l0 = tid / SPLIT_ROWS; lstep = SPLIT_THREADS / SPLIT_ROWS; }
     else          { rl = tid / 8;          l0 = tid % 8;          lstep = 8; }
@@ -133,31 +191,17 @@ split_kernel(const SplitPair pp) {
   }
   __syncthreads();
 
-  // ---- pass 2: digits, tile by tile along K
+  // ---- digits, tile by tile along K
   const int S = p.S;
   const long long plane = p.out_rows * p.kpad;
   __half* outz = p.out + static_cast<long long>(z) * S * plane;
   const bool dbg = (p.dbg_digits != nullptr) && z == 0;
   const long long dplane = p.out_rows * 2LL * K;
-  // tile width along K: 64, or K rounded up to 8 for short rows (so no thread idles on padding)
-  const int TK = K >= SPLIT_TK ? SPLIT_TK : ((K + 7) & ~7);
-  const int per = TK / 8;                      // consecutive l per thread
   for (int lt = 0; lt < K; lt += TK) {
-    // load a 32 x TK tile (coalesced along the stored contiguous direction)
-    for (int idx = tid; idx < SPLIT_ROWS * TK; idx += SPLIT_THREADS) {
-      int rl, ll;
-      if (!p.trans) { rl = idx % SPLIT_ROWS; ll = idx / SPLIT_ROWS; }
-      else          { ll = idx % TK;         rl = idx / TK; }
-      const int r = r0 + rl, l = lt + ll;
-      double2 v = make_double2(0.0, 0.0);
-      if (r < R && l < K) v = p.trans ? P[l + r * ld] : P[r + l * ld];
-      if (p.conj) v.y = -v.y;
-      // a non-finite scalar was already flagged; split it as zero
-      if (!isfinite(v.x)) v.x = 0.0;
-      if (!isfinite(v.y)) v.y = 0.0;
-      tile[rl][ll] = v;
+    if (!one_tile) {
+      load_tile(lt);
+      __syncthreads();
     }
-    __syncthreads();
     // each thread: one row, 8 consecutive l
     {
       const int rl = tid / 8;
@@ -170,11 +214,11 @@ split_kernel(const SplitPair pp) {
       if (r < R && vec) {
         const int e = rowexp[rl];
         if constexpr (VEC >= 8) {
-          if (per == 8) split_run<8>(p, &tile[rl][lg], e, r, l0, K, outz, plane);
-          else if (per == 4) split_run<4>(p, &tile[rl][lg], e, r, l0, K, outz, plane);
-          else split_run<2>(p, &tile[rl][lg], e, r, l0, K, outz, plane);
+          if (per == 8) split_run<8, W64>(p, &tile[rl][lg], e, r, l0, K, outz, plane);
+          else if (per == 4) split_run<4, W64>(p, &tile[rl][lg], e, r, l0, K, outz, plane);
+          else split_run<2, W64>(p, &tile[rl][lg], e, r, l0, K, outz, plane);
         } else {
-          split_run<2>(p, &tile[rl][lg], e, r, l0, K, outz, plane);
+          split_run<2, W64>(p, &tile[rl][lg], e, r, l0, K, outz, plane);
         }
       } else if (r < R) {
         const int e = rowexp[rl];
@@ -237,8 +281,14 @@ void launch_split(const SplitParams& a, int rows_a, const SplitParams* b, int ro
   if (b) pp.s[1] = *b;
   const int rows = std::max(rows_a, b ? rows_b : 0);
   dim3 grid((rows + SPLIT_ROWS - 1) / SPLIT_ROWS, batch, pp.nsides);
-  if (kmax <= 16) split_kernel<2><<<grid, SPLIT_THREADS, 0, st>>>(pp);
-  else split_kernel<8><<<grid, SPLIT_THREADS, 0, st>>>(pp);
+  const bool w64 = pp.s[0].nbits <= 62 && (pp.nsides < 2 || pp.s[1].nbits <= 62);
+  if (kmax <= 16) {
+    if (w64) split_kernel<2, true><<<grid, SPLIT_THREADS, 0, st>>>(pp);
+    else split_kernel<2, false><<<grid, SPLIT_THREADS, 0, st>>>(pp);
+  } else {
+    if (w64) split_kernel<8, true><<<grid, SPLIT_THREADS, 0, st>>>(pp);
+    else split_kernel<8, false><<<grid, SPLIT_THREADS, 0, st>>>(pp);
+  }
   record_launch();
 }
 
