@@ -80,12 +80,15 @@ __global__ void __launch_bounds__(RS_THREADS) residue_split_kernel(const SplitPa
     if (!p.trans) { rl = idx % RS_ROWS; l = idx / RS_ROWS; if (rl >= nr) continue; }
     else          { rl = idx / K;       l = idx % K; }
     const int r = r0 + rl;
-    double2 v = p.trans ? P[l + r * ld] : P[r + l * ld];
-    if (p.conj) v.y = -v.y;
-    if (!isfinite(v.x)) v.x = 0.0;
-    if (!isfinite(v.y)) v.y = 0.0;
+    // bit operations only (no binary64 compares or negations on the FP64 pipe); a non-finite
+    // scalar (already flagged) is split as zero
+    longlong2 v = reinterpret_cast<const longlong2*>(P)[p.trans ? l + r * ld : r + l * ld];
+    if (p.conj) v.y ^= static_cast<long long>(0x8000000000000000ull);
+    if ((v.x & 0x7FF0000000000000ll) == 0x7FF0000000000000ll) v.x = 0;
+    if ((v.y & 0x7FF0000000000000ll) == 0x7FF0000000000000ll) v.y = 0;
     const int e = rowexp[rl];
-    __int128 Xr = integer_image(v.x, e, p.nbits), Xi = integer_image(v.y, e, p.nbits);
+    __int128 Xr = integer_image(__longlong_as_double(v.x), e, p.nbits);
+    __int128 Xi = integer_image(__longlong_as_double(v.y), e, p.nbits);
     int dr[8], di[8];                                   // balanced base-256 digits, d[s] weight 256^s
 #pragma unroll
     for (int s = 0; s < 7; ++s) { dr[s] = next_digit(Xr); di[s] = next_digit(Xi); }

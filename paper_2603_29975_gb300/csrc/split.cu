@@ -134,16 +134,20 @@ split_kernel(const SplitPair pp) {
       if (!p.trans) { rl = idx % SPLIT_ROWS; ll = idx / SPLIT_ROWS; }
       else          { ll = idx % TK;         rl = idx / TK; }
       const int r = r0 + rl, l = lt + ll;
-      double2 v = make_double2(0.0, 0.0);
-      if (r < R && l < K) v = p.trans ? P[l + r * ld] : P[r + l * ld];
-      if (p.conj) v.y = -v.y;
-      if (!isfinite(v.x) || !isfinite(v.y)) {
+      // integer operations on the bit patterns only (binary64 compares and negations would
+      // occupy this GPU's scarce FP64 pipe)
+      longlong2 v = make_longlong2(0, 0);
+      if (r < R && l < K) v = reinterpret_cast<const longlong2*>(P)[p.trans ? l + r * ld : r + l * ld];
+      if (p.conj) v.y ^= static_cast<long long>(0x8000000000000000ull);
+      const bool fx = (v.x & 0x7FF0000000000000ll) == 0x7FF0000000000000ll;
+      const bool fy = (v.y & 0x7FF0000000000000ll) == 0x7FF0000000000000ll;
+      if (fx || fy) {
         bad = 1;
         rowbad[rl] = 1;
-        if (!isfinite(v.x)) v.x = 0.0;
-        if (!isfinite(v.y)) v.y = 0.0;
+        if (fx) v.x = 0;
+        if (fy) v.y = 0;
       }
-      tile[rl][ll] = v;
+      tile[rl][ll] = make_double2(__longlong_as_double(v.x), __longlong_as_double(v.y));
     }
   };
 
