@@ -50,7 +50,7 @@ def test_split_subnormal_and_extreme_rows(ozk_mod, handle):
     assert np.array_equal(ozk_mod.to_numpy(d).astype(np.int64), d_ref)
 
 
-@pytest.mark.parametrize("S,mode", [(1, 0), (4, 0), (7, 0), (8, 0), (9, 0), (12, 0), (3, 1), (5, 1), (8, 1)])
+@pytest.mark.parametrize("S,mode", [(1, 0), (4, 0), (5, 0), (7, 0), (8, 0), (9, 0), (12, 0), (3, 1), (5, 1), (8, 1)])
 @pytest.mark.parametrize("mnk", [(7, 5, 3), (129, 40, 77), (256, 65, 300)])
 def test_group_sums_bit_exact(ozk_mod, handle, S, mode, mnk):
     m, n, k = mnk
@@ -181,8 +181,10 @@ def test_config1_full_size_bit_exact_and_error(ozk_mod, handle):
     assert np.linalg.norm(got - X) / np.linalg.norm(X) <= 1e-13
 
 
-@pytest.mark.parametrize("S", [3, 7, 10])
+@pytest.mark.parametrize("S", [3, 5, 7, 10])
 def test_large_k_multi_chunk(ozk_mod, handle, S):
+    """K' = 5000 spans several exactness chunks: the 128-bit multi-chunk epilogue (at S = 5 in
+    the compile-time S = 5 kernel instance)."""
     m, n, k = 64, 16, 2500
     A, B = rand_complex(m, k, 70), rand_complex(k, n, 71)
     C = _dev(ozk_mod, np.zeros((m, n), dtype=np.complex128))
