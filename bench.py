@@ -583,7 +583,7 @@ def comparisons(ozk, h, args, dev, t_np, G_np):
             ozk.kkr_build_m(h, tb, Gd, M)
             tau = torch.zeros((B, B), dtype=torch.complex128, device=dev).t()
             ev[0].record()
-            ozk.kkr_tau00(h, M, t0d, tau, S=S, nb=nb_override or args.nb)
+            ozk.kkr_tau00(h, M, t0d, tau, S=S, nb=0 if nb_override == -1 else (nb_override or args.nb))
             ev[1].record()
             torch.cuda.synchronize()
             ms += ev[0].elapsed_time(ev[1])
@@ -596,8 +596,10 @@ def comparisons(ozk, h, args, dev, t_np, G_np):
     out["dmma_tau00_solves_per_s_single"] = round(1e3 / ms_dmma, 2)
     errs = {}
     for S in (3, 4, 5, 6, 7, 8, 9):
-        tau, ms = solve(S, 2)
-        errs[str(S)] = {"rel_err_vs_dmma_fp64": float(rel_err(tau, tau_ref)), "single_solve_ms": round(ms, 3)}
+        solve(S, 1, nb_override=-1)               # first call: the single-matrix panel width is tuned
+        tau, ms = solve(S, 2, nb_override=-1)
+        errs[str(S)] = {"rel_err_vs_dmma_fp64": float(rel_err(tau, tau_ref)), "single_solve_ms": round(ms, 3),
+                        "nb": "autotuned for one matrix"}
     out["tau00_per_S"] = errs
     # single ZGEMM, 512^3 (configuration 1) and 2048^3
     for (m, S) in ((512, 7), (2048, 7)):

@@ -310,7 +310,9 @@ ozk_status_t kkr_build_m_shared_sizes(ozk_handle_t handle, int natoms, const int
  * pivoting in binary64), L = M[0:p, p:q] D^-1 written in place, M[0:p, 0:p] -= L M[p:q, 0:p].
  *   S >= 1: both GEMMs are the emulated ZGEMM with S slices.
  *   S <= 0: both GEMMs are binary64 DMMA GEMMs (the baseline).
- *   nb <= OZK_NB_MAX (the pivot block is held in shared memory).
+ *   nb <= OZK_NB_MAX (the pivot block is held in shared memory).  nb = 0: for S >= 1 the
+ *   width kkr_tau00_autotune picks for one matrix of order n (tuned on the first such call,
+ *   which must not be captured, and cached in the handle); for S <= 0, 32.
  *   M   : DEVICE n x n column major (ld n), DESTROYED (overwritten by the factorisation).
  *   t0  : DEVICE b x b column major.  tau00: DEVICE b x b column major output.
  *   b <= 64 (16 for lmax = 3; 50 for lmax = 4 with spin), nb a multiple of b.  Site 0 occupies

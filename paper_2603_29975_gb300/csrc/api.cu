@@ -916,11 +916,28 @@ ozk_status_t kkr_build_m(ozk_handle_t h, int L, int b, const void* t, const void
   return cuda_check(cudaGetLastError(), "build_m launch");
 }
 
+static std::vector<int> tune_key(int nsolves, const int* n, int b, int S);
+
 // tau_00 of one matrix: eliminate panels J = [p, q) from the trailing end, centre last.  Each
 // panel: D^-1 of its pivot block (binary64 Gauss-Jordan), L = M_RJ D^-1 and M_RR -= L M_JR as
 // emulated GEMMs (S >= 1) or binary64 DMMA GEMMs (S <= 0).
 ozk_status_t kkr_tau00(ozk_handle_t h, int n, int b, void* Mv, const void* t0, void* tau, int S, int nb) {
   if (!h || !Mv || !t0 || !tau) return set_error(OZK_ERR_ARG, "null argument");
+  if (nb == 0 && b > 0 && b <= 64 && n > 0 && n % b == 0) {
+    // the panel width kkr_tau00_autotune picks for one matrix of this size (emulated), or 32
+    // (binary64 DMMA)
+    if (S <= 0) {
+      nb = std::min(GJINV_MAX, (32 + b - 1) / b * b);
+    } else {
+      auto it = h->tuned_nb.find(tune_key(1, &n, b, S));
+      if (it != h->tuned_nb.end()) {
+        nb = it->second;
+      } else {
+        ozk_status_t st = kkr_tau00_autotune(h, 1, &n, b, S, &nb, nullptr);
+        if (st) return st;
+      }
+    }
+  }
   if (b <= 0 || n <= 0 || n % b || nb < b || nb % b || b > 64 || nb > GJINV_MAX)
     return set_error(OZK_ERR_ARG, "need n % b == 0, b <= 64, b <= nb <= 112, nb % b == 0");
   double2* M = static_cast<double2*>(Mv);

@@ -197,6 +197,27 @@ def test_autotuned_panel_width_is_cached_and_used(ozk_mod):
     h.close()
 
 
+def test_single_solve_autotuned_panel_width(ozk_mod):
+    """kkr_tau00 with nb = 0 tunes the panel width for one matrix on its first call (cached per
+    handle) and then equals a call with that width bit for bit."""
+    h = ozk_mod.Handle()
+    t, G, M = _system(27)
+    runs = []
+    for _ in range(2):
+        tau = ozk_mod.colmajor_cuda(np.zeros((16, 16), dtype=np.complex128))
+        ozk_mod.kkr_tau00(h, ozk_mod.colmajor_cuda(M), ozk_mod.colmajor_cuda(t[0]), tau, S=7, nb=0)
+        runs.append(ozk_mod.to_numpy(tau))
+    assert h.status() == 0
+    best, _ = ozk_mod.kkr_tau00_autotune(h, [M.shape[0]], 16, S=7)
+    tau = ozk_mod.colmajor_cuda(np.zeros((16, 16), dtype=np.complex128))
+    ozk_mod.kkr_tau00(h, ozk_mod.colmajor_cuda(M), ozk_mod.colmajor_cuda(t[0]), tau, S=7, nb=best)
+    fixed = ozk_mod.to_numpy(tau)
+    assert np.array_equal(runs[0], runs[1])
+    full = kkr.tau00_full(M, t[0])
+    assert kkr.rel_err(runs[0], full) <= 1e-10 and kkr.rel_err(fixed, full) <= 1e-10
+    h.close()
+
+
 def test_build_m_shared_sizes_uses_leading_blocks_of_G(ozk_mod, handle):
     """Atoms with LIZs of 9, 15 and 27 sites on one lattice: atom a's M is I - t_a G[:n_a, :n_a]
     with the leading block of the 27-site G, block row by block row as the oracle forms it."""
