@@ -476,9 +476,11 @@ __device__ __forceinline__ void epilogue_fast64(const GemmParams& p, const EpiCt
       fe[q] = in ? p.f[x.z * p.f_stride + jc] : 0;
       cv[q] = (in && needC && jc >= x.skip_n) ? x.Cz[x.crow + jc * x.ldc] : make_double2(0.0, 0.0);
     }
+    // I - Z: RN(-V) = -RN(V), so the off-diagonal outputs 0 - z need no binary64 operation
+    const bool negate = p.mode == EPI_IMINUS;
     double zz[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) zz[j] = round_v64(V[8 * half + j], x.er + fe[j >> 1]);
+    for (int j = 0; j < 8; ++j) zz[j] = round_v64(negate ? -V[8 * half + j] : V[8 * half + j], x.er + fe[j >> 1]);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int jc = jc0 + 4 * half + q;
@@ -491,7 +493,7 @@ __device__ __forceinline__ void epilogue_fast64(const GemmParams& p, const EpiCt
         } else if (p.mode == EPI_LU) {
           *dst = make_double2(cv[q].x - zr, cv[q].y - zi);
         } else if (p.mode == EPI_IMINUS) {
-          *dst = make_double2((jc == x.grow ? 1.0 : 0.0) - zr, 0.0 - zi);
+          *dst = make_double2(jc == x.grow ? 1.0 + zr : zr, zi);   // zr, zi hold -z
         } else {
           const double xr = p.ar * zr - p.ai * zi, xi = p.ar * zi + p.ai * zr;
           const double yr = p.br * cv[q].x - p.bi * cv[q].y, yi = p.br * cv[q].y + p.bi * cv[q].x;
