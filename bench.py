@@ -601,6 +601,24 @@ def comparisons(ozk, h, args, dev, t_np, G_np):
         errs[str(S)] = {"rel_err_vs_dmma_fp64": float(rel_err(tau, tau_ref)), "single_solve_ms": round(ms, 3),
                         "nb": "autotuned for one matrix"}
     out["tau00_per_S"] = errs
+    # the LU variant (pivot blocks factored, emulated ZTRSMs): single solves
+    lu = {}
+    for S in (5, 7):
+        for nb in (32, 64):
+            taus, ms = [], 0.0
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            for r in range(3):
+                ozk.kkr_build_m(h, tb, Gd, M)
+                tau = torch.zeros((B, B), dtype=torch.complex128, device=dev).t()
+                ev[0].record()
+                ozk.kkr_tau00_lu(h, M, t0d, tau, S=S, nb=nb)
+                ev[1].record()
+                torch.cuda.synchronize()
+                if r:
+                    ms += ev[0].elapsed_time(ev[1]) / 2
+                taus.append(tau.cpu().numpy())
+            lu[f"S{S}_nb{nb}"] = {"single_solve_ms": round(ms, 3), "rel_err_vs_dmma_fp64": float(rel_err(taus[-1], tau_ref))}
+    out["tau00_lu_variant"] = lu
     # single ZGEMM, 512^3 (configuration 1) and 2048^3
     for (m, S) in ((512, 7), (2048, 7)):
         A, Bm = synth.zgemm_operands(m, m, m)

@@ -322,7 +322,25 @@ ozk_status_t kkr_build_m_shared_sizes(ozk_handle_t handle, int natoms, const int
 ozk_status_t kkr_tau00(ozk_handle_t handle, int n, int b, void* M, const void* t0, void* tau00,
                        int S, int nb);
 
-/* Batched tau_00 over `nsolves` independent (atom, energy) matrices of sizes n[i] (HOST
+/* Right-side triangular solve with emulated GEMMs (paper Sec. 3.2: the ZGEMM and ZTRSM mix of
+ * the LU-based inversion): solves X T = B for X and overwrites B with it.  T: DEVICE n x n
+ * column major (ld ldt >= n), upper (uplo 'U') or lower ('L') triangular, its stored diagonal
+ * used (diag 'N') or taken as ones ('U'); the other triangle is not read.  B: DEVICE m x n
+ * column major (ld ldb >= m).  Block columns of 16: each block column of X is B's block column
+ * minus the already solved columns times T's block column (an emulated GEMM with S slices),
+ * times the binary64 inverse of T's 16 x 16 diagonal block (an emulated GEMM).  A zero
+ * diagonal element of a non-unit T sets OZK_ERR_SINGULAR.  S in 1..16. */
+ozk_status_t ozaki_ztrsm(ozk_handle_t handle, char uplo, char diag, int m, int n, const void* T, int ldt,
+                         void* B, int ldb, int S);
+
+/* tau_00 as kkr_tau00, with every pivot block factored instead of inverted: P D = L U (binary64,
+ * partial pivoting; the row interchanges are applied to the panel's row strip too), then
+ * M_RJ := M_RJ U^-1 L^-1 by two emulated ZTRSMs (ozaki_ztrsm) and M_RR -= M_RJ (P M_JR) by an
+ * emulated GEMM.  Arguments as kkr_tau00 (nb >= b explicit, S >= 1). */
+ozk_status_t kkr_tau00_lu(ozk_handle_t handle, int n, int b, void* M, const void* t0, void* tau00,
+                          int S, int nb);
+
+/* Batched tau_00 over `nsolves` independent (atom, energy) matrices of sizes n[i] (HOST/* Batched tau_00 over `nsolves` independent (atom, energy) matrices of sizes n[i] (HOST
  * array, multiples of b): M, t0, tau00 are DEVICE arrays of DEVICE pointers.  All solves
  * advance panel by panel in lockstep; each step is one batched launch per kernel.
  * nb = 0: the panel width kkr_tau00_autotune chose for these sizes, b and S (tuned on the

@@ -44,7 +44,7 @@ EXPORTS = ["ozk_create", "ozk_destroy", "ozk_set_stream", "ozk_get_status", "ozk
            "ozk_selector_get_params", "ozk_selector_load", "ozk_selector_save", "ozk_selector_configure",
            "ozk_selector_features", "ozk_selector_predict", "ozk_selector_train_step", "ozk_selector_gradient",
            "ozk_selector_last", "ozk_rel_diff", "kkr_build_m_shared", "kkr_tau00_autotune",
-           "kkr_build_m_shared_sizes", "kkr_contour_trace", "ozaki2_zgemm"]
+           "kkr_build_m_shared_sizes", "kkr_contour_trace", "ozaki2_zgemm", "ozaki_ztrsm", "kkr_tau00_lu"]
 KIND_NAMES = ["split", "slice_gemm", "gj", "build_m", "dmma", "other"]
 
 _lib = None
@@ -86,6 +86,8 @@ def lib():
         L.kkr_build_m_shared_sizes.argtypes = [vp, i, ip, i, vp, vp, i, vp, i]
         L.kkr_contour_trace.argtypes = [vp, i, i, vp, dp, dp, dp]
         L.ozaki2_zgemm.argtypes = [vp, c, c, i, i, i, dp, vp, i, vp, i, dp, vp, i, i]
+        L.ozaki_ztrsm.argtypes = [vp, c, c, i, i, vp, i, vp, i, i]
+        L.kkr_tau00_lu.argtypes = [vp, i, i, vp, vp, vp, i, i]
         L.ozaki_zgemm_noalloc.argtypes = [vp, c, c, i, i, i, dp, vp, i, vp, i, dp, vp, i, i, i, vp]
         fp, u64, f32 = ctypes.POINTER(ctypes.c_float), ctypes.c_uint64, ctypes.c_float
         L.ozk_selector_init.argtypes = [vp, u64]
@@ -402,6 +404,25 @@ def kkr_tau00(h: Handle, M, t0, tau, S: int = 7, nb: int = 64):
     b = t0.shape[0]
     _ld(M, n)
     _check(lib().kkr_tau00(h.ptr, n, b, _ptr(M), _ptr(t0), _ptr(tau), S, nb), "kkr_tau00")
+    return tau
+
+
+def ozaki_ztrsm(h: Handle, T, B, uplo: str = "U", diag: str = "N", S: int = 7):
+    """X T = B for X, B overwritten (right side; T triangular, column-major tensors)."""
+    m, n = B.shape
+    if T.shape != (n, n):
+        raise OzkError("T must be n x n for an m x n B")
+    _check(lib().ozaki_ztrsm(h.ptr, uplo.encode(), diag.encode(), m, n, _ptr(T), _ld(T, n), _ptr(B), _ld(B, m), S),
+           "ozaki_ztrsm")
+    return B
+
+
+def kkr_tau00_lu(h: Handle, M, t0, tau, S: int = 7, nb: int = 64):
+    """tau_00 with LU-factored pivot blocks and emulated ZTRSMs (M is overwritten)."""
+    n = M.shape[0]
+    b = t0.shape[0]
+    _ld(M, n)
+    _check(lib().kkr_tau00_lu(h.ptr, n, b, _ptr(M), _ptr(t0), _ptr(tau), S, nb), "kkr_tau00_lu")
     return tau
 
 

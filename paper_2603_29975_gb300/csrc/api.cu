@@ -1017,6 +1017,140 @@ ozk_status_t kkr_tau00(ozk_handle_t h, int n, int b, void* Mv, const void* t0, v
   return cuda_check(cudaGetLastError(), "kkr_tau00 launches");
 }
 
+// ---- emulated ZTRSM (right side) and the LU-based tau_00
+// X T = B solved in place (B := X), B m x w, T w x w triangular, by block columns of ZTRSM_BT:
+// block column j of X is (B_j - the solved columns times T's block column j) times the inverse
+// of T's diagonal block; the update and the product by the block inverse are emulated GEMMs,
+// the block inverse is binary64.  Upper T: block columns in order 0, 1, ...; lower: from the
+// last.  Workspace at ws_offset: the block inverse, then the GEMM workspace.
+constexpr int ZTRSM_BT = 16;
+
+static ozk_status_t ztrsm_right(ozk_context* h, bool upper, bool unit, int m, int w, const double2* T, long long ldt,
+                                double2* B, long long ldb, int S, size_t ws_offset) {
+  const int bt = ZTRSM_BT;
+  const int nblk = (w + bt - 1) / bt;
+  double2* tinv = reinterpret_cast<double2*>(static_cast<uint8_t*>(h->ws) + ws_offset);
+  const size_t gemm_off = ws_offset + align_up(sizeof(double2) * bt * bt, 1024);
+  for (int step = 0; step < nblk; ++step) {
+    const int j = upper ? step : nblk - 1 - step;
+    const int c0 = j * bt, r = std::min(bt, w - c0);
+    double2* Bj = B + static_cast<long long>(c0) * ldb;
+    const int k0 = upper ? 0 : c0 + r;             // first solved column used by the update
+    const int kk = upper ? c0 : w - c0 - r;        // number of solved columns
+    if (kk > 0 && m > 0) {
+      EmuGemm g;                                   // B_j -= X_solved T[solved, block j]
+      g.oa = {0, 0}; g.ob = {0, 0}; g.batch = 1;
+      g.mmax = g.m = m; g.nmax = g.n = r; g.kmax = g.k = kk;
+      g.A = B + static_cast<long long>(k0) * ldb; g.lda = static_cast<int>(ldb);
+      g.B = T + k0 + static_cast<long long>(c0) * ldt; g.ldb = static_cast<int>(ldt);
+      g.C = Bj; g.ldc = static_cast<int>(ldb);
+      g.S = S; g.ar = -1; g.br = 1;
+      ozk_status_t st = run_emulated(h, g, gemm_off);
+      if (st) return st;
+    }
+    {
+      Prof pr(h, OZK_KIND_GJ, 8.0 * r * r * r / 3.0, 32.0 * r * r);
+      launch_tri_inv(T + c0 + static_cast<long long>(c0) * ldt, ldt, r, upper ? 1 : 0, unit ? 1 : 0, tinv, bt,
+                     h->d_status, h->stream);
+    }
+    if (m > 0) {
+      EmuGemm g;                                   // B_j := B_j T_jj^-1 (in place: A is split first)
+      g.oa = {0, 0}; g.ob = {0, 0}; g.batch = 1;
+      g.mmax = g.m = m; g.nmax = g.n = r; g.kmax = g.k = r;
+      g.A = Bj; g.lda = static_cast<int>(ldb); g.B = tinv; g.ldb = bt; g.C = Bj; g.ldc = static_cast<int>(ldb);
+      g.S = S; g.ar = 1; g.br = 0;
+      ozk_status_t st = run_emulated(h, g, gemm_off);
+      if (st) return st;
+    }
+  }
+  return OZK_OK;
+}
+
+static size_t ztrsm_ws_bytes(int m, int w, int S, ozk_status_t* st) {
+  EmuGemm probe;
+  probe.mmax = std::max(m, 1); probe.nmax = ZTRSM_BT; probe.kmax = std::max(w, ZTRSM_BT); probe.S = S;
+  GemmPlan P;
+  *st = plan_gemm(probe, &P);
+  return align_up(sizeof(double2) * ZTRSM_BT * ZTRSM_BT, 1024) + P.total;
+}
+
+ozk_status_t ozaki_ztrsm(ozk_handle_t h, char uplo, char diag, int m, int n, const void* T, int ldt, void* B, int ldb,
+                         int S) {
+  if (!h) return set_error(OZK_ERR_ARG, "null handle");
+  const bool upper = uplo == 'U' || uplo == 'u', unit = diag == 'U' || diag == 'u';
+  if (!(upper || uplo == 'L' || uplo == 'l') || !(unit || diag == 'N' || diag == 'n'))
+    return set_error(OZK_ERR_ARG, "uplo must be 'U' or 'L', diag 'N' or 'U'");
+  if (m < 0 || n < 0) return set_error(OZK_ERR_ARG, "negative dimension");
+  if (S < 1 || S > 16) return set_error(OZK_ERR_ARG, "S must be in 1..16");
+  if (m == 0 || n == 0) return OZK_OK;
+  if (!T || !B) return set_error(OZK_ERR_ARG, "null argument");
+  if (ldt < n || ldb < m) return set_error(OZK_ERR_ARG, "ldt < n or ldb < m");
+  ozk_status_t st = OZK_OK;
+  const size_t need = ztrsm_ws_bytes(m, n, S, &st);
+  if (st) return st;
+  st = ensure_ws(h, need);
+  if (st) return st;
+  st = ztrsm_right(h, upper, unit, m, n, static_cast<const double2*>(T), ldt, static_cast<double2*>(B), ldb, S, 0);
+  if (st) return st;
+  return cuda_check(cudaGetLastError(), "ozaki_ztrsm launches");
+}
+
+// tau_00 with the pivot blocks factored instead of inverted: per panel P D = L U (binary64,
+// partial pivoting, the interchanges also applied to the row strip M_JR), M_RJ := M_RJ U^-1 L^-1
+// by two emulated right-side ZTRSMs, M_RR -= M_RJ (P M_JR) by an emulated GEMM -- the
+// ZGEMM + ZTRSM mix of an LU-based inversion.  Same Schur complement S_00 as kkr_tau00.
+ozk_status_t kkr_tau00_lu(ozk_handle_t h, int n, int b, void* Mv, const void* t0, void* tau, int S, int nb) {
+  if (!h || !Mv || !t0 || !tau) return set_error(OZK_ERR_ARG, "null argument");
+  if (S < 1) return set_error(OZK_ERR_ARG, "the LU variant runs emulated GEMMs (S >= 1)");
+  if (b <= 0 || n <= 0 || n % b || nb < b || nb % b || b > 64 || nb > GJINV_MAX)
+    return set_error(OZK_ERR_ARG, "need n % b == 0, b <= 64, b <= nb <= 112, nb % b == 0");
+  double2* M = static_cast<double2*>(Mv);
+  ozk_status_t st = OZK_OK;
+  size_t need = ztrsm_ws_bytes(n, nb, S, &st);
+  if (st) return st;
+  {
+    EmuGemm probe;
+    probe.mmax = n; probe.nmax = n; probe.kmax = nb; probe.S = S;
+    GemmPlan P;
+    st = plan_gemm(probe, &P);
+    if (st) return st;
+    need = std::max(need, P.total);
+  }
+  st = ensure_ws(h, need);
+  if (st) return st;
+  for (int q = n; q > b;) {
+    const int p = std::max(q - nb, b), w = q - p;
+    double2* D = M + p + static_cast<long long>(p) * n;
+    double2* Lp = M + static_cast<long long>(p) * n;            // M[0:p, p:q]
+    double2* Up = M + p;                                         // M[p:q, 0:p]
+    {
+      Prof pr(h, OZK_KIND_GJ, 8.0 * w * w * w / 3.0, 32.0 * w * w);
+      launch_lu_panel(D, n, w, Up, n, p, h->d_status, h->stream);
+    }
+    st = ztrsm_right(h, true, false, p, w, D, n, Lp, n, S, 0);    // M_RJ U^-1
+    if (st) return st;
+    st = ztrsm_right(h, false, true, p, w, D, n, Lp, n, S, 0);    // then L^-1 (unit lower)
+    if (st) return st;
+    EmuGemm g2;                                                   // M_RR -= M_RJ (P M_JR)
+    g2.oa = {0, 0}; g2.ob = {0, 0}; g2.batch = 1;
+    g2.mmax = g2.m = p; g2.nmax = g2.n = p; g2.kmax = g2.k = w;
+    g2.A = Lp; g2.lda = n; g2.B = Up; g2.ldb = n; g2.C = M; g2.ldc = n;
+    g2.S = S; g2.ar = -1; g2.br = 1;
+    st = run_emulated(h, g2, 0);
+    if (st) return st;
+    q = p;
+  }
+  GjParams gj{};
+  gj.D = nullptr; gj.D1 = M; gj.ldd1 = n; gj.nb1 = b;
+  gj.R1 = static_cast<const double2*>(t0); gj.ldr1 = b; gj.nrhs = b;
+  gj.X1 = static_cast<double2*>(tau); gj.ldx1 = b; gj.status = h->d_status;
+  {
+    Prof pr(h, OZK_KIND_GJ, 8.0 * b * b * 2.0 * b, 48.0 * b * b);
+    launch_gj(gj, b, b, 1, h->stream);
+  }
+  return cuda_check(cudaGetLastError(), "kkr_tau00_lu launches");
+}
+
 // Shared-G build.  Lh (HOST, per atom) may be null: every atom has L sites and G has order L b;
 // otherwise atom a has Lh[a] sites, L = max Lh[a], and its G is the leading block of G (ld ldg).
 static ozk_status_t build_m_shared_impl(ozk_context* h, int natoms, const int* Lh, int L, int b,

@@ -320,6 +320,164 @@ gjinv_kernel(const GjParams p) {
   }
 }
 
+// In-place LU factorisation with partial pivoting of a w x w pivot block (w <= GJINV_MAX,
+// binary64): P D = L U with L unit lower triangular (its multipliers stored below the
+// diagonal) and U upper triangular, written back over D; every row interchange of step k is
+// applied to the whole block row, and afterwards -- in the same order -- to the rows of the
+// panel's row strip Rs (w rows, ncols columns, leading dimension ldr), so that the trailing
+// update can use the interchanged strip directly.  w^3 / 3 complex multiply-adds.
+__global__ void __launch_bounds__(GJINV_THREADS)
+lu_panel_kernel(double2* D, long long ldd, int w, double2* Rs, long long ldr, int ncols, int* status) {
+  extern __shared__ double2 A[];            // [w][w] column major
+  __shared__ int perm[GJINV_MAX];
+  __shared__ int s_piv, s_sing;
+  __shared__ double2 s_pinv;
+  const int tid = threadIdx.x;
+  const int ww = w * w;
+  for (int idx = tid; idx < ww; idx += GJINV_THREADS) {
+    const int j = idx / w, i = idx - j * w;
+    A[idx] = D[i + j * ldd];
+  }
+  if (tid == 0) s_sing = 0;
+  __syncthreads();
+  for (int k = 0; k < w; ++k) {
+    if (tid < 32) {
+      double best = -1.0;
+      int bi = k;
+      for (int r = k + tid; r < w; r += 32) {
+        const double2 v = A[r + k * w];
+        const double a = v.x * v.x + v.y * v.y;
+        if (a > best) { best = a; bi = r; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_down_sync(0xffffffffu, best, o);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (tid == 0) {
+        s_piv = bi;
+        perm[k] = bi;
+        if (best <= 0.0) {
+          s_sing = 1;
+        } else {
+          const double2 v = A[bi + k * w];
+          const double inv = 1.0 / best;               // the one division of the step
+          s_pinv = make_double2(v.x * inv, -v.y * inv);
+        }
+      }
+    }
+    __syncthreads();
+    if (s_sing) break;
+    const int piv = s_piv;
+    if (piv != k)
+      for (int j = tid; j < w; j += GJINV_THREADS) {
+        const double2 t = A[k + j * w];
+        A[k + j * w] = A[piv + j * w];
+        A[piv + j * w] = t;
+      }
+    __syncthreads();
+    const double2 pinv = s_pinv;
+    for (int i = k + 1 + tid; i < w; i += GJINV_THREADS) A[i + k * w] = cmul(A[i + k * w], pinv);
+    __syncthreads();
+    const int r = w - k - 1;                // trailing block rows / columns k+1 .. w-1
+    for (int idx = tid; idx < r * r; idx += GJINV_THREADS) {
+      const int jj = idx / r, ii = idx - jj * r;
+      const int i = k + 1 + ii, j = k + 1 + jj;
+      const double2 l = A[i + k * w], u = A[k + j * w];
+      double2 y = A[i + j * w];
+      y.x = fma(-l.x, u.x, y.x);
+      y.x = fma(l.y, u.y, y.x);
+      y.y = fma(-l.x, u.y, y.y);
+      y.y = fma(-l.y, u.x, y.y);
+      A[i + j * w] = y;
+    }
+    __syncthreads();
+  }
+  const bool singular = s_sing != 0;
+  if (singular && tid == 0) flag_error(status, OZK_ERR_SINGULAR);
+  for (int idx = tid; idx < ww; idx += GJINV_THREADS) {
+    const int j = idx / w, i = idx - j * w;
+    D[i + j * ldd] = A[idx];
+  }
+  if (singular) return;
+  // the same interchanges, in order, on the row strip
+  for (int k = 0; k < w; ++k) {
+    const int pk = perm[k];
+    if (pk != k)
+      for (int j = tid; j < ncols; j += GJINV_THREADS) {
+        const double2 t = Rs[k + j * ldr];
+        Rs[k + j * ldr] = Rs[pk + j * ldr];
+        Rs[pk + j * ldr] = t;
+      }
+    __syncthreads();
+  }
+}
+
+void launch_lu_panel(double2* D, long long ldd, int w, double2* Rs, long long ldr, int ncols, int* status,
+                     cudaStream_t st) {
+  const size_t smem = sizeof(double2) * static_cast<size_t>(w) * w;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(lu_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  lu_panel_kernel<<<1, GJINV_THREADS, smem, st>>>(D, ldd, w, Rs, ldr, ncols, status);
+  record_launch();
+}
+
+// Inverse of the r x r triangular diagonal block T (leading dimension ldt) into X (leading
+// dimension ldx), binary64: upper or lower triangular, with its stored diagonal or (unit) with
+// ones there.  The other triangle of T is ignored.  Thread c computes column c by substitution.
+// r <= TRI_INV_MAX.
+// a / d for a nonzero d; flags a singular block and returns 0 otherwise
+__device__ __forceinline__ double2 cdiv_checked(double2 a, double2 d, int* status) {
+  const double den = d.x * d.x + d.y * d.y;
+  if (den == 0.0) { flag_error(status, OZK_ERR_SINGULAR); return make_double2(0.0, 0.0); }
+  return make_double2((a.x * d.x + a.y * d.y) / den, (a.y * d.x - a.x * d.y) / den);
+}
+
+__global__ void tri_inv_kernel(const double2* T, long long ldt, int r, int upper, int unit, double2* X, long long ldx,
+                               int* status) {
+  __shared__ double2 t[TRI_INV_MAX][TRI_INV_MAX + 1];
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < r * r; idx += blockDim.x) {
+    const int j = idx / r, i = idx - j * r;
+    t[i][j] = T[i + j * ldt];
+  }
+  __syncthreads();
+  for (int c = tid; c < r; c += blockDim.x) {
+    double2 x[TRI_INV_MAX];
+    if (upper) {
+      for (int i = r - 1; i >= 0; --i) {
+        if (i > c) { x[i] = make_double2(0.0, 0.0); continue; }
+        double2 acc = make_double2(i == c ? 1.0 : 0.0, 0.0);
+        for (int j = i + 1; j <= c; ++j) {
+          const double2 u = t[i][j];
+          acc.x -= u.x * x[j].x - u.y * x[j].y;
+          acc.y -= u.x * x[j].y + u.y * x[j].x;
+        }
+        x[i] = unit ? acc : cdiv_checked(acc, t[i][i], status);
+      }
+    } else {
+      for (int i = 0; i < r; ++i) {
+        if (i < c) { x[i] = make_double2(0.0, 0.0); continue; }
+        double2 acc = make_double2(i == c ? 1.0 : 0.0, 0.0);
+        for (int j = c; j < i; ++j) {
+          const double2 l = t[i][j];
+          acc.x -= l.x * x[j].x - l.y * x[j].y;
+          acc.y -= l.x * x[j].y + l.y * x[j].x;
+        }
+        x[i] = unit ? acc : cdiv_checked(acc, t[i][i], status);
+      }
+    }
+    for (int i = 0; i < r; ++i) X[i + c * ldx] = x[i];
+  }
+}
+
+void launch_tri_inv(const double2* T, long long ldt, int r, int upper, int unit, double2* X, long long ldx, int* status,
+                    cudaStream_t st) {
+  tri_inv_kernel<<<1, TRI_INV_MAX, 0, st>>>(T, ldt, r, upper, unit, X, ldx, status);
+  record_launch();
+}
+
 void launch_gjinv(const GjParams& p, int max_w, int batch, cudaStream_t st) {
   const size_t smem = sizeof(double2) * static_cast<size_t>(max_w) * max_w;
   if (smem > 48 * 1024)

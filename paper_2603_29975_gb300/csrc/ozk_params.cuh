@@ -137,6 +137,14 @@ void launch_gj(const GjParams& p, int max_nb, int max_nrhs, int batch, cudaStrea
 // unused
 constexpr int GJINV_MAX = OZK_NB_MAX;
 void launch_gjinv(const GjParams& p, int max_w, int batch, cudaStream_t st);
+// P D = L U in place (w <= GJINV_MAX) with the row interchanges applied to the row strip Rs
+// (w x ncols, leading dimension ldr) as well
+void launch_lu_panel(double2* D, long long ldd, int w, double2* Rs, long long ldr, int ncols, int* status,
+                     cudaStream_t st);
+// X = inverse of the r x r triangular block T (upper or lower; unit: ones on the diagonal)
+constexpr int TRI_INV_MAX = 32;
+void launch_tri_inv(const double2* T, long long ldt, int r, int upper, int unit, double2* X, long long ldx, int* status,
+                    cudaStream_t st);
 void launch_build_m(int n, int b, const double2* t, const double2* G, double2* M, cudaStream_t st);
 void launch_build_m_batched(const int* L, int b, const double2* const* t, const double2* const* G, double2* const* M,
                             int nmax, int batch, cudaStream_t st);
