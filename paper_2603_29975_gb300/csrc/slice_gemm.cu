@@ -115,6 +115,26 @@ __device__ __forceinline__ bool issue_kblock(uint32_t tmem, uint32_t a_lo, uint3
   return true;
 }
 
+// A later K-block of a chunk: every accumulator is live, so the partners of A slice s can share
+// one A read.  The B slices sit back to back in shared memory (slice t at row (t - 1) BN) and
+// group g = s + t at TMEM column (g - 2) BN, so A_s x [B_1 .. B_nt]^T is a single MMA of
+// N = nt BN landing on the columns of groups s + 1 .. s + nt (split at N = 256).  Same products,
+// same accumulators as the pair-by-pair order; a third of the A traffic out of shared memory.
+template <int S, bool FULLSET, int BN>
+__device__ __forceinline__ void issue_kblock_stacked(uint32_t tmem, uint32_t a_lo, uint32_t b_lo, uint32_t hi) {
+#pragma unroll
+  for (int s = 1; s <= S; ++s) {
+    constexpr int NMAX = 256;
+    const int ncols = (FULLSET ? S : S + 1 - s) * BN;
+#pragma unroll
+    for (int c0 = 0; c0 < ncols; c0 += NMAX) {
+      const int n = ncols - c0 < NMAX ? ncols - c0 : NMAX;
+      mma_f16_lo(tmem + (s - 1) * BN + c0, a_lo + (s - 1) * (GEMM_BM * 32 / 16), b_lo + c0 * (32 / 16), hi,
+                 idesc_f16_f32(GEMM_BM, n), 1u);
+    }
+  }
+}
+
 template <int S, bool FULLSET, int BN>
 __device__ __forceinline__ bool issue_kblock_any(bool firstkb, uint32_t tmem, uint32_t a_lo, uint32_t b_lo, uint32_t hi,
                                                  uint32_t idesc, uint64_t* acc_empty, uint32_t rel_parity,
@@ -122,8 +142,8 @@ __device__ __forceinline__ bool issue_kblock_any(bool firstkb, uint32_t tmem, ui
   if (firstkb)
     return issue_kblock<S, FULLSET, BN, true>(tmem, a_lo, b_lo, hi, idesc, acc_empty, rel_parity, wait_release, status,
                                               abort_flag);
-  return issue_kblock<S, FULLSET, BN, false>(tmem, a_lo, b_lo, hi, idesc, acc_empty, rel_parity, wait_release, status,
-                                             abort_flag);
+  issue_kblock_stacked<S, FULLSET, BN>(tmem, a_lo, b_lo, hi);
+  return true;
 }
 
 // Runtime schedule (S > 8, or S > 4 with the full pair set: the 32-column tiles).
