@@ -423,22 +423,17 @@ __device__ __forceinline__ void epilogue_halves(const GemmParams& p, const EpiCt
 }
 
 // RN-even of V 2^E for a two's-complement V with |V| < 2^63 (the exact sum when it fits in 64
-// bits): normalise, keep 53 bits, round half to even on the 11 bits below; integer
-// instructions only.  Results outside the normal range take the general routine.
+// bits).  The int64 -> binary64 conversion is that rounding (RN-even of the integer to 53
+// bits); while the result stays normal, the scaling by 2^E is exact and is an addition to the
+// exponent field.  Results outside the normal range take the general routine, which rounds
+// once at the subnormal position.
 __device__ __forceinline__ double round_v64(long long V, int E) {
-  const bool neg = V < 0;
-  const unsigned long long u = neg ? 0ull - static_cast<unsigned long long>(V) : static_cast<unsigned long long>(V);
-  if (u == 0ull) return 0.0;
-  const int lz = __clzll(u);
-  const unsigned long long M = u << lz;
-  const int q = E - lz + 11;                          // ulp exponent of a normal 53-bit result
-  if (q < -1074 || q > 970) return round_scaled_dev(static_cast<__int128>(V), E);
-  unsigned long long keep = M >> 11;
-  const unsigned int rem = static_cast<unsigned int>(M) & 0x7FFu;
-  keep += (rem > 0x400u || (rem == 0x400u && (keep & 1ull))) ? 1ull : 0ull;
-  unsigned long long bits = (static_cast<unsigned long long>(q + 1074) << 52) + keep;
-  if (neg) bits |= 0x8000000000000000ull;
-  return __longlong_as_double(static_cast<long long>(bits));
+  const double d = __ll2double_rn(V);
+  const long long bits = __double_as_longlong(d);
+  const int ed = static_cast<int>((bits >> 52) & 0x7FF);
+  if (ed == 0) return d;                                // V = 0
+  if (ed + E < 1 || ed + E > 2046) return round_scaled_dev(static_cast<__int128>(V), E);
+  return __longlong_as_double(bits + (static_cast<long long>(E) << 52));
 }
 
 // Epilogue of one 128 x 64 tile when the exact sum of every output fits in 64 bits: one
