@@ -348,6 +348,21 @@ ozk_status_t run_emulated(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0
   gp.S = S; gp.ngroups = P.G; gp.kblocks = P.kblocks; gp.chunk_kb = P.chunk_kb; gp.nstage = P.nstage;
   gp.magic = P.magic;
   {
+    // group g receives the products of its own pairs only: 16 per K-block and pair, each at most
+    // 2^14 in magnitude, so a group of np pairs stays within 2^22 when 16 np chunk_kb <= 256
+    int np[32] = {0};
+    for (int s1 = 1; s1 <= S; ++s1)
+      for (int t1 = 1; t1 <= S; ++t1) {
+        if (diag && s1 != t1) continue;
+        if (!diag && g.pair_mode != OZK_PAIRS_FULL && s1 + t1 > S + 1) continue;
+        const int gi = diag ? s1 - 1 : s1 + t1 - 2;
+        if (gi < 32) ++np[gi];
+      }
+    gp.magic_mask = 0;
+    for (int gi = 0; gi < std::min(P.G, 32); ++gi)
+      if (np[gi] > 0 && 16LL * np[gi] * P.chunk_kb <= 256) gp.magic_mask |= static_cast<int>(1u << gi);
+  }
+  {
     // the 64-bit epilogue: one exactness chunk and |sum| < 2^(ceil(log2 terms) + 14 + 8 (G - 1) + 1)
     // <= 2^63, terms = the digit products one accumulator receives
     const double terms = 16.0 * P.kblocks * P.maxpairs;

@@ -67,6 +67,22 @@ __device__ __forceinline__ int acc_to_int(uint32_t bits, bool magic) {
   return magic ? (__float_as_int(x + 12582912.0f) - 0x4B400000) : __float2int_rn(x);
 }
 
+// V[j] += v_j w for 8 exact FP32 accumulators of one group.  MAGIC (uniform over the warp):
+// the group's accumulators stay within 2^22 in magnitude, so one FP32 add and a reinterpret
+// convert them (x + 1.5 2^23 lies in [2^23, 2^24], where every integer is representable);
+// otherwise the hardware conversion.  The branch keeps the conversion unit out of the first
+// case.
+__device__ __forceinline__ void fold8(long long* V, const uint32_t (&v)[8], long long w, bool magic) {
+  if (magic) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      V[j] += static_cast<long long>(__float_as_int(__uint_as_float(v[j]) + 12582912.0f) - 0x4B400000) * w;
+  } else {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) V[j] += static_cast<long long>(__float2int_rn(__uint_as_float(v[j]))) * w;
+  }
+}
+
 __device__ __forceinline__ void tmem_ld2(uint32_t taddr, uint32_t& a, uint32_t& b) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(a), "=r"(b) : "r"(taddr));
 }
@@ -442,8 +458,8 @@ __device__ __forceinline__ double round_v64(long long V, int E) {
 // 2^(8 (G - 1 - g)) and its accumulator released; then the thread's C values and column
 // exponents are requested, the 16 sums rounded (their latency hides the loads') and combined.
 template <int G>
-__device__ __forceinline__ void epilogue_fast64(const GemmParams& p, const EpiCtx& x, uint64_t* acc_empty, bool magic,
-                                                int lane) {
+__device__ __forceinline__ void epilogue_fast64(const GemmParams& p, const EpiCtx& x, uint64_t* acc_empty,
+                                                uint32_t magic_mask, int lane) {
   constexpr int BN = 64;
   const bool needC = p.mode == EPI_LU || p.mode == EPI_GENERAL;
   const int jc0 = (x.n0 + x.c0) / 2;                  // this thread's 8 complex columns
@@ -471,11 +487,9 @@ __device__ __forceinline__ void epilogue_fast64(const GemmParams& p, const EpiCt
     __syncwarp();
     if (lane == 0) mbar_arrive(&acc_empty[gi]);         // group gi may be overwritten now
     const long long w = 1ll << (8 * (G - 1 - gi));
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      V[j] += static_cast<long long>(acc_to_int(v[j], magic)) * w;
-      V[j + 8] += static_cast<long long>(acc_to_int(u[j], magic)) * w;
-    }
+    const bool mg = (magic_mask >> gi) & 1u;
+    fold8(V, v, w, mg);
+    fold8(V + 8, u, w, mg);
   }
   if (!active) return;
   // two halves of 4 complex columns: a half's C values and exponents are requested, its 8 sums
@@ -683,6 +697,7 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     const int c0 = slab * COLS;                  // first local stacked column of this thread
     const uint32_t tbase = tmem + (static_cast<uint32_t>(quad * 32) << 16) + c0;
     const bool magic = p.magic != 0;
+    const uint32_t magic_mask = magic ? 0xFFFFFFFFu : static_cast<uint32_t>(p.magic_mask);
     const bool horner = nchunks == 1;
     uint32_t cc = 0;
     bool ok = true;
@@ -707,16 +722,16 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
           // tiles); longer K: the group-wise drain that releases accumulators earliest (1.14x
           // on 976 x 976 x 64)
           if constexpr (SF > 0) {
-            if (SF <= 5 && p.fit64) epilogue_fast64<(SF <= 5 ? SF : 5)>(p, x, acc_empty, magic, lane);
+            if (SF <= 5 && p.fit64) epilogue_fast64<(SF <= 5 ? SF : 5)>(p, x, acc_empty, magic_mask, lane);
             else if (p.kblocks <= 2) epilogue_halves<SF>(p, x, acc_empty, magic, lane);
             else epilogue_fast<SF>(p, x, acc_empty, magic, lane);
           } else if (p.fit64 && G <= 5) {
             switch (G) {
-              case 1: epilogue_fast64<1>(p, x, acc_empty, magic, lane); break;
-              case 2: epilogue_fast64<2>(p, x, acc_empty, magic, lane); break;
-              case 3: epilogue_fast64<3>(p, x, acc_empty, magic, lane); break;
-              case 4: epilogue_fast64<4>(p, x, acc_empty, magic, lane); break;
-              default: epilogue_fast64<5>(p, x, acc_empty, magic, lane); break;
+              case 1: epilogue_fast64<1>(p, x, acc_empty, magic_mask, lane); break;
+              case 2: epilogue_fast64<2>(p, x, acc_empty, magic_mask, lane); break;
+              case 3: epilogue_fast64<3>(p, x, acc_empty, magic_mask, lane); break;
+              case 4: epilogue_fast64<4>(p, x, acc_empty, magic_mask, lane); break;
+              default: epilogue_fast64<5>(p, x, acc_empty, magic_mask, lane); break;
             }
           } else if (p.kblocks <= 2) {
             switch (G) {
