@@ -40,7 +40,7 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # nb = 64 chosen by the autotuner), from the ncu capture summarised in
 # profiles/slice_gemm_kkr_batch256_dram.md; set back to None whenever the kernel, the
 # workload or the step's launch sequence changes until it is captured again
-SLICE_GEMM_DRAM_BYTES_PER_LAUNCH = None
+SLICE_GEMM_DRAM_BYTES_PER_LAUNCH = 1823.92e6
 
 
 def parse():
