@@ -260,3 +260,41 @@ def test_contour_trace_matches_oracle(ozk_mod, handle):
     assert abs(integral - want) <= 1e-10 * abs(want)
     # the traces are those of the returned blocks
     assert np.allclose(tr, [np.trace(ozk_mod.to_numpy(x)) for x in taus], rtol=1e-15, atol=0)
+
+
+def test_full_size_batch_sampled_atoms(ozk_mod, handle):
+    """The timed step at full size: 256 atoms of the bcc LIZ-65 system (n = 1040, b = 16,
+    E = 0.5 + 0.05i) sharing G, M built by the shared-G emulated block-row GEMMs, all solves in
+    one batched call at S = 5, nb = 64.  Sampled atoms: M bit for bit against the oracle's
+    emulated block-row update, tau_00 against the oracle's block LU with the same S and panels
+    (only the binary64 pivot inverses round differently) and within 1e-10 of the binary64
+    full inverse of the binary64 M."""
+    import torch
+    L, b, natoms, S, nb = 65, 16, 256, 5, 64
+    n = L * b
+    E0 = 0.5 + 0.05j
+    t_first, G, _ = synth.kkr_system(L, b, E0, atom=0)
+    ts = [t_first] + [synth.kkr_t(L, b, atom=a) for a in range(1, natoms)]
+    tdev = [_tblocks(ozk_mod, t) for t in ts]
+    Ms = [torch.empty((n, n), dtype=torch.complex128, device="cuda") for _ in range(natoms)]
+    taus = [torch.zeros((b, b), dtype=torch.complex128, device="cuda") for _ in range(natoms)]
+    ptr = lambda xs: torch.tensor([x.data_ptr() for x in xs], dtype=torch.int64, device="cuda")
+    pt, pm, ptau = ptr(tdev), ptr(Ms), ptr(taus)
+    ozk_mod.kkr_build_m_shared_ptrs(handle, natoms, L, b, pt, ozk_mod.colmajor_cuda(G), pm, S=S)
+    torch.cuda.synchronize()
+    assert handle.status() == 0
+    sample = [0, 131, 255]
+    # Ms hold M^T row-major = M column-major: the transpose of the stored array is M
+    M_gpu = {a: Ms[a].cpu().numpy().T.copy() for a in sample}
+    ozk_mod.kkr_tau00_batched_ptrs(handle, [n] * natoms, b, pm, pt, ptau, S=S, nb=nb)
+    torch.cuda.synchronize()
+    assert handle.status() == 0
+    eye = np.eye(n, dtype=np.complex128)
+    for a in sample:
+        rows_checked = range(L) if a == 0 else (0, 32, L - 1)
+        for i in rows_checked:
+            rows = slice(i * b, (i + 1) * b)
+            assert np.array_equal(M_gpu[a][rows], co.zgemm_lu(eye[rows], ts[a][i], G[rows], S))
+        got = taus[a].cpu().numpy().T
+        assert kkr.rel_err(got, co.tau00_block(M_gpu[a], ts[a][0], nb, S=S)) < 1e-13
+        assert kkr.rel_err(got, co.tau00_full(kkr.kkr_build(ts[a], G), ts[a][0])) <= 1e-10
