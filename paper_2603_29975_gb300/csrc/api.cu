@@ -479,7 +479,9 @@ static ozk_status_t sel_scratch(ozk_context* h, int m, int n, int k, bool needD,
   auto take = [&](size_t bytes) { const size_t o = off; off = align_up(off + std::max<size_t>(bytes, 1), 256); return o; };
   const size_t P = SEL_PROBES;
   const size_t o_ar = take(8 * size_t(m)), o_ae = take(4 * size_t(m)), o_ash = take(8 * size_t(m)), o_az = take(4 * size_t(m));
+  const size_t o_acr = take(8 * size_t(m));
   const size_t o_br = take(8 * size_t(n)), o_be = take(4 * size_t(n)), o_bsh = take(8 * size_t(n)), o_bz = take(4 * size_t(n));
+  const size_t o_bcr = take(8 * size_t(n));
   const size_t o_ex = take(8), o_X = take(16 * P * n), o_yh = take(16 * P * k), o_yl = take(16 * P * k);
   const size_t o_zh = take(16 * P * m), o_zl = take(16 * P * m), o_Wh = take(16 * P * m), o_Wl = take(16 * P * m);
   // chunk partials of the row-strided products: y (k rows over n), zs and W (m rows over k, n)
@@ -492,9 +494,9 @@ static ozk_status_t sel_scratch(ozk_context* h, int m, int n, int k, bool needD,
   if (st) return st;
   uint8_t* b = static_cast<uint8_t*>(h->sel_ws);
   s->a = {reinterpret_cast<double*>(b + o_ar), reinterpret_cast<int*>(b + o_ae), reinterpret_cast<double*>(b + o_ash),
-          reinterpret_cast<int*>(b + o_az)};
+          reinterpret_cast<int*>(b + o_az), reinterpret_cast<double*>(b + o_acr)};
   s->b = {reinterpret_cast<double*>(b + o_br), reinterpret_cast<int*>(b + o_be), reinterpret_cast<double*>(b + o_bsh),
-          reinterpret_cast<int*>(b + o_bz)};
+          reinterpret_cast<int*>(b + o_bz), reinterpret_cast<double*>(b + o_bcr)};
   s->ex = reinterpret_cast<int*>(b + o_ex);
   s->X = reinterpret_cast<double2*>(b + o_X);
   s->yh = reinterpret_cast<double2*>(b + o_yh);

@@ -176,7 +176,8 @@ constexpr int SEL_SMIN = OZK_SEL_SMIN, SEL_SMAX = OZK_SEL_SMAX, SEL_PROBES = 4;
 constexpr int SEL_NPARAMS = OZK_SEL_NPARAMS;
 static_assert(SEL_NPARAMS == SEL_NH * SEL_NF + SEL_NH + SEL_NH * SEL_NH + SEL_NH + SEL_NO * SEL_NH + SEL_NO,
               "selector parameter count");
-struct SelVecStats { double* r; int* e; double* sh; int* z; };   // per-vector arrays
+// per-vector arrays; cr: the crest log2 |v|_max + log2 sqrt(2 len) - log2 ||v|| of a nonzero vector
+struct SelVecStats { double* r; int* e; double* sh; int* z; double* cr; };
 struct SelBases { uint64_t b[2 * SEL_PROBES]; };                 // SplitMix64 stream bases
 struct SelAux { int S; int E; double z2; double resid; double diff; float pred[SEL_NO]; };
 uint64_t sm_base_host(uint64_t seed, uint64_t stream);

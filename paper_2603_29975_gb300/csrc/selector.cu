@@ -71,6 +71,14 @@ __device__ __forceinline__ int frexp_exp(double r) {
   return e;
 }
 
+// crest of a vector of len complex entries: log2 of its largest |Re|, |Im| over its RMS scalar,
+// log2(r) + log2 sqrt(2 len) - log2 ||v|| with ||v||^2 = sh 2^(2e); 0 for a zero vector
+__device__ __forceinline__ double crest_of(double r, int e, double sh, int len) {
+  if (!(r > 0.0)) return 0.0;
+  const double half_l2k = 0.5 * log2(2.0 * len);
+  return log2(ldexp(r, -e)) + half_l2k - 0.5 * log2(sh);
+}
+
 // op(M) = M: vector i is row i, entries M[i + l ld] -- one thread per vector (coalesced)
 __global__ void vec_stats_rows_kernel(const double2* M, long long ld, int count, int len, SelVecStats out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -93,6 +101,7 @@ __global__ void vec_stats_rows_kernel(const double2* M, long long ld, int count,
   out.e[i] = e;
   out.sh[i] = sh;
   out.z[i] = z;
+  out.cr[i] = crest_of(r, e, sh, len);
 }
 
 // op(M) = M^T or M^H: vector i is column i of M, contiguous -- one warp per vector
@@ -125,6 +134,7 @@ __global__ void vec_stats_cols_kernel(const double2* M, long long ld, int count,
     out.e[w] = e;
     out.sh[w] = sh;
     out.z[w] = z;
+    out.cr[w] = crest_of(r, e, sh, len);
   }
 }
 
@@ -205,34 +215,29 @@ __device__ __forceinline__ void cacc_out(const CAcc& A, double2& h, double2& l) 
   l.y = e;
 }
 
-constexpr int GEMV_CHUNK = 64;
+constexpr int GEMV_CHUNK = 16;
 
 // op(M) = M (rows strided): grid.x over blocks of 64 rows, grid.y over chunks of GEMV_CHUNK of
-// the reduction; each thread writes its row's partial double-doubles of its chunk.
+// the reduction, grid.z over the probes; each thread writes its row's partial double-double of
+// its chunk and probe (short dependency chains across many blocks: the compensated sums run on
+// the binary64 pipe).
 __global__ void gemv_rows_kernel(const double2* M, long long ld, int rows, int len, const double2* Xh,
                                  const double2* Xl, int ldx, double2* part, const int* ex, int eidx) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows) return;
   const int E = ex ? ex[eidx] : 0;
+  const int q = blockIdx.z;
   const int l0 = blockIdx.y * GEMV_CHUNK, l1 = min(len, l0 + GEMV_CHUNK);
-  CAcc acc[SEL_PROBES];
-#pragma unroll
-  for (int q = 0; q < SEL_PROBES; ++q) acc[q] = CAcc{0.0, 0.0, 0.0, 0.0};
+  CAcc acc{0.0, 0.0, 0.0, 0.0};
   for (int l = l0; l < l1; ++l) {
     const double2 a = M[i + l * ld];
     const double ar = ldexp(a.x, -E), ai = ldexp(a.y, -E);
-#pragma unroll
-    for (int q = 0; q < SEL_PROBES; ++q)
-      cmac(acc[q], ar, ai, Xh[l + q * ldx], Xl ? Xl[l + q * ldx] : make_double2(0.0, 0.0));
+    cmac(acc, ar, ai, Xh[l + q * ldx], Xl ? Xl[l + q * ldx] : make_double2(0.0, 0.0));
   }
   // part[chunk][q][row] as (s re, s im) then (c re, c im)
-  const long long base = static_cast<long long>(blockIdx.y) * SEL_PROBES * rows;
-#pragma unroll
-  for (int q = 0; q < SEL_PROBES; ++q) {
-    const long long o = 2 * (base + static_cast<long long>(q) * rows + i);
-    part[o] = make_double2(acc[q].rs, acc[q].is);
-    part[o + 1] = make_double2(acc[q].rc, acc[q].ic);
-  }
+  const long long o = 2 * ((static_cast<long long>(blockIdx.y) * SEL_PROBES + q) * rows + i);
+  part[o] = make_double2(acc.rs, acc.is);
+  part[o + 1] = make_double2(acc.rc, acc.ic);
 }
 
 // sum the chunks of gemv_rows_kernel in order: Y = Yh + Yl (rows x SEL_PROBES, ld rows)
@@ -313,15 +318,14 @@ struct CrestStats { double mean, max, std, espread, log2sum_sh, log2sum_one, cou
 
 // Statistics of the nonzero vectors of one operand (see the feature list below).  Emax is the
 // operand's max exponent (ex[]).
-__device__ CrestStats crest_stats(const SelVecStats v, int count, int k, int Emax, double* sh) {
+__device__ CrestStats crest_stats(const SelVecStats v, int count, int Emax, double* sh) {
   CrestStats c{0, 0, 0, 0, -INFINITY, -INFINITY, 0};
-  const double half_l2k = 0.5 * log2(2.0 * k);
   double n = 0, s = 0, mx = -INFINITY, se = 0, ssh = 0, sone = 0;
   for (int i = threadIdx.x; i < count; i += RED_T) {
     const double r = v.r[i];
     if (r > 0.0) {
       const int e = v.e[i];
-      const double cr = log2(ldexp(r, -e)) + half_l2k - 0.5 * log2(v.sh[i]);
+      const double cr = v.cr[i];
       n += 1;
       s += cr;
       mx = fmax(mx, cr);
@@ -340,10 +344,8 @@ __device__ CrestStats crest_stats(const SelVecStats v, int count, int k, int Ema
   const double mean = s / n;
   double d2 = 0;
   for (int i = threadIdx.x; i < count; i += RED_T) {
-    const double r = v.r[i];
-    if (r > 0.0) {
-      const int e = v.e[i];
-      const double cr = log2(ldexp(r, -e)) + half_l2k - 0.5 * log2(v.sh[i]);
+    if (v.r[i] > 0.0) {
+      const double cr = v.cr[i];
       d2 += (cr - mean) * (cr - mean);
     }
   }
@@ -377,8 +379,8 @@ __global__ void __launch_bounds__(RED_T) selector_features_kernel(SelVecStats a,
   // zs: the leading parts of the double-double probe product
   __shared__ double sh[RED_T];
   const int EA = ex[0], EB = ex[1];
-  const CrestStats ca = crest_stats(a, m, k, EA, sh);
-  const CrestStats cb = crest_stats(b, n, k, EB, sh);
+  const CrestStats ca = crest_stats(a, m, EA, sh);
+  const CrestStats cb = crest_stats(b, n, EB, sh);
   double z2 = 0, x2 = 0, za = 0, zb = 0;
   for (int i = threadIdx.x; i < m * SEL_PROBES; i += RED_T) z2 += zs[i].x * zs[i].x + zs[i].y * zs[i].y;
   for (int i = threadIdx.x; i < n * SEL_PROBES; i += RED_T) x2 += X[i].x * X[i].x + X[i].y * X[i].y;
@@ -653,7 +655,8 @@ void launch_gemv(const double2* M, long long ld, int rows, int len, int op, cons
   if (rows <= 0) return;
   if (op == 0) {
     const int nch = std::max(1, gemv_chunks(len));
-    gemv_rows_kernel<<<dim3(blocks(rows, 64), nch), 64, 0, st>>>(M, ld, rows, len, Xh, Xl, ldx, part, ex, eidx);
+    gemv_rows_kernel<<<dim3(blocks(rows, 64), nch, SEL_PROBES), 64, 0, st>>>(M, ld, rows, len, Xh, Xl, ldx, part, ex,
+                                                                              eidx);
     record_launch();
     gemv_reduce_kernel<<<blocks(static_cast<long long>(rows) * SEL_PROBES, 128), 128, 0, st>>>(part, rows, nch, Yh,
                                                                                               Yl);
