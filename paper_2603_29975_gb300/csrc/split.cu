@@ -98,7 +98,7 @@ __device__ __forceinline__ void split_run(const SplitParams& p, const double2* v
 // from global memory once: the tile is loaded, the row maxima are taken from it, then the
 // digits; longer rows take a scan pass and then the tiles one by one.
 template <int VEC, bool W64>
-__global__ void __launch_bounds__(SPLIT_THREADS, VEC == 2 ? (W64 ? 5 : 4) : (W64 ? 3 : 2))
+__global__ void __launch_bounds__(SPLIT_THREADS, VEC == 2 ? (W64 ? 5 : 4) : (W64 ? 4 : 2))
 split_kernel(const SplitPair pp) {
   if (static_cast<int>(blockIdx.z) >= pp.nsides) return;
   const SplitParams& p = pp.s[blockIdx.z];
