@@ -129,25 +129,41 @@ split_kernel(const SplitPair pp) {
   // non-finite scalars are flagged (their row's exponent becomes 0, as a non-finite maximum
   // gives) and split as zero
   auto load_tile = [&](int lt) {
-    for (int idx = tid; idx < SPLIT_ROWS * TK; idx += SPLIT_THREADS) {
+    // all of a thread's loads are issued before any is used, so their latencies overlap (tiles
+    // are at most 16 wide in the VEC = 2 instance, which serves K <= 16 only)
+    constexpr int NPT = SPLIT_ROWS * (VEC == 2 ? 16 : SPLIT_TK) / SPLIT_THREADS;
+    longlong2 v[NPT];
+#pragma unroll
+    for (int u = 0; u < NPT; ++u) {
+      const int idx = tid + u * SPLIT_THREADS;
       int rl, ll;
       if (!p.trans) { rl = idx % SPLIT_ROWS; ll = idx / SPLIT_ROWS; }
       else          { ll = idx % TK;         rl = idx / TK; }
       const int r = r0 + rl, l = lt + ll;
+      v[u] = make_longlong2(0, 0);
+      if (idx < SPLIT_ROWS * TK && r < R && l < K)
+        v[u] = reinterpret_cast<const longlong2*>(P)[p.trans ? l + r * ld : r + l * ld];
+    }
+#pragma unroll
+    for (int u = 0; u < NPT; ++u) {
+      const int idx = tid + u * SPLIT_THREADS;
+      if (idx >= SPLIT_ROWS * TK) break;
+      int rl, ll;
+      if (!p.trans) { rl = idx % SPLIT_ROWS; ll = idx / SPLIT_ROWS; }
+      else          { ll = idx % TK;         rl = idx / TK; }
       // integer operations on the bit patterns only (binary64 compares and negations would
       // occupy this GPU's scarce FP64 pipe)
-      longlong2 v = make_longlong2(0, 0);
-      if (r < R && l < K) v = reinterpret_cast<const longlong2*>(P)[p.trans ? l + r * ld : r + l * ld];
-      if (p.conj) v.y ^= static_cast<long long>(0x8000000000000000ull);
-      const bool fx = (v.x & 0x7FF0000000000000ll) == 0x7FF0000000000000ll;
-      const bool fy = (v.y & 0x7FF0000000000000ll) == 0x7FF0000000000000ll;
+      longlong2 w = v[u];
+      if (p.conj) w.y ^= static_cast<long long>(0x8000000000000000ull);
+      const bool fx = (w.x & 0x7FF0000000000000ll) == 0x7FF0000000000000ll;
+      const bool fy = (w.y & 0x7FF0000000000000ll) == 0x7FF0000000000000ll;
       if (fx || fy) {
         bad = 1;
         rowbad[rl] = 1;
-        if (fx) v.x = 0;
-        if (fy) v.y = 0;
+        if (fx) w.x = 0;
+        if (fy) w.y = 0;
       }
-      tile[rl][ll] = make_double2(__longlong_as_double(v.x), __longlong_as_double(v.y));
+      tile[rl][ll] = make_double2(__longlong_as_double(w.x), __longlong_as_double(w.y));
     }
   };
 
