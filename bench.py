@@ -46,7 +46,7 @@ SLICE_GEMM_DRAM_BYTES_PER_LAUNCH = 1823.92e6
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=256, help="atoms per GPU per step")
@@ -69,8 +69,10 @@ def peaks():
 
 # ----------------------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples (SM clock, throttle reasons), started before the warm-up so that it is
+    sampling when the timed region begins; only the samples whose timestamps fall inside the
+    timed region's wall-clock window are summarised."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -78,11 +80,16 @@ class ClockSampler:
         self.index = index
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         self.p = None
+        self.window = None
+
+    def mark(self, t0, t1):
+        """The timed region as local wall-clock datetimes (nvidia-smi stamps local time)."""
+        self.window = (t0, t1)
 
     def start(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
@@ -97,18 +104,24 @@ class ClockSampler:
             self.p.kill()
         self.f.flush()
         self.f.seek(0)
+        import datetime
         sms, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        slack = datetime.timedelta(milliseconds=50)
         for line in self.f.read().splitlines():
             c = [x.strip() for x in line.split(",")]
-            if len(c) < 9:
+            if len(c) < 10:
                 continue
             try:
-                sms.append(float(c[1]))
-                mx = float(c[2])
+                ts = datetime.datetime.strptime(c[0], "%Y/%m/%d %H:%M:%S.%f")
+                sm, smax = float(c[2]), float(c[3])
             except ValueError:
                 continue
-            for nm, v in zip(names, c[5:9]):
+            if self.window and not (self.window[0] - slack <= ts <= self.window[1] + slack):
+                continue
+            sms.append(sm)
+            mx = smax
+            for nm, v in zip(names, c[6:10]):
                 if v.lower() == "active":
                     reasons.add(nm)
         os.unlink(self.f.name)
@@ -208,6 +221,9 @@ def run_ours(args):
         ozk.kkr_build_m_shared_ptrs(h, batch, L_SITES, B, pt, G, pm, S=args.S_chosen)
         ozk.kkr_tau00_batched_ptrs(h, ns, B, pm, pt0, ptau, S=args.S_chosen if fixed_S else S_solve, nb=args.nb)
 
+    import datetime
+    clk = ClockSampler(local)
+    clk.start()                                   # sampling before the timed region begins
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -215,13 +231,12 @@ def run_ours(args):
         raise RuntimeError("device status set during warm-up")
     stream = torch.cuda.current_stream()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clk = ClockSampler(local)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    clk.start()
     l0 = ozk.launch_count()
     h.profile_begin()
+    d0 = datetime.datetime.now()
     t_wall = time.perf_counter()
     for k in range(args.steps):
         flush.fill_(float(k))                     # L2 flush between timed steps (not timed)
@@ -230,6 +245,7 @@ def run_ours(args):
         evs[k][1].record(stream)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
+    clk.mark(d0, datetime.datetime.now())
     prof = h.profile_end()
     launches = ozk.launch_count() - l0
     clocks = clk.stop()
@@ -683,7 +699,9 @@ def run_reference(args):
     t, G, _ = synth.kkr_system(L_SITES, B, E0, atom=0)
     M = kkr.kkr_build(t, G)
     nb = args.nb or 64                            # the GPU arm autotunes; the oracle uses 64
-    S = args.S or 7                               # the GPU arm's selector runs on the GPU; the oracle uses 7
+    # the GPU arm's selector (a GPU computation) picks S = 5 for this workload at 1e-10 per GEMM;
+    # the oracle solves at that S unless one is given
+    S = args.S or 5
     for _ in range(args.warmup):
         co.tau00_block(M, t[0], nb, S=S)
     t1 = time.perf_counter()
