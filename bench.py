@@ -292,6 +292,9 @@ def run_ours(args):
             "clocks": clocks, "wall_s_timed": round(t_wall, 3)}
     if not args.no_extras:
         line["graph"] = graph_measure(ozk, h, args, step, flush)
+        line["batched_solve_vs_dmma"] = batched_dmma_measure(
+            ozk, h, args, lambda: ozk.kkr_build_m_shared_ptrs(h, batch, L_SITES, B, pt, G, pm, S=args.S_chosen),
+            ns, pm, pt0, ptau, taus)
         line["e2e"] = e2e_measure(ozk, h, args, dev, t_np, G_np, batch)
         del Ms, ts, G, flush
         torch.cuda.empty_cache()
@@ -310,6 +313,37 @@ def run_ours(args):
     h.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def batched_dmma_measure(ozk, h, args, build, ns, pm, pt0, ptau, taus):
+    """The batched solve alone (M rebuilt, untimed, before every run): the step's emulated solve
+    against the same batched algorithm with every GEMM in binary64 on the DMMA kernel, on the
+    step's 256 matrices; tau_00 of every atom compared."""
+    import numpy as np
+    import torch
+    out, res = {}, {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for label, S, nb in (("emulated", args.S_chosen, args.nb), ("dmma_nb32", -1, 32), ("dmma_nb64", -1, 64)):
+        ms = 0.0
+        for r in range(2):                        # the first run warms up
+            build()
+            torch.cuda.synchronize()
+            e0.record()
+            ozk.kkr_tau00_batched_ptrs(h, ns, B, pm, pt0, ptau, S=S, nb=nb)
+            e1.record()
+            torch.cuda.synchronize()
+            if r:
+                ms = e0.elapsed_time(e1)
+        if h.status():
+            raise RuntimeError("device status set in the batched comparison")
+        res[label] = np.stack([t.cpu().numpy() for t in taus])
+        out[label] = {"S": S, "nb": nb, "solve_ms": round(ms, 3), "solves_per_s": round(len(ns) / (ms / 1e3), 2)}
+    d = res["emulated"] - res["dmma_nb32"]
+    per_atom = np.sqrt((np.abs(d) ** 2).sum(axis=(1, 2)) / (np.abs(res["dmma_nb32"]) ** 2).sum(axis=(1, 2)))
+    out["max_rel_err_emulated_vs_dmma"] = float(per_atom.max())
+    out["speedup_vs_best_dmma"] = round(min(out["dmma_nb32"]["solve_ms"], out["dmma_nb64"]["solve_ms"])
+                                        / out["emulated"]["solve_ms"], 2)
+    return out
 
 
 def graph_measure(ozk, h, args, step, flush):

@@ -348,7 +348,9 @@ ozk_status_t kkr_tau00_lu(ozk_handle_t handle, int n, int b, void* M, const void
  * S = 0: the slice-count selector chooses S once for the call, from the operands of solve 0's
  * first trailing update (the L and U panels of its unfactored M) at the handle's tolerance;
  * ozk_selector_last reports the choice.  Synchronises; no per-GEMM residual check on this
- * path.  S < 0 is an error (the batched path is emulated). */
+ * path.  S < 0: every GEMM in binary64 on the DMMA kernel (the native-precision baseline of
+ * the same batched algorithm; L = M_RJ D^-1 goes to per-solve scratch in the handle's
+ * workspace; nb = 0 means 32, as in kkr_tau00). */
 ozk_status_t kkr_tau00_batched(ozk_handle_t handle, int nsolves, const int* n, int b,
                                void* const* M, const void* const* t0, void* const* tau00,
                                int S, int nb);

@@ -1245,7 +1245,8 @@ static ozk_status_t tau00_batched_impl(ozk_handle_t h, int nsolves, const int* n
   if (!h || !n || !M || !t0 || !tau) return set_error(OZK_ERR_ARG, "null argument");
   if (nsolves < 0) return set_error(OZK_ERR_ARG, "negative nsolves");
   if (nsolves == 0) return OZK_OK;
-  if (S <= 0) return set_error(OZK_ERR_ARG, "batched solves run the emulated path (S >= 1)");
+  if (S == 0) return set_error(OZK_ERR_ARG, "S = 0 is resolved to a slice count before the solves");
+  const bool dmma = S < 0;                     // binary64 DMMA GEMMs instead of emulated ones
   if (b <= 0 || b > 64 || nb < b || nb % b || nb > GJINV_MAX)
     return set_error(OZK_ERR_ARG, "need b <= 64, b <= nb <= 112, nb % b == 0");
   int nmax = 0;
@@ -1262,16 +1263,25 @@ static ozk_status_t tau00_batched_impl(ozk_handle_t h, int nsolves, const int* n
   const size_t off_tab = align_up(off_dinv + ns * nb * nb * sizeof(double2), 1024);
   const size_t n_ptr = 8, n_int = 16;
   const size_t off_g1 = align_up(off_tab + ns * (n_ptr * sizeof(void*) + n_int * sizeof(int)), 1024);
-  EmuGemm probe;
-  probe.batch = nsolves; probe.mmax = nmax; probe.nmax = nb; probe.kmax = nb; probe.S = S;
-  GemmPlan P;
-  ozk_status_t st = plan_gemm(probe, &P);
-  if (st) return st;
-  const size_t off_g2 = align_up(off_g1 + P.total, 1024);
-  probe.nmax = nmax;
-  st = plan_gemm(probe, &P);
-  if (st) return st;
-  st = ensure_ws(h, off_g2 + P.total);
+  size_t off_g2 = off_g1, total = off_g1;
+  ozk_status_t st = OZK_OK;
+  if (!dmma) {
+    EmuGemm probe;
+    probe.batch = nsolves; probe.mmax = nmax; probe.nmax = nb; probe.kmax = nb; probe.S = S;
+    GemmPlan P;
+    st = plan_gemm(probe, &P);
+    if (st) return st;
+    off_g2 = align_up(off_g1 + P.total, 1024);
+    probe.nmax = nmax;
+    st = plan_gemm(probe, &P);
+    if (st) return st;
+    total = off_g2 + P.total;
+  } else {
+    // binary64 path: L = M_RJ D^-1 of every solve into its own nmax x nb scratch (a tiled GEMM
+    // cannot overwrite its own operand), then pointer and leading-dimension tables of it
+    total = align_up(off_g1 + ns * nmax * nb * sizeof(double2), 1024) + ns * (sizeof(void*) + sizeof(int));
+  }
+  st = ensure_ws(h, total);
   if (st) return st;
   const int* dn = nullptr;
   st = size_table(h, std::vector<int>(n, n + nsolves), &dn);
@@ -1289,6 +1299,15 @@ static ozk_status_t tau00_batched_impl(ozk_handle_t h, int nsolves, const int* n
   t.lda1 = pi + 3 * ns; t.ldb1 = pi + 4 * ns; t.ldc1 = pi + 5 * ns; t.m1 = pi + 6 * ns; t.n1 = pi + 7 * ns; t.k1 = pi + 8 * ns;
   t.lda2 = pi + 9 * ns; t.ldb2 = pi + 10 * ns; t.ldc2 = pi + 11 * ns; t.m2 = pi + 12 * ns; t.n2 = pi + 13 * ns; t.k2 = pi + 14 * ns;
   double2* const* Mp = reinterpret_cast<double2* const*>(M);
+  double2** tL = nullptr;
+  int* tLld = nullptr;
+  if (dmma) {
+    const size_t off_lt = align_up(off_g1 + ns * nmax * nb * sizeof(double2), 1024);
+    tL = reinterpret_cast<double2**>(ws + off_lt);
+    tLld = reinterpret_cast<int*>(ws + off_lt + ns * sizeof(void*));
+    launch_strided_ptrs(tL, tLld, reinterpret_cast<double2*>(ws + off_g1), static_cast<long long>(nmax) * nb, nmax,
+                        nsolves, h->stream);
+  }
 
   auto gemm_tables = [&](int which, int mmax, int nmaxg, int kmax, double smnk, double smk, double snk, bool lu,
                          int sides, bool gemm, cudaStream_t stream) -> ozk_status_t {
@@ -1332,6 +1351,34 @@ static ozk_status_t tau00_batched_impl(ozk_handle_t h, int nsolves, const int* n
     {
       Prof pr(h, OZK_KIND_OTHER, 0.0, 0.0);
       launch_kkr_step(s, nsolves, dn, Mp, b, nb, dinv, t, h->stream);
+    }
+    if (dmma) {
+      GjParams gj{};
+      gj.D = t.D; gj.ldd = t.ldd; gj.nb = t.nbv; gj.R = nullptr; gj.X = t.X; gj.ldx = t.ldx; gj.nrhs = 0;
+      gj.status = h->d_status;
+      {
+        Prof pr(h, OZK_KIND_GJ, 8.0 * sw3, 32.0 * sw);
+        launch_gjinv(gj, wmax, nsolves, h->stream);
+      }
+      DmmaParams d1{};                                   // L = M_RJ D^-1 into the scratch
+      d1.batch = nsolves; d1.m = pmax; d1.n = wmax; d1.k = wmax;
+      d1.tm = t.m1; d1.tn = t.n1; d1.tk = t.k1;
+      d1.tA = t.A1; d1.tlda = t.lda1; d1.tB = t.B1; d1.tldb = t.ldb1; d1.tC = tL; d1.tldc = tLld;
+      d1.ar = 1; d1.br = 0;
+      {
+        Prof pr(h, OZK_KIND_DMMA, 8.0 * s1, 0.0);
+        launch_dmma(d1, h->stream);
+      }
+      DmmaParams d2{};                                   // M_RR -= L M_JR
+      d2.batch = nsolves; d2.m = pmax; d2.n = pmax; d2.k = wmax;
+      d2.tm = t.m2; d2.tn = t.n2; d2.tk = t.k2;
+      d2.tA = tL; d2.tlda = tLld; d2.tB = t.B2; d2.tldb = t.ldb2; d2.tC = t.C2; d2.tldc = t.ldc2;
+      d2.ar = -1; d2.br = 1;
+      {
+        Prof pr(h, OZK_KIND_DMMA, 8.0 * s3, 0.0);
+        launch_dmma(d2, h->stream);
+      }
+      continue;
     }
     st = cuda_check(cudaEventRecord(h->ev_fork, h->stream), "record fork");
     if (!st) st = cuda_check(cudaStreamWaitEvent(h->aux, h->ev_fork, 0), "side stream wait");
@@ -1656,6 +1703,7 @@ ozk_status_t kkr_tau00_batched(ozk_handle_t h, int nsolves, const int* n, int b,
     ozk_status_t st = select_S_for_solves(h, M, n, b, nb, &S);
     if (st) return st;
   }
+  if (nb == 0 && nsolves > 0 && S < 0) nb = std::min(GJINV_MAX, (32 + b - 1) / b * b);   // binary64: as kkr_tau00
   if (nb == 0 && nsolves > 0) {
     auto it = h->tuned_nb.find(tune_key(nsolves, n, b, S));
     if (it != h->tuned_nb.end()) {

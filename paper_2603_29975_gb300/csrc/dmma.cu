@@ -5,6 +5,8 @@
 // C = alpha op(A) op(B) + beta C, column major.  A CTA computes a 32 x 32 complex tile with
 // four warps (2 x 2), each warp a 16 x 16 tile of 2 x 2 blocks of 8 x 8.  Complex products
 // are four real MMAs per block: Cr += Ar Br, Cr += (-Ai) Bi, Ci += Ar Bi, Ci += Ai Br.
+#include <algorithm>
+
 #include "ozk_params.cuh"
 
 namespace ozk {
@@ -26,18 +28,27 @@ zgemm_dmma_kernel(const DmmaParams p) {
   __shared__ double Br[DM_KT][DM_TILE + 1], Bi[DM_KT][DM_TILE + 1];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int i0 = blockIdx.y * DM_TILE, j0 = blockIdx.x * DM_TILE;
+  const bool batched = p.tm != nullptr;
+  const int z = blockIdx.z;
+  const int m = batched ? p.tm[z] : p.m, n = batched ? p.tn[z] : p.n, kdim = batched ? p.tk[z] : p.k;
+  if (i0 >= m || j0 >= n) return;                 // whole CTA outside this problem
+  const double2* A = batched ? p.tA[z] : p.A;
+  const double2* B = batched ? p.tB[z] : p.B;
+  double2* C = batched ? p.tC[z] : p.C;
+  const long long lda = batched ? p.tlda[z] : p.lda, ldb = batched ? p.tldb[z] : p.ldb;
+  const long long ldc = batched ? p.tldc[z] : p.ldc;
   const int wr = (warp >> 1) * 16, wc = (warp & 1) * 16;
   const int g = lane >> 2, q = lane & 3;
   double cr[2][2][2] = {}, ci[2][2][2] = {};
 
-  for (int l0 = 0; l0 < p.k; l0 += DM_KT) {
+  for (int l0 = 0; l0 < kdim; l0 += DM_KT) {
     // A tile: 32 rows x 8 k ; B tile: 8 k x 32 cols  (256 complex each, 2 per thread)
     for (int idx = tid; idx < DM_TILE * DM_KT; idx += DM_THREADS) {
       int r, l;
       if (!p.transa) { r = idx % DM_TILE; l = idx / DM_TILE; } else { l = idx % DM_KT; r = idx / DM_KT; }
       const int gi = i0 + r, gl = l0 + l;
       double2 v = make_double2(0.0, 0.0);
-      if (gi < p.m && gl < p.k) v = p.transa ? p.A[gl + gi * p.lda] : p.A[gi + gl * p.lda];
+      if (gi < m && gl < kdim) v = p.transa ? A[gl + gi * lda] : A[gi + gl * lda];
       if (p.conja) v.y = -v.y;
       Ar[l][r] = v.x; Ai[l][r] = v.y;
     }
@@ -46,7 +57,7 @@ zgemm_dmma_kernel(const DmmaParams p) {
       if (!p.transb) { l = idx % DM_KT; c = idx / DM_KT; } else { c = idx % DM_TILE; l = idx / DM_TILE; }
       const int gj = j0 + c, gl = l0 + l;
       double2 v = make_double2(0.0, 0.0);
-      if (gj < p.n && gl < p.k) v = p.transb ? p.B[gj + gl * p.ldb] : p.B[gl + gj * p.ldb];
+      if (gj < n && gl < kdim) v = p.transb ? B[gj + gl * ldb] : B[gl + gj * ldb];
       if (p.conjb) v.y = -v.y;
       Br[l][c] = v.x; Bi[l][c] = v.y;
     }
@@ -86,9 +97,9 @@ zgemm_dmma_kernel(const DmmaParams p) {
       for (int h = 0; h < 2; ++h) {
         const int gi = i0 + wr + a * 8 + g;
         const int gj = j0 + wc + b * 8 + 2 * q + h;
-        if (gi < p.m && gj < p.n) {
+        if (gi < m && gj < n) {
           const double zr = cr[a][b][h], zi = ci[a][b][h];
-          double2* dst = p.C + gi + gj * p.ldc;
+          double2* dst = C + gi + gj * ldc;
           double xr = p.ar * zr - p.ai * zi, xi = p.ar * zi + p.ai * zr;
           if (p.br != 0.0 || p.bi != 0.0) {
             const double2 cv = *dst;
@@ -101,8 +112,23 @@ zgemm_dmma_kernel(const DmmaParams p) {
 }
 
 void launch_dmma(const DmmaParams& p, cudaStream_t st) {
-  dim3 grid((p.n + DM_TILE - 1) / DM_TILE, (p.m + DM_TILE - 1) / DM_TILE);
+  if (p.m <= 0 || p.n <= 0) return;
+  dim3 grid((p.n + DM_TILE - 1) / DM_TILE, (p.m + DM_TILE - 1) / DM_TILE, p.tm ? std::max(p.batch, 1) : 1);
   zgemm_dmma_kernel<<<grid, DM_THREADS, 0, st>>>(p);
+  record_launch();
+}
+
+__global__ void strided_ptrs_kernel(double2** out, int* ld, double2* base, long long stride, int ldv, int n) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  if (z < n) {
+    out[z] = base + z * stride;
+    ld[z] = ldv;
+  }
+}
+
+void launch_strided_ptrs(double2** out, int* ld, double2* base, long long stride, int ldv, int n, cudaStream_t st) {
+  if (n <= 0) return;
+  strided_ptrs_kernel<<<(n + 127) / 128, 128, 0, st>>>(out, ld, base, stride, ldv, n);
   record_launch();
 }
 

@@ -116,8 +116,17 @@ struct DmmaParams {
   const double2* B; long long ldb;
   double2* C; long long ldc;
   double ar, ai, br, bi;
+  // batched form (tm != nullptr): problem z = blockIdx.z takes its sizes, pointers and leading
+  // dimensions from these device tables; m, n above are then the largest sizes (grid extent)
+  int batch;
+  const int *tm, *tn, *tk;
+  const double2* const* tA; const int* tlda;
+  const double2* const* tB; const int* tldb;
+  double2* const* tC; const int* tldc;
 };
 void launch_dmma(const DmmaParams& p, cudaStream_t st);
+// out[z] = base + z * stride and ld[z] = ldv for z < n (pointer tables of per-problem scratch)
+void launch_strided_ptrs(double2** out, int* ld, double2* base, long long stride, int ldv, int n, cudaStream_t st);
 
 // ---- lu.cu: Gauss-Jordan solves, M build, scaling
 struct GjParams {
