@@ -9,16 +9,18 @@
 //     (128 rows) and one of B (BN rows) per pipeline stage, 32-byte swizzle;
 //   * warp 1 (one lane) issues tcgen05.mma kind::f16 for every pair (s, t) of the pair set,
 //     accumulating pair products of the same weight class g = s + t into one FP32 TMEM
-//     accumulator per group (G groups x BN columns of the 512);
+//     accumulator per group (G groups x BN columns of the 512); after a chunk's first K-block
+//     the partners of each A slice share one MMA over the stacked B slices;
 //   * warps 2..17 drain the accumulators.  Every product of two digits is an integer of
 //     magnitude <= 2^14 and each accumulator receives at most 1024 of them per "exactness
 //     chunk" of K, so every FP32 value is an exact integer <= 2^24.  The epilogue converts
-//     it to int32 and adds it, shifted by its group weight 8 (g_max - g) bits, into a 128-bit
-//     integer per output element; after the last chunk that integer times 2^(e_i + f_j + c)
-//     is rounded once to binary64 with integer instructions only, then stored (C = Z), or
+//     it to int32 and adds it, shifted by its group weight 8 (g_max - g) bits, into a 64-bit
+//     (when the exact sum fits) or 128-bit integer per output element; after the last chunk
+//     that integer times 2^(e_i + f_j + c) is rounded once to binary64 (the int64 -> binary64
+//     conversion, or integer instructions for the 128-bit sum), then stored (C = Z), or
 //     subtracted from C (LU update), or combined with alpha/beta.
-// No FP64 instruction touches the products; the only binary64 arithmetic is the final
-// subtraction / alpha-beta combination per element.
+// No floating-point instruction touches the products' sums before that one rounding; the
+// only binary64 arithmetic after it is the subtraction / alpha-beta combination per element.
 #include <algorithm>
 
 #include "ozk_params.cuh"
@@ -87,16 +89,9 @@ __device__ __forceinline__ void tmem_ld2(uint32_t taddr, uint32_t& a, uint32_t& 
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(a), "=r"(b) : "r"(taddr));
 }
 
-// Epilogue of one 128 x 64 tile for a single exactness chunk and G <= 8 groups (compile-time):
-// the exact sum of the group values v_g (|v| <= 2^24) is H 2^(8 NL) + L with H = the first
-// NH = min(G, 4) groups and L = the rest, each accumulated by 32 x 32 -> 64-bit multiply-adds
-// with constant weights 2^24, 2^16, 2^8, 1 (|H|, |L| < 2^49).  A thread owns one row and 16
-// stacked columns (8 complex), handled in two halves of 8; the second half releases every
-// group accumulator to the next tile's MMAs.  C and the column exponents of a half are
-// loaded before its arithmetic.
-// Compile-time slice-pair schedule: pairs (s, t) in order of their group g = s + t, the first
-// pair of each group flagged.  The MMA issuer walks it fully unrolled, so one MMA costs two
-// 32-bit descriptor additions and the tcgen05.mma itself.
+// Compile-time slice-pair schedule (a chunk's first K-block): pairs (s, t) in order of their
+// group g = s + t, the first pair of each group flagged.  The MMA issuer walks it fully
+// unrolled, so one MMA costs two 32-bit descriptor additions and the tcgen05.mma itself.
 __device__ __forceinline__ void mma_f16_lo(uint32_t d_tmem, uint32_t a_lo, uint32_t b_lo, uint32_t hi, uint32_t idesc,
                                            uint32_t accumulate) {
   const uint64_t ad = (static_cast<uint64_t>(hi) << 32) | a_lo;
@@ -245,6 +240,13 @@ __device__ __forceinline__ void prefetch_l2(const void* ptr) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<uint64_t>(ptr)));
 }
 
+// Epilogue of one 128 x 64 tile for a single exactness chunk and G <= 8 groups (compile-time):
+// the exact sum of the group values v_g (|v| <= 2^24) is H 2^(8 NL) + L with H = the first
+// NH = min(G, 4) groups and L = the rest, each accumulated by 32 x 32 -> 64-bit multiply-adds
+// with constant weights 2^24, 2^16, 2^8, 1 (|H|, |L| < 2^49).  A thread owns one row and 16
+// stacked columns (8 complex), handled in two halves of 8; the second half releases every
+// group accumulator to the next tile's MMAs.  C and the column exponents of a half are
+// loaded before its arithmetic.
 template <int G>
 __device__ __forceinline__ void epilogue_fast(const GemmParams& p, const EpiCtx& x, uint64_t* acc_empty, bool magic,
                                               int lane) {
