@@ -320,3 +320,23 @@ def test_batched_dmma_equals_single_dmma(ozk_mod, handle):
         got = ozk_mod.to_numpy(taus[i])
         assert np.array_equal(got, single[i])
         assert kkr.rel_err(got, co.tau00_full(M, t[0])) <= 1e-12
+
+
+def test_config4_full_size_against_binary64_solve(ozk_mod, handle):
+    """The largest workload at full size: bcc LIZ 113, b = 50 (lmax = 4 with spin), n = 5650,
+    single emulated solves at S = 5 and 7 with 100-wide panels, within 1e-10 of tau_00 from a
+    binary64 library LU solve of the same M."""
+    import torch
+    L, b = 113, 50
+    t, G, _ = synth.kkr_system(L, b, 0.5 + 0.05j, atom=0)
+    M = kkr.kkr_build(t, G)
+    ref = kkr.tau00_lapack(M, t[0])
+    M0 = ozk_mod.colmajor_cuda(M)
+    t0 = ozk_mod.colmajor_cuda(t[0])
+    for S in (5, 7):
+        Md = M0.clone()
+        tau = ozk_mod.colmajor_cuda(np.zeros((b, b), dtype=np.complex128))
+        ozk_mod.kkr_tau00(handle, Md, t0, tau, S=S, nb=100)
+        torch.cuda.synchronize()
+        assert handle.status() == 0
+        assert kkr.rel_err(ozk_mod.to_numpy(tau), ref) <= 1e-10

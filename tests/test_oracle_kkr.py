@@ -61,6 +61,14 @@ def test_tau00_full_against_library_solve():
     assert kkr.rel_err(co.tau00_full(M, t[0]), ref) < 1e-13
 
 
+def test_tau00_lapack_against_gauss_jordan():
+    """The library-solve reference used at the largest sizes agrees with the oracle's own
+    Gauss-Jordan inverse (two independent computations of [M^-1]_00 t_0), also for b = 50."""
+    for L, b in ((15, 16), (5, 50)):
+        t, G, M = _system(L, b=b)
+        assert kkr.rel_err(kkr.tau00_lapack(M, t[0]), co.tau00_full(M, t[0])) < 1e-13
+
+
 @pytest.mark.parametrize("nb,leaf", [(16, None), (32, None), (48, None), (64, 16), (48, 16), (128, 16)])
 def test_block_lu_agrees_with_full_inverse(nb, leaf):
     t, G, M = _system(15)
