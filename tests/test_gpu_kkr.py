@@ -71,24 +71,27 @@ def test_tau00_wider_panels(ozk_mod, handle):
         assert kkr.rel_err(ozk_mod.to_numpy(tau), full) <= 1e-10
 
 
-def test_batched_equals_single(ozk_mod, handle):
+@pytest.mark.parametrize("S", [7, 9])
+def test_batched_equals_single(ozk_mod, handle, S):
+    """Batched lockstep solves equal single solves bit for bit; S = 9 takes the 128-bit integer
+    images and the 128-bit reconstruction."""
     sizes = [27, 9, 51, 15, 2]
     Es = [0.5 + 0.05j, -1.0 + 0.3j, 0.69 + 0.01j, 0.2 + 0.9j, 0.6 + 0.2j]
     systems = [_system(L, E, atom=i) for i, (L, E) in enumerate(zip(sizes, Es))]
     single = []
     for t, G, M in systems:
         tau = ozk_mod.colmajor_cuda(np.zeros((16, 16), dtype=np.complex128))
-        ozk_mod.kkr_tau00(handle, ozk_mod.colmajor_cuda(M), ozk_mod.colmajor_cuda(t[0]), tau, S=7, nb=64)
+        ozk_mod.kkr_tau00(handle, ozk_mod.colmajor_cuda(M), ozk_mod.colmajor_cuda(t[0]), tau, S=S, nb=64)
         single.append(ozk_mod.to_numpy(tau))
     Ms = [ozk_mod.colmajor_cuda(M) for t, G, M in systems]
     t0s = [ozk_mod.colmajor_cuda(t[0]) for t, G, M in systems]
     taus = [ozk_mod.colmajor_cuda(np.zeros((16, 16), dtype=np.complex128)) for _ in systems]
-    ozk_mod.kkr_tau00_batched(handle, Ms, t0s, taus, S=7, nb=64)
+    ozk_mod.kkr_tau00_batched(handle, Ms, t0s, taus, S=S, nb=64)
     assert handle.status() == 0
     for i, (t, G, M) in enumerate(systems):
         got = ozk_mod.to_numpy(taus[i])
         assert np.array_equal(got, single[i])
-        assert kkr.rel_err(got, kkr.tau00_full(M, t[0])) <= 1e-10
+        assert kkr.rel_err(got, co.tau00_full(M, t[0])) <= 1e-10
 
 
 def test_singular_pivot_sets_status(ozk_mod, handle):
