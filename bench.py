@@ -676,22 +676,23 @@ def comparisons(ozk, h, args, dev, t_np, G_np):
         Bd = ozk.colmajor_cuda(Bm)
         C = ozk.colmajor_cuda(np.zeros((m, m), dtype=np.complex128))
         C2 = ozk.colmajor_cuda(np.zeros((m, m), dtype=np.complex128))
-        for _ in range(2):
+        for _ in range(3):                        # warm-up
             ozk.ozaki_zgemm(h, Ad, Bd, C, S=S)
             ozk.ozk_zgemm_dmma(h, Ad, Bd, C2)
         torch.cuda.synchronize()
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-        reps = 5
-        e[0].record()
-        for _ in range(reps):
-            ozk.ozaki_zgemm(h, Ad, Bd, C, S=S)
-        e[1].record()
-        for _ in range(2):
-            ozk.ozk_zgemm_dmma(h, Ad, Bd, C2)
-        e[2].record()
-        torch.cuda.synchronize()
-        t_emu = e[0].elapsed_time(e[1]) / reps
-        t_dm = e[1].elapsed_time(e[2]) / 2
+
+        def median_ms(call, reps=20):
+            # CUDA events around every call, the median of the runs
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+            for a, b in ev:
+                a.record()
+                call()
+                b.record()
+            torch.cuda.synchronize()
+            return statistics.median(a.elapsed_time(b) for a, b in ev)
+
+        t_emu = median_ms(lambda: ozk.ozaki_zgemm(h, Ad, Bd, C, S=S))
+        t_dm = median_ms(lambda: ozk.ozk_zgemm_dmma(h, Ad, Bd, C2))
         fl = 8.0 * m ** 3
         out[f"zgemm_{m}^3_S{S}"] = {"emulated_eff_fp64_tflops": round(fl / t_emu / 1e9, 3),
                                     "dmma_tflops": round(fl / t_dm / 1e9, 3),
