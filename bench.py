@@ -96,6 +96,8 @@ class ClockSampler:
 
     def stop(self):
         if self.p is None:
+            self.f.close()
+            os.unlink(self.f.name)
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.p.terminate()
         try:
