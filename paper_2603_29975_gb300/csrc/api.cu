@@ -321,9 +321,9 @@ ozk_status_t run_emulated(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0
   else { sq.X = g.tB; sq.ld = g.tldb; sq.rows = g.tn; sq.kdim = g.tk; }
   const bool split_a = (g.split_sides & 1) != 0, split_b = (g.split_sides & 2) != 0;
   if (split_a || split_b) {
-    // algorithmic bytes: read 16 per complex element (twice: scan + split), write S x 2 fp16
-    // (left operand) or S x 4 fp16 (right operand, two stacked rows per column)
-    Prof pr(h, OZK_KIND_SPLIT, 0.0, (split_a ? smk * (32.0 + 4.0 * S) : 0.0) + (split_b ? snk * (32.0 + 8.0 * S) : 0.0),
+    // algorithmic bytes: read 16 per complex element, write S x 2 fp16 (left operand) or S x 4
+    // fp16 (right operand, two stacked rows per column)
+    Prof pr(h, OZK_KIND_SPLIT, 0.0, (split_a ? smk * (16.0 + 4.0 * S) : 0.0) + (split_b ? snk * (16.0 + 8.0 * S) : 0.0),
             stream);
     if (diag) {
       if (split_a) launch_residue_split(sp, *g.oz2, g.mmax, g.batch, stream);
