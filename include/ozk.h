@@ -121,8 +121,10 @@ ozk_status_t ozk_profile_end(ozk_handle_t handle, uint64_t* launches, double* ms
  * conjugate transpose), exactly the BLAS ZGEMM argument list plus the slice count S.
  *   alpha, beta : HOST pointers to two doubles (re, im).
  *   A, B, C     : DEVICE pointers, column major, lda/ldb/ldc >= rows of the stored matrix.
- *   S           : 1..16 slices (B = 8S - 1 bits), or 0: the slice-count selector chooses S
- *                 in 3..10 and checks the result (see the selector section; triangular pairs).
+ *   S           : 1..16 slices (B = 8S - 1 bits); 0: the slice-count selector chooses S
+ *                 in 3..10 and checks the result (see the selector section; triangular pairs);
+ *                 < 0: the binary64 DMMA GEMM (ozk_zgemm_dmma, pair_mode ignored).  The same
+ *                 rule holds for every S argument of this library.
  *                 pair_mode: OZK_PAIRS_TRI / _FULL.
  * Epilogues: beta == 0 stores RN(alpha Z) (alpha == 1: bitwise equal to the oracle);
  * alpha == -1, beta == 1 computes C - RN(Z) with one binary64 subtraction (bitwise equal
@@ -135,7 +137,8 @@ ozk_status_t ozaki_zgemm(ozk_handle_t handle, char transa, char transb, int m, i
 
 /* Batched form: `batch` independent problems; A, B, C are DEVICE arrays of `batch` DEVICE
  * pointers; m, n, k, lda, ldb, ldc are HOST arrays of `batch` entries (variable sizes).
- * Problems with m, n == 0 are skipped. */
+ * Problems with m, n == 0 are skipped.  S >= 1 emulated, S < 0 binary64 DMMA over the same
+ * tables; S = 0 (the selector, a single-GEMM mode) returns OZK_ERR_ARG. */
 ozk_status_t ozaki_zgemm_vbatched(ozk_handle_t handle, char transa, char transb,
                                   const int* m, const int* n, const int* k,
                                   const double* alpha, const void* const* A, const int* lda,
@@ -308,11 +311,18 @@ ozk_status_t kkr_build_m_shared_sizes(ozk_handle_t handle, int natoms, const int
  * Schur complement left there.
  * Each panel: D^-1 of its pivot block D = M[p:q, p:q] (in-place Gauss-Jordan with partial
  * pivoting in binary64), L = M[0:p, p:q] D^-1 written in place, M[0:p, 0:p] -= L M[p:q, 0:p].
+ * The operation on (t, G, LIZ) is kkr_build_m (or kkr_build_m_shared for atoms sharing G)
+ * followed by this call on the M it built.  The slice count follows the ozaki_zgemm rule:
  *   S >= 1: both GEMMs are the emulated ZGEMM with S slices.
- *   S <= 0: both GEMMs are binary64 DMMA GEMMs (the baseline).
+ *   S = 0:  every GEMM is the emulated ZGEMM at the slice count the selector picks for its
+ *           operands, with the residual check and the S = 10 fallback of ozaki_zgemm (S = 0);
+ *           needs selector parameters, synchronises per GEMM, cannot be captured;
+ *           ozk_selector_last reports the last GEMM of the solve.
+ *   S < 0:  both GEMMs are binary64 DMMA GEMMs (the native-precision baseline).
  *   nb <= OZK_NB_MAX (the pivot block is held in shared memory).  nb = 0: for S >= 1 the
  *   width kkr_tau00_autotune picks for one matrix of order n (tuned on the first such call,
- *   which must not be captured, and cached in the handle); for S <= 0, 32.
+ *   which must not be captured, and cached in the handle; S = 0 takes the width tuned at
+ *   S = 7); for S < 0, 32.
  *   M   : DEVICE n x n column major (ld n), DESTROYED (overwritten by the factorisation).
  *   t0  : DEVICE b x b column major.  tau00: DEVICE b x b column major output.
  *   b <= 64 (16 for lmax = 3; 50 for lmax = 4 with spin), nb a multiple of b.  Site 0 occupies
@@ -340,7 +350,7 @@ ozk_status_t ozaki_ztrsm(ozk_handle_t handle, char uplo, char diag, int m, int n
 ozk_status_t kkr_tau00_lu(ozk_handle_t handle, int n, int b, void* M, const void* t0, void* tau00,
                           int S, int nb);
 
-/* Batched tau_00 over `nsolves` independent (atom, energy) matrices of sizes n[i] (HOST/* Batched tau_00 over `nsolves` independent (atom, energy) matrices of sizes n[i] (HOST
+/* Batched tau_00 over `nsolves` independent (atom, energy) matrices of sizes n[i] (HOST
  * array, multiples of b): M, t0, tau00 are DEVICE arrays of DEVICE pointers.  All solves
  * advance panel by panel in lockstep; each step is one batched launch per kernel.
  * nb = 0: the panel width kkr_tau00_autotune chose for these sizes, b and S (tuned on the

@@ -1,10 +1,12 @@
 // C ABI of libozk (declared in include/ozk.h): handle, workspace, TMA descriptors, and the
 // host-side drivers of the emulated ZGEMM and of the block-LU tau_00 solve.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <vector>
 
 #include "ozk_params.cuh"
@@ -540,7 +542,7 @@ static ozk_status_t read_aux(ozk_context* h, const SelAux* d, SelAux* out) {
 }
 
 // S = 0: choose S, compute the product, check it with the probes, fall back to SMAX.
-static ozk_status_t zgemm_auto(ozk_context* h, const EmuGemm& g) {
+static ozk_status_t zgemm_auto(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0) {
   if (!h->sel_ready)
     return set_error(OZK_ERR_ARG, "S = 0 needs selector parameters (ozk_selector_init, _load or _set_params)");
   if (capturing(h->stream))
@@ -568,7 +570,7 @@ static ozk_status_t zgemm_auto(ozk_context* h, const EmuGemm& g) {
   d.pair_mode = OZK_PAIRS_TRI;
   auto product_and_check = [&](int S, double* r) -> ozk_status_t {
     d.S = S;
-    ozk_status_t e = run_emulated(h, d);
+    ozk_status_t e = run_emulated(h, d, ws_offset);
     if (e) return e;
     launch_gemv(d.C, d.ldc, m, n, 0, s.X, nullptr, n, s.Wh, s.Wl, s.part, nullptr, 0, h->stream);
     launch_residual(s.Wh, s.Wl, s.zh, s.zl, m, s.aux, h->stream);
@@ -688,6 +690,7 @@ ozk_status_t ozaki_zgemm(ozk_handle_t h, char transa, char transb, int m, int n,
                          const void* A, int lda, const void* B, int ldb, const double* beta, void* C, int ldc,
                          int S, int pair_mode) {
   if (!h || !alpha || !beta) return set_error(OZK_ERR_ARG, "null argument");
+  if (S < 0) return ozk_zgemm_dmma(h, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
   EmuGemm g;
   if (!parse_op(transa, &g.oa) || !parse_op(transb, &g.ob)) return set_error(OZK_ERR_ARG, "bad trans flag");
   ozk_status_t st = check_dims(g.oa, g.ob, m, n, k, lda, ldb, ldc);
@@ -822,14 +825,18 @@ ozk_status_t ozaki_zgemm_vbatched(ozk_handle_t h, char transa, char transb, cons
     mm = std::max(mm, m[i]); nn = std::max(nn, n[i]); kk = std::max(kk, k[i]);
   }
   if (mm == 0 || nn == 0) return OZK_OK;
+  if (S == 0) return set_error(OZK_ERR_ARG, "vbatched: S = 0 (the selector) is a single-GEMM mode");
   g.batch = batch; g.mmax = mm; g.nmax = nn; g.kmax = kk;
   g.ar = alpha[0]; g.ai = alpha[1]; g.br = beta[0]; g.bi = beta[1];
   g.S = S; g.pair_mode = pair_mode;
   GemmPlan P;
-  ozk_status_t st = plan_gemm(g, &P);
-  if (st) return st;
-  st = ensure_ws(h, P.total);
-  if (st) return st;
+  ozk_status_t st = OZK_OK;
+  if (S > 0) {
+    st = plan_gemm(g, &P);
+    if (st) return st;
+    st = ensure_ws(h, P.total);
+    if (st) return st;
+  }
   // device table of sizes: m, n, k, lda, ldb, ldc
   std::vector<int> tab(6 * static_cast<size_t>(batch));
   for (int i = 0; i < batch; ++i) {
@@ -849,6 +856,20 @@ ozk_status_t ozaki_zgemm_vbatched(ozk_handle_t h, char transa, char transb, cons
     g.sum_mnk += static_cast<double>(m[i]) * n[i] * k[i];
     g.sum_mk += static_cast<double>(m[i]) * k[i];
     g.sum_nk += static_cast<double>(n[i]) * k[i];
+  }
+  if (S < 0) {
+    // binary64 DMMA GEMMs over the same tables (the native-precision baseline)
+    DmmaParams d{};
+    d.batch = batch; d.m = mm; d.n = nn; d.k = kk;
+    d.transa = g.oa.trans; d.conja = g.oa.conj; d.transb = g.ob.trans; d.conjb = g.ob.conj;
+    d.tm = g.tm; d.tn = g.tn; d.tk = g.tk;
+    d.tA = g.tA; d.tlda = g.tlda; d.tB = g.tB; d.tldb = g.tldb; d.tC = g.tC; d.tldc = g.tldc;
+    d.ar = g.ar; d.ai = g.ai; d.br = g.br; d.bi = g.bi;
+    {
+      Prof pr(h, OZK_KIND_DMMA, 8.0 * g.sum_mnk, 0.0);
+      launch_dmma(d, h->stream);
+    }
+    return cuda_check(cudaGetLastError(), "batched DMMA launch");
   }
   return run_emulated(h, g);
 }
@@ -937,20 +958,30 @@ static std::vector<int> tune_key(int nsolves, const int* n, int b, int S);
 
 // tau_00 of one matrix: eliminate panels J = [p, q) from the trailing end, centre last.  Each
 // panel: D^-1 of its pivot block (binary64 Gauss-Jordan), L = M_RJ D^-1 and M_RR -= L M_JR as
-// emulated GEMMs (S >= 1) or binary64 DMMA GEMMs (S <= 0).
+// emulated GEMMs with S slices (S >= 1), with the slice count the selector picks for each GEMM
+// and its residual check (S = 0), or as binary64 DMMA GEMMs (S < 0).
 ozk_status_t kkr_tau00(ozk_handle_t h, int n, int b, void* Mv, const void* t0, void* tau, int S, int nb) {
   if (!h || !Mv || !t0 || !tau) return set_error(OZK_ERR_ARG, "null argument");
+  if (S > 16) return set_error(OZK_ERR_ARG, "S must be <= 16");
+  const bool dmma = S < 0, auto_S = S == 0;
+  if (auto_S) {
+    if (!h->sel_ready)
+      return set_error(OZK_ERR_ARG, "S = 0 needs selector parameters (ozk_selector_init, _load or _set_params)");
+    if (capturing(h->stream))
+      return set_error(OZK_ERR_CAPTURE, "S = 0 synchronises to read the selector's choices and cannot be captured");
+  }
   if (nb == 0 && b > 0 && b <= 64 && n > 0 && n % b == 0) {
-    // the panel width kkr_tau00_autotune picks for one matrix of this size (emulated), or 32
-    // (binary64 DMMA)
-    if (S <= 0) {
+    // the panel width kkr_tau00_autotune picks for one matrix of this size (emulated; S = 0:
+    // tuned at S = 7), or 32 (binary64 DMMA)
+    if (dmma) {
       nb = std::min(GJINV_MAX, (32 + b - 1) / b * b);
     } else {
-      auto it = h->tuned_nb.find(tune_key(1, &n, b, S));
+      const int St = auto_S ? 7 : S;
+      auto it = h->tuned_nb.find(tune_key(1, &n, b, St));
       if (it != h->tuned_nb.end()) {
         nb = it->second;
       } else {
-        ozk_status_t st = kkr_tau00_autotune(h, 1, &n, b, S, &nb, nullptr);
+        ozk_status_t st = kkr_tau00_autotune(h, 1, &n, b, St, &nb, nullptr);
         if (st) return st;
       }
     }
@@ -958,21 +989,25 @@ ozk_status_t kkr_tau00(ozk_handle_t h, int n, int b, void* Mv, const void* t0, v
   if (b <= 0 || n <= 0 || n % b || nb < b || nb % b || b > 64 || nb > GJINV_MAX)
     return set_error(OZK_ERR_ARG, "need n % b == 0, b <= 64, b <= nb <= 112, nb % b == 0");
   double2* M = static_cast<double2*>(Mv);
+  // workspace: [D^-1, nb x nb][L scratch, n x nb (DMMA and S = 0)][GEMM workspace (emulated)]
   const size_t dinv_bytes = align_up(sizeof(double2) * nb * nb, 1024);
+  const size_t ltmp_bytes = (dmma || auto_S) ? align_up(sizeof(double2) * static_cast<size_t>(n) * nb, 1024) : 0;
+  const size_t off_gemm = dinv_bytes + ltmp_bytes;
   {
-    size_t need = dinv_bytes + sizeof(double2) * static_cast<size_t>(n) * nb;
-    if (S > 0) {
+    size_t need = off_gemm;
+    if (!dmma) {
       EmuGemm probe;
-      probe.mmax = n; probe.nmax = n; probe.kmax = nb; probe.S = S;
+      probe.mmax = n; probe.nmax = n; probe.kmax = nb; probe.S = auto_S ? SEL_SMAX : S;
       GemmPlan P;
       ozk_status_t st = plan_gemm(probe, &P);
       if (st) return st;
-      need = std::max(need, dinv_bytes + P.total);
+      need += P.total;
     }
     ozk_status_t st = ensure_ws(h, need);
     if (st) return st;
   }
   double2* Dinv = static_cast<double2*>(h->ws);
+  double2* Ltmp = reinterpret_cast<double2*>(static_cast<uint8_t*>(h->ws) + dinv_bytes);
   for (int q = n; q > b;) {
     const int p = std::max(q - nb, b), w = q - p, r = p;
     GjParams gj{};
@@ -984,24 +1019,36 @@ ozk_status_t kkr_tau00(ozk_handle_t h, int n, int b, void* Mv, const void* t0, v
     }
     double2* Lp = M + static_cast<long long>(p) * n;            // M[0:p, p:q]
     const double2* Up = M + p;                                   // M[p:q, 0:p]
-    if (S > 0) {
-      EmuGemm g1;                                                 // L = M_RJ D^-1, in place
+    if (!dmma) {
+      EmuGemm g1;                                                 // L = M_RJ D^-1
       g1.oa = {0, 0}; g1.ob = {0, 0}; g1.batch = 1;
       g1.mmax = g1.m = r; g1.nmax = g1.n = w; g1.kmax = g1.k = w;
-      g1.A = Lp; g1.lda = n; g1.B = Dinv; g1.ldb = w; g1.C = Lp; g1.ldc = n;
+      g1.A = Lp; g1.lda = n; g1.B = Dinv; g1.ldb = w;
       g1.S = S; g1.ar = 1; g1.br = 0;
-      ozk_status_t st = run_emulated(h, g1, dinv_bytes);
-      if (st) return st;
       EmuGemm g2;                                                 // M_RR -= L M_JR
       g2.oa = {0, 0}; g2.ob = {0, 0}; g2.batch = 1;
       g2.mmax = g2.m = r; g2.nmax = g2.n = r; g2.kmax = g2.k = w;
       g2.A = Lp; g2.lda = n; g2.B = Up; g2.ldb = n; g2.C = M; g2.ldc = n;
       g2.S = S; g2.ar = -1; g2.br = 1;
-      st = run_emulated(h, g2, dinv_bytes);
+      ozk_status_t st;
+      if (!auto_S) {
+        g1.C = Lp; g1.ldc = n;                                    // in place: both operands split first
+        st = run_emulated(h, g1, off_gemm);
+        if (!st) st = run_emulated(h, g2, off_gemm);
+      } else {
+        // the selector may recompute a product at S = 10, so L goes to the scratch (its operand
+        // M_RJ stays intact) and is copied over M_RJ afterwards
+        g1.C = Ltmp; g1.ldc = r;
+        st = zgemm_auto(h, g1, off_gemm);
+        if (!st)
+          st = cuda_check(cudaMemcpy2DAsync(Lp, sizeof(double2) * n, Ltmp, sizeof(double2) * r, sizeof(double2) * r,
+                                            w, cudaMemcpyDeviceToDevice, h->stream),
+                          "copy L panel");
+        if (!st) st = zgemm_auto(h, g2, off_gemm);
+      }
       if (st) return st;
     } else {
       // binary64 DMMA baseline: L = M_RJ Dinv into the scratch, copy back, then update
-      double2* Ltmp = reinterpret_cast<double2*>(static_cast<uint8_t*>(h->ws) + dinv_bytes);
       DmmaParams d1{};
       d1.m = r; d1.n = w; d1.k = w; d1.A = Lp; d1.lda = n; d1.B = Dinv; d1.ldb = w;
       d1.C = Ltmp; d1.ldc = r; d1.ar = 1; d1.br = 0;
@@ -1809,25 +1856,33 @@ static __device__ int g_noalloc_status;
 
 namespace {
 constexpr int kMaxDevices = 64;
-void* g_noalloc_ptr[kMaxDevices] = {};
-int* g_noalloc_status_ptr[kMaxDevices] = {};
+struct NoallocAddr { void* scratch; int* status; };
+std::atomic<const NoallocAddr*> g_noalloc_addr[kMaxDevices] = {};
+std::mutex g_noalloc_mu;
 
 // Device address of the static scratch for the current device, looked up once per device
-// (the name is only a host-side stand-in for the device symbol).
+// (the name is only a host-side stand-in for the device symbol).  Host threads that make their
+// first call at the same time serialise on a mutex; later calls read the published addresses
+// without locking.
 ozk_status_t noalloc_setup(int dev, void** scratch, int** status) {
   if (dev < 0 || dev >= kMaxDevices) return set_error(OZK_ERR_ARG, "device index out of range for the static scratch");
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    void* s = nullptr;
-    ozk_status_t st = cuda_check(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress(scratch)");
-    if (st) return st;
-    st = cuda_check(cudaGetSymbolAddress(&s, g_noalloc_status), "cudaGetSymbolAddress(status)");
-    if (st) return st;
-    g_noalloc_ptr[dev] = p;
-    g_noalloc_status_ptr[dev] = static_cast<int*>(s);
+  const NoallocAddr* a = g_noalloc_addr[dev].load(std::memory_order_acquire);
+  if (!a) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    a = g_noalloc_addr[dev].load(std::memory_order_relaxed);
+    if (!a) {
+      void* p = nullptr;
+      void* s = nullptr;
+      ozk_status_t st = cuda_check(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress(scratch)");
+      if (st) return st;
+      st = cuda_check(cudaGetSymbolAddress(&s, g_noalloc_status), "cudaGetSymbolAddress(status)");
+      if (st) return st;
+      a = new NoallocAddr{p, static_cast<int*>(s)};      // kept until the process exits
+      g_noalloc_addr[dev].store(a, std::memory_order_release);
+    }
   }
-  *scratch = g_noalloc_ptr[dev];
-  *status = g_noalloc_status_ptr[dev];
+  *scratch = a->scratch;
+  *status = a->status;
   return OZK_OK;
 }
 }  // namespace

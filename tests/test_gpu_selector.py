@@ -283,6 +283,47 @@ def test_batched_solve_with_selected_S(ozk_mod):
     h.close()
 
 
+def test_single_solve_S_rule(ozk_mod):
+    """kkr_tau00 follows the ABI's slice-count rule: S = 0 runs every GEMM of the solve through
+    the selector (its choice and residual check per GEMM; here a network that always picks S = 6
+    and products that pass the check, so bit for bit the S = 6 solve, with ozk_selector_last
+    updated), S < 0 runs every GEMM as a binary64 DMMA GEMM (bit for bit the batched DMMA form)."""
+    import torch
+    from oracle import kkr
+    h = ozk_mod.Handle()
+    p = np.zeros(sel.NPARAMS, dtype=np.float32)
+    p[sel.OFF_B3:] = [-3, -5, -8, -11, -14, -16, -16, -16]        # S = 6 at 1e-10, margin 0.3
+    h.selector_set_params(p)
+    h.selector_configure(tol=1e-10, margin=0.3)
+    t, G = synth.kkr_system(27, 16, 0.5 + 0.05j, atom=4)[:2]
+    M = kkr.kkr_build(t, G)
+
+    def single(S):
+        tau = ozk_mod.colmajor_cuda(np.zeros((16, 16), dtype=np.complex128))
+        ozk_mod.kkr_tau00(h, ozk_mod.colmajor_cuda(M), ozk_mod.colmajor_cuda(t[0]), tau, S=S, nb=64)
+        torch.cuda.synchronize()
+        return ozk_mod.to_numpy(tau)
+
+    auto = single(0)
+    seed0 = h.selector_last()["probe_seed"]
+    assert np.array_equal(single(0), auto)
+    info = h.selector_last()
+    assert info["S_selected"] == 6 and info["S_used"] == 6 and not info["fallback"]
+    assert info["residual_ok"]
+    # one selector call per GEMM: two per panel, 7 panels of (432 - 16) columns at nb = 64
+    assert info["probe_seed"] - seed0 == 14
+    assert np.array_equal(auto, single(6))
+    dm = single(-1)
+    Ms = [ozk_mod.colmajor_cuda(M)]
+    taus = [ozk_mod.colmajor_cuda(np.zeros((16, 16), dtype=np.complex128))]
+    ozk_mod.kkr_tau00_batched(h, Ms, [ozk_mod.colmajor_cuda(t[0])], taus, S=-1, nb=64)
+    assert np.array_equal(dm, ozk_mod.to_numpy(taus[0]))
+    full = kkr.tau00_full(M, t[0])
+    assert kkr.rel_err(auto, full) <= 1e-10 and kkr.rel_err(dm, full) <= 1e-12
+    assert h.status() == 0
+    h.close()
+
+
 def test_trained_selector_gains_over_fixed_S(ozk_mod):
     """The committed trained parameters on instances of an unseen seed: every returned product
     meets the tolerance against the S = 12 reference, and the products cost far fewer slice

@@ -216,6 +216,27 @@ def test_dmma_within_binary64_bound(ozk_mod, handle):
     assert np.all(np.abs(got - X) <= 2 * gamma * (np.abs(A) @ np.abs(B)))
 
 
+def test_negative_S_is_the_dmma_gemm(ozk_mod, handle):
+    """One slice-count rule across the ABI: S < 0 runs the binary64 DMMA GEMM, in the single
+    call (bit for bit ozk_zgemm_dmma) and in the variable-size batch."""
+    A, B = rand_complex(70, 33, 21), rand_complex(33, 45, 22)
+    C0 = rand_complex(70, 45, 23)
+    C1, C2 = _dev(ozk_mod, C0), _dev(ozk_mod, C0)
+    ozk_mod.ozaki_zgemm(handle, _dev(ozk_mod, A), _dev(ozk_mod, B), C1, S=-1, alpha=-1.0, beta=1.0)
+    ozk_mod.ozk_zgemm_dmma(handle, _dev(ozk_mod, A), _dev(ozk_mod, B), C2, alpha=-1.0, beta=1.0)
+    assert np.array_equal(ozk_mod.to_numpy(C1), ozk_mod.to_numpy(C2))
+    shapes = [(17, 9, 30), (40, 21, 5), (3, 64, 64)]
+    As = [_dev(ozk_mod, rand_complex(m, k, 30 + i)) for i, (m, n, k) in enumerate(shapes)]
+    Bs = [_dev(ozk_mod, rand_complex(k, n, 40 + i)) for i, (m, n, k) in enumerate(shapes)]
+    Cs = [_dev(ozk_mod, np.zeros((m, n), dtype=np.complex128)) for m, n, k in shapes]
+    ozk_mod.ozaki_zgemm_vbatched(handle, As, Bs, Cs, S=-1)
+    for a, b, c in zip(As, Bs, Cs):
+        want = _dev(ozk_mod, np.zeros(tuple(c.shape), dtype=np.complex128))
+        ozk_mod.ozk_zgemm_dmma(handle, a, b, want)
+        assert np.array_equal(ozk_mod.to_numpy(c), ozk_mod.to_numpy(want))
+    assert handle.status() == 0
+
+
 def test_degenerate_calls(ozk_mod, handle):
     import torch
     A = _dev(ozk_mod, rand_complex(5, 4, 1))
@@ -225,9 +246,8 @@ def test_degenerate_calls(ozk_mod, handle):
     # alpha = 0: C = beta C
     ozk_mod.ozaki_zgemm(handle, A, B, C, S=4, alpha=0.0, beta=2.0)
     assert np.array_equal(ozk_mod.to_numpy(C), 2.0 * C0)
-    # S = 0 is the slice-count selector (tests/test_gpu_selector.py); negative and > 16 are invalid
-    with pytest.raises(ozk_mod.OzkError):
-        ozk_mod.ozaki_zgemm(handle, A, B, C, S=-1)
+    # S = 0 is the slice-count selector (tests/test_gpu_selector.py), S < 0 the binary64 DMMA
+    # GEMM (test_negative_S_is_the_dmma_gemm); above 16 is invalid
     with pytest.raises(ozk_mod.OzkError):
         ozk_mod.ozaki_zgemm(handle, A, B, C, S=17)
 
