@@ -114,6 +114,11 @@ ozk_status_t ozk_profile_begin(ozk_handle_t handle);
  * multiply-adds x 2 of all slice pairs, P_S 8 m n k; DMMA: 8 m n k) and algorithmic bytes. */
 ozk_status_t ozk_profile_end(ozk_handle_t handle, uint64_t* launches, double* ms, double* flops,
                              double* bytes);
+/* Per kind (OZK_KERNEL_KINDS entries), the bytes the kernels of the last ozk_profile_end window
+ * read and wrote in this library's storage layout, beside the algorithmic `bytes` of that call:
+ * the split's algorithmic figure counts int8 digits (2S bytes per left-operand element, 3S per
+ * right-operand element: Re, Im, -Im), while the fp16-held planes move 4S and 8S. */
+ozk_status_t ozk_profile_moved(ozk_handle_t handle, double* moved);
 
 /* ---- emulated ZGEMM (paper Sec. 2.2, Sec. 3.2) ------------------------------------ */
 

@@ -44,7 +44,8 @@ EXPORTS = ["ozk_create", "ozk_destroy", "ozk_set_stream", "ozk_get_status", "ozk
            "ozk_selector_get_params", "ozk_selector_load", "ozk_selector_save", "ozk_selector_configure",
            "ozk_selector_features", "ozk_selector_predict", "ozk_selector_train_step", "ozk_selector_gradient",
            "ozk_selector_last", "ozk_rel_diff", "kkr_build_m_shared", "kkr_tau00_autotune",
-           "kkr_build_m_shared_sizes", "kkr_contour_trace", "ozaki2_zgemm", "ozaki_ztrsm", "kkr_tau00_lu"]
+           "kkr_build_m_shared_sizes", "kkr_contour_trace", "ozaki2_zgemm", "ozaki_ztrsm", "kkr_tau00_lu",
+           "ozk_profile_moved"]
 KIND_NAMES = ["split", "slice_gemm", "gj", "build_m", "dmma", "other"]
 
 _lib = None
@@ -104,6 +105,7 @@ def lib():
         L.ozk_rel_diff.argtypes = [vp, i, i, vp, i, vp, i, dp]
         L.ozk_profile_begin.argtypes = [vp]
         L.ozk_profile_end.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), dp, dp, dp]
+        L.ozk_profile_moved.argtypes = [vp, dp]
         for name in EXPORTS:
             if name not in ("ozk_zgemm_workspace_size", "ozk_last_error", "ozk_launch_count"):
                 getattr(L, name).restype = ctypes.c_int
@@ -185,8 +187,10 @@ class Handle:
         n = (ctypes.c_uint64 * K)()
         ms, fl, by = (ctypes.c_double * K)(), (ctypes.c_double * K)(), (ctypes.c_double * K)()
         _check(lib().ozk_profile_end(self._h, n, ms, fl, by), "ozk_profile_end")
+        mv = (ctypes.c_double * K)()
+        _check(lib().ozk_profile_moved(self._h, mv), "ozk_profile_moved")
         return {KIND_NAMES[k]: {"launches": int(n[k]), "ms": float(ms[k]), "flops": float(fl[k]),
-                                "bytes": float(by[k])} for k in range(K)}
+                                "bytes": float(by[k]), "bytes_moved": float(mv[k])} for k in range(K)}
 
     # ---- slice-count selector
     def selector_init(self, seed: int = 1):

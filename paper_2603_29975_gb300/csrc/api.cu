@@ -73,7 +73,7 @@ using namespace ozk;
 
 // Per-kernel-kind launch profiler: CUDA events recorded on the handle's stream around each
 // launch while enabled, with the algorithmic flops and bytes of that launch.
-struct ProfRec { int kind; cudaEvent_t a, b; double flops, bytes; };
+struct ProfRec { int kind; cudaEvent_t a, b; double flops, bytes, moved; };
 
 struct ozk_context {
   int device = 0;
@@ -83,6 +83,7 @@ struct ozk_context {
   size_t ws_bytes = 0;
   bool prof = false;
   std::vector<ProfRec> recs;
+  double prof_moved[OZK_KERNEL_KINDS] = {};    // bytes moved per kind at the last ozk_profile_end
   std::vector<cudaEvent_t> pool;
   size_t pool_used = 0;
   // device copies of the host size lists of batched calls, kept by content for the life of
@@ -124,17 +125,19 @@ cudaEvent_t prof_event(ozk_context* h) {
 // RAII scope: records a start event before and a stop event after the launches in its body.
 // Launches enqueued while the stream is being captured are not timed (they run later, as graph
 // nodes).
+// `bytes` is the launch's algorithmic byte count; `moved` (negative: the same) the bytes its
+// kernels read and write in this library's storage layout.
 struct Prof {
-  ozk_context* h; int kind; double flops, bytes; cudaStream_t st; cudaEvent_t a = nullptr; bool on = false;
-  Prof(ozk_context* hh, int k, double f, double by, cudaStream_t s = nullptr)
-      : h(hh), kind(k), flops(f), bytes(by), st(s ? s : hh->stream) {
+  ozk_context* h; int kind; double flops, bytes, moved; cudaStream_t st; cudaEvent_t a = nullptr; bool on = false;
+  Prof(ozk_context* hh, int k, double f, double by, cudaStream_t s = nullptr, double mv = -1.0)
+      : h(hh), kind(k), flops(f), bytes(by), moved(mv < 0 ? by : mv), st(s ? s : hh->stream) {
     if (h->prof && !capturing(st)) { on = true; a = prof_event(h); cudaEventRecord(a, st); }
   }
   ~Prof() {
     if (on) {
       cudaEvent_t b = prof_event(h);
       cudaEventRecord(b, st);
-      h->recs.push_back({kind, a, b, flops, bytes});
+      h->recs.push_back({kind, a, b, flops, bytes, moved});
     }
   }
 };
@@ -323,10 +326,11 @@ ozk_status_t run_emulated(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0
   else { sq.X = g.tB; sq.ld = g.tldb; sq.rows = g.tn; sq.kdim = g.tk; }
   const bool split_a = (g.split_sides & 1) != 0, split_b = (g.split_sides & 2) != 0;
   if (split_a || split_b) {
-    // algorithmic bytes: read 16 per complex element, write S x 2 fp16 (left operand) or S x 4
-    // fp16 (right operand, two stacked rows per column)
-    Prof pr(h, OZK_KIND_SPLIT, 0.0, (split_a ? smk * (16.0 + 4.0 * S) : 0.0) + (split_b ? snk * (16.0 + 8.0 * S) : 0.0),
-            stream);
+    // algorithmic bytes (int8 digits): read 16 per complex element, write 2S (left operand: Re,
+    // Im) or 3S (right operand: Re, Im, -Im); moved: the fp16 planes written here, S x 2 x 2
+    // (left) or S x 4 x 2 (right, two stacked rows per column)
+    Prof pr(h, OZK_KIND_SPLIT, 0.0, (split_a ? smk * (16.0 + 2.0 * S) : 0.0) + (split_b ? snk * (16.0 + 3.0 * S) : 0.0),
+            stream, (split_a ? smk * (16.0 + 4.0 * S) : 0.0) + (split_b ? snk * (16.0 + 8.0 * S) : 0.0));
     if (diag) {
       if (split_a) launch_residue_split(sp, *g.oz2, g.mmax, g.batch, stream);
       if (split_b) launch_residue_split(sq, *g.oz2, g.nmax, g.batch, stream);
@@ -1801,7 +1805,7 @@ ozk_status_t ozk_profile_end(ozk_handle_t h, uint64_t* launches, double* ms, dou
   h->prof = false;
   ozk_status_t st = cuda_check(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
   if (st) return st;
-  for (int k = 0; k < OZK_KERNEL_KINDS; ++k) { launches[k] = 0; ms[k] = 0; flops[k] = 0; bytes[k] = 0; }
+  for (int k = 0; k < OZK_KERNEL_KINDS; ++k) { launches[k] = 0; ms[k] = 0; flops[k] = 0; bytes[k] = 0; h->prof_moved[k] = 0; }
   for (const ProfRec& r : h->recs) {
     float t = 0.f;
     st = cuda_check(cudaEventElapsedTime(&t, r.a, r.b), "cudaEventElapsedTime");
@@ -1810,8 +1814,15 @@ ozk_status_t ozk_profile_end(ozk_handle_t h, uint64_t* launches, double* ms, dou
     ms[r.kind] += t;
     flops[r.kind] += r.flops;
     bytes[r.kind] += r.bytes;
+    h->prof_moved[r.kind] += r.moved;
   }
   h->recs.clear();
+  return OZK_OK;
+}
+
+ozk_status_t ozk_profile_moved(ozk_handle_t h, double* moved) {
+  if (!h || !moved) return set_error(OZK_ERR_ARG, "null argument");
+  for (int k = 0; k < OZK_KERNEL_KINDS; ++k) moved[k] = h->prof_moved[k];
   return OZK_OK;
 }
 

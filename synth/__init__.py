@@ -132,27 +132,58 @@ def kkr_system(L: int, b: int, E: complex, seed: int = 20260331, atom: int = 0,
     The stream numbers separate t and G draws and the atom index, so that atoms of a
     batch get independent matrices from one seed.
     """
-    n = L * b
     pos = bcc_sites(L)
-    st = 4 * atom
     t = kkr_t(L, b, seed=seed, atom=atom)
-    # G
+    G = _structure_G(_random_R(L, b, seed, atom), pos, t, E, max_norm)
+    return t, G, pos
+
+
+def kkr_contour_G(L: int, b: int, energies, seed: int = 20260331, atom: int = 0, max_norm: float = 0.9,
+                  workers: int = 1):
+    """G at each energy of ``energies``, element for element what ``kkr_system(L, b, E, seed,
+    atom)[1]`` returns, with the random block factors R drawn once for all energies (the
+    energy enters only through exp(i k r) and the rescaling).  A generator of n x n arrays in
+    the order of ``energies``; ``workers`` > 1 computes them on that many threads."""
+    pos = bcc_sites(L)
+    t = kkr_t(L, b, seed=seed, atom=atom)
+    R = _random_R(L, b, seed, atom)
+    if workers <= 1:
+        for E in energies:
+            yield _structure_G(R, pos, t, E, max_norm)
+        return
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(workers) as ex:
+        yield from ex.map(lambda E: _structure_G(R, pos, t, E, max_norm), list(energies))
+
+
+def _random_R(L: int, b: int, seed: int, atom: int) -> np.ndarray:
+    """R_ij entries (U(-1, 1) + i U(-1, 1)) / sqrt(b) of the structure-constant stand-in."""
+    n = L * b
+    st = 4 * atom
     idx = np.arange(n * n, dtype=np.uint64)
     Rr = 2.0 * uniform(seed, st + 2, idx) - 1.0
     Ri = 2.0 * uniform(seed, st + 3, idx) - 1.0
-    G = ((Rr + 1j * Ri) / math.sqrt(b)).reshape(n, n)
+    return ((Rr + 1j * Ri) / math.sqrt(b)).reshape(n, n)
+
+
+def _structure_G(R: np.ndarray, pos: np.ndarray, t: np.ndarray, E: complex, max_norm: float) -> np.ndarray:
+    """G_ij = R_ij exp(-r_ij / 1.5) exp(i k r_ij) (zero diagonal blocks), rescaled so that the
+    power-iteration estimate of ||t G||_2 is at most max_norm."""
+    L = pos.shape[0]
+    b = R.shape[0] // L
     d = np.sqrt(((pos[:, None, :] - pos[None, :, :]) ** 2).sum(-1))      # L x L
     kk = np.sqrt(complex(E))
     with np.errstate(divide="ignore", invalid="ignore"):
         f = np.exp(-d / 1.5) * np.exp(1j * kk * d)
     f[np.arange(L), np.arange(L)] = 0.0
-    G = G * np.kron(f, np.ones((b, b)))
+    # the site factor f_IJ multiplies every element of block (I, J)
+    G = (R.reshape(L, b, L, b) * f[:, None, :, None]).reshape(L * b, L * b)
     # power-iteration estimate of ||t G||_2, then rescale G
     tG = block_diag_times(t, G)
     nrm = _norm2_estimate(tG)
     if nrm > max_norm:
         G *= max_norm / nrm
-    return t, G, pos
+    return G
 
 
 def kkr_t(L: int, b: int, seed: int = 20260331, atom: int = 0) -> np.ndarray:
@@ -176,7 +207,7 @@ def _norm2_estimate(X: np.ndarray, iters: int = 30) -> float:
     s = 0.0
     for _ in range(iters):
         w = X @ v
-        v = X.conj().T @ w
+        v = np.dot(w.conj(), X).conj()                 # X^H w without a conjugated copy of X
         s = np.linalg.norm(v)
         if s == 0:
             return 0.0

@@ -83,6 +83,6 @@ def test_reference_arm_prints_one_contract_line():
     assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "tau00 solves/s"
     assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 1
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
-    assert d["cpu_baseline"]["cores"] >= 1 and "S=5" in d["cpu_baseline"]["sample"]
+    assert d["cpu_baseline"]["cores"] >= 1 and "S=7" in d["cpu_baseline"]["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert "workload" in d["config"]

@@ -342,3 +342,47 @@ def test_config4_full_size_against_binary64_solve(ozk_mod, handle):
         torch.cuda.synchronize()
         assert handle.status() == 0
         assert kkr.rel_err(ozk_mod.to_numpy(tau), ref) <= 1e-10
+
+
+def test_config3_full_size_sampled_atoms(ozk_mod, handle):
+    """The timed workload at full size: 256 atoms with LIZ sizes drawn from 27..169 sites
+    (n = 448..2704, b = 16) at three of the 32 contour energies, each energy with its own G.  M
+    of every atom is built by the shared-G emulated block-row GEMMs and all 256 tau_00 are solved
+    in one batched call at S = 7 with the autotuned panel width (the launch configuration the
+    benchmark times).  For the smallest and the largest atom at each energy: every block row of
+    M bit for bit against the oracle's emulated block-row update, tau_00 against the oracle's
+    block LU of the same M (only the binary64 pivot inverses round differently) and within
+    1e-10 of a binary64 library solve of the binary64 M."""
+    import torch
+    b, S, natoms = 16, 7, 256
+    Ls = [int(v) for v in synth.liz_sizes(natoms)]
+    ns = [L * b for L in Ls]
+    E, _ = synth.contour(32)
+    zs = [0, 16, 31]
+    nb, _ = ozk_mod.kkr_tau00_autotune(handle, ns, b, S=S)
+    ts = [synth.kkr_t(L, b, atom=a) for a, L in enumerate(Ls)]
+    tdev = [_tblocks(ozk_mod, t) for t in ts]
+    Ms = [torch.empty((n, n), dtype=torch.complex128, device="cuda") for n in ns]
+    taus = [torch.zeros((b, b), dtype=torch.complex128, device="cuda") for _ in ns]
+    ptr = lambda xs: torch.tensor([x.data_ptr() for x in xs], dtype=torch.int64, device="cuda")
+    pt, pm, ptau = ptr(tdev), ptr(Ms), ptr(taus)
+    sample = [int(np.argmin(Ls)), int(np.argmax(Ls))]
+    for z, G in zip(zs, synth.kkr_contour_G(169, b, [complex(E[z]) for z in zs], workers=3)):
+        Gd = ozk_mod.colmajor_cuda(G)
+        ozk_mod.kkr_build_m_shared_sizes_ptrs(handle, Ls, b, pt, Gd, pm, S=S)
+        torch.cuda.synchronize()
+        M_gpu = {a: Ms[a].cpu().numpy().T.copy() for a in sample}
+        ozk_mod.kkr_tau00_batched_ptrs(handle, ns, b, pm, pt, ptau, S=S, nb=nb)
+        torch.cuda.synchronize()
+        assert handle.status() == 0
+        for a in sample:
+            n = ns[a]
+            for i in range(Ls[a]):
+                rows = slice(i * b, (i + 1) * b)
+                eye = np.zeros((b, n), dtype=np.complex128)
+                eye[:, rows] = np.eye(b)
+                assert np.array_equal(M_gpu[a][rows], co.zgemm_lu(eye, ts[a][i], G[rows, :n], S)), (z, a, i)
+            got = taus[a].cpu().numpy().T
+            assert kkr.rel_err(got, co.tau00_block(M_gpu[a], ts[a][0], nb, S=S)) < 1e-13, (z, a)
+            ref = kkr.tau00_lapack(kkr.kkr_build(ts[a], G[:n, :n]), ts[a][0])
+            assert kkr.rel_err(got, ref) <= 1e-10, (z, a)

@@ -161,3 +161,13 @@ def test_contour_trace_of_a_polynomial_is_exact():
     th0 = np.arcsin(0.005)
     za, zb = -0.3 + np.exp(1j * (np.pi - th0)), -0.3 + np.exp(1j * th0)
     assert abs(integral - b * (zb ** 2 - za ** 2) / 2) < 1e-11
+
+
+def test_contour_G_equals_the_single_energy_recipe():
+    """kkr_contour_G draws the random block factors once for all energies: each G it yields is
+    element for element the G of kkr_system at that energy (same seed and atom)."""
+    E, _ = synth.contour(32)
+    zs = [0, 7, 31]
+    got = list(synth.kkr_contour_G(15, 16, [complex(E[z]) for z in zs], atom=2, workers=2))
+    for z, G in zip(zs, got):
+        assert np.array_equal(G, synth.kkr_system(15, 16, complex(E[z]), atom=2)[1])
