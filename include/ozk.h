@@ -278,6 +278,16 @@ ozk_status_t ozk_group_sums_debug(ozk_handle_t handle, char transa, char transb,
                                   int k, const void* A, int lda, const void* B, int ldb, int S,
                                   int pair_mode, int64_t* groups);
 
+/* Failure-path hook of the bounded device waits (the paper has no counterpart; every wait of
+ * the tensor-core kernel is bounded so that a lost arrival cannot hang the GPU).  The next
+ * slice-GEMM launch enqueued on this handle first makes one thread of every CTA wait on a
+ * barrier that no thread ever arrives at, with a budget of `cycles` SM clock cycles, before the
+ * CTA has issued any TMA copy or MMA.  The wait gives up, sets OZK_ERR_TIMEOUT in the device
+ * status word, and the CTA skips its tiles, releases its tensor memory and exits: that GEMM
+ * leaves its output unwritten.  The launch after it runs normally.  cycles <= 0 clears a pending
+ * request. */
+ozk_status_t ozk_debug_stall_next_gemm(ozk_handle_t handle, long long cycles);
+
 /* ---- KKR tau_00 (paper Sec. 3.2) ----------------------------------------------------- */
 
 /* M = I - t G for a LIZ of L sites with b x b blocks (n = L b).

@@ -16,6 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libozk.so")
 
 OZK_OK = 0
+OZK_ERR_TIMEOUT = 4
 OZK_PAIRS_TRI = 0
 OZK_PAIRS_FULL = 1
 OZK_SEL_FEATURES = 16
@@ -45,7 +46,7 @@ EXPORTS = ["ozk_create", "ozk_destroy", "ozk_set_stream", "ozk_get_status", "ozk
            "ozk_selector_features", "ozk_selector_predict", "ozk_selector_train_step", "ozk_selector_gradient",
            "ozk_selector_last", "ozk_rel_diff", "kkr_build_m_shared", "kkr_tau00_autotune",
            "kkr_build_m_shared_sizes", "kkr_contour_trace", "ozaki2_zgemm", "ozaki_ztrsm", "kkr_tau00_lu",
-           "ozk_profile_moved"]
+           "ozk_profile_moved", "ozk_debug_stall_next_gemm"]
 KIND_NAMES = ["split", "slice_gemm", "gj", "build_m", "dmma", "other"]
 
 _lib = None
@@ -106,6 +107,7 @@ def lib():
         L.ozk_profile_begin.argtypes = [vp]
         L.ozk_profile_end.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), dp, dp, dp]
         L.ozk_profile_moved.argtypes = [vp, dp]
+        L.ozk_debug_stall_next_gemm.argtypes = [vp, ctypes.c_longlong]
         for name in EXPORTS:
             if name not in ("ozk_zgemm_workspace_size", "ozk_last_error", "ozk_launch_count"):
                 getattr(L, name).restype = ctypes.c_int
@@ -177,6 +179,10 @@ class Handle:
 
     def reserve(self, nbytes: int):
         _check(lib().ozk_reserve(self._h, nbytes), "ozk_reserve")
+
+    def debug_stall_next_gemm(self, cycles: int):
+        """Test hook: the next slice-GEMM launch's bounded waits run out after `cycles` SM cycles."""
+        _check(lib().ozk_debug_stall_next_gemm(self._h, int(cycles)), "ozk_debug_stall_next_gemm")
 
     def profile_begin(self):
         _check(lib().ozk_profile_begin(self._h), "ozk_profile_begin")

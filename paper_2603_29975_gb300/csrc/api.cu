@@ -105,6 +105,7 @@ struct ozk_context {
   // and the events that fork it from and join it to the handle's stream
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  long long stall_next = 0;                 // ozk_debug_stall_next_gemm: budget for the next launch
 };
 
 namespace {
@@ -379,6 +380,8 @@ ozk_status_t run_emulated(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0
   const int gmax = (g.pair_mode == OZK_PAIRS_FULL) ? 2 * S : S + 1;
   gp.base_exp = -2 * (8 * S - 1) + 8 * (2 * S - gmax);
   gp.diag_pairs = diag ? 1 : 0;
+  gp.stall_cycles = h->stall_next;
+  h->stall_next = 0;
   gp.resid = g.resid; gp.ldres = g.ldres;
   gp.ar = g.ar; gp.ai = g.ai; gp.br = g.br; gp.bi = g.bi;
   if (g.mode >= 0) gp.mode = g.mode;
@@ -1817,6 +1820,12 @@ ozk_status_t ozk_profile_end(ozk_handle_t h, uint64_t* launches, double* ms, dou
     h->prof_moved[r.kind] += r.moved;
   }
   h->recs.clear();
+  return OZK_OK;
+}
+
+ozk_status_t ozk_debug_stall_next_gemm(ozk_handle_t h, long long cycles) {
+  if (!h) return set_error(OZK_ERR_ARG, "null handle");
+  h->stall_next = cycles > 0 ? cycles : 0;
   return OZK_OK;
 }
 

@@ -102,6 +102,9 @@ struct GemmParams {
   // EPI_RESIDUES: group g of problem z, row r, stacked column c at resid[((z G + g) m1 + r) ldres + c]
   int* resid; long long ldres;
   int diag_pairs;                // 1: the pair list is not the tri/full set (runtime issue)
+  // test hook of the bounded waits (> 0): before any copy or MMA, every CTA waits on a barrier
+  // that no thread arrives at with this budget of SM cycles, gives up and exits
+  long long stall_cycles;
   uint8_t ps[MAX_PAIRS], pt[MAX_PAIRS], pg[MAX_PAIRS], pfirst[MAX_PAIRS];
 };
 void launch_slice_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const GemmParams& p, int BN,

@@ -146,13 +146,46 @@ __device__ __forceinline__ void issue_kblock_stacked(uint32_t tmem, uint32_t a_l
   }
 }
 
+// A chunk's first K-block with the triangular pair set: slice s = 1 pairs with every t = 1..S,
+// so it is the first writer of every group g = 1 + t.  Once the epilogue has released all the
+// accumulators of the previous chunk, A_1 x [B_1 .. B_S]^T overwrites every group in one
+// stacked MMA (accumulate = 0) and the later A slices accumulate onto it, as in the later
+// K-blocks: S MMAs (plus the N = 256 splits) instead of one per pair.
+template <int S, int BN>
+__device__ __forceinline__ bool issue_kblock_first_stacked(uint32_t tmem, uint32_t a_lo, uint32_t b_lo, uint32_t hi,
+                                                           uint64_t* acc_empty, uint32_t rel_parity, bool wait_release,
+                                                           int* status, volatile int* abort_flag) {
+  if (wait_release) {
+#pragma unroll
+    for (int g = 0; g < S; ++g)
+      if (!mbar_wait(&acc_empty[g], rel_parity, status, abort_flag)) return false;
+    tc_fence_after();
+  }
+#pragma unroll
+  for (int s = 1; s <= S; ++s) {
+    constexpr int NMAX = 256;
+    const int ncols = (S + 1 - s) * BN;
+#pragma unroll
+    for (int c0 = 0; c0 < ncols; c0 += NMAX) {
+      const int n = ncols - c0 < NMAX ? ncols - c0 : NMAX;
+      mma_f16_lo(tmem + (s - 1) * BN + c0, a_lo + (s - 1) * (GEMM_BM * 32 / 16), b_lo + c0 * (32 / 16), hi,
+                 idesc_f16_f32(GEMM_BM, n), s > 1 ? 1u : 0u);
+    }
+  }
+  return true;
+}
+
 template <int S, bool FULLSET, int BN>
 __device__ __forceinline__ bool issue_kblock_any(bool firstkb, uint32_t tmem, uint32_t a_lo, uint32_t b_lo, uint32_t hi,
                                                  uint32_t idesc, uint64_t* acc_empty, uint32_t rel_parity,
                                                  bool wait_release, int* status, volatile int* abort_flag) {
-  if (firstkb)
+  if (firstkb) {
+    if constexpr (!FULLSET)
+      return issue_kblock_first_stacked<S, BN>(tmem, a_lo, b_lo, hi, acc_empty, rel_parity, wait_release, status,
+                                               abort_flag);
     return issue_kblock<S, FULLSET, BN, true>(tmem, a_lo, b_lo, hi, idesc, acc_empty, rel_parity, wait_release, status,
                                               abort_flag);
+  }
   issue_kblock_stacked<S, FULLSET, BN>(tmem, a_lo, b_lo, hi);
   return true;
 }
@@ -564,7 +597,8 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   uint64_t* acc_full = empty + nstage;
   uint64_t* acc_empty = acc_full + 1;          // one per group accumulator
   uint64_t* done_bar = acc_empty + 16;
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(done_bar + 1);
+  uint64_t* stall_bar = done_bar + 1;          // the test hook's barrier: no thread arrives at it
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(stall_bar + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
 
   const int warp = threadIdx.x >> 5;
@@ -574,6 +608,7 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     mbar_init(acc_full, 1);
     for (int i = 0; i < 16; ++i) mbar_init(&acc_empty[i], GEMM_EPI_WARPS);
     mbar_init(done_bar, 1);
+    mbar_init(stall_bar, 1);
     *abort_flag = 0;
     mbar_fence_init();
     prefetch_tensormap(&tmA);
@@ -584,6 +619,13 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
+  if (p.stall_cycles > 0) {
+    // failure-path test: one thread's bounded wait runs out (OZK_ERR_TIMEOUT, abort flag set)
+    // before any TMA copy or MMA has been issued; every role then skips its loop
+    if (threadIdx.x == 32) mbar_wait(stall_bar, 0, p.status, abort_flag, p.stall_cycles);
+    __syncthreads();
+  }
+  const bool stalled = *abort_flag != 0;
 
   const int nkb = p.kblocks;
   const int nchunks = (nkb + p.chunk_kb - 1) / p.chunk_kb;
@@ -620,7 +662,7 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     if (lane == 0) {
       // ---------------- TMA producer: one ring of stages across all tiles
       uint32_t kbc = 0;
-      bool ok = true;
+      bool ok = !stalled;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         int z, m0, n0, m_z, n2_z;
         if (!tile_of(t, z, m0, n0, m_z, n2_z)) continue;
@@ -653,7 +695,7 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       // the next tile overlap the reconstruction of the current one.
       const uint32_t idesc = idesc_f16_f32(GEMM_BM, BN);
       uint32_t kbc = 0, cc = 0;
-      bool ok = true;
+      bool ok = !stalled;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         int z, m0, n0, m_z, n2_z;
         if (!tile_of(t, z, m0, n0, m_z, n2_z)) continue;
@@ -702,7 +744,7 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     const uint32_t magic_mask = magic ? 0xFFFFFFFFu : static_cast<uint32_t>(p.magic_mask);
     const bool horner = nchunks == 1;
     uint32_t cc = 0;
-    bool ok = true;
+    bool ok = !stalled;
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       int z, m0, n0, m_z, n2_z;
       if (!tile_of(t, z, m0, n0, m_z, n2_z)) continue;
@@ -853,7 +895,7 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
 
 size_t gemm_smem_bytes(int S, int BN, int nstage) {
   const size_t stage = static_cast<size_t>(S) * (GEMM_BM + BN) * 32;
-  return 1024 + nstage * stage + (2 * nstage + 18) * 8 + 16;
+  return 1024 + nstage * stage + (2 * nstage + 19) * 8 + 16;
 }
 
 static int num_sms() {
@@ -878,10 +920,15 @@ void launch_slice_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const GemmP
   const long long ntiles = static_cast<long long>(p.tpp) * batch;
   const int grid = static_cast<int>(std::min<long long>(ntiles, num_sms()));
   const size_t smem = gemm_smem_bytes(p.S, BN, p.nstage);
-  if (BN == 64 && p.S == 5 && !p.fullset && !p.diag_pairs) {
-    // the slice count the selector picks for the KKR workloads: a compact instance
+  const bool tri = BN == 64 && !p.fullset && !p.diag_pairs;
+  if (tri && p.S == 5) {
+    // the slice count the selector picks for most KKR GEMMs: a compact instance
     cudaFuncSetAttribute(slice_gemm_kernel<64, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     slice_gemm_kernel<64, 5><<<grid, GEMM_THREADS, smem, st>>>(ta, tb, p);
+  } else if (tri && p.S == 7) {
+    // 55 bits, the precision of the batched contour workload
+    cudaFuncSetAttribute(slice_gemm_kernel<64, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    slice_gemm_kernel<64, 7><<<grid, GEMM_THREADS, smem, st>>>(ta, tb, p);
   } else if (BN == 64) {
     cudaFuncSetAttribute(slice_gemm_kernel<64, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     slice_gemm_kernel<64, 0><<<grid, GEMM_THREADS, smem, st>>>(ta, tb, p);
