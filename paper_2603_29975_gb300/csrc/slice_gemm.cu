@@ -222,9 +222,21 @@ __device__ __forceinline__ bool issue_dispatch(int S, bool fullset, bool firstkb
       switch (S) { case 1: OZK_ISSUE(1, true); case 2: OZK_ISSUE(2, true); case 3: OZK_ISSUE(3, true);
                    default: OZK_ISSUE(4, true); }
     }
+  } else {
+    // 32-column tiles: the triangular sets of S = 9 (the selector's largest regular choice)
+    // and S = 10 (its fallback); the caller sends every other case to the runtime schedule
+    if (S == 9) OZK_ISSUE(9, false);
+    OZK_ISSUE(10, false);
   }
 #undef OZK_ISSUE
-  return false;
+}
+
+// the compile-time schedules of issue_dispatch cover this launch
+template <int BN>
+__device__ __forceinline__ bool dispatch_covers(const GemmParams& p, int S) {
+  if (p.diag_pairs) return false;
+  if constexpr (BN == 64) return true;
+  return !p.fullset && (S == 9 || S == 10);
 }
 
 struct EpiCtx {
@@ -713,7 +725,7 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
               ok = issue_kblock_any<SF, false, BN>(kb == kb0, tmem, static_cast<uint32_t>(da), static_cast<uint32_t>(db),
                                                    static_cast<uint32_t>(da >> 32), idesc, acc_empty, (cc - 1) & 1,
                                                    cc > 0, p.status, abort_flag);
-            else if (BN == 64 && !p.diag_pairs)
+            else if (dispatch_covers<BN>(p, S))
               ok = issue_dispatch<BN>(S, p.fullset != 0, kb == kb0, tmem, static_cast<uint32_t>(da),
                                       static_cast<uint32_t>(db), static_cast<uint32_t>(da >> 32), idesc, acc_empty,
                                       (cc - 1) & 1, cc > 0, p.status, abort_flag);
