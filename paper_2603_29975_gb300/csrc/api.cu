@@ -370,11 +370,11 @@ ozk_status_t run_emulated(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0
       if (np[gi] > 0 && 16LL * np[gi] * P.chunk_kb <= 256) gp.magic_mask |= static_cast<int>(1u << gi);
   }
   {
-    // the 64-bit epilogue: one exactness chunk and |sum| < 2^(ceil(log2 terms) + 14 + 8 (G - 1) + 1)
-    // <= 2^63, terms = the digit products one accumulator receives
+    // the 64-bit epilogue: |sum| < 2^(ceil(log2 terms) + 14 + 8 (G - 1) + 1) <= 2^63, terms = the
+    // digit products one group receives over all its exactness chunks
     const double terms = 16.0 * P.kblocks * P.maxpairs;
     const int bits = static_cast<int>(std::ceil(std::log2(terms))) + 14 + 8 * (P.G - 1) + 1;
-    gp.fit64 = (P.chunk_kb >= P.kblocks && P.G <= 5 && bits <= 63) ? 1 : 0;
+    gp.fit64 = (P.G <= 5 && bits <= 63) ? 1 : 0;
   }
   gp.fullset = g.pair_mode == OZK_PAIRS_FULL ? 1 : 0;
   const int gmax = (g.pair_mode == OZK_PAIRS_FULL) ? 2 * S : S + 1;

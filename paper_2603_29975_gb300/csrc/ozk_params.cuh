@@ -74,7 +74,7 @@ struct GemmParams {
   int base_exp;           // -2B + 8 (2S - g_max)
   int magic;              // 1: every accumulator stays below 2^22 (FP32 add-and-reinterpret conversion)
   int magic_mask;         // bit g: the accumulators of group g stay within 2^22 (same conversion)
-  int fit64;              // 1: every exact output sum fits in 64 bits (single chunk, G <= 5)
+  int fit64;              // 1: every exact output sum fits in 64 bits (G <= 5, all chunks)
   int ntx, nty, batch;    // tile grid (set by the launcher): column tiles, row tiles, problems
   int fullset;            // 1: all S x S pairs, 0: triangular s + t <= S + 1
   // skip box: outputs with row < skm and complex column < skn are neither computed (whole

@@ -32,34 +32,42 @@ constexpr int GEMM_EPI_WARPS = 16;
 constexpr int GEMM_THREADS = (2 + GEMM_EPI_WARPS) * 32;
 
 
-// RN-even of (hi 2^64 + lo) 2^E, the 128-bit two's-complement integer given as halves.
-// Normal results take the short path; subnormal or overflowing ones the general routine.
-__device__ __forceinline__ double round_hl(long long hi, unsigned long long lo, int E) {
-  const bool neg = hi < 0;
-  unsigned long long uh = static_cast<unsigned long long>(hi);
-  if (neg) {                                          // |value|
-    lo = ~lo + 1ull;
-    uh = ~uh + (lo == 0ull ? 1ull : 0ull);
+// RN-even of (H 2^S8 + L) 2^E for int64 H, L with |H| < 2^56 and |L| < 2^(S8 + 30), S8 <= 32,
+// through the int64 -> binary64 conversion (RN-even to 53 bits) of one 64-bit integer:
+// H' = H + floor(L / 2^S8) and Ll = L mod 2^S8 give the exact T = H' 2^S8 + Ll.  When T fits in
+// 62 bits it is converted as it is; otherwise T is shifted right by sh <= S8 bits (so that
+// 2^61 <= |T'| < 2^62) and the dropped bits of Ll are jammed into bit 0 of T' as a sticky bit:
+// T' then has more than two bits below the rounding position and no midpoint on its odd bit,
+// so its RN-even is that of T / 2^sh (round-to-odd argument).  The scaling by 2^(E + sh) is an
+// exponent-field addition while the result stays normal; other results take the general
+// 128-bit routine.
+template <int S8>
+__device__ __forceinline__ double round_hl_jam(long long H, long long L, int E) {
+  long long Hp = H, Ll = 0;
+  if constexpr (S8 > 0) {
+    Hp = H + (L >> S8);
+    Ll = L & ((1ll << S8) - 1);
   }
-  if ((uh | lo) == 0ull) return 0.0;
-  const int lz = uh ? __clzll(uh) : 64 + __clzll(lo);
-  unsigned long long M;
-  bool sticky;
-  if (lz >= 64) { M = lo << (lz - 64); sticky = false; }
-  else if (lz == 0) { M = uh; sticky = lo != 0ull; }
-  else { M = (uh << lz) | (lo >> (64 - lz)); sticky = (lo << lz) != 0ull; }
-  const int q = E + 64 - lz + 11;                     // ulp exponent of a normal 53-bit result
-  if (q < -1074 || q > 970) {
-    const unsigned __int128 mag = (static_cast<unsigned __int128>(uh) << 64) | lo;
-    const __int128 sv = neg ? -static_cast<__int128>(mag) : static_cast<__int128>(mag);
-    return round_scaled_dev(sv, E);
+  const unsigned long long mag = static_cast<unsigned long long>(Hp < 0 ? -Hp : Hp);
+  const int b = 64 - __clzll(mag);                        // bit length of |H'|
+  const int sh = max(0, b + S8 - 62);
+  long long T;
+  if constexpr (S8 > 0) {
+    T = static_cast<long long>(static_cast<unsigned long long>(Hp) << (S8 - sh)) + (Ll >> sh);
+    T |= (Ll & ((1ll << sh) - 1)) != 0 ? 1ll : 0ll;
+  } else {
+    T = Hp;
   }
-  unsigned long long keep = M >> 11;
-  const unsigned long long rem = M & 0x7FFull;
-  keep += ((rem > 0x400ull) || (rem == 0x400ull && (sticky || (keep & 1ull)))) ? 1ull : 0ull;
-  unsigned long long bits = (static_cast<unsigned long long>(q + 1074) << 52) + keep;
-  if (neg) bits |= 0x8000000000000000ull;
-  return __longlong_as_double(static_cast<long long>(bits));
+  const double d = __ll2double_rn(T);
+  const long long bits = __double_as_longlong(d);
+  const int ed = static_cast<int>((bits >> 52) & 0x7FF);
+  if (ed == 0) return d;                                    // T = 0
+  const int Et = E + sh;
+  if (ed + Et < 1 || ed + Et > 2046) {
+    const __int128 v = (static_cast<__int128>(H) << S8) + static_cast<__int128>(L);
+    return round_scaled_dev(v, E);
+  }
+  return __longlong_as_double(bits + (static_cast<long long>(Et) << 52));
 }
 
 // Exact FP32 integer accumulator value -> int32.  "magic": |v| < 2^22, one FP32 add puts the
@@ -155,12 +163,6 @@ template <int S, int BN>
 __device__ __forceinline__ bool issue_kblock_first_stacked(uint32_t tmem, uint32_t a_lo, uint32_t b_lo, uint32_t hi,
                                                            uint64_t* acc_empty, uint32_t rel_parity, bool wait_release,
                                                            int* status, volatile int* abort_flag) {
-  if (wait_release) {
-#pragma unroll
-    for (int g = 0; g < S; ++g)
-      if (!mbar_wait(&acc_empty[g], rel_parity, status, abort_flag)) return false;
-    tc_fence_after();
-  }
 #pragma unroll
   for (int s = 1; s <= S; ++s) {
     constexpr int NMAX = 256;
@@ -168,6 +170,14 @@ __device__ __forceinline__ bool issue_kblock_first_stacked(uint32_t tmem, uint32
 #pragma unroll
     for (int c0 = 0; c0 < ncols; c0 += NMAX) {
       const int n = ncols - c0 < NMAX ? ncols - c0 : NMAX;
+      if (s == 1 && wait_release) {
+        // the groups this MMA overwrites (TMEM columns [c0, c0 + n)): it starts as soon as the
+        // epilogue has released them, while the later groups are still being drained
+#pragma unroll
+        for (int g = c0 / BN; g < (c0 + n) / BN; ++g)
+          if (!mbar_wait(&acc_empty[g], rel_parity, status, abort_flag)) return false;
+        tc_fence_after();
+      }
       mma_f16_lo(tmem + (s - 1) * BN + c0, a_lo + (s - 1) * (GEMM_BM * 32 / 16), b_lo + c0 * (32 / 16), hi,
                  idesc_f16_f32(GEMM_BM, n), s > 1 ? 1u : 0u);
     }
@@ -285,16 +295,48 @@ __device__ __forceinline__ void prefetch_l2(const void* ptr) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<uint64_t>(ptr)));
 }
 
-// Epilogue of one 128 x 64 tile for a single exactness chunk and G <= 8 groups (compile-time):
-// the exact sum of the group values v_g (|v| <= 2^24) is H 2^(8 NL) + L with H = the first
-// NH = min(G, 4) groups and L = the rest, each accumulated by 32 x 32 -> 64-bit multiply-adds
-// with constant weights 2^24, 2^16, 2^8, 1 (|H|, |L| < 2^49).  A thread owns one row and 16
-// stacked columns (8 complex), handled in two halves of 8; the second half releases every
-// group accumulator to the next tile's MMAs.  C and the column exponents of a half are
-// loaded before its arithmetic.
+// Waits of the epilogue for the accumulators of one tile: its exactness chunks complete one
+// after the other on acc_full (chunk counter cc, running over the CTA's tiles).
+struct ChunkWait {
+  uint64_t* acc_full;
+  int nchunks;
+  uint32_t* cc;
+  int* status;
+  volatile int* abort_flag;
+  __device__ __forceinline__ bool next() {
+    if (!mbar_wait(acc_full, *cc & 1, status, abort_flag)) return false;
+    tc_fence_after();
+    ++*cc;
+    return true;
+  }
+};
+
+// Release every group accumulator of every chunk of a tile without reading it (a warp with no
+// output in the tile).
 template <int G>
-__device__ __forceinline__ void epilogue_fast(const GemmParams& p, const EpiCtx& x, uint64_t* acc_empty, bool magic,
-                                              int lane) {
+__device__ __forceinline__ bool release_unread(uint64_t* acc_empty, ChunkWait& cw, int lane) {
+  for (int c = 0; c < cw.nchunks; ++c) {
+    if (!cw.next()) return false;
+#pragma unroll
+    for (int gi = 0; gi < G; ++gi) {
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[gi]);
+    }
+  }
+  return true;
+}
+
+// Epilogue of one 128 x 64 tile for G <= 8 groups (compile-time) over the tile's exactness
+// chunks: the exact sum of the group values v_g (|v| <= 2^24 per chunk) is H 2^(8 NL) + L with
+// H = the first NH = min(G, 4) groups and L = the rest, each accumulated over the chunks by
+// 32 x 32 -> 64-bit multiply-adds with constant weights 2^24, 2^16, 2^8, 1 (|H|, |L| < 2^49 per
+// chunk).  A thread owns one row and 16 stacked columns (8 complex).  Each group accumulator is
+// released as soon as it is read, so the MMAs of the next chunk or tile start while the last
+// chunk is rounded and written.  Returns false if a wait gave up.
+template <int G>
+__device__ __forceinline__ bool epilogue_fast(const GemmParams& p, const EpiCtx& x, uint64_t* acc_empty, bool magic,
+                                              int lane, ChunkWait& cw) {
   constexpr int NH = G < 4 ? G : 4;
   constexpr int NL = G - NH;
   constexpr int S8 = 8 * NL;
@@ -303,47 +345,41 @@ __device__ __forceinline__ void epilogue_fast(const GemmParams& p, const EpiCtx&
   const int jc0 = (x.n0 + x.c0) / 2;                  // this thread's 8 complex columns
   const int jend = min(min(jc0 + 8, (x.n2_z + 1) / 2), x.jlim);
   const bool active = x.rowok && max(jc0, x.skip_n) < jend;
-  if (!__any_sync(0xffffffffu, active)) {
-    // nothing of this warp is written: release the accumulators unread
-#pragma unroll
-    for (int gi = 0; gi < G; ++gi) {
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&acc_empty[gi]);
-    }
-    return;
-  }
-  // C lines towards L2 now, consumed after the drain
-  if (needC && active) {
-#pragma unroll
-    for (int jj = 0; jj < 8; ++jj)
-      if (jc0 + jj < jend) prefetch_l2(x.Cz + x.crow + (jc0 + jj) * x.ldc);
-  }
+  if (!__any_sync(0xffffffffu, active)) return release_unread<G>(acc_empty, cw, lane);
   // phase A: drain -- fold every group of the 16 columns into H, L and release its
-  // accumulator at once, so the next tile's MMAs start while phase B runs
+  // accumulator at once, chunk after chunk
   long long H[16], L[16];
 #pragma unroll
   for (int j = 0; j < 16; ++j) { H[j] = 0; L[j] = 0; }
+  for (int c = 0; c < cw.nchunks; ++c) {
+    if (!cw.next()) return false;
+    if (c == cw.nchunks - 1 && needC && active) {
+      // C lines towards L2 now, consumed after the drain
 #pragma unroll
-  for (int gi = 0; gi < G; ++gi) {
-    uint32_t v[8], u[8];
-    tmem_ld8(x.tbase + gi * BN, v);
-    tmem_ld8(x.tbase + gi * BN + 8, u);
-    tmem_wait_ld();
-    tc_fence_before();
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&acc_empty[gi]);         // group gi may be overwritten now
-    const int w = gi < NH ? (1 << (8 * (NH - 1 - gi))) : (1 << (8 * (NL - 1 - (gi - NH))));
+      for (int jj = 0; jj < 8; ++jj)
+        if (jc0 + jj < jend) prefetch_l2(x.Cz + x.crow + (jc0 + jj) * x.ldc);
+    }
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const long long a = static_cast<long long>(acc_to_int(v[j], magic)) * w;
-      const long long b = static_cast<long long>(acc_to_int(u[j], magic)) * w;
-      if (gi < NH) { H[j] += a; H[j + 8] += b; } else { L[j] += a; L[j + 8] += b; }
+    for (int gi = 0; gi < G; ++gi) {
+      uint32_t v[8], u[8];
+      tmem_ld8(x.tbase + gi * BN, v);
+      tmem_ld8(x.tbase + gi * BN + 8, u);
+      tmem_wait_ld();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[gi]);         // group gi may be overwritten now
+      const int w = gi < NH ? (1 << (8 * (NH - 1 - gi))) : (1 << (8 * (NL - 1 - (gi - NH))));
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const long long a = static_cast<long long>(acc_to_int(v[j], magic)) * w;
+        const long long b = static_cast<long long>(acc_to_int(u[j], magic)) * w;
+        if (gi < NH) { H[j] += a; H[j + 8] += b; } else { L[j] += a; L[j + 8] += b; }
+      }
     }
   }
-  if (!active) return;
+  if (!active) return true;
   // phase B: round and write, the next column's loads issued one step ahead (C was sent
-  // towards L2 before the drain)
+  // towards L2 before the last drain)
   double2 cv = make_double2(0.0, 0.0);
   int fe = 0;
   auto load_col = [&](int jj, double2& c, int& f) {
@@ -363,14 +399,7 @@ __device__ __forceinline__ void epilogue_fast(const GemmParams& p, const EpiCtx&
       const int E = x.er + fe;
       double zz[2];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const long long Hh = H[2 * jj + h], Lh = L[2 * jj + h];
-        long long hi = S8 ? (Hh >> (64 - S8)) : (Hh >> 63);
-        const unsigned long long lo = static_cast<unsigned long long>(Hh) << S8;
-        const unsigned long long lo2 = lo + static_cast<unsigned long long>(Lh);
-        hi += (Lh >> 63) + (lo2 < lo ? 1 : 0);
-        zz[h] = round_hl(hi, lo2, E);
-      }
+      for (int h = 0; h < 2; ++h) zz[h] = round_hl_jam<S8>(H[2 * jj + h], L[2 * jj + h], E);
       double2* dst = x.Cz + x.crow + jc * x.ldc;
       if (p.mode == EPI_STORE) {
         if (p.ar == 1.0 && p.ai == 0.0) *dst = make_double2(zz[0], zz[1]);
@@ -388,6 +417,7 @@ __device__ __forceinline__ void epilogue_fast(const GemmParams& p, const EpiCtx&
     cv = cn;
     fe = fn;
   }
+  return true;
 }
 
 // Variant of epilogue_fast processing the 16 columns in two halves of 8: per half, the
@@ -395,8 +425,8 @@ __device__ __forceinline__ void epilogue_fast(const GemmParams& p, const EpiCtx&
 // group g is folded) and the half's C values are loaded before its drain; the accumulators are
 // released during the second half.
 template <int G>
-__device__ __forceinline__ void epilogue_halves(const GemmParams& p, const EpiCtx& x, uint64_t* acc_empty, bool magic,
-                                                int lane) {
+__device__ __forceinline__ bool epilogue_halves(const GemmParams& p, const EpiCtx& x, uint64_t* acc_empty, bool magic,
+                                                int lane, ChunkWait& cw) {
   constexpr int NH = G < 4 ? G : 4;
   constexpr int NL = G - NH;
   constexpr int S8 = 8 * NL;
@@ -405,15 +435,8 @@ __device__ __forceinline__ void epilogue_halves(const GemmParams& p, const EpiCt
   const int jc0 = (x.n0 + x.c0) / 2;
   const int jend = min(min(jc0 + 8, (x.n2_z + 1) / 2), x.jlim);
   const bool active = x.rowok && max(jc0, x.skip_n) < jend;
-  if (!__any_sync(0xffffffffu, active)) {
-#pragma unroll
-    for (int gi = 0; gi < G; ++gi) {
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&acc_empty[gi]);
-    }
-    return;
-  }
+  if (!__any_sync(0xffffffffu, active)) return release_unread<G>(acc_empty, cw, lane);
+  if (!cw.next()) return false;                      // one exactness chunk (at most two K-blocks)
 #pragma unroll
   for (int half = 0; half < 2; ++half) {
     const int jh = jc0 + 4 * half;                     // first complex column of this half
@@ -458,14 +481,7 @@ __device__ __forceinline__ void epilogue_halves(const GemmParams& p, const EpiCt
           const int E = x.er + fe[q];
           double zz[2];
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const long long Hh = H[2 * q + h], Lh = L[2 * q + h];
-            long long hi = S8 ? (Hh >> (64 - S8)) : (Hh >> 63);
-            const unsigned long long lo = static_cast<unsigned long long>(Hh) << S8;
-            const unsigned long long lo2 = lo + static_cast<unsigned long long>(Lh);
-            hi += (Lh >> 63) + (lo2 < lo ? 1 : 0);
-            zz[h] = round_hl(hi, lo2, E);
-          }
+          for (int h = 0; h < 2; ++h) zz[h] = round_hl_jam<S8>(H[2 * q + h], L[2 * q + h], E);
           double2* dst = x.Cz + x.crow + jc * x.ldc;
           if (p.mode == EPI_STORE) {
             if (p.ar == 1.0 && p.ai == 0.0) *dst = make_double2(zz[0], zz[1]);
@@ -483,6 +499,7 @@ __device__ __forceinline__ void epilogue_halves(const GemmParams& p, const EpiCt
       }
     }
   }
+  return true;
 }
 
 // RN-even of V 2^E for a two's-complement V with |V| < 2^63 (the exact sum when it fits in 64
@@ -499,46 +516,42 @@ __device__ __forceinline__ double round_v64(long long V, int E) {
   return __longlong_as_double(bits + (static_cast<long long>(E) << 52));
 }
 
-// Epilogue of one 128 x 64 tile when the exact sum of every output fits in 64 bits: one
-// exactness chunk, G <= 5 groups, ceil(log2(terms)) + 14 + 8 (G - 1) + 1 <= 63 (checked on the
-// host).  Every group is folded into one int64 per stacked column with the weight
-// 2^(8 (G - 1 - g)) and its accumulator released; then the thread's C values and column
-// exponents are requested, the 16 sums rounded (their latency hides the loads') and combined.
+// Epilogue of one 128 x 64 tile when the exact sum of every output fits in 64 bits: G <= 5
+// groups, ceil(log2(terms)) + 14 + 8 (G - 1) + 1 <= 63 over all the tile's exactness chunks
+// (checked on the host).  Chunk after chunk, every group is folded into one int64 per stacked
+// column with the weight 2^(8 (G - 1 - g)) and its accumulator released; then the thread's C
+// values and column exponents are requested, the 16 sums rounded (their latency hides the
+// loads') and combined.
 template <int G>
-__device__ __forceinline__ void epilogue_fast64(const GemmParams& p, const EpiCtx& x, uint64_t* acc_empty,
-                                                uint32_t magic_mask, int lane) {
+__device__ __forceinline__ bool epilogue_fast64(const GemmParams& p, const EpiCtx& x, uint64_t* acc_empty,
+                                                uint32_t magic_mask, int lane, ChunkWait& cw) {
   constexpr int BN = 64;
   const bool needC = p.mode == EPI_LU || p.mode == EPI_GENERAL;
   const int jc0 = (x.n0 + x.c0) / 2;                  // this thread's 8 complex columns
   const int jend = min(min(jc0 + 8, (x.n2_z + 1) / 2), x.jlim);
   const bool active = x.rowok && max(jc0, x.skip_n) < jend;
-  if (!__any_sync(0xffffffffu, active)) {
-#pragma unroll
-    for (int gi = 0; gi < G; ++gi) {
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&acc_empty[gi]);
-    }
-    return;
-  }
+  if (!__any_sync(0xffffffffu, active)) return release_unread<G>(acc_empty, cw, lane);
   long long V[16];
 #pragma unroll
   for (int j = 0; j < 16; ++j) V[j] = 0;
+  for (int c = 0; c < cw.nchunks; ++c) {
+    if (!cw.next()) return false;
 #pragma unroll
-  for (int gi = 0; gi < G; ++gi) {
-    uint32_t v[8], u[8];
-    tmem_ld8(x.tbase + gi * BN, v);
-    tmem_ld8(x.tbase + gi * BN + 8, u);
-    tmem_wait_ld();
-    tc_fence_before();
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&acc_empty[gi]);         // group gi may be overwritten now
-    const long long w = 1ll << (8 * (G - 1 - gi));
-    const bool mg = (magic_mask >> gi) & 1u;
-    fold8(V, v, w, mg);
-    fold8(V + 8, u, w, mg);
+    for (int gi = 0; gi < G; ++gi) {
+      uint32_t v[8], u[8];
+      tmem_ld8(x.tbase + gi * BN, v);
+      tmem_ld8(x.tbase + gi * BN + 8, u);
+      tmem_wait_ld();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[gi]);         // group gi may be overwritten now
+      const long long w = 1ll << (8 * (G - 1 - gi));
+      const bool mg = (magic_mask >> gi) & 1u;
+      fold8(V, v, w, mg);
+      fold8(V + 8, u, w, mg);
+    }
   }
-  if (!active) return;
+  if (!active) return true;
   // two halves of 4 complex columns: a half's C values and exponents are requested, its 8 sums
   // rounded while they arrive, then combined and stored
 #pragma unroll
@@ -578,6 +591,7 @@ __device__ __forceinline__ void epilogue_fast64(const GemmParams& p, const EpiCt
       }
     }
   }
+  return true;
 }
 
 // SF = 0: the slice count, pair schedule and epilogue variant are chosen at run time.  SF > 0:
@@ -763,55 +777,56 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       const int row = m0 + quad * 32 + lane;
       const bool rowok = row < m_z;
       if constexpr (COLS == 16) {
-        if (horner && G <= 8 && p.mode != EPI_GROUPS && p.mode != EPI_RESIDUES) {
+        if (G <= 8 && p.mode != EPI_GROUPS && p.mode != EPI_RESIDUES) {
           EpiCtx x;
           x.row = row; x.z = z; x.m_z = m_z; x.n2_z = n2_z; x.n0 = n0; x.c0 = c0; x.tbase = tbase;
           x.rowok = rowok;
           x.skip_n = (row < (single ? p.skm1 : (p.skm ? p.skm[z] : 0))) ? (single ? p.skn1 : p.skn[z]) : 0;
           out_row(p, single, z, row, x.rowok, x.Cz, x.crow, x.grow, x.ldc, x.jlim);
           x.er = x.rowok ? p.e[z * p.e_stride + row] + p.base_exp : 0;
-          if (!mbar_wait(acc_full, cc & 1, p.status, abort_flag)) { ok = false; break; }
-          tc_fence_after();
-          ++cc;
+          ChunkWait cw{acc_full, nchunks, &cc, p.status, abort_flag};
           // short K (at most two K-blocks per tile): the epilogue bounds the tile, and the
           // two-halves variant with streamed TMEM loads is faster (1.18x on 1024 x 1040 x 16
           // tiles); longer K: the group-wise drain that releases accumulators earliest (1.14x
           // on 976 x 976 x 64)
+          const bool halves = p.kblocks <= 2 && nchunks == 1;
+          bool e_ok;
           if constexpr (SF > 0) {
-            if (SF <= 5 && p.fit64) epilogue_fast64<(SF <= 5 ? SF : 5)>(p, x, acc_empty, magic_mask, lane);
-            else if (p.kblocks <= 2) epilogue_halves<SF>(p, x, acc_empty, magic, lane);
-            else epilogue_fast<SF>(p, x, acc_empty, magic, lane);
+            if (SF <= 5 && p.fit64) e_ok = epilogue_fast64<(SF <= 5 ? SF : 5)>(p, x, acc_empty, magic_mask, lane, cw);
+            else if (halves) e_ok = epilogue_halves<SF>(p, x, acc_empty, magic, lane, cw);
+            else e_ok = epilogue_fast<SF>(p, x, acc_empty, magic, lane, cw);
           } else if (p.fit64 && G <= 5) {
             switch (G) {
-              case 1: epilogue_fast64<1>(p, x, acc_empty, magic_mask, lane); break;
-              case 2: epilogue_fast64<2>(p, x, acc_empty, magic_mask, lane); break;
-              case 3: epilogue_fast64<3>(p, x, acc_empty, magic_mask, lane); break;
-              case 4: epilogue_fast64<4>(p, x, acc_empty, magic_mask, lane); break;
-              default: epilogue_fast64<5>(p, x, acc_empty, magic_mask, lane); break;
+              case 1: e_ok = epilogue_fast64<1>(p, x, acc_empty, magic_mask, lane, cw); break;
+              case 2: e_ok = epilogue_fast64<2>(p, x, acc_empty, magic_mask, lane, cw); break;
+              case 3: e_ok = epilogue_fast64<3>(p, x, acc_empty, magic_mask, lane, cw); break;
+              case 4: e_ok = epilogue_fast64<4>(p, x, acc_empty, magic_mask, lane, cw); break;
+              default: e_ok = epilogue_fast64<5>(p, x, acc_empty, magic_mask, lane, cw); break;
             }
-          } else if (p.kblocks <= 2) {
+          } else if (halves) {
             switch (G) {
-              case 1: epilogue_halves<1>(p, x, acc_empty, magic, lane); break;
-              case 2: epilogue_halves<2>(p, x, acc_empty, magic, lane); break;
-              case 3: epilogue_halves<3>(p, x, acc_empty, magic, lane); break;
-              case 4: epilogue_halves<4>(p, x, acc_empty, magic, lane); break;
-              case 5: epilogue_halves<5>(p, x, acc_empty, magic, lane); break;
-              case 6: epilogue_halves<6>(p, x, acc_empty, magic, lane); break;
-              case 7: epilogue_halves<7>(p, x, acc_empty, magic, lane); break;
-              default: epilogue_halves<8>(p, x, acc_empty, magic, lane); break;
+              case 1: e_ok = epilogue_halves<1>(p, x, acc_empty, magic, lane, cw); break;
+              case 2: e_ok = epilogue_halves<2>(p, x, acc_empty, magic, lane, cw); break;
+              case 3: e_ok = epilogue_halves<3>(p, x, acc_empty, magic, lane, cw); break;
+              case 4: e_ok = epilogue_halves<4>(p, x, acc_empty, magic, lane, cw); break;
+              case 5: e_ok = epilogue_halves<5>(p, x, acc_empty, magic, lane, cw); break;
+              case 6: e_ok = epilogue_halves<6>(p, x, acc_empty, magic, lane, cw); break;
+              case 7: e_ok = epilogue_halves<7>(p, x, acc_empty, magic, lane, cw); break;
+              default: e_ok = epilogue_halves<8>(p, x, acc_empty, magic, lane, cw); break;
             }
           } else {
             switch (G) {
-              case 1: epilogue_fast<1>(p, x, acc_empty, magic, lane); break;
-              case 2: epilogue_fast<2>(p, x, acc_empty, magic, lane); break;
-              case 3: epilogue_fast<3>(p, x, acc_empty, magic, lane); break;
-              case 4: epilogue_fast<4>(p, x, acc_empty, magic, lane); break;
-              case 5: epilogue_fast<5>(p, x, acc_empty, magic, lane); break;
-              case 6: epilogue_fast<6>(p, x, acc_empty, magic, lane); break;
-              case 7: epilogue_fast<7>(p, x, acc_empty, magic, lane); break;
-              default: epilogue_fast<8>(p, x, acc_empty, magic, lane); break;
+              case 1: e_ok = epilogue_fast<1>(p, x, acc_empty, magic, lane, cw); break;
+              case 2: e_ok = epilogue_fast<2>(p, x, acc_empty, magic, lane, cw); break;
+              case 3: e_ok = epilogue_fast<3>(p, x, acc_empty, magic, lane, cw); break;
+              case 4: e_ok = epilogue_fast<4>(p, x, acc_empty, magic, lane, cw); break;
+              case 5: e_ok = epilogue_fast<5>(p, x, acc_empty, magic, lane, cw); break;
+              case 6: e_ok = epilogue_fast<6>(p, x, acc_empty, magic, lane, cw); break;
+              case 7: e_ok = epilogue_fast<7>(p, x, acc_empty, magic, lane, cw); break;
+              default: e_ok = epilogue_fast<8>(p, x, acc_empty, magic, lane, cw); break;
             }
           }
+          if (!e_ok) { ok = false; break; }
           continue;
         }
       }
