@@ -336,9 +336,10 @@ static void put_block(double* dst, int ldd, int r0, int c0, int rows, int cols, 
  * of M towards the front, so the remainder is always the leading block R = [0, p) and the
  * centre block (site 0, rows/cols 0..b-1) is eliminated last.  leaf = 0: the whole panel is
  * one pivot block (L_RJ = M_RJ D^-1, M_RR -= L_RJ M_JR).  leaf = w > 0: the panel is factored
- * leaf by leaf from its last w-wide leaf [a, a+w): L column M[0:a, a:a+w] D_a^-1, then the
- * rank-w update of [0, a) x [0, a) outside [0, p) x [0, p); after the panel, [0, p) x [0, p)
- * gets the whole panel's update M[0:p, p:q] M[p:q, 0:p] at once.
+ * leaf by leaf from its last w-wide leaf [a, a+w) (the front leaf narrower when w does not
+ * divide the panel width): L column M[0:a, a:a+w] D_a^-1, then the rank-w update of
+ * [0, a) x [0, a) outside [0, p) x [0, p); after the panel, [0, p) x [0, p) gets the whole
+ * panel's update M[0:p, p:q] M[p:q, 0:p] at once.
  * S = 0: binary64 GEMMs; S > 0: every GEMM is the emulated ZGEMM. */
 static int gemm_into(const double* X, const double* Y, int m, int n, int k, int S, int full, int lu, double* C) {
     if (S > 0) return oz_zgemm(X, Y, m, n, k, S, full, lu, C);
@@ -358,8 +359,11 @@ int oz_tau00_block(const double* M, const double* t0, int n, int b, int nb, int 
     int st = OZ_OK;
     for (int q = n; q > b && !st;) {
         int p = q - nb > b ? q - nb : b;
-        int w = leaf > 0 ? leaf : q - p;
-        for (int a = q - w; a >= p && !st; a -= w) {
+        int wl = leaf > 0 ? leaf : q - p;
+        /* leaves [a, hi) from the end of the panel; the front one narrower when the panel width
+           is not a multiple of the leaf width */
+        for (int hi = q; hi > p && !st; hi -= wl) {
+            const int a = hi - wl > p ? hi - wl : p, w = hi - a;
             double* D = (double*)malloc(sizeof(double) * 2 * (size_t)w * w);
             double* Lc = (double*)malloc(sizeof(double) * 2 * (size_t)(a > 0 ? a : 1) * w);
             double* T = (double*)malloc(sizeof(double) * 2 * (size_t)(a > 0 ? a : 1) * w);

@@ -73,10 +73,11 @@ def tau00_block(M: np.ndarray, t0: np.ndarray, nb: int, S=None, mode: str = "tri
     """Block LU eliminating from the trailing end, the centre block last (module docstring).
 
     leaf=None: each panel J = [p, q) is one pivot block (D = M_JJ inverted whole).
-    leaf=w:    the panel is factored leaf by leaf (w x w pivot blocks, from its last leaf):
-               L column of the leaf, then its rank-w update of the rows and columns of
-               [0, a) outside [0, p) x [0, p); the update of [0, p) x [0, p) by the whole
-               panel is applied once afterwards.  Same block LU, fewer trailing updates."""
+    leaf=w:    the panel is factored leaf by leaf (w x w pivot blocks, from its last leaf; the
+               front leaf narrower when w does not divide the panel width): L column of the
+               leaf, then its rank-w update of the rows and columns of [0, a) outside
+               [0, p) x [0, p); the update of [0, p) x [0, p) by the whole panel is applied
+               once afterwards.  Same block LU, fewer and deeper trailing updates."""
     b = t0.shape[0]
     A = np.array(M, dtype=np.complex128)
     n = A.shape[0]
@@ -90,16 +91,18 @@ def tau00_block(M: np.ndarray, t0: np.ndarray, nb: int, S=None, mode: str = "tri
     q = n                                   # panel J = [p, q), remainder R = [0, p)
     while q > b:
         p = max(q - nb, b)
-        w = (q - p) if leaf is None else leaf
-        a = q - w
-        while a >= p:                        # leaves [a, a + w), last one first
+        wl = (q - p) if leaf is None else leaf
+        hi = q
+        while hi > p:                        # leaves [a, hi), last one first
+            a = max(hi - wl, p)
+            w = hi - a
             Dinv = gepp_inverse(A[a:a + w, a:a + w])
             A[:a, a:a + w] = mul(A[:a, a:a + w], Dinv)                       # L column
             if a > p:
                 box = A[:p, :p].copy()
                 A[:a, :a] = sub_mul(A[:a, :a], A[:a, a:a + w], A[a:a + w, :a])  # outside the box
                 A[:p, :p] = box
-            a -= w
+            hi = a
         A[:p, :p] = sub_mul(A[:p, :p], A[:p, p:q], A[p:q, :p])                 # deferred update
         q = p
     return gepp_inverse(A[:b, :b]) @ t0

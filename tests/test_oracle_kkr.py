@@ -69,7 +69,8 @@ def test_tau00_lapack_against_gauss_jordan():
         assert kkr.rel_err(kkr.tau00_lapack(M, t[0]), co.tau00_full(M, t[0])) < 1e-13
 
 
-@pytest.mark.parametrize("nb,leaf", [(16, None), (32, None), (48, None), (64, 16), (48, 16), (128, 16)])
+@pytest.mark.parametrize("nb,leaf", [(16, None), (32, None), (48, None), (64, 16), (48, 16), (128, 16), (128, 48),
+                                     (96, 64), (192, 64)])
 def test_block_lu_agrees_with_full_inverse(nb, leaf):
     t, G, M = _system(15)
     ref = kkr.tau00_full(M, t[0])
@@ -84,6 +85,9 @@ def test_leafwise_panel_equals_whole_panel_in_exact_arithmetic():
     a = kkr.tau00_block(M, t[0], 64, leaf=16)
     b = kkr.tau00_block(M, t[0], 64)
     assert kkr.rel_err(a, b) < 1e-13
+    # ragged front leaves (a 128-wide panel in leaves of 48, 48, 32; 96 in 64 and 32)
+    for nb, leaf in ((128, 48), (96, 64)):
+        assert kkr.rel_err(kkr.tau00_block(M, t[0], nb, leaf=leaf), kkr.tau00_block(M, t[0], nb)) < 1e-13
 
 
 def test_two_site_closed_form():
@@ -111,14 +115,14 @@ def test_degenerate_t_and_G():
 def test_emulated_block_lu_error_per_S():
     t, G, M = _system(15)
     ref = kkr.tau00_full(M, t[0])
-    for leaf in (None, 16):                     # whole-panel pivot blocks, and leaf by leaf
-        errs = {S: kkr.rel_err(co.tau00_block(M, t[0], 64, S=S, leaf=leaf), ref) for S in (3, 4, 5, 6, 7)}
+    for nb, leaf in ((64, None), (64, 16), (128, 48)):     # whole-panel pivot blocks, and leaf by leaf
+        errs = {S: kkr.rel_err(co.tau00_block(M, t[0], nb, S=S, leaf=leaf), ref) for S in (3, 4, 5, 6, 7)}
         assert errs[7] <= 1e-10
         for S in (3, 4, 5, 6):
             assert errs[S + 1] < errs[S]
         # the Python and C restatements of the algorithm agree to rounding
-        py = kkr.tau00_block(M, t[0], 64, S=5, leaf=leaf)
-        assert kkr.rel_err(py, co.tau00_block(M, t[0], 64, S=5, leaf=leaf)) < 1e-13
+        py = kkr.tau00_block(M, t[0], nb, S=5, leaf=leaf)
+        assert kkr.rel_err(py, co.tau00_block(M, t[0], nb, S=5, leaf=leaf)) < 1e-13
 
 
 def test_config2_system_is_well_posed():
