@@ -57,7 +57,8 @@ def parse():
     ap.add_argument("--S", type=int, default=S_DEFAULT,
                     help="slices of every GEMM; 0 = chosen by the trained slice-count selector at --tol")
     ap.add_argument("--tol", type=float, default=1e-10, help="selector tolerance (relative Frobenius, per GEMM)")
-    ap.add_argument("--nb", type=int, default=0, help="panel width; 0 = autotuned for the workload")
+    ap.add_argument("--nb", type=int, default=0, help="panel width; 0 = panel and leaf widths autotuned for the workload")
+    ap.add_argument("--leaf", type=int, default=0, help="pivot-block (leaf) width; 0 = the panel width")
     ap.add_argument("--no-extras", action="store_true", help="skip comparisons and the CPU baseline")
     return ap.parse_args()
 
@@ -153,7 +154,7 @@ def eff_flops(ns) -> float:
     return sum(8.0 / 3.0 * float(n) ** 3 for n in ns)
 
 
-def workload_config(args, world, Ls=None, nb=None, S=None):
+def workload_config(args, world, Ls=None, nb=None, S=None, leaf=None):
     Ls = Ls if Ls is not None else workload(args.atoms)[0]
     ns = [L * B for L in Ls]
     S = S if S is not None else args.S
@@ -164,7 +165,8 @@ def workload_config(args, world, Ls=None, nb=None, S=None):
                         f"emulated GEMMs; lockstep batched block LU; every GEMM emulated, {stxt}; one step = the "
                         f"{args.atoms} solves of one energy, steps cycle through the {NENERGIES} energies",
             "atoms_per_gpu": args.atoms, "energies": NENERGIES, "liz_sites": [min(Ls), max(Ls)],
-            "n_range": [min(ns), max(ns)], "S": S if S else "selector", "nb": nb if nb else "autotuned",
+            "n_range": [min(ns), max(ns)], "S": S if S else "selector", "panel": nb if nb else "autotuned",
+            "leaf": (leaf or nb) if nb else "autotuned",
             "eff_fp64_flops_per_step": eff_flops(ns),
             "l2": f"inputs larger than L2: each step's M of all atoms is {sum(n * n for n in ns) * 16 / 2**30:.1f} GiB",
             "parallelism": f"dp{world} (independent atoms per GPU)"}
@@ -224,13 +226,13 @@ def run_ours(args):
         ozk.kkr_tau00_batched_ptrs(h, ns, B, pm, pt, ptau[0], S=0, nb=64)
         S = h.selector_last()["S_used"]
     tune_ms = None
-    nb = args.nb
-    if nb == 0:                                    # panel width from the autotuner (untimed)
-        nb, tune_ms = ozk.kkr_tau00_autotune(h, ns, B, S=S)
+    nb, leaf = args.nb, (args.leaf or args.nb)
+    if nb == 0:                                    # panel and leaf widths from the autotuner (untimed)
+        (nb, leaf), tune_ms = ozk.kkr_tau00_autotune_panels(h, ns, B, S=S)
 
     def step(z):
         ozk.kkr_build_m_shared_sizes_ptrs(h, Ls, B, pt, Gcol[z], pm, S=S)
-        ozk.kkr_tau00_batched_ptrs(h, ns, B, pm, pt, ptau[z], S=S, nb=nb)
+        ozk.kkr_tau00_batched_ptrs(h, ns, B, pm, pt, ptau[z], S=S, nb=nb, leaf=leaf)
 
     import datetime
     clk = ClockSampler(local)
@@ -308,8 +310,9 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int8 digits (fp16-held) x tensor cores -> exact int -> f64",
             "data": "synthetic (seeded SplitMix64; bcc LIZ, KKR-shaped t and G per contour energy)",
-            "config": dict(workload_config(args, world, Ls_all, nb, S),
-                           nb_autotune_ms=None if tune_ms is None else {str(k): round(v, 3) for k, v in tune_ms.items()}),
+            "config": dict(workload_config(args, world, Ls_all, nb, S, leaf),
+                           autotune_ms=None if tune_ms is None else {f"{k[0]}/{k[1]}": round(v, 3)
+                                                                      for k, v in tune_ms.items()}),
             "eff_fp64_tflops": round(eff_tflops, 3),
             "roofline": roofline, "roofline_split": roofline_split, "kernels": kernels,
             "gpu_launches": int(launches),
@@ -317,13 +320,13 @@ def run_ours(args):
             "clocks": clocks, "wall_s_timed": round(t_wall, 3),
             "step_ms_range": [round(min(step_ms), 3), round(max(step_ms), 3)]}
     if not args.no_extras:
-        ctx = dict(ozk=ozk, h=h, args=args, dev=dev, Ls=Ls, ns=ns, nb=nb, S=S, pt=pt, pm=pm, Ms=Ms,
+        ctx = dict(ozk=ozk, h=h, args=args, dev=dev, Ls=Ls, ns=ns, nb=nb, leaf=leaf, S=S, pt=pt, pm=pm, Ms=Ms,
                    Gcol=Gcol, taus=taus, ptau=ptau, t_np=t_np, E=E, step=step)
         line["graph"] = graph_measure(ctx)
         line["batched_solve_vs_dmma"] = batched_dmma_measure(ctx)
         line["selected_S"] = selector_on_workload(ctx)
         line["e2e"] = e2e_measure(ctx)
-        line["cpu_baseline"] = cpu_baseline(Ls, t_np, ctx, S, nb)
+        line["cpu_baseline"] = cpu_baseline(Ls, t_np, ctx, S, nb, leaf)
         del Ms, tdev, Gd, Gcol, taus, ctx
         torch.cuda.empty_cache()
         line["config2_batch256"] = config2_measure(ozk, h, dev)
@@ -386,20 +389,21 @@ def batched_dmma_measure(c):
     out, res = {}, {}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     z = 0
-    for label, S, nb, runs in (("emulated", c["S"], c["nb"], 2), ("dmma", -1, 32, 1)):
+    for label, S, nb, leaf, runs in (("emulated", c["S"], c["nb"], c["leaf"], 2), ("dmma", -1, 32, 32, 1)):
         ms = 0.0
         for r in range(runs):                     # emulated: the first run warms up
             ozk.kkr_build_m_shared_sizes_ptrs(h, Ls, B, pt, c["Gcol"][z], pm, S=c["S"])
             torch.cuda.synchronize()
             e0.record()
-            ozk.kkr_tau00_batched_ptrs(h, ns, B, pm, pt, c["ptau"][z], S=S, nb=nb)
+            ozk.kkr_tau00_batched_ptrs(h, ns, B, pm, pt, c["ptau"][z], S=S, nb=nb, leaf=leaf)
             e1.record()
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1)
         if h.status():
             raise RuntimeError("device status set in the batched comparison")
         res[label] = c["taus"][z].cpu().numpy()
-        out[label] = {"S": S, "nb": nb, "solve_ms": round(ms, 3), "solves_per_s": round(len(ns) / (ms / 1e3), 2)}
+        out[label] = {"S": S, "panel": nb, "leaf": leaf, "solve_ms": round(ms, 3),
+                      "solves_per_s": round(len(ns) / (ms / 1e3), 2)}
     per_atom = _rel_err_per_atom(res["emulated"], res["dmma"])
     out["energy_index"] = z
     out["max_rel_err_emulated_vs_dmma"] = float(per_atom.max())
@@ -421,15 +425,15 @@ def selector_on_workload(c):
     h.selector_configure(tol=args.tol, margin=0.3)
     ns, Ls, pt, pm = c["ns"], c["Ls"], c["pt"], c["pm"]
     ozk.kkr_build_m_shared_sizes_ptrs(h, Ls, B, pt, c["Gcol"][0], pm, S=c["S"])
-    ozk.kkr_tau00_batched_ptrs(h, ns, B, pm, pt, c["ptau"][0], S=0, nb=c["nb"])
+    ozk.kkr_tau00_batched_ptrs(h, ns, B, pm, pt, c["ptau"][0], S=0, nb=c["nb"], leaf=c["leaf"])
     torch.cuda.synchronize()
     Ssel = h.selector_last()["S_used"]
     err = float(_rel_err_per_atom(c["taus"][0].cpu().numpy(), c["tau_dmma_z0"]).max()) if "tau_dmma_z0" in c else None
-    nb, _ = ozk.kkr_tau00_autotune(h, ns, B, S=Ssel)
+    (nb, leaf), _ = ozk.kkr_tau00_autotune_panels(h, ns, B, S=Ssel)
 
     def step(z):
         ozk.kkr_build_m_shared_sizes_ptrs(h, Ls, B, pt, c["Gcol"][z], pm, S=Ssel)
-        ozk.kkr_tau00_batched_ptrs(h, ns, B, pm, pt, c["ptau"][z], S=Ssel, nb=nb)
+        ozk.kkr_tau00_batched_ptrs(h, ns, B, pm, pt, c["ptau"][z], S=Ssel, nb=nb, leaf=leaf)
 
     step(1)
     torch.cuda.synchronize()
@@ -443,7 +447,7 @@ def selector_on_workload(c):
     ms = a.elapsed_time(b) / len(zs)
     if h.status():
         raise RuntimeError("device status set in the selector's run")
-    return {"S_selected": Ssel, "tol_per_gemm": args.tol, "nb": nb, "ms_per_step": round(ms, 3),
+    return {"S_selected": Ssel, "tol_per_gemm": args.tol, "panel": nb, "leaf": leaf, "ms_per_step": round(ms, 3),
             "solves_per_s": round(len(ns) / (ms / 1e3), 2), "energies_timed": zs,
             "tau00_max_rel_err_vs_dmma_energy0": err,
             "note": "the headline stays at the stated S; this is the selector's choice beside it"}
@@ -476,7 +480,7 @@ def e2e_measure(c):
         for a in range(len(td)):
             td[a].copy_(th[a], non_blocking=True)
         ozk.kkr_build_m_shared_sizes_ptrs(h, Ls, B, pt, Gd.t(), c["pm"], S=c["S"])
-        ozk.kkr_tau00_batched_ptrs(h, ns, B, c["pm"], pt, ptau, S=c["S"], nb=c["nb"])
+        ozk.kkr_tau00_batched_ptrs(h, ns, B, c["pm"], pt, ptau, S=c["S"], nb=c["nb"], leaf=c["leaf"])
         tau_h.copy_(taus, non_blocking=True)
 
     step(0)
@@ -495,7 +499,7 @@ def e2e_measure(c):
             "d2h_bytes_per_step": int(tau_h.numel() * 16), "steps": len(zs)}
 
 
-def _oracle_step_atom(co, t, G, n, S, nb):
+def _oracle_step_atom(co, t, G, n, S, nb, leaf=None):
     """The oracle's version of one atom's share of a step: M = I - t G[:n, :n] block row by block
     row with emulated products, then the block-LU tau_00 with emulated GEMMs."""
     import numpy as np
@@ -505,10 +509,10 @@ def _oracle_step_atom(co, t, G, n, S, nb):
         eye = np.zeros((B, n), dtype=np.complex128)
         eye[:, rows] = np.eye(B)
         M[rows] = co.zgemm_lu(eye, t[i], G[rows, :n], S)
-    return co.tau00_block(M, t[0], nb, S=S)
+    return co.tau00_block(M, t[0], nb, S=S, leaf=leaf if leaf and leaf != nb else None)
 
 
-def cpu_baseline(Ls, t_np, c, S, nb):
+def cpu_baseline(Ls, t_np, c, S, nb, leaf):
     """The oracle (plain C, OpenMP on all host cores) on a bounded sample of the workload: the
     atoms in order, each built and solved at energy 0, until about 15 s of CPU work; solves/s of
     the sample scaled to the workload's size mix by n^3."""
@@ -521,7 +525,7 @@ def cpu_baseline(Ls, t_np, c, S, nb):
     t1 = time.perf_counter()
     while done < len(Ls) and (done == 0 or time.perf_counter() - t1 < 15.0):
         n = Ls[done] * B
-        _oracle_step_atom(co, t_np[done], G, n, S, nb)
+        _oracle_step_atom(co, t_np[done], G, n, S, nb, leaf)
         n3 += float(n) ** 3
         done += 1
     dt = time.perf_counter() - t1
@@ -530,7 +534,8 @@ def cpu_baseline(Ls, t_np, c, S, nb):
     return {"value": round(raw * (n3 / done) / mix_n3, 4), "unit": "tau00 solves/s", "cores": co.num_threads(),
             "kind": "oracle",
             "sample": f"atoms 0..{done - 1} of the workload (n {min(Ls[:done]) * B}..{max(Ls[:done]) * B}) at energy 0, "
-                      f"M built and tau_00 solved by oracle/c (OpenMP) with S={S}, {nb}-wide panels, {dt:.1f} s: "
+                      f"M built and tau_00 solved by oracle/c (OpenMP) with S={S}, {nb}-wide panels of "
+                      f"{leaf}-wide leaves, {dt:.1f} s: "
                       f"{raw:.4f} solves/s on the sample, scaled by mean n^3 of sample / mix",
             "raw_sample_solves_per_s": round(raw, 4)}
 
@@ -554,11 +559,11 @@ def config2_measure(ozk, h, dev, natoms=256, steps=5):
     pt, pm, ptau = i64(tdev), i64(Ms), i64(taus)
     out = {"atoms": natoms, "n": n, "eff_fp64_flops_per_solve": 8.0 / 3.0 * n ** 3}
     for S in (7, 5):
-        nb, _ = ozk.kkr_tau00_autotune(h, [n] * natoms, B, S=S)
+        (nb, leaf), _ = ozk.kkr_tau00_autotune_panels(h, [n] * natoms, B, S=S)
 
         def step():
             ozk.kkr_build_m_shared_ptrs(h, natoms, L, B, pt, G, pm, S=S)
-            ozk.kkr_tau00_batched_ptrs(h, [n] * natoms, B, pm, pt, ptau, S=S, nb=nb)
+            ozk.kkr_tau00_batched_ptrs(h, [n] * natoms, B, pm, pt, ptau, S=S, nb=nb, leaf=leaf)
 
         step()
         torch.cuda.synchronize()
@@ -569,7 +574,8 @@ def config2_measure(ozk, h, dev, natoms=256, steps=5):
         b.record()
         torch.cuda.synchronize()
         ms = a.elapsed_time(b) / steps
-        out[f"S{S}"] = {"nb": nb, "ms_per_step": round(ms, 3), "solves_per_s": round(natoms / (ms / 1e3), 1),
+        out[f"S{S}"] = {"panel": nb, "leaf": leaf, "ms_per_step": round(ms, 3),
+                        "solves_per_s": round(natoms / (ms / 1e3), 1),
                         "eff_fp64_tflops": round(natoms * 8.0 / 3.0 * n ** 3 / (ms / 1e3) / 1e12, 3)}
     if h.status():
         raise RuntimeError("device status set in the n = 1040 batch")

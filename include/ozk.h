@@ -343,7 +343,8 @@ ozk_status_t kkr_build_m_shared_sizes(ozk_handle_t handle, int natoms, const int
  *   b <= 64 (16 for lmax = 3; 50 for lmax = 4 with spin), nb a multiple of b.  Site 0 occupies
  *   rows/cols 0..b-1; the final S_00^-1 t_0 is a Gauss-Jordan solve (a 4-warp kernel up to
  *   16 x 16, a 256-thread one above). */
-#define OZK_NB_MAX 112            /* largest panel width of the tau_00 solves */
+#define OZK_NB_MAX 112            /* largest pivot-block (leaf) width of the tau_00 solves */
+#define OZK_PANEL_MAX 448         /* largest panel width of kkr_tau00_batched_panels */
 ozk_status_t kkr_tau00(ozk_handle_t handle, int n, int b, void* M, const void* t0, void* tau00,
                        int S, int nb);
 
@@ -368,8 +369,9 @@ ozk_status_t kkr_tau00_lu(ozk_handle_t handle, int n, int b, void* M, const void
 /* Batched tau_00 over `nsolves` independent (atom, energy) matrices of sizes n[i] (HOST
  * array, multiples of b): M, t0, tau00 are DEVICE arrays of DEVICE pointers.  All solves
  * advance panel by panel in lockstep; each step is one batched launch per kernel.
- * nb = 0: the panel width kkr_tau00_autotune chose for these sizes, b and S (tuned on the
- * first such call, which must not be captured).
+ * nb = 0: the panel and leaf widths an autotuner chose for these sizes, b and S (a cached
+ * kkr_tau00_autotune or kkr_tau00_autotune_panels result; without one, the latter runs on the
+ * first such call, which must not be captured); see kkr_tau00_batched_panels.
  * S = 0: the slice-count selector chooses S once for the call, from the operands of solve 0's
  * first trailing update (the L and U panels of its unfactored M) at the handle's tolerance;
  * ozk_selector_last reports the choice.  Synchronises; no per-GEMM residual check on this
@@ -379,6 +381,23 @@ ozk_status_t kkr_tau00_lu(ozk_handle_t handle, int n, int b, void* M, const void
 ozk_status_t kkr_tau00_batched(ozk_handle_t handle, int nsolves, const int* n, int b,
                                void* const* M, const void* const* t0, void* const* tau00,
                                int S, int nb);
+
+/* The same batched tau_00 with panels of width W (a multiple of b, <= OZK_PANEL_MAX) factored
+ * leaf by leaf (paper Sec. 3.2's LU-based inversion with each panel's trailing update
+ * deferred): the leaves [a, hi) of width w (a multiple of b, <= OZK_NB_MAX; the front leaf of a
+ * panel narrower when w does not divide its width) are taken from the panel's end; per leaf
+ * the binary64 inverse of its pivot block, L = M[0:a, a:hi] D^-1 in place and the update of
+ * the frame of [0, a) x [0, a) outside [0, p) x [0, p) (emulated GEMMs with k = w); per panel
+ * [p, q) one deferred update M[0:p, 0:p] -= M[0:p, p:q] M[p:q, 0:p], an emulated GEMM with
+ * k = q - p.  In exact arithmetic this is the block LU of kkr_tau00_batched; the pivot blocks
+ * stay w wide (the binary64 work of whole panels of width w) while the dominant updates get
+ * W-deep products.  w = 0 or w = W: one leaf per panel (kkr_tau00_batched with nb = W).
+ * W = 0: the (W, w) pair kkr_tau00_autotune_panels picks for these sizes, b and S (tuned on
+ * the first such call, which must not be captured, and cached).  S as kkr_tau00_batched; the
+ * binary64 DMMA form (S < 0) needs w = W. */
+ozk_status_t kkr_tau00_batched_panels(ozk_handle_t handle, int nsolves, const int* n, int b,
+                                      void* const* M, const void* const* t0, void* const* tau00,
+                                      int S, int W, int w);
 
 /* Contour-integrated observable of the tau_00 blocks of the energy points z_i of a contour:
  * traces[i] = Tr tau_00(z_i) and *integral = sum_i w_i Tr tau_00(z_i) (the quadrature of the
@@ -396,6 +415,17 @@ ozk_status_t kkr_contour_trace(ozk_handle_t handle, int nsolves, int b, const vo
  * the handle for nb = 0.  Synchronises; cannot be captured. */
 ozk_status_t kkr_tau00_autotune(ozk_handle_t handle, int nsolves, const int* n, int b, int S, int* nb_best,
                                 float* times);
+
+/* Autotuner over (W, w) pairs of kkr_tau00_batched_panels: whole-panel pivot blocks W = w = b,
+ * 2b, ... <= OZK_NB_MAX, then panels of two and three leaves (W = 2w, 3w) for every leaf width w
+ * (a multiple of b) from 48 to 96.  Times each on scratch test matrices of the sizes n[] as
+ * kkr_tau00_autotune does, returns the fastest pair in *W_best, *w_best and caches it for
+ * W = 0 (and nb = 0 of kkr_tau00_batched).  Optional HOST outputs: times[] (ms) and cand[]
+ * (W, w per candidate), each with room for `cap` candidates (OZK_ERR_ARG if too short; the
+ * count is written to *ncand when ncand is not NULL). */
+ozk_status_t kkr_tau00_autotune_panels(ozk_handle_t handle, int nsolves, const int* n, int b, int S,
+                                       int* W_best, int* w_best, float* times, int* cand, int cap,
+                                       int* ncand);
 
 #ifdef __cplusplus
 }

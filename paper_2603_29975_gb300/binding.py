@@ -25,6 +25,7 @@ OZK_SEL_NPARAMS = 5768
 OZK_SEL_SMIN, OZK_SEL_SMAX = 3, 10
 OZK_SEL_NO_FALLBACK = 1
 OZK_NB_MAX = 112
+OZK_PANEL_MAX = 448
 SELECTOR_WEIGHTS = os.path.join(HERE, "selector_weights.bin")
 
 
@@ -46,7 +47,8 @@ EXPORTS = ["ozk_create", "ozk_destroy", "ozk_set_stream", "ozk_get_status", "ozk
            "ozk_selector_features", "ozk_selector_predict", "ozk_selector_train_step", "ozk_selector_gradient",
            "ozk_selector_last", "ozk_rel_diff", "kkr_build_m_shared", "kkr_tau00_autotune",
            "kkr_build_m_shared_sizes", "kkr_contour_trace", "ozaki2_zgemm", "ozaki_ztrsm", "kkr_tau00_lu",
-           "ozk_profile_moved", "ozk_debug_stall_next_gemm"]
+           "ozk_profile_moved", "ozk_debug_stall_next_gemm", "kkr_tau00_batched_panels",
+           "kkr_tau00_autotune_panels"]
 KIND_NAMES = ["split", "slice_gemm", "gj", "build_m", "dmma", "other"]
 
 _lib = None
@@ -82,6 +84,8 @@ def lib():
         L.kkr_build_m.argtypes = [vp, i, i, vp, vp, vp]
         L.kkr_tau00.argtypes = [vp, i, i, vp, vp, vp, i, i]
         L.kkr_tau00_batched.argtypes = [vp, i, ip, i, vp, vp, vp, i, i]
+        L.kkr_tau00_batched_panels.argtypes = [vp, i, ip, i, vp, vp, vp, i, i, i]
+        L.kkr_tau00_autotune_panels.argtypes = [vp, i, ip, i, i, ip, ip, ctypes.POINTER(ctypes.c_float), ip, i, ip]
         L.kkr_build_m_batched.argtypes = [vp, i, ip, i, vp, vp, vp]
         L.kkr_build_m_shared.argtypes = [vp, i, i, i, vp, vp, vp, i]
         L.kkr_tau00_autotune.argtypes = [vp, i, ip, i, i, ip, ctypes.POINTER(ctypes.c_float)]
@@ -408,6 +412,19 @@ def kkr_tau00_autotune(h: Handle, n_list, b: int, S: int = 7):
     return best.value, {nb: float(times[i]) for i, nb in enumerate(cands)}
 
 
+def kkr_tau00_autotune_panels(h: Handle, n_list, b: int, S: int = 7):
+    """Time every (panel, leaf) width pair for these sizes; returns ((W, w), {(W, w): ms})."""
+    ns = len(n_list)
+    n = (ctypes.c_int * ns)(*[int(v) for v in n_list])
+    cap = 64
+    times = (ctypes.c_float * cap)()
+    cand = (ctypes.c_int * (2 * cap))()
+    W, w, nc = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib().kkr_tau00_autotune_panels(h.ptr, ns, n, b, S, ctypes.byref(W), ctypes.byref(w), times, cand, cap,
+                                           ctypes.byref(nc)), "kkr_tau00_autotune_panels")
+    return (W.value, w.value), {(cand[2 * c], cand[2 * c + 1]): float(times[c]) for c in range(nc.value)}
+
+
 def kkr_tau00(h: Handle, M, t0, tau, S: int = 7, nb: int = 64):
     """tau_00 = [M^-1]_00 t_0 (M is overwritten)."""
     n = M.shape[0]
@@ -436,27 +453,31 @@ def kkr_tau00_lu(h: Handle, M, t0, tau, S: int = 7, nb: int = 64):
     return tau
 
 
-def kkr_tau00_batched(h: Handle, Ms, t0s, taus, S: int = 7, nb: int = 64):
-    """Batched tau_00 over lists of column-major tensors (the Ms are overwritten)."""
+def kkr_tau00_batched(h: Handle, Ms, t0s, taus, S: int = 7, nb: int = 64, leaf: int = None):
+    """Batched tau_00 over lists of column-major tensors (the Ms are overwritten).  With `leaf`
+    given, nb is the panel width and leaf the pivot-block width (kkr_tau00_batched_panels)."""
     import torch
     ns = len(Ms)
     b = t0s[0].shape[0]
-    n = (ctypes.c_int * ns)(*[int(M.shape[0]) for M in Ms])
     dev = Ms[0].device
     pm = torch.tensor([_ptr(M) for M in Ms], dtype=torch.int64, device=dev)
     pt = torch.tensor([_ptr(t) for t in t0s], dtype=torch.int64, device=dev)
     pu = torch.tensor([_ptr(u) for u in taus], dtype=torch.int64, device=dev)
-    _check(lib().kkr_tau00_batched(h.ptr, ns, n, b, pm.data_ptr(), pt.data_ptr(), pu.data_ptr(), S, nb),
-           "kkr_tau00_batched")
+    kkr_tau00_batched_ptrs(h, [int(M.shape[0]) for M in Ms], b, pm, pt, pu, S=S, nb=nb, leaf=leaf)
     return taus, (pm, pt, pu)
 
 
-def kkr_tau00_batched_ptrs(h: Handle, n_list, b: int, pm, pt, pu, S: int = 7, nb: int = 64):
-    """Batched tau_00 with device pointer arrays already built (int64 CUDA tensors)."""
+def kkr_tau00_batched_ptrs(h: Handle, n_list, b: int, pm, pt, pu, S: int = 7, nb: int = 64, leaf: int = None):
+    """Batched tau_00 with device pointer arrays already built (int64 CUDA tensors).  With `leaf`
+    given, nb is the panel width and leaf the pivot-block width (kkr_tau00_batched_panels)."""
     ns = len(n_list)
     n = (ctypes.c_int * ns)(*[int(v) for v in n_list])
-    _check(lib().kkr_tau00_batched(h.ptr, ns, n, b, pm.data_ptr(), pt.data_ptr(), pu.data_ptr(), S, nb),
-           "kkr_tau00_batched")
+    if leaf is None:
+        _check(lib().kkr_tau00_batched(h.ptr, ns, n, b, pm.data_ptr(), pt.data_ptr(), pu.data_ptr(), S, nb),
+               "kkr_tau00_batched")
+    else:
+        _check(lib().kkr_tau00_batched_panels(h.ptr, ns, n, b, pm.data_ptr(), pt.data_ptr(), pu.data_ptr(), S, nb,
+                                              leaf), "kkr_tau00_batched_panels")
 
 
 # ----------------------------------------------------------------------------- selector

@@ -99,8 +99,8 @@ struct ozk_context {
   void* sel_ws = nullptr;                   // selector scratch (features, probes, products)
   size_t sel_ws_bytes = 0;
   ozk_selector_info sel_last{};
-  // panel widths chosen by kkr_tau00_autotune, keyed by (sizes..., b, S)
-  std::map<std::vector<int>, int> tuned_nb;
+  // panel and leaf widths (W, w) chosen by the autotuners, keyed by (sizes..., b, S)
+  std::map<std::vector<int>, std::pair<int, int>> tuned_nb;
   // side stream of the batched solve (operand splits that overlap the pivot-block inverses)
   // and the events that fork it from and join it to the handle's stream
   cudaStream_t aux = nullptr;
@@ -250,7 +250,7 @@ struct EmuGemm {
 
 struct GemmPlan {
   int G, BN, maxpairs, npairs, kpad, rowsA, rowsB, nstage, chunk_kb, kblocks, magic;
-  size_t offA, offB, offE, offF, total;
+  size_t offA, offB, offE, offF, offT, total;
 };
 
 ozk_status_t plan_gemm(const EmuGemm& g, GemmPlan* P) {
@@ -287,6 +287,7 @@ ozk_status_t plan_gemm(const EmuGemm& g, GemmPlan* P) {
   P->offB = off; off = align_up(off + static_cast<size_t>(g.batch) * S * P->rowsB * P->kpad * 2, 1024);
   P->offE = off; off = align_up(off + static_cast<size_t>(g.batch) * P->rowsA * 4, 256);
   P->offF = off; off = align_up(off + static_cast<size_t>(g.batch) * std::max(g.nmax, 1) * 4, 256);
+  P->offT = off; off = align_up(off + (static_cast<size_t>(g.batch) + 1) * 4, 256);   // tile prefix sums
   P->total = off;
   return OZK_OK;
 }
@@ -417,6 +418,12 @@ ozk_status_t run_emulated(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0
     }
   }
   gp.npairs = np;
+  if (!single) {
+    // problems of different sizes: every CTA enumerates exactly the tiles of each problem
+    int* tp = reinterpret_cast<int*>(ws + P.offT);
+    gp.tile_prefix = tp;
+    launch_tile_prefix(gp, P.BN, g.batch, tp, stream);
+  }
   {
     // algorithmic integer ops: every pair is one real GEMM m x 2n x 2k (8 m n k)
     Prof pr(h, OZK_KIND_SLICE_GEMM, 8.0 * np * smnk, 0.0, stream);
@@ -985,8 +992,8 @@ ozk_status_t kkr_tau00(ozk_handle_t h, int n, int b, void* Mv, const void* t0, v
     } else {
       const int St = auto_S ? 7 : S;
       auto it = h->tuned_nb.find(tune_key(1, &n, b, St));
-      if (it != h->tuned_nb.end()) {
-        nb = it->second;
+      if (it != h->tuned_nb.end() && it->second.first == it->second.second) {
+        nb = it->second.first;
       } else {
         ozk_status_t st = kkr_tau00_autotune(h, 1, &n, b, St, &nb, nullptr);
         if (st) return st;
@@ -1294,34 +1301,44 @@ ozk_status_t kkr_build_m_shared_sizes(ozk_handle_t h, int natoms, const int* L, 
   return build_m_shared_impl(h, natoms, L, Lmax, b, t, G, ldg, M, S);
 }
 
+// Batched block LU of `nsolves` matrices in lockstep.  Panels J = [p, q) of width W are
+// eliminated from the trailing end of every M, each leaf by leaf (leaves of width w from the
+// panel's end, the front one narrower when w does not divide the panel): per leaf [a, hi) the
+// pivot block's binary64 inverse, L = M[0:a, a:hi] D^-1 in place, and the leaf's update of the
+// frame of [0, a) x [0, a) outside [0, p) x [0, p); per panel the deferred update
+// M[0:p, 0:p] -= M[0:p, p:q] M[p:q, 0:p] with K = W (w = W: one leaf, no frame, the plain
+// panel-by-panel block LU).
 static ozk_status_t tau00_batched_impl(ozk_handle_t h, int nsolves, const int* n, int b, void* const* M,
-                                       const void* const* t0, void* const* tau, int S, int nb) {
+                                       const void* const* t0, void* const* tau, int S, int W, int w) {
   if (!h || !n || !M || !t0 || !tau) return set_error(OZK_ERR_ARG, "null argument");
   if (nsolves < 0) return set_error(OZK_ERR_ARG, "negative nsolves");
   if (nsolves == 0) return OZK_OK;
   if (S == 0) return set_error(OZK_ERR_ARG, "S = 0 is resolved to a slice count before the solves");
+  if (w == 0) w = W;
   const bool dmma = S < 0;                     // binary64 DMMA GEMMs instead of emulated ones
-  if (b <= 0 || b > 64 || nb < b || nb % b || nb > GJINV_MAX)
-    return set_error(OZK_ERR_ARG, "need b <= 64, b <= nb <= 112, nb % b == 0");
+  if (b <= 0 || b > 64 || w < b || w % b || w > GJINV_MAX || W < w || W % b || W > OZK_PANEL_MAX)
+    return set_error(OZK_ERR_ARG, "need b <= 64, b <= w <= 112, w <= W <= 448, w and W multiples of b");
+  if (dmma && W != w) return set_error(OZK_ERR_ARG, "the binary64 DMMA solve eliminates whole panels (w = W)");
+  const int nleaves = (W + w - 1) / w;
   int nmax = 0;
   for (int i = 0; i < nsolves; ++i) {
     if (n[i] <= 0 || n[i] % b) return set_error(OZK_ERR_ARG, "every n[i] must be a positive multiple of b");
     nmax = std::max(nmax, n[i]);
   }
-  const int panels = (nmax - b + nb - 1) / nb;
-  // workspace layout: [D^-1 per solve, nb x nb][step tables][GEMM 1 workspace][GEMM 2
-  // workspace] -- separate GEMM workspaces, so both GEMMs' early operand splits can run on the
-  // side stream while the pivot blocks are inverted
+  const int panels = (nmax - b + W - 1) / W;
+  // workspace layout: [D^-1 per solve, w x w][step tables][GEMM 1 workspace][GEMM 2 workspace]
+  // [GEMM 3 workspace] -- separate GEMM workspaces, so that the early operand splits of GEMMs 1
+  // and 2 can run on the side stream while the pivot blocks are inverted
   const size_t ns = static_cast<size_t>(nsolves);
   const size_t off_dinv = 0;
-  const size_t off_tab = align_up(off_dinv + ns * nb * nb * sizeof(double2), 1024);
-  const size_t n_ptr = 8, n_int = 16;
+  const size_t off_tab = align_up(off_dinv + ns * w * w * sizeof(double2), 1024);
+  const size_t n_ptr = 11, n_int = 26;
   const size_t off_g1 = align_up(off_tab + ns * (n_ptr * sizeof(void*) + n_int * sizeof(int)), 1024);
-  size_t off_g2 = off_g1, total = off_g1;
+  size_t off_g2 = off_g1, off_g3 = off_g1, total = off_g1;
   ozk_status_t st = OZK_OK;
   if (!dmma) {
     EmuGemm probe;
-    probe.batch = nsolves; probe.mmax = nmax; probe.nmax = nb; probe.kmax = nb; probe.S = S;
+    probe.batch = nsolves; probe.mmax = nmax; probe.nmax = w; probe.kmax = w; probe.S = S;
     GemmPlan P;
     st = plan_gemm(probe, &P);
     if (st) return st;
@@ -1329,11 +1346,15 @@ static ozk_status_t tau00_batched_impl(ozk_handle_t h, int nsolves, const int* n
     probe.nmax = nmax;
     st = plan_gemm(probe, &P);
     if (st) return st;
-    total = off_g2 + P.total;
+    off_g3 = align_up(off_g2 + P.total, 1024);
+    probe.kmax = W;
+    st = plan_gemm(probe, &P);
+    if (st) return st;
+    total = off_g3 + P.total;
   } else {
-    // binary64 path: L = M_RJ D^-1 of every solve into its own nmax x nb scratch (a tiled GEMM
+    // binary64 path: L = M_RJ D^-1 of every solve into its own nmax x w scratch (a tiled GEMM
     // cannot overwrite its own operand), then pointer and leading-dimension tables of it
-    total = align_up(off_g1 + ns * nmax * nb * sizeof(double2), 1024) + ns * (sizeof(void*) + sizeof(int));
+    total = align_up(off_g1 + ns * nmax * w * sizeof(double2), 1024) + ns * (sizeof(void*) + sizeof(int));
   }
   st = ensure_ws(h, total);
   if (st) return st;
@@ -1344,119 +1365,162 @@ static ozk_status_t tau00_batched_impl(ozk_handle_t h, int nsolves, const int* n
   double2* dinv = reinterpret_cast<double2*>(ws + off_dinv);
   uint8_t* pp = ws + off_tab;                  // ns x n_ptr pointer slots
   int* pi = reinterpret_cast<int*>(ws + off_tab + ns * n_ptr * sizeof(void*));
+  auto slot = [&](int k) { return pp + k * ns * sizeof(void*); };
   KkrStep t;
-  t.D = reinterpret_cast<const double2**>(pp + 0 * ns * sizeof(void*)); t.X = reinterpret_cast<double2**>(pp + 1 * ns * sizeof(void*));
-  t.A1 = reinterpret_cast<const double2**>(pp + 2 * ns * sizeof(void*)); t.B1 = reinterpret_cast<const double2**>(pp + 3 * ns * sizeof(void*));
-  t.C1 = reinterpret_cast<double2**>(pp + 4 * ns * sizeof(void*)); t.A2 = reinterpret_cast<const double2**>(pp + 5 * ns * sizeof(void*));
-  t.B2 = reinterpret_cast<const double2**>(pp + 6 * ns * sizeof(void*)); t.C2 = reinterpret_cast<double2**>(pp + 7 * ns * sizeof(void*));
-  t.ldd = pi + 0 * ns; t.nbv = pi + 1 * ns; t.ldx = pi + 2 * ns;
-  t.lda1 = pi + 3 * ns; t.ldb1 = pi + 4 * ns; t.ldc1 = pi + 5 * ns; t.m1 = pi + 6 * ns; t.n1 = pi + 7 * ns; t.k1 = pi + 8 * ns;
-  t.lda2 = pi + 9 * ns; t.ldb2 = pi + 10 * ns; t.ldc2 = pi + 11 * ns; t.m2 = pi + 12 * ns; t.n2 = pi + 13 * ns; t.k2 = pi + 14 * ns;
+  t.D = reinterpret_cast<const double2**>(slot(0)); t.X = reinterpret_cast<double2**>(slot(1));
+  t.A1 = reinterpret_cast<const double2**>(slot(2)); t.B1 = reinterpret_cast<const double2**>(slot(3));
+  t.C1 = reinterpret_cast<double2**>(slot(4)); t.A2 = reinterpret_cast<const double2**>(slot(5));
+  t.B2 = reinterpret_cast<const double2**>(slot(6)); t.C2 = reinterpret_cast<double2**>(slot(7));
+  t.A3 = reinterpret_cast<const double2**>(slot(8)); t.B3 = reinterpret_cast<const double2**>(slot(9));
+  t.C3 = reinterpret_cast<double2**>(slot(10));
+  int k = 0;
+  auto ints = [&]() { return pi + (k++) * ns; };
+  t.ldd = ints(); t.nbv = ints(); t.ldx = ints();
+  t.lda1 = ints(); t.ldb1 = ints(); t.ldc1 = ints(); t.m1 = ints(); t.n1 = ints(); t.k1 = ints();
+  t.lda2 = ints(); t.ldb2 = ints(); t.ldc2 = ints(); t.m2 = ints(); t.n2 = ints(); t.k2 = ints();
+  t.skm2 = ints(); t.skn2 = ints();
+  t.lda3 = ints(); t.ldb3 = ints(); t.ldc3 = ints(); t.m3 = ints(); t.n3 = ints(); t.k3 = ints();
+  if (static_cast<size_t>(k) > n_int) return set_error(OZK_ERR_ARG, "step table layout");
   double2* const* Mp = reinterpret_cast<double2* const*>(M);
   double2** tL = nullptr;
   int* tLld = nullptr;
   if (dmma) {
-    const size_t off_lt = align_up(off_g1 + ns * nmax * nb * sizeof(double2), 1024);
+    const size_t off_lt = align_up(off_g1 + ns * nmax * w * sizeof(double2), 1024);
     tL = reinterpret_cast<double2**>(ws + off_lt);
     tLld = reinterpret_cast<int*>(ws + off_lt + ns * sizeof(void*));
-    launch_strided_ptrs(tL, tLld, reinterpret_cast<double2*>(ws + off_g1), static_cast<long long>(nmax) * nb, nmax,
+    launch_strided_ptrs(tL, tLld, reinterpret_cast<double2*>(ws + off_g1), static_cast<long long>(nmax) * w, nmax,
                         nsolves, h->stream);
   }
 
   auto gemm_tables = [&](int which, int mmax, int nmaxg, int kmax, double smnk, double smk, double snk, bool lu,
-                         int sides, bool gemm, cudaStream_t stream) -> ozk_status_t {
+                         int sides, bool gemm, cudaStream_t stream, int box) -> ozk_status_t {
     EmuGemm g;
     g.oa = {0, 0}; g.ob = {0, 0}; g.batch = nsolves; g.mmax = mmax; g.nmax = nmaxg; g.kmax = kmax; g.S = S;
     if (which == 1) {
       g.tA = t.A1; g.tlda = t.lda1; g.tB = t.B1; g.tldb = t.ldb1; g.tC = t.C1; g.tldc = t.ldc1;
       g.tm = t.m1; g.tn = t.n1; g.tk = t.k1;
-    } else {
+    } else if (which == 2) {
       g.tA = t.A2; g.tlda = t.lda2; g.tB = t.B2; g.tldb = t.ldb2; g.tC = t.C2; g.tldc = t.ldc2;
       g.tm = t.m2; g.tn = t.n2; g.tk = t.k2;
+      g.tskm = t.skm2; g.tskn = t.skn2; g.box_m = box; g.box_n = box;
+    } else {
+      g.tA = t.A3; g.tlda = t.lda3; g.tB = t.B3; g.tldb = t.ldb3; g.tC = t.C3; g.tldc = t.ldc3;
+      g.tm = t.m3; g.tn = t.n3; g.tk = t.k3;
     }
     g.ar = lu ? -1 : 1; g.br = lu ? 1 : 0;
     g.sum_mnk = smnk; g.sum_mk = smk; g.sum_nk = snk;
     g.split_sides = sides; g.run_gemm = gemm; g.stream = stream;
-    return run_emulated(h, g, which == 1 ? off_g1 : off_g2);
+    return run_emulated(h, g, which == 1 ? off_g1 : (which == 2 ? off_g2 : off_g3));
   };
 
-  // panel s of every solve: J = [p, q), q = n - s nb, p = max(q - nb, b), w = q - p.
-  // D^-1 of the w x w pivot block (binary64), L = M_RJ D^-1 in place (m = p, n = k = w),
-  // M_RR -= L M_JR (m = n = p, k = w); the centre block is eliminated last.  M_RJ (GEMM 1's A)
-  // and M_JR (GEMM 2's B) do not depend on D^-1: they are split on the side stream while the
-  // pivot blocks are inverted (binary64-bound, HBM-bound work side by side)
+  // leaf j of panel s: every solve's sizes (host mirror of kkr_step_kernel) for the launch
+  // extents and the profiler's algorithmic counts
   for (int s = 0; s < panels; ++s) {
-    int pmax = 0, wmax = 0, nact = 0;
-    double s1 = 0, sa = 0, sw = 0, s3 = 0, sw3 = 0;
-    for (int i = 0; i < nsolves; ++i) {
-      const int q = n[i] - s * nb;
-      if (q <= b) continue;
-      const int p = std::max(q - nb, b), w = q - p;
-      ++nact;
-      pmax = std::max(pmax, p);
-      wmax = std::max(wmax, w);
-      s1 += static_cast<double>(p) * w * w;
-      sa += static_cast<double>(p) * w;
-      sw += static_cast<double>(w) * w;
-      s3 += static_cast<double>(p) * p * w;
-      sw3 += static_cast<double>(w) * w * w;
-    }
-    if (nact == 0) continue;
-    {
-      Prof pr(h, OZK_KIND_OTHER, 0.0, 0.0);
-      launch_kkr_step(s, nsolves, dn, Mp, b, nb, dinv, t, h->stream);
-    }
-    if (dmma) {
-      GjParams gj{};
-      gj.D = t.D; gj.ldd = t.ldd; gj.nb = t.nbv; gj.R = nullptr; gj.X = t.X; gj.ldx = t.ldx; gj.nrhs = 0;
-      gj.status = h->d_status;
-      {
-        Prof pr(h, OZK_KIND_GJ, 8.0 * sw3, 32.0 * sw);
-        launch_gjinv(gj, wmax, nsolves, h->stream);
+    for (int j = 0; j < nleaves; ++j) {
+      int amax = 0, wmax = 0, fmax = 0, pmax3 = 0, kmax3 = 0, nact = 0, box = 0;
+      double s1 = 0, sa1 = 0, sw1 = 0, sw3g = 0, sw2 = 0, s2 = 0, sa2 = 0, sb2 = 0, s3 = 0, sa3 = 0;
+      bool any3 = false, any2 = false;
+      for (int i = 0; i < nsolves; ++i) {
+        const int q = n[i] - s * W;
+        if (q <= b) continue;
+        const int p = std::max(q - W, b);
+        if (j == nleaves - 1) {
+          any3 = true;
+          pmax3 = std::max(pmax3, p);
+          kmax3 = std::max(kmax3, q - p);
+          s3 += static_cast<double>(p) * p * (q - p);
+          sa3 += static_cast<double>(p) * (q - p);
+        }
+        const int hi = q - j * w;
+        if (hi <= p) continue;
+        const int a = std::max(hi - w, p), wl = hi - a;
+        ++nact;
+        amax = std::max(amax, a);
+        wmax = std::max(wmax, wl);
+        s1 += static_cast<double>(a) * wl * wl;
+        sa1 += static_cast<double>(a) * wl;
+        sw1 += static_cast<double>(wl) * wl;
+        sw3g += static_cast<double>(wl) * wl * wl;
+        if (a > p) {
+          // the frame: rows [p, a) x [0, a) and rows [0, p) x [p, a)
+          any2 = true;
+          fmax = std::max(fmax, a);
+          box = box == 0 ? p : std::min(box, p);
+          const double fr = static_cast<double>(a) * a - static_cast<double>(p) * p;
+          s2 += fr * wl;
+          sa2 += static_cast<double>(a) * wl;
+          sb2 += static_cast<double>(a) * wl;
+          sw2 += fr;
+        }
       }
-      DmmaParams d1{};                                   // L = M_RJ D^-1 into the scratch
-      d1.batch = nsolves; d1.m = pmax; d1.n = wmax; d1.k = wmax;
-      d1.tm = t.m1; d1.tn = t.n1; d1.tk = t.k1;
-      d1.tA = t.A1; d1.tlda = t.lda1; d1.tB = t.B1; d1.tldb = t.ldb1; d1.tC = tL; d1.tldc = tLld;
-      d1.ar = 1; d1.br = 0;
+      if (nact == 0 && !any3) continue;
       {
-        Prof pr(h, OZK_KIND_DMMA, 8.0 * s1, 0.0);
-        launch_dmma(d1, h->stream);
+        Prof pr(h, OZK_KIND_OTHER, 0.0, 0.0);
+        launch_kkr_step(s, j, nleaves, nsolves, dn, Mp, b, W, w, dinv, t, h->stream);
       }
-      DmmaParams d2{};                                   // M_RR -= L M_JR
-      d2.batch = nsolves; d2.m = pmax; d2.n = pmax; d2.k = wmax;
-      d2.tm = t.m2; d2.tn = t.n2; d2.tk = t.k2;
-      d2.tA = tL; d2.tlda = tLld; d2.tB = t.B2; d2.tldb = t.ldb2; d2.tC = t.C2; d2.tldc = t.ldc2;
-      d2.ar = -1; d2.br = 1;
-      {
-        Prof pr(h, OZK_KIND_DMMA, 8.0 * s3, 0.0);
-        launch_dmma(d2, h->stream);
+      if (dmma) {
+        // one leaf per panel (w = W): the GEMM 3 of this leaf is the trailing update
+        GjParams gj{};
+        gj.D = t.D; gj.ldd = t.ldd; gj.nb = t.nbv; gj.R = nullptr; gj.X = t.X; gj.ldx = t.ldx; gj.nrhs = 0;
+        gj.status = h->d_status;
+        {
+          Prof pr(h, OZK_KIND_GJ, 8.0 * sw3g, 32.0 * sw1);
+          launch_gjinv(gj, wmax, nsolves, h->stream);
+        }
+        DmmaParams d1{};                                   // L = M_RJ D^-1 into the scratch
+        d1.batch = nsolves; d1.m = amax; d1.n = wmax; d1.k = wmax;
+        d1.tm = t.m1; d1.tn = t.n1; d1.tk = t.k1;
+        d1.tA = t.A1; d1.tlda = t.lda1; d1.tB = t.B1; d1.tldb = t.ldb1; d1.tC = tL; d1.tldc = tLld;
+        d1.ar = 1; d1.br = 0;
+        {
+          Prof pr(h, OZK_KIND_DMMA, 8.0 * s1, 0.0);
+          launch_dmma(d1, h->stream);
+        }
+        DmmaParams d2{};                                   // M_RR -= L M_JR
+        d2.batch = nsolves; d2.m = pmax3; d2.n = pmax3; d2.k = kmax3;
+        d2.tm = t.m3; d2.tn = t.n3; d2.tk = t.k3;
+        d2.tA = tL; d2.tlda = tLld; d2.tB = t.B3; d2.tldb = t.ldb3; d2.tC = t.C3; d2.tldc = t.ldc3;
+        d2.ar = -1; d2.br = 1;
+        {
+          Prof pr(h, OZK_KIND_DMMA, 8.0 * s3, 0.0);
+          launch_dmma(d2, h->stream);
+        }
+        continue;
       }
-      continue;
+      if (nact > 0) {
+        // M_RJ of the leaf (GEMM 1's A) and its U rows (GEMM 2's B) do not depend on D^-1: they
+        // are split on the side stream while the pivot blocks are inverted
+        st = cuda_check(cudaEventRecord(h->ev_fork, h->stream), "record fork");
+        if (!st) st = cuda_check(cudaStreamWaitEvent(h->aux, h->ev_fork, 0), "side stream wait");
+        if (st) return st;
+        GjParams gj{};
+        gj.D = t.D; gj.ldd = t.ldd; gj.nb = t.nbv; gj.R = nullptr; gj.X = t.X; gj.ldx = t.ldx; gj.nrhs = 0;
+        gj.status = h->d_status;
+        {
+          Prof pr(h, OZK_KIND_GJ, 8.0 * sw3g, 32.0 * sw1);
+          launch_gjinv(gj, wmax, nsolves, h->stream);
+        }
+        st = gemm_tables(1, amax, wmax, wmax, s1, sa1, sw1, false, 1, false, h->aux, 0);
+        if (!st && any2) st = gemm_tables(2, fmax, fmax, wmax, s2, sa2, sb2, true, 2, false, h->aux, box);
+        if (!st) st = cuda_check(cudaEventRecord(h->ev_join, h->aux), "record join");
+        if (!st) st = cuda_check(cudaStreamWaitEvent(h->stream, h->ev_join, 0), "join side stream");
+        if (st) return st;
+        st = gemm_tables(1, amax, wmax, wmax, s1, sa1, sw1, false, 2, true, h->stream, 0);
+        if (st) return st;
+        if (any2) {
+          st = gemm_tables(2, fmax, fmax, wmax, s2, sa2, sb2, true, 1, true, h->stream, box);
+          if (st) return st;
+        }
+      }
+      if (any3) {
+        st = gemm_tables(3, pmax3, pmax3, kmax3, s3, sa3, sa3, true, 3, true, h->stream, 0);
+        if (st) return st;
+      }
     }
-    st = cuda_check(cudaEventRecord(h->ev_fork, h->stream), "record fork");
-    if (!st) st = cuda_check(cudaStreamWaitEvent(h->aux, h->ev_fork, 0), "side stream wait");
-    if (st) return st;
-    GjParams gj{};
-    gj.D = t.D; gj.ldd = t.ldd; gj.nb = t.nbv; gj.R = nullptr; gj.X = t.X; gj.ldx = t.ldx; gj.nrhs = 0;
-    gj.status = h->d_status;
-    {
-      Prof pr(h, OZK_KIND_GJ, 8.0 * sw3, 32.0 * sw);
-      launch_gjinv(gj, wmax, nsolves, h->stream);
-    }
-    st = gemm_tables(1, pmax, wmax, wmax, s1, sa, sw, false, 1, false, h->aux);
-    if (!st) st = gemm_tables(2, pmax, pmax, wmax, s3, sa, sa, true, 2, false, h->aux);
-    if (!st) st = cuda_check(cudaEventRecord(h->ev_join, h->aux), "record join");
-    if (!st) st = cuda_check(cudaStreamWaitEvent(h->stream, h->ev_join, 0), "join side stream");
-    if (st) return st;
-    st = gemm_tables(1, pmax, wmax, wmax, s1, sa, sw, false, 2, true, h->stream);
-    if (st) return st;
-    st = gemm_tables(2, pmax, pmax, wmax, s3, sa, sa, true, 1, true, h->stream);
-    if (st) return st;
   }
   {
     Prof pr(h, OZK_KIND_OTHER, 0.0, 0.0);
-    launch_kkr_step(-1, nsolves, dn, Mp, b, nb, dinv, t, h->stream);
+    launch_kkr_step(-1, 0, nleaves, nsolves, dn, Mp, b, W, w, dinv, t, h->stream);
   }
   GjParams gj{};
   gj.D = t.D; gj.ldd = t.ldd; gj.nb = t.nbv;
@@ -1647,9 +1711,11 @@ static std::vector<int> tune_key(int nsolves, const int* n, int b, int S) {
   return key;
 }
 
-ozk_status_t kkr_tau00_autotune(ozk_handle_t h, int nsolves, const int* n, int b, int S, int* nb_best, float* times) {
-  if (!h || !n || !nb_best) return set_error(OZK_ERR_ARG, "null argument");
-  if (nsolves < 1 || S < 1 || b < 1 || b > 64) return set_error(OZK_ERR_ARG, "need nsolves >= 1, S >= 1, 1 <= b <= 64");
+// Times the batched solve on scratch copies of diagonally dominant test matrices of the given
+// sizes for every (W, w) candidate (one warm and one timed run each); the index of the fastest
+// into *best and the times into times[] (may be null).
+static ozk_status_t autotune_impl(ozk_context* h, int nsolves, const int* n, int b, int S,
+                                  const std::vector<std::pair<int, int>>& cands, int* best, float* times) {
   if (capturing(h->stream)) return set_error(OZK_ERR_CAPTURE, "autotuning times launches and cannot be captured");
   size_t total = 0;
   for (int i = 0; i < nsolves; ++i) {
@@ -1679,13 +1745,11 @@ ozk_status_t kkr_tau00_autotune(ozk_handle_t h, int nsolves, const int* n, int b
   st = size_table(h, std::vector<int>(n, n + nsolves), &dn);
   if (!st) st = cuda_check(cudaMemcpyAsync(ptrs, hp.data(), sizeof(void*) * hp.size(), cudaMemcpyHostToDevice, h->stream),
                            "upload autotune pointers");
-  std::vector<int> cands;
-  for (int nb = b; nb <= GJINV_MAX; nb += b) cands.push_back(nb);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (!st) st = cuda_check(cudaEventCreate(&e0), "cudaEventCreate");
   if (!st) st = cuda_check(cudaEventCreate(&e1), "cudaEventCreate");
-  float best = 0.0f;
-  int best_nb = 0;
+  float best_ms = 0.0f;
+  *best = -1;
   const bool prof = h->prof;
   h->prof = false;                                                    // tuning runs are not profiled
   for (size_t c = 0; c < cands.size() && !st; ++c) {
@@ -1694,23 +1758,59 @@ ozk_status_t kkr_tau00_autotune(ozk_handle_t h, int nsolves, const int* n, int b
       launch_fill_test(reinterpret_cast<double2* const*>(ptrs), dn, nsolves, b, tall, h->stream);
       cudaEventRecord(e0, h->stream);
       st = tau00_batched_impl(h, nsolves, n, b, ptrs, reinterpret_cast<const void* const*>(ptrs + nsolves),
-                              ptrs + 2 * nsolves, S, cands[c]);
+                              ptrs + 2 * nsolves, S, cands[c].first, cands[c].second);
       cudaEventRecord(e1, h->stream);
       if (!st) st = cuda_check(cudaEventSynchronize(e1), "cudaEventSynchronize");
       if (!st) st = cuda_check(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
     }
     if (st) break;
     if (times) times[c] = ms;
-    if (best_nb == 0 || ms < best) { best = ms; best_nb = cands[c]; }
+    if (*best < 0 || ms < best_ms) { best_ms = ms; *best = static_cast<int>(c); }
   }
   h->prof = prof;
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   cudaStreamSynchronize(h->stream);
   cudaFree(mem);
+  return st;
+}
+
+ozk_status_t kkr_tau00_autotune(ozk_handle_t h, int nsolves, const int* n, int b, int S, int* nb_best, float* times) {
+  if (!h || !n || !nb_best) return set_error(OZK_ERR_ARG, "null argument");
+  if (nsolves < 1 || S < 1 || b < 1 || b > 64) return set_error(OZK_ERR_ARG, "need nsolves >= 1, S >= 1, 1 <= b <= 64");
+  std::vector<std::pair<int, int>> cands;
+  for (int nb = b; nb <= GJINV_MAX; nb += b) cands.push_back({nb, nb});
+  int best = -1;
+  ozk_status_t st = autotune_impl(h, nsolves, n, b, S, cands, &best, times);
   if (st) return st;
-  h->tuned_nb[tune_key(nsolves, n, b, S)] = best_nb;
-  *nb_best = best_nb;
+  h->tuned_nb[tune_key(nsolves, n, b, S)] = cands[best];
+  *nb_best = cands[best].first;
+  return OZK_OK;
+}
+
+ozk_status_t kkr_tau00_autotune_panels(ozk_handle_t h, int nsolves, const int* n, int b, int S, int* W_best,
+                                       int* w_best, float* times, int* cand, int cap, int* ncand) {
+  if (!h || !n || !W_best || !w_best) return set_error(OZK_ERR_ARG, "null argument");
+  if (nsolves < 1 || S < 1 || b < 1 || b > 64) return set_error(OZK_ERR_ARG, "need nsolves >= 1, S >= 1, 1 <= b <= 64");
+  // whole-panel pivot blocks nb = b, 2b, ... <= 112, then panels of 2 and 3 leaves of every
+  // leaf width w (a multiple of b) from 48 to 96
+  std::vector<std::pair<int, int>> cands;
+  for (int nb = b; nb <= GJINV_MAX; nb += b) cands.push_back({nb, nb});
+  for (int w = b; w <= std::min(96, GJINV_MAX); w += b) {
+    if (w < 48) continue;
+    for (int g = 2; g <= 3; ++g)
+      if (g * w <= OZK_PANEL_MAX) cands.push_back({g * w, w});
+  }
+  if (ncand) *ncand = static_cast<int>(cands.size());
+  if (times && static_cast<int>(cands.size()) > cap) return set_error(OZK_ERR_ARG, "times/cand arrays too short");
+  int best = -1;
+  ozk_status_t st = autotune_impl(h, nsolves, n, b, S, cands, &best, times);
+  if (st) return st;
+  if (cand)
+    for (size_t c = 0; c < cands.size(); ++c) { cand[2 * c] = cands[c].first; cand[2 * c + 1] = cands[c].second; }
+  h->tuned_nb[tune_key(nsolves, n, b, S)] = cands[best];
+  *W_best = cands[best].first;
+  *w_best = cands[best].second;
   return OZK_OK;
 }
 
@@ -1749,25 +1849,32 @@ static ozk_status_t select_S_for_solves(ozk_context* h, void* const* M, const in
   return OZK_OK;
 }
 
-ozk_status_t kkr_tau00_batched(ozk_handle_t h, int nsolves, const int* n, int b, void* const* M, const void* const* t0,
-                               void* const* tau, int S, int nb) {
+ozk_status_t kkr_tau00_batched_panels(ozk_handle_t h, int nsolves, const int* n, int b, void* const* M,
+                                      const void* const* t0, void* const* tau, int S, int W, int w) {
   if (!h || !n) return set_error(OZK_ERR_ARG, "null argument");
   if (S == 0 && nsolves > 0) {
     if (!M || n[0] <= 0) return set_error(OZK_ERR_ARG, "bad solve 0");
-    ozk_status_t st = select_S_for_solves(h, M, n, b, nb, &S);
+    ozk_status_t st = select_S_for_solves(h, M, n, b, w > 0 ? w : W, &S);
     if (st) return st;
   }
-  if (nb == 0 && nsolves > 0 && S < 0) nb = std::min(GJINV_MAX, (32 + b - 1) / b * b);   // binary64: as kkr_tau00
-  if (nb == 0 && nsolves > 0) {
+  if (W == 0 && nsolves > 0 && S < 0) W = w = std::min(GJINV_MAX, (32 + b - 1) / b * b);   // binary64: as kkr_tau00
+  if (W == 0 && nsolves > 0) {
     auto it = h->tuned_nb.find(tune_key(nsolves, n, b, S));
     if (it != h->tuned_nb.end()) {
-      nb = it->second;
+      W = it->second.first;
+      w = it->second.second;
     } else {
-      ozk_status_t st = kkr_tau00_autotune(h, nsolves, n, b, S, &nb, nullptr);
+      ozk_status_t st = kkr_tau00_autotune_panels(h, nsolves, n, b, S, &W, &w, nullptr, nullptr, 0, nullptr);
       if (st) return st;
     }
   }
-  return tau00_batched_impl(h, nsolves, n, b, M, t0, tau, S, nb);
+  return tau00_batched_impl(h, nsolves, n, b, M, t0, tau, S, W, w);
+}
+
+ozk_status_t kkr_tau00_batched(ozk_handle_t h, int nsolves, const int* n, int b, void* const* M, const void* const* t0,
+                               void* const* tau, int S, int nb) {
+  if (nb > GJINV_MAX) return set_error(OZK_ERR_ARG, "nb <= 112 (the pivot block is held in shared memory)");
+  return kkr_tau00_batched_panels(h, nsolves, n, b, M, t0, tau, S, nb, nb);
 }
 
 ozk_status_t kkr_contour_trace(ozk_handle_t h, int nsolves, int b, const void* const* tau, const double* w,

@@ -666,32 +666,45 @@ namespace ozk {
 // D^-1 into the solve's nb x nb slot of dinv), GEMM 1 (L = M[0:p, p:q] D^-1, in place) and GEMM 2
 // (M[0:p, 0:p] -= L M[p:q, 0:p]); step < 0 the final S_00 solve.  Finished solves get zero
 // sizes.
-__global__ void kkr_step_kernel(int step, int nsolves, const int* __restrict__ n, double2* const* M, int b, int nb,
-                                double2* dinv, KkrStep t) {
+__global__ void kkr_step_kernel(int panel, int leaf, int nleaves, int nsolves, const int* __restrict__ n,
+                                double2* const* M, int b, int W, int w, double2* dinv, KkrStep t) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nsolves) return;
   const int ni = n[i];
   double2* Mi = M[i];
-  double2* Di = dinv + static_cast<long long>(i) * nb * nb;
+  double2* Di = dinv + static_cast<long long>(i) * w * w;
   // defaults: nothing to do
-  t.D[i] = Mi; t.ldd[i] = ni; t.nbv[i] = 0; t.X[i] = Di; t.ldx[i] = nb;
-  t.A1[i] = Mi; t.lda1[i] = ni; t.B1[i] = Di; t.ldb1[i] = nb; t.C1[i] = Mi; t.ldc1[i] = ni;
+  t.D[i] = Mi; t.ldd[i] = ni; t.nbv[i] = 0; t.X[i] = Di; t.ldx[i] = w;
+  t.A1[i] = Mi; t.lda1[i] = ni; t.B1[i] = Di; t.ldb1[i] = w; t.C1[i] = Mi; t.ldc1[i] = ni;
   t.m1[i] = 0; t.n1[i] = 0; t.k1[i] = b;
   t.A2[i] = Mi; t.lda2[i] = ni; t.B2[i] = Mi; t.ldb2[i] = ni; t.C2[i] = Mi; t.ldc2[i] = ni;
-  t.m2[i] = 0; t.n2[i] = 0; t.k2[i] = b;
-  if (step < 0) { t.nbv[i] = b; return; }
-  const int q = ni - step * nb;
+  t.m2[i] = 0; t.n2[i] = 0; t.k2[i] = b; t.skm2[i] = 0; t.skn2[i] = 0;
+  t.A3[i] = Mi; t.lda3[i] = ni; t.B3[i] = Mi; t.ldb3[i] = ni; t.C3[i] = Mi; t.ldc3[i] = ni;
+  t.m3[i] = 0; t.n3[i] = 0; t.k3[i] = b;
+  if (panel < 0) { t.nbv[i] = b; return; }
+  const int q = ni - panel * W;
   if (q <= b) return;
-  const int p = max(q - nb, b), w = q - p;
-  t.D[i] = Mi + p + static_cast<long long>(p) * ni; t.nbv[i] = w;
-  double2* Lp = Mi + static_cast<long long>(p) * ni;          // M[0:p, p:q]
-  t.A1[i] = Lp; t.C1[i] = Lp; t.m1[i] = p; t.n1[i] = w; t.k1[i] = w;
-  t.A2[i] = Lp; t.B2[i] = Mi + p; t.m2[i] = p; t.n2[i] = p; t.k2[i] = w;
+  const int p = max(q - W, b);
+  if (leaf == nleaves - 1) {                                  // the panel's deferred update
+    t.A3[i] = Mi + static_cast<long long>(p) * ni;            // M[0:p, p:q]
+    t.B3[i] = Mi + p;                                         // M[p:q, 0:p]
+    t.m3[i] = p; t.n3[i] = p; t.k3[i] = q - p;
+  }
+  const int hi = q - leaf * w;
+  if (hi <= p) return;
+  const int a = max(hi - w, p), wl = hi - a;
+  t.D[i] = Mi + a + static_cast<long long>(a) * ni; t.nbv[i] = wl;
+  double2* La = Mi + static_cast<long long>(a) * ni;          // M[0:a, a:hi]
+  t.A1[i] = La; t.C1[i] = La; t.m1[i] = a; t.n1[i] = wl; t.k1[i] = wl;
+  if (a > p) {                                                // frame of the leaf
+    t.A2[i] = La; t.B2[i] = Mi + a; t.m2[i] = a; t.n2[i] = a; t.k2[i] = wl;
+    t.skm2[i] = p; t.skn2[i] = p;
+  }
 }
 
-void launch_kkr_step(int step, int nsolves, const int* n, double2* const* M, int b, int nb, double2* dinv,
-                     const KkrStep& t, cudaStream_t st) {
-  kkr_step_kernel<<<(nsolves + 127) / 128, 128, 0, st>>>(step, nsolves, n, M, b, nb, dinv, t);
+void launch_kkr_step(int panel, int leaf, int nleaves, int nsolves, const int* n, double2* const* M, int b, int W,
+                     int w, double2* dinv, const KkrStep& t, cudaStream_t st) {
+  kkr_step_kernel<<<(nsolves + 127) / 128, 128, 0, st>>>(panel, leaf, nleaves, nsolves, n, M, b, W, w, dinv, t);
   record_launch();
 }
 

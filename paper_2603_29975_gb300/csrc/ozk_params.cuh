@@ -105,10 +105,16 @@ struct GemmParams {
   // test hook of the bounded waits (> 0): before any copy or MMA, every CTA waits on a barrier
   // that no thread arrives at with this budget of SM cycles, gives up and exits
   long long stall_cycles;
+  // batched problems of different sizes: exclusive prefix sums of every problem's own tile count
+  // ([batch + 1] ints on the device, written by launch_tile_prefix before the GEMM); nullptr:
+  // every problem enumerates the tile grid of the largest one (uniform batches, single problems)
+  const int* tile_prefix;
   uint8_t ps[MAX_PAIRS], pt[MAX_PAIRS], pg[MAX_PAIRS], pfirst[MAX_PAIRS];
 };
 void launch_slice_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const GemmParams& p, int BN,
                        int max_m, int max_n, int batch, cudaStream_t st);
+// the tile prefix sums of a batched GEMM (p.m, p.n and the skip-box tables) into out[0..batch]
+void launch_tile_prefix(const GemmParams& p, int BN, int batch, int* out, cudaStream_t st);
 size_t gemm_smem_bytes(int S, int BN, int nstage);
 
 // ---- dmma.cu: binary64 DMMA ZGEMM
@@ -168,19 +174,25 @@ void launch_fill_test(double2* const* M, const int* n, int nsolves, int b, doubl
 void launch_contour_trace(const double2* const* tau, int nsolves, int b, const double2* w, double2* tr, double2* out,
                           cudaStream_t st);
 
-// Per-step tables of the batched tau_00 driver, filled on the device for step `step`.
+// Per-step tables of the batched tau_00 driver, filled on the device for one leaf of one panel.
 struct KkrStep {
-  // pivot block inverse (or, at the end, the S_00^-1 t_0 solve)
+  // pivot block inverse of the leaf (or, at the end, the S_00^-1 t_0 solve)
   const double2** D; int* ldd; int* nbv; double2** X; int* ldx;
-  // GEMM 1: L = M_RJ D^-1 (in place), GEMM 2: M_RR -= L M_JR
+  // GEMM 1: L = M[0:a, a:hi] D^-1 in place
   const double2** A1; int* lda1; const double2** B1; int* ldb1; double2** C1; int* ldc1; int* m1; int* n1; int* k1;
+  // GEMM 2: the leaf's frame update M[0:a, 0:a] -= L M[a:hi, 0:a] outside the box [0, p) x [0, p)
   const double2** A2; int* lda2; const double2** B2; int* ldb2; double2** C2; int* ldc2; int* m2; int* n2; int* k2;
+  int* skm2; int* skn2;
+  // GEMM 3 (last leaf of a panel): the panel's deferred update M[0:p, 0:p] -= M[0:p, p:q] M[p:q, 0:p]
+  const double2** A3; int* lda3; const double2** B3; int* ldb3; double2** C3; int* ldc3; int* m3; int* n3; int* k3;
 };
-// step >= 0: tables of panel `step` (J = [p, q), q = n - step nb, p = max(q - nb, b); D^-1 into
-// dinv, pitch nb); step < 0: the final S_00^-1 t_0 solve (D = the centre block).  Solves with
-// nothing left to eliminate get empty problems.
-void launch_kkr_step(int step, int nsolves, const int* n, double2* const* M, int b, int nb, double2* dinv,
-                     const KkrStep& t, cudaStream_t st);
+// Panel `panel` of solve i: q = n_i - panel W, p = max(q - W, b); its leaf `leaf` is
+// [max(hi - w, p), hi) with hi = q - leaf w (absent when hi <= p); D^-1 goes to dinv + i w w
+// (pitch w).  The leaf's frame update is empty when the leaf starts at p; GEMM 3 is filled for
+// leaf == nleaves - 1 only.  panel < 0: the final S_00^-1 t_0 solve (D = the centre block).
+// Solves with nothing left to eliminate get empty problems.
+void launch_kkr_step(int panel, int leaf, int nleaves, int nsolves, const int* n, double2* const* M, int b, int W,
+                     int w, double2* dinv, const KkrStep& t, cudaStream_t st);
 
 // ---- selector.cu: slice-count selector (features, probes, residual check, perceptron)
 constexpr int SEL_NF = OZK_SEL_FEATURES, SEL_NH = 64, SEL_NO = OZK_SEL_OUTPUTS;

@@ -608,7 +608,7 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   constexpr int COLS = BN / 4;            // stacked columns per epilogue thread
   const bool single = p.m == nullptr;
   const int ntx = p.ntx, nty = p.nty;
-  const int ntiles = p.tpp * p.batch;
+  const int ntiles = p.tile_prefix ? p.tile_prefix[p.batch] : p.tpp * p.batch;
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -661,6 +661,34 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   // it; tiles wholly inside the box are never enumerated.  Returns false for indices past the
   // problem's own tiles or outside its extent (skipped by all roles alike).
   auto tile_of = [&](int t, int& z, int& m0, int& n0, int& m_z, int& n2_z) -> bool {
+    if (p.tile_prefix) {
+      // exact enumeration: problem z owns tiles [prefix[z], prefix[z + 1]) of its own grid
+      int lo = 0, hi = p.batch;
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (p.tile_prefix[mid] <= t) lo = mid; else hi = mid;
+      }
+      z = lo;
+      const int r = t - p.tile_prefix[z];
+      m_z = p.m[z];
+      n2_z = 2 * p.n[z];
+      const int ntx_z = (n2_z + BN - 1) / BN, nty_z = (m_z + GEMM_BM - 1) / GEMM_BM;
+      const int km = p.skm ? p.skm[z] : 0, kn = p.skn ? p.skn[z] : 0;
+      const int ky = min(km / GEMM_BM, nty_z), kx = min((2 * kn) / BN, ntx_z);
+      const int count1 = (nty_z - ky) * ntx_z;
+      int x, y;
+      if (r < count1) {
+        y = ky + r / ntx_z;
+        x = r - (y - ky) * ntx_z;
+      } else {
+        const int w = ntx_z - kx, r2 = r - count1;
+        y = r2 / w;
+        x = kx + (r2 - y * w);
+      }
+      m0 = y * GEMM_BM;
+      n0 = x * BN;
+      return true;
+    }
     z = t / p.tpp;
     const int r = t - z * p.tpp;
     m_z = single ? p.m1 : p.m[z];
@@ -944,6 +972,7 @@ void launch_slice_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const GemmP
   p.batch = batch;
   const int ky = std::min(p.box_m / GEMM_BM, p.nty), kx = std::min((2 * p.box_n) / BN, p.ntx);
   p.tpp = p.ntx * p.nty - kx * ky;
+  // with exact enumeration the tile count is on the device: one persistent CTA per SM
   const long long ntiles = static_cast<long long>(p.tpp) * batch;
   const int grid = static_cast<int>(std::min<long long>(ntiles, num_sms()));
   const size_t smem = gemm_smem_bytes(p.S, BN, p.nstage);
@@ -963,6 +992,45 @@ void launch_slice_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const GemmP
     cudaFuncSetAttribute(slice_gemm_kernel<32, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     slice_gemm_kernel<32, 0><<<grid, GEMM_THREADS, smem, st>>>(ta, tb, p);
   }
+  record_launch();
+}
+
+// Tile counts of the problems of a batched GEMM (each over its own grid, tiles wholly inside
+// its skip box left out) and their exclusive prefix sums: one CTA, chunks of 1024 problems.
+__global__ void __launch_bounds__(1024) tile_prefix_kernel(const int* __restrict__ m, const int* __restrict__ n,
+                                                           const int* __restrict__ skm, const int* __restrict__ skn,
+                                                           int batch, int BN, int* __restrict__ out) {
+  __shared__ int part[1024];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < batch; base += 1024) {
+    const int z = base + static_cast<int>(threadIdx.x);
+    int c = 0;
+    if (z < batch && m[z] > 0 && n[z] > 0) {
+      const int ntx = (2 * n[z] + BN - 1) / BN, nty = (m[z] + GEMM_BM - 1) / GEMM_BM;
+      const int km = skm ? skm[z] : 0, kn = skn ? skn[z] : 0;
+      const int ky = min(km / GEMM_BM, nty), kx = min((2 * kn) / BN, ntx);
+      c = ntx * nty - kx * ky;
+    }
+    part[threadIdx.x] = c;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {          // inclusive scan (Hillis-Steele)
+      const int v = threadIdx.x >= static_cast<unsigned>(off) ? part[threadIdx.x - off] : 0;
+      __syncthreads();
+      part[threadIdx.x] += v;
+      __syncthreads();
+    }
+    if (z < batch) out[z] = carry + part[threadIdx.x] - c;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += part[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[batch] = carry;
+}
+
+void launch_tile_prefix(const GemmParams& p, int BN, int batch, int* out, cudaStream_t st) {
+  tile_prefix_kernel<<<1, 1024, 0, st>>>(p.m, p.n, p.skm, p.skn, batch, BN, out);
   record_launch();
 }
 

@@ -93,6 +93,70 @@ def test_batched_equals_single(ozk_mod, handle, S):
         assert kkr.rel_err(got, co.tau00_full(M, t[0])) <= 1e-10
 
 
+@pytest.mark.parametrize("S,W,w", [(7, 128, 48), (7, 96, 32), (5, 192, 64), (9, 64, 32)])
+def test_batched_leaf_panels_vs_oracle(ozk_mod, handle, S, W, w):
+    """Panels of width W eliminated leaf by leaf (w-wide pivot blocks from the panel's end, a
+    ragged front leaf where w does not divide the panel, the frame of each leaf updated by a
+    GEMM with a skip box, one deferred K = W update per panel), mixed sizes in one batched call:
+    tau_00 against the oracle's leaf-wise block LU of the same M (only the binary64 pivot
+    inverses round differently) and within 1e-10 of the binary64 full inverse (S >= 7)."""
+    sizes = [27, 9, 15, 2, 20]
+    Es = [0.5 + 0.05j, -1.0 + 0.3j, 0.69 + 0.01j, 0.2 + 0.9j, 0.6 + 0.2j]
+    systems = [_system(L, E, atom=i) for i, (L, E) in enumerate(zip(sizes, Es))]
+    Ms = [ozk_mod.colmajor_cuda(M) for t, G, M in systems]
+    t0s = [ozk_mod.colmajor_cuda(t[0]) for t, G, M in systems]
+    taus = [ozk_mod.colmajor_cuda(np.zeros((16, 16), dtype=np.complex128)) for _ in systems]
+    ozk_mod.kkr_tau00_batched(handle, Ms, t0s, taus, S=S, nb=W, leaf=w)
+    assert handle.status() == 0
+    for i, (t, G, M) in enumerate(systems):
+        got = ozk_mod.to_numpy(taus[i])
+        assert kkr.rel_err(got, co.tau00_block(M, t[0], W, S=S, leaf=w)) < 1e-13, i
+        if S >= 7:
+            assert kkr.rel_err(got, co.tau00_full(M, t[0])) <= 1e-10, i
+
+
+def test_one_leaf_panels_equal_the_plain_batched_solve(ozk_mod, handle):
+    """w = W is the plain panel-by-panel block LU: bit for bit kkr_tau00_batched with nb = W."""
+    sizes = [27, 15, 9]
+    systems = [_system(L, 0.4 + 0.1j, atom=i) for i, L in enumerate(sizes)]
+
+    def run(**kw):
+        Ms = [ozk_mod.colmajor_cuda(M) for t, G, M in systems]
+        t0s = [ozk_mod.colmajor_cuda(t[0]) for t, G, M in systems]
+        taus = [ozk_mod.colmajor_cuda(np.zeros((16, 16), dtype=np.complex128)) for _ in systems]
+        ozk_mod.kkr_tau00_batched(handle, Ms, t0s, taus, S=7, **kw)
+        return [ozk_mod.to_numpy(x) for x in taus]
+
+    for a, b_ in zip(run(nb=64), run(nb=64, leaf=64)):
+        assert np.array_equal(a, b_)
+    assert handle.status() == 0
+
+
+def test_panel_autotuner_caches_a_pair(ozk_mod):
+    """kkr_tau00_autotune_panels times whole-panel and leaf-wise candidates and caches the
+    fastest (W, w); nb = 0 then runs exactly that pair (bitwise)."""
+    import torch
+    h = ozk_mod.Handle()
+    sizes = [27, 15, 27]
+    systems = [_system(L, 0.5 + 0.05j, atom=i) for i, L in enumerate(sizes)]
+    (W, w), times = ozk_mod.kkr_tau00_autotune_panels(h, [L * 16 for L in sizes], 16, S=7)
+    assert (W, w) in times and times[(W, w)] == min(times.values())
+    assert (64, 64) in times and (128, 64) in times and (288, 96) in times
+
+    def run(**kw):
+        Ms = [ozk_mod.colmajor_cuda(M) for t, G, M in systems]
+        t0s = [ozk_mod.colmajor_cuda(t[0]) for t, G, M in systems]
+        taus = [ozk_mod.colmajor_cuda(np.zeros((16, 16), dtype=np.complex128)) for _ in systems]
+        ozk_mod.kkr_tau00_batched(h, Ms, t0s, taus, S=7, **kw)
+        torch.cuda.synchronize()
+        return [ozk_mod.to_numpy(x) for x in taus]
+
+    for a, f in zip(run(nb=0), run(nb=W, leaf=w)):
+        assert np.array_equal(a, f)
+    assert h.status() == 0
+    h.close()
+
+
 def test_singular_pivot_sets_status(ozk_mod, handle):
     M = np.eye(32, dtype=np.complex128)
     M[16:, 16:] = 0.0                    # the first eliminated pivot block is exactly singular
@@ -348,8 +412,8 @@ def test_config3_full_size_sampled_atoms(ozk_mod, handle):
     """The timed workload at full size: 256 atoms with LIZ sizes drawn from 27..169 sites
     (n = 448..2704, b = 16) at three of the 32 contour energies, each energy with its own G.  M
     of every atom is built by the shared-G emulated block-row GEMMs and all 256 tau_00 are solved
-    in one batched call at S = 7 with the autotuned panel width (the launch configuration the
-    benchmark times).  For the smallest and the largest atom at each energy: every block row of
+    in one batched call at S = 7 with the autotuned panel and leaf widths (the launch
+    configuration the benchmark times).  For the smallest and the largest atom at each energy: every block row of
     M bit for bit against the oracle's emulated block-row update, tau_00 against the oracle's
     block LU of the same M (only the binary64 pivot inverses round differently) and within
     1e-10 of a binary64 library solve of the binary64 M."""
@@ -359,7 +423,7 @@ def test_config3_full_size_sampled_atoms(ozk_mod, handle):
     ns = [L * b for L in Ls]
     E, _ = synth.contour(32)
     zs = [0, 16, 31]
-    nb, _ = ozk_mod.kkr_tau00_autotune(handle, ns, b, S=S)
+    (W, w), _ = ozk_mod.kkr_tau00_autotune_panels(handle, ns, b, S=S)
     ts = [synth.kkr_t(L, b, atom=a) for a, L in enumerate(Ls)]
     tdev = [_tblocks(ozk_mod, t) for t in ts]
     Ms = [torch.empty((n, n), dtype=torch.complex128, device="cuda") for n in ns]
@@ -372,7 +436,7 @@ def test_config3_full_size_sampled_atoms(ozk_mod, handle):
         ozk_mod.kkr_build_m_shared_sizes_ptrs(handle, Ls, b, pt, Gd, pm, S=S)
         torch.cuda.synchronize()
         M_gpu = {a: Ms[a].cpu().numpy().T.copy() for a in sample}
-        ozk_mod.kkr_tau00_batched_ptrs(handle, ns, b, pm, pt, ptau, S=S, nb=nb)
+        ozk_mod.kkr_tau00_batched_ptrs(handle, ns, b, pm, pt, ptau, S=S, nb=W, leaf=w)
         torch.cuda.synchronize()
         assert handle.status() == 0
         for a in sample:
@@ -383,6 +447,6 @@ def test_config3_full_size_sampled_atoms(ozk_mod, handle):
                 eye[:, rows] = np.eye(b)
                 assert np.array_equal(M_gpu[a][rows], co.zgemm_lu(eye, ts[a][i], G[rows, :n], S)), (z, a, i)
             got = taus[a].cpu().numpy().T
-            assert kkr.rel_err(got, co.tau00_block(M_gpu[a], ts[a][0], nb, S=S)) < 1e-13, (z, a)
+            assert kkr.rel_err(got, co.tau00_block(M_gpu[a], ts[a][0], W, S=S, leaf=w)) < 1e-13, (z, a, W, w)
             ref = kkr.tau00_lapack(kkr.kkr_build(ts[a], G[:n, :n]), ts[a][0])
             assert kkr.rel_err(got, ref) <= 1e-10, (z, a)
