@@ -17,8 +17,8 @@
 //     it to int32 and adds it, shifted by its group weight 8 (g_max - g) bits, into a 64-bit
 //     (when the exact sum fits) or 128-bit integer per output element; after the last chunk
 //     that integer times 2^(e_i + f_j + c) is rounded once to binary64 (the int64 -> binary64
-//     conversion, or integer instructions for the 128-bit sum), then stored (C = Z), or
-//     subtracted from C (LU update), or combined with alpha/beta.
+//     conversion of the exact sum, or of a sticky-jammed 64-bit image of the 128-bit sum),
+//     then stored (C = Z), or subtracted from C (LU update), or combined with alpha/beta.
 // No floating-point instruction touches the products' sums before that one rounding; the
 // only binary64 arithmetic after it is the subtraction / alpha-beta combination per element.
 #include <algorithm>
@@ -29,7 +29,12 @@ namespace ozk {
 
 constexpr int GEMM_BM = 128;
 constexpr int GEMM_EPI_WARPS = 16;
-constexpr int GEMM_THREADS = (2 + GEMM_EPI_WARPS) * 32;
+// warpgroup 0 (warps 0..3): TMA producer (warp 0), MMA issuer (warp 1), two idle warps; it
+// hands registers to the four epilogue warpgroups (setmaxnreg), whose exact 128-bit sums need
+// more than the 96 registers a thread of a 20-warp CTA starts with
+constexpr int GEMM_CTRL_WARPS = 4;
+constexpr int GEMM_THREADS = (GEMM_CTRL_WARPS + GEMM_EPI_WARPS) * 32;
+constexpr int GEMM_CTRL_REGS = 64, GEMM_EPI_REGS = 104;
 
 
 // RN-even of (H 2^S8 + L) 2^E for int64 H, L with |H| < 2^56 and |L| < 2^(S8 + 30), S8 <= 32,
@@ -333,7 +338,9 @@ __device__ __forceinline__ bool release_unread(uint64_t* acc_empty, ChunkWait& c
 // 32 x 32 -> 64-bit multiply-adds with constant weights 2^24, 2^16, 2^8, 1 (|H|, |L| < 2^49 per
 // chunk).  A thread owns one row and 16 stacked columns (8 complex).  Each group accumulator is
 // released as soon as it is read, so the MMAs of the next chunk or tile start while the last
-// chunk is rounded and written.  Returns false if a wait gave up.
+// chunk is rounded and written.  The 16 sums are rounded as soon as the drain ends (the two
+// 64-bit halves of every sum die there), then all of the thread's C values are requested at
+// once and combined.  Returns false if a wait gave up.
 template <int G>
 __device__ __forceinline__ bool epilogue_fast(const GemmParams& p, const EpiCtx& x, uint64_t* acc_empty, bool magic,
                                               int lane, ChunkWait& cw) {
@@ -378,44 +385,41 @@ __device__ __forceinline__ bool epilogue_fast(const GemmParams& p, const EpiCtx&
     }
   }
   if (!active) return true;
-  // phase B: round and write, the next column's loads issued one step ahead (C was sent
-  // towards L2 before the last drain)
-  double2 cv = make_double2(0.0, 0.0);
-  int fe = 0;
-  auto load_col = [&](int jj, double2& c, int& f) {
-    const int jc = jc0 + jj;
-    const bool in = jc < jend;
-    f = in ? p.f[x.z * p.f_stride + jc] : 0;
-    c = (in && needC && jc >= x.skip_n) ? x.Cz[x.crow + jc * x.ldc] : make_double2(0.0, 0.0);
-  };
-  load_col(0, cv, fe);
+  // the 16 roundings (column exponents from memory), then phase B: every C value of the
+  // thread requested at once, combined and written
+  double zz[16];
 #pragma unroll
   for (int jj = 0; jj < 8; ++jj) {
-    double2 cn = make_double2(0.0, 0.0);
-    int fn = 0;
-    if (jj < 7) load_col(jj + 1, cn, fn);
+    const int jc = jc0 + jj;
+    const int E = x.er + (jc < jend ? p.f[x.z * p.f_stride + jc] : 0);
+    zz[2 * jj] = round_hl_jam<S8>(H[2 * jj], L[2 * jj], E);
+    zz[2 * jj + 1] = round_hl_jam<S8>(H[2 * jj + 1], L[2 * jj + 1], E);
+  }
+  double2 cv[8];
+#pragma unroll
+  for (int jj = 0; jj < 8; ++jj) {
+    const int jc = jc0 + jj;
+    cv[jj] = (needC && jc < jend && jc >= x.skip_n) ? x.Cz[x.crow + jc * x.ldc] : make_double2(0.0, 0.0);
+  }
+#pragma unroll
+  for (int jj = 0; jj < 8; ++jj) {
     const int jc = jc0 + jj;
     if (jc < jend && jc >= x.skip_n) {
-      const int E = x.er + fe;
-      double zz[2];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) zz[h] = round_hl_jam<S8>(H[2 * jj + h], L[2 * jj + h], E);
+      const double zr = zz[2 * jj], zi = zz[2 * jj + 1];
       double2* dst = x.Cz + x.crow + jc * x.ldc;
       if (p.mode == EPI_STORE) {
-        if (p.ar == 1.0 && p.ai == 0.0) *dst = make_double2(zz[0], zz[1]);
-        else *dst = make_double2(p.ar * zz[0] - p.ai * zz[1], p.ar * zz[1] + p.ai * zz[0]);
+        if (p.ar == 1.0 && p.ai == 0.0) *dst = make_double2(zr, zi);
+        else *dst = make_double2(p.ar * zr - p.ai * zi, p.ar * zi + p.ai * zr);
       } else if (p.mode == EPI_LU) {
-        *dst = make_double2(cv.x - zz[0], cv.y - zz[1]);
+        *dst = make_double2(cv[jj].x - zr, cv[jj].y - zi);
       } else if (p.mode == EPI_IMINUS) {
-        *dst = make_double2((jc == x.grow ? 1.0 : 0.0) - zz[0], 0.0 - zz[1]);
+        *dst = make_double2((jc == x.grow ? 1.0 : 0.0) - zr, 0.0 - zi);
       } else {
-        const double xr = p.ar * zz[0] - p.ai * zz[1], xi = p.ar * zz[1] + p.ai * zz[0];
-        const double yr = p.br * cv.x - p.bi * cv.y, yi = p.br * cv.y + p.bi * cv.x;
+        const double xr = p.ar * zr - p.ai * zi, xi = p.ar * zi + p.ai * zr;
+        const double yr = p.br * cv[jj].x - p.bi * cv[jj].y, yi = p.br * cv[jj].y + p.bi * cv[jj].x;
         *dst = make_double2(xr + yr, xi + yi);
       }
     }
-    cv = cn;
-    fe = fn;
   }
   return true;
 }
@@ -712,6 +716,10 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     return m0 < m_z && n0 < n2_z;
   };
 
+  // the 20 warps start with 96 registers each (61440 for the CTA); warpgroup 0 keeps 64 and the
+  // epilogue warpgroups take 104 (128 x 64 + 512 x 104 = 61440)
+  if (warp < GEMM_CTRL_WARPS) {
+  asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(GEMM_CTRL_REGS));
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer: one ring of stages across all tiles
@@ -788,10 +796,12 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         if (clock64() - t0 > kWaitBudget) { flag_error(p.status, OZK_ERR_TIMEOUT); break; }
       }
     }
+  }
   } else {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(GEMM_EPI_REGS));
     // ---------------- epilogue: 16 warps = 4 TMEM lane quadrants x 4 column slabs
     const int quad = warp & 3;
-    const int slab = (warp - 2) >> 2;
+    const int slab = (warp - GEMM_CTRL_WARPS) >> 2;
     const int c0 = slab * COLS;                  // first local stacked column of this thread
     const uint32_t tbase = tmem + (static_cast<uint32_t>(quad * 32) << 16) + c0;
     const bool magic = p.magic != 0;
@@ -858,6 +868,7 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
           continue;
         }
       }
+      if constexpr (SF > 0) continue;            // compile-time instances take only the fast epilogues
       __int128 T[COLS];
 #pragma unroll
       for (int j = 0; j < COLS; ++j) T[j] = 0;
@@ -976,7 +987,8 @@ void launch_slice_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const GemmP
   const long long ntiles = static_cast<long long>(p.tpp) * batch;
   const int grid = static_cast<int>(std::min<long long>(ntiles, num_sms()));
   const size_t smem = gemm_smem_bytes(p.S, BN, p.nstage);
-  const bool tri = BN == 64 && !p.fullset && !p.diag_pairs;
+  // the compile-time instances hold only the fast epilogues (no integer group dumps)
+  const bool tri = BN == 64 && !p.fullset && !p.diag_pairs && p.mode != EPI_GROUPS && p.mode != EPI_RESIDUES;
   if (tri && p.S == 5) {
     // the slice count the selector picks for most KKR GEMMs: a compact instance
     cudaFuncSetAttribute(slice_gemm_kernel<64, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));

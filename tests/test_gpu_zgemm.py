@@ -113,6 +113,46 @@ def test_zgemm_lu_update_64bit_sums_bit_exact(ozk_mod, handle, S, k):
     assert np.array_equal(ozk_mod.to_numpy(C), co.zgemm_lu(C0, A, B, S))
 
 
+@pytest.mark.parametrize("S,k", [(5, 64), (7, 64), (7, 112), (9, 40)])
+def test_lu_update_subtraction_edge_cases(ozk_mod, handle, S, k):
+    """C - RN(Z) with C built around the rounded product Z itself: C = Z (exact cancellation to
+    +0), C = -Z (doubling), Z one or two ulps away (massive cancellation), C = +-0, C far above
+    and far below Z (the aligned operand only a sticky bit), C of the same and of the opposite
+    sign with half-ulp distances (ties of the subtraction's rounding), subnormal and infinite C.
+    The epilogue's integer subtraction matches the binary64 subtraction of the oracle bit for
+    bit (the rare operands take the binary64 path)."""
+    m, n = 131, 77
+    A, B = rand_complex(m, k, 81 + S), rand_complex(k, n, 82 + k)
+    Z = co.zgemm(A, B, S)
+    rng = np.random.default_rng(2026 + S)
+    kind = rng.integers(0, 12, size=(m, n))
+    re, im = Z.real.copy(), Z.imag.copy()
+
+    def craft(z, kd):
+        out = z.copy()
+        out[kd == 0] = z[kd == 0]
+        out[kd == 1] = -z[kd == 1]
+        out[kd == 2] = np.nextafter(z[kd == 2], np.inf)
+        out[kd == 3] = np.nextafter(np.nextafter(z[kd == 3], -np.inf), -np.inf)
+        out[kd == 4] = 0.0
+        out[kd == 5] = -0.0
+        out[kd == 6] = z[kd == 6] * 2.0 ** 70
+        out[kd == 7] = z[kd == 7] * 2.0 ** -70
+        out[kd == 8] = z[kd == 8] * (1 + 2.0 ** -52) * 0.5
+        out[kd == 9] = -z[kd == 9] * 3.0 * 2.0 ** -54
+        out[kd == 10] = 5e-324 * (1 + (np.arange((kd == 10).sum()) % 7))
+        out[kd == 11] = z[kd == 11] * 1.5
+        return out
+
+    C0 = craft(re, kind) + 1j * craft(im, (kind + 3) % 12)
+    C0[0, 0] = complex(np.inf, 1.0)
+    C = _dev(ozk_mod, C0)
+    ozk_mod.ozaki_zgemm(handle, _dev(ozk_mod, A), _dev(ozk_mod, B), C, S=S, alpha=-1.0, beta=1.0)
+    got, want = ozk_mod.to_numpy(C), co.zgemm_lu(C0, A, B, S)
+    eq = (got.real.view(np.int64) == want.real.view(np.int64)) & (got.imag.view(np.int64) == want.imag.view(np.int64))
+    assert eq.all(), np.argwhere(~eq)[:5]
+
+
 def test_zgemm_64bit_sums_large_group_values(ozk_mod, handle):
     """Rows and columns of (127/255)(1 + i), whose five balanced digits are all 127: the
     five-pair group sums of the imaginary parts reach 128 * 5 * 127^2 ~ 2^23.3, past the range
