@@ -42,9 +42,11 @@ LIZ_MAX = 169                                  # largest LIZ of the 27..169 rang
 S_DEFAULT = 7
 L2_CONFIG2, E_CONFIG2 = 65, 0.5 + 0.05j        # the single-atom system (n = 1040)
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# dram__bytes_read.sum + dram__bytes_write.sum per slice-GEMM launch of this workload, scaled
-# from the ncu capture named in the design doc; None until the current kernel has been captured
-SLICE_GEMM_DRAM_BYTES_PER_LAUNCH = None
+# dram__bytes_read.sum + dram__bytes_write.sum per slice-GEMM launch of this workload (256
+# atoms, S = 7, W = 192, w = 64), scaled from the ncu capture of the 16-atom case in
+# profiles/slice_gemm_config3_16atoms_full.md by each launch kind's algorithmic work; set back
+# to None whenever the kernel or the step's launch sequence changes until captured again
+SLICE_GEMM_DRAM_BYTES_PER_LAUNCH = 1.747e9
 
 
 def parse():
@@ -286,7 +288,8 @@ def run_ours(args):
     roofline = {"bound": "tensor", "kernel": "slice_gemm_kernel (tcgen05 kind::f16, fp16-held int8 digits)",
                 "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4), "peak_source": f"{pk_kind} bf16 sustained (fp16 same rate)",
-                "traffic": SLICE_GEMM_DRAM_BYTES_PER_LAUNCH if (args.atoms, S) == (NATOMS, S_DEFAULT) else None,
+                "traffic": SLICE_GEMM_DRAM_BYTES_PER_LAUNCH if (args.atoms, S, nb, leaf) == (NATOMS, S_DEFAULT, 192, 64)
+                else None,
                 "algorithmic_flops_per_launch": per_launch, "launches": sg["launches"],
                 "avg_launch_us": round(1e3 * sg["ms"] / max(1, sg["launches"]), 2)}
     sp = prof["split"]

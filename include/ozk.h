@@ -237,6 +237,15 @@ ozk_status_t ozk_selector_train_step(ozk_handle_t handle, int N, const float* X,
 /* Gradient of that loss with respect to the parameters, into a DEVICE array of
  * OZK_SEL_NPARAMS floats, without updating them. */
 ozk_status_t ozk_selector_gradient(ozk_handle_t handle, int N, const float* X, const float* T, float* grad);
+/* Training-data log of the selector: while active, every S = 0 GEMM on this handle (ozaki_zgemm
+ * and the GEMMs of kkr_tau00 with S = 0) also writes one row of its 16 features (DEVICE array
+ * `features`, 16 floats per row) and of the log10 relative Frobenius errors of its products at
+ * S = 3..10 against the S = 12 product, floored at -17 (DEVICE array `targets`, 8 floats per
+ * row), up to `capacity` rows; later GEMMs are not recorded.  Each logged GEMM runs nine extra
+ * emulated products.  ozk_selector_log_end stops logging, synchronises and returns the number
+ * of rows written. */
+ozk_status_t ozk_selector_log_begin(ozk_handle_t handle, float* features, float* targets, int capacity);
+ozk_status_t ozk_selector_log_end(ozk_handle_t handle, int* count);
 /* What the last S = 0 ozaki_zgemm on this handle chose and measured. */
 ozk_status_t ozk_selector_last(ozk_handle_t handle, ozk_selector_info* info);
 /* ||X - Y||_F / ||Y||_F of two m x n DEVICE matrices (column major) into *rel (HOST);

@@ -48,7 +48,7 @@ EXPORTS = ["ozk_create", "ozk_destroy", "ozk_set_stream", "ozk_get_status", "ozk
            "ozk_selector_last", "ozk_rel_diff", "kkr_build_m_shared", "kkr_tau00_autotune",
            "kkr_build_m_shared_sizes", "kkr_contour_trace", "ozaki2_zgemm", "ozaki_ztrsm", "kkr_tau00_lu",
            "ozk_profile_moved", "ozk_debug_stall_next_gemm", "kkr_tau00_batched_panels",
-           "kkr_tau00_autotune_panels"]
+           "kkr_tau00_autotune_panels", "ozk_selector_log_begin", "ozk_selector_log_end"]
 KIND_NAMES = ["split", "slice_gemm", "gj", "build_m", "dmma", "other"]
 
 _lib = None
@@ -107,6 +107,8 @@ def lib():
         L.ozk_selector_train_step.argtypes = [vp, i, vp, vp, f32, dp]
         L.ozk_selector_gradient.argtypes = [vp, i, vp, vp, vp]
         L.ozk_selector_last.argtypes = [vp, ctypes.POINTER(SelectorInfo)]
+        L.ozk_selector_log_begin.argtypes = [vp, vp, vp, i]
+        L.ozk_selector_log_end.argtypes = [vp, ip]
         L.ozk_rel_diff.argtypes = [vp, i, i, vp, i, vp, i, dp]
         L.ozk_profile_begin.argtypes = [vp]
         L.ozk_profile_end.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), dp, dp, dp]
@@ -227,6 +229,17 @@ class Handle:
 
     def selector_configure(self, tol: float = 1e-10, margin: float = 0.3, flags: int = 0):
         _check(lib().ozk_selector_configure(self._h, tol, margin, flags), "ozk_selector_configure")
+
+    def selector_log_begin(self, features, targets):
+        """Start logging selector training rows into float32 CUDA tensors (N x 16, N x 8)."""
+        _check(lib().ozk_selector_log_begin(self._h, _f32(features, (features.shape[0], OZK_SEL_FEATURES)),
+                                            _f32(targets, (features.shape[0], OZK_SEL_OUTPUTS)),
+                                            int(features.shape[0])), "ozk_selector_log_begin")
+
+    def selector_log_end(self) -> int:
+        n = ctypes.c_int(0)
+        _check(lib().ozk_selector_log_end(self._h, ctypes.byref(n)), "ozk_selector_log_end")
+        return n.value
 
     def selector_last(self) -> dict:
         info = SelectorInfo()

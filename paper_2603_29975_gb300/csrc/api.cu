@@ -106,6 +106,12 @@ struct ozk_context {
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   long long stall_next = 0;                 // ozk_debug_stall_next_gemm: budget for the next launch
+  // selector training-data log (ozk_selector_log_begin): DEVICE rows of features and targets
+  float* sel_log_f = nullptr;
+  float* sel_log_t = nullptr;
+  int sel_log_cap = 0, sel_log_n = 0;
+  void* sel_log_ws = nullptr;               // reference and trial products of the logged GEMMs
+  size_t sel_log_ws_bytes = 0;
 };
 
 namespace {
@@ -555,6 +561,51 @@ static ozk_status_t read_aux(ozk_context* h, const SelAux* d, SelAux* out) {
   return cuda_check(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
 }
 
+// Training-data row of the selector for the GEMM g (features already in s.f): the log10
+// relative Frobenius errors of its products at S = 3..10 against the S = 12 product.
+constexpr int SEL_SREF = 12;
+static ozk_status_t sel_log_gemm(ozk_context* h, const EmuGemm& g, const SelScratch& s, size_t ws_offset) {
+  const int m = g.m, n = g.n;
+  const size_t prod = align_up(sizeof(double2) * static_cast<size_t>(m) * n, 256);
+  const size_t need = 2 * prod + align_up(sizeof(double) * 2 * static_cast<size_t>(n), 256) + 256;
+  if (need > h->sel_log_ws_bytes) {
+    ozk_status_t st = cuda_check(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    if (st) return st;
+    if (h->sel_log_ws) cudaFree(h->sel_log_ws);
+    h->sel_log_ws = nullptr;
+    h->sel_log_ws_bytes = 0;
+    st = cuda_check(cudaMalloc(&h->sel_log_ws, need + (need >> 2)), "cudaMalloc(selector log scratch)");
+    if (st) return st;
+    h->sel_log_ws_bytes = need + (need >> 2);
+  }
+  uint8_t* base = static_cast<uint8_t*>(h->sel_log_ws);
+  double2* ref = reinterpret_cast<double2*>(base);
+  double2* trial = reinterpret_cast<double2*>(base + prod);
+  double* part = reinterpret_cast<double*>(base + 2 * prod);
+  double* rel = reinterpret_cast<double*>(base + 2 * prod + align_up(sizeof(double) * 2 * static_cast<size_t>(n), 256));
+  const int row = h->sel_log_n++;
+  ozk_status_t st = cuda_check(cudaMemcpyAsync(h->sel_log_f + static_cast<size_t>(row) * SEL_NF, s.f,
+                                               sizeof(float) * SEL_NF, cudaMemcpyDeviceToDevice, h->stream),
+                               "copy features");
+  if (st) return st;
+  EmuGemm d = g;
+  d.ar = 1; d.ai = 0; d.br = 0; d.bi = 0;
+  d.pair_mode = OZK_PAIRS_TRI;
+  d.mode = -1;
+  d.ldc = m;
+  d.C = ref; d.S = SEL_SREF;
+  st = run_emulated(h, d, ws_offset);
+  for (int S = SEL_SMIN; S <= SEL_SMAX && !st; ++S) {
+    d.C = trial; d.S = S;
+    st = run_emulated(h, d, ws_offset);
+    if (st) break;
+    launch_rel_diff(m, n, trial, m, ref, m, part, rel, h->stream);
+    launch_log_err(rel, h->sel_log_t + static_cast<size_t>(row) * SEL_NO + (S - SEL_SMIN), h->stream);
+  }
+  if (st) return st;
+  return cuda_check(cudaGetLastError(), "selector log launches");
+}
+
 // S = 0: choose S, compute the product, check it with the probes, fall back to SMAX.
 static ozk_status_t zgemm_auto(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0) {
   if (!h->sel_ready)
@@ -570,6 +621,10 @@ static ozk_status_t zgemm_auto(ozk_context* h, const EmuGemm& g, size_t ws_offse
   info.probe_seed = h->sel_seed + h->sel_calls++;
   st = sel_features(h, g.oa, g.ob, m, n, k, g.A, g.lda, g.B, g.ldb, info.probe_seed, s);
   if (st) return st;
+  if (h->sel_log_f && h->sel_log_n < h->sel_log_cap) {
+    st = sel_log_gemm(h, g, s, ws_offset);
+    if (st) return st;
+  }
   launch_mlp_forward(h->sel_p, s.f, 1, nullptr, nullptr, s.Y, h->stream);
   launch_choose(s.Y, static_cast<float>(std::log10(h->sel_tol) - h->sel_margin), s.aux, h->stream);
   SelAux aux;
@@ -657,6 +712,7 @@ ozk_status_t ozk_destroy(ozk_handle_t h) {
   if (h->d_status) cudaFree(h->d_status);
   if (h->sel_p) cudaFree(h->sel_p);
   if (h->sel_ws) cudaFree(h->sel_ws);
+  if (h->sel_log_ws) cudaFree(h->sel_log_ws);
   for (auto& kv : h->tables) cudaFree(kv.second);
   for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
   if (h->aux) cudaStreamDestroy(h->aux);
@@ -1011,7 +1067,8 @@ ozk_status_t kkr_tau00(ozk_handle_t h, int n, int b, void* Mv, const void* t0, v
     size_t need = off_gemm;
     if (!dmma) {
       EmuGemm probe;
-      probe.mmax = n; probe.nmax = n; probe.kmax = nb; probe.S = auto_S ? SEL_SMAX : S;
+      // S = 0: room for the fallback products (and for the reference products of a selector log)
+      probe.mmax = n; probe.nmax = n; probe.kmax = nb; probe.S = auto_S ? (h->sel_log_f ? SEL_SREF : SEL_SMAX) : S;
       GemmPlan P;
       ozk_status_t st = plan_gemm(probe, &P);
       if (st) return st;
@@ -1928,6 +1985,24 @@ ozk_status_t ozk_profile_end(ozk_handle_t h, uint64_t* launches, double* ms, dou
   }
   h->recs.clear();
   return OZK_OK;
+}
+
+ozk_status_t ozk_selector_log_begin(ozk_handle_t h, float* features, float* targets, int capacity) {
+  if (!h || !features || !targets || capacity < 1) return set_error(OZK_ERR_ARG, "need buffers and capacity >= 1");
+  h->sel_log_f = features;
+  h->sel_log_t = targets;
+  h->sel_log_cap = capacity;
+  h->sel_log_n = 0;
+  return OZK_OK;
+}
+
+ozk_status_t ozk_selector_log_end(ozk_handle_t h, int* count) {
+  if (!h || !count) return set_error(OZK_ERR_ARG, "null argument");
+  *count = h->sel_log_n;
+  h->sel_log_f = nullptr;
+  h->sel_log_t = nullptr;
+  h->sel_log_cap = h->sel_log_n = 0;
+  return cuda_check(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
 }
 
 ozk_status_t ozk_debug_stall_next_gemm(ozk_handle_t h, long long cycles) {

@@ -230,5 +230,7 @@ void launch_mlp_train(float* P, float* gbuf, float* m, float* v, int t, float lr
 void launch_mlp_grad_only(const float* P, float* gbuf, const float* X, const float* T, int N, float* Z1, float* Z2,
                           float* Y, float* dY, float* dZ2, float* dZ1, cudaStream_t st);
 void launch_choose(const float* Y, float lim, SelAux* aux, cudaStream_t st);
+// *dst = log10(*rel) floored at -17 (selector training targets)
+void launch_log_err(const double* rel, float* dst, cudaStream_t st);
 
 }  // namespace ozk

@@ -726,6 +726,17 @@ void launch_mlp_grad_only(const float* P, float* gbuf, const float* X, const flo
   record_launch();
 }
 
+// log10 of a relative error, floored at 1e-17 (training targets of the selector)
+__global__ void log_err_kernel(const double* rel, float* dst) {
+  const double r = *rel;
+  dst[0] = r > 1e-17 ? static_cast<float>(log10(r)) : -17.0f;
+}
+
+void launch_log_err(const double* rel, float* dst, cudaStream_t st) {
+  log_err_kernel<<<1, 1, 0, st>>>(rel, dst);
+  record_launch();
+}
+
 void launch_choose(const float* Y, float lim, SelAux* aux, cudaStream_t st) {
   choose_kernel<<<1, 32, 0, st>>>(Y, lim, aux);
   record_launch();

@@ -523,9 +523,8 @@ __device__ __forceinline__ double round_v64(long long V, int E) {
 // Epilogue of one 128 x 64 tile when the exact sum of every output fits in 64 bits: G <= 5
 // groups, ceil(log2(terms)) + 14 + 8 (G - 1) + 1 <= 63 over all the tile's exactness chunks
 // (checked on the host).  Chunk after chunk, every group is folded into one int64 per stacked
-// column with the weight 2^(8 (G - 1 - g)) and its accumulator released; then the thread's C
-// values and column exponents are requested, the 16 sums rounded (their latency hides the
-// loads') and combined.
+// column with the weight 2^(8 (G - 1 - g)) and its accumulator released; then the 16 sums are
+// rounded and all of the thread's C values requested at once and combined.
 template <int G>
 __device__ __forceinline__ bool epilogue_fast64(const GemmParams& p, const EpiCtx& x, uint64_t* acc_empty,
                                                 uint32_t magic_mask, int lane, ChunkWait& cw) {
@@ -556,42 +555,41 @@ __device__ __forceinline__ bool epilogue_fast64(const GemmParams& p, const EpiCt
     }
   }
   if (!active) return true;
-  // two halves of 4 complex columns: a half's C values and exponents are requested, its 8 sums
-  // rounded while they arrive, then combined and stored
+  // the 16 roundings (column exponents from memory; I - Z: RN(-V) = -RN(V), so the
+  // off-diagonal outputs 0 - z need no binary64 operation), then every C value of the thread
+  // requested at once, combined and written
+  const bool negate = p.mode == EPI_IMINUS;
+  double zz[16];
 #pragma unroll
-  for (int half = 0; half < 2; ++half) {
-    double2 cv[4];
-    int fe[4];
+  for (int jj = 0; jj < 8; ++jj) {
+    const int jc = jc0 + jj;
+    const int E = x.er + (jc < jend ? p.f[x.z * p.f_stride + jc] : 0);
+    zz[2 * jj] = round_v64(negate ? -V[2 * jj] : V[2 * jj], E);
+    zz[2 * jj + 1] = round_v64(negate ? -V[2 * jj + 1] : V[2 * jj + 1], E);
+  }
+  double2 cv[8];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int jc = jc0 + 4 * half + q;
-      const bool in = jc < jend;
-      fe[q] = in ? p.f[x.z * p.f_stride + jc] : 0;
-      cv[q] = (in && needC && jc >= x.skip_n) ? x.Cz[x.crow + jc * x.ldc] : make_double2(0.0, 0.0);
-    }
-    // I - Z: RN(-V) = -RN(V), so the off-diagonal outputs 0 - z need no binary64 operation
-    const bool negate = p.mode == EPI_IMINUS;
-    double zz[8];
+  for (int jj = 0; jj < 8; ++jj) {
+    const int jc = jc0 + jj;
+    cv[jj] = (needC && jc < jend && jc >= x.skip_n) ? x.Cz[x.crow + jc * x.ldc] : make_double2(0.0, 0.0);
+  }
 #pragma unroll
-    for (int j = 0; j < 8; ++j) zz[j] = round_v64(negate ? -V[8 * half + j] : V[8 * half + j], x.er + fe[j >> 1]);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int jc = jc0 + 4 * half + q;
-      if (jc < jend && jc >= x.skip_n) {
-        double2* dst = x.Cz + x.crow + jc * x.ldc;
-        const double zr = zz[2 * q], zi = zz[2 * q + 1];
-        if (p.mode == EPI_STORE) {
-          if (p.ar == 1.0 && p.ai == 0.0) *dst = make_double2(zr, zi);
-          else *dst = make_double2(p.ar * zr - p.ai * zi, p.ar * zi + p.ai * zr);
-        } else if (p.mode == EPI_LU) {
-          *dst = make_double2(cv[q].x - zr, cv[q].y - zi);
-        } else if (p.mode == EPI_IMINUS) {
-          *dst = make_double2(jc == x.grow ? 1.0 + zr : zr, zi);   // zr, zi hold -z
-        } else {
-          const double xr = p.ar * zr - p.ai * zi, xi = p.ar * zi + p.ai * zr;
-          const double yr = p.br * cv[q].x - p.bi * cv[q].y, yi = p.br * cv[q].y + p.bi * cv[q].x;
-          *dst = make_double2(xr + yr, xi + yi);
-        }
+  for (int jj = 0; jj < 8; ++jj) {
+    const int jc = jc0 + jj;
+    if (jc < jend && jc >= x.skip_n) {
+      double2* dst = x.Cz + x.crow + jc * x.ldc;
+      const double zr = zz[2 * jj], zi = zz[2 * jj + 1];
+      if (p.mode == EPI_STORE) {
+        if (p.ar == 1.0 && p.ai == 0.0) *dst = make_double2(zr, zi);
+        else *dst = make_double2(p.ar * zr - p.ai * zi, p.ar * zi + p.ai * zr);
+      } else if (p.mode == EPI_LU) {
+        *dst = make_double2(cv[jj].x - zr, cv[jj].y - zi);
+      } else if (p.mode == EPI_IMINUS) {
+        *dst = make_double2(jc == x.grow ? 1.0 + zr : zr, zi);   // zr, zi hold -z
+      } else {
+        const double xr = p.ar * zr - p.ai * zi, xi = p.ar * zi + p.ai * zr;
+        const double yr = p.br * cv[jj].x - p.bi * cv[jj].y, yi = p.br * cv[jj].y + p.bi * cv[jj].x;
+        *dst = make_double2(xr + yr, xi + yi);
       }
     }
   }

@@ -107,6 +107,96 @@ def generate_instances(count, seed, kkr_sizes=(15, 27, 51, 65), energies=4):
     return out
 
 
+def contour_solves(natoms=256, energies=(0, 4, 8, 12, 16, 20, 24, 28), stride=4, offset=0):
+    """(atom, LIZ sites, energy index) of single solves drawn from the batched contour workload:
+    every `stride`-th of its `natoms` atoms (LIZ sizes drawn from 27..169 sites) at the given
+    contour points."""
+    import synth
+    Ls = [int(v) for v in synth.liz_sizes(natoms)]
+    return [(a, Ls[a], z) for a in range(offset, natoms, stride) for z in energies]
+
+
+def log_contour(ozk, h, solves, nbs=(32, 64), capacity=200000):
+    """Training rows logged from the GEMMs of block-LU solves of the contour workload.  Every
+    (atom, energy) M = I - t G (binary64 build on the GPU, G of the 169-site LIZ at that contour
+    point, the atom's leading block) is solved by kkr_tau00 with S = 0 and panel widths cycling
+    through `nbs` while the handle's selector log is on: each of the solve's GEMMs (the panels'
+    L = M_RJ D^-1 and trailing updates M_RR -= L M_JR) adds its features and its log10 errors at
+    S = 3..10.  Returns X (N x 16), T (N x 8) and the atom of every row (the split key)."""
+    import torch
+    import synth
+    b = 16
+    E, _ = synth.contour(32)
+    zs = sorted({z for _, _, z in solves})
+    Gs = dict(zip(zs, synth.kkr_contour_G(169, b, [complex(E[z]) for z in zs])))
+    F = torch.zeros((capacity, 16), dtype=torch.float32, device="cuda")
+    T = torch.zeros((capacity, 8), dtype=torch.float32, device="cuda")
+    groups = []
+    done = 0
+    for i, (a, L, z) in enumerate(solves):
+        if done >= capacity:
+            break
+        n = L * b
+        t = synth.kkr_t(L, b, atom=a)
+        tb = torch.from_numpy(np.ascontiguousarray(np.transpose(t, (0, 2, 1)))).cuda()
+        Gd = ozk.colmajor_cuda(Gs[z][:n, :n])
+        M = torch.empty((n, n), dtype=torch.complex128, device="cuda").t()
+        ozk.kkr_build_m(h, tb, Gd, M)
+        tau = torch.zeros((b, b), dtype=torch.complex128, device="cuda").t()
+        t0 = ozk.colmajor_cuda(t[0])
+        h.selector_log_begin(F[done:], T[done:])
+        ozk.kkr_tau00(h, M, t0, tau, S=0, nb=nbs[i % len(nbs)])
+        rows = h.selector_log_end()
+        groups += [a] * rows
+        done += rows
+    if h.status():
+        raise RuntimeError("device status set while logging")
+    return F[:done].cpu().numpy(), T[:done].cpu().numpy(), np.array(groups)
+
+
+def solve_times(ozk, h, solves, S_list, nb=64, tol=1e-10):
+    """Single solves of the contour workload at S = 0 (the selector per GEMM, with its check)
+    and at each fixed S of S_list: summed milliseconds (CUDA events around every solve) and the
+    largest relative error of tau_00 against the binary64 DMMA solve."""
+    import torch
+    import synth
+    b = 16
+    E, _ = synth.contour(32)
+    zs = sorted({z for _, _, z in solves})
+    Gs = dict(zip(zs, synth.kkr_contour_G(169, b, [complex(E[z]) for z in zs])))
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    h.selector_configure(tol=tol, margin=0.3)
+    out = {str(S): {"ms_total": 0.0, "max_rel_err_vs_dmma": 0.0} for S in [0] + list(S_list)}
+    for a, L, z in solves:
+        n = L * b
+        t = synth.kkr_t(L, b, atom=a)
+        tb = torch.from_numpy(np.ascontiguousarray(np.transpose(t, (0, 2, 1)))).cuda()
+        Gd = ozk.colmajor_cuda(Gs[z][:n, :n])
+        M0 = torch.empty((n, n), dtype=torch.complex128, device="cuda").t()
+        ozk.kkr_build_m(h, tb, Gd, M0)
+        t0 = ozk.colmajor_cuda(t[0])
+
+        def run(S, timed=True):
+            M = M0.clone()
+            tau = torch.zeros((b, b), dtype=torch.complex128, device="cuda").t()
+            ev[0].record()
+            ozk.kkr_tau00(h, M, t0, tau, S=S, nb=32 if S < 0 else nb)
+            ev[1].record()
+            torch.cuda.synchronize()
+            return tau.cpu().numpy(), ev[0].elapsed_time(ev[1])
+
+        ref, _ = run(-1)
+        for S in [0] + list(S_list):
+            run(S)                                                   # warm (workspace, scratch)
+            tau, ms = run(S)
+            e = float(np.linalg.norm(tau - ref) / np.linalg.norm(ref))
+            out[str(S)]["ms_total"] += ms
+            out[str(S)]["max_rel_err_vs_dmma"] = max(out[str(S)]["max_rel_err_vs_dmma"], e)
+    if h.status():
+        raise RuntimeError("device status set in the timed solves")
+    return out
+
+
 def label(ozk, h, instances, with_times=True):
     """Features (N x 16), target log10 errors (N x 8) and per-S times in ms (N x 8)."""
     import torch

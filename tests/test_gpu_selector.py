@@ -324,6 +324,48 @@ def test_single_solve_S_rule(ozk_mod):
     h.close()
 
 
+def test_selector_log_records_features_and_targets(ozk_mod):
+    """While the selector log is on, every S = 0 GEMM writes its features (those of the probe
+    seed it used) and the log10 errors of its products at S = 3..10 against S = 12 (floored at
+    -17); GEMMs past the capacity are not recorded and the products are unchanged."""
+    import torch
+    h = ozk_mod.Handle()
+    h.selector_load()
+    h.selector_configure(tol=1e-10)
+    cap = 2
+    F = torch.zeros((cap, 16), dtype=torch.float32, device="cuda")
+    T = torch.zeros((cap, 8), dtype=torch.float32, device="cuda")
+    inst = [(rand_complex(40, 24, 91 + i), rand_complex(24, 30, 95 + i)) for i in range(3)]
+    h.selector_log_begin(F, T)
+    seeds, outs = [], []
+    for A, B in inst:
+        C = ozk_mod.colmajor_cuda(np.zeros((40, 30), dtype=np.complex128))
+        ozk_mod.ozaki_zgemm(h, ozk_mod.colmajor_cuda(A), ozk_mod.colmajor_cuda(B), C, S=0)
+        seeds.append(h.selector_last()["probe_seed"])
+        outs.append(ozk_mod.to_numpy(C))
+    assert h.selector_log_end() == cap
+    for i, (A, B) in enumerate(inst[:cap]):
+        Ad, Bd = ozk_mod.colmajor_cuda(A), ozk_mod.colmajor_cuda(B)
+        f = ozk_mod.to_numpy(ozk_mod.selector_features(h, Ad, Bd, seed=seeds[i]))
+        assert np.array_equal(f, F[i].cpu().numpy())
+        ref = ozk_mod.colmajor_cuda(np.zeros((40, 30), dtype=np.complex128))
+        ozk_mod.ozaki_zgemm(h, Ad, Bd, ref, S=12)
+        for o, S in enumerate(range(3, 11)):
+            C = ozk_mod.colmajor_cuda(np.zeros((40, 30), dtype=np.complex128))
+            ozk_mod.ozaki_zgemm(h, Ad, Bd, C, S=S)
+            e = ozk_mod.rel_diff(h, C, ref)
+            want = max(math.log10(e), -17.0) if e > 1e-17 else -17.0
+            assert abs(float(T[i, o]) - want) <= 1e-5 * max(1.0, abs(want))
+        # the logged call's product is the product at the S the selector used
+        assert kkr_rel(outs[i], co.zgemm(A, B, 12)) <= 1e-10
+    assert h.status() == 0
+    h.close()
+
+
+def kkr_rel(X, Y):
+    return float(np.linalg.norm(X - Y) / np.linalg.norm(Y))
+
+
 def test_trained_selector_gains_over_fixed_S(ozk_mod):
     """The committed trained parameters on instances of an unseen seed: every returned product
     meets the tolerance against the S = 12 reference, and the products cost far fewer slice
