@@ -223,7 +223,7 @@ def run_ours(args):
         if not os.path.exists(ozk.SELECTOR_WEIGHTS):
             raise RuntimeError("--S 0 needs the trained selector parameters " + ozk.SELECTOR_WEIGHTS)
         h.selector_load()
-        h.selector_configure(tol=args.tol, margin=0.3)
+        h.selector_configure(tol=args.tol)
         ozk.kkr_build_m_shared_sizes_ptrs(h, Ls, B, pt, Gcol[0], pm, S=S_DEFAULT)
         ozk.kkr_tau00_batched_ptrs(h, ns, B, pm, pt, ptau[0], S=0, nb=64)
         S = h.selector_last()["S_used"]
@@ -416,44 +416,54 @@ def batched_dmma_measure(c):
 
 
 def selector_on_workload(c):
-    """The trained selector on the same workload: the slice count it picks (once per batched call,
-    from solve 0's first trailing update at the tolerance), the throughput at that S over 8
-    energies, and tau_00 at that S against the binary64 DMMA solve of energy 0."""
+    """The trained selector on the same workload, timed inside the step: every step builds M at
+    the stated S and solves with S = 0 (per call: the selector's pick over up to 8 sampled
+    solves' first trailing updates, their probe checks, the S = 10 fallback), against the same
+    step at fixed S = 5, the stated S and S = 10 (the slice count a caller without the network
+    must take to be safe); tau_00 of energy 0 against the binary64 DMMA solve for each."""
     import numpy as np
     import torch
     ozk, h, args = c["ozk"], c["h"], c["args"]
     if not os.path.exists(ozk.SELECTOR_WEIGHTS):
         return {"unavailable": "no trained selector parameters in the package"}
     h.selector_load()
-    h.selector_configure(tol=args.tol, margin=0.3)
+    h.selector_configure(tol=args.tol)
     ns, Ls, pt, pm = c["ns"], c["Ls"], c["pt"], c["pm"]
-    ozk.kkr_build_m_shared_sizes_ptrs(h, Ls, B, pt, c["Gcol"][0], pm, S=c["S"])
-    ozk.kkr_tau00_batched_ptrs(h, ns, B, pm, pt, c["ptau"][0], S=0, nb=c["nb"], leaf=c["leaf"])
-    torch.cuda.synchronize()
-    Ssel = h.selector_last()["S_used"]
-    err = float(_rel_err_per_atom(c["taus"][0].cpu().numpy(), c["tau_dmma_z0"]).max()) if "tau_dmma_z0" in c else None
-    (nb, leaf), _ = ozk.kkr_tau00_autotune_panels(h, ns, B, S=Ssel)
-
-    def step(z):
-        ozk.kkr_build_m_shared_sizes_ptrs(h, Ls, B, pt, c["Gcol"][z], pm, S=Ssel)
-        ozk.kkr_tau00_batched_ptrs(h, ns, B, pm, pt, c["ptau"][z], S=Ssel, nb=nb, leaf=leaf)
-
-    step(1)
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nb, leaf = c["nb"], c["leaf"]
     zs = list(range(0, NENERGIES, NENERGIES // 8))
-    a.record()
-    for z in zs:
-        step(z)
-    b.record()
-    torch.cuda.synchronize()
-    ms = a.elapsed_time(b) / len(zs)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"tol_per_gemm": args.tol, "panel": nb, "leaf": leaf, "energies_timed": zs, "steps": {}}
+
+    def run(S_build, S_solve):
+        def step(z):
+            ozk.kkr_build_m_shared_sizes_ptrs(h, Ls, B, pt, c["Gcol"][z], pm, S=S_build)
+            ozk.kkr_tau00_batched_ptrs(h, ns, B, pm, pt, c["ptau"][z], S=S_solve, nb=nb, leaf=leaf)
+        step(zs[1])
+        torch.cuda.synchronize()
+        a.record()
+        for z in zs:
+            step(z)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / len(zs)
+        rec = {"ms_per_step": round(ms, 3), "solves_per_s": round(len(ns) / (ms / 1e3), 2)}
+        if S_solve == 0:
+            info = h.selector_last()
+            rec.update({"S_used_last_step": info["S_used"], "sampled_solves": info["gemms"],
+                        "fallback": info["fallback"], "max_residual_estimate": info["residual"]})
+        step(0)
+        torch.cuda.synchronize()
+        if "tau_dmma_z0" in c:
+            rec["tau00_max_rel_err_vs_dmma_energy0"] = float(
+                _rel_err_per_atom(c["taus"][0].cpu().numpy(), c["tau_dmma_z0"]).max())
+        return rec
+
+    out["steps"]["S0_selector"] = run(c["S"], 0)
+    for S in sorted({5, c["S"], 10}):
+        out["steps"][f"S{S}_fixed"] = run(S, S)
     if h.status():
         raise RuntimeError("device status set in the selector's run")
-    return {"S_selected": Ssel, "tol_per_gemm": args.tol, "panel": nb, "leaf": leaf, "ms_per_step": round(ms, 3),
-            "solves_per_s": round(len(ns) / (ms / 1e3), 2), "energies_timed": zs,
-            "tau00_max_rel_err_vs_dmma_energy0": err,
-            "note": "the headline stays at the stated S; this is the selector's choice beside it"}
+    return out
 
 
 def e2e_measure(c):
@@ -645,6 +655,23 @@ def config4_measure(ozk, h, dev):
         ms = ev[0].elapsed_time(ev[1])
         out["zgemm_5650"][str(S)] = {"ms": round(ms, 1), "eff_tflops": round(gflops / ms / 1e9, 3),
                                      "rel_err_vs_dmma": ozk.rel_diff(h, C, C_ref)}
+    if os.path.exists(ozk.SELECTOR_WEIGHTS):
+        # S = 0 on the same product: the selector's choice, the product and its probe check in one
+        # call (two host synchronisations), against the fixed slice counts above
+        h.selector_load()
+        h.selector_configure(tol=1e-10)
+        ozk.ozaki_zgemm(h, M0, M0, C, S=0)
+        torch.cuda.synchronize()
+        ev[0].record()
+        ozk.ozaki_zgemm(h, M0, M0, C, S=0)
+        ev[1].record()
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1])
+        info = h.selector_last()
+        out["zgemm_5650"]["0"] = {"ms": round(ms, 1), "eff_tflops": round(gflops / ms / 1e9, 3),
+                                  "rel_err_vs_dmma": ozk.rel_diff(h, C, C_ref), "S_selected": info["S_selected"],
+                                  "S_used": info["S_used"], "residual_estimate": info["residual"],
+                                  "tol": 1e-10}
     out["zgemm_5650_ozaki2"] = {}
     for nm in (10, 12, 14, 16):
         ozk.ozaki2_zgemm(h, M0, M0, C, nmod=nm)
@@ -713,6 +740,12 @@ def selector_measure(ozk):
     inst = seltrain.generate_instances(96, 4242, kkr_sizes=(15, 27), energies=2)
     X, T, times = seltrain.label(ozk, h2, inst)
     res = seltrain.evaluate(ozk, h2, inst, X, T, times, tol=1e-10)
+    # single tau_00 solves of atoms the training never saw (a = 3 mod 4) of the contour workload:
+    # S = 0 (a choice per GEMM, deferred checks) against fixed S, all against binary64 DMMA
+    held_out = [a for a in range(NATOMS) if a % 4 == 3][1::8]
+    solves = seltrain.contour_solves(held_out, (6,))
+    res["contour_single_solves"] = {"atoms": held_out, "energy_index": 6,
+                                    "S": seltrain.solve_times(ozk, h2, solves, (5, 6, 7, 10), tol=1e-10)}
     h2.close()
     return res
 

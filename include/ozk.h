@@ -207,6 +207,8 @@ typedef struct {
     double residual_selected;  /* residual estimate of the product at S_selected */
     float predicted_log10_err[OZK_SEL_OUTPUTS];   /* for S = 3..10 */
     uint64_t probe_seed;       /* seed of the probe vectors of this call */
+    int gemms;                 /* kkr_tau00 (S = 0): GEMMs of the solve; ozaki_zgemm: 0 */
+    int S_count[OZK_SEL_OUTPUTS];                 /* kkr_tau00 (S = 0): GEMMs chosen at S = 3..10 */
 } ozk_selector_info;
 
 /* Random initial parameters (He-scaled normals from a counter-based generator seeded by
@@ -220,7 +222,10 @@ ozk_status_t ozk_selector_get_params(ozk_handle_t handle, float* params);
 ozk_status_t ozk_selector_load(ozk_handle_t handle, const char* path);
 ozk_status_t ozk_selector_save(ozk_handle_t handle, const char* path);
 /* Tolerance on the relative Frobenius error (default 1e-10), safety margin in decades
- * subtracted from log10(tol) when choosing (default 0.3), flags (OZK_SEL_NO_FALLBACK). */
+ * subtracted from log10(tol) when choosing (default 0.6: the check passes a product whose
+ * estimate is at most tol / 2, and the 4-probe estimate scatters around the true error, so
+ * the choice aims at tol / 4 for a product whose error is as predicted to pass), flags
+ * (OZK_SEL_NO_FALLBACK). */
 ozk_status_t ozk_selector_configure(ozk_handle_t handle, double tol, double margin, int flags);
 /* The 16 features of op(A) op(B) into a DEVICE array of 16 floats, with the probe vectors
  * of `probe_seed`.  k >= 1. */
@@ -246,7 +251,8 @@ ozk_status_t ozk_selector_gradient(ozk_handle_t handle, int N, const float* X, c
  * of rows written. */
 ozk_status_t ozk_selector_log_begin(ozk_handle_t handle, float* features, float* targets, int capacity);
 ozk_status_t ozk_selector_log_end(ozk_handle_t handle, int* count);
-/* What the last S = 0 ozaki_zgemm on this handle chose and measured. */
+/* What the last S = 0 call on this handle (ozaki_zgemm, kkr_tau00 or a batched solve) chose
+ * and measured. */
 ozk_status_t ozk_selector_last(ozk_handle_t handle, ozk_selector_info* info);
 /* ||X - Y||_F / ||Y||_F of two m x n DEVICE matrices (column major) into *rel (HOST);
  * synchronises the stream. */
@@ -339,9 +345,14 @@ ozk_status_t kkr_build_m_shared_sizes(ozk_handle_t handle, int natoms, const int
  * followed by this call on the M it built.  The slice count follows the ozaki_zgemm rule:
  *   S >= 1: both GEMMs are the emulated ZGEMM with S slices.
  *   S = 0:  every GEMM is the emulated ZGEMM at the slice count the selector picks for its
- *           operands, with the residual check and the S = 10 fallback of ozaki_zgemm (S = 0);
- *           needs selector parameters, synchronises per GEMM, cannot be captured;
- *           ozk_selector_last reports the last GEMM of the solve.
+ *           operands (one stream synchronisation per GEMM to read the choice), followed by
+ *           the probe residual check of ozaki_zgemm (S = 0), recorded on the device.  The
+ *           record is read once when the solve ends; if any check failed, M is restored from
+ *           a copy taken at the start (n x n in the workspace) and the solve is redone with
+ *           every GEMM at S = 10, again checked (OZK_SEL_NO_FALLBACK: no copy, and a failed
+ *           check returns OZK_ERR_RESIDUAL).  Needs selector parameters; cannot be captured.
+ *           ozk_selector_last reports the solve: the largest S chosen (S_selected), the GEMMs
+ *           per S (S_count), the largest residual estimate, and whether it was redone.
  *   S < 0:  both GEMMs are binary64 DMMA GEMMs (the native-precision baseline).
  *   nb <= OZK_NB_MAX (the pivot block is held in shared memory).  nb = 0: for S >= 1 the
  *   width kkr_tau00_autotune picks for one matrix of order n (tuned on the first such call,
@@ -381,10 +392,13 @@ ozk_status_t kkr_tau00_lu(ozk_handle_t handle, int n, int b, void* M, const void
  * nb = 0: the panel and leaf widths an autotuner chose for these sizes, b and S (a cached
  * kkr_tau00_autotune or kkr_tau00_autotune_panels result; without one, the latter runs on the
  * first such call, which must not be captured); see kkr_tau00_batched_panels.
- * S = 0: the slice-count selector chooses S once for the call, from the operands of solve 0's
- * first trailing update (the L and U panels of its unfactored M) at the handle's tolerance;
- * ozk_selector_last reports the choice.  Synchronises; no per-GEMM residual check on this
- * path.  S < 0: every GEMM in binary64 on the DMMA kernel (the native-precision baseline of
+ * S = 0: one slice count serves every launch of the call (a launch covers all solves), so the
+ * selector picks S for the leading block (at most 512 x 512 outputs) of the first trailing
+ * update (the L and U panels of the unfactored M) of up to 8 sampled solves (the largest, the
+ * smallest and solves spread over the call) and the call takes the largest pick; each sampled product is then computed at that S and checked
+ * with the probes, and a failed check sends the whole call to S = 10 (OZK_SEL_NO_FALLBACK:
+ * OZK_ERR_RESIDUAL).  ozk_selector_last reports the choice, the sample size (gemms) and the
+ * largest residual estimate.  Synchronises once per sampled solve.  S < 0: every GEMM in binary64 on the DMMA kernel (the native-precision baseline of
  * the same batched algorithm; L = M_RJ D^-1 goes to per-solve scratch in the handle's
  * workspace; nb = 0 means 32, as in kkr_tau00). */
 ozk_status_t kkr_tau00_batched(ozk_handle_t handle, int nsolves, const int* n, int b,

@@ -34,7 +34,8 @@ class SelectorInfo(ctypes.Structure):
     _fields_ = [("S_selected", ctypes.c_int), ("S_used", ctypes.c_int), ("fallback", ctypes.c_int),
                 ("residual_ok", ctypes.c_int), ("residual", ctypes.c_double),
                 ("residual_selected", ctypes.c_double),
-                ("predicted_log10_err", ctypes.c_float * OZK_SEL_OUTPUTS), ("probe_seed", ctypes.c_uint64)]
+                ("predicted_log10_err", ctypes.c_float * OZK_SEL_OUTPUTS), ("probe_seed", ctypes.c_uint64),
+                ("gemms", ctypes.c_int), ("S_count", ctypes.c_int * OZK_SEL_OUTPUTS)]
 STATUS_NAMES = {1: "ARG", 2: "NONFINITE", 3: "SINGULAR", 4: "TIMEOUT", 5: "CUDA", 6: "RANGE",
                 7: "CAPTURE", 8: "RESIDUAL", 9: "NOFILE"}
 
@@ -227,7 +228,7 @@ class Handle:
     def selector_save(self, path: str):
         _check(lib().ozk_selector_save(self._h, os.fsencode(path)), "ozk_selector_save")
 
-    def selector_configure(self, tol: float = 1e-10, margin: float = 0.3, flags: int = 0):
+    def selector_configure(self, tol: float = 1e-10, margin: float = 0.6, flags: int = 0):
         _check(lib().ozk_selector_configure(self._h, tol, margin, flags), "ozk_selector_configure")
 
     def selector_log_begin(self, features, targets):
@@ -248,7 +249,8 @@ class Handle:
                 "residual_ok": bool(info.residual_ok), "residual": info.residual,
                 "residual_selected": info.residual_selected,
                 "predicted_log10_err": [float(v) for v in info.predicted_log10_err],
-                "probe_seed": int(info.probe_seed)}
+                "probe_seed": int(info.probe_seed), "gemms": info.gemms,
+                "S_count": {3 + o: int(info.S_count[o]) for o in range(OZK_SEL_OUTPUTS) if info.S_count[o]}}
 
     def close(self):
         if self._h:

@@ -93,7 +93,7 @@ struct ozk_context {
   float* sel_p = nullptr;
   int sel_t = 0;
   bool sel_ready = false;
-  double sel_tol = 1e-10, sel_margin = 0.3;
+  double sel_tol = 1e-10, sel_margin = 0.6;
   int sel_flags = 0;
   uint64_t sel_seed = 0x5E1EC7ull, sel_calls = 0;
   void* sel_ws = nullptr;                   // selector scratch (features, probes, products)
@@ -178,6 +178,18 @@ static ozk_status_t ensure_ws(ozk_context* h, size_t bytes) {
 // invalidates graphs captured before.
 constexpr size_t kMaxTables = 4096;
 
+// room for k more tables before a function takes several: a cache flush in the middle would
+// free the tables it already holds
+static ozk_status_t table_room(ozk_context* h, size_t k) {
+  if (h->tables.size() + k <= kMaxTables) return OZK_OK;
+  if (capturing(h->stream)) return set_error(OZK_ERR_CAPTURE, "size-table cache full during stream capture");
+  ozk_status_t st = cuda_check(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+  if (st) return st;
+  for (auto& kv : h->tables) cudaFree(kv.second);
+  h->tables.clear();
+  return OZK_OK;
+}
+
 static ozk_status_t size_table(ozk_context* h, std::vector<int>&& key, const int** out) {
   auto it = h->tables.find(key);
   if (it != h->tables.end()) { *out = it->second; return OZK_OK; }
@@ -246,6 +258,10 @@ struct EmuGemm {
   const Oz2Tables* oz2 = nullptr; int beta = 0; int* resid = nullptr; long long ldres = 0;
   double2* const* crow = nullptr; int crow_b = 0;   // row-block scatter of the output
   const int* crow_n = nullptr;                // per-output order (device), or none
+  const int* crow_perm = nullptr;             // row block a of the plane -> output crow_perm[a]
+  // remapped GEMM problems over the split planes of a uniform batch: problem z (of gbatch)
+  // multiplies rows [remap[2z + 1], + gm[z]) of plane remap[2z] by its first gn[z] columns
+  const int* remap = nullptr; int gbatch = 0; const int* gm = nullptr; const int* gn = nullptr;
   // partial runs: split only the operands in split_sides (1: A, 2: B, 3: both; an operand left
   // out must already be split into this workspace by an earlier run of the same problem), and
   // the slice GEMM only if run_gemm; on `stream` (nullptr: the handle's stream)
@@ -293,7 +309,8 @@ ozk_status_t plan_gemm(const EmuGemm& g, GemmPlan* P) {
   P->offB = off; off = align_up(off + static_cast<size_t>(g.batch) * S * P->rowsB * P->kpad * 2, 1024);
   P->offE = off; off = align_up(off + static_cast<size_t>(g.batch) * P->rowsA * 4, 256);
   P->offF = off; off = align_up(off + static_cast<size_t>(g.batch) * std::max(g.nmax, 1) * 4, 256);
-  P->offT = off; off = align_up(off + (static_cast<size_t>(g.batch) + 1) * 4, 256);   // tile prefix sums
+  P->offT = off;                                                     // tile prefix sums
+  off = align_up(off + (static_cast<size_t>(std::max(g.batch, g.gbatch)) + 1) * 4, 256);
   P->total = off;
   return OZK_OK;
 }
@@ -399,7 +416,11 @@ ozk_status_t run_emulated(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0
   gp.groups = g.groups; gp.status = h->d_status;
   if (single) { gp.m = nullptr; gp.m1 = g.m; gp.n1 = g.n; gp.C1 = g.C; gp.ldc1 = g.ldc; gp.skm1 = g.skm; gp.skn1 = g.skn; }
   else { gp.m = g.tm; gp.n = g.tn; gp.C = g.tC; gp.ldc = g.tldc; gp.skm = g.tskm; gp.skn = g.tskn; }
-  gp.crow = g.crow; gp.crow_b = g.crow_b; gp.crow_n = g.crow_n;
+  gp.crow = g.crow; gp.crow_b = g.crow_b; gp.crow_n = g.crow_n; gp.crow_perm = g.crow_perm;
+  if (g.remap) {
+    gp.remap = reinterpret_cast<const int2*>(g.remap);
+    gp.m = g.gm; gp.n = g.gn; gp.C = nullptr; gp.ldc = nullptr; gp.skm = gp.skn = nullptr;
+  }
   gp.box_m = single ? g.skm : (g.tskm ? g.box_m : 0);
   gp.box_n = single ? g.skn : (g.tskn ? g.box_n : 0);
   int np = 0;
@@ -424,16 +445,17 @@ ozk_status_t run_emulated(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0
     }
   }
   gp.npairs = np;
-  if (!single) {
+  const int gbatch = g.remap ? g.gbatch : g.batch;
+  if (!single || g.remap) {
     // problems of different sizes: every CTA enumerates exactly the tiles of each problem
     int* tp = reinterpret_cast<int*>(ws + P.offT);
     gp.tile_prefix = tp;
-    launch_tile_prefix(gp, P.BN, g.batch, tp, stream);
+    launch_tile_prefix(gp, P.BN, gbatch, tp, stream);
   }
   {
     // algorithmic integer ops: every pair is one real GEMM m x 2n x 2k (8 m n k)
     Prof pr(h, OZK_KIND_SLICE_GEMM, 8.0 * np * smnk, 0.0, stream);
-    launch_slice_gemm(ta, tb, gp, P.BN, g.mmax, g.nmax, g.batch, stream);
+    launch_slice_gemm(ta, tb, gp, P.BN, g.remap ? std::min(g.mmax, 128) : g.mmax, g.nmax, gbatch, stream);
   }
   return cuda_check(cudaGetLastError(), "slice GEMM launch");
 }
@@ -606,8 +628,12 @@ static ozk_status_t sel_log_gemm(ozk_context* h, const EmuGemm& g, const SelScra
   return cuda_check(cudaGetLastError(), "selector log launches");
 }
 
-// S = 0: choose S, compute the product, check it with the probes, fall back to SMAX.
-static ozk_status_t zgemm_auto(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0) {
+// S = 0: choose S, compute the product, check it with the probes, fall back to SMAX.  Inside a
+// solve (defer != null) the check is recorded on the device instead (no second host read, no
+// per-GEMM fallback: the solve is redone at SMAX when any check failed), and force_S > 0 skips
+// the choice (the redone solve, still checked).
+static ozk_status_t zgemm_auto(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0, SelDefer* defer = nullptr,
+                               int force_S = 0) {
   if (!h->sel_ready)
     return set_error(OZK_ERR_ARG, "S = 0 needs selector parameters (ozk_selector_init, _load or _set_params)");
   if (capturing(h->stream))
@@ -621,15 +647,19 @@ static ozk_status_t zgemm_auto(ozk_context* h, const EmuGemm& g, size_t ws_offse
   info.probe_seed = h->sel_seed + h->sel_calls++;
   st = sel_features(h, g.oa, g.ob, m, n, k, g.A, g.lda, g.B, g.ldb, info.probe_seed, s);
   if (st) return st;
-  if (h->sel_log_f && h->sel_log_n < h->sel_log_cap) {
+  if (h->sel_log_f && h->sel_log_n < h->sel_log_cap && force_S == 0) {
     st = sel_log_gemm(h, g, s, ws_offset);
     if (st) return st;
   }
-  launch_mlp_forward(h->sel_p, s.f, 1, nullptr, nullptr, s.Y, h->stream);
-  launch_choose(s.Y, static_cast<float>(std::log10(h->sel_tol) - h->sel_margin), s.aux, h->stream);
-  SelAux aux;
-  st = read_aux(h, s.aux, &aux);
-  if (st) return st;
+  SelAux aux{};
+  if (force_S > 0) {
+    aux.S = force_S;
+  } else {
+    launch_mlp_forward(h->sel_p, s.f, 1, nullptr, nullptr, s.Y, h->stream);
+    launch_choose(s.Y, static_cast<float>(std::log10(h->sel_tol) - h->sel_margin), s.aux, h->stream);
+    st = read_aux(h, s.aux, &aux);
+    if (st) return st;
+  }
   info.S_selected = aux.S;
   for (int o = 0; o < SEL_NO; ++o) info.predicted_log10_err[o] = aux.pred[o];
   EmuGemm d = g;
@@ -648,14 +678,24 @@ static ozk_status_t zgemm_auto(ozk_context* h, const EmuGemm& g, size_t ws_offse
     *r = a2.resid;
     return e;
   };
+  // the 4-probe estimate scatters around the true error: a product passes when its estimate is
+  // at most half the tolerance
+  const double pass = 0.5 * h->sel_tol;
+  if (defer) {
+    d.S = aux.S;
+    st = run_emulated(h, d, ws_offset);
+    if (st) return st;
+    launch_gemv(d.C, d.ldc, m, n, 0, s.X, nullptr, n, s.Wh, s.Wl, s.part, nullptr, 0, h->stream);
+    launch_residual(s.Wh, s.Wl, s.zh, s.zl, m, s.aux, h->stream);
+    launch_defer_check(s.aux, aux.S, force_S == 0, pass, defer, h->stream);
+    if (!direct) launch_axpby(m, n, s.D, m, g.C, g.ldc, g.ar, g.ai, g.br, g.bi, h->stream);
+    return cuda_check(cudaGetLastError(), "deferred check launches");
+  }
   double r = 0.0;
   st = product_and_check(aux.S, &r);
   if (st) return st;
   info.residual_selected = r;
   info.S_used = aux.S;
-  // the 4-probe estimate scatters around the true error: a product passes when its estimate is
-  // at most half the tolerance
-  const double pass = 0.5 * h->sel_tol;
   if (!(r <= pass) && !(h->sel_flags & OZK_SEL_NO_FALLBACK) && aux.S < SEL_SMAX) {
     st = product_and_check(SEL_SMAX, &r);
     if (st) return st;
@@ -1026,10 +1066,15 @@ ozk_status_t kkr_build_m(ozk_handle_t h, int L, int b, const void* t, const void
 
 static std::vector<int> tune_key(int nsolves, const int* n, int b, int S);
 
+static ozk_status_t tau00_single(ozk_context* h, int n, int b, double2* M, const void* t0, void* tau, int S, int nb,
+                                 size_t off_gemm, SelDefer* defer, int force_S);
+
 // tau_00 of one matrix: eliminate panels J = [p, q) from the trailing end, centre last.  Each
 // panel: D^-1 of its pivot block (binary64 Gauss-Jordan), L = M_RJ D^-1 and M_RR -= L M_JR as
 // emulated GEMMs with S slices (S >= 1), with the slice count the selector picks for each GEMM
-// and its residual check (S = 0), or as binary64 DMMA GEMMs (S < 0).
+// and its residual check (S = 0), or as binary64 DMMA GEMMs (S < 0).  With S = 0 the checks are
+// recorded on the device and read once at the end: if any failed, M is restored from a copy
+// taken at the start and the solve is redone with every GEMM at S = 10 (still checked).
 ozk_status_t kkr_tau00(ozk_handle_t h, int n, int b, void* Mv, const void* t0, void* tau, int S, int nb) {
   if (!h || !Mv || !t0 || !tau) return set_error(OZK_ERR_ARG, "null argument");
   if (S > 16) return set_error(OZK_ERR_ARG, "S must be <= 16");
@@ -1059,10 +1104,15 @@ ozk_status_t kkr_tau00(ozk_handle_t h, int n, int b, void* Mv, const void* t0, v
   if (b <= 0 || n <= 0 || n % b || nb < b || nb % b || b > 64 || nb > GJINV_MAX)
     return set_error(OZK_ERR_ARG, "need n % b == 0, b <= 64, b <= nb <= 112, nb % b == 0");
   double2* M = static_cast<double2*>(Mv);
-  // workspace: [D^-1, nb x nb][L scratch, n x nb (DMMA and S = 0)][GEMM workspace (emulated)]
+  // workspace: [D^-1, nb x nb][L scratch, n x nb (DMMA and S = 0)][S = 0: check record, copy
+  // of M][GEMM workspace (emulated)]
   const size_t dinv_bytes = align_up(sizeof(double2) * nb * nb, 1024);
   const size_t ltmp_bytes = (dmma || auto_S) ? align_up(sizeof(double2) * static_cast<size_t>(n) * nb, 1024) : 0;
-  const size_t off_gemm = dinv_bytes + ltmp_bytes;
+  const size_t mat_bytes = sizeof(double2) * static_cast<size_t>(n) * n;
+  const size_t rec_bytes = auto_S ? 1024 : 0;
+  const bool keep_copy = auto_S && !(h->sel_flags & OZK_SEL_NO_FALLBACK);
+  const size_t copy_bytes = keep_copy ? align_up(mat_bytes, 1024) : 0;
+  const size_t off_gemm = dinv_bytes + ltmp_bytes + rec_bytes + copy_bytes;
   {
     size_t need = off_gemm;
     if (!dmma) {
@@ -1077,6 +1127,54 @@ ozk_status_t kkr_tau00(ozk_handle_t h, int n, int b, void* Mv, const void* t0, v
     ozk_status_t st = ensure_ws(h, need);
     if (st) return st;
   }
+  if (!auto_S) return tau00_single(h, n, b, M, t0, tau, S, nb, off_gemm, nullptr, 0);
+  uint8_t* base = static_cast<uint8_t*>(h->ws);
+  SelDefer* rec = reinterpret_cast<SelDefer*>(base + dinv_bytes + ltmp_bytes);
+  double2* Mcopy = reinterpret_cast<double2*>(base + dinv_bytes + ltmp_bytes + rec_bytes);
+  auto run_checked = [&](int force_S, SelDefer* out) -> ozk_status_t {
+    ozk_status_t e = cuda_check(cudaMemsetAsync(rec, 0, sizeof(SelDefer), h->stream), "clear check record");
+    if (!e) e = tau00_single(h, n, b, M, t0, tau, 0, nb, off_gemm, rec, force_S);
+    if (!e) e = cuda_check(cudaMemcpyAsync(out, rec, sizeof(SelDefer), cudaMemcpyDeviceToHost, h->stream),
+                           "read check record");
+    if (!e) e = cuda_check(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    return e;
+  };
+  ozk_status_t st = OZK_OK;
+  if (keep_copy) st = cuda_check(cudaMemcpyAsync(Mcopy, M, mat_bytes, cudaMemcpyDeviceToDevice, h->stream), "copy M");
+  SelDefer r1{};
+  if (!st) st = run_checked(0, &r1);
+  if (st) return st;
+  ozk_selector_info info{};
+  for (int o = 0; o < SEL_NO; ++o) {
+    info.S_count[o] = r1.count[o];
+    info.gemms += r1.count[o];
+    if (r1.count[o]) info.S_selected = SEL_SMIN + o;
+    info.predicted_log10_err[o] = r1.pred[o];
+  }
+  info.S_used = info.S_selected;
+  info.residual = info.residual_selected = r1.max_resid;
+  info.residual_ok = r1.failed ? 0 : 1;
+  info.probe_seed = h->sel_seed + h->sel_calls - 1;
+  if (r1.failed && keep_copy) {
+    SelDefer r2{};
+    st = cuda_check(cudaMemcpyAsync(M, Mcopy, mat_bytes, cudaMemcpyDeviceToDevice, h->stream), "restore M");
+    if (!st) st = run_checked(SEL_SMAX, &r2);
+    if (st) return st;
+    info.S_used = SEL_SMAX;
+    info.fallback = 1;
+    info.residual = r2.max_resid;
+    info.residual_ok = r2.failed ? 0 : 1;
+  }
+  h->sel_last = info;
+  if (r1.failed && !keep_copy)
+    return set_error(OZK_ERR_RESIDUAL, "a residual check of the solve failed and fallback is disabled");
+  return OZK_OK;
+}
+
+static ozk_status_t tau00_single(ozk_context* h, int n, int b, double2* M, const void* t0, void* tau, int S, int nb,
+                                 size_t off_gemm, SelDefer* defer, int force_S) {
+  const bool dmma = S < 0, auto_S = S == 0;
+  const size_t dinv_bytes = align_up(sizeof(double2) * nb * nb, 1024);
   double2* Dinv = static_cast<double2*>(h->ws);
   double2* Ltmp = reinterpret_cast<double2*>(static_cast<uint8_t*>(h->ws) + dinv_bytes);
   for (int q = n; q > b;) {
@@ -1110,12 +1208,12 @@ ozk_status_t kkr_tau00(ozk_handle_t h, int n, int b, void* Mv, const void* t0, v
         // the selector may recompute a product at S = 10, so L goes to the scratch (its operand
         // M_RJ stays intact) and is copied over M_RJ afterwards
         g1.C = Ltmp; g1.ldc = r;
-        st = zgemm_auto(h, g1, off_gemm);
+        st = zgemm_auto(h, g1, off_gemm, defer, force_S);
         if (!st)
           st = cuda_check(cudaMemcpy2DAsync(Lp, sizeof(double2) * n, Ltmp, sizeof(double2) * r, sizeof(double2) * r,
                                             w, cudaMemcpyDeviceToDevice, h->stream),
                           "copy L panel");
-        if (!st) st = zgemm_auto(h, g2, off_gemm);
+        if (!st) st = zgemm_auto(h, g2, off_gemm, defer, force_S);
       }
       if (st) return st;
     } else {
@@ -1299,6 +1397,10 @@ static ozk_status_t build_m_shared_impl(ozk_context* h, int natoms, const int* L
   const int* dL = nullptr;
   const int* dn = nullptr;
   double sum_n2 = static_cast<double>(natoms) * n * n;       // useful outputs: sum of n_a^2
+  {
+    ozk_status_t st = table_room(h, 8);
+    if (st) return st;
+  }
   if (Lh) {
     std::vector<int> nv(natoms);
     sum_n2 = 0;
@@ -1308,9 +1410,45 @@ static ozk_status_t build_m_shared_impl(ozk_context* h, int natoms, const int* L
     st = size_table(h, std::move(nv), &dn);
     if (st) return st;
   }
+  // mixed sizes: the atoms stacked by decreasing LIZ (ties in input order), and block row i
+  // cut into problems of up to 128 stacked rows, each as wide as its first (largest) atom: the
+  // stacked rows of atoms without block row i and the columns past an atom's order are never
+  // enumerated as tiles (only their rows inside a partly used tile are, and are not written)
+  const int* dperm = nullptr;
+  const int* dremap = nullptr;
+  const int* dgm = nullptr;
+  const int* dgn = nullptr;
+  int nprob = 0;
+  if (Lh && natoms > 1) {
+    std::vector<int> perm(natoms);
+    for (int a = 0; a < natoms; ++a) perm[a] = a;
+    std::stable_sort(perm.begin(), perm.end(), [&](int x, int y) { return Lh[x] > Lh[y]; });
+    std::vector<int> remap, gm, gn;
+    for (int i = 0; i < L; ++i) {
+      int cnt = 0;                                   // atoms with block row i: a prefix of the order
+      while (cnt < natoms && Lh[perm[cnt]] > i) ++cnt;
+      const long long live = static_cast<long long>(cnt) * b;
+      for (long long r0 = 0; r0 < live; r0 += 128) {
+        remap.push_back(i);
+        remap.push_back(static_cast<int>(r0));
+        gm.push_back(static_cast<int>(std::min<long long>(128, live - r0)));
+        gn.push_back(Lh[perm[r0 / b]] * b);
+      }
+    }
+    nprob = static_cast<int>(gm.size());
+    ozk_status_t st = size_table(h, std::move(perm), &dperm);
+    if (!st) st = size_table(h, std::move(remap), &dremap);
+    if (!st) st = size_table(h, std::move(gm), &dgm);
+    if (!st) st = size_table(h, std::move(gn), &dgn);
+    if (st) return st;
+  }
   EmuGemm g;
   g.oa = {0, 0}; g.ob = {0, 0}; g.batch = L;
   g.mmax = g.m = static_cast<int>(rows); g.nmax = g.n = static_cast<int>(n); g.kmax = g.k = b;
+  if (dremap) {
+    g.remap = dremap; g.gbatch = nprob; g.gm = dgm; g.gn = dgn;
+    g.crow_perm = dperm;
+  }
   g.lda = static_cast<int>(rows); g.zsA = rows * b;
   g.B = static_cast<const double2*>(G); g.ldb = ldg; g.zsB = b;
   g.C = nullptr; g.ldc = static_cast<int>(n);
@@ -1328,7 +1466,7 @@ static ozk_status_t build_m_shared_impl(ozk_context* h, int natoms, const int* L
   g.A = stack;
   {
     Prof pr(h, OZK_KIND_BUILD_M, 0.0, 32.0 * static_cast<double>(L) * rows * b);
-    launch_stack_t(reinterpret_cast<const double2* const*>(t), dL, natoms, L, b, stack, h->stream);
+    launch_stack_t(reinterpret_cast<const double2* const*>(t), dL, dperm, natoms, L, b, stack, h->stream);
   }
   st = cuda_check(cudaGetLastError(), "stack_t launch");
   if (st) return st;
@@ -1871,38 +2009,125 @@ ozk_status_t kkr_tau00_autotune_panels(ozk_handle_t h, int nsolves, const int* n
   return OZK_OK;
 }
 
-// S = 0 for a batched solve: the selector's choice for the operands of solve 0's first
-// trailing update (the L panel M[0:p, p:q] and the U panel M[p:q, 0:p] of the unfactored M,
-// q = n_0, p = max(q - nb, b)), made once for the whole call.
-static ozk_status_t select_S_for_solves(ozk_context* h, void* const* M, const int* n, int b, int nb, int* S_out) {
+// S = 0 for a batched solve.  One slice count serves every GEMM launch of the call (a launch
+// covers all solves), so it is chosen from a sample of up to 8 solves: the largest, the
+// smallest and solves spread over the call.  For each sampled solve the selector picks S for
+// the leading block (at most 512 x 512 outputs) of its first trailing update (L panel
+// M[0:p, p:q] times U panel M[p:q, 0:p] of the unfactored M, q = n_i, p = max(q - w, b)); the
+// call takes the largest pick.  Every sampled product is then computed at that S and checked
+// with the probes (recorded on the device, read once); if any check fails the call runs at
+// S = 10.  The block bounds the check, whose compensated binary64 probe products cost
+// O(outputs x probes).
+constexpr int SEL_BATCH_SAMPLES = 8;
+constexpr int SEL_BATCH_BLOCK = 512;
+static ozk_status_t select_S_for_solves(ozk_context* h, int nsolves, void* const* M, const int* n, int b, int w,
+                                        int* S_out) {
   if (!h->sel_ready)
     return set_error(OZK_ERR_ARG, "S = 0 needs selector parameters (ozk_selector_init, _load or _set_params)");
   if (capturing(h->stream)) return set_error(OZK_ERR_CAPTURE, "S = 0 reads the selector's choice and cannot be captured");
-  void* m0 = nullptr;
-  ozk_status_t st = cuda_check(cudaMemcpy(&m0, M, sizeof(void*), cudaMemcpyDeviceToHost), "read M[0]");
+  std::vector<void*> mp(nsolves);
+  ozk_status_t st = cuda_check(cudaMemcpy(mp.data(), M, sizeof(void*) * nsolves, cudaMemcpyDeviceToHost), "read M");
   if (st) return st;
-  const int n0 = n[0];
-  const int q = n0, p = std::max(q - (nb > 0 ? nb : 64), b);
-  if (q <= b || p <= 0) { *S_out = SEL_SMAX; return OZK_OK; }
-  const double2* M0 = static_cast<const double2*>(m0);
-  SelScratch sc;
-  st = sel_scratch(h, p, p, q - p, false, &sc);
-  if (st) return st;
+  std::vector<int> pick;
+  auto add = [&](int i) {
+    if (n[i] > b && std::find(pick.begin(), pick.end(), i) == pick.end()) pick.push_back(i);
+  };
+  add(static_cast<int>(std::max_element(n, n + nsolves) - n));
+  add(static_cast<int>(std::min_element(n, n + nsolves) - n));
+  for (int j = 0; j < SEL_BATCH_SAMPLES && static_cast<int>(pick.size()) < SEL_BATCH_SAMPLES; ++j)
+    add(static_cast<int>((static_cast<long long>(j) * nsolves) / SEL_BATCH_SAMPLES));
   ozk_selector_info info{};
-  info.probe_seed = h->sel_seed + h->sel_calls++;
-  st = sel_features(h, OpFlags{0, 0}, OpFlags{0, 0}, p, p, q - p, M0 + static_cast<long long>(p) * n0, n0, M0 + p, n0,
-                    info.probe_seed, sc);
+  if (pick.empty()) {
+    info.S_selected = info.S_used = SEL_SMAX;
+    h->sel_last = info;
+    *S_out = SEL_SMAX;
+    return OZK_OK;
+  }
+  const int wp = w > 0 ? w : 64;
+  auto gemm_of = [&](int i) {
+    EmuGemm g;
+    const int q = n[i], p = std::max(q - wp, b);
+    const double2* Mi = static_cast<const double2*>(mp[i]);
+    g.oa = {0, 0}; g.ob = {0, 0}; g.batch = 1;
+    const int pb = std::min(p, SEL_BATCH_BLOCK);
+    g.mmax = g.m = pb; g.nmax = g.n = pb; g.kmax = g.k = q - p;
+    g.A = Mi + static_cast<long long>(p) * q; g.lda = q; g.B = Mi + p; g.ldb = q;
+    g.ar = 1; g.ai = 0; g.br = 0; g.bi = 0;
+    g.pair_mode = OZK_PAIRS_TRI;
+    return g;
+  };
+  int S = SEL_SMIN;
+  for (int i : pick) {
+    const EmuGemm g = gemm_of(i);
+    SelScratch sc;
+    st = sel_scratch(h, g.m, g.n, g.k, false, &sc);
+    if (!st) {
+      info.probe_seed = h->sel_seed + h->sel_calls++;
+      st = sel_features(h, g.oa, g.ob, g.m, g.n, g.k, g.A, g.lda, g.B, g.ldb, info.probe_seed, sc);
+    }
+    if (st) return st;
+    launch_mlp_forward(h->sel_p, sc.f, 1, nullptr, nullptr, sc.Y, h->stream);
+    launch_choose(sc.Y, static_cast<float>(std::log10(h->sel_tol) - h->sel_margin), sc.aux, h->stream);
+    SelAux aux;
+    st = read_aux(h, sc.aux, &aux);
+    if (st) return st;
+    S = std::max(S, aux.S);
+    if (i == pick.front())
+      for (int o = 0; o < SEL_NO; ++o) info.predicted_log10_err[o] = aux.pred[o];
+  }
+  info.S_selected = info.S_used = S;
+  // the checks: each sampled product at S into the scratch D, its record in the selector log
+  // scratch (the GEMM workspace at offset 0 is free before the solve starts)
+  SelDefer* rec = nullptr;
+  {
+    const size_t need = 256;
+    if (h->sel_log_ws_bytes < need) {
+      st = cuda_check(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+      if (st) return st;
+      if (h->sel_log_ws) cudaFree(h->sel_log_ws);
+      h->sel_log_ws = nullptr;
+      h->sel_log_ws_bytes = 0;
+      st = cuda_check(cudaMalloc(&h->sel_log_ws, need), "cudaMalloc(check record)");
+      if (st) return st;
+      h->sel_log_ws_bytes = need;
+    }
+    rec = static_cast<SelDefer*>(h->sel_log_ws);
+  }
+  SelDefer r{};
+  st = cuda_check(cudaMemsetAsync(rec, 0, sizeof(SelDefer), h->stream), "clear check record");
+  for (int i : pick) {
+    if (st) return st;
+    EmuGemm g = gemm_of(i);
+    SelScratch sc;
+    st = sel_scratch(h, g.m, g.n, g.k, true, &sc);
+    if (st) return st;
+    st = sel_features(h, g.oa, g.ob, g.m, g.n, g.k, g.A, g.lda, g.B, g.ldb, h->sel_seed + h->sel_calls++, sc);
+    if (st) return st;
+    g.C = sc.D; g.ldc = g.m; g.S = S; g.mode = -1;
+    st = run_emulated(h, g, 0);
+    if (st) return st;
+    launch_gemv(sc.D, g.m, g.m, g.n, 0, sc.X, nullptr, g.n, sc.Wh, sc.Wl, sc.part, nullptr, 0, h->stream);
+    launch_residual(sc.Wh, sc.Wl, sc.zh, sc.zl, g.m, sc.aux, h->stream);
+    launch_defer_check(sc.aux, S, false, 0.5 * h->sel_tol, rec, h->stream);
+    st = cuda_check(cudaGetLastError(), "check launches");
+  }
+  if (!st) st = cuda_check(cudaMemcpyAsync(&r, rec, sizeof(SelDefer), cudaMemcpyDeviceToHost, h->stream), "read record");
+  if (!st) st = cuda_check(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
   if (st) return st;
-  launch_mlp_forward(h->sel_p, sc.f, 1, nullptr, nullptr, sc.Y, h->stream);
-  launch_choose(sc.Y, static_cast<float>(std::log10(h->sel_tol) - h->sel_margin), sc.aux, h->stream);
-  SelAux aux;
-  st = read_aux(h, sc.aux, &aux);
-  if (st) return st;
-  info.S_selected = info.S_used = aux.S;
-  info.residual = info.residual_selected = -1.0;      // no per-GEMM check on the batched path
-  for (int o = 0; o < SEL_NO; ++o) info.predicted_log10_err[o] = aux.pred[o];
+  info.gemms = static_cast<int>(pick.size());
+  info.S_count[S - SEL_SMIN] = info.gemms;
+  info.residual = info.residual_selected = r.max_resid;
+  info.residual_ok = r.failed ? 0 : 1;
+  if (r.failed) {
+    if (h->sel_flags & OZK_SEL_NO_FALLBACK) {
+      h->sel_last = info;
+      return set_error(OZK_ERR_RESIDUAL, "a sampled product failed its residual check and fallback is disabled");
+    }
+    info.S_used = SEL_SMAX;
+    info.fallback = 1;
+  }
   h->sel_last = info;
-  *S_out = aux.S;
+  *S_out = info.S_used;
   return OZK_OK;
 }
 
@@ -1911,7 +2136,7 @@ ozk_status_t kkr_tau00_batched_panels(ozk_handle_t h, int nsolves, const int* n,
   if (!h || !n) return set_error(OZK_ERR_ARG, "null argument");
   if (S == 0 && nsolves > 0) {
     if (!M || n[0] <= 0) return set_error(OZK_ERR_ARG, "bad solve 0");
-    ozk_status_t st = select_S_for_solves(h, M, n, b, w > 0 ? w : W, &S);
+    ozk_status_t st = select_S_for_solves(h, nsolves, M, n, b, w > 0 ? w : W, &S);
     if (st) return st;
   }
   if (W == 0 && nsolves > 0 && S < 0) W = w = std::min(GJINV_MAX, (32 + b - 1) / b * b);   // binary64: as kkr_tau00

@@ -554,8 +554,10 @@ void launch_build_m_batched(const int* L, int b, const double2* const* t, const 
 }
 
 // Stacked left operands of the shared-G build: problem i is the (natoms b) x b column-major
-// matrix whose rows a b .. a b + b - 1 are t_a's block i (t_a: L column-major b x b blocks).
-__global__ void stack_t_kernel(const double2* const* t, const int* Lt, int natoms, int L, int b, double2* out) {
+// matrix whose rows a b .. a b + b - 1 are block i of t_{perm[a]} (t_a: L column-major b x b
+// blocks; perm null: the identity).
+__global__ void stack_t_kernel(const double2* const* t, const int* Lt, const int* perm, int natoms, int L, int b,
+                               double2* out) {
   const long long rows = static_cast<long long>(natoms) * b, per = rows * b;
   const long long tot = per * L;
   for (long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; idx < tot;
@@ -564,7 +566,8 @@ __global__ void stack_t_kernel(const double2* const* t, const int* Lt, int natom
     const long long rem = idx - i * per;
     const int c = static_cast<int>(rem / rows);
     const int ar = static_cast<int>(rem - c * rows);
-    const int a = ar / b, r = ar - a * b;
+    const int as = ar / b, r = ar - as * b;
+    const int a = perm ? perm[as] : as;
     // block rows past an atom's own LIZ are zero (that atom's rows of the product are not kept)
     out[idx] = (Lt && i >= Lt[a]) ? make_double2(0.0, 0.0)
                                   : t[a][static_cast<long long>(i) * b * b + r + static_cast<long long>(c) * b];
@@ -633,10 +636,11 @@ void launch_fill_test(double2* const* M, const int* n, int nsolves, int b, doubl
   record_launch();
 }
 
-void launch_stack_t(const double2* const* t, const int* Lt, int natoms, int L, int b, double2* out, cudaStream_t st) {
+void launch_stack_t(const double2* const* t, const int* Lt, const int* perm, int natoms, int L, int b, double2* out,
+                    cudaStream_t st) {
   const long long tot = static_cast<long long>(natoms) * b * b * L;
   const unsigned blocks = static_cast<unsigned>(std::min<long long>((tot + 255) / 256, 8192));
-  stack_t_kernel<<<blocks, 256, 0, st>>>(t, Lt, natoms, L, b, out);
+  stack_t_kernel<<<blocks, 256, 0, st>>>(t, Lt, perm, natoms, L, b, out);
   record_launch();
 }
 

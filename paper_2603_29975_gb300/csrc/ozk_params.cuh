@@ -99,6 +99,12 @@ struct GemmParams {
   // the output crow[r / crow_b], whose order and leading dimension are crow_n[r / crow_b]
   // (or ldc1 for every output when crow_n is null); rows past that order are not written
   double2* const* crow; int crow_b; const int* crow_n;
+  // crow_perm (optional): row block a of the operand plane belongs to output crow[crow_perm[a]]
+  const int* crow_perm;
+  // remap (optional, with p.m / p.n tables): problem z reads operand plane remap[z].x (left
+  // and right operands, row and column exponents) from plane row remap[z].y on, so that
+  // several problems share one split; with crow, its output rows follow that plane row
+  const int2* remap;
   // EPI_RESIDUES: group g of problem z, row r, stacked column c at resid[((z G + g) m1 + r) ldres + c]
   int* resid; long long ldres;
   int diag_pairs;                // 1: the pair list is not the tri/full set (runtime issue)
@@ -169,7 +175,9 @@ void launch_build_m_batched(const int* L, int b, const double2* const* t, const 
                             int nmax, int batch, cudaStream_t st);
 void launch_scale(int m, int n, double2* C, long long ldc, double br, double bi, cudaStream_t st);
 // Lt (device, per atom block counts) may be null: every atom has L blocks
-void launch_stack_t(const double2* const* t, const int* Lt, int natoms, int L, int b, double2* out, cudaStream_t st);
+// perm (optional): position a of the stack holds atom perm[a]
+void launch_stack_t(const double2* const* t, const int* Lt, const int* perm, int natoms, int L, int b, double2* out,
+                    cudaStream_t st);
 void launch_fill_test(double2* const* M, const int* n, int nsolves, int b, double2* t0, cudaStream_t st);
 void launch_contour_trace(const double2* const* tau, int nsolves, int b, const double2* w, double2* tr, double2* out,
                           cudaStream_t st);
@@ -230,6 +238,11 @@ void launch_mlp_train(float* P, float* gbuf, float* m, float* v, int t, float lr
 void launch_mlp_grad_only(const float* P, float* gbuf, const float* X, const float* T, int N, float* Z1, float* Z2,
                           float* Y, float* dY, float* dZ2, float* dZ1, cudaStream_t st);
 void launch_choose(const float* Y, float lim, SelAux* aux, cudaStream_t st);
+// Record of the deferred residual checks of the S = 0 GEMMs of one solve: failed = 1 once a
+// residual estimate exceeds its bound (or is not finite), the GEMMs counted per S = 3..10, the
+// largest residual estimate and the predictions of the last GEMM.
+struct SelDefer { int failed; int count[SEL_NO]; double max_resid; float pred[SEL_NO]; };
+void launch_defer_check(const SelAux* aux, int S, bool with_pred, double pass, SelDefer* rec, cudaStream_t st);
 // *dst = log10(*rel) floored at -17 (selector training targets)
 void launch_log_err(const double* rel, float* dst, cudaStream_t st);
 

@@ -625,6 +625,17 @@ __global__ void choose_kernel(const float* Y, float lim, SelAux* aux) {
   aux->S = S;
 }
 
+// deferred check of one GEMM of a solve (S its slice count): no host read in between
+__global__ void defer_check_kernel(const SelAux* aux, int S, int with_pred, double pass, SelDefer* rec) {
+  if (threadIdx.x) return;
+  const double r = aux->resid;
+  if (!(r <= pass)) rec->failed = 1;
+  if (S >= SEL_SMIN && S <= SEL_SMAX) rec->count[S - SEL_SMIN] += 1;
+  if (!(r <= rec->max_resid)) rec->max_resid = r;
+  if (with_pred)
+    for (int o = 0; o < SEL_NO; ++o) rec->pred[o] = aux->pred[o];
+}
+
 // ------------------------------------------------------------------ launchers
 static unsigned blocks(long long n, int t) { return static_cast<unsigned>((n + t - 1) / t); }
 
@@ -739,6 +750,11 @@ void launch_log_err(const double* rel, float* dst, cudaStream_t st) {
 
 void launch_choose(const float* Y, float lim, SelAux* aux, cudaStream_t st) {
   choose_kernel<<<1, 32, 0, st>>>(Y, lim, aux);
+  record_launch();
+}
+
+void launch_defer_check(const SelAux* aux, int S, bool with_pred, double pass, SelDefer* rec, cudaStream_t st) {
+  defer_check_kernel<<<1, 32, 0, st>>>(aux, S, with_pred ? 1 : 0, pass, rec);
   record_launch();
 }
 

@@ -266,12 +266,15 @@ struct EpiCtx {
 
 // output matrix, row offset, matrix row, leading dimension and column count of tile row
 // `row` of problem z; clears rowok for rows past their matrix
-__device__ __forceinline__ void out_row(const GemmParams& p, bool single, int z, int row, bool& rowok, double2*& Cz,
-                                        long long& crow, int& grow, long long& ldc, int& jlim) {
+// (za, ra: the operand plane and first plane row of the problem; z, 0 without a remap table)
+__device__ __forceinline__ void out_row(const GemmParams& p, bool single, int z, int row, int za, int ra, bool& rowok,
+                                        double2*& Cz, long long& crow, int& grow, long long& ldc, int& jlim) {
   if (p.crow) {
-    const int a = row / p.crow_b, rl = row - a * p.crow_b;
+    const int pr = ra + row;                                  // row of the operand plane
+    const int as = pr / p.crow_b, rl = pr - as * p.crow_b;
+    const int a = p.crow_perm ? (rowok ? p.crow_perm[as] : 0) : as;
     Cz = rowok ? p.crow[a] : nullptr;
-    crow = static_cast<long long>(z) * p.crow_b + rl;
+    crow = static_cast<long long>(za) * p.crow_b + rl;
     grow = static_cast<int>(crow);
     if (p.crow_n) {
       const int na = rowok ? p.crow_n[a] : 0;
@@ -726,6 +729,8 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         int z, m0, n0, m_z, n2_z;
         if (!tile_of(t, z, m0, n0, m_z, n2_z)) continue;
+        int za = z, ra = 0;
+        if (p.remap) { const int2 rm = p.remap[z]; za = rm.x; ra = rm.y; }
         for (int kb = 0; kb < nkb; ++kb, ++kbc) {
           const int stage = kbc % nstage;
           const uint32_t ph = kbc / nstage;
@@ -735,8 +740,8 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
           }
           uint8_t* sa = smem + stage * stage_bytes;
           mbar_arrive_expect_tx(&full[stage], stage_bytes);
-          tma_load_3d(&tmA, sa, &full[stage], kb * 16, m0, z * S);
-          tma_load_3d(&tmB, sa + a_bytes, &full[stage], kb * 16, n0, z * S);
+          tma_load_3d(&tmA, sa, &full[stage], kb * 16, ra + m0, za * S);
+          tma_load_3d(&tmB, sa + a_bytes, &full[stage], kb * 16, n0, za * S);
         }
       }
       if (!ok || *abort_flag) {
@@ -810,16 +815,18 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       int z, m0, n0, m_z, n2_z;
       if (!tile_of(t, z, m0, n0, m_z, n2_z)) continue;
+      int za = z, ra = 0;
+      if (p.remap) { const int2 rm = p.remap[z]; za = rm.x; ra = rm.y; }
       const int row = m0 + quad * 32 + lane;
       const bool rowok = row < m_z;
       if constexpr (COLS == 16) {
         if (G <= 8 && p.mode != EPI_GROUPS && p.mode != EPI_RESIDUES) {
           EpiCtx x;
-          x.row = row; x.z = z; x.m_z = m_z; x.n2_z = n2_z; x.n0 = n0; x.c0 = c0; x.tbase = tbase;
+          x.row = row; x.z = za; x.m_z = m_z; x.n2_z = n2_z; x.n0 = n0; x.c0 = c0; x.tbase = tbase;
           x.rowok = rowok;
           x.skip_n = (row < (single ? p.skm1 : (p.skm ? p.skm[z] : 0))) ? (single ? p.skn1 : p.skn[z]) : 0;
-          out_row(p, single, z, row, x.rowok, x.Cz, x.crow, x.grow, x.ldc, x.jlim);
-          x.er = x.rowok ? p.e[z * p.e_stride + row] + p.base_exp : 0;
+          out_row(p, single, z, row, za, ra, x.rowok, x.Cz, x.crow, x.grow, x.ldc, x.jlim);
+          x.er = x.rowok ? p.e[za * p.e_stride + ra + row] + p.base_exp : 0;
           ChunkWait cw{acc_full, nchunks, &cc, p.status, abort_flag};
           // short K (at most two K-blocks per tile): the epilogue bounds the tile, and the
           // two-halves variant with streamed TMEM loads is faster (1.18x on 1024 x 1040 x 16
@@ -918,15 +925,16 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       long long crow = 0, ldc = 0;
       int grow = 0, jlim = 0;
       bool rowok2 = rowok;
-      if (p.mode != EPI_GROUPS && p.mode != EPI_RESIDUES) out_row(p, single, z, row, rowok2, Cz, crow, grow, ldc, jlim);
+      if (p.mode != EPI_GROUPS && p.mode != EPI_RESIDUES)
+        out_row(p, single, z, row, za, ra, rowok2, Cz, crow, grow, ldc, jlim);
       if (p.mode != EPI_GROUPS && p.mode != EPI_RESIDUES && rowok2) {
-        const int er = p.e[z * p.e_stride + row] + p.base_exp;
+        const int er = p.e[za * p.e_stride + ra + row] + p.base_exp;
         const int skip_n = (row < (single ? p.skm1 : (p.skm ? p.skm[z] : 0))) ? (single ? p.skn1 : p.skn[z]) : 0;
 #pragma unroll
         for (int j = 0; j < COLS; j += 2) {
           const int jc = (n0 + c0 + j) >> 1;          // complex column
           if (2 * jc < n2_z && jc >= skip_n && jc < jlim) {
-            const int E = er + p.f[z * p.f_stride + jc];
+            const int E = er + p.f[za * p.f_stride + jc];
             const double zr = round_scaled_dev(T[j], E);
             const double zi = round_scaled_dev(T[j + 1], E);
             double2* dst = Cz + crow + jc * ldc;

@@ -107,16 +107,16 @@ def generate_instances(count, seed, kkr_sizes=(15, 27, 51, 65), energies=4):
     return out
 
 
-def contour_solves(natoms=256, energies=(0, 4, 8, 12, 16, 20, 24, 28), stride=4, offset=0):
-    """(atom, LIZ sites, energy index) of single solves drawn from the batched contour workload:
-    every `stride`-th of its `natoms` atoms (LIZ sizes drawn from 27..169 sites) at the given
-    contour points."""
+def contour_solves(atoms, energies, natoms=256):
+    """(atom, LIZ sites, energy index) of single solves drawn from the batched contour workload
+    (`natoms` atoms with LIZ sizes drawn from 27..169 sites, 32 contour points): the given
+    atoms at the given contour points."""
     import synth
     Ls = [int(v) for v in synth.liz_sizes(natoms)]
-    return [(a, Ls[a], z) for a in range(offset, natoms, stride) for z in energies]
+    return [(a, Ls[a], z) for a in atoms for z in energies]
 
 
-def log_contour(ozk, h, solves, nbs=(32, 64), capacity=200000):
+def log_contour(ozk, h, solves, nbs=(32, 64), capacity=200000, seconds=None):
     """Training rows logged from the GEMMs of block-LU solves of the contour workload.  Every
     (atom, energy) M = I - t G (binary64 build on the GPU, G of the 169-site LIZ at that contour
     point, the atom's leading block) is solved by kkr_tau00 with S = 0 and panel widths cycling
@@ -133,8 +133,9 @@ def log_contour(ozk, h, solves, nbs=(32, 64), capacity=200000):
     T = torch.zeros((capacity, 8), dtype=torch.float32, device="cuda")
     groups = []
     done = 0
+    t_start = time.time()
     for i, (a, L, z) in enumerate(solves):
-        if done >= capacity:
+        if done >= capacity or (seconds is not None and time.time() - t_start > seconds):
             break
         n = L * b
         t = synth.kkr_t(L, b, atom=a)
@@ -165,7 +166,7 @@ def solve_times(ozk, h, solves, S_list, nb=64, tol=1e-10):
     zs = sorted({z for _, _, z in solves})
     Gs = dict(zip(zs, synth.kkr_contour_G(169, b, [complex(E[z]) for z in zs])))
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    h.selector_configure(tol=tol, margin=0.3)
+    h.selector_configure(tol=tol)
     out = {str(S): {"ms_total": 0.0, "max_rel_err_vs_dmma": 0.0} for S in [0] + list(S_list)}
     for a, L, z in solves:
         n = L * b
@@ -192,6 +193,13 @@ def solve_times(ozk, h, solves, S_list, nb=64, tol=1e-10):
             e = float(np.linalg.norm(tau - ref) / np.linalg.norm(ref))
             out[str(S)]["ms_total"] += ms
             out[str(S)]["max_rel_err_vs_dmma"] = max(out[str(S)]["max_rel_err_vs_dmma"], e)
+            if S == 0:
+                info = h.selector_last()
+                o = out["0"]
+                o["redone_at_S10"] = o.get("redone_at_S10", 0) + int(info["fallback"])
+                hist = o.setdefault("gemms_per_S", {})
+                for k, v in info["S_count"].items():
+                    hist[str(k)] = hist.get(str(k), 0) + v
     if h.status():
         raise RuntimeError("device status set in the timed solves")
     return out
@@ -261,7 +269,7 @@ def choose(pred, tol, margin):
     return SMAX
 
 
-def evaluate(ozk, h, instances, X, T, times, tol=1e-10, margin=0.3, run_auto=True):
+def evaluate(ozk, h, instances, X, T, times, tol=1e-10, margin=0.6, run_auto=True):
     """Selector quality on labelled instances: chosen S, violations before the residual check
     (label of the chosen S above tol) and after it (the S = 0 call's product against the
     reference), and time against fixed S."""
@@ -308,6 +316,9 @@ def evaluate(ozk, h, instances, X, T, times, tol=1e-10, margin=0.3, run_auto=Tru
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--contour", action="store_true",
+                    help="add rows logged from single solves of the 256-atom contour workload")
+    ap.add_argument("--log-seconds", type=float, default=300.0)
     ap.add_argument("--count", type=int, default=2400)
     ap.add_argument("--seed", type=int, default=20260401)
     ap.add_argument("--steps", type=int, default=4000)
@@ -327,11 +338,38 @@ def main(argv=None):
     X, T, times = label(ozk, h, inst)
     t2 = time.time()
     tr, te = split(inst, seed=args.seed)
-    hist = train(ozk, h, X[tr], T[tr], steps=args.steps, lr=args.lr, seed=args.seed)
+    Xtr, Ttr = X[tr], T[tr]
+    rep = {"generate_s": t1 - t0, "label_s": t2 - t1}
+    if args.contour:
+        # atoms a = 3 (mod 4) are held out; the others are logged at every 4th contour point in
+        # a seeded order until the time budget ends
+        rng = np.random.default_rng(args.seed)
+        train_solves = contour_solves([a for a in range(256) if a % 4 != 3], range(0, 32, 4))
+        rng.shuffle(train_solves)
+        test_atoms = [a for a in range(256) if a % 4 == 3][::4]
+        test_log = contour_solves(test_atoms, (2, 10, 18, 26))
+        test_time = contour_solves(test_atoms, (6, 22))
+        h.selector_load()                      # any parameters: the S = 0 solves only carry the log
+        h.selector_configure(tol=args.tol)
+        t2 = time.time()
+        Xc, Tc, gc = log_contour(ozk, h, train_solves, seconds=args.log_seconds)
+        t3 = time.time()
+        Xct, Tct, gct = log_contour(ozk, h, test_log)
+        rep.update({"contour_log_s": t3 - t2, "contour_train_rows": int(len(Xc)),
+                    "contour_train_atoms": int(len(set(gc.tolist()))), "contour_test_rows": int(len(Xct)),
+                    "contour_test_atoms": int(len(set(gct.tolist())))})
+        Xtr, Ttr = np.concatenate([Xtr, Xc]), np.concatenate([Ttr, Tc])
+        t2 = time.time()
+    hist = train(ozk, h, Xtr, Ttr, steps=args.steps, lr=args.lr, seed=args.seed)
     t3 = time.time()
-    rep = {"generate_s": t1 - t0, "label_s": t2 - t1, "train_s": t3 - t2, "train_loss": hist,
-           "train": evaluate(ozk, h, [inst[i] for i in tr], X[tr], T[tr], times[tr], tol=args.tol, run_auto=False),
-           "test": evaluate(ozk, h, [inst[i] for i in te], X[te], T[te], times[te], tol=args.tol)}
+    rep.update({"train_rows": int(len(Xtr)), "train_s": t3 - t2, "train_loss": hist,
+                "train": evaluate(ozk, h, [inst[i] for i in tr], X[tr], T[tr], times[tr], tol=args.tol, run_auto=False),
+                "test": evaluate(ozk, h, [inst[i] for i in te], X[te], T[te], times[te], tol=args.tol)})
+    if args.contour:
+        rep["contour_test"] = evaluate(ozk, h, None, Xct, Tct, None, tol=args.tol, run_auto=False)
+        h.selector_configure(tol=args.tol)
+        rep["contour_test_solves"] = {"solves": len(test_time),
+                                      "S": solve_times(ozk, h, test_time, (5, 6, 7, 10), tol=args.tol)}
     if args.out:
         h.selector_save(args.out)
     text = json.dumps(rep, indent=1)

@@ -308,6 +308,37 @@ def test_build_m_shared_sizes_uses_leading_blocks_of_G(ozk_mod, handle):
         assert np.abs(got - kkr.kkr_build(ts[a], G[:n, :n])).max() <= 1e-14
 
 
+def test_build_m_shared_sizes_many_atoms_ragged_chunks(ozk_mod, handle):
+    """13 atoms of 2..20 sites with b = 12: the build stacks the atoms by decreasing LIZ and cuts
+    every block row into problems of 128 stacked rows, which here split atoms between problems
+    (128 is not a multiple of 12); every atom's M is still I - t_a G[:n_a, :n_a] formed block
+    row by block row as the oracle forms it, bit for bit, and nothing past n_a is written."""
+    import torch
+    b, S = 12, 7
+    rng = np.random.default_rng(77)
+    Ls = [int(v) for v in rng.integers(2, 21, size=13)]
+    Lmax = max(Ls)
+    _, G, _ = synth.kkr_system(Lmax, b, 0.4 + 0.2j, atom=3)
+    ts = [synth.kkr_t(L, b, atom=a) for a, L in enumerate(Ls)]
+    nmax = Lmax * b
+    # each atom's M sits in the leading block of an nmax x nmax canvas with leading dimension n_a
+    canvas = [torch.full((nmax * nmax,), complex("nan+nanj"), dtype=torch.complex128, device="cuda") for _ in Ls]
+    ptr = lambda xs: torch.tensor([x.data_ptr() for x in xs], dtype=torch.int64, device="cuda")
+    tdev = [_tblocks(ozk_mod, t) for t in ts]
+    Gd = ozk_mod.colmajor_cuda(G)
+    ozk_mod.kkr_build_m_shared_sizes_ptrs(handle, Ls, b, ptr(tdev), Gd, ptr(canvas), S=S)
+    assert handle.status() == 0
+    for a, L in enumerate(Ls):
+        n = L * b
+        flat = canvas[a].cpu().numpy()
+        got = flat[:n * n].reshape(n, n).T
+        assert np.all(np.isnan(flat[n * n:]))
+        eye = np.eye(n, dtype=np.complex128)
+        for i in range(L):
+            rows = slice(i * b, (i + 1) * b)
+            assert np.array_equal(got[rows], co.zgemm_lu(eye[rows], ts[a][i], G[rows, :n], S))
+
+
 def test_contour_trace_matches_oracle(ozk_mod, handle):
     """tau_00 at 8 contour energies (one batched solve), their traces and the quadrature sum
     against the oracle's full-inverse tau_00."""

@@ -252,8 +252,10 @@ def test_residual_check_resolves_cancelled_products(ozk_mod, handle):
 
 
 def test_batched_solve_with_selected_S(ozk_mod):
-    """S = 0 on the batched KKR solve: the selector's choice from solve 0's panels, applied to
-    the whole call (bitwise the explicit-S solve); S < 0 solves in binary64."""
+    """S = 0 on the batched KKR solve: the selector's choice over the sampled solves' first
+    trailing updates, checked and applied to the whole call (bitwise the explicit-S solve); a
+    network that claims S = 3 fails the sampled checks and the call runs at S = 10; S < 0
+    solves in binary64."""
     import torch
     from oracle import kkr
     h = ozk_mod.Handle()
@@ -274,9 +276,16 @@ def test_batched_solve_with_selected_S(ozk_mod):
 
     auto = run(0)
     info = h.selector_last()
-    assert info["S_selected"] == 6 and info["S_used"] == 6
+    assert info["S_selected"] == 6 and info["S_used"] == 6 and info["gemms"] == 2 and info["residual_ok"]
     for a, b6 in zip(auto, run(6)):
         assert np.array_equal(a, b6)
+    h.selector_set_params(_const_params(-30.0))
+    h.selector_configure(tol=1e-10, margin=0.0)
+    low = run(0)
+    info = h.selector_last()
+    assert info["S_selected"] == 3 and info["fallback"] and info["S_used"] == 10 and not info["residual_ok"]
+    for a, b10 in zip(low, run(10)):
+        assert np.array_equal(a, b10)
     # S < 0 is the binary64 DMMA form of the same batched solve
     for a, d in zip(auto, run(-1)):
         assert kkr.rel_err(a, d) <= 1e-12
@@ -309,9 +318,10 @@ def test_single_solve_S_rule(ozk_mod):
     assert np.array_equal(single(0), auto)
     info = h.selector_last()
     assert info["S_selected"] == 6 and info["S_used"] == 6 and not info["fallback"]
-    assert info["residual_ok"]
+    assert info["residual_ok"] and 0 < info["residual"] <= 0.5e-10
     # one selector call per GEMM: two per panel, 7 panels of (432 - 16) columns at nb = 64
     assert info["probe_seed"] - seed0 == 14
+    assert info["gemms"] == 14 and info["S_count"] == {6: 14}
     assert np.array_equal(auto, single(6))
     dm = single(-1)
     Ms = [ozk_mod.colmajor_cuda(M)]
@@ -320,6 +330,38 @@ def test_single_solve_S_rule(ozk_mod):
     assert np.array_equal(dm, ozk_mod.to_numpy(taus[0]))
     full = kkr.tau00_full(M, t[0])
     assert kkr.rel_err(auto, full) <= 1e-10 and kkr.rel_err(dm, full) <= 1e-12
+    assert h.status() == 0
+    h.close()
+
+
+def test_single_solve_failed_check_redoes_the_solve_at_S_max(ozk_mod):
+    """A network that claims S = 3 is exact enough: the GEMMs of the S = 0 solve run at S = 3,
+    their deferred probe checks fail, and the solve is redone from the saved M with every GEMM at
+    S = 10 (bit for bit the S = 10 solve); with the fallback disabled the solve reports
+    OZK_ERR_RESIDUAL."""
+    import torch
+    from oracle import kkr
+    h = ozk_mod.Handle()
+    h.selector_set_params(_const_params(-30.0))
+    h.selector_configure(tol=1e-10, margin=0.0)
+    t, G = synth.kkr_system(27, 16, 0.5 + 0.05j, atom=5)[:2]
+    M = kkr.kkr_build(t, G)
+
+    def single(S):
+        tau = ozk_mod.colmajor_cuda(np.zeros((16, 16), dtype=np.complex128))
+        ozk_mod.kkr_tau00(h, ozk_mod.colmajor_cuda(M), ozk_mod.colmajor_cuda(t[0]), tau, S=S, nb=64)
+        torch.cuda.synchronize()
+        return ozk_mod.to_numpy(tau)
+
+    auto = single(0)
+    info = h.selector_last()
+    assert info["S_selected"] == 3 and info["fallback"] and info["S_used"] == 10
+    assert info["residual_ok"] and info["residual"] <= 0.5e-10 and info["S_count"] == {3: 14}
+    assert np.array_equal(auto, single(10))
+    assert kkr.rel_err(auto, kkr.tau00_full(M, t[0])) <= 1e-10
+    h.selector_configure(tol=1e-10, margin=0.0, flags=ozk_mod.OZK_SEL_NO_FALLBACK)
+    with pytest.raises(ozk_mod.OzkError, match="RESIDUAL"):
+        single(0)
     assert h.status() == 0
     h.close()
 
