@@ -615,25 +615,34 @@ def config4_measure(ozk, h, dev):
     M = torch.empty_like(M0)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
 
+    # the emulated solves: leaf-by-leaf panels, (W, w) tuned once for this matrix at S = 7
+    (W4, w4), _ = ozk.kkr_tau00_autotune_panels(h, [n], b4, S=7)
+
     def solve(S, nb):
         M.copy_(M0)
         tau = torch.zeros((b4, b4), dtype=torch.complex128, device=dev).t()
         ev[0].record()
-        ozk.kkr_tau00(h, M, t0, tau, S=S, nb=nb)
+        if S < 0:
+            ozk.kkr_tau00(h, M, t0, tau, S=S, nb=nb)
+        else:
+            ozk.kkr_tau00_batched(h, [M], [t0], [tau], S=S, nb=W4, leaf=w4)
         ev[1].record()
         torch.cuda.synchronize()
         return tau.cpu().numpy(), ev[0].elapsed_time(ev[1])
 
     ref, ms_ref = solve(-1, 50)
     flops = 8.0 / 3.0 * n ** 3
+    solve(7, 0)
     h.profile_begin()
-    solve(7, 100)
+    solve(7, 0)
     prof7 = h.profile_end()
     out = {"n": n, "b": b4, "dmma_tau00_ms": round(ms_ref, 1), "dmma_eff_tflops": round(flops / ms_ref / 1e9, 3),
+           "panel": W4, "leaf": w4,
            "tau00_S7_kind_ms": {k: round(v["ms"], 2) for k, v in prof7.items() if v["launches"]},
            "tau00": {}, "zgemm_5650": {}}
     for S in range(3, 11):
-        tau, ms = solve(S, 100)
+        solve(S, 0)                               # warm (workspace of this S)
+        tau, ms = solve(S, 0)
         out["tau00"][str(S)] = {"rel_err_vs_dmma": rel_err(tau, ref), "ms": round(ms, 1),
                                 "eff_tflops": round(flops / ms / 1e9, 3)}
     C_ref = torch.empty_like(M0)

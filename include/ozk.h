@@ -355,9 +355,11 @@ ozk_status_t kkr_build_m_shared_sizes(ozk_handle_t handle, int natoms, const int
  *           per S (S_count), the largest residual estimate, and whether it was redone.
  *   S < 0:  both GEMMs are binary64 DMMA GEMMs (the native-precision baseline).
  *   nb <= OZK_NB_MAX (the pivot block is held in shared memory).  nb = 0: for S >= 1 the
- *   width kkr_tau00_autotune picks for one matrix of order n (tuned on the first such call,
- *   which must not be captured, and cached in the handle; S = 0 takes the width tuned at
- *   S = 7); for S < 0, 32.
+ *   (W, w) pair kkr_tau00_autotune_panels picks for one matrix of order n (tuned on the first
+ *   such call, which must not be captured, and cached in the handle); with leaves (w < W) the
+ *   solve is the one-matrix case of kkr_tau00_batched_panels (leaves narrower than the panels
+ *   cut the binary64 pivot-inverse work, which runs on one SM per inverse for a single
+ *   matrix), with whole panels (w = W) this path with nb = W.  S = 0 takes the whole-panel width kkr_tau00_autotune picks at S = 7; S < 0, 32.
  *   M   : DEVICE n x n column major (ld n), DESTROYED (overwritten by the factorisation).
  *   t0  : DEVICE b x b column major.  tau00: DEVICE b x b column major output.
  *   b <= 64 (16 for lmax = 3; 50 for lmax = 4 with spin), nb a multiple of b.  Site 0 occupies
@@ -440,8 +442,8 @@ ozk_status_t kkr_tau00_autotune(ozk_handle_t handle, int nsolves, const int* n, 
                                 float* times);
 
 /* Autotuner over (W, w) pairs of kkr_tau00_batched_panels: whole-panel pivot blocks W = w = b,
- * 2b, ... <= OZK_NB_MAX, then panels of two and three leaves (W = 2w, 3w) for every leaf width w
- * (a multiple of b) from 48 to 96.  Times each on scratch test matrices of the sizes n[] as
+ * 2b, ... <= OZK_NB_MAX, then panels of g leaves (W = g w <= OZK_PANEL_MAX, g = 2..4; g = 2..8
+ * for nsolves = 1) for every leaf width w (a multiple of b) from 48 to 96.  Times each on scratch test matrices of the sizes n[] as
  * kkr_tau00_autotune does, returns the fastest pair in *W_best, *w_best and caches it for
  * W = 0 (and nb = 0 of kkr_tau00_batched).  Optional HOST outputs: times[] (ms) and cand[]
  * (W, w per candidate), each with room for `cap` candidates (OZK_ERR_ARG if too short; the

@@ -105,12 +105,14 @@ struct ozk_context {
   // and the events that fork it from and join it to the handle's stream
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_join3 = nullptr;           // the side stream's split of a panel's deferred-update U rows
   long long stall_next = 0;                 // ozk_debug_stall_next_gemm: budget for the next launch
   // selector training-data log (ozk_selector_log_begin): DEVICE rows of features and targets
   float* sel_log_f = nullptr;
   float* sel_log_t = nullptr;
   int sel_log_cap = 0, sel_log_n = 0;
   void* sel_log_ws = nullptr;               // reference and trial products of the logged GEMMs
+  void** one_ptrs = nullptr;                // DEVICE (M, t0, tau) of a single solve run by the batched solver
   size_t sel_log_ws_bytes = 0;
 };
 
@@ -733,10 +735,12 @@ ozk_status_t ozk_create(ozk_handle_t* handle) {
   }
   if (!st) st = cuda_check(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming), "cudaEventCreate");
   if (!st) st = cuda_check(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming), "cudaEventCreate");
+  if (!st) st = cuda_check(cudaEventCreateWithFlags(&h->ev_join3, cudaEventDisableTiming), "cudaEventCreate");
   if (st) {
     if (h->d_status) cudaFree(h->d_status);
     if (h->aux) cudaStreamDestroy(h->aux);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     delete h;
     return st;
   }
@@ -753,11 +757,13 @@ ozk_status_t ozk_destroy(ozk_handle_t h) {
   if (h->sel_p) cudaFree(h->sel_p);
   if (h->sel_ws) cudaFree(h->sel_ws);
   if (h->sel_log_ws) cudaFree(h->sel_log_ws);
+  if (h->one_ptrs) cudaFree(h->one_ptrs);
   for (auto& kv : h->tables) cudaFree(kv.second);
   for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
   if (h->aux) cudaStreamDestroy(h->aux);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->ev_join3) cudaEventDestroy(h->ev_join3);
   delete h;
   return OZK_OK;
 }
@@ -1068,6 +1074,8 @@ static std::vector<int> tune_key(int nsolves, const int* n, int b, int S);
 
 static ozk_status_t tau00_single(ozk_context* h, int n, int b, double2* M, const void* t0, void* tau, int S, int nb,
                                  size_t off_gemm, SelDefer* defer, int force_S);
+static ozk_status_t tau00_batched_impl(ozk_handle_t h, int nsolves, const int* n, int b, void* const* M,
+                                       const void* const* t0, void* const* tau, int S, int W, int w);
 
 // tau_00 of one matrix: eliminate panels J = [p, q) from the trailing end, centre last.  Each
 // panel: D^-1 of its pivot block (binary64 Gauss-Jordan), L = M_RJ D^-1 and M_RR -= L M_JR as
@@ -1085,9 +1093,37 @@ ozk_status_t kkr_tau00(ozk_handle_t h, int n, int b, void* Mv, const void* t0, v
     if (capturing(h->stream))
       return set_error(OZK_ERR_CAPTURE, "S = 0 synchronises to read the selector's choices and cannot be captured");
   }
+  if (nb == 0 && S >= 1 && b > 0 && b <= 64 && n > 0 && n % b == 0) {
+    // emulated with a fixed S: the panel and leaf widths kkr_tau00_autotune_panels picks for one
+    // matrix of this order (tuned on the first such call, cached); leaf panels run on the
+    // batched solver (a single matrix's pivot inverses run on one SM each, so narrow leaves
+    // inside wide panels cut the binary64 work that bounds the solve), whole panels below
+    int W = 0, w = 0;
+    auto it = h->tuned_nb.find(tune_key(1, &n, b, S));
+    if (it != h->tuned_nb.end()) {
+      W = it->second.first;
+      w = it->second.second;
+    } else {
+      ozk_status_t st = kkr_tau00_autotune_panels(h, 1, &n, b, S, &W, &w, nullptr, nullptr, 0, nullptr);
+      if (st) return st;
+    }
+    if (W == w) {
+      nb = W;                     // whole panels: the single-matrix path has fewer launches per panel
+    } else {
+      if (!h->one_ptrs) {
+        ozk_status_t st = cuda_check(cudaMalloc(&h->one_ptrs, 3 * sizeof(void*)), "cudaMalloc(pointer table)");
+        if (st) { h->one_ptrs = nullptr; return st; }
+      }
+      launch_set_ptrs(h->one_ptrs, Mv, const_cast<void*>(t0), tau, h->stream);
+      ozk_status_t st = cuda_check(cudaGetLastError(), "pointer table launch");
+      if (st) return st;
+      const int nn = n;
+      return tau00_batched_impl(h, 1, &nn, b, h->one_ptrs, h->one_ptrs + 1, h->one_ptrs + 2, S, W, w);
+    }
+  }
   if (nb == 0 && b > 0 && b <= 64 && n > 0 && n % b == 0) {
-    // the panel width kkr_tau00_autotune picks for one matrix of this size (emulated; S = 0:
-    // tuned at S = 7), or 32 (binary64 DMMA)
+    // the panel width kkr_tau00_autotune picks for one matrix of this size (S = 0: tuned at
+    // S = 7), or 32 (binary64 DMMA)
     if (dmma) {
       nb = std::min(GJINV_MAX, (32 + b - 1) / b * b);
     } else {
@@ -1649,6 +1685,7 @@ static ozk_status_t tau00_batched_impl(ozk_handle_t h, int nsolves, const int* n
         }
       }
       if (nact == 0 && !any3) continue;
+      bool early3 = false;                           // GEMM 3's right operand split on the side stream
       {
         Prof pr(h, OZK_KIND_OTHER, 0.0, 0.0);
         launch_kkr_step(s, j, nleaves, nsolves, dn, Mp, b, W, w, dinv, t, h->stream);
@@ -1698,6 +1735,14 @@ static ozk_status_t tau00_batched_impl(ozk_handle_t h, int nsolves, const int* n
         st = gemm_tables(1, amax, wmax, wmax, s1, sa1, sw1, false, 1, false, h->aux, 0);
         if (!st && any2) st = gemm_tables(2, fmax, fmax, wmax, s2, sa2, sb2, true, 2, false, h->aux, box);
         if (!st) st = cuda_check(cudaEventRecord(h->ev_join, h->aux), "record join");
+        // last leaf: the U rows M[p:q, 0:p] of the deferred update are final (the earlier
+        // leaves' frame updates were their last writers), so they are split on the side stream
+        // too, joined only before the deferred update
+        if (!st && any3) {
+          early3 = true;
+          st = gemm_tables(3, pmax3, pmax3, kmax3, s3, sa3, sa3, true, 2, false, h->aux, 0);
+          if (!st) st = cuda_check(cudaEventRecord(h->ev_join3, h->aux), "record join");
+        }
         if (!st) st = cuda_check(cudaStreamWaitEvent(h->stream, h->ev_join, 0), "join side stream");
         if (st) return st;
         st = gemm_tables(1, amax, wmax, wmax, s1, sa1, sw1, false, 2, true, h->stream, 0);
@@ -1708,7 +1753,12 @@ static ozk_status_t tau00_batched_impl(ozk_handle_t h, int nsolves, const int* n
         }
       }
       if (any3) {
-        st = gemm_tables(3, pmax3, pmax3, kmax3, s3, sa3, sa3, true, 3, true, h->stream, 0);
+        if (early3) {
+          st = cuda_check(cudaStreamWaitEvent(h->stream, h->ev_join3, 0), "join side stream");
+          if (!st) st = gemm_tables(3, pmax3, pmax3, kmax3, s3, sa3, sa3, true, 1, true, h->stream, 0);
+        } else {
+          st = gemm_tables(3, pmax3, pmax3, kmax3, s3, sa3, sa3, true, 3, true, h->stream, 0);
+        }
         if (st) return st;
       }
     }
@@ -1987,13 +2037,15 @@ ozk_status_t kkr_tau00_autotune_panels(ozk_handle_t h, int nsolves, const int* n
                                        int* w_best, float* times, int* cand, int cap, int* ncand) {
   if (!h || !n || !W_best || !w_best) return set_error(OZK_ERR_ARG, "null argument");
   if (nsolves < 1 || S < 1 || b < 1 || b > 64) return set_error(OZK_ERR_ARG, "need nsolves >= 1, S >= 1, 1 <= b <= 64");
-  // whole-panel pivot blocks nb = b, 2b, ... <= 112, then panels of 2 and 3 leaves of every
-  // leaf width w (a multiple of b) from 48 to 96
+  // whole-panel pivot blocks nb = b, 2b, ... <= 112, then panels of 2 to 4 leaves (one matrix:
+  // up to 8, its inverses having the GPU to themselves) of every leaf width w (a multiple of
+  // b) from 48 to 96
   std::vector<std::pair<int, int>> cands;
   for (int nb = b; nb <= GJINV_MAX; nb += b) cands.push_back({nb, nb});
+  const int gmax = nsolves == 1 ? 8 : 4;
   for (int w = b; w <= std::min(96, GJINV_MAX); w += b) {
     if (w < 48) continue;
-    for (int g = 2; g <= 3; ++g)
+    for (int g = 2; g <= gmax; ++g)
       if (g * w <= OZK_PANEL_MAX) cands.push_back({g * w, w});
   }
   if (ncand) *ncand = static_cast<int>(cands.size());

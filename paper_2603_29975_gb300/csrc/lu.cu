@@ -631,6 +631,15 @@ __global__ void fill_test_kernel(double2* const* M, const int* n, int b, double2
     for (int i = threadIdx.x; i < b * b; i += blockDim.x) t0[i] = make_double2(i % (b + 1) == 0 ? 1.0 : 0.0, 0.0);
 }
 
+__global__ void set_ptrs_kernel(void** dst, void* a, void* b, void* c) {
+  if (threadIdx.x == 0) { dst[0] = a; dst[1] = b; dst[2] = c; }
+}
+
+void launch_set_ptrs(void** dst, void* a, void* b, void* c, cudaStream_t st) {
+  set_ptrs_kernel<<<1, 32, 0, st>>>(dst, a, b, c);
+  record_launch();
+}
+
 void launch_fill_test(double2* const* M, const int* n, int nsolves, int b, double2* t0, cudaStream_t st) {
   fill_test_kernel<<<dim3(1024, nsolves), 256, 0, st>>>(M, n, b, t0);
   record_launch();

@@ -179,6 +179,8 @@ void launch_scale(int m, int n, double2* C, long long ldc, double br, double bi,
 void launch_stack_t(const double2* const* t, const int* Lt, const int* perm, int natoms, int L, int b, double2* out,
                     cudaStream_t st);
 void launch_fill_test(double2* const* M, const int* n, int nsolves, int b, double2* t0, cudaStream_t st);
+// dst[0..2] = a, b, c (device pointer table of a one-solve call of the batched solver)
+void launch_set_ptrs(void** dst, void* a, void* b, void* c, cudaStream_t st);
 void launch_contour_trace(const double2* const* tau, int nsolves, int b, const double2* w, double2* tr, double2* out,
                           cudaStream_t st);
 

@@ -264,23 +264,36 @@ def test_autotuned_panel_width_is_cached_and_used(ozk_mod):
 
 
 def test_single_solve_autotuned_panel_width(ozk_mod):
-    """kkr_tau00 with nb = 0 tunes the panel width for one matrix on its first call (cached per
-    handle) and then equals a call with that width bit for bit."""
+    """kkr_tau00 with nb = 0 (S >= 1) tunes the (panel, leaf) pair for one matrix on its first
+    call (cached per handle; eight leaves per panel allowed for one matrix): leaf panels run on
+    the batched solver, whole panels on the single-matrix path.  A second call, and the entry
+    the cached pair selects, give the same bits; tau_00 matches the oracle's block LU with
+    those widths and the full inverse."""
     h = ozk_mod.Handle()
     t, G, M = _system(27)
+    n = M.shape[0]
     runs = []
     for _ in range(2):
         tau = ozk_mod.colmajor_cuda(np.zeros((16, 16), dtype=np.complex128))
         ozk_mod.kkr_tau00(h, ozk_mod.colmajor_cuda(M), ozk_mod.colmajor_cuda(t[0]), tau, S=7, nb=0)
         runs.append(ozk_mod.to_numpy(tau))
     assert h.status() == 0
-    best, _ = ozk_mod.kkr_tau00_autotune(h, [M.shape[0]], 16, S=7)
-    tau = ozk_mod.colmajor_cuda(np.zeros((16, 16), dtype=np.complex128))
-    ozk_mod.kkr_tau00(h, ozk_mod.colmajor_cuda(M), ozk_mod.colmajor_cuda(t[0]), tau, S=7, nb=best)
-    fixed = ozk_mod.to_numpy(tau)
     assert np.array_equal(runs[0], runs[1])
+    (W, w), times = ozk_mod.kkr_tau00_autotune_panels(h, [n], 16, S=7)
+    assert (8 * 48, 48) in times and (64, 64) in times
+    tau = ozk_mod.colmajor_cuda(np.zeros((16, 16), dtype=np.complex128))
+    ozk_mod.kkr_tau00(h, ozk_mod.colmajor_cuda(M), ozk_mod.colmajor_cuda(t[0]), tau, S=7, nb=0)
+    again = ozk_mod.to_numpy(tau)
+    taus = [ozk_mod.colmajor_cuda(np.zeros((16, 16), dtype=np.complex128))]
+    if W == w:              # whole panels: the single-matrix path with nb = W
+        ozk_mod.kkr_tau00(h, ozk_mod.colmajor_cuda(M), ozk_mod.colmajor_cuda(t[0]), taus[0], S=7, nb=W)
+    else:                   # leaf panels: the one-matrix case of the batched solver
+        ozk_mod.kkr_tau00_batched(h, [ozk_mod.colmajor_cuda(M)], [ozk_mod.colmajor_cuda(t[0])], taus, S=7, nb=W,
+                                  leaf=w)
+    assert np.array_equal(again, ozk_mod.to_numpy(taus[0]))
     full = kkr.tau00_full(M, t[0])
-    assert kkr.rel_err(runs[0], full) <= 1e-10 and kkr.rel_err(fixed, full) <= 1e-10
+    assert kkr.rel_err(runs[0], full) <= 1e-10 and kkr.rel_err(again, full) <= 1e-10
+    assert kkr.rel_err(again, co.tau00_block(M, t[0], W, S=7, leaf=w)) <= 1e-13
     h.close()
 
 
@@ -421,8 +434,9 @@ def test_batched_dmma_equals_single_dmma(ozk_mod, handle):
 
 def test_config4_full_size_against_binary64_solve(ozk_mod, handle):
     """The largest workload at full size: bcc LIZ 113, b = 50 (lmax = 4 with spin), n = 5650,
-    single emulated solves at S = 5 and 7 with 100-wide panels, within 1e-10 of tau_00 from a
-    binary64 library LU solve of the same M."""
+    single emulated solves at S = 5 and 7 with 100-wide panels and with the panel and leaf
+    widths tuned for this matrix (nb = 0: leaf panels on the batched solver, the configuration
+    the benchmark times), within 1e-10 of tau_00 from a binary64 library LU solve of the same M."""
     import torch
     L, b = 113, 50
     t, G, _ = synth.kkr_system(L, b, 0.5 + 0.05j, atom=0)
@@ -431,12 +445,13 @@ def test_config4_full_size_against_binary64_solve(ozk_mod, handle):
     M0 = ozk_mod.colmajor_cuda(M)
     t0 = ozk_mod.colmajor_cuda(t[0])
     for S in (5, 7):
-        Md = M0.clone()
-        tau = ozk_mod.colmajor_cuda(np.zeros((b, b), dtype=np.complex128))
-        ozk_mod.kkr_tau00(handle, Md, t0, tau, S=S, nb=100)
-        torch.cuda.synchronize()
-        assert handle.status() == 0
-        assert kkr.rel_err(ozk_mod.to_numpy(tau), ref) <= 1e-10
+        for nb in (100, 0):
+            Md = M0.clone()
+            tau = ozk_mod.colmajor_cuda(np.zeros((b, b), dtype=np.complex128))
+            ozk_mod.kkr_tau00(handle, Md, t0, tau, S=S, nb=nb)
+            torch.cuda.synchronize()
+            assert handle.status() == 0
+            assert kkr.rel_err(ozk_mod.to_numpy(tau), ref) <= 1e-10
 
 
 def test_config3_full_size_sampled_atoms(ozk_mod, handle):
