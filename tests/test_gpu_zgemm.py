@@ -232,6 +232,32 @@ def test_large_k_multi_chunk(ozk_mod, handle, S):
     assert np.array_equal(ozk_mod.to_numpy(C), co.zgemm(A, B, S))
 
 
+@pytest.mark.parametrize("k,lu", [(192, True), (500, False), (1100, True)])
+def test_multi_chunk_many_tiles_sampled(ozk_mod, handle, k, lu):
+    """S = 7 (the compile-time instance) with 3, 7 and 16 exactness chunks (K' = 2k) over 512
+    tiles, several per persistent CTA, so the accumulator hand-offs run across tiles and chunks:
+    each output is still the exact sum rounded once.  Row i of op(A) and column j of op(B) fix
+    their own exponents, so the oracle's product of sampled rows and columns is the same block
+    of the full product, bit for bit (store and LU update)."""
+    m, n, S = 2048, 1024, 7
+    A, B = rand_complex(m, k, 300 + k), rand_complex(k, n, 301 + k)
+    C0 = rand_complex(m, n, 302) if lu else np.zeros((m, n), dtype=np.complex128)
+    C = _dev(ozk_mod, C0)
+    if lu:
+        ozk_mod.ozaki_zgemm(handle, _dev(ozk_mod, A), _dev(ozk_mod, B), C, S=S, alpha=-1.0, beta=1.0)
+    else:
+        ozk_mod.ozaki_zgemm(handle, _dev(ozk_mod, A), _dev(ozk_mod, B), C, S=S)
+    got = ozk_mod.to_numpy(C)
+    assert handle.status() == 0
+    rng = np.random.default_rng(k)
+    rows = np.sort(rng.choice(m, 48, replace=False))
+    cols = np.sort(rng.choice(n, 40, replace=False))
+    rows[0], cols[-1] = 0, n - 1                      # the first row tile and the last column tile
+    Z = co.zgemm(A[rows], B[:, cols], S)
+    want = C0[np.ix_(rows, cols)] - Z if lu else Z
+    assert np.array_equal(got[np.ix_(rows, cols)], want)
+
+
 def test_vbatched_matches_single(ozk_mod, handle):
     shapes = [(40, 30, 20), (129, 64, 16), (7, 3, 20), (200, 100, 5)]
     As, Bs, Cs, refs = [], [], [], []
