@@ -43,10 +43,11 @@ S_DEFAULT = 7
 L2_CONFIG2, E_CONFIG2 = 65, 0.5 + 0.05j        # the single-atom system (n = 1040)
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # dram__bytes_read.sum + dram__bytes_write.sum per slice-GEMM launch of this workload (256
-# atoms, S = 7, W = 192, w = 64), scaled from the ncu capture of the 16-atom case in
-# profiles/slice_gemm_config3_16atoms_full.md by each launch kind's algorithmic work; set back
-# to None whenever the kernel or the step's launch sequence changes until captured again
-SLICE_GEMM_DRAM_BYTES_PER_LAUNCH = 1.747e9
+# atoms, S = 7, W = 192, w = 64), scaled from the ncu captures of the 16-atom case
+# (profiles/slice_gemm_config3_16atoms_full.md, profiles/slice_gemm_build_16atoms_full.md) by
+# each launch kind's algorithmic work; set back to None whenever the kernel or the step's
+# launch sequence changes until captured again
+SLICE_GEMM_DRAM_BYTES_PER_LAUNCH = 1.903e9
 
 
 def parse():
