@@ -254,6 +254,32 @@ __device__ __forceinline__ bool dispatch_covers(const GemmParams& p, int S) {
   return !p.fullset && (S == 9 || S == 10);
 }
 
+// Tiles of one problem of a batched GEMM (m rows, n2 stacked columns) with a skip box
+// [0, km) x [0, kn) (rows, complex columns) whose outputs are neither computed nor written: the
+// part beside the box, rows [0, km) x stacked columns [2 kn, n2), in ku x xu tiles of a grid
+// that starts at row 0 and stacked column 2 kn (the last tile row clipped at row km, mu), then
+// the part below it, rows [km, m) x all columns, in nl x ntx tiles of a grid that starts at row
+// km (m0l).  Each part's grid starts at the box edge, so a strip of one tile's width beside or
+// below the box takes one tile row or column, not two.  Without a box (km or kn zero) the whole
+// grid is the second part.
+struct BoxTiles { int ku, xu, mu, n0u, nl, ntx, m0l; };
+__host__ __device__ __forceinline__ BoxTiles box_tiles(int m, int n2, int km, int kn, int BN) {
+  BoxTiles b;
+  b.ntx = (n2 + BN - 1) / BN;
+  if (km > 0 && kn > 0) {
+    b.mu = km < m ? km : m;
+    b.ku = (b.mu + GEMM_BM - 1) / GEMM_BM;
+    b.n0u = 2 * kn;
+    b.xu = n2 > b.n0u ? (n2 - b.n0u + BN - 1) / BN : 0;
+    b.m0l = km;
+    b.nl = m > km ? (m - km + GEMM_BM - 1) / GEMM_BM : 0;
+  } else {
+    b.mu = 0; b.ku = 0; b.n0u = 0; b.xu = 0; b.m0l = 0;
+    b.nl = (m + GEMM_BM - 1) / GEMM_BM;
+  }
+  return b;
+}
+
 struct EpiCtx {
   int row, z, m_z, n2_z, n0, c0, skip_n, er;
   int grow;              // row of the output matrix (the diagonal test of EPI_IMINUS)
@@ -661,10 +687,12 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   const int nkb = p.kblocks;
   const int nchunks = (nkb + p.chunk_kb - 1) / p.chunk_kb;
 
-  // tile decode.  Problem z owns tiles [z tpp, (z + 1) tpp): the tile rows below its skip box
-  // (all columns, column tile fastest), then the tiles right of the box in the rows beside
-  // it; tiles wholly inside the box are never enumerated.  Returns false for indices past the
-  // problem's own tiles or outside its extent (skipped by all roles alike).
+  // tile decode.  With exact enumeration (tile_prefix), problem z owns tiles [prefix[z],
+  // prefix[z + 1]) laid out by box_tiles.  Otherwise problem z owns tiles [z tpp, (z + 1) tpp)
+  // of the largest problem's grid: the tile rows below its skip box (all columns, column tile
+  // fastest), then the tiles right of the box in the rows beside it; tiles wholly inside the
+  // box are never enumerated.  Returns false for indices past the problem's own tiles or
+  // outside its extent (skipped by all roles alike).
   auto tile_of = [&](int t, int& z, int& m0, int& n0, int& m_z, int& n2_z) -> bool {
     if (p.tile_prefix) {
       // exact enumeration: problem z owns tiles [prefix[z], prefix[z + 1]) of its own grid
@@ -677,21 +705,17 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       const int r = t - p.tile_prefix[z];
       m_z = p.m[z];
       n2_z = 2 * p.n[z];
-      const int ntx_z = (n2_z + BN - 1) / BN, nty_z = (m_z + GEMM_BM - 1) / GEMM_BM;
-      const int km = p.skm ? p.skm[z] : 0, kn = p.skn ? p.skn[z] : 0;
-      const int ky = min(km / GEMM_BM, nty_z), kx = min((2 * kn) / BN, ntx_z);
-      const int count1 = (nty_z - ky) * ntx_z;
-      int x, y;
-      if (r < count1) {
-        y = ky + r / ntx_z;
-        x = r - (y - ky) * ntx_z;
-      } else {
-        const int w = ntx_z - kx, r2 = r - count1;
-        y = r2 / w;
-        x = kx + (r2 - y * w);
+      const BoxTiles bt = box_tiles(m_z, n2_z, p.skm ? p.skm[z] : 0, p.skn ? p.skn[z] : 0, BN);
+      if (r < bt.ku * bt.xu) {                  // beside the box (rows clipped at its edge)
+        const int y = r / bt.xu;
+        m0 = y * GEMM_BM;
+        n0 = bt.n0u + (r - y * bt.xu) * BN;
+        m_z = bt.mu;
+      } else {                                  // below the box, or the whole grid
+        const int r2 = r - bt.ku * bt.xu, y = r2 / bt.ntx;
+        m0 = bt.m0l + y * GEMM_BM;
+        n0 = (r2 - y * bt.ntx) * BN;
       }
-      m0 = y * GEMM_BM;
-      n0 = x * BN;
       return true;
     }
     z = t / p.tpp;
@@ -1026,10 +1050,8 @@ __global__ void __launch_bounds__(1024) tile_prefix_kernel(const int* __restrict
     const int z = base + static_cast<int>(threadIdx.x);
     int c = 0;
     if (z < batch && m[z] > 0 && n[z] > 0) {
-      const int ntx = (2 * n[z] + BN - 1) / BN, nty = (m[z] + GEMM_BM - 1) / GEMM_BM;
-      const int km = skm ? skm[z] : 0, kn = skn ? skn[z] : 0;
-      const int ky = min(km / GEMM_BM, nty), kx = min((2 * kn) / BN, ntx);
-      c = ntx * nty - kx * ky;
+      const BoxTiles bt = box_tiles(m[z], 2 * n[z], skm ? skm[z] : 0, skn ? skn[z] : 0, BN);
+      c = bt.ku * bt.xu + bt.nl * bt.ntx;
     }
     part[threadIdx.x] = c;
     __syncthreads();

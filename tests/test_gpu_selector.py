@@ -404,6 +404,36 @@ def test_selector_log_records_features_and_targets(ozk_mod):
     h.close()
 
 
+def test_selector_log_rows_of_a_solve(ozk_mod):
+    """The log hook inside a KKR solve (how the training set is gathered from the contour
+    workload): kkr_tau00 with S = 0 writes one row per GEMM of the solve (two per panel), with
+    finite features and targets that fall with S (each a log10 relative error at most 0,
+    floored at -17); the solve's tau_00 is unchanged in accuracy."""
+    import torch
+    from oracle import kkr
+    h = ozk_mod.Handle()
+    h.selector_load()
+    h.selector_configure(tol=1e-10)
+    t, G = synth.kkr_system(27, 16, 0.5 + 0.05j, atom=9)[:2]
+    M = kkr.kkr_build(t, G)
+    F = torch.zeros((40, 16), dtype=torch.float32, device="cuda")
+    T = torch.zeros((40, 8), dtype=torch.float32, device="cuda")
+    tau = ozk_mod.colmajor_cuda(np.zeros((16, 16), dtype=np.complex128))
+    h.selector_log_begin(F, T)
+    ozk_mod.kkr_tau00(h, ozk_mod.colmajor_cuda(M), ozk_mod.colmajor_cuda(t[0]), tau, S=0, nb=64)
+    rows = h.selector_log_end()
+    assert rows == 14 == h.selector_last()["gemms"]              # 7 panels of (432 - 16) columns
+    Fh, Th = F[:rows].cpu().numpy(), T[:rows].cpu().numpy()
+    assert np.all(np.isfinite(Fh)) and np.all(np.isfinite(Th))
+    assert np.all(Th <= 0.0) and np.all(Th >= -17.0)
+    assert np.all(np.diff(Th, axis=1) <= 0.3)                   # errors fall with S (to the floor)
+    assert np.all(Th[:, 0] > Th[:, -1])
+    assert not np.any(F[rows:].cpu().numpy())                   # nothing past the solve's rows
+    assert kkr.rel_err(ozk_mod.to_numpy(tau), kkr.tau00_full(M, t[0])) <= 1e-10
+    assert h.status() == 0
+    h.close()
+
+
 def kkr_rel(X, Y):
     return float(np.linalg.norm(X - Y) / np.linalg.norm(Y))
 
