@@ -47,7 +47,7 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # (profiles/slice_gemm_config3_16atoms_full.md, profiles/slice_gemm_build_16atoms_full.md) by
 # each launch kind's algorithmic work; set back to None whenever the kernel or the step's
 # launch sequence changes until captured again
-SLICE_GEMM_DRAM_BYTES_PER_LAUNCH = None
+SLICE_GEMM_DRAM_BYTES_PER_LAUNCH = 2.205e9
 
 
 def parse():
