@@ -113,6 +113,7 @@ struct ozk_context {
   int sel_log_cap = 0, sel_log_n = 0;
   void* sel_log_ws = nullptr;               // reference and trial products of the logged GEMMs
   void** one_ptrs = nullptr;                // DEVICE (M, t0, tau) of a single solve run by the batched solver
+  SelDefer* sel_rec = nullptr;              // DEVICE record of the batched call's sampled checks
   size_t sel_log_ws_bytes = 0;
 };
 
@@ -269,12 +270,14 @@ struct EmuGemm {
   // the slice GEMM only if run_gemm; on `stream` (nullptr: the handle's stream)
   int split_sides = 3;
   bool run_gemm = true;
+  bool ksplit_ok = false;                     // split K allowed (a whole-workspace single GEMM call)
   cudaStream_t stream = nullptr;
 };
 
 struct GemmPlan {
   int G, BN, maxpairs, npairs, kpad, rowsA, rowsB, nstage, chunk_kb, kblocks, magic;
-  size_t offA, offB, offE, offF, offT, total;
+  int ksplit;                                 // split-K units per tile (single problems with few tiles)
+  size_t offA, offB, offE, offF, offT, offP, offGA, offGB, total;
 };
 
 ozk_status_t plan_gemm(const EmuGemm& g, GemmPlan* P) {
@@ -313,6 +316,31 @@ ozk_status_t plan_gemm(const EmuGemm& g, GemmPlan* P) {
   P->offF = off; off = align_up(off + static_cast<size_t>(g.batch) * std::max(g.nmax, 1) * 4, 256);
   P->offT = off;                                                     // tile prefix sums
   off = align_up(off + (static_cast<size_t>(std::max(g.batch, g.gbatch)) + 1) * 4, 256);
+  // row maxima of the K-parallel split (left, right operand)
+  P->offGA = off; off = align_up(off + static_cast<size_t>(g.batch) * P->rowsA * 8, 256);
+  P->offGB = off; off = align_up(off + static_cast<size_t>(g.batch) * std::max(g.nmax, 1) * 8, 256);
+  // split K: a single problem whose tiles fill less than half of the SMs and whose K spans
+  // several exactness chunks runs up to 8 units per tile, each over a share of the chunks,
+  // whose exact partial sums (two int64 per stacked output) a finishing kernel adds and rounds;
+  // for the 128-bit epilogue of the triangular schedules on 64-column tiles (store, LU and
+  // general modes)
+  P->ksplit = 1;
+  P->offP = off;
+  {
+    const double terms = 16.0 * P->kblocks * P->maxpairs;
+    const int bits = static_cast<int>(std::ceil(std::log2(terms))) + 14 + 8 * (P->G - 1) + 1;
+    const bool fit64 = P->G <= 5 && bits <= 63;
+    const bool modes = g.mode < 0 || g.mode == EPI_STORE || g.mode == EPI_LU || g.mode == EPI_GENERAL;
+    if (g.ksplit_ok && g.batch == 1 && g.tm == nullptr && !g.remap && !g.crow && !diag && g.pair_mode == OZK_PAIRS_TRI &&
+        P->BN == 64 && P->G <= 8 && !fit64 && modes && g.m > 0 && g.n > 0) {
+      const int nch = (P->kblocks + P->chunk_kb - 1) / P->chunk_kb;
+      const long long tiles = static_cast<long long>((g.m + 127) / 128) * ((2LL * g.n + 63) / 64);
+      const int sms = gpu_sm_count();
+      if (nch >= 2 && 2 * tiles <= sms)
+        P->ksplit = static_cast<int>(std::min<long long>({static_cast<long long>(nch), sms / tiles, 8LL}));
+    }
+    if (P->ksplit > 1) off = align_up(off + static_cast<size_t>(P->ksplit) * 2 * g.n * g.m * sizeof(long long) * 2, 256);
+  }
   P->total = off;
   return OZK_OK;
 }
@@ -339,6 +367,8 @@ ozk_status_t run_emulated(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0
   sp.trans = g.oa.trans; sp.conj = g.oa.conj; sp.side = 0;
   sp.out_rows = P.rowsA; sp.out = As; sp.exps = e; sp.exp_stride = P.rowsA;
   sp.dbg_digits = g.dbg_digits_a;
+  sp.gmax = reinterpret_cast<unsigned long long*>(ws + P.offGA);
+  sp.kgroups = 1;
   if (single) { sp.X = nullptr; sp.X1 = g.A; sp.ld1 = g.lda; sp.rows1 = g.m; sp.k1 = g.k; sp.zstride1 = g.zsA; }
   else { sp.X = g.tA; sp.ld = g.tlda; sp.rows = g.tm; sp.kdim = g.tk; }
   const double smnk = g.sum_mnk >= 0 ? g.sum_mnk : static_cast<double>(g.m) * g.n * g.k;
@@ -349,6 +379,7 @@ ozk_status_t run_emulated(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0
   sq.trans = g.ob.trans ? 0 : 1; sq.conj = g.ob.conj; sq.side = 1;
   sq.out_rows = P.rowsB; sq.out = Bs; sq.exps = f; sq.exp_stride = std::max(g.nmax, 1);
   sq.dbg_digits = nullptr;
+  sq.gmax = reinterpret_cast<unsigned long long*>(ws + P.offGB);
   if (single) { sq.X = nullptr; sq.X1 = g.B; sq.ld1 = g.ldb; sq.rows1 = g.n; sq.k1 = g.k; sq.zstride1 = g.zsB; }
   else { sq.X = g.tB; sq.ld = g.tldb; sq.rows = g.tn; sq.kdim = g.tk; }
   const bool split_a = (g.split_sides & 1) != 0, split_b = (g.split_sides & 2) != 0;
@@ -454,10 +485,16 @@ ozk_status_t run_emulated(ozk_context* h, const EmuGemm& g, size_t ws_offset = 0
     gp.tile_prefix = tp;
     launch_tile_prefix(gp, P.BN, gbatch, tp, stream);
   }
+  if (P.ksplit > 1) {
+    gp.ksplit = P.ksplit;
+    gp.part = reinterpret_cast<longlong2*>(ws + P.offP);
+  }
   {
-    // algorithmic integer ops: every pair is one real GEMM m x 2n x 2k (8 m n k)
+    // algorithmic integer ops: every pair is one real GEMM m x 2n x 2k (8 m n k); a split K's
+    // finishing kernel belongs to the same product
     Prof pr(h, OZK_KIND_SLICE_GEMM, 8.0 * np * smnk, 0.0, stream);
     launch_slice_gemm(ta, tb, gp, P.BN, g.remap ? std::min(g.mmax, 128) : g.mmax, g.nmax, gbatch, stream);
+    if (P.ksplit > 1) launch_finish_split(gp, stream);
   }
   return cuda_check(cudaGetLastError(), "slice GEMM launch");
 }
@@ -758,6 +795,7 @@ ozk_status_t ozk_destroy(ozk_handle_t h) {
   if (h->sel_ws) cudaFree(h->sel_ws);
   if (h->sel_log_ws) cudaFree(h->sel_log_ws);
   if (h->one_ptrs) cudaFree(h->one_ptrs);
+  if (h->sel_rec) cudaFree(h->sel_rec);
   for (auto& kv : h->tables) cudaFree(kv.second);
   for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
   if (h->aux) cudaStreamDestroy(h->aux);
@@ -825,6 +863,7 @@ ozk_status_t ozaki_zgemm(ozk_handle_t h, char transa, char transb, int m, int n,
   g.ar = alpha[0]; g.ai = alpha[1]; g.br = beta[0]; g.bi = beta[1];
   g.S = S; g.pair_mode = pair_mode;
   if (S == 0) return zgemm_auto(h, g);
+  g.ksplit_ok = true;                         // the call owns the whole workspace
   return run_emulated(h, g);
 }
 
@@ -2128,23 +2167,13 @@ static ozk_status_t select_S_for_solves(ozk_context* h, int nsolves, void* const
       for (int o = 0; o < SEL_NO; ++o) info.predicted_log10_err[o] = aux.pred[o];
   }
   info.S_selected = info.S_used = S;
-  // the checks: each sampled product at S into the scratch D, its record in the selector log
-  // scratch (the GEMM workspace at offset 0 is free before the solve starts)
-  SelDefer* rec = nullptr;
-  {
-    const size_t need = 256;
-    if (h->sel_log_ws_bytes < need) {
-      st = cuda_check(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
-      if (st) return st;
-      if (h->sel_log_ws) cudaFree(h->sel_log_ws);
-      h->sel_log_ws = nullptr;
-      h->sel_log_ws_bytes = 0;
-      st = cuda_check(cudaMalloc(&h->sel_log_ws, need), "cudaMalloc(check record)");
-      if (st) return st;
-      h->sel_log_ws_bytes = need;
-    }
-    rec = static_cast<SelDefer*>(h->sel_log_ws);
+  // the checks: each sampled product at S into the scratch D (the GEMM workspace at offset 0 is
+  // free before the solve starts), recorded on the device
+  if (!h->sel_rec) {
+    st = cuda_check(cudaMalloc(&h->sel_rec, sizeof(SelDefer)), "cudaMalloc(check record)");
+    if (st) { h->sel_rec = nullptr; return st; }
   }
+  SelDefer* rec = h->sel_rec;
   SelDefer r{};
   st = cuda_check(cudaMemsetAsync(rec, 0, sizeof(SelDefer), h->stream), "clear check record");
   for (int i : pick) {

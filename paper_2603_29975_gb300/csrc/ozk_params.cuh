@@ -27,6 +27,12 @@ struct SplitParams {
   // uniform batch starts at X1 + z * zstride1
   const double2* X1; int ld1, rows1, k1;
   long long zstride1;
+  // K-parallel split (operands with few row blocks and long rows): gmax[z exp_stride + r] holds
+  // the bit pattern of row r's largest |Re|, |Im| (taken by split_rowmax_kernel over K
+  // segments), and kgroups CTAs share each row block's K tiles; kgroups <= 1: one CTA per row
+  // block scans and splits the whole row
+  unsigned long long* gmax;
+  int kgroups;
 };
 struct SplitPair { SplitParams s[2]; int nsides; };
 
@@ -115,12 +121,22 @@ struct GemmParams {
   // ([batch + 1] ints on the device, written by launch_tile_prefix before the GEMM); nullptr:
   // every problem enumerates the tile grid of the largest one (uniform batches, single problems)
   const int* tile_prefix;
+  // split K (single problems with fewer tiles than SMs): ksplit > 1 work units per tile, unit
+  // u covering tile u / ksplit and exactness chunks [c0, c1) of its K; each unit writes the exact
+  // 64-bit halves (H, L) of its partial sums to part[(u % ksplit) m + row][stacked column]
+  // (longlong2) and finish_split adds the units and rounds once
+  int ksplit;
+  longlong2* part;
   uint8_t ps[MAX_PAIRS], pt[MAX_PAIRS], pg[MAX_PAIRS], pfirst[MAX_PAIRS];
 };
 void launch_slice_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const GemmParams& p, int BN,
                        int max_m, int max_n, int batch, cudaStream_t st);
 // the tile prefix sums of a batched GEMM (p.m, p.n and the skip-box tables) into out[0..batch]
 void launch_tile_prefix(const GemmParams& p, int BN, int batch, int* out, cudaStream_t st);
+// the split-K units' partial sums of a single problem added, rounded once and combined with C
+// (the modes of the slice GEMM's epilogue: store, LU, general)
+void launch_finish_split(const GemmParams& p, cudaStream_t st);
+int gpu_sm_count();
 size_t gemm_smem_bytes(int S, int BN, int nstage);
 
 // ---- dmma.cu: binary64 DMMA ZGEMM

@@ -282,6 +282,7 @@ __host__ __device__ __forceinline__ BoxTiles box_tiles(int m, int n2, int km, in
 
 struct EpiCtx {
   int row, z, m_z, n2_z, n0, c0, skip_n, er;
+  int sp;                // split-K: the unit's K slice (its partial sums go to p.part)
   int grow;              // row of the output matrix (the diagonal test of EPI_IMINUS)
   int jlim;              // complex columns of the output row's matrix
   uint32_t tbase;
@@ -412,6 +413,18 @@ __device__ __forceinline__ bool epilogue_fast(const GemmParams& p, const EpiCtx&
         if (gi < NH) { H[j] += a; H[j + 8] += b; } else { L[j] += a; L[j + 8] += b; }
       }
     }
+  }
+  if (p.ksplit > 1) {
+    // split K: the exact 64-bit halves of this unit's partial sums, column-major (coalesced over
+    // the warp's rows); finish_split adds the units and rounds once
+    if (x.rowok) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int col = x.n0 + x.c0 + j;
+        if (col < x.n2_z) p.part[(static_cast<long long>(x.sp) * x.n2_z + col) * p.m1 + x.row] = make_longlong2(H[j], L[j]);
+      }
+    }
+    return true;
   }
   if (!active) return true;
   // the 16 roundings (column exponents from memory), then phase B: every C value of the
@@ -639,7 +652,14 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   constexpr int COLS = BN / 4;            // stacked columns per epilogue thread
   const bool single = p.m == nullptr;
   const int ntx = p.ntx, nty = p.nty;
-  const int ntiles = p.tile_prefix ? p.tile_prefix[p.batch] : p.tpp * p.batch;
+  const int ks = p.ksplit > 1 ? p.ksplit : 1;
+  const int ntiles = (p.tile_prefix ? p.tile_prefix[p.batch] : p.tpp * p.batch) * ks;
+  // work unit u: tile u / ks, exactness chunks [c0, c1) of its K
+  auto unit_chunks = [&](int u, int nch, int& c0, int& c1) {
+    const int sp = u - (u / ks) * ks;
+    c0 = sp * nch / ks;
+    c1 = (sp + 1) * nch / ks;
+  };
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -752,10 +772,13 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       bool ok = !stalled;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         int z, m0, n0, m_z, n2_z;
-        if (!tile_of(t, z, m0, n0, m_z, n2_z)) continue;
+        if (!tile_of(t / ks, z, m0, n0, m_z, n2_z)) continue;
         int za = z, ra = 0;
         if (p.remap) { const int2 rm = p.remap[z]; za = rm.x; ra = rm.y; }
-        for (int kb = 0; kb < nkb; ++kb, ++kbc) {
+        int c0, c1;
+        unit_chunks(t, nchunks, c0, c1);
+        const int kbe = min(nkb, c1 * p.chunk_kb);
+        for (int kb = c0 * p.chunk_kb; kb < kbe; ++kb, ++kbc) {
           const int stage = kbc % nstage;
           const uint32_t ph = kbc / nstage;
           if (kbc >= static_cast<uint32_t>(nstage) && !mbar_wait(&empty[stage], (ph - 1) & 1, p.status, abort_flag)) {
@@ -787,8 +810,10 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       bool ok = !stalled;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         int z, m0, n0, m_z, n2_z;
-        if (!tile_of(t, z, m0, n0, m_z, n2_z)) continue;
-        for (int c = 0; c < nchunks && ok; ++c, ++cc) {
+        if (!tile_of(t / ks, z, m0, n0, m_z, n2_z)) continue;
+        int cb, ce;
+        unit_chunks(t, nchunks, cb, ce);
+        for (int c = cb; c < ce && ok; ++c, ++cc) {
           const int kb0 = c * p.chunk_kb;
           const int kb1 = min(nkb, kb0 + p.chunk_kb);
           for (int kb = kb0; kb < kb1 && ok; ++kb, ++kbc) {
@@ -838,7 +863,10 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     bool ok = !stalled;
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       int z, m0, n0, m_z, n2_z;
-      if (!tile_of(t, z, m0, n0, m_z, n2_z)) continue;
+      if (!tile_of(t / ks, z, m0, n0, m_z, n2_z)) continue;
+      int ucb, uce;
+      unit_chunks(t, nchunks, ucb, uce);
+      const int unch = uce - ucb;                // exactness chunks of this unit
       int za = z, ra = 0;
       if (p.remap) { const int2 rm = p.remap[z]; za = rm.x; ra = rm.y; }
       const int row = m0 + quad * 32 + lane;
@@ -851,7 +879,8 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
           x.skip_n = (row < (single ? p.skm1 : (p.skm ? p.skm[z] : 0))) ? (single ? p.skn1 : p.skn[z]) : 0;
           out_row(p, single, z, row, za, ra, x.rowok, x.Cz, x.crow, x.grow, x.ldc, x.jlim);
           x.er = x.rowok ? p.e[za * p.e_stride + ra + row] + p.base_exp : 0;
-          ChunkWait cw{acc_full, nchunks, &cc, p.status, abort_flag};
+          x.sp = t - (t / ks) * ks;
+          ChunkWait cw{acc_full, unch, &cc, p.status, abort_flag};
           // short K (at most two K-blocks per tile): the epilogue bounds the tile, and the
           // two-halves variant with streamed TMEM loads is faster (1.18x on 1024 x 1040 x 16
           // tiles); longer K: the group-wise drain that releases accumulators earliest (1.14x
@@ -1005,6 +1034,8 @@ static int num_sms() {
   return n;
 }
 
+int gpu_sm_count() { return num_sms(); }
+
 void launch_slice_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const GemmParams& p0, int BN,
                        int max_m, int max_n, int batch, cudaStream_t st) {
   GemmParams p = p0;
@@ -1014,7 +1045,7 @@ void launch_slice_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const GemmP
   const int ky = std::min(p.box_m / GEMM_BM, p.nty), kx = std::min((2 * p.box_n) / BN, p.ntx);
   p.tpp = p.ntx * p.nty - kx * ky;
   // with exact enumeration the tile count is on the device: one persistent CTA per SM
-  const long long ntiles = static_cast<long long>(p.tpp) * batch;
+  const long long ntiles = static_cast<long long>(p.tpp) * batch * std::max(1, p.ksplit);
   const int grid = static_cast<int>(std::min<long long>(ntiles, num_sms()));
   const size_t smem = gemm_smem_bytes(p.S, BN, p.nstage);
   // the compile-time instances hold only the fast epilogues (no integer group dumps)
@@ -1033,6 +1064,60 @@ void launch_slice_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const GemmP
   } else {
     cudaFuncSetAttribute(slice_gemm_kernel<32, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     slice_gemm_kernel<32, 0><<<grid, GEMM_THREADS, smem, st>>>(ta, tb, p);
+  }
+  record_launch();
+}
+
+// Split K of a single problem: output (row, complex column jc) is the sum over the units of
+// their exact 64-bit halves (H, L) of the real and imaginary stacked columns 2 jc, 2 jc + 1 (the
+// integer sums are split between the units, so their sum is the sum the one-unit epilogue
+// forms), rounded once by the same routine and combined with C in the slice GEMM's modes.
+template <int G>
+__global__ void __launch_bounds__(256) finish_split_kernel(const __grid_constant__ GemmParams p) {
+  constexpr int NH = G < 4 ? G : 4;
+  constexpr int NL = G - NH;
+  constexpr int S8 = 8 * NL;
+  const int m = p.m1, n = p.n1, n2 = 2 * n;
+  const long long total = static_cast<long long>(m) * n;
+  for (long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
+       idx += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int row = static_cast<int>(idx % m), jc = static_cast<int>(idx / m);
+    long long Hr = 0, Lr = 0, Hi = 0, Li = 0;
+    for (int sp = 0; sp < p.ksplit; ++sp) {
+      const longlong2 a = p.part[(static_cast<long long>(sp) * n2 + 2 * jc) * m + row];
+      const longlong2 b = p.part[(static_cast<long long>(sp) * n2 + 2 * jc + 1) * m + row];
+      Hr += a.x; Lr += a.y; Hi += b.x; Li += b.y;
+    }
+    const int E = p.e[row] + p.base_exp + p.f[jc];
+    const double zr = round_hl_jam<S8>(Hr, Lr, E), zi = round_hl_jam<S8>(Hi, Li, E);
+    double2* dst = p.C1 + row + static_cast<long long>(jc) * p.ldc1;
+    if (p.mode == EPI_STORE) {
+      if (p.ar == 1.0 && p.ai == 0.0) *dst = make_double2(zr, zi);
+      else *dst = make_double2(p.ar * zr - p.ai * zi, p.ar * zi + p.ai * zr);
+    } else if (p.mode == EPI_LU) {
+      const double2 cv = *dst;
+      *dst = make_double2(cv.x - zr, cv.y - zi);
+    } else {
+      const double2 cv = *dst;
+      const double xr = p.ar * zr - p.ai * zi, xi = p.ar * zi + p.ai * zr;
+      const double yr = p.br * cv.x - p.bi * cv.y, yi = p.br * cv.y + p.bi * cv.x;
+      *dst = make_double2(xr + yr, xi + yi);
+    }
+  }
+}
+
+void launch_finish_split(const GemmParams& p, cudaStream_t st) {
+  const long long total = static_cast<long long>(p.m1) * p.n1;
+  const unsigned blocks = static_cast<unsigned>(std::min<long long>((total + 255) / 256, 8L * num_sms()));
+  switch (p.ngroups) {
+    case 1: finish_split_kernel<1><<<blocks, 256, 0, st>>>(p); break;
+    case 2: finish_split_kernel<2><<<blocks, 256, 0, st>>>(p); break;
+    case 3: finish_split_kernel<3><<<blocks, 256, 0, st>>>(p); break;
+    case 4: finish_split_kernel<4><<<blocks, 256, 0, st>>>(p); break;
+    case 5: finish_split_kernel<5><<<blocks, 256, 0, st>>>(p); break;
+    case 6: finish_split_kernel<6><<<blocks, 256, 0, st>>>(p); break;
+    case 7: finish_split_kernel<7><<<blocks, 256, 0, st>>>(p); break;
+    default: finish_split_kernel<8><<<blocks, 256, 0, st>>>(p); break;
   }
   record_launch();
 }

@@ -106,11 +106,15 @@ split_kernel(const SplitPair pp) {
   const bool single = p.X == nullptr;
   const int R = single ? p.rows1 : p.rows[z];
   const int K = single ? p.k1 : p.kdim[z];
-  const int r0 = blockIdx.x * SPLIT_ROWS;
+  // K-parallel: CTA x = row block x / kgroups, the kg-th share of its K tiles
+  const int kgs = p.kgroups > 1 ? p.kgroups : 1;
+  const int kg = static_cast<int>(blockIdx.x) % kgs;
+  const int r0 = (static_cast<int>(blockIdx.x) / kgs) * SPLIT_ROWS;
   if (r0 >= R) return;
   const double2* __restrict__ P = single ? p.X1 + z * p.zstride1 : p.X[z];
   const long long ld = single ? p.ld1 : p.ld[z];
   const int tid = threadIdx.x;
+  const bool kpar = kgs > 1 && K > SPLIT_TK;
   const bool one_tile = K <= SPLIT_TK;
 
   __shared__ unsigned long long rowmax[SPLIT_ROWS];
@@ -167,7 +171,13 @@ split_kernel(const SplitPair pp) {
     }
   };
 
-  if (one_tile) {
+  if (kpar) {
+    // row maxima taken by the pre-pass over all of K (a non-finite maximum flags the row)
+    if (tid < SPLIT_ROWS && r0 + tid < R) {
+      rowmax[tid] = p.gmax[z * p.exp_stride + r0 + tid];
+      if (rowmax[tid] >= 0x7FF0000000000000ull) bad = 1;
+    }
+  } else if (one_tile) {
     load_tile(0);
     __syncthreads();
     // row maxima from the tile: 8 threads per row, combined by shuffles
@@ -207,7 +217,7 @@ split_kernel(const SplitPair pp) {
     const unsigned long long a = rowmax[tid];
     const int e = (a >= 0x7FF0000000000000ull) ? 0 : frexp_exponent_from_bits(a);
     rowexp[tid] = e;
-    if (r0 + tid < R) p.exps[z * p.exp_stride + r0 + tid] = e;
+    if (r0 + tid < R && kg == 0) p.exps[z * p.exp_stride + r0 + tid] = e;
   }
   __syncthreads();
 
@@ -217,7 +227,13 @@ split_kernel(const SplitPair pp) {
   __half* outz = p.out + static_cast<long long>(z) * S * plane;
   const bool dbg = (p.dbg_digits != nullptr) && z == 0;
   const long long dplane = p.out_rows * 2LL * K;
-  for (int lt = 0; lt < K; lt += TK) {
+  int lt_begin = 0, lt_end = K;
+  if (kpar) {
+    const int ntk = (K + TK - 1) / TK, per_g = (ntk + kgs - 1) / kgs;
+    lt_begin = kg * per_g * TK;
+    lt_end = min(K, (kg + 1) * per_g * TK);
+  }
+  for (int lt = lt_begin; lt < lt_end; lt += TK) {
     if (!one_tile) {
       load_tile(lt);
       __syncthreads();
@@ -279,9 +295,9 @@ split_kernel(const SplitPair pp) {
     }
     __syncthreads();
   }
-  // zero the K padding [2K, kpad) of the rows this CTA owns
+  // zero the K padding [2K, kpad) of the rows this CTA owns (one CTA of a row block)
   const int pad = static_cast<int>(p.kpad) - 2 * K;
-  if (pad > 0) {
+  if (pad > 0 && kg == kgs - 1) {
     const int rows_out = p.side == 0 ? 1 : 2;
     const int nr = min(SPLIT_ROWS, R - r0) * rows_out;
     for (int idx = tid; idx < S * nr * pad; idx += SPLIT_THREADS) {
@@ -293,6 +309,46 @@ split_kernel(const SplitPair pp) {
   }
 }
 
+// Row maxima for the K-parallel split: CTA x covers 32 rows (x / nseg) and K segment x % nseg
+// of SPLIT_KSEG elements; each row's largest |Re|, |Im| bit pattern (non-finite values compare
+// above every finite one) reaches gmax by one 64-bit atomicMax per row and CTA.
+constexpr int SPLIT_KSEG = 512;
+__global__ void __launch_bounds__(SPLIT_THREADS) split_rowmax_kernel(const SplitPair pp, int nseg) {
+  if (static_cast<int>(blockIdx.z) >= pp.nsides) return;
+  const SplitParams& p = pp.s[blockIdx.z];
+  if (!p.gmax) return;
+  const int z = blockIdx.y;
+  const bool single = p.X == nullptr;
+  const int R = single ? p.rows1 : p.rows[z];
+  const int K = single ? p.k1 : p.kdim[z];
+  const int r0 = (static_cast<int>(blockIdx.x) / nseg) * SPLIT_ROWS;
+  const int l_lo = (static_cast<int>(blockIdx.x) % nseg) * SPLIT_KSEG;
+  if (r0 >= R || l_lo >= K) return;
+  const int l_hi = min(K, l_lo + SPLIT_KSEG);
+  const double2* __restrict__ P = single ? p.X1 + z * p.zstride1 : p.X[z];
+  const long long ld = single ? p.ld1 : p.ld[z];
+  __shared__ unsigned long long mx_s[SPLIT_ROWS];
+  const int tid = threadIdx.x;
+  if (tid < SPLIT_ROWS) mx_s[tid] = 0ull;
+  __syncthreads();
+  int rl, l0, lstep;
+  if (!p.trans) { rl = tid % SPLIT_ROWS; l0 = tid / SPLIT_ROWS; lstep = SPLIT_THREADS / SPLIT_ROWS; }
+  else          { rl = tid / 8;          l0 = tid % 8;          lstep = 8; }
+  const int r = r0 + rl;
+  if (r < R) {
+    unsigned long long mx = 0ull;
+    for (int l = l_lo + l0; l < l_hi; l += lstep) {
+      const double2 v = p.trans ? P[l + r * ld] : P[r + l * ld];
+      const unsigned long long a = static_cast<unsigned long long>(__double_as_longlong(v.x)) & 0x7FFFFFFFFFFFFFFFull;
+      const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v.y)) & 0x7FFFFFFFFFFFFFFFull;
+      mx = max(mx, max(a, b));
+    }
+    atomicMax(&mx_s[rl], mx);
+  }
+  __syncthreads();
+  if (tid < SPLIT_ROWS && r0 + tid < R) atomicMax(&p.gmax[z * p.exp_stride + r0 + tid], mx_s[tid]);
+}
+
 void launch_split(const SplitParams& a, int rows_a, const SplitParams* b, int rows_b, int kmax, int batch,
                   cudaStream_t st) {
   SplitPair pp;
@@ -300,7 +356,28 @@ void launch_split(const SplitParams& a, int rows_a, const SplitParams* b, int ro
   pp.nsides = b ? 2 : 1;
   if (b) pp.s[1] = *b;
   const int rows = std::max(rows_a, b ? rows_b : 0);
-  dim3 grid((rows + SPLIT_ROWS - 1) / SPLIT_ROWS, batch, pp.nsides);
+  const int rblocks = (rows + SPLIT_ROWS - 1) / SPLIT_ROWS;
+  // few row blocks and rows longer than one tile: share each row block's K tiles among kgroups
+  // CTAs, after a pre-pass that takes the row maxima over K segments
+  int kgroups = 1;
+  const bool can_kpar = pp.s[0].gmax && (pp.nsides < 2 || pp.s[1].gmax);
+  if (can_kpar && kmax > SPLIT_TK) {
+    const long long ctas = static_cast<long long>(rblocks) * batch * pp.nsides;
+    const int sms = gpu_sm_count();
+    if (ctas < sms) {
+      const int ntk = (kmax + SPLIT_TK - 1) / SPLIT_TK;
+      kgroups = static_cast<int>(std::min<long long>(ntk, std::max<long long>(1, (2LL * sms) / ctas)));
+    }
+  }
+  for (int sd = 0; sd < pp.nsides; ++sd) pp.s[sd].kgroups = kgroups;
+  if (kgroups > 1) {
+    const int nseg = (kmax + SPLIT_KSEG - 1) / SPLIT_KSEG;
+    for (int sd = 0; sd < pp.nsides; ++sd)
+      cudaMemsetAsync(pp.s[sd].gmax, 0, sizeof(unsigned long long) * pp.s[sd].exp_stride * batch, st);
+    split_rowmax_kernel<<<dim3(rblocks * nseg, batch, pp.nsides), SPLIT_THREADS, 0, st>>>(pp, nseg);
+    record_launch();
+  }
+  dim3 grid(rblocks * kgroups, batch, pp.nsides);
   const bool w64 = pp.s[0].nbits <= 62 && (pp.nsides < 2 || pp.s[1].nbits <= 62);
   if (kmax <= 16) {
     if (w64) split_kernel<2, true><<<grid, SPLIT_THREADS, 0, st>>>(pp);

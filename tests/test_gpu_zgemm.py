@@ -221,6 +221,31 @@ def test_config1_full_size_bit_exact_and_error(ozk_mod, handle):
     assert np.linalg.norm(got - X) / np.linalg.norm(X) <= 1e-13
 
 
+def test_split_k_store_lu_and_general(ozk_mod, handle):
+    """A product with few tiles and a long K (m = 200, n = 100, k = 800: 8 tiles, 12 exactness
+    chunks at S = 7) runs split K: 8 units per tile add their exact partial sums, rounded once by
+    the finishing kernel.  Store (transposed operands), LU update and general alpha, beta equal
+    the single-unit results (the oracle's) bit for bit, resp. within the binary64 bound of the
+    general combination."""
+    m, n, k, S = 200, 100, 800, 7
+    Aop, Bop, C0 = rand_complex(m, k, 501), rand_complex(k, n, 502), rand_complex(m, n, 503)
+    Z = co.zgemm(Aop, Bop, S)
+    C = _dev(ozk_mod, np.zeros((m, n), dtype=np.complex128))
+    ozk_mod.ozaki_zgemm(handle, _dev(ozk_mod, stored(Aop, "T")), _dev(ozk_mod, stored(Bop, "C")), C, S=S,
+                        transa="T", transb="C")
+    assert np.array_equal(ozk_mod.to_numpy(C), Z)
+    C = _dev(ozk_mod, C0)
+    ozk_mod.ozaki_zgemm(handle, _dev(ozk_mod, Aop), _dev(ozk_mod, Bop), C, S=S, alpha=-1.0, beta=1.0)
+    assert np.array_equal(ozk_mod.to_numpy(C), C0 - Z)
+    al, be = 0.75 - 0.5j, -1.25 + 2j
+    C = _dev(ozk_mod, C0)
+    ozk_mod.ozaki_zgemm(handle, _dev(ozk_mod, Aop), _dev(ozk_mod, Bop), C, S=S, alpha=al, beta=be)
+    got = ozk_mod.to_numpy(C)
+    scale = np.abs(al) * np.abs(Z) + np.abs(be) * np.abs(C0)
+    assert np.all(np.abs(got - (al * Z + be * C0)) <= 8 * np.finfo(float).eps * scale)
+    assert handle.status() == 0
+
+
 @pytest.mark.parametrize("S", [3, 5, 7, 10])
 def test_large_k_multi_chunk(ozk_mod, handle, S):
     """K' = 5000 spans several exactness chunks: the 128-bit multi-chunk epilogue (at S = 5 in
@@ -316,6 +341,30 @@ def test_degenerate_calls(ozk_mod, handle):
     # GEMM (test_negative_S_is_the_dmma_gemm); above 16 is invalid
     with pytest.raises(ozk_mod.OzkError):
         ozk_mod.ozaki_zgemm(handle, A, B, C, S=17)
+
+
+def test_k_parallel_split_matches_row_parallel_split(ozk_mod, handle):
+    """Operands with few row blocks and long rows take the K-parallel split (row maxima by a
+    pre-pass over K segments, each row block's K tiles shared among CTAs); the same rows inside
+    a tall operand take the one-CTA-per-row-block split.  Each output row depends only on its own
+    row and B, so both give the same bits, non-finite entries included (flagged, split as zero,
+    their row's exponent 0)."""
+    m, n, k, S = 40, 12, 700, 7
+    A, B = rand_complex(m, k, 611), rand_complex(k, n, 612)
+    A[5, 600] = np.nan
+    A[30, 10] = np.inf
+    small = _dev(ozk_mod, np.zeros((m, n), dtype=np.complex128))
+    ozk_mod.ozaki_zgemm(handle, _dev(ozk_mod, A), _dev(ozk_mod, B), small, S=S)
+    assert handle.status() & (1 << 2)
+    tall_A = np.vstack([A, rand_complex(6000 - m, k, 613)])
+    tall = _dev(ozk_mod, np.zeros((6000, n), dtype=np.complex128))
+    ozk_mod.ozaki_zgemm(handle, _dev(ozk_mod, tall_A), _dev(ozk_mod, B), tall, S=S)
+    assert handle.status() & (1 << 2)
+    got, want = ozk_mod.to_numpy(small), ozk_mod.to_numpy(tall)[:m]
+    assert np.array_equal(np.isnan(got), np.isnan(want))
+    assert np.array_equal(np.nan_to_num(got), np.nan_to_num(want))
+    keep = [i for i in range(m) if i not in (5, 30)]
+    assert np.array_equal(got[keep], co.zgemm(A[keep], B, S))
 
 
 def test_nonfinite_input_sets_status(ozk_mod, handle):
