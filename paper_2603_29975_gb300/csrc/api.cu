@@ -710,8 +710,8 @@ static ozk_status_t zgemm_auto(ozk_context* h, const EmuGemm& g, size_t ws_offse
     d.S = S;
     ozk_status_t e = run_emulated(h, d, ws_offset);
     if (e) return e;
-    launch_gemv(d.C, d.ldc, m, n, 0, s.X, nullptr, n, s.Wh, s.Wl, s.part, nullptr, 0, h->stream);
-    launch_residual(s.Wh, s.Wl, s.zh, s.zl, m, s.aux, h->stream);
+    launch_gemv(d.C, d.ldc, m, n, 0, s.X, nullptr, n, s.Wh, s.Wl, s.part, nullptr, 0, h->stream, true);
+    launch_residual(s.Wh, s.Wl, s.zh, s.zl, m, s.aux, reinterpret_cast<double*>(s.part), h->stream);
     SelAux a2;
     e = read_aux(h, s.aux, &a2);
     *r = a2.resid;
@@ -724,8 +724,8 @@ static ozk_status_t zgemm_auto(ozk_context* h, const EmuGemm& g, size_t ws_offse
     d.S = aux.S;
     st = run_emulated(h, d, ws_offset);
     if (st) return st;
-    launch_gemv(d.C, d.ldc, m, n, 0, s.X, nullptr, n, s.Wh, s.Wl, s.part, nullptr, 0, h->stream);
-    launch_residual(s.Wh, s.Wl, s.zh, s.zl, m, s.aux, h->stream);
+    launch_gemv(d.C, d.ldc, m, n, 0, s.X, nullptr, n, s.Wh, s.Wl, s.part, nullptr, 0, h->stream, true);
+    launch_residual(s.Wh, s.Wl, s.zh, s.zl, m, s.aux, reinterpret_cast<double*>(s.part), h->stream);
     launch_defer_check(s.aux, aux.S, force_S == 0, pass, defer, h->stream);
     if (!direct) launch_axpby(m, n, s.D, m, g.C, g.ldc, g.ar, g.ai, g.br, g.bi, h->stream);
     return cuda_check(cudaGetLastError(), "deferred check launches");
@@ -2187,8 +2187,8 @@ static ozk_status_t select_S_for_solves(ozk_context* h, int nsolves, void* const
     g.C = sc.D; g.ldc = g.m; g.S = S; g.mode = -1;
     st = run_emulated(h, g, 0);
     if (st) return st;
-    launch_gemv(sc.D, g.m, g.m, g.n, 0, sc.X, nullptr, g.n, sc.Wh, sc.Wl, sc.part, nullptr, 0, h->stream);
-    launch_residual(sc.Wh, sc.Wl, sc.zh, sc.zl, g.m, sc.aux, h->stream);
+    launch_gemv(sc.D, g.m, g.m, g.n, 0, sc.X, nullptr, g.n, sc.Wh, sc.Wl, sc.part, nullptr, 0, h->stream, true);
+    launch_residual(sc.Wh, sc.Wl, sc.zh, sc.zl, g.m, sc.aux, reinterpret_cast<double*>(sc.part), h->stream);
     launch_defer_check(sc.aux, S, false, 0.5 * h->sel_tol, rec, h->stream);
     st = cuda_check(cudaGetLastError(), "check launches");
   }

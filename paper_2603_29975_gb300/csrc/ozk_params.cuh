@@ -239,12 +239,16 @@ void launch_max_exp(const SelVecStats& a, int ma, const SelVecStats& b, int nb, 
 // op: 0 = rows of M (strided; uses `part`, gemv_chunks(len) x SEL_PROBES x rows x 2 double2),
 // 1 = columns of M, 2 = conjugated columns of M
 int gemv_chunks(int len);
+// plain: binary64 sums inside each chunk of the row-strided form (the chunk partials still
+// added in double-double)
 void launch_gemv(const double2* M, long long ld, int rows, int len, int op, const double2* Xh, const double2* Xl,
-                 int ldx, double2* Yh, double2* Yl, double2* part, const int* ex, int eidx, cudaStream_t st);
+                 int ldx, double2* Yh, double2* Yl, double2* part, const int* ex, int eidx, cudaStream_t st,
+                 bool plain = false);
 void launch_selector_features(const SelVecStats& a, int m, const SelVecStats& b, int n, int k, const double2* X,
                               const double2* zs, const int* ex, float* f, SelAux* aux, cudaStream_t st);
+// rpart: scratch of two doubles per block, min(256, ceil(4 m / 256)) blocks (the partials)
 void launch_residual(const double2* Wh, const double2* Wl, const double2* zh, const double2* zl, int m, SelAux* aux,
-                     cudaStream_t st);
+                     double* rpart, cudaStream_t st);
 void launch_rel_diff(int m, int n, const double2* X, long long ldx, const double2* Y, long long ldy, double* part,
                      double* out, cudaStream_t st);
 void launch_axpby(int m, int n, const double2* D, long long ldd, double2* C, long long ldc, double ar, double ai,

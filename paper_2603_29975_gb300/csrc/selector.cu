@@ -221,6 +221,11 @@ constexpr int GEMV_CHUNK = 16;
 // the reduction, grid.z over the probes; each thread writes its row's partial double-double of
 // its chunk and probe (short dependency chains across many blocks: the compensated sums run on
 // the binary64 pipe).
+// PLAIN: the chunk's products and sums in binary64 (fused multiply-adds, Xl ignored); the
+// chunk partials are still added in double-double by gemv_reduce_kernel, so the result is off
+// by at most about GEMV_CHUNK eps sum_l |m_l x_l| (the residual check's product W = D X, whose
+// compensated sums ran on the binary64 pipe at four times the cost)
+template <bool PLAIN>
 __global__ void gemv_rows_kernel(const double2* M, long long ld, int rows, int len, const double2* Xh,
                                  const double2* Xl, int ldx, double2* part, const int* ex, int eidx) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -232,7 +237,13 @@ __global__ void gemv_rows_kernel(const double2* M, long long ld, int rows, int l
   for (int l = l0; l < l1; ++l) {
     const double2 a = M[i + l * ld];
     const double ar = ldexp(a.x, -E), ai = ldexp(a.y, -E);
-    cmac(acc, ar, ai, Xh[l + q * ldx], Xl ? Xl[l + q * ldx] : make_double2(0.0, 0.0));
+    if constexpr (PLAIN) {
+      const double2 x = Xh[l + q * ldx];
+      acc.rs = __fma_rn(ar, x.x, __fma_rn(-ai, x.y, acc.rs));
+      acc.is = __fma_rn(ar, x.y, __fma_rn(ai, x.x, acc.is));
+    } else {
+      cmac(acc, ar, ai, Xh[l + q * ldx], Xl ? Xl[l + q * ldx] : make_double2(0.0, 0.0));
+    }
   }
   // part[chunk][q][row] as (s re, s im) then (c re, c im)
   const long long o = 2 * ((static_cast<long long>(blockIdx.y) * SEL_PROBES + q) * rows + i);
@@ -240,18 +251,26 @@ __global__ void gemv_rows_kernel(const double2* M, long long ld, int rows, int l
   part[o + 1] = make_double2(acc.rc, acc.ic);
 }
 
-// sum the chunks of gemv_rows_kernel in order: Y = Yh + Yl (rows x SEL_PROBES, ld rows)
+// sum the chunks of gemv_rows_kernel in double-double: Y = Yh + Yl (rows x SEL_PROBES, ld
+// rows); one warp per output, the lanes' partial sums combined by shuffles
 __global__ void gemv_reduce_kernel(const double2* part, int rows, int nchunks, double2* Yh, double2* Yl) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int idx = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (idx >= rows * SEL_PROBES) return;
   CAcc A{0.0, 0.0, 0.0, 0.0};
-  for (int c = 0; c < nchunks; ++c) {
+  for (int c = lane; c < nchunks; c += 32) {
     const long long o = 2 * (static_cast<long long>(c) * SEL_PROBES * rows + idx);
     const double2 sv = part[o], cv = part[o + 1];
     dd_add(A.rs, A.rc, sv.x, cv.x);
     dd_add(A.is, A.ic, sv.y, cv.y);
   }
-  cacc_out(A, Yh[idx], Yl[idx]);
+  for (int o = 16; o; o >>= 1) {
+    const double rs = __shfl_xor_sync(0xffffffffu, A.rs, o), rc = __shfl_xor_sync(0xffffffffu, A.rc, o);
+    const double is = __shfl_xor_sync(0xffffffffu, A.is, o), ic = __shfl_xor_sync(0xffffffffu, A.ic, o);
+    dd_add(A.rs, A.rc, rs, rc);
+    dd_add(A.is, A.ic, is, ic);
+  }
+  if (lane == 0) cacc_out(A, Yh[idx], Yl[idx]);
 }
 
 // op(M) = M^T or M^H (row i of op(M) is column i of M, contiguous): one warp per row
@@ -420,12 +439,13 @@ __global__ void __launch_bounds__(RED_T) selector_features_kernel(SelVecStats a,
 
 // residual: r^2 = ||2^-E W - zs||^2 / ||zs||^2 with W = D X (m x SEL_PROBES), both
 // double-doubles, the difference formed before it is rounded
+// (block partials of num and den into rpart, then residual_final_kernel sums them in order)
 __global__ void __launch_bounds__(RED_T) residual_kernel(const double2* Wh, const double2* Wl, const double2* zh,
-                                                         const double2* zl, int m, SelAux* aux) {
+                                                         const double2* zl, int m, SelAux* aux, double* rpart) {
   __shared__ double sh[RED_T];
   const int E = aux->E;
   double num = 0, den = 0;
-  for (int i = threadIdx.x; i < m * SEL_PROBES; i += RED_T) {
+  for (int i = blockIdx.x * RED_T + threadIdx.x; i < m * SEL_PROBES; i += gridDim.x * RED_T) {
     double dx, ex, dy, ey;
     two_sum(ldexp(Wh[i].x, -E), -zh[i].x, dx, ex);
     two_sum(ldexp(Wh[i].y, -E), -zh[i].y, dy, ey);
@@ -433,6 +453,21 @@ __global__ void __launch_bounds__(RED_T) residual_kernel(const double2* Wh, cons
     dy = dy + (ey + (ldexp(Wl[i].y, -E) - zl[i].y));
     num += dx * dx + dy * dy;
     den += zh[i].x * zh[i].x + zh[i].y * zh[i].y;
+  }
+  num = block_sum(num, sh);
+  den = block_sum(den, sh);
+  if (threadIdx.x == 0) {
+    rpart[2 * blockIdx.x] = num;
+    rpart[2 * blockIdx.x + 1] = den;
+  }
+}
+
+__global__ void __launch_bounds__(RED_T) residual_final_kernel(const double* rpart, int nblocks, SelAux* aux) {
+  __shared__ double sh[RED_T];
+  double num = 0, den = 0;
+  for (int b = threadIdx.x; b < nblocks; b += RED_T) {
+    num += rpart[2 * b];
+    den += rpart[2 * b + 1];
   }
   num = block_sum(num, sh);
   den = block_sum(den, sh);
@@ -662,15 +697,17 @@ void launch_max_exp(const SelVecStats& a, int ma, const SelVecStats& b, int nb, 
 int gemv_chunks(int len) { return (len + GEMV_CHUNK - 1) / GEMV_CHUNK; }
 
 void launch_gemv(const double2* M, long long ld, int rows, int len, int op, const double2* Xh, const double2* Xl,
-                 int ldx, double2* Yh, double2* Yl, double2* part, const int* ex, int eidx, cudaStream_t st) {
+                 int ldx, double2* Yh, double2* Yl, double2* part, const int* ex, int eidx, cudaStream_t st,
+                 bool plain) {
   if (rows <= 0) return;
   if (op == 0) {
     const int nch = std::max(1, gemv_chunks(len));
-    gemv_rows_kernel<<<dim3(blocks(rows, 64), nch, SEL_PROBES), 64, 0, st>>>(M, ld, rows, len, Xh, Xl, ldx, part, ex,
-                                                                              eidx);
+    const dim3 grid(blocks(rows, 64), nch, SEL_PROBES);
+    if (plain) gemv_rows_kernel<true><<<grid, 64, 0, st>>>(M, ld, rows, len, Xh, Xl, ldx, part, ex, eidx);
+    else gemv_rows_kernel<false><<<grid, 64, 0, st>>>(M, ld, rows, len, Xh, Xl, ldx, part, ex, eidx);
     record_launch();
-    gemv_reduce_kernel<<<blocks(static_cast<long long>(rows) * SEL_PROBES, 128), 128, 0, st>>>(part, rows, nch, Yh,
-                                                                                              Yl);
+    gemv_reduce_kernel<<<blocks(static_cast<long long>(rows) * SEL_PROBES * 32, 256), 256, 0, st>>>(part, rows, nch,
+                                                                                                   Yh, Yl);
   } else {
     gemv_cols_kernel<<<blocks(static_cast<long long>(rows) * 32, 256), 256, 0, st>>>(M, ld, rows, len, op == 2, Xh,
                                                                                      Xl, ldx, Yh, Yl, rows, ex, eidx);
@@ -685,8 +722,11 @@ void launch_selector_features(const SelVecStats& a, int m, const SelVecStats& b,
 }
 
 void launch_residual(const double2* Wh, const double2* Wl, const double2* zh, const double2* zl, int m, SelAux* aux,
-                     cudaStream_t st) {
-  residual_kernel<<<1, RED_T, 0, st>>>(Wh, Wl, zh, zl, m, aux);
+                     double* rpart, cudaStream_t st) {
+  const int nb = static_cast<int>(std::min<long long>(256, blocks(static_cast<long long>(m) * SEL_PROBES, RED_T)));
+  residual_kernel<<<nb, RED_T, 0, st>>>(Wh, Wl, zh, zl, m, aux, rpart);
+  record_launch();
+  residual_final_kernel<<<1, RED_T, 0, st>>>(rpart, nb, aux);
   record_launch();
 }
 
