@@ -2107,8 +2107,7 @@ ozk_status_t kkr_tau00_autotune_panels(ozk_handle_t h, int nsolves, const int* n
 // M[0:p, p:q] times U panel M[p:q, 0:p] of the unfactored M, q = n_i, p = max(q - w, b)); the
 // call takes the largest pick.  Every sampled product is then computed at that S and checked
 // with the probes (recorded on the device, read once); if any check fails the call runs at
-// S = 10.  The block bounds the check, whose compensated binary64 probe products cost
-// O(outputs x probes).
+// S = 10.  The block bounds the check, whose binary64 probe products cost O(outputs x probes).
 constexpr int SEL_BATCH_SAMPLES = 8;
 constexpr int SEL_BATCH_BLOCK = 512;
 static ozk_status_t select_S_for_solves(ozk_context* h, int nsolves, void* const* M, const int* n, int b, int w,
