@@ -371,7 +371,7 @@ __device__ __forceinline__ bool release_unread(uint64_t* acc_empty, ChunkWait& c
 // chunk is rounded and written.  The 16 sums are rounded as soon as the drain ends (the two
 // 64-bit halves of every sum die there), then all of the thread's C values are requested at
 // once and combined.  Returns false if a wait gave up.
-template <int G>
+template <int G, bool KS = false>
 __device__ __forceinline__ bool epilogue_fast(const GemmParams& p, const EpiCtx& x, uint64_t* acc_empty, bool magic,
                                               int lane, ChunkWait& cw) {
   constexpr int NH = G < 4 ? G : 4;
@@ -414,7 +414,7 @@ __device__ __forceinline__ bool epilogue_fast(const GemmParams& p, const EpiCtx&
       }
     }
   }
-  if (p.ksplit > 1) {
+  if constexpr (KS) {
     // split K: the exact 64-bit halves of this unit's partial sums, column-major (coalesced over
     // the warp's rows); finish_split adds the units and rounds once
     if (x.rowok) {
@@ -643,7 +643,7 @@ __device__ __forceinline__ bool epilogue_fast64(const GemmParams& p, const EpiCt
 // contain just that schedule and group count -- the tensor pipe is fed markedly faster from
 // the compact code (about 67 instead of 100 cycles per 128 x 64 x 16 MMA in a probe of the
 // same issue loop) and the epilogue warps run a fraction of the instructions' footprint.
-template <int BN, int SF>
+template <int BN, int SF, bool KS>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
 slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                   const __grid_constant__ GemmParams p) {
@@ -652,7 +652,8 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
   constexpr int COLS = BN / 4;            // stacked columns per epilogue thread
   const bool single = p.m == nullptr;
   const int ntx = p.ntx, nty = p.nty;
-  const int ks = p.ksplit > 1 ? p.ksplit : 1;
+  // KS instances run split K (p.ksplit units per tile); the others one unit per tile
+  const int ks = KS ? (p.ksplit > 1 ? p.ksplit : 1) : 1;
   const int ntiles = (p.tile_prefix ? p.tile_prefix[p.batch] : p.tpp * p.batch) * ks;
   // work unit u: tile u / ks, exactness chunks [c0, c1) of its K
   auto unit_chunks = [&](int u, int nch, int& c0, int& c1) {
@@ -890,7 +891,7 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
           if constexpr (SF > 0) {
             if (SF <= 5 && p.fit64) e_ok = epilogue_fast64<(SF <= 5 ? SF : 5)>(p, x, acc_empty, magic_mask, lane, cw);
             else if (halves) e_ok = epilogue_halves<SF>(p, x, acc_empty, magic, lane, cw);
-            else e_ok = epilogue_fast<SF>(p, x, acc_empty, magic, lane, cw);
+            else e_ok = epilogue_fast<SF, KS>(p, x, acc_empty, magic, lane, cw);
           } else if (p.fit64 && G <= 5) {
             switch (G) {
               case 1: e_ok = epilogue_fast64<1>(p, x, acc_empty, magic_mask, lane, cw); break;
@@ -912,14 +913,14 @@ slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
             }
           } else {
             switch (G) {
-              case 1: e_ok = epilogue_fast<1>(p, x, acc_empty, magic, lane, cw); break;
-              case 2: e_ok = epilogue_fast<2>(p, x, acc_empty, magic, lane, cw); break;
-              case 3: e_ok = epilogue_fast<3>(p, x, acc_empty, magic, lane, cw); break;
-              case 4: e_ok = epilogue_fast<4>(p, x, acc_empty, magic, lane, cw); break;
-              case 5: e_ok = epilogue_fast<5>(p, x, acc_empty, magic, lane, cw); break;
-              case 6: e_ok = epilogue_fast<6>(p, x, acc_empty, magic, lane, cw); break;
-              case 7: e_ok = epilogue_fast<7>(p, x, acc_empty, magic, lane, cw); break;
-              default: e_ok = epilogue_fast<8>(p, x, acc_empty, magic, lane, cw); break;
+              case 1: e_ok = epilogue_fast<1, KS>(p, x, acc_empty, magic, lane, cw); break;
+              case 2: e_ok = epilogue_fast<2, KS>(p, x, acc_empty, magic, lane, cw); break;
+              case 3: e_ok = epilogue_fast<3, KS>(p, x, acc_empty, magic, lane, cw); break;
+              case 4: e_ok = epilogue_fast<4, KS>(p, x, acc_empty, magic, lane, cw); break;
+              case 5: e_ok = epilogue_fast<5, KS>(p, x, acc_empty, magic, lane, cw); break;
+              case 6: e_ok = epilogue_fast<6, KS>(p, x, acc_empty, magic, lane, cw); break;
+              case 7: e_ok = epilogue_fast<7, KS>(p, x, acc_empty, magic, lane, cw); break;
+              default: e_ok = epilogue_fast<8, KS>(p, x, acc_empty, magic, lane, cw); break;
             }
           }
           if (!e_ok) { ok = false; break; }
@@ -1050,21 +1051,28 @@ void launch_slice_gemm(const CUtensorMap& ta, const CUtensorMap& tb, const GemmP
   const size_t smem = gemm_smem_bytes(p.S, BN, p.nstage);
   // the compile-time instances hold only the fast epilogues (no integer group dumps)
   const bool tri = BN == 64 && !p.fullset && !p.diag_pairs && p.mode != EPI_GROUPS && p.mode != EPI_RESIDUES;
-  if (tri && p.S == 5) {
+  const bool ks = p.ksplit > 1;                 // split K: its own instances (the unit bookkeeping
+                                                // costs the others registers)
+#define OZK_LAUNCH(BN_, SF_, KS_)                                                                          \
+  do {                                                                                                     \
+    cudaFuncSetAttribute(slice_gemm_kernel<BN_, SF_, KS_>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                         static_cast<int>(smem));                                                          \
+    slice_gemm_kernel<BN_, SF_, KS_><<<grid, GEMM_THREADS, smem, st>>>(ta, tb, p);                         \
+  } while (0)
+  if (tri && p.S == 5 && !ks) {
     // the slice count the selector picks for most KKR GEMMs: a compact instance
-    cudaFuncSetAttribute(slice_gemm_kernel<64, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    slice_gemm_kernel<64, 5><<<grid, GEMM_THREADS, smem, st>>>(ta, tb, p);
+    OZK_LAUNCH(64, 5, false);
   } else if (tri && p.S == 7) {
     // 55 bits, the precision of the batched contour workload
-    cudaFuncSetAttribute(slice_gemm_kernel<64, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    slice_gemm_kernel<64, 7><<<grid, GEMM_THREADS, smem, st>>>(ta, tb, p);
+    if (ks) OZK_LAUNCH(64, 7, true);
+    else OZK_LAUNCH(64, 7, false);
   } else if (BN == 64) {
-    cudaFuncSetAttribute(slice_gemm_kernel<64, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    slice_gemm_kernel<64, 0><<<grid, GEMM_THREADS, smem, st>>>(ta, tb, p);
+    if (ks) OZK_LAUNCH(64, 0, true);
+    else OZK_LAUNCH(64, 0, false);
   } else {
-    cudaFuncSetAttribute(slice_gemm_kernel<32, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    slice_gemm_kernel<32, 0><<<grid, GEMM_THREADS, smem, st>>>(ta, tb, p);
+    OZK_LAUNCH(32, 0, false);
   }
+#undef OZK_LAUNCH
   record_launch();
 }
 
