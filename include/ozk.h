@@ -443,7 +443,7 @@ ozk_status_t kkr_tau00_autotune(ozk_handle_t handle, int nsolves, const int* n, 
 
 /* Autotuner over (W, w) pairs of kkr_tau00_batched_panels: whole-panel pivot blocks W = w = b,
  * 2b, ... <= OZK_NB_MAX, then panels of g leaves (W = g w <= OZK_PANEL_MAX, g = 2..4; g = 2..8
- * for nsolves = 1) for every leaf width w (a multiple of b) from 48 to 96.  Times each on scratch test matrices of the sizes n[] as
+ * for nsolves = 1) for every leaf width w (a multiple of b) from 32 to 96.  Times each on scratch test matrices of the sizes n[] as
  * kkr_tau00_autotune does, returns the fastest pair in *W_best, *w_best and caches it for
  * W = 0 (and nb = 0 of kkr_tau00_batched).  Optional HOST outputs: times[] (ms) and cand[]
  * (W, w per candidate), each with room for `cap` candidates (OZK_ERR_ARG if too short; the

@@ -431,7 +431,7 @@ def kkr_tau00_autotune_panels(h: Handle, n_list, b: int, S: int = 7):
     """Time every (panel, leaf) width pair for these sizes; returns ((W, w), {(W, w): ms})."""
     ns = len(n_list)
     n = (ctypes.c_int * ns)(*[int(v) for v in n_list])
-    cap = 64
+    cap = 256
     times = (ctypes.c_float * cap)()
     cand = (ctypes.c_int * (2 * cap))()
     W, w, nc = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)

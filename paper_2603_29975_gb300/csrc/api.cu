@@ -2078,12 +2078,12 @@ ozk_status_t kkr_tau00_autotune_panels(ozk_handle_t h, int nsolves, const int* n
   if (nsolves < 1 || S < 1 || b < 1 || b > 64) return set_error(OZK_ERR_ARG, "need nsolves >= 1, S >= 1, 1 <= b <= 64");
   // whole-panel pivot blocks nb = b, 2b, ... <= 112, then panels of 2 to 4 leaves (one matrix:
   // up to 8, its inverses having the GPU to themselves) of every leaf width w (a multiple of
-  // b) from 48 to 96
+  // b) from 32 to 96
   std::vector<std::pair<int, int>> cands;
   for (int nb = b; nb <= GJINV_MAX; nb += b) cands.push_back({nb, nb});
   const int gmax = nsolves == 1 ? 8 : 4;
   for (int w = b; w <= std::min(96, GJINV_MAX); w += b) {
-    if (w < 48) continue;
+    if (w < 32) continue;
     for (int g = 2; g <= gmax; ++g)
       if (g * w <= OZK_PANEL_MAX) cands.push_back({g * w, w});
   }

@@ -115,6 +115,33 @@ def test_batched_leaf_panels_vs_oracle(ozk_mod, handle, S, W, w):
             assert kkr.rel_err(got, co.tau00_full(M, t[0])) <= 1e-10, i
 
 
+def test_pivot_inverse_forms_agree_across_batch_sizes(ozk_mod, handle):
+    """Pivot blocks of order <= 64 are inverted with the block in registers when a launch has
+    at most one block per SM and in shared memory otherwise: the same solves in a batch larger
+    than the SM count and in a small batch agree to binary64 rounding, and both match the
+    oracle's leaf-wise block LU of the same M."""
+    import torch
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    sizes = [9, 14, 5, 11]
+    systems = [_system(L, 0.45 + 0.07j * (i + 1), atom=i) for i, L in enumerate(sizes)]
+
+    def run(reps):
+        Ms = [ozk_mod.colmajor_cuda(systems[i % len(systems)][2]) for i in range(reps)]
+        t0s = [ozk_mod.colmajor_cuda(systems[i % len(systems)][0][0]) for i in range(reps)]
+        taus = [ozk_mod.colmajor_cuda(np.zeros((16, 16), dtype=np.complex128)) for _ in range(reps)]
+        ozk_mod.kkr_tau00_batched(handle, Ms, t0s, taus, S=7, nb=128, leaf=64)
+        assert handle.status() == 0
+        return [ozk_mod.to_numpy(x) for x in taus]
+
+    small = run(len(systems))
+    large = run(nsm + 8)
+    for i, (t, G, M) in enumerate(systems):
+        want = co.tau00_block(M, t[0], 128, S=7, leaf=64)
+        assert kkr.rel_err(small[i], want) < 1e-13, i
+        for r in range(i, nsm + 8, len(systems)):
+            assert kkr.rel_err(large[r], small[i]) < 1e-13, (i, r)
+
+
 def test_one_leaf_panels_equal_the_plain_batched_solve(ozk_mod, handle):
     """w = W is the plain panel-by-panel block LU: bit for bit kkr_tau00_batched with nb = W."""
     sizes = [27, 15, 9]
@@ -167,16 +194,19 @@ def test_singular_pivot_sets_status(ozk_mod, handle):
 
 
 @pytest.mark.parametrize("S", [-1, 7])
-def test_pivot_blocks_need_row_interchanges(ozk_mod, handle, S):
+@pytest.mark.parametrize("nb", [48, 64, 80])
+def test_pivot_blocks_need_row_interchanges(ozk_mod, handle, S, nb):
     """Pivot blocks whose diagonal is zero (every panel's leading element needs a row
     interchange): the in-place Gauss-Jordan inverse with partial pivoting still gives tau_00
-    of the full-inverse oracle."""
+    of the full-inverse oracle.  Pivot blocks of order <= 64 are inverted with the block in
+    registers, wider ones in shared memory."""
     rng = np.random.default_rng(20260403)
-    n, b, nb = 160, 16, 48
+    b = 16
+    n = b + 3 * nb
     M = 0.02 * (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
-    # every block of the elimination (centre [0, 16), panels [16, 64), [64, 112), [112, 160))
-    # dominated by its reversal permutation, with a zero diagonal
-    for lo, hi in ((0, 16), (16, 64), (64, 112), (112, 160)):
+    # every block of the elimination (centre [0, 16) and three panels of nb) dominated by its
+    # reversal permutation, with a zero diagonal
+    for lo, hi in ((0, b), (b, b + nb), (b + nb, b + 2 * nb), (b + 2 * nb, n)):
         for r in range(hi - lo):
             M[lo + r, hi - 1 - r] += 1.0
     np.fill_diagonal(M, 0.0)
