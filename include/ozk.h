@@ -435,7 +435,8 @@ ozk_status_t kkr_contour_trace(ozk_handle_t handle, int nsolves, int b, const vo
 
 /* Autotuner of the batched solve: times kkr_tau00_batched on scratch matrices of the sizes
  * n[0..nsolves-1] (diagonally dominant test matrices, allocated and freed here) for every
- * panel width nb = b, 2b, ... <= OZK_NB_MAX, returns the fastest in *nb_best (HOST) and the times in
+ * panel width nb = b, 2b, ... <= OZK_NB_MAX, returns in *nb_best (HOST) the smallest nb among
+ * those within 1 % of the fastest, and the times in
  * ms in times[] (HOST, one per candidate in that order; may be NULL), and caches the choice in
  * the handle for nb = 0.  Synchronises; cannot be captured. */
 ozk_status_t kkr_tau00_autotune(ozk_handle_t handle, int nsolves, const int* n, int b, int S, int* nb_best,
@@ -443,9 +444,10 @@ ozk_status_t kkr_tau00_autotune(ozk_handle_t handle, int nsolves, const int* n, 
 
 /* Autotuner over (W, w) pairs of kkr_tau00_batched_panels: whole-panel pivot blocks W = w = b,
  * 2b, ... <= OZK_NB_MAX, then panels of g leaves (W = g w <= OZK_PANEL_MAX, g = 2..4; g = 2..8
- * for nsolves = 1) for every leaf width w (a multiple of b) from 32 to 96.  Times each on scratch test matrices of the sizes n[] as
- * kkr_tau00_autotune does, returns the fastest pair in *W_best, *w_best and caches it for
- * W = 0 (and nb = 0 of kkr_tau00_batched).  Optional HOST outputs: times[] (ms) and cand[]
+ * for nsolves = 1) for every leaf width w (a multiple of b) from 32 to 96.  Times each on
+ * scratch test matrices of the sizes n[] as kkr_tau00_autotune does, returns in *W_best,
+ * *w_best the smallest pair (by W, then w) among those within 1 % of the fastest and caches it
+ * for W = 0 (and nb = 0 of kkr_tau00_batched).  Optional HOST outputs: times[] (ms) and cand[]
  * (W, w per candidate), each with room for `cap` candidates (OZK_ERR_ARG if too short; the
  * count is written to *ncand when ncand is not NULL). */
 ozk_status_t kkr_tau00_autotune_panels(ozk_handle_t handle, int nsolves, const int* n, int b, int S,

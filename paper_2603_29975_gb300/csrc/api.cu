@@ -2032,7 +2032,7 @@ static ozk_status_t autotune_impl(ozk_context* h, int nsolves, const int* n, int
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (!st) st = cuda_check(cudaEventCreate(&e0), "cudaEventCreate");
   if (!st) st = cuda_check(cudaEventCreate(&e1), "cudaEventCreate");
-  float best_ms = 0.0f;
+  std::vector<float> ms_all(cands.size(), 0.0f);
   *best = -1;
   const bool prof = h->prof;
   h->prof = false;                                                    // tuning runs are not profiled
@@ -2049,7 +2049,14 @@ static ozk_status_t autotune_impl(ozk_context* h, int nsolves, const int* n, int
     }
     if (st) break;
     if (times) times[c] = ms;
-    if (*best < 0 || ms < best_ms) { best_ms = ms; *best = static_cast<int>(c); }
+    ms_all[c] = ms;
+  }
+  if (!st && !cands.empty()) {
+    // the smallest (W, w) among the candidates within 1 % of the fastest: timing noise between
+    // near-equal pairs does not decide, and the narrower panel needs less workspace
+    const float fastest = *std::min_element(ms_all.begin(), ms_all.end());
+    for (size_t c = 0; c < cands.size(); ++c)
+      if (ms_all[c] <= 1.01f * fastest && (*best < 0 || cands[c] < cands[*best])) *best = static_cast<int>(c);
   }
   h->prof = prof;
   if (e0) cudaEventDestroy(e0);

@@ -161,13 +161,16 @@ def test_one_leaf_panels_equal_the_plain_batched_solve(ozk_mod, handle):
 
 def test_panel_autotuner_caches_a_pair(ozk_mod):
     """kkr_tau00_autotune_panels times whole-panel and leaf-wise candidates and caches the
-    fastest (W, w); nb = 0 then runs exactly that pair (bitwise)."""
+    smallest (W, w) within 1 % of the fastest; nb = 0 then runs exactly that pair (bitwise)."""
     import torch
     h = ozk_mod.Handle()
     sizes = [27, 15, 27]
     systems = [_system(L, 0.5 + 0.05j, atom=i) for i, L in enumerate(sizes)]
     (W, w), times = ozk_mod.kkr_tau00_autotune_panels(h, [L * 16 for L in sizes], 16, S=7)
-    assert (W, w) in times and times[(W, w)] == min(times.values())
+    # the smallest pair (by W, then w) within 1 % of the fastest
+    lim = np.float32(1.01) * np.float32(min(times.values()))    # as the library compares
+    near = [c for c, v in times.items() if np.float32(v) <= lim]
+    assert (W, w) in times and (W, w) == min(near)
     assert (64, 64) in times and (128, 64) in times and (288, 96) in times
 
     def run(**kw):
@@ -267,15 +270,17 @@ def test_tau00_lmax4_spin_blocks(ozk_mod, handle, S, nb):
 
 
 def test_autotuned_panel_width_is_cached_and_used(ozk_mod):
-    """kkr_tau00_autotune times every nb = b, 2b, ..., 112 and caches the fastest; nb = 0 then
-    runs exactly that nb (bitwise equal results)."""
+    """kkr_tau00_autotune times every nb = b, 2b, ..., 112 and caches the smallest nb within 1 %
+    of the fastest; nb = 0 then runs exactly that nb (bitwise equal results)."""
     import torch
     h = ozk_mod.Handle()
     sizes = [27, 15, 27]
     systems = [_system(L, 0.5 + 0.05j, atom=i) for i, L in enumerate(sizes)]
     best, times = ozk_mod.kkr_tau00_autotune(h, [L * 16 for L in sizes], 16, S=7)
     assert sorted(times) == list(range(16, 113, 16)) and best in times
-    assert all(v > 0 for v in times.values()) and times[best] == min(times.values())
+    assert all(v > 0 for v in times.values())
+    lim = np.float32(1.01) * np.float32(min(times.values()))    # as the library compares
+    assert best == min(c for c, v in times.items() if np.float32(v) <= lim)
 
     def run(nb):
         Ms = [ozk_mod.colmajor_cuda(M) for t, G, M in systems]
