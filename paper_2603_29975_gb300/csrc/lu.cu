@@ -218,7 +218,7 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 }
 
 __global__ void __launch_bounds__(GJINV_THREADS)
-gjinv_kernel(const GjParams p) {
+gjinv_kernel(const GjParams p, int skip_lo, int skip_hi) {
   extern __shared__ double2 A[];            // [w][w] column major
   __shared__ double2 colk[GJINV_MAX];
   __shared__ int perm[GJINV_MAX];
@@ -228,7 +228,7 @@ gjinv_kernel(const GjParams p) {
   const int z = blockIdx.x;
   const bool single = p.D == nullptr;
   const int w = single ? p.nb1 : p.nb[z];
-  if (w <= 0) return;
+  if (w <= 0 || (w > skip_lo && w <= skip_hi)) return;  // those blocks: gjinv_reg_kernel
   const double2* D = single ? p.D1 : p.D[z];
   const long long ldd = single ? p.ldd1 : p.ldd[z];
   double2* X = single ? p.X1 : p.X[z];
@@ -334,9 +334,12 @@ gjinv_kernel(const GjParams p) {
 // w^3 complex multiply-adds per block, as in gjinv_kernel; 350 against 423 us per 64 x 64
 // block on one SM.  Its 128 registers a thread fill half of an SM's register file, so two
 // such CTAs on one SM leave no room for the side stream's split CTAs that run beside the
-// shared-memory kernel: it serves launches of at most one block per SM.
+// shared-memory kernel: it serves launches of at most one block per SM.  Rows at or beyond w
+// are skipped, but a warp spans 32 columns whatever w is, so narrower blocks (w = 48: 3/4 of
+// the lanes busy) stay with the shared-memory kernel.
 constexpr int GJR_THREADS = 256;
 constexpr int GJR_W = 64;
+constexpr int GJR_MIN_W = 56;                   // narrower blocks stay with gjinv_kernel
 constexpr int GJR_RG = GJR_THREADS / GJR_W;     // row groups
 constexpr int GJR_RPT = GJR_W / GJR_RG;         // rows per thread
 
@@ -360,7 +363,7 @@ gjinv_reg_kernel(const GjParams p) {
   const int z = blockIdx.x;
   const bool single = p.D == nullptr;
   const int w = single ? p.nb1 : p.nb[z];
-  if (w <= 0) return;
+  if (w <= GJR_MIN_W || w > GJR_W) return;             // gjinv_kernel's blocks
   const double2* D = single ? p.D1 : p.D[z];
   const long long ldd = single ? p.ldd1 : p.ldd[z];
   double2* X = single ? p.X1 : p.X[z];
@@ -422,6 +425,7 @@ gjinv_reg_kernel(const GjParams p) {
 #pragma unroll
     for (int c = 0; c < GJR_RPT; ++c) {
       const int i = rb + GJR_RG * c;
+      if (i >= w || j >= w) continue;                   // padding (i is uniform across a warp)
       const double2 f = colk[i];
       double2 y = colK ? make_double2(0.0, 0.0) : (i == piv ? ok : a[c]);
       y.x = fma(-f.x, x.x, y.x);
@@ -617,15 +621,21 @@ void launch_tri_inv(const double2* T, long long ldt, int r, int upper, int unit,
 }
 
 void launch_gjinv(const GjParams& p, int max_w, int batch, cudaStream_t st) {
-  if (max_w <= GJR_W && batch <= gpu_sm_count()) {
+  // the register form takes the blocks of order 56 < w <= 64 when every block of the launch
+  // has an SM to itself, the shared-memory kernel the others; which form inverts a block
+  // depends on its own order and the launch's size only, so a block comes out the same alone
+  // and in a small batch
+  const bool single = p.D == nullptr;                      // one block, of order max_w
+  const bool reg = max_w > GJR_MIN_W && batch <= gpu_sm_count() && (!single || max_w <= GJR_W);
+  if (reg) {
     gjinv_reg_kernel<<<batch, GJR_THREADS, 0, st>>>(p);
     record_launch();
-    return;
+    if (single) return;
   }
   const size_t smem = sizeof(double2) * static_cast<size_t>(max_w) * max_w;
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(gjinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  gjinv_kernel<<<batch, GJINV_THREADS, smem, st>>>(p);
+  gjinv_kernel<<<batch, GJINV_THREADS, smem, st>>>(p, reg ? GJR_MIN_W : 0, reg ? GJR_W : 0);
   record_launch();
 }
 
