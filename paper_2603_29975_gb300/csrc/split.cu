@@ -91,15 +91,115 @@ __device__ __forceinline__ void split_run(const SplitParams& p, const double2* v
   }
 }
 
+// The same digits for a compile-time slice count SF (nbits = 8 SF - 1, 64-bit images), with
+// no dependent chain per digit.  With C = 128 (1 + 256 + ... + 256^(SF-2)), Y = X + C holds
+// the balanced digits d_s + 128 of the SF - 1 lower places as its low bytes and the top digit
+// as Y >> 8 (SF - 1): X = sum_s d_s 256^s with every lower d_s in [-128, 127], so adding 128
+// at each lower place lifts it into [0, 255] without carries, and base-256 digits are unique.
+// Plane SF - 1 - s takes byte s of Y.  Two elements' bytes go into the halves of one word,
+// offset by 0x6580 = (bit pattern of 1536 in binary16) - 128, which makes each half the bit
+// pattern of 1536 + d (the binade [1024, 2048) has unit spacing); one packed subtraction of
+// 1536 leaves d, and subtracting the word from 1536 leaves -d, both exact (+0 for d = 0, as
+// the int -> half conversion gives).  The top digit (|d| <= 128) takes the offset 0x6600.
+__host__ __device__ constexpr long long digit_bias(int S) {
+  long long c = 0;
+  for (int s = 0; s < S - 1; ++s) c = c * 256 + 128;
+  return c;
+}
+
+struct Y64 { uint32_t lo, hi; };
+
+// biased binary16 pair (bit patterns of 1536 + d) of plane `s` for two elements
+template <int SF>
+__device__ __forceinline__ uint32_t biased_pair(int s, Y64 a, Y64 b) {
+  if (s > 0) {
+    const int k = SF - 1 - s;                               // byte of Y, 0 .. SF - 2
+    const uint32_t wa = k < 4 ? a.lo : a.hi, wb = k < 4 ? b.lo : b.hi;
+    const uint32_t kk = static_cast<uint32_t>(k & 3);
+    const uint32_t w = __byte_perm(wa, wb, kk | ((kk + 4u) << 8));
+    return (w & 0x00FF00FFu) + 0x65806580u;
+  }
+  constexpr int sh = 8 * (SF - 1);
+  const long long ya = static_cast<long long>((static_cast<unsigned long long>(a.hi) << 32) | a.lo);
+  const long long yb = static_cast<long long>((static_cast<unsigned long long>(b.hi) << 32) | b.lo);
+  const uint32_t ta = static_cast<uint32_t>(static_cast<int>(ya >> sh) + 0x6600);
+  const uint32_t tb = static_cast<uint32_t>(static_cast<int>(yb >> sh) + 0x6600);
+  return __byte_perm(ta, tb, 0x5410);
+}
+
+__device__ __forceinline__ uint32_t half2_bits(__half2 h) {
+  return static_cast<uint32_t>(__half_as_ushort(__low2half(h))) |
+         (static_cast<uint32_t>(__half_as_ushort(__high2half(h))) << 16);
+}
+__device__ __forceinline__ __half2 bits_half2(uint32_t w) {
+  return __halves2half2(__ushort_as_half(static_cast<unsigned short>(w & 0xFFFFu)),
+                        __ushort_as_half(static_cast<unsigned short>(w >> 16)));
+}
+// d (NEG: -d) of both halves of a biased pair
+template <bool NEG>
+__device__ __forceinline__ uint32_t pair_digits(uint32_t biased) {
+  const __half2 k1536 = __half2half2(__ushort_as_half(0x6600));
+  return half2_bits(NEG ? __hsub2(k1536, bits_half2(biased)) : __hsub2(bits_half2(biased), k1536));
+}
+
+template <int NW>
+__device__ __forceinline__ void store_words(__half* dst, const uint32_t (&w)[NW]) {
+  if constexpr (NW == 4) *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+  else if constexpr (NW == 2) *reinterpret_cast<uint2*>(dst) = make_uint2(w[0], w[1]);
+  else *reinterpret_cast<uint32_t*>(dst) = w[0];
+}
+
+template <int PER, int SF>
+__device__ __forceinline__ void split_run_fixed(const SplitParams& p, const double2* v, int e, int r, int l, int K,
+                                                __half* outz, long long plane) {
+  static_assert(PER >= 2 && PER % 2 == 0, "pairs of elements");
+  constexpr long long C = digit_bias(SF);
+  constexpr int NW = PER / 2;
+  Y64 yr[PER], yi[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const unsigned long long a = static_cast<unsigned long long>(integer_image64(v[q].x, e, 8 * SF - 1) + C);
+    const unsigned long long b = static_cast<unsigned long long>(integer_image64(v[q].y, e, 8 * SF - 1) + C);
+    yr[q] = Y64{static_cast<uint32_t>(a), static_cast<uint32_t>(a >> 32)};
+    yi[q] = Y64{static_cast<uint32_t>(b), static_cast<uint32_t>(b >> 32)};
+  }
+#pragma unroll
+  for (int s = SF - 1; s >= 0; --s) {
+    uint32_t br[NW], bi[NW], dr[NW], di[NW];
+#pragma unroll
+    for (int h = 0; h < NW; ++h) {
+      br[h] = biased_pair<SF>(s, yr[2 * h], yr[2 * h + 1]);
+      bi[h] = biased_pair<SF>(s, yi[2 * h], yi[2 * h + 1]);
+      dr[h] = pair_digits<false>(br[h]);
+      di[h] = pair_digits<false>(bi[h]);
+    }
+    __half* o = outz + s * plane;
+    if (p.side == 0) {
+      store_words<NW>(o + static_cast<long long>(r) * p.kpad + l, dr);
+      store_words<NW>(o + static_cast<long long>(r) * p.kpad + K + l, di);
+    } else {
+      uint32_t ni[NW];
+#pragma unroll
+      for (int h = 0; h < NW; ++h) ni[h] = pair_digits<true>(bi[h]);
+      const long long row0 = 2LL * r, row1 = 2LL * r + 1;
+      store_words<NW>(o + row0 * p.kpad + l, dr);
+      store_words<NW>(o + row0 * p.kpad + K + l, ni);
+      store_words<NW>(o + row1 * p.kpad + l, di);
+      store_words<NW>(o + row1 * p.kpad + K + l, dr);
+    }
+  }
+}
+
 // Both operands of one emulated GEMM in one launch: blockIdx.z selects the side.  VEC: the
 // widest digit run stored as one vector (8 in general; 2 for K <= 16, where the runs are 2 wide
 // and the smaller register footprint keeps more CTAs resident).  W64: 64-bit integer images
 // (S <= 7).  Rows of at most SPLIT_TK elements (every panel operand of the block LU) are read
 // from global memory once: the tile is loaded, the row maxima are taken from it, then the
 // digits; longer rows take a scan pass and then the tiles one by one.
-template <int VEC, bool W64>
+template <int VEC, bool W64, int SF = 0>
 __global__ void __launch_bounds__(SPLIT_THREADS, VEC == 2 ? (W64 ? 5 : 4) : (W64 ? 4 : 2))
 split_kernel(const SplitPair pp) {
+  static_assert(SF == 0 || (W64 && VEC == 8), "compile-time slice counts: 64-bit images, 8-wide runs");
   if (static_cast<int>(blockIdx.z) >= pp.nsides) return;
   const SplitParams& p = pp.s[blockIdx.z];
   const int z = blockIdx.y;
@@ -249,7 +349,11 @@ split_kernel(const SplitPair pp) {
                        l0 + per <= K;
       if (r < R && vec) {
         const int e = rowexp[rl];
-        if constexpr (VEC >= 8) {
+        if constexpr (SF > 0) {
+          if (per == 8) split_run_fixed<8, SF>(p, &tile[rl][lg], e, r, l0, K, outz, plane);
+          else if (per == 4) split_run_fixed<4, SF>(p, &tile[rl][lg], e, r, l0, K, outz, plane);
+          else split_run_fixed<2, SF>(p, &tile[rl][lg], e, r, l0, K, outz, plane);
+        } else if constexpr (VEC >= 8) {
           if (per == 8) split_run<8, W64>(p, &tile[rl][lg], e, r, l0, K, outz, plane);
           else if (per == 4) split_run<4, W64>(p, &tile[rl][lg], e, r, l0, K, outz, plane);
           else split_run<2, W64>(p, &tile[rl][lg], e, r, l0, K, outz, plane);
@@ -383,7 +487,16 @@ void launch_split(const SplitParams& a, int rows_a, const SplitParams* b, int ro
     if (w64) split_kernel<2, true><<<grid, SPLIT_THREADS, 0, st>>>(pp);
     else split_kernel<2, false><<<grid, SPLIT_THREADS, 0, st>>>(pp);
   } else {
-    if (w64) split_kernel<8, true><<<grid, SPLIT_THREADS, 0, st>>>(pp);
+    // compile-time slice counts for the common S = 7 and S = 5 (nbits = 8 S - 1 on every side)
+    int sf = 0;
+    for (int S : {7, 5}) {
+      bool all = true;
+      for (int sd = 0; sd < pp.nsides; ++sd) all = all && pp.s[sd].S == S && pp.s[sd].nbits == 8 * S - 1;
+      if (all) { sf = S; break; }
+    }
+    if (sf == 7) split_kernel<8, true, 7><<<grid, SPLIT_THREADS, 0, st>>>(pp);
+    else if (sf == 5) split_kernel<8, true, 5><<<grid, SPLIT_THREADS, 0, st>>>(pp);
+    else if (w64) split_kernel<8, true><<<grid, SPLIT_THREADS, 0, st>>>(pp);
     else split_kernel<8, false><<<grid, SPLIT_THREADS, 0, st>>>(pp);
   }
   record_launch();

@@ -78,6 +78,38 @@ def test_group_sums_extreme_digits(ozk_mod, handle):
         assert np.array_equal(G[g - 2], ref[g])
 
 
+@pytest.mark.parametrize("S", [5, 7])
+@pytest.mark.parametrize("k", [64, 128, 200])
+def test_fixed_slice_count_split_bit_exact(ozk_mod, handle, S, k):
+    """S = 5 and S = 7 split with compile-time slice counts (every digit one byte of the
+    biased integer image, turned into binary16 by a packed subtraction): the product of
+    operands whose rows hold the extreme digits (top digit 128 from 1 - 2^-53 at the row
+    maximum, alternating signs, zeros of both signs, subnormals next to normal values) is
+    bit-exact against the oracle; K a multiple of 8 so that every run is 8 wide, and a ragged
+    last tile at k = 200."""
+    rng = np.random.default_rng(100 + S + k)
+    m, n = 96, 80
+    big = 0.9999999999999999
+    A = rand_complex(m, k, seed=31 + S)
+    B = rand_complex(k, n, seed=32 + S)
+    A[0, :] = big - big * 1j
+    A[1, :] = 0.0
+    A[1, ::2] = -0.0 + 0.0j
+    A[2, :] = 5e-324 * (1 + 1j)
+    A[2, 5] = big + 0j
+    A[3, :] = big * np.where(np.arange(k) % 2, 1.0, -1.0) * (1 - 1j)
+    A[4, :] = rng.integers(-3, 4, k) * 2.0 ** -20 + 1j * rng.integers(-3, 4, k)
+    B[:, 0] = -big + big * 1j
+    B[:, 1] = 0.0
+    B[:, 2] = np.ldexp(1.0, -1022) * (1 - 1j)
+    B[7, 2] = -big * 1j
+    B[:, 3] = big * np.where(np.arange(k) % 3, -1.0, 1.0) * (1 + 1j)
+    C = ozk_mod.colmajor_cuda(np.zeros((m, n), dtype=np.complex128))
+    ozk_mod.ozaki_zgemm(handle, _dev(ozk_mod, A), _dev(ozk_mod, B), C, S=S)
+    assert np.array_equal(ozk_mod.to_numpy(C), co.zgemm(A, B, S))
+    assert handle.status() == 0
+
+
 @pytest.mark.parametrize("S", [3, 5, 7, 9])
 @pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "C"), ("C", "T")])
 def test_zgemm_store_bit_exact(ozk_mod, handle, S, ta, tb):
