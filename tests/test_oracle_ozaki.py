@@ -83,6 +83,33 @@ def test_digit_reconstruction_invariant(S):
                 assert X[i, l] == int(exact)          # truncation toward zero
 
 
+@pytest.mark.parametrize("S", [2, 3, 5, 7, 8])
+def test_balanced_digits_are_bytes_of_the_biased_image(S):
+    """The identity the split's compile-time-S path rests on: with C = 128 (1 + 256 + ... +
+    256^(S-2)), the balanced digits of X below the top are the bytes of Y = X + C minus 128 and
+    the top digit is floor(Y / 256^(S-1)); and a digit d (|d| <= 511) is the binary16 value
+    whose bit pattern is 0x6600 + d minus 1536 (exactly, +0 for d = 0), -d the value 1536
+    minus it."""
+    rng = random.Random(40 + S)
+    lim = 2 ** (8 * S - 1) - 1
+    xs = [0, 1, -1, lim, -lim, 127, -128, 128, -129] + [rng.randint(-lim, lim) for _ in range(500)]
+    D = oz.balanced_digits(np.array(xs, dtype=object), S)
+    C = sum(128 * 256 ** t for t in range(S - 1))
+    for i, X in enumerate(xs):
+        Y = X + C
+        for t in range(1, S):                       # D[t]: place S - 1 - t from the bottom
+            assert int(D[t, i]) + 128 == (Y >> (8 * (S - 1 - t))) & 255
+        assert int(D[0, i]) == Y >> (8 * (S - 1))
+    d = np.arange(-511, 512)
+    biased = (0x6600 + d).astype(np.uint16).view(np.float16)
+    k = np.float16(1536)
+    assert k.view(np.uint16) == 0x6600
+    assert np.array_equal(((biased - k).astype(np.float16)).view(np.uint16), d.astype(np.float16).view(np.uint16))
+    neg = (k - biased).astype(np.float16)
+    assert np.array_equal(neg.astype(np.int64), -d)
+    assert neg[d == 0].view(np.uint16)[0] == 0      # +0, as the int -> half conversion gives
+
+
 def test_negated_imag_block_is_digitwise_negation():
     B = _rand(6, 5, 7)
     f, D = oz.split_right(B, 4)
