@@ -399,6 +399,46 @@ def test_k_parallel_split_matches_row_parallel_split(ozk_mod, handle):
     assert np.array_equal(got[keep], co.zgemm(A[keep], B, S))
 
 
+@pytest.mark.parametrize("S,ta,tb", [(7, "N", "N"), (7, "C", "T"), (5, "T", "C")])
+def test_many_row_blocks_split_bit_exact_on_sampled_rows(ozk_mod, handle, S, ta, tb):
+    """Operands of one K tile and thousands of row blocks (the split's one-tile path at full
+    occupancy): a 49152 x 64 x 64 product (left operand) and a 64 x 49152 x 64 product (right
+    operand), stored transposed or conjugated, bit-exact against the oracle on sampled rows
+    (columns), which the oracle computes from those rows (columns) alone."""
+    import torch
+    k, big = 64, 49152
+    rng = np.random.default_rng(7 + S)
+    for m, n in ((big, 64), (64, big)):
+        Aop = rand_complex(m, k, seed=51 + S)
+        Bop = rand_complex(k, n, seed=52 + S)
+        Aop[5, :] = 0.9999999999999999 * (1 - 1j)            # top digits 128
+        Bop[:, 6] = -0.9999999999999999 + 0.5j
+        C = ozk_mod.colmajor_cuda(np.zeros((m, n), dtype=np.complex128))
+        ozk_mod.ozaki_zgemm(handle, _dev(ozk_mod, stored(Aop, ta)), _dev(ozk_mod, stored(Bop, tb)), C, S=S,
+                            transa=ta, transb=tb)
+        assert handle.status() == 0
+        got = ozk_mod.to_numpy(C)
+        if m == big:
+            rows = np.concatenate([[0, 5, 31, 32, m - 1], rng.choice(m, 250, replace=False)])
+            assert np.array_equal(got[rows], co.zgemm(np.ascontiguousarray(Aop[rows]), Bop, S))
+        else:
+            cols = np.concatenate([[0, 6, 31, 32, n - 1], rng.choice(n, 250, replace=False)])
+            assert np.array_equal(got[:, cols], co.zgemm(Aop, np.ascontiguousarray(Bop[:, cols]), S))
+        del C
+        torch.cuda.empty_cache()
+
+
+def test_nonfinite_input_in_a_large_operand_sets_status(ozk_mod, handle):
+    """A NaN in one row of a 49152-row operand sets the status."""
+    A = rand_complex(49152, 64, 3)
+    A[40000, 17] = np.nan
+    B = rand_complex(64, 16, 4)
+    C = _dev(ozk_mod, np.zeros((49152, 16), dtype=np.complex128))
+    ozk_mod.ozaki_zgemm(handle, _dev(ozk_mod, A), _dev(ozk_mod, B), C, S=7)
+    assert handle.status() & (1 << 2)
+    assert handle.status() == 0
+
+
 def test_nonfinite_input_sets_status(ozk_mod, handle):
     A = rand_complex(20, 8, 1)
     A[4, 2] = np.nan
